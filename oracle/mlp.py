@@ -1,0 +1,164 @@
+"""Oracle: the GMC velocity network and flow-ODE sampler in FP64 (test
+infrastructure only).
+
+What it computes, in the paper's order:
+  * Eq. 8 -- a sample is x(1) of dx/dt = v_theta(x, t), x(0) ~ N(0, I),
+    integrated from t = 0 to 1 with a fixed number of steps (the paper times a
+    fixed-step ODE; here explicit Euler or the explicit midpoint rule).
+  * Eq. 10 / Eq. 11 -- the condition c is the entry state and cell in optical
+    coordinates and the state x is the exit state y = (p_exit, Omega_exit, s).
+    This build uses a square cell and directions on the unit circle, so
+    c = (xi_in, cos theta_in, sin theta_in, ln tau, c_scat) and
+    y = (p, cos theta_out, sin theta_out, ln s).
+  * v_theta is a plain feed-forward network: input [c_std (5), x (4),
+    emb(t) (16)], four hidden layers of width 256 with SiLU, linear output 4.
+    emb(t) = [sin(2^j pi t)]_{j<8} followed by [cos(2^j pi t)]_{j<8}.
+  * Decoding (the fourth stage of the transport algorithm): destandardize,
+    wrap p into [0,4), split it into face and position, renormalize the
+    direction, make it point out of the exit face, s = exp(ln s).
+
+Matrix products use numpy's matmul in float64 (a library primitive); nothing
+is blocked, fused or reordered beyond the definitions above.
+
+Weight file ("GMCW" version 1, little-endian):
+  char magic[4] = "GMCW"; u32 version; u32 n_layers = 5; u32 dims[6];
+  u32 n_cond, n_state, n_emb, flags;
+  f32 cond_mean[5], cond_std[5], y_mean[4], y_std[4];
+  then per layer l: f32 W_l[dims[l+1]][dims[l]] (out x in), f32 b_l[dims[l+1]].
+"""
+import struct
+
+import numpy as np
+
+N_COND = 5
+N_STATE = 4
+N_EMB = 16
+HIDDEN = 256
+DIMS = (N_COND + N_STATE + N_EMB, HIDDEN, HIDDEN, HIDDEN, HIDDEN, N_STATE)
+S_MIN = 1e-7
+
+
+class Net:
+    """FP64 copy of a weight file: W[l] (out x in), b[l], standardization."""
+
+    def __init__(self, W, b, cond_mean, cond_std, y_mean, y_std):
+        self.W = [np.asarray(w, dtype=np.float64) for w in W]
+        self.b = [np.asarray(v, dtype=np.float64) for v in b]
+        self.cond_mean = np.asarray(cond_mean, dtype=np.float64)
+        self.cond_std = np.asarray(cond_std, dtype=np.float64)
+        self.y_mean = np.asarray(y_mean, dtype=np.float64)
+        self.y_std = np.asarray(y_std, dtype=np.float64)
+
+
+def read_weights(path):
+    with open(path, "rb") as f:
+        blob = f.read()
+    if blob[:4] != b"GMCW":
+        raise ValueError("not a GMCW weight file")
+    version, n_layers = struct.unpack_from("<2I", blob, 4)
+    dims = struct.unpack_from("<6I", blob, 12)
+    n_cond, n_state, n_emb, _flags = struct.unpack_from("<4I", blob, 36)
+    if version != 1 or n_layers != 5 or tuple(dims) != DIMS or (n_cond, n_state, n_emb) != (
+            N_COND, N_STATE, N_EMB):
+        raise ValueError("unsupported weight file layout")
+    off = 52
+    stats = np.frombuffer(blob, dtype="<f4", count=18, offset=off).astype(np.float64)
+    off += 18 * 4
+    W, b = [], []
+    for l in range(5):
+        n_out, n_in = dims[l + 1], dims[l]
+        W.append(np.frombuffer(blob, dtype="<f4", count=n_out * n_in, offset=off)
+                 .reshape(n_out, n_in).astype(np.float64))
+        off += n_out * n_in * 4
+        b.append(np.frombuffer(blob, dtype="<f4", count=n_out, offset=off).astype(np.float64))
+        off += n_out * 4
+    if off != len(blob):
+        raise ValueError("weight file has trailing or missing bytes")
+    return Net(W, b, stats[0:5], stats[5:10], stats[10:14], stats[14:18])
+
+
+def time_embedding(t):
+    """emb(t) for t of shape [B] -> [B, 16]."""
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    freq = (2.0 ** np.arange(8)) * np.pi
+    ang = t[:, None] * freq[None, :]
+    return np.concatenate([np.sin(ang), np.cos(ang)], axis=1)
+
+
+def silu(z):
+    return z / (1.0 + np.exp(-z))
+
+
+def standardize_cond(net, cond):
+    """cond: [5, B] raw features -> [B, 5] standardized."""
+    cond = np.asarray(cond, dtype=np.float64)
+    return ((cond.T - net.cond_mean) / net.cond_std)
+
+
+def velocity(net, cn, x, t):
+    """v_theta(x, t | c): cn [B,5] standardized condition, x [B,4], t scalar or [B]."""
+    B = x.shape[0]
+    t = np.broadcast_to(np.asarray(t, dtype=np.float64), (B,))
+    h = np.concatenate([cn, x, time_embedding(t)], axis=1)
+    for l in range(4):
+        h = silu(h @ net.W[l].T + net.b[l])
+    return h @ net.W[4].T + net.b[4]
+
+
+def integrate(vfun, x0, steps, integrator="euler"):
+    """Fixed-step integration of dx/dt = vfun(x, t) from t = 0 to 1.
+
+    Euler:    x_{k+1} = x_k + h v(x_k, t_k)
+    midpoint: x_{k+1} = x_k + h v(x_k + (h/2) v(x_k, t_k), t_k + h/2)
+    with h = 1/steps and t_k = k h.
+    """
+    x = np.array(x0, dtype=np.float64)
+    h = 1.0 / steps
+    for k in range(steps):
+        t = k * h
+        if integrator == "euler":
+            x = x + h * vfun(x, t)
+        elif integrator == "midpoint":
+            xm = x + 0.5 * h * vfun(x, t)
+            x = x + h * vfun(xm, t + 0.5 * h)
+        else:
+            raise ValueError(integrator)
+    return x
+
+
+def sample(net, cond, noise, steps, integrator="euler"):
+    """Eq. 8: x(1) from x(0) = noise ([4, B]) for raw conditions cond ([5, B]).
+
+    Returns the standardized x(1) as [4, B].
+    """
+    cn = standardize_cond(net, cond)
+    x0 = np.asarray(noise, dtype=np.float64).T
+    return integrate(lambda x, t: velocity(net, cn, x, t), x0, steps, integrator).T
+
+
+OUTWARD = np.array([[0.0, -1.0], [1.0, 0.0], [0.0, 1.0], [-1.0, 0.0]])
+
+
+def decode(net, y_raw):
+    """Standardized ODE output [4, B] -> exit state dict (canonical frame).
+
+    face in {0 bottom, 1 right, 2 top, 3 left}, q the counter-clockwise
+    position on that face, (ux, uy) a unit direction pointing out of the face,
+    s the track length in optical units (at least S_MIN).
+    """
+    y = np.asarray(y_raw, dtype=np.float64).T * net.y_std + net.y_mean
+    p = np.mod(y[:, 0], 4.0)
+    face = np.minimum(np.floor(p), 3.0).astype(np.int64)
+    q = np.clip(p - face, 0.0, 1.0)
+    ux, uy = y[:, 1].copy(), y[:, 2].copy()
+    norm = np.hypot(ux, uy)
+    n_out = OUTWARD[face]
+    zero = norm == 0.0
+    ux = np.where(zero, n_out[:, 0], ux / np.where(zero, 1.0, norm))
+    uy = np.where(zero, n_out[:, 1], uy / np.where(zero, 1.0, norm))
+    dot = ux * n_out[:, 0] + uy * n_out[:, 1]
+    inward = dot < 0.0
+    ux = np.where(inward, ux - 2.0 * dot * n_out[:, 0], ux)
+    uy = np.where(inward, uy - 2.0 * dot * n_out[:, 1], uy)
+    s = np.maximum(np.exp(y[:, 3]), S_MIN)
+    return {"face": face, "q": q, "ux": ux, "uy": uy, "s": s, "inward": inward}

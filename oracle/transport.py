@@ -1,0 +1,238 @@
+"""Oracle: cell transmissions and transport solves (test infrastructure only).
+
+* `transmit` -- the FP64 random-walk cell transmission of the Monte Carlo
+  method section (Eq. 4-6), canonical frame: entry on the left face at
+  y = xi tau with direction (cos, sin); analog (survival c) or implicit
+  capture. Implemented in C (walk.c).
+* `solve_analog` -- standard Monte Carlo with implicit capture on a grid,
+  one history at a time, track-length flux tally (Eq. 5-7). C (solve.c).
+* `solve_gmc` -- the four-stage GMC transport algorithm, one wave of live
+  particles at a time:
+    1. rotate each particle's state into the canonical left-entry frame;
+    2. draw z ~ N(0, I) and sample the exit state (or, for pinning the loop,
+       run the random walk in that frame instead);
+    3. attenuate by exp(-sigma_a s) and tally Delta w / (V sigma_a);
+    4. rotate the exit back to global coordinates and cross into the
+       neighbour; stop at the domain edge, roulette below the weight cutoff.
+  Births in a source cell are walked to their first face crossing with the
+  random walk (the paper's separate internal-source model is not built).
+
+Global faces use the same counter-clockwise numbering as a cell in its own
+frame: 0 = south (y-), 1 = east (x+), 2 = north (y+), 3 = west (x-). A
+particle entering through global face F is seen in the frame rotated by
+r = (F + 1) mod 4 quarter turns, which maps the canonical left face (3) onto
+F; canonical face f maps to global face (f + r) mod 4 with the same
+counter-clockwise parameter q, and directions rotate by r quarter turns.
+Crossing face G at parameter q enters the neighbour through face (G + 2) mod 4
+with canonical entry position xi = q.
+"""
+import ctypes
+
+import numpy as np
+
+from ._clib import lib
+from . import rng
+from . import mlp
+
+MODE_ANALOG = 0
+MODE_IMPLICIT = 1
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def transmit(xi, cos_in, sin_in, tau, c, mode, seed, ids=None, events=None, id0=0, ctr0=0):
+    """Batched canonical-frame random-walk transmission in FP64."""
+    xi, cos_in, sin_in, tau, c = (_c(a, np.float64) for a in (xi, cos_in, sin_in, tau, c))
+    n = xi.shape[0]
+    out = {k: np.zeros(n, dtype=np.float64) for k in ("q", "ux", "uy", "s")}
+    status = np.zeros(n, dtype=np.int32)
+    face = np.zeros(n, dtype=np.int32)
+    ncoll = np.zeros(n, dtype=np.int64)
+    if ids is None:
+        lib().orc_transmit_batch(n, xi.ctypes.data, cos_in.ctypes.data, sin_in.ctypes.data,
+                                 tau.ctypes.data, c.ctypes.data, mode, seed, id0, ctr0,
+                                 status.ctypes.data, face.ctypes.data, out["q"].ctypes.data,
+                                 out["ux"].ctypes.data, out["uy"].ctypes.data,
+                                 out["s"].ctypes.data, ncoll.ctypes.data)
+        ev = None
+    else:
+        ids = _c(ids, np.uint64)
+        events = _c(events, np.uint32)
+        ev = np.zeros(n, dtype=np.uint32)
+        lib().orc_transmit_ids(n, xi.ctypes.data, cos_in.ctypes.data, sin_in.ctypes.data,
+                               tau.ctypes.data, c.ctypes.data, mode, seed, ids.ctypes.data,
+                               events.ctypes.data, status.ctypes.data, face.ctypes.data,
+                               out["q"].ctypes.data, out["ux"].ctypes.data,
+                               out["uy"].ctypes.data, out["s"].ctypes.data, ncoll.ctypes.data,
+                               ev.ctypes.data)
+    out.update(status=status, face=face, ncoll=ncoll, events=ev)
+    return out
+
+
+def walk_one(tau, c, mode, x, y, ux, uy, seed, pid, event0):
+    """One random walk from an arbitrary point (cell frame, optical units)."""
+    status = ctypes.c_int32()
+    face = ctypes.c_int32()
+    ncoll = ctypes.c_int64()
+    ev = ctypes.c_uint32()
+    out = np.zeros(6, dtype=np.float64)
+    lib().orc_walk_one(float(tau), float(c), mode, float(x), float(y), float(ux), float(uy),
+                       seed, int(pid), int(event0), ctypes.byref(status), ctypes.byref(face),
+                       out.ctypes.data, ctypes.byref(ncoll), ctypes.byref(ev))
+    return {"status": status.value, "face": face.value, "q": out[0], "x": out[1], "y": out[2],
+            "ux": out[3], "uy": out[4], "s": out[5], "ncoll": ncoll.value, "event": ev.value}
+
+
+def solve_analog(tau, c, src, n_hist, seed, w_cut=1e-4, p_survive=0.1):
+    """Standard MC solve; tau, c, src are [ny, nx]. Returns (flux [ny, nx], stats dict)."""
+    tau, c, src = (_c(a, np.float64) for a in (tau, c, src))
+    ny, nx = tau.shape
+    flux = np.zeros((ny, nx), dtype=np.float64)
+    st = np.zeros(6, dtype=np.float64)
+    rc = lib().orc_solve_analog(nx, ny, tau.ctypes.data, c.ctypes.data, src.ctypes.data,
+                                n_hist, seed, w_cut, p_survive, flux.ctypes.data, st.ctypes.data)
+    if rc != 0:
+        raise ValueError("orc_solve_analog failed: %d" % rc)
+    return flux, _stats(st)
+
+
+def _stats(st):
+    return {"leak": st[0], "absorbed": st[1], "roulette_net": st[2], "transmissions": st[3],
+            "collisions": st[4], "roulette_kills": st[5]}
+
+
+def rot(ux, uy, k):
+    """Rotate direction(s) by k quarter turns counter-clockwise."""
+    k = np.mod(k, 4)
+    rx = np.select([k == 0, k == 1, k == 2, k == 3], [ux, -uy, -ux, uy])
+    ry = np.select([k == 0, k == 1, k == 2, k == 3], [uy, ux, -uy, -ux])
+    return rx, ry
+
+
+def deposit(w, s, tau, c):
+    """Delta w of Eq. 6 and the Eq. 7 flux score for track length s (optical units)."""
+    a = 1.0 - c
+    pos = a > 0.0
+    a_safe = np.where(pos, a, 1.0)
+    dw = np.where(pos, w * (-np.expm1(-a_safe * s)), 0.0)
+    score = np.where(pos, dw / (a_safe * tau), w * s / tau)
+    return dw, score
+
+
+def mlp_sampler(net, steps, integrator, seed):
+    """Stage 2 with the flow ODE: noise at (id, event, TAG_NOISE), one event used."""
+    def f(xi, cos_c, sin_c, tau, c, ids, events):
+        cond = np.stack([xi, cos_c, sin_c, np.log(tau), c])
+        z = rng.normals_for(seed, ids, events, rng.TAG_NOISE)
+        d = mlp.decode(net, mlp.sample(net, cond, z, steps, integrator))
+        return d["face"], d["q"], d["ux"], d["uy"], d["s"], np.asarray(events, np.uint32) + 1
+    return f
+
+
+def walk_sampler(seed):
+    """Stage 2 replaced by the implicit-capture random walk in the canonical frame."""
+    def f(xi, cos_c, sin_c, tau, c, ids, events):
+        r = transmit(xi, cos_c, sin_c, tau, c, MODE_IMPLICIT, seed, ids=ids, events=events)
+        return r["face"], r["q"], r["ux"], r["uy"], r["s"], r["events"]
+    return f
+
+
+def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max_waves=100000):
+    """Event-based GMC solve; tau, c, src are [ny, nx]. Returns (flux, stats)."""
+    tau = np.asarray(tau, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
+    ny, nx = tau.shape
+    tf, cf = tau.ravel(), c.ravel()
+    flux = np.zeros(ny * nx, dtype=np.float64)
+    st = np.zeros(6, dtype=np.float64)
+    srcf = np.maximum(np.asarray(src, dtype=np.float64).ravel(), 0.0)
+    cdf = np.cumsum(srcf)
+    total = cdf[-1]
+    ids = np.arange(n_hist, dtype=np.uint64)
+    ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
+    cells = np.searchsorted(cdf, ub[0] * total, side="left")
+
+    # Births: walk from the birth point to the first face crossing (cell frame).
+    live = {k: [] for k in ("id", "i", "j", "F", "xi", "gx", "gy", "w", "ev")}
+    for h in range(n_hist):
+        k = int(cells[h])
+        i, j = k % nx, k // nx
+        t, cc = tf[k], cf[k]
+        ang = 2.0 * np.pi * ub[3, h]
+        r = walk_one(t, cc, MODE_IMPLICIT, ub[1, h] * t, ub[2, h] * t, np.cos(ang), np.sin(ang),
+                     seed, h, 0)
+        st[3] += 1
+        st[4] += r["ncoll"]
+        dw, score = deposit(1.0, r["s"], t, cc)
+        flux[k] += score
+        st[1] += dw
+        w = 1.0 - dw
+        w, alive = _roulette(seed, np.array([h], np.uint64), np.array([r["event"]], np.uint32),
+                             np.array([w]), w_cut, p_survive, st)
+        if not alive[0]:
+            continue
+        _advance_one(live, h, i, j, r["face"], r["q"], r["ux"], r["uy"], w[0], r["event"],
+                     nx, ny, st)
+    L = {k: np.asarray(v) for k, v in live.items()}
+    L["id"] = L["id"].astype(np.uint64)
+    L["ev"] = L["ev"].astype(np.uint32)
+    for L_i in ("i", "j", "F"):
+        L[L_i] = L[L_i].astype(np.int64)
+
+    waves = 0
+    while L["id"].size > 0:
+        waves += 1
+        if waves > max_waves:
+            raise RuntimeError("too many waves")
+        cell = L["j"] * nx + L["i"]
+        t, cc = tf[cell], cf[cell]
+        rr = np.mod(L["F"] + 1, 4)
+        cx, cy = rot(L["gx"], L["gy"], -rr)
+        face, q, ux, uy, s, ev = sampler(L["xi"], cx, cy, t, cc, L["id"], L["ev"])
+        st[3] += cell.size
+        dw, score = deposit(L["w"], s, t, cc)
+        np.add.at(flux, cell, score)
+        st[1] += dw.sum()
+        w = L["w"] - dw
+        w, alive = _roulette(seed, L["id"], ev, w, w_cut, p_survive, st)
+        G = np.mod(np.asarray(face) + rr, 4)
+        gx, gy = rot(ux, uy, rr)
+        ni = L["i"] + np.where(G == 1, 1, 0) - np.where(G == 3, 1, 0)
+        nj = L["j"] + np.where(G == 2, 1, 0) - np.where(G == 0, 1, 0)
+        inside = (ni >= 0) & (ni < nx) & (nj >= 0) & (nj < ny)
+        st[0] += w[alive & ~inside].sum()
+        keep = alive & inside
+        L = {"id": L["id"][keep], "i": ni[keep], "j": nj[keep], "F": np.mod(G[keep] + 2, 4),
+             "xi": np.asarray(q)[keep], "gx": gx[keep], "gy": gy[keep], "w": w[keep],
+             "ev": np.asarray(ev, np.uint32)[keep]}
+    stats = _stats(st)
+    stats["waves"] = waves
+    return (flux / n_hist).reshape(ny, nx), stats
+
+
+def _roulette(seed, ids, events, w, w_cut, p_survive, st):
+    w = np.asarray(w, dtype=np.float64).copy()
+    alive = np.ones(w.shape, dtype=bool)
+    low = w < w_cut
+    if low.any():
+        u = rng.uniforms_for(seed, ids[low], events[low], rng.TAG_ROULETTE)[0]
+        surv = u <= p_survive
+        wl = w[low]
+        st[2] += np.sum(np.where(surv, wl / p_survive - wl, -wl))
+        st[5] += np.sum(~surv)
+        w[low] = np.where(surv, wl / p_survive, wl)
+        alive[np.flatnonzero(low)[~surv]] = False
+    return w, alive
+
+
+def _advance_one(live, h, i, j, G, q, gx, gy, w, ev, nx, ny, st):
+    ni = i + (1 if G == 1 else 0) - (1 if G == 3 else 0)
+    nj = j + (1 if G == 2 else 0) - (1 if G == 0 else 0)
+    if not (0 <= ni < nx and 0 <= nj < ny):
+        st[0] += w
+        return
+    for k, v in (("id", h), ("i", ni), ("j", nj), ("F", (G + 2) % 4), ("xi", q), ("gx", gx),
+                 ("gy", gy), ("w", w), ("ev", ev)):
+        live[k].append(v)

@@ -1,0 +1,164 @@
+/*
+ * Oracle: random-walk cell transmission in FP64 (test infrastructure only).
+ *
+ * Follows the Monte Carlo method section of the paper: a particle streams
+ * along its direction until it either scatters or reaches the cell boundary;
+ * the free-flight length is d_s = -ln(xi)/sigma (Eq. 4) with xi in (0,1], the
+ * step is min(d_b, d_s), a scattering draws a new direction from the
+ * (isotropic) kernel, and the track length in the cell accumulates to
+ * Delta s_tot (Eq. 5-7).
+ *
+ * Two absorption modes:
+ *  - IMPLICIT (implicit capture, as the paper uses): flights are sampled with
+ *    the scattering cross section, sigma = c in optical units; the particle is
+ *    never killed, its weight is attenuated afterwards by exp(-(1-c) s) (Eq. 5).
+ *  - ANALOG (discrete absorption, the plain method GMC replaces): flights are
+ *    sampled with sigma_t = 1; at each collision the particle survives with
+ *    probability c, otherwise it is absorbed there.
+ *
+ * Random numbers: one Philox draw (4 uniforms) per flight, at counter
+ * (id, event, TAG_WALK): u0 -> flight length, u1 -> survival test (analog
+ * mode: survive iff u1 <= c), u2 -> new direction angle 2*pi*u2.
+ */
+#include <math.h>
+#include <stdint.h>
+#include "oracle.h"
+
+static const double ORC_TWO_PI = 6.283185307179586476925286766559;
+
+static void exit_point(double tau, int face, double x, double y, orc_walk_result *res)
+{
+    double q;
+    switch (face) {
+    case 0: q = x / tau; y = 0.0; break;
+    case 1: q = y / tau; x = tau; break;
+    case 2: q = (tau - x) / tau; y = tau; break;
+    default: q = (tau - y) / tau; x = 0.0; break;
+    }
+    if (q < 0.0) q = 0.0;
+    if (q > 1.0) q = 1.0;
+    res->face = face;
+    res->q = q;
+    res->x = x;
+    res->y = y;
+}
+
+void orc_walk_box(double tau, double c, int mode, double x, double y, double ux, double uy,
+                  uint64_t seed, uint64_t id, uint32_t event0, orc_walk_result *res)
+{
+    const double rate = (mode == ORC_MODE_IMPLICIT) ? c : 1.0;
+    uint32_t event = event0;
+    double s = 0.0;
+    int64_t ncoll = 0;
+    for (;;) {
+        double u[4];
+        orc_uniform4(seed, id, event, ORC_TAG_WALK, u);
+        ++event;
+        double d = (rate > 0.0) ? -log(u[0]) / rate : INFINITY;
+        double dbx = INFINITY, dby = INFINITY;
+        if (ux > 0.0) dbx = (tau - x) / ux;
+        else if (ux < 0.0) dbx = -x / ux;
+        if (uy > 0.0) dby = (tau - y) / uy;
+        else if (uy < 0.0) dby = -y / uy;
+        double db = dbx <= dby ? dbx : dby;
+        if (d >= db) {
+            /* streams to the boundary: the x-face wins exact corner ties */
+            s += db;
+            double xe = x + db * ux, ye = y + db * uy;
+            int face = (dbx <= dby) ? (ux > 0.0 ? 1 : 3) : (uy > 0.0 ? 2 : 0);
+            exit_point(tau, face, xe, ye, res);
+            res->status = ORC_EXITED;
+            res->ux = ux;
+            res->uy = uy;
+            break;
+        }
+        s += d;
+        x += d * ux;
+        y += d * uy;
+        ++ncoll;
+        if (mode == ORC_MODE_ANALOG && u[1] > c) {
+            res->status = ORC_ABSORBED;
+            res->face = -1;
+            res->q = 0.0;
+            res->x = x;
+            res->y = y;
+            res->ux = ux;
+            res->uy = uy;
+            break;
+        }
+        double phi = ORC_TWO_PI * u[2];
+        ux = cos(phi);
+        uy = sin(phi);
+    }
+    res->s = s;
+    res->ncoll = ncoll;
+    res->event = event;
+}
+
+/*
+ * Batched canonical-frame transmission: particle i enters the left face at
+ * y = xi[i]*tau[i] with direction (cos_in[i], sin_in[i]); Philox id = id0+i,
+ * first event ctr0. Outputs are arrays of length n.
+ */
+void orc_transmit_batch(int64_t n, const double *xi, const double *cos_in, const double *sin_in,
+                        const double *tau, const double *c, int mode, uint64_t seed, uint64_t id0,
+                        uint32_t ctr0, int32_t *status, int32_t *face, double *q, double *ux,
+                        double *uy, double *s, int64_t *ncoll)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        orc_walk_result r;
+        orc_walk_box(tau[i], c[i], mode, 0.0, xi[i] * tau[i], cos_in[i], sin_in[i], seed,
+                     id0 + (uint64_t)i, ctr0, &r);
+        status[i] = r.status;
+        face[i] = r.face;
+        q[i] = r.q;
+        ux[i] = r.ux;
+        uy[i] = r.uy;
+        s[i] = r.s;
+        ncoll[i] = r.ncoll;
+    }
+}
+
+/* Single general walk, exposed for the Python event-loop oracle. */
+void orc_walk_one(double tau, double c, int mode, double x, double y, double ux, double uy,
+                  uint64_t seed, uint64_t id, uint32_t event0, int32_t *status, int32_t *face,
+                  double *out /* q, x, y, ux, uy, s */, int64_t *ncoll, uint32_t *event)
+{
+    orc_walk_result r;
+    orc_walk_box(tau, c, mode, x, y, ux, uy, seed, id, event0, &r);
+    *status = r.status;
+    *face = r.face;
+    out[0] = r.q;
+    out[1] = r.x;
+    out[2] = r.y;
+    out[3] = r.ux;
+    out[4] = r.uy;
+    out[5] = r.s;
+    *ncoll = r.ncoll;
+    *event = r.event;
+}
+
+/*
+ * Canonical-frame transmission with per-particle Philox ids and first
+ * events; event_out[i] receives the next unused event counter.
+ */
+void orc_transmit_ids(int64_t n, const double *xi, const double *cos_in, const double *sin_in,
+                      const double *tau, const double *c, int mode, uint64_t seed,
+                      const uint64_t *ids, const uint32_t *events, int32_t *status, int32_t *face,
+                      double *q, double *ux, double *uy, double *s, int64_t *ncoll,
+                      uint32_t *event_out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        orc_walk_result r;
+        orc_walk_box(tau[i], c[i], mode, 0.0, xi[i] * tau[i], cos_in[i], sin_in[i], seed, ids[i],
+                     events[i], &r);
+        status[i] = r.status;
+        face[i] = r.face;
+        q[i] = r.q;
+        ux[i] = r.ux;
+        uy[i] = r.uy;
+        s[i] = r.s;
+        ncoll[i] = r.ncoll;
+        event_out[i] = r.event;
+    }
+}

@@ -1,0 +1,105 @@
+"""Seeded synthetic inputs for the tests and the benchmark.
+
+This module only draws inputs (cell entries, materials, noise, random network
+weights) and writes them in the agreed formats. It holds none of the method's
+arithmetic, and both the CUDA path's callers and the oracle's callers consume
+what it returns. Random numbers come from numpy's Philox bit generator keyed
+by the seed.
+
+Workload recipes (the paper's geometries and data are not available, so each
+input is drawn from the distributions the workload names):
+  * cell entries: xi ~ U[0,1), sin(theta) ~ U(-1,1) (an inward direction with
+    cosine-weighted density on the entry face), cos(theta) = sqrt(1 - sin^2);
+  * sampler conditions: tau log-uniform in [0.1, 1000], c uniform in
+    [0.5, 0.999], entries as above; condition vector
+    (xi, cos theta, sin theta, ln tau, c);
+  * network: 25 -> 256 -> 256 -> 256 -> 256 -> 4, weights Kaiming-normal
+    N(0, 2 / fan_in), zero biases, identity standardization;
+  * grid: n x n cells, tau log-uniform in [0.1, 500], c drawn from
+    {0.5, 0.999} per 16 x 16 block, unit source spread over the central 8 x 8
+    cells.
+"""
+import struct
+
+import numpy as np
+
+DIMS = (25, 256, 256, 256, 256, 4)
+
+
+def generator(seed):
+    return np.random.Generator(np.random.Philox(key=int(seed)))
+
+
+def cell_entries(n, seed):
+    """Entry states on the left face: dict of float32 arrays xi, cos, sin."""
+    g = generator(seed)
+    xi = g.random(n)
+    sn = g.uniform(-1.0, 1.0, n)
+    cs = np.sqrt(np.maximum(1.0 - sn * sn, 0.0))
+    return {"xi": xi.astype(np.float32), "cos": cs.astype(np.float32),
+            "sin": sn.astype(np.float32)}
+
+
+def materials(n, seed, tau_range=(0.1, 1000.0), c_range=(0.5, 0.999)):
+    """tau log-uniform and c uniform, float32."""
+    g = generator(seed)
+    lo, hi = np.log(tau_range[0]), np.log(tau_range[1])
+    tau = np.exp(g.uniform(lo, hi, n))
+    c = g.uniform(c_range[0], c_range[1], n)
+    return tau.astype(np.float32), c.astype(np.float32)
+
+
+def sampler_conditions(n, seed, tau_range=(0.1, 1000.0), c_range=(0.5, 0.999)):
+    """Condition vectors [5, n] float32: (xi, cos, sin, ln tau, c); plus tau and c."""
+    e = cell_entries(n, seed)
+    tau, c = materials(n, seed + 7919, tau_range, c_range)
+    cond = np.stack([e["xi"], e["cos"], e["sin"], np.log(tau).astype(np.float32), c])
+    return np.ascontiguousarray(cond, dtype=np.float32), tau, c
+
+
+def gaussian_noise(n, seed):
+    """Standard normal draws [4, n] float32."""
+    return np.ascontiguousarray(generator(seed).standard_normal((4, n)), dtype=np.float32)
+
+
+def kaiming_weights(seed=1):
+    """Kaiming-normal weights (fan-in), zero biases, identity standardization."""
+    g = generator(seed)
+    W, b = [], []
+    for l in range(5):
+        fan_in, fan_out = DIMS[l], DIMS[l + 1]
+        W.append((g.standard_normal((fan_out, fan_in)) * np.sqrt(2.0 / fan_in)).astype(np.float32))
+        b.append(np.zeros(fan_out, dtype=np.float32))
+    return {"W": W, "b": b, "cond_mean": np.zeros(5, np.float32), "cond_std": np.ones(5, np.float32),
+            "y_mean": np.zeros(4, np.float32), "y_std": np.ones(4, np.float32)}
+
+
+def write_weights(path, net):
+    """Write a dict like `kaiming_weights()` returns as a GMCW version-1 file."""
+    with open(path, "wb") as f:
+        f.write(b"GMCW")
+        f.write(struct.pack("<2I", 1, 5))
+        f.write(struct.pack("<6I", *DIMS))
+        f.write(struct.pack("<4I", 5, 4, 16, 0))
+        for k in ("cond_mean", "cond_std", "y_mean", "y_std"):
+            f.write(np.asarray(net[k], dtype="<f4").tobytes())
+        for l in range(5):
+            f.write(np.ascontiguousarray(net["W"][l], dtype="<f4").tobytes())
+            f.write(np.ascontiguousarray(net["b"][l], dtype="<f4").tobytes())
+
+
+def grid_problem(n=128, seed=2, tau_range=(0.1, 500.0), c_values=(0.5, 0.999), block=16,
+                 source=8):
+    """Heterogeneous n x n grid: tau [n,n], c [n,n], src [n,n] (float32, row = y index)."""
+    g = generator(seed)
+    lo, hi = np.log(tau_range[0]), np.log(tau_range[1])
+    tau = np.exp(g.uniform(lo, hi, (n, n)))
+    nb = (n + block - 1) // block
+    pick = g.integers(0, len(c_values), (nb, nb))
+    cb = np.asarray(c_values, dtype=np.float64)[pick]
+    c = np.kron(cb, np.ones((block, block)))[:n, :n]
+    src = np.zeros((n, n))
+    a = max((n - source) // 2, 0)
+    src[a:a + source, a:a + source] = 1.0
+    src /= src.sum()
+    return tau.astype(np.float32), c.astype(np.float32), src.astype(np.float32)

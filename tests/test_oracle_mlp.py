@@ -1,0 +1,174 @@
+"""Pins for the oracle's velocity network, flow-ODE integrator (Eq. 8) and
+exit-state decoding (Eq. 11)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp
+
+
+def _zero_net():
+    net = synth.kaiming_weights(1)
+    net["W"] = [np.zeros_like(w) for w in net["W"]]
+    return net
+
+
+def _load(tmp_path, net, name="w.bin"):
+    p = str(tmp_path / name)
+    synth.write_weights(p, net)
+    return mlp.read_weights(p)
+
+
+def test_weight_file_round_trip(tmp_path):
+    net = synth.kaiming_weights(1)
+    net["cond_mean"] = np.arange(5, dtype=np.float32)
+    net["y_std"] = np.array([1.5, 2.0, 2.5, 3.0], np.float32)
+    o = _load(tmp_path, net)
+    for l in range(5):
+        np.testing.assert_array_equal(o.W[l], net["W"][l].astype(np.float64))
+        np.testing.assert_array_equal(o.b[l], net["b"][l].astype(np.float64))
+    np.testing.assert_array_equal(o.cond_mean, np.arange(5))
+    np.testing.assert_array_equal(o.y_std, [1.5, 2.0, 2.5, 3.0])
+    # Kaiming-normal: per-layer sample std close to sqrt(2 / fan_in)
+    for l, fan_in in enumerate(synth.DIMS[:-1]):
+        if net["W"][l].size > 10000:
+            assert abs(net["W"][l].std() / math.sqrt(2.0 / fan_in) - 1) < 0.02
+
+
+def test_weight_file_rejects_garbage(tmp_path):
+    p = tmp_path / "bad.bin"
+    p.write_bytes(b"NOPE" + b"\0" * 64)
+    with pytest.raises(ValueError):
+        mlp.read_weights(str(p))
+
+
+def test_time_embedding_values():
+    e = mlp.time_embedding(np.array([0.0, 0.25]))
+    np.testing.assert_allclose(e[0], [0.0] * 8 + [1.0] * 8, atol=0)
+    expect = [math.sin(2 ** j * math.pi * 0.25) for j in range(8)] + \
+             [math.cos(2 ** j * math.pi * 0.25) for j in range(8)]
+    np.testing.assert_allclose(e[1], expect, atol=1e-15)
+
+
+@pytest.mark.parametrize("integrator", ["euler", "midpoint"])
+@pytest.mark.parametrize("steps", [1, 3, 16])
+def test_constant_velocity_is_exact(tmp_path, integrator, steps):
+    # All weights zero except the output bias: v = b5, so x(1) = x(0) + b5.
+    net = _zero_net()
+    net["b"][4] = np.array([0.5, -1.25, 2.0, 0.125], np.float32)
+    o = _load(tmp_path, net)
+    cond, _, _ = synth.sampler_conditions(64, 3)
+    z = synth.gaussian_noise(64, 4)
+    y = mlp.sample(o, cond, z, steps, integrator)
+    np.testing.assert_allclose(y, z.astype(np.float64) + net["b"][4][:, None].astype(np.float64),
+                               rtol=0, atol=1e-14)
+
+
+def _silu(z):
+    return z / (1.0 + math.exp(-z))
+
+
+def test_single_path_through_the_network(tmp_path):
+    # One chain of units: input column 5 (= x_0, after the 5 condition
+    # features) -> hidden unit 0 of every layer -> output 0. Then
+    # v_0 = silu^4(a x_0) and the other outputs are 0; K = 1 Euler gives
+    # x_0(1) = x_0 + silu^4(a x_0).
+    net = _zero_net()
+    a = float(np.float32(0.7))  # the file stores float32 weights
+    net["W"][0][0, 5] = a
+    for l in (1, 2, 3):
+        net["W"][l][0, 0] = 1.0
+    net["W"][4][0, 0] = 1.0
+    o = _load(tmp_path, net)
+    cond, _, _ = synth.sampler_conditions(8, 5)
+    z = synth.gaussian_noise(8, 6)
+    y = mlp.sample(o, cond, z, 1, "euler")
+    for i in range(8):
+        x0 = float(z[0, i])
+        expect = x0 + _silu(_silu(_silu(_silu(a * x0))))
+        assert abs(y[0, i] - expect) < 1e-14
+        np.testing.assert_allclose(y[1:, i], z[1:, i].astype(np.float64), atol=0)
+
+
+def test_condition_and_time_columns(tmp_path):
+    # Input order [cond(5), x(4), emb(16)] and condition standardization:
+    # hidden unit 0 reads standardized ln tau (column 3) and unit 1 reads
+    # emb column 9 + 2 = sin(4 pi t); the output sums the two chains.
+    net = _zero_net()
+    net["cond_mean"] = np.array([0, 0, 0, 1.5, 0], np.float32)
+    net["cond_std"] = np.array([1, 1, 1, 2.0, 1], np.float32)
+    net["W"][0][0, 3] = 1.0
+    net["W"][0][1, 9 + 2] = 1.0
+    for l in (1, 2, 3):
+        net["W"][l][0, 0] = 1.0
+        net["W"][l][1, 1] = 1.0
+    net["W"][4][2, 0] = 1.0
+    net["W"][4][3, 1] = 1.0
+    o = _load(tmp_path, net)
+    cond, _, _ = synth.sampler_conditions(4, 8)
+    z = synth.gaussian_noise(4, 9)
+    steps = 4
+    y = mlp.sample(o, cond, z, steps, "euler")
+    f4 = lambda v: _silu(_silu(_silu(_silu(v))))
+    for i in range(4):
+        u = (float(cond[3, i]) - 1.5) / 2.0
+        e2 = float(z[2, i]) + f4(u)
+        e3 = float(z[3, i]) + sum(f4(math.sin(4 * math.pi * k / steps)) for k in range(steps)) / steps
+        assert abs(y[2, i] - e2) < 1e-13 and abs(y[3, i] - e3) < 1e-13
+
+
+@pytest.mark.parametrize("steps", [1, 5, 16])
+def test_integrators_on_linear_field(steps):
+    # dx/dt = a x: Euler gives (1 + a h)^K x0, the midpoint rule
+    # (1 + a h + (a h)^2 / 2)^K x0.
+    a, h = -0.8, 1.0 / steps
+    x0 = np.array([[1.0, -2.0, 0.5, 3.0]])
+    ye = mlp.integrate(lambda x, t: a * x, x0, steps, "euler")
+    ym = mlp.integrate(lambda x, t: a * x, x0, steps, "midpoint")
+    np.testing.assert_allclose(ye, (1 + a * h) ** steps * x0, rtol=1e-14)
+    np.testing.assert_allclose(ym, (1 + a * h + 0.5 * (a * h) ** 2) ** steps * x0, rtol=1e-14)
+
+
+def test_integrators_on_time_field():
+    # dx/dt = cos(t): Euler is the left Riemann sum, midpoint the midpoint sum.
+    K = 8
+    ye = mlp.integrate(lambda x, t: np.cos(t) + 0 * x, np.zeros((1, 1)), K, "euler")
+    ym = mlp.integrate(lambda x, t: np.cos(t) + 0 * x, np.zeros((1, 1)), K, "midpoint")
+    assert abs(ye[0, 0] - sum(math.cos(k / K) for k in range(K)) / K) < 1e-15
+    assert abs(ym[0, 0] - sum(math.cos((k + 0.5) / K) for k in range(K)) / K) < 1e-15
+
+
+def test_decode_rules(tmp_path):
+    net = _zero_net()
+    net["y_mean"] = np.array([0, 0, 0, 0], np.float32)
+    net["y_std"] = np.array([1, 1, 1, 1], np.float32)
+    o = _load(tmp_path, net)
+    y = np.array([
+        [4.25, 0.0, 0.0, math.log(2.0)],      # wraps to bottom face, q = 0.25
+        [-0.5, -0.6, 0.8, 0.0],               # wraps to left face, q = 0.5
+        [1.5, -3.0, 4.0, -40.0],              # right face, inward -> reflected
+        [2.75, 0.6, -0.8, 1.0],               # top face, inward -> reflected
+    ]).T
+    d = mlp.decode(o, y)
+    np.testing.assert_array_equal(d["face"], [0, 3, 1, 2])
+    np.testing.assert_allclose(d["q"], [0.25, 0.5, 0.5, 0.75], atol=1e-15)
+    # zero direction -> outward normal of the bottom face
+    np.testing.assert_allclose([d["ux"][0], d["uy"][0]], [0.0, -1.0])
+    np.testing.assert_allclose([d["ux"][1], d["uy"][1]], [-0.6, 0.8])
+    np.testing.assert_allclose([d["ux"][2], d["uy"][2]], [0.6, 0.8])
+    np.testing.assert_allclose([d["ux"][3], d["uy"][3]], [0.6, 0.8])
+    np.testing.assert_array_equal(d["inward"], [False, False, True, True])
+    np.testing.assert_allclose(d["s"], [2.0, 1.0, mlp.S_MIN, math.e])
+
+
+def test_decode_destandardizes(tmp_path):
+    net = _zero_net()
+    net["y_mean"] = np.array([2.0, 0.0, 0.0, 1.0], np.float32)
+    net["y_std"] = np.array([0.5, 2.0, 2.0, 0.25], np.float32)
+    o = _load(tmp_path, net)
+    d = mlp.decode(o, np.array([[1.0], [0.3], [0.4], [-4.0]]))
+    assert d["face"][0] == 2 and abs(d["q"][0] - 0.5) < 1e-15
+    np.testing.assert_allclose([d["ux"][0], d["uy"][0]], [0.6, 0.8])
+    assert abs(d["s"][0] - 1.0) < 1e-15

@@ -1,0 +1,122 @@
+"""Pins for the oracle's transport solves (Eq. 5-7, Eq. 12 and the four-stage
+GMC loop)."""
+import math
+
+import numpy as np
+from scipy import integrate
+
+import synth
+from oracle import stats as ostats
+from oracle import transport as T
+
+
+def escape_expectation(tau):
+    """E[exp(-tau l)] for a uniform point in the unit square and an isotropic
+    direction, l the distance to the boundary. By the square's symmetry only
+    directions in (0, pi/2) are needed; with a, b the distances to the right
+    and top edges, l = min(a / cos, b / sin), and the b-integral is closed."""
+    def inner(a, th):
+        c, s = math.cos(th), math.sin(th)
+        m = a * math.tan(th)
+        part1 = (s / tau) * (1.0 - math.exp(-tau * min(m, 1.0) / s))
+        part2 = max(1.0 - m, 0.0) * math.exp(-tau * a / c)
+        return part1 + part2
+
+    def over_a(th):
+        brk = [min(1.0, 1.0 / math.tan(th))] if th > math.pi / 4 else None
+        return integrate.quad(inner, 0.0, 1.0, args=(th,), points=brk, epsabs=1e-12, limit=200)[0]
+    return (2.0 / math.pi) * integrate.quad(over_a, 1e-12, math.pi / 2 - 1e-12, epsabs=1e-11,
+                                            limit=400)[0]
+
+
+def test_single_cell_pure_absorber_closed_form():
+    # c = 0: births fly straight out; the score is (1 - e^{-s}) / tau and the
+    # leaked weight e^{-s} with s the optical distance to the boundary.
+    tau = 2.0
+    e = escape_expectation(tau)
+    runs = []
+    leaks = []
+    for k in range(8):
+        flux, st = T.solve_analog(np.full((1, 1), tau), np.zeros((1, 1)), np.ones((1, 1)),
+                                  20000, seed=100 + k, w_cut=0.0)
+        runs.append(flux[0, 0])
+        leaks.append(st["leak"] / 20000)
+        assert abs(st["leak"] + st["absorbed"] - 20000) < 1e-8
+    runs, leaks = np.array(runs), np.array(leaks)
+    se = runs.std(ddof=1) / math.sqrt(len(runs))
+    assert abs(runs.mean() - (1.0 - e) / tau) < 4 * se
+    assert abs(leaks.mean() - e) < 4 * leaks.std(ddof=1) / math.sqrt(len(leaks))
+
+
+def test_weight_balance_is_exact():
+    # Implicit capture conserves weight exactly: deposited + leaked weight
+    # equals the source weight, apart from the roulette's explicit changes.
+    tau, c, src = synth.grid_problem(n=8, seed=5, tau_range=(0.1, 5.0), block=4, source=2)
+    n = 3000
+    flux, st = T.solve_analog(tau, c, src, n, seed=9)
+    total = st["absorbed"] + st["leak"] - st["roulette_net"]
+    assert abs(total - n) < 1e-8 * n
+    # and the flux tally is the deposit divided by sigma_a (Eq. 7)
+    sig_a = (1.0 - c.astype(np.float64)) * tau.astype(np.float64)
+    assert abs(np.sum(flux * sig_a) * n - st["absorbed"]) < 1e-8 * n
+
+
+def _zscores(a_runs, b_runs):
+    a, b = np.asarray(a_runs), np.asarray(b_runs)
+    se = np.sqrt(a.var(axis=0, ddof=1) / a.shape[0] + b.var(axis=0, ddof=1) / b.shape[0])
+    d = a.mean(axis=0) - b.mean(axis=0)
+    ok = se > 0
+    z = np.zeros_like(d)
+    z[ok] = d[ok] / se[ok]
+    assert np.all(d[~ok] == 0)
+    return z
+
+
+def test_event_loop_with_walk_sampler_matches_mc():
+    # Pins the four-stage loop (rotation into the left-entry frame, decoding,
+    # rotation back, crossing) independently of the network: with stage 2
+    # replaced by the random walk run in the canonical frame, the loop must
+    # reproduce the standard MC flux cell by cell.
+    tau, c, src = synth.grid_problem(n=6, seed=11, tau_range=(0.1, 4.0), block=3, source=2)
+    K, n = 6, 2500
+    mc, gm = [], []
+    mc_leak, gm_leak = [], []
+    for k in range(K):
+        f1, s1 = T.solve_analog(tau, c, src, n, seed=200 + k)
+        f2, s2 = T.solve_gmc(tau, c, src, n, seed=300 + k, sampler=T.walk_sampler(300 + k))
+        mc.append(f1.ravel())
+        gm.append(f2.ravel())
+        mc_leak.append(s1["leak"] / n)
+        gm_leak.append(s2["leak"] / n)
+        assert abs(s2["absorbed"] + s2["leak"] - s2["roulette_net"] - n) < 1e-8 * n
+    z = _zscores(mc, gm)
+    assert np.max(np.abs(z)) < 4.5
+    assert np.mean(np.abs(z) > 3) < 0.05
+    assert abs(_zscores(np.array(mc_leak)[:, None], np.array(gm_leak)[:, None])[0]) < 4
+
+
+def test_rotation_rules():
+    # Canonical face f maps to global face (f + r) mod 4 with r = (F + 1) mod 4
+    # for a particle entering through global face F; directions rotate by r.
+    for F in range(4):
+        r = (F + 1) % 4
+        # the canonical entry direction +x must point into the cell through F
+        gx, gy = T.rot(np.array([1.0]), np.array([0.0]), r)
+        inward = {0: (0, 1), 1: (-1, 0), 2: (0, -1), 3: (1, 0)}[F]
+        assert (round(gx[0]), round(gy[0])) == inward
+        assert (3 + r) % 4 == F
+    ux, uy = T.rot(np.array([0.6]), np.array([0.8]), 1)
+    assert (ux[0], uy[0]) == (-0.8, 0.6)
+    bx, by = T.rot(ux, uy, -1)
+    assert (bx[0], by[0]) == (0.6, 0.8)
+
+
+def test_sigma_bar_decays_as_inverse_sqrt_n():
+    # Eq. 12 over K = 5 runs: sigma_bar(N) ~ N^{-1/2}.
+    tau, c, src = synth.grid_problem(n=8, seed=13, tau_range=(0.1, 3.0), block=4, source=2)
+    sb = []
+    for n in (1000, 4000, 16000):
+        runs = [T.solve_analog(tau, c, src, n, seed=1000 * n + k)[0].ravel() for k in range(5)]
+        sb.append(ostats.sigma_bar(runs))
+    slope = np.polyfit(np.log([1000, 4000, 16000]), np.log(sb), 1)[0]
+    assert -0.62 < slope < -0.38, (slope, sb)
