@@ -1,0 +1,208 @@
+/*
+ * gmc.h -- C ABI of the GB300 Generative Monte Carlo library (libgmc.so).
+ *
+ * Generative Monte Carlo replaces the collision-by-collision random walk
+ * inside a mesh cell by a sample of the cell's exit state drawn from a
+ * learned conditional distribution p(y | c) (section "Generative Monte Carlo
+ * Sampler"): the exit state y = (p_exit, Omega_exit, s) (Eq. 11) is x(1) of
+ * the flow ODE dx/dt = v_theta(x, t), x(0) ~ N(0, I) (Eq. 8), conditioned on
+ * the entry state and the cell in optical coordinates (Eq. 10).
+ *
+ * Geometry and units used by every entry point:
+ *  - A cell is the square [0,tau]^2 in optical coordinates (sigma_t = 1);
+ *    tau is its optical side and c = sigma_s / sigma_t its scattering ratio.
+ *    Directions are unit vectors of the plane (cos theta, sin theta).
+ *  - Canonical frame (stage 1 of the transport algorithm): the particle
+ *    enters the left face x = 0 at y = xi * tau, xi in [0,1], moving with
+ *    cos theta > 0.
+ *  - Faces are numbered counter-clockwise from the corner (0,0): 0 bottom,
+ *    1 right, 2 top, 3 left. The unwrapped perimeter coordinate is
+ *    p = face + q in [0,4) with q the counter-clockwise position on the face:
+ *    bottom x = q tau, right y = q tau, top x = (1-q) tau, left y = (1-q) tau.
+ *  - Path lengths s are in optical units (total mean free paths).
+ *
+ * Conventions:
+ *  - Every call returns a gmc_status; nothing throws across the ABI. On error
+ *    gmc_last_error(ctx) describes the failure.
+ *  - Array arguments are structure-of-arrays, row k of an [m][n] array
+ *    starting at element k*n. Unless a parameter says "host", array pointers
+ *    may be device pointers (the call runs asynchronously on the context's
+ *    stream) or host pointers (the call copies inputs in and results out
+ *    through context-owned device buffers and returns when results are on
+ *    the host). The caller owns every buffer it passes; the context owns its
+ *    weights, particle banks and scratch.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with counter
+ *    (id_lo, id_hi, event, tag) and key (seed_lo, seed_hi); tags: 1 walk
+ *    flights, 2 flow-ODE noise, 3 roulette, 4 births. Uniforms lie in (0,1].
+ */
+#ifndef GMC_H
+#define GMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gmc_status {
+    GMC_OK = 0,
+    GMC_EINVAL = -1,     /* bad argument (null pointer, size, range) */
+    GMC_ENOMEM = -2,     /* device or host allocation failed */
+    GMC_ECUDA = -3,      /* a CUDA runtime call failed */
+    GMC_ETIMEOUT = -4,   /* a bounded device-side wait ran out */
+    GMC_EFORMAT = -5,    /* malformed or unsupported weight file */
+    GMC_ENOTIMPL = -6,   /* option not implemented */
+    GMC_EBUSY = -7,      /* result not ready yet (serving) */
+    GMC_ENOWEIGHTS = -8, /* a GMC call before gmc_load_weights */
+    GMC_EIO = -9         /* file could not be read or written */
+} gmc_status;
+
+typedef enum gmc_precision { GMC_FP32 = 0, GMC_BF16 = 1, GMC_FP8 = 2 } gmc_precision;
+typedef enum gmc_integrator { GMC_EULER = 0, GMC_MIDPOINT = 1 } gmc_integrator;
+typedef enum gmc_absorb_mode { GMC_ABSORB_ANALOG = 0, GMC_ABSORB_IMPLICIT = 1 } gmc_absorb_mode;
+typedef enum gmc_method { GMC_METHOD_ANALOG = 0, GMC_METHOD_GMC = 1 } gmc_method;
+
+typedef struct gmc_ctx gmc_ctx;
+
+/* Options of the GMC sampler and of transport solves (gmc_set_config). */
+typedef struct gmc_config {
+    int steps;             /* ODE steps K (Eq. 8), >= 1; default 16 */
+    int integrator;        /* gmc_integrator; default GMC_EULER */
+    int precision;         /* gmc_precision of the velocity network; default GMC_BF16 */
+    double w_cut;          /* roulette threshold on the particle weight; default 1e-4 */
+    double p_survive;      /* roulette survival probability; default 0.1 */
+    int64_t bank_capacity; /* particles in flight per wave in transport_solve; default 2^21 */
+} gmc_config;
+
+/* Per-solve counters (all weights per history-weight unit, not normalized). */
+typedef struct gmc_solve_stats {
+    double leaked;          /* weight that left the domain */
+    double absorbed;        /* deposited weight, sum of Delta w (Eq. 6) */
+    double roulette_net;    /* weight added (+) or removed (-) by roulette */
+    int64_t transmissions;  /* cell transmissions, births included */
+    int64_t collisions;     /* scatterings simulated by random walks */
+    int64_t roulette_kills; /* histories ended by roulette */
+    int64_t waves;          /* event waves of the particle loop */
+    int64_t inward_fixes;   /* sampled exit directions that pointed into the cell */
+    double seconds;         /* device time of the solve */
+} gmc_solve_stats;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` with its own stream. */
+gmc_status gmc_create(gmc_ctx **out, int device);
+/* Frees the context and every device buffer it owns. Null is accepted. */
+gmc_status gmc_destroy(gmc_ctx *ctx);
+/* Uses `cuda_stream` (a cudaStream_t, or null for the context's own stream)
+   for every later call; the caller keeps ownership of a stream it passes. */
+gmc_status gmc_set_stream(gmc_ctx *ctx, void *cuda_stream);
+/* Waits until all work queued by the context has finished. */
+gmc_status gmc_synchronize(gmc_ctx *ctx);
+gmc_status gmc_get_config(const gmc_ctx *ctx, gmc_config *out);
+/* Validates and applies `cfg` (steps in [1, 256], w_cut >= 0,
+   p_survive in (0, 1], bank_capacity in [1024, 2^28]). */
+gmc_status gmc_set_config(gmc_ctx *ctx, const gmc_config *cfg);
+const char *gmc_status_str(gmc_status s);
+const char *gmc_last_error(const gmc_ctx *ctx);
+
+/* ---- random numbers ------------------------------------------------------ */
+
+/* Raw Philox4x32-10 blocks for ids id0 .. id0+n-1 at one (event, tag):
+   out [n][4] u32. */
+gmc_status gmc_philox(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uint32_t event,
+                      uint32_t tag, uint32_t *out);
+/* Box-Muller normals from the same blocks: u = (x+1) 2^-32,
+   z0,z1 = sqrt(-2 ln u0) (cos, sin)(2 pi u1), z2,z3 likewise from u2,u3.
+   out [4][n] float. */
+gmc_status gmc_normals(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uint32_t event,
+                       uint32_t tag, float *out);
+
+/* ---- GMC sampler (stage 2 of the transport algorithm) --------------------- */
+
+/*
+ * Loads a velocity network from a "GMCW" version-1 file (host path):
+ * magic "GMCW", u32 version = 1, u32 n_layers = 5, u32 dims[6] =
+ * {25,256,256,256,256,4}, u32 n_cond = 5, n_state = 4, n_emb = 16, flags;
+ * f32 cond_mean[5], cond_std[5], y_mean[4], y_std[4]; then per layer
+ * f32 W[out][in], f32 b[out]. The network input is [standardized condition
+ * (5), state x (4), emb(t) (16)] with emb(t) = [sin(2^j pi t)]_{j<8},
+ * [cos(2^j pi t)]_{j<8}; hidden layers use SiLU. Returns GMC_EIO if the file
+ * cannot be read, GMC_EFORMAT on any layout mismatch. The FP32 weights are
+ * kept and the BF16 / FP8 packed copies are derived from them.
+ */
+gmc_status gmc_load_weights(gmc_ctx *ctx, const char *path);
+/* Same, from a host buffer holding the file's bytes. */
+gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes);
+
+/*
+ * Samples n exit states (Eq. 8, Eq. 11) with the loaded network.
+ *  cond    [5][n] float: xi, cos theta_in, sin theta_in, ln tau, c (raw,
+ *          standardized inside with the file's cond_mean / cond_std).
+ *  noise   [4][n] float x(0), or null: then x(0) is drawn as gmc_normals with
+ *          ids id0+i, event 0, tag 2.
+ *  steps   ODE steps K >= 1 (h = 1/K, t_k = k h); integrator gmc_integrator.
+ *  precision gmc_precision: FP32 (SIMT, FP32 throughout), BF16 (tcgen05
+ *          tensor cores, BF16 operands, FP32 accumulation and state).
+ *  y_raw   [4][n] float, nullable: standardized x(1).
+ *  exit    [4][n] float, nullable: decoded exit state in the canonical frame:
+ *          p in [0,4) (wrapped), exit direction (ux, uy) made unit and
+ *          pointing out of face floor(p) (an inward normal component is
+ *          reflected), s = max(exp(ln s), 1e-7).
+ * At least one of y_raw / exit must be non-null. n = 0 is a no-op.
+ */
+gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
+                        uint64_t seed, uint64_t id0, int steps, int integrator, int precision,
+                        float *y_raw, float *exit);
+
+/* ---- analog random-walk transmission (the method GMC replaces) ------------ */
+
+/*
+ * Random-walk transmission through one cell per particle (section "Monte
+ * Carlo Method", Eq. 4): free flights d = -ln(u)/sigma, step min(d_b, d),
+ * isotropic scattering. mode GMC_ABSORB_ANALOG: sigma = 1 and each collision
+ * survives with probability c (survive iff u1 <= c), otherwise the particle
+ * is absorbed; GMC_ABSORB_IMPLICIT: sigma = c, no absorption (the weight
+ * factor exp(-(1-c) s) of Eq. 5 is left to the caller).
+ * Philox: flight j of particle i uses counter (id0+i, event0+j, tag 1):
+ * u0 -> flight, u1 -> survival, u2 -> new angle 2 pi u2.
+ *  xi, cos_in, sin_in, tau, c  [n] float (tau > 0, c in [0,1], cos_in > 0).
+ *  status  [n] int32: 0 exited, 1 absorbed.
+ *  exit    [4][n] float: p = face + q (-1 if absorbed), final direction
+ *          (ux, uy), track length s in the cell.
+ *  ncoll   [n] uint32, nullable: collisions (scatterings and absorption).
+ */
+gmc_status analog_transmit(gmc_ctx *ctx, int64_t n, const float *xi, const float *cos_in,
+                           const float *sin_in, const float *tau, const float *c, int mode,
+                           uint64_t seed, uint64_t id0, uint32_t event0, int32_t *status,
+                           float *exit, uint32_t *ncoll);
+
+/* ---- transport solve (the four-stage transport algorithm) ----------------- */
+
+/*
+ * Scalar flux of a fixed-source problem on an nx x ny grid of unit cells
+ * (cell (i,j) at element j*nx+i; physical side 1, so V = 1, sigma_t = tau,
+ * sigma_a = (1-c) tau), vacuum boundaries, isotropic volumetric source
+ * `source` (relative strengths, >= 0, not all zero; the birth cell is drawn
+ * in proportion, the point uniformly, the direction isotropically).
+ * Every cell crossing deposits Delta w = w (1 - exp(-sigma_a Delta s))
+ * (Eq. 6) and scores Delta w / (V sigma_a) (Eq. 7) into the cell's FP64
+ * tally; the weight is attenuated by exp(-sigma_a Delta s) (Eq. 5); below
+ * w_cut the particle plays roulette (survive with p_survive, weight /=
+ * p_survive). method GMC_METHOD_ANALOG walks every cell with implicit
+ * capture; GMC_METHOD_GMC walks only the birth cell and samples every later
+ * cell crossing with the network (config steps / integrator / precision).
+ *  tau, c, source  host [ny*nx] float (tau > 0, c in [0,1]; for GMC,
+ *                  tau in [0.05, 2000] and c in [0.4, 1]).
+ *  flux            host [ny*nx] double: flux per source particle.
+ *  stats           host, nullable.
+ * Blocking: returns when the flux is on the host.
+ */
+gmc_status transport_solve(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                           const float *source, int64_t n_histories, int method, uint64_t seed,
+                           double *flux, gmc_solve_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMC_H */

@@ -1,0 +1,448 @@
+// C ABI: contexts, errors, configuration, weight loading, and the batched
+// entry points gmc_philox, gmc_normals, gmc_transmit and analog_transmit.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gmc_internal.cuh"
+
+namespace gmc {
+
+gmc_status set_error(gmc_ctx *ctx, gmc_status s, const char *fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return s;
+}
+
+gmc_status cuda_error(gmc_ctx *ctx, cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(ctx, GMC_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(ctx, GMC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_device_pointer(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t ensure(Buffer &b, size_t bytes) {
+  if (b.bytes >= bytes && b.ptr) return cudaSuccess;
+  if (b.ptr) cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.bytes = 0;
+  size_t want = bytes < 256 ? 256 : bytes;
+  cudaError_t e = cudaMalloc(&b.ptr, want);
+  if (e == cudaSuccess) b.bytes = want;
+  return e;
+}
+
+namespace {
+
+// One array argument of a batched call: device pointers pass through, host
+// pointers are staged through a context buffer.
+struct Arg {
+  const void *user = nullptr;
+  void *dev = nullptr;
+  size_t bytes = 0;
+  bool host = false;
+};
+
+cudaError_t stage_in(gmc_ctx *ctx, int slot, Arg &a) {
+  if (!a.user) return cudaSuccess;
+  if (is_device_pointer(a.user)) {
+    a.dev = const_cast<void *>(a.user);
+    return cudaSuccess;
+  }
+  a.host = true;
+  cudaError_t e = ensure(ctx->stage[slot], a.bytes);
+  if (e != cudaSuccess) return e;
+  a.dev = ctx->stage[slot].ptr;
+  return cudaMemcpyAsync(a.dev, a.user, a.bytes, cudaMemcpyHostToDevice, ctx->stream);
+}
+
+cudaError_t stage_out_prepare(gmc_ctx *ctx, int slot, Arg &a) {
+  if (!a.user) return cudaSuccess;
+  if (is_device_pointer(a.user)) {
+    a.dev = const_cast<void *>(a.user);
+    return cudaSuccess;
+  }
+  a.host = true;
+  cudaError_t e = ensure(ctx->stage[slot], a.bytes);
+  if (e != cudaSuccess) return e;
+  a.dev = ctx->stage[slot].ptr;
+  return cudaSuccess;
+}
+
+cudaError_t stage_out_finish(gmc_ctx *ctx, Arg &a) {
+  if (!a.user || !a.host) return cudaSuccess;
+  return cudaMemcpyAsync(const_cast<void *>(a.user), a.dev, a.bytes, cudaMemcpyDeviceToHost,
+                         ctx->stream);
+}
+
+gmc_config default_config() {
+  gmc_config c;
+  c.steps = 16;
+  c.integrator = GMC_EULER;
+  c.precision = GMC_BF16;
+  c.w_cut = 1e-4;
+  c.p_survive = 0.1;
+  c.bank_capacity = (int64_t)1 << 21;
+  return c;
+}
+
+struct Reader {
+  const unsigned char *p;
+  size_t n, off = 0;
+  bool u32(uint32_t *v) {
+    if (off + 4 > n) return false;
+    std::memcpy(v, p + off, 4);
+    off += 4;
+    return true;
+  }
+  bool f32(float *v, size_t count) {
+    if (off + 4 * count > n) return false;
+    std::memcpy(v, p + off, 4 * count);
+    off += 4 * count;
+    return true;
+  }
+};
+
+}  // namespace
+}  // namespace gmc
+
+using namespace gmc;
+
+extern "C" {
+
+const char *gmc_status_str(gmc_status s) {
+  switch (s) {
+    case GMC_OK: return "GMC_OK";
+    case GMC_EINVAL: return "GMC_EINVAL";
+    case GMC_ENOMEM: return "GMC_ENOMEM";
+    case GMC_ECUDA: return "GMC_ECUDA";
+    case GMC_ETIMEOUT: return "GMC_ETIMEOUT";
+    case GMC_EFORMAT: return "GMC_EFORMAT";
+    case GMC_ENOTIMPL: return "GMC_ENOTIMPL";
+    case GMC_EBUSY: return "GMC_EBUSY";
+    case GMC_ENOWEIGHTS: return "GMC_ENOWEIGHTS";
+    case GMC_EIO: return "GMC_EIO";
+  }
+  return "GMC_UNKNOWN";
+}
+
+const char *gmc_last_error(const gmc_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+gmc_status gmc_create(gmc_ctx **out, int device) {
+  if (!out) return GMC_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return GMC_EINVAL;
+  }
+  gmc_ctx *ctx = new (std::nothrow) gmc_ctx();
+  if (!ctx) return GMC_ENOMEM;
+  ctx->device = device;
+  ctx->cfg = default_config();
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int) * 4);
+  if (e != cudaSuccess) {
+    gmc_destroy(ctx);
+    return e == cudaErrorMemoryAllocation ? GMC_ENOMEM : GMC_ECUDA;
+  }
+  ctx->stream = ctx->own_stream;
+  *out = ctx;
+  return GMC_OK;
+}
+
+gmc_status gmc_destroy(gmc_ctx *ctx) {
+  if (!ctx) return GMC_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto &b : ctx->stage)
+    if (b.ptr) cudaFree(b.ptr);
+  for (auto &b : ctx->solve)
+    if (b.ptr) cudaFree(b.ptr);
+  if (ctx->d_f32) cudaFree(ctx->d_f32);
+  if (ctx->d_tc) cudaFree(ctx->d_tc);
+  if (ctx->d_tc_bias) cudaFree(ctx->d_tc_bias);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+  return GMC_OK;
+}
+
+gmc_status gmc_set_stream(gmc_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return GMC_EINVAL;
+  ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+  return GMC_OK;
+}
+
+gmc_status gmc_synchronize(gmc_ctx *ctx) {
+  if (!ctx) return GMC_EINVAL;
+  cudaSetDevice(ctx->device);
+  GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return GMC_OK;
+}
+
+gmc_status gmc_get_config(const gmc_ctx *ctx, gmc_config *out) {
+  if (!ctx || !out) return GMC_EINVAL;
+  *out = ctx->cfg;
+  return GMC_OK;
+}
+
+gmc_status gmc_set_config(gmc_ctx *ctx, const gmc_config *cfg) {
+  if (!ctx || !cfg) return GMC_EINVAL;
+  if (cfg->steps < 1 || cfg->steps > 256)
+    return set_error(ctx, GMC_EINVAL, "steps must be in [1, 256], got %d", cfg->steps);
+  if (cfg->integrator != GMC_EULER && cfg->integrator != GMC_MIDPOINT)
+    return set_error(ctx, GMC_EINVAL, "unknown integrator %d", cfg->integrator);
+  if (cfg->precision < GMC_FP32 || cfg->precision > GMC_FP8)
+    return set_error(ctx, GMC_EINVAL, "unknown precision %d", cfg->precision);
+  if (!(cfg->w_cut >= 0.0) || !(cfg->p_survive > 0.0 && cfg->p_survive <= 1.0))
+    return set_error(ctx, GMC_EINVAL, "need w_cut >= 0 and p_survive in (0, 1]");
+  if (cfg->bank_capacity < 1024 || cfg->bank_capacity > ((int64_t)1 << 28))
+    return set_error(ctx, GMC_EINVAL, "bank_capacity must be in [1024, 2^28]");
+  ctx->cfg = *cfg;
+  return GMC_OK;
+}
+
+gmc_status gmc_philox(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uint32_t event,
+                      uint32_t tag, uint32_t *out) {
+  if (!ctx || n < 0 || (n > 0 && !out)) return set_error(ctx, GMC_EINVAL, "gmc_philox: bad arguments");
+  if (n == 0) return GMC_OK;
+  cudaSetDevice(ctx->device);
+  Arg o;
+  o.user = out;
+  o.bytes = (size_t)n * 16;
+  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 0, o));
+  GMC_CUDA_TRY(ctx, launch_philox(ctx->stream, n, seed, id0, event, tag, (uint32_t *)o.dev));
+  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o));
+  if (o.host) GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return GMC_OK;
+}
+
+gmc_status gmc_normals(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uint32_t event,
+                       uint32_t tag, float *out) {
+  if (!ctx || n < 0 || (n > 0 && !out)) return set_error(ctx, GMC_EINVAL, "gmc_normals: bad arguments");
+  if (n == 0) return GMC_OK;
+  cudaSetDevice(ctx->device);
+  Arg o;
+  o.user = out;
+  o.bytes = (size_t)n * 16;
+  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 0, o));
+  GMC_CUDA_TRY(ctx, launch_normals(ctx->stream, n, seed, id0, event, tag, (float *)o.dev));
+  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o));
+  if (o.host) GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return GMC_OK;
+}
+
+gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes) {
+  if (!ctx || !blob) return set_error(ctx, GMC_EINVAL, "gmc_load_weights_buffer: null argument");
+  static const uint32_t dims_ok[6] = {25, 256, 256, 256, 256, 4};
+  Reader rd{(const unsigned char *)blob, nbytes};
+  if (nbytes < 4 || std::memcmp(blob, "GMCW", 4) != 0)
+    return set_error(ctx, GMC_EFORMAT, "weight file: bad magic");
+  rd.off = 4;
+  uint32_t version, nl, dims[6], ncond, nstate, nemb, flags;
+  bool ok = rd.u32(&version) && rd.u32(&nl);
+  for (int i = 0; i < 6 && ok; ++i) ok = rd.u32(&dims[i]);
+  ok = ok && rd.u32(&ncond) && rd.u32(&nstate) && rd.u32(&nemb) && rd.u32(&flags);
+  if (!ok) return set_error(ctx, GMC_EFORMAT, "weight file: truncated header");
+  if (version != 1 || nl != 5 || ncond != 5 || nstate != 4 || nemb != 16)
+    return set_error(ctx, GMC_EFORMAT, "weight file: unsupported version or layout");
+  for (int i = 0; i < 6; ++i)
+    if (dims[i] != dims_ok[i])
+      return set_error(ctx, GMC_EFORMAT, "weight file: layer dims must be 25-256-256-256-256-4");
+  float st[18];
+  if (!rd.f32(st, 18)) return set_error(ctx, GMC_EFORMAT, "weight file: truncated statistics");
+  for (int l = 0; l < 5; ++l) {
+    if (!rd.f32(ctx->host_w[l], (size_t)dims[l + 1] * dims[l]) || !rd.f32(ctx->host_b[l], dims[l + 1]))
+      return set_error(ctx, GMC_EFORMAT, "weight file: truncated layer %d", l);
+  }
+  if (rd.off != nbytes) return set_error(ctx, GMC_EFORMAT, "weight file: trailing bytes");
+  for (int k = 0; k < 5; ++k)
+    if (!(st[5 + k] > 0.0f)) return set_error(ctx, GMC_EFORMAT, "weight file: cond_std must be > 0");
+  for (int k = 0; k < 18; ++k)
+    if (!std::isfinite(st[k])) return set_error(ctx, GMC_EFORMAT, "weight file: non-finite statistics");
+
+  NetStats ns;
+  for (int k = 0; k < 5; ++k) {
+    ns.cond_mean[k] = st[k];
+    ns.cond_inv_std[k] = 1.0f / st[5 + k];
+  }
+  for (int k = 0; k < 4; ++k) {
+    ns.y_mean[k] = st[10 + k];
+    ns.y_std[k] = st[14 + k];
+  }
+
+  // FP32 transposed block
+  const size_t n1 = 32 * 256, nh = 256 * 256;
+  const size_t total = n1 + 256 + 3 * (nh + 256) + 4 * 256 + 4;
+  std::vector<float> h(total, 0.0f);
+  float *p = h.data();
+  float *w1t = p; p += n1;
+  float *b1 = p; p += 256;
+  float *wt[3], *bt[3];
+  for (int l = 0; l < 3; ++l) { wt[l] = p; p += nh; bt[l] = p; p += 256; }
+  float *w5 = p; p += 4 * 256;
+  float *b5 = p; p += 4;
+  for (int c = 0; c < 256; ++c)
+    for (int k = 0; k < 25; ++k) w1t[k * 256 + c] = ctx->host_w[0][c * 25 + k];
+  std::memcpy(b1, ctx->host_b[0], 256 * 4);
+  for (int l = 0; l < 3; ++l) {
+    for (int c = 0; c < 256; ++c)
+      for (int k = 0; k < 256; ++k) wt[l][k * 256 + c] = ctx->host_w[l + 1][c * 256 + k];
+    std::memcpy(bt[l], ctx->host_b[l + 1], 256 * 4);
+  }
+  std::memcpy(w5, ctx->host_w[4], 4 * 256 * 4);
+  std::memcpy(b5, ctx->host_b[4], 4 * 4);
+
+  cudaSetDevice(ctx->device);
+  GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (!ctx->d_f32) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_f32, total * sizeof(float)));
+  GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_f32, h.data(), total * sizeof(float), cudaMemcpyHostToDevice));
+  float *d = ctx->d_f32;
+  ctx->f32.w1t = d; d += n1;
+  ctx->f32.b1 = d; d += 256;
+  ctx->f32.w2t = d; d += nh;
+  ctx->f32.b2 = d; d += 256;
+  ctx->f32.w3t = d; d += nh;
+  ctx->f32.b3 = d; d += 256;
+  ctx->f32.w4t = d; d += nh;
+  ctx->f32.b4 = d; d += 256;
+  ctx->f32.w5 = d; d += 4 * 256;
+  ctx->f32.b5 = d;
+
+  // packed operands of the tensor-core path
+  const size_t tcb = tc_packed_bytes();
+  if (tcb > 0) {
+    std::vector<unsigned char> packed(tcb);
+    std::vector<float> bias(5 * 256, 0.0f);
+    tc_pack_host(ctx->host_w, ctx->host_b, packed.data(), bias.data());
+    if (!ctx->d_tc) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_tc, tcb));
+    if (!ctx->d_tc_bias) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_tc_bias, 5 * 256 * sizeof(float)));
+    GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_tc, packed.data(), tcb, cudaMemcpyHostToDevice));
+    GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_tc_bias, bias.data(), 5 * 256 * sizeof(float),
+                                 cudaMemcpyHostToDevice));
+    ctx->tc_bytes = tcb;
+  }
+  ctx->stats = ns;
+  ctx->has_weights = true;
+  return GMC_OK;
+}
+
+gmc_status gmc_load_weights(gmc_ctx *ctx, const char *path) {
+  if (!ctx || !path) return set_error(ctx, GMC_EINVAL, "gmc_load_weights: null argument");
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return set_error(ctx, GMC_EIO, "cannot open weight file '%s'", path);
+  std::vector<unsigned char> blob;
+  unsigned char buf[1 << 16];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) blob.insert(blob.end(), buf, buf + got);
+  const bool err = std::ferror(f) != 0;
+  std::fclose(f);
+  if (err) return set_error(ctx, GMC_EIO, "read error on '%s'", path);
+  return gmc_load_weights_buffer(ctx, blob.data(), blob.size());
+}
+
+gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
+                        uint64_t seed, uint64_t id0, int steps, int integrator, int precision,
+                        float *y_raw, float *exit) {
+  if (!ctx) return GMC_EINVAL;
+  if (n < 0) return set_error(ctx, GMC_EINVAL, "gmc_transmit: n < 0");
+  if (n == 0) return GMC_OK;
+  if (!cond || (!y_raw && !exit)) return set_error(ctx, GMC_EINVAL, "gmc_transmit: null array");
+  if (steps < 1 || steps > 256) return set_error(ctx, GMC_EINVAL, "gmc_transmit: steps in [1,256]");
+  if (integrator != GMC_EULER && integrator != GMC_MIDPOINT)
+    return set_error(ctx, GMC_EINVAL, "gmc_transmit: unknown integrator");
+  if (!ctx->has_weights) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_transmit: no weights loaded");
+  if (precision == GMC_FP8) return set_error(ctx, GMC_ENOTIMPL, "gmc_transmit: FP8 not built");
+  if (precision != GMC_FP32 && precision != GMC_BF16)
+    return set_error(ctx, GMC_EINVAL, "gmc_transmit: unknown precision");
+  cudaSetDevice(ctx->device);
+  Arg a_cond, a_noise, a_y, a_exit;
+  a_cond.user = cond; a_cond.bytes = (size_t)n * 5 * 4;
+  a_noise.user = noise; a_noise.bytes = (size_t)n * 4 * 4;
+  a_y.user = y_raw; a_y.bytes = (size_t)n * 4 * 4;
+  a_exit.user = exit; a_exit.bytes = (size_t)n * 4 * 4;
+  GMC_CUDA_TRY(ctx, stage_in(ctx, 0, a_cond));
+  GMC_CUDA_TRY(ctx, stage_in(ctx, 1, a_noise));
+  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 2, a_y));
+  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 3, a_exit));
+  if (precision == GMC_FP32) {
+    GMC_CUDA_TRY(ctx, launch_sampler_f32(ctx->stream, ctx->f32, ctx->stats, n, (const float *)a_cond.dev,
+                                         (const float *)a_noise.dev, seed, id0, steps, integrator,
+                                         (float *)a_y.dev, (float *)a_exit.dev));
+  } else {
+    if (!ctx->d_tc) return set_error(ctx, GMC_ENOTIMPL, "gmc_transmit: BF16 path not built");
+    cudaError_t e = launch_sampler_tc(ctx->stream, ctx->d_tc, ctx->d_tc_bias, ctx->stats, n,
+                                      (const float *)a_cond.dev, (const float *)a_noise.dev, seed,
+                                      id0, steps, integrator, (float *)a_y.dev,
+                                      (float *)a_exit.dev, ctx->d_err);
+    if (e == cudaErrorNotSupported) return set_error(ctx, GMC_ENOTIMPL, "gmc_transmit: BF16 path not built");
+    if (e != cudaSuccess) return cuda_error(ctx, e, "launch_sampler_tc");
+  }
+  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, a_y));
+  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, a_exit));
+  if (a_cond.host || a_noise.host || a_y.host || a_exit.host)
+    GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return GMC_OK;
+}
+
+gmc_status analog_transmit(gmc_ctx *ctx, int64_t n, const float *xi, const float *cos_in,
+                           const float *sin_in, const float *tau, const float *c, int mode,
+                           uint64_t seed, uint64_t id0, uint32_t event0, int32_t *status,
+                           float *exit, uint32_t *ncoll) {
+  if (!ctx) return GMC_EINVAL;
+  if (n < 0) return set_error(ctx, GMC_EINVAL, "analog_transmit: n < 0");
+  if (n == 0) return GMC_OK;
+  if (!xi || !cos_in || !sin_in || !tau || !c || !status || !exit)
+    return set_error(ctx, GMC_EINVAL, "analog_transmit: null array");
+  if (mode != GMC_ABSORB_ANALOG && mode != GMC_ABSORB_IMPLICIT)
+    return set_error(ctx, GMC_EINVAL, "analog_transmit: unknown mode");
+  cudaSetDevice(ctx->device);
+  Arg in[5], o_status, o_exit, o_ncoll;
+  const float *ins[5] = {xi, cos_in, sin_in, tau, c};
+  for (int k = 0; k < 5; ++k) {
+    in[k].user = ins[k];
+    in[k].bytes = (size_t)n * 4;
+    GMC_CUDA_TRY(ctx, stage_in(ctx, k, in[k]));
+  }
+  o_status.user = status; o_status.bytes = (size_t)n * 4;
+  o_exit.user = exit; o_exit.bytes = (size_t)n * 16;
+  o_ncoll.user = ncoll; o_ncoll.bytes = (size_t)n * 4;
+  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 5, o_status));
+  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 6, o_exit));
+  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 7, o_ncoll));
+  GMC_CUDA_TRY(ctx, launch_analog(ctx->stream, n, (const float *)in[0].dev, (const float *)in[1].dev,
+                                  (const float *)in[2].dev, (const float *)in[3].dev,
+                                  (const float *)in[4].dev, mode, seed, id0, event0,
+                                  (int32_t *)o_status.dev, (float *)o_exit.dev,
+                                  (uint32_t *)o_ncoll.dev));
+  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_status));
+  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_exit));
+  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_ncoll));
+  bool host = o_status.host || o_exit.host || o_ncoll.host;
+  for (auto &a : in) host = host || a.host;
+  if (host) GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return GMC_OK;
+}
+
+}  // extern "C"

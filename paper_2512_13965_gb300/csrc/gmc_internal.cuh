@@ -1,0 +1,104 @@
+// Internal declarations shared by the translation units of libgmc.so.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "../../include/gmc.h"
+
+namespace gmc {
+
+constexpr int kCond = 5, kState = 4, kEmb = 16, kIn = kCond + kState + kEmb, kHidden = 256;
+constexpr int kIn1Pad = 32;  // layer-1 input padded to 32 columns
+constexpr float kSMin = 1e-7f;
+
+// FP32 network, transposed for the SIMT path: w1t [32][256] (rows 25..31
+// zero), w2t..w4t [256][256] with wt[k][c] = W[c][k]; w5 [4][256] as in the
+// file; biases as in the file.
+struct NetF32 {
+  const float *w1t, *b1, *w2t, *b2, *w3t, *b3, *w4t, *b4, *w5, *b5;
+};
+
+// Standardization of the file: cond_mean[5], cond_std[5], y_mean[4], y_std[4].
+struct NetStats {
+  float cond_mean[kCond], cond_inv_std[kCond], y_mean[kState], y_std[kState];
+};
+
+// Packed operands of the tensor-core path (built by sampler_tc.cu).
+struct NetTC;
+
+struct Buffer {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace gmc
+
+struct gmc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  std::string last_error;
+  gmc_config cfg{};
+  std::mutex mu;
+
+  // weights
+  bool has_weights = false;
+  float host_w[5][256 * 256];  // unused tail for small layers
+  float host_b[5][256];
+  gmc::NetStats stats{};
+  float *d_f32 = nullptr;  // FP32 transposed block
+  gmc::NetF32 f32{};
+  void *d_tc = nullptr;  // packed BF16 operands
+  size_t tc_bytes = 0;
+  float *d_tc_bias = nullptr;  // per-layer biases for the tensor-core path
+  int *d_err = nullptr;        // device error word (bounded waits)
+
+  // staging buffers for host-pointer calls
+  gmc::Buffer stage[8];
+  // transport-solve scratch
+  gmc::Buffer solve[16];
+};
+
+namespace gmc {
+
+gmc_status set_error(gmc_ctx *ctx, gmc_status s, const char *fmt, ...);
+gmc_status cuda_error(gmc_ctx *ctx, cudaError_t e, const char *what);
+bool is_device_pointer(const void *p);
+// Grows buffer `b` to at least `bytes` (never shrinks).
+cudaError_t ensure(Buffer &b, size_t bytes);
+
+#define GMC_CUDA_TRY(ctx, expr)                                   \
+  do {                                                            \
+    cudaError_t e__ = (expr);                                     \
+    if (e__ != cudaSuccess) return ::gmc::cuda_error(ctx, e__, #expr); \
+  } while (0)
+
+// Launchers implemented in the kernel translation units. All are
+// asynchronous on `stream` and take device pointers only.
+cudaError_t launch_philox(cudaStream_t stream, int64_t n, uint64_t seed, uint64_t id0,
+                          uint32_t event, uint32_t tag, uint32_t *out);
+cudaError_t launch_normals(cudaStream_t stream, int64_t n, uint64_t seed, uint64_t id0,
+                           uint32_t event, uint32_t tag, float *out);
+cudaError_t launch_sampler_f32(cudaStream_t stream, const NetF32 &net, const NetStats &st,
+                               int64_t n, const float *cond, const float *noise, uint64_t seed,
+                               uint64_t id0, int steps, int integrator, float *y_raw, float *exit);
+cudaError_t launch_analog(cudaStream_t stream, int64_t n, const float *xi, const float *cos_in,
+                          const float *sin_in, const float *tau, const float *c, int mode,
+                          uint64_t seed, uint64_t id0, uint32_t event0, int32_t *status,
+                          float *exit, uint32_t *ncoll);
+
+// Tensor-core sampler (sampler_tc.cu).
+size_t tc_packed_bytes();
+void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
+                  float *bias_host);
+cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const float *bias,
+                              const NetStats &st, int64_t n, const float *cond,
+                              const float *noise, uint64_t seed, uint64_t id0, int steps,
+                              int integrator, float *y_raw, float *exit, int *err);
+
+}  // namespace gmc

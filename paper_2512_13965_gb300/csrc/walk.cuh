@@ -1,0 +1,107 @@
+// Random-walk transport through one square cell (section "Monte Carlo
+// Method", Eq. 4): free flights d = -ln(u)/sigma with u in (0,1], step
+// min(d_b, d), isotropic scattering; analog mode kills at a collision with
+// probability 1 - c, implicit-capture mode samples flights with sigma = c and
+// never kills. Used by analog_transmit, by the births of transport_solve and
+// by its analog method.
+//
+// Position arithmetic runs in T (float, or double in optically thick cells);
+// the variates (log, sincos) are drawn in float.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "philox.cuh"
+
+namespace gmc {
+
+constexpr uint32_t kMaxFlights = 1u << 28;  // bound on one walk (never reached in practice)
+constexpr float kTau64 = 64.0f;             // cells thicker than this walk in FP64
+
+enum : int { kExited = 0, kAbsorbed = 1, kTruncated = 2 };
+
+struct WalkResult {
+  int status;       // kExited / kAbsorbed / kTruncated
+  int face;         // exit face 0..3 (cell frame), -1 otherwise
+  float q;          // counter-clockwise position on the exit face
+  float ux, uy;     // final direction
+  float s;          // track length, optical units
+  uint32_t ncoll;   // collisions
+  uint32_t event;   // next unused Philox event
+};
+
+template <typename T>
+__device__ __forceinline__ WalkResult walk_box(T tau, float c, int implicit, T x, T y, float ux,
+                                               float uy, uint64_t seed, uint64_t id,
+                                               uint32_t event) {
+  const float rate = implicit ? c : 1.0f;
+  const T inf = (T)INFINITY;
+  T s = 0;
+  uint32_t ncoll = 0;
+  WalkResult w;
+  w.status = kTruncated;
+  w.face = -1;
+  w.q = 0.0f;
+  for (uint32_t it = 0; it < kMaxFlights; ++it) {
+    const uint4 r = philox_draw(seed, id, event, kTagWalk);
+    ++event;
+    const T d = rate > 0.0f ? (T)(-logf(u01(r.x)) / rate) : inf;
+    T dbx = inf, dby = inf;
+    if (ux > 0.0f) dbx = (tau - x) / (T)ux;
+    else if (ux < 0.0f) dbx = -x / (T)ux;
+    if (uy > 0.0f) dby = (tau - y) / (T)uy;
+    else if (uy < 0.0f) dby = -y / (T)uy;
+    const bool xface = dbx <= dby;
+    T db = xface ? dbx : dby;
+    if (db < (T)0) db = (T)0;
+    if (d >= db) {
+      s += db;
+      int face;
+      T along;
+      if (xface) {
+        face = ux > 0.0f ? 1 : 3;
+        along = y + db * (T)uy;
+      } else {
+        face = uy > 0.0f ? 2 : 0;
+        along = x + db * (T)ux;
+      }
+      // counter-clockwise position: bottom x, right y, top tau - x, left tau - y
+      T qn = (face == 0 || face == 1) ? along / tau : (tau - along) / tau;
+      float q = (float)qn;
+      q = fminf(fmaxf(q, 0.0f), 1.0f);
+      w.status = kExited;
+      w.face = face;
+      w.q = q;
+      break;
+    }
+    s += d;
+    x += d * (T)ux;
+    y += d * (T)uy;
+    ++ncoll;
+    if (!implicit && u01(r.y) > c) {
+      w.status = kAbsorbed;
+      break;
+    }
+    sincospif(2.0f * u01(r.z), &uy, &ux);
+  }
+  w.ux = ux;
+  w.uy = uy;
+  w.s = (float)s;
+  w.ncoll = ncoll;
+  w.event = event;
+  return w;
+}
+
+// Walk from a point given in normalized cell coordinates (X, Y in [0,1]),
+// picking the position precision from the cell's optical size.
+__device__ __forceinline__ WalkResult walk_cell(float tau, float c, int implicit, float X, float Y,
+                                                float ux, float uy, uint64_t seed, uint64_t id,
+                                                uint32_t event) {
+  if (tau > kTau64)
+    return walk_box<double>((double)tau, c, implicit, (double)X * tau, (double)Y * tau, ux, uy,
+                            seed, id, event);
+  return walk_box<float>(tau, c, implicit, X * tau, Y * tau, ux, uy, seed, id, event);
+}
+
+}  // namespace gmc

@@ -16,3 +16,24 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def tmpdir_session(tmp_path_factory):
     return tmp_path_factory.mktemp("gmc")
+
+
+@pytest.fixture(scope="session")
+def gpu_ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2512_13965_gb300 as g
+    ctx = g.Context(0)
+    yield ctx
+    ctx.close()
+
+
+@pytest.fixture(scope="session")
+def kaiming_file(tmp_path_factory):
+    import synth
+    p = tmp_path_factory.mktemp("w") / "kaiming_seed1.bin"
+    synth.write_weights(str(p), synth.kaiming_weights(1))
+    return str(p)
