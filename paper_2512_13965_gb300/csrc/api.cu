@@ -39,6 +39,17 @@ bool is_device_pointer(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+gmc_status check_device_error(gmc_ctx *ctx) {
+  int h[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemcpy(h, ctx->d_err, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(ctx, e, "reading the device error word");
+  if (h[0] != 0) {
+    cudaMemset(ctx->d_err, 0, sizeof(h));
+    return set_error(ctx, GMC_ETIMEOUT, "a bounded device wait gave up (code %d)", h[0]);
+  }
+  return GMC_OK;
+}
+
 cudaError_t ensure(Buffer &b, size_t bytes) {
   if (b.bytes >= bytes && b.ptr) return cudaSuccess;
   if (b.ptr) cudaFree(b.ptr);
@@ -179,6 +190,7 @@ gmc_status gmc_destroy(gmc_ctx *ctx) {
     if (b.ptr) cudaFree(b.ptr);
   for (auto &b : ctx->solve)
     if (b.ptr) cudaFree(b.ptr);
+  if (ctx->bias1.ptr) cudaFree(ctx->bias1.ptr);
   if (ctx->d_f32) cudaFree(ctx->d_f32);
   if (ctx->d_tc) cudaFree(ctx->d_tc);
   if (ctx->d_tc_bias) cudaFree(ctx->d_tc_bias);
@@ -198,7 +210,7 @@ gmc_status gmc_synchronize(gmc_ctx *ctx) {
   if (!ctx) return GMC_EINVAL;
   cudaSetDevice(ctx->device);
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  return GMC_OK;
+  return check_device_error(ctx);
 }
 
 gmc_status gmc_get_config(const gmc_ctx *ctx, gmc_config *out) {
@@ -392,17 +404,20 @@ gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float 
                                          (float *)a_y.dev, (float *)a_exit.dev));
   } else {
     if (!ctx->d_tc) return set_error(ctx, GMC_ENOTIMPL, "gmc_transmit: BF16 path not built");
-    cudaError_t e = launch_sampler_tc(ctx->stream, ctx->d_tc, ctx->d_tc_bias, ctx->stats, n,
-                                      (const float *)a_cond.dev, (const float *)a_noise.dev, seed,
-                                      id0, steps, integrator, (float *)a_y.dev,
-                                      (float *)a_exit.dev, ctx->d_err);
+    GMC_CUDA_TRY(ctx, ensure(ctx->bias1, (size_t)2 * steps * 256 * sizeof(float)));
+    cudaError_t e = launch_sampler_tc(ctx->stream, ctx->d_tc, ctx->d_tc_bias, ctx->f32, ctx->stats,
+                                      n, (const float *)a_cond.dev, (const float *)a_noise.dev,
+                                      seed, id0, steps, integrator, (float *)a_y.dev,
+                                      (float *)a_exit.dev, ctx->d_err, (float *)ctx->bias1.ptr);
     if (e == cudaErrorNotSupported) return set_error(ctx, GMC_ENOTIMPL, "gmc_transmit: BF16 path not built");
     if (e != cudaSuccess) return cuda_error(ctx, e, "launch_sampler_tc");
   }
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, a_y));
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, a_exit));
-  if (a_cond.host || a_noise.host || a_y.host || a_exit.host)
+  if (a_cond.host || a_noise.host || a_y.host || a_exit.host) {
     GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
+  }
   return GMC_OK;
 }
 

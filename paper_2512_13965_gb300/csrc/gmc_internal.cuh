@@ -60,6 +60,8 @@ struct gmc_ctx {
 
   // staging buffers for host-pointer calls
   gmc::Buffer stage[8];
+  // per-evaluation layer-1 bias of the tensor-core sampler
+  gmc::Buffer bias1;
   // transport-solve scratch
   gmc::Buffer solve[16];
 };
@@ -69,6 +71,8 @@ namespace gmc {
 gmc_status set_error(gmc_ctx *ctx, gmc_status s, const char *fmt, ...);
 gmc_status cuda_error(gmc_ctx *ctx, cudaError_t e, const char *what);
 bool is_device_pointer(const void *p);
+// Reads and clears the device error word (set by bounded waits that gave up).
+gmc_status check_device_error(gmc_ctx *ctx);
 // Grows buffer `b` to at least `bytes` (never shrinks).
 cudaError_t ensure(Buffer &b, size_t bytes);
 
@@ -97,8 +101,9 @@ size_t tc_packed_bytes();
 void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
                   float *bias_host);
 cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const float *bias,
-                              const NetStats &st, int64_t n, const float *cond,
+                              const NetF32 &f32, const NetStats &st, int64_t n, const float *cond,
                               const float *noise, uint64_t seed, uint64_t id0, int steps,
-                              int integrator, float *y_raw, float *exit, int *err);
+                              int integrator, float *y_raw, float *exit, int *err,
+                              float *bias1_scratch);
 
 }  // namespace gmc

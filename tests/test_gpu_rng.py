@@ -36,6 +36,9 @@ def test_normals_close_to_fp64(gpu_ctx):
     torch.cuda.synchronize()
     got = out.cpu().numpy().astype(np.float64)
     expect = oracle.rng.normal_batch(9, n, id0=100, event=3, tag=2)
+    # u = (x+1) 2^-32 rounded to float is off by up to 2^-25 near u = 1, which
+    # perturbs sqrt(-2 ln u0) by ~3e-8 / r for small radii r: about 1e-4 of
+    # the draws (r < 0.015) exceed 2e-6, none should exceed 1e-3.
     err = np.abs(got - expect) / (1.0 + np.abs(expect))
-    assert np.mean(err < 2e-6) > 0.99999
+    assert np.mean(err < 2e-6) > 0.9995
     assert err.max() < 1e-3
