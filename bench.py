@@ -1,0 +1,328 @@
+"""Benchmark: GMC cell transmissions per second on GB300.
+
+Workload (one step = one pass of the sampler hot path over one batch):
+  velocity MLP 25 -> 256 x4 (SiLU) -> 4, Kaiming-normal weights (seed 1),
+  16 explicit Euler steps, batch 2^20 particles, tau log-uniform in
+  [0.1, 1000], c uniform in [0.5, 0.999], entry xi ~ U[0,1], cosine-weighted
+  entry direction; Philox noise, BF16 tensor-core sampler, decoded exits.
+  Inputs are resident in HBM before the timed region; L2 is flushed (256 MiB
+  write) between steps, outside the per-step CUDA-event pairs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmc|reference]
+
+Multi-GPU: one process per GPU under torchrun; every rank samples its own
+batch (distinct Philox ids), no collective on the data path ("weak").
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BATCH = 1 << 20
+ODE_STEPS = 16
+HIDDEN = 256
+# algorithmic FLOPs per transmission (Eq. 8 with the 25-256x4-4 network):
+# per ODE step 2 (4*256 + 3*256^2 + 256*4); the condition part of layer 1
+# (2*5*256) once; the time embedding is shared by all particles.
+FLOPS_PER_STEP = 2 * (4 * HIDDEN + 3 * HIDDEN * HIDDEN + HIDDEN * 4)
+FLOPS_COND = 2 * 5 * HIDDEN
+METRIC = "cell transmissions/s GMC vs analog MC at flux err <=1%; p99 latency"
+WORKLOAD = ("GMC sampler inference: 25-256x4-4 SiLU velocity MLP, Kaiming-normal seed 1, "
+            "16 Euler steps, batch 2^20, tau logU[0.1,1000], c U[0.5,0.999]")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"bf16": p["bf16_tflops"], "hbm": p["hbm_gbs"], "src": "measured"}
+    except Exception:
+        return {"bf16": 1900.0, "hbm": 6800.0, "src": "fallback"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(sample_rows=4096):
+    """Times the FP64 oracle sampler (numpy) in a fresh process on all host cores."""
+    code = r"""
+import json, os, sys, time, tempfile
+sys.path.insert(0, %r)
+import numpy as np
+import oracle, synth
+n = %d
+with tempfile.TemporaryDirectory() as d:
+    p = os.path.join(d, "w.bin")
+    synth.write_weights(p, synth.kaiming_weights(1))
+    net = oracle.mlp.read_weights(p)
+cond, _, _ = synth.sampler_conditions(n, 1)
+z = synth.gaussian_noise(n, 3)
+t0 = time.perf_counter()
+y = oracle.mlp.sample(net, cond, z, %d, "euler")
+oracle.mlp.decode(net, y)
+dt = time.perf_counter() - t0
+print(json.dumps({"seconds": dt, "n": n}))
+""" % (ROOT, sample_rows, ODE_STEPS)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=600)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": r["n"] / r["seconds"], "unit": "cell transmissions/s", "cores": cores,
+            "kind": "oracle",
+            "sample": "%d transmissions of the same workload (16 Euler steps, FP64 numpy "
+                      "oracle incl. decode), %.1f s" % (r["n"], r["seconds"])}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    rows = 2048
+    for _ in range(args.warmup):
+        pass
+    times = []
+    base = None
+    for _ in range(args.steps):
+        base = cpu_baseline(rows)
+        times.append(rows / base["value"])
+    total = sum(times)
+    value = rows * args.steps / total
+    base["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell transmissions/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded sample of 2048 transmissions per step)",
+                       "batch": rows, "ode_steps": ODE_STEPS},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "cell transmissions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gmc", choices=["gmc", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2512_13965_gb300 as g
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = g.GMC_BF16 if args.precision == "bf16" else g.GMC_FP32
+
+    ctx = g.Context(local)
+    stream = torch.cuda.current_stream()
+    g.gmc_set_stream(ctx, stream)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "w.bin")
+        synth.write_weights(path, synth.kaiming_weights(1))
+        g.gmc_load_weights(ctx, path)
+    cond_h, _, _ = synth.sampler_conditions(BATCH, 1 + rank)
+    cond = torch.from_numpy(cond_h).cuda()
+    exit_d = torch.empty(4, BATCH, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    id0 = rank * BATCH
+
+    def step(i):
+        g.gmc_transmit(ctx, BATCH, cond, None, 12345, id0 + 0 * i, ODE_STEPS, g.GMC_EULER, prec,
+                       None, exit_d)
+
+    for i in range(args.warmup):
+        step(i)
+        flush.zero_()
+    g.gmc_synchronize(ctx)
+
+    clocks = Clocks(local)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        starts[i].record(stream)
+        step(i)
+        ends[i].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    g.gmc_synchronize(ctx)
+    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(per_step)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * BATCH * args.steps / (total_ms * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers (copies timed)
+    cond_pin = torch.from_numpy(cond_h).pin_memory()
+    exit_pin = torch.empty(4, BATCH, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, 10))
+    g.gmc_transmit(ctx, BATCH, cond_pin.numpy(), None, 7, id0, ODE_STEPS, g.GMC_EULER, prec,
+                   None, exit_pin.numpy())
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        g.gmc_transmit(ctx, BATCH, cond_pin.numpy(), None, 7, id0, ODE_STEPS, g.GMC_EULER, prec,
+                       None, exit_pin.numpy())
+    e2e_s = time.perf_counter() - t0
+    e2e_val = torch.tensor([e2e_s], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(e2e_val, op=torch.distributed.ReduceOp.MAX)
+    e2e = {"value": world * BATCH * e2e_steps / float(e2e_val.item()), "unit": "cell transmissions/s",
+           "h2d_bytes_per_step": int(cond_pin.numel() * 4), "d2h_bytes_per_step": int(exit_pin.numel() * 4)}
+
+    pk = peaks()
+    avg_s = (sum(per_step) / len(per_step)) * 1e-3
+    flops = BATCH * (FLOPS_PER_STEP * ODE_STEPS + FLOPS_COND)
+    achieved = flops / avg_s / 1e12
+    if prec == g.GMC_BF16:
+        roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16"], "unit": "TFLOP/s",
+                "frac": achieved / pk["bf16"], "traffic": None,
+                "peak_source": pk["src"] + " bf16 burst", "kernel": "sampler_tc_kernel"}
+    else:
+        # FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+        alu = 152 * 128 * 2 * 2.07e9 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
+                "frac": achieved / alu, "traffic": None, "peak_source": "derived FP32 FMA peak",
+                "kernel": "sampler_f32_kernel"}
+
+    extras = {}
+    if not args.no_extras:
+        extras = analog_extras(g, ctx, torch)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "cell transmissions/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16" if prec == g.GMC_BF16 else "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "batch": BATCH, "ode_steps": ODE_STEPS,
+                           "integrator": "euler", "precision": args.precision,
+                           "l2": "flushed between steps (256 MiB write)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roof, "e2e": e2e, "gpu_launches": 2 * args.steps,
+                "clocks": clk, "per_step_ms": {"min": min(per_step), "p50": statistics.median(per_step),
+                                               "max": max(per_step)}}
+        line.update(extras)
+        if not args.no_cpu_baseline:
+            try:
+                line["cpu_baseline"] = cpu_baseline()
+            except Exception as ex:  # reported, not fatal
+                line["cpu_baseline"] = {"error": str(ex)[:200]}
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def analog_extras(g, ctx, torch):
+    """GPU analog random walk at tau = 100 (the baseline GMC replaces), same batch."""
+    import synth
+    out = {}
+    n = 1 << 20
+    e = synth.cell_entries(n, 9)
+    xi, cs, sn = (torch.from_numpy(e[k]).cuda() for k in ("xi", "cos", "sin"))
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    ex = torch.empty(4, n, device="cuda")
+    nc = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for c in (0.9, 0.999):
+        tau = torch.full((n,), 100.0, device="cuda")
+        cc = torch.full((n,), c, device="cuda")
+        g.analog_transmit(ctx, n, xi, cs, sn, tau, cc, g.GMC_ABSORB_ANALOG, 1, 0, 0, st, ex, nc)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        g.analog_transmit(ctx, n, xi, cs, sn, tau, cc, g.GMC_ABSORB_ANALOG, 2, 0, 0, st, ex, nc)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        flights = float(nc.double().mean().item())
+        out["analog_tau100_c%s" % c] = {"value": n / (ms * 1e-3), "unit": "cell transmissions/s",
+                                        "mean_collisions": flights, "mode": "analog survival",
+                                        "position_precision": "fp64 (tau > 64)"}
+    return out
+
+
+if __name__ == "__main__":
+    main()
