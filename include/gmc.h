@@ -155,6 +155,29 @@ gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float 
                         uint64_t seed, uint64_t id0, int steps, int integrator, int precision,
                         float *y_raw, float *exit);
 
+/*
+ * gmc_transmit without any device allocation during the call (the paper has
+ * no counterpart: this serves callers that cannot call cudaMalloc, such as
+ * code under a framework that owns the device allocator, code inside a
+ * latency-critical loop or graph-recording section, or hosts that allocate
+ * only at start-up). Same arguments and results as gmc_transmit with
+ * precision GMC_BF16, except:
+ *  - every array must be device memory (host pointers give GMC_EINVAL);
+ *  - steps must be in [1, 256]: the layer-1 bias table lives in a static
+ *    512 KiB device array (512 network evaluations), held by every GPU that
+ *    loads the library until the process exits; larger values give
+ *    GMC_EINVAL;
+ *  - the first call on a device resolves that array's address (and may load
+ *    the library's device code); make it before any stream capture;
+ *  - all calls on a device share the array: calls whose kernels overlap on
+ *    the GPU race and must be serialized by the caller.
+ * Asynchronous on the context's stream; a bounded-wait failure is reported
+ * by the next gmc_synchronize.
+ */
+gmc_status gmc_transmit_noalloc(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
+                                uint64_t seed, uint64_t id0, int steps, int integrator,
+                                float *y_raw, float *exit);
+
 /* ---- analog random-walk transmission (the method GMC replaces) ------------ */
 
 /*

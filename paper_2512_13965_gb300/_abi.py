@@ -63,6 +63,7 @@ def _load():
         "gmc_load_weights": [P, ctypes.c_char_p],
         "gmc_load_weights_buffer": [P, P, sz],
         "gmc_transmit": [P, i64, P, P, u64, u64, i32, i32, i32, P, P],
+        "gmc_transmit_noalloc": [P, i64, P, P, u64, u64, i32, i32, P, P],
         "analog_transmit": [P, i64, P, P, P, P, P, i32, u64, u64, u32, P, P, P],
         "transport_solve": [P, i32, i32, P, P, P, i64, i32, u64, P,
                             ctypes.POINTER(gmc_solve_stats)],
@@ -180,6 +181,11 @@ def gmc_load_weights_buffer(ctx, blob):
 def gmc_transmit(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw, exit):
     return ctx.check(lib.gmc_transmit(ctx.handle, n, _ptr(cond), _ptr(noise), seed, id0, steps,
                                       integrator, precision, _ptr(y_raw), _ptr(exit)))
+
+
+def gmc_transmit_noalloc(ctx, n, cond, noise, seed, id0, steps, integrator, y_raw, exit):
+    return ctx.check(lib.gmc_transmit_noalloc(ctx.handle, n, _ptr(cond), _ptr(noise), seed, id0,
+                                              steps, integrator, _ptr(y_raw), _ptr(exit)))
 
 
 def analog_transmit(ctx, n, xi, cos_in, sin_in, tau, c, mode, seed, id0, event0, status, exit,
