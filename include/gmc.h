@@ -33,7 +33,8 @@
  *    weights, particle banks and scratch.
  *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with counter
  *    (id_lo, id_hi, event, tag) and key (seed_lo, seed_hi); tags: 1 walk
- *    flights, 2 flow-ODE noise, 3 roulette, 4 births. Uniforms lie in (0,1].
+ *    flights, 2 flow-ODE noise, 3 roulette, 4 births, 5 training data,
+ *    6 training batches. Uniforms lie in (0,1].
  */
 #ifndef GMC_H
 #define GMC_H
@@ -85,7 +86,8 @@ typedef struct gmc_solve_stats {
     int64_t roulette_kills; /* histories ended by roulette */
     int64_t waves;          /* event waves of the particle loop */
     int64_t inward_fixes;   /* sampled exit directions that pointed into the cell */
-    double seconds;         /* device time of the solve */
+    double seconds;         /* device time from admission to the last wave */
+    double latency;         /* host wall time from submission to completion */
 } gmc_solve_stats;
 
 /* ---- context ------------------------------------------------------------ */
@@ -224,6 +226,106 @@ gmc_status analog_transmit(gmc_ctx *ctx, int64_t n, const float *xi, const float
 gmc_status transport_solve(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
                            const float *source, int64_t n_histories, int method, uint64_t seed,
                            double *flux, gmc_solve_stats *stats);
+
+/* ---- serving: continuous batching of transport solves ---------------------- */
+
+/* One transport solve (arguments of transport_solve; arrays are host memory
+   and are copied by gmc_submit, so the caller may free them afterwards). */
+typedef struct gmc_solve_req {
+    int nx, ny;
+    const float *tau, *c, *source;
+    int64_t n_histories;
+    uint64_t seed;
+} gmc_solve_req;
+
+typedef struct gmc_serve_config {
+    int method;           /* gmc_method used for every request */
+    size_t memory_budget; /* device bytes for admitted requests' grids and
+                             tallies (24 B per cell, rounded); >= 1 MiB */
+} gmc_serve_config;
+
+/*
+ * Starts a worker thread that runs the wave engine of transport_solve over
+ * every admitted request at once: requests share one particle bank
+ * (bank_capacity from gmc_config), each new wave gives free bank slots to
+ * the births of admitted requests in equal shares, and a request is admitted
+ * (first come, first served) as soon as its grid, CDF and tally fit in the
+ * memory budget and one of 64 request slots is free. Its result equals that
+ * of transport_solve alone (same random numbers; only the order of FP64
+ * additions differs). The server uses its own stream and buffers; loading
+ * weights or changing the configuration while it runs is not supported.
+ */
+gmc_status gmc_serve_start(gmc_ctx *ctx, const gmc_serve_config *cfg);
+/* Queues a solve; *ticket identifies it. GMC_ENOMEM if the request alone
+   exceeds the memory budget, GMC_EINVAL as transport_solve. */
+gmc_status gmc_submit(gmc_ctx *ctx, const gmc_solve_req *req, uint64_t *ticket);
+/* GMC_EBUSY while the request runs; GMC_OK once done, filling flux (host
+   [ny*nx] double, flux per source particle) and stats (nullable); the ticket
+   is then retired. */
+gmc_status gmc_poll(gmc_ctx *ctx, uint64_t ticket, double *flux, gmc_solve_stats *stats);
+/* As gmc_poll, blocking up to timeout_s seconds (GMC_ETIMEOUT after). */
+gmc_status gmc_wait(gmc_ctx *ctx, uint64_t ticket, double timeout_s, double *flux,
+                    gmc_solve_stats *stats);
+/* Stops the worker; unfinished requests are dropped. */
+gmc_status gmc_serve_stop(gmc_ctx *ctx);
+
+/* ---- learning the sampler (conditional flow matching, Eq. 9) ------------ */
+
+/* AdamW and batch options of gmc_train_begin. */
+typedef struct gmc_train_config {
+    int64_t batch;       /* rows per step, in [1, 2^20]; e.g. 8192 */
+    double lr;           /* learning rate, e.g. 1e-3 */
+    double beta1, beta2; /* e.g. 0.9, 0.999 */
+    double eps;          /* e.g. 1e-8 */
+    double weight_decay; /* decoupled weight decay, e.g. 0.01 */
+    uint64_t seed;       /* Philox key of the batch draws (tag 6) */
+} gmc_train_config;
+
+/*
+ * Training data (section "Network Architecture and Inputs": exit states of
+ * pure-scattering Monte Carlo transmissions): for sample i, Philox block
+ * (i, 0, tag 5) gives ln tau uniform in [ln tau_lo, ln tau_hi], c uniform in
+ * [c_lo, c_hi], xi uniform, sin theta uniform in (-1, 1); the implicit-capture
+ * walk (analog_transmit mode GMC_ABSORB_IMPLICIT, flights from event 1) runs
+ * from the left face. cond [5][n] = (xi, cos, sin, ln tau, c) and
+ * y [4][n] = (p, cos theta_out, sin theta_out, ln s): device memory.
+ */
+gmc_status gmc_train_data(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, float tau_hi,
+                          float c_lo, float c_hi, float *cond, float *y);
+/*
+ * Starts training on the device dataset (cond, y as gmc_train_data writes;
+ * the caller keeps them alive while training). Standardization statistics
+ * (mean and standard deviation of the 5 condition and 4 target components)
+ * are computed from the data; the FP32 master weights start from the loaded
+ * network (gmc_load_weights must have been called); AdamW moments start at 0.
+ */
+gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const float *y,
+                           const gmc_train_config *cfg);
+/*
+ * n_steps optimizer steps: batch rows from Philox (row r of step k uses
+ * (k*batch + r, 0, tag 6): sample index, t in (0,1]; (.., 1, tag 6): x0),
+ * x_t = (1-t) x0 + t x1, loss = mean_b ||v(x_t, t | c) - (x1 - x0)||^2
+ * (Eq. 9), hand-written backward, AdamW:
+ * p <- p (1 - lr wd) - lr m_hat / (sqrt(v_hat) + eps).
+ * losses: host [n_steps] float, nullable (blocking when given).
+ */
+gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses);
+/*
+ * Loss and gradient of Eq. 9 at the current master weights for an explicit
+ * batch (host arrays): cn [B][5] standardized conditions, x1 [B][4]
+ * standardized targets, x0 [B][4] noise, t [B]. grad: host array of
+ * gmc_train_param_count() floats in the order W1 [256][32] (input columns
+ * 25..31 are padding), b1, W2, b2, W3, b3, W4, b4, W5 [4][256], b5.
+ * B must not exceed the configured batch.
+ */
+gmc_status gmc_train_grad(gmc_ctx *ctx, int64_t B, const float *cn, const float *x1,
+                          const float *x0, const float *t, double *loss, float *grad);
+/* Copies the FP32 master weights (layout of gmc_train_grad) to host `out`. */
+gmc_status gmc_train_params(gmc_ctx *ctx, float *out);
+int64_t gmc_train_param_count(void);
+/* Makes the trained network (with its standardization) the sampler's
+   network; also writes it as a GMCW file when `path` is not null. */
+gmc_status gmc_train_commit(gmc_ctx *ctx, const char *path);
 
 #ifdef __cplusplus
 }

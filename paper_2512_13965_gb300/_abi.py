@@ -33,10 +33,26 @@ class gmc_solve_stats(ctypes.Structure):
                 ("roulette_net", ctypes.c_double), ("transmissions", ctypes.c_int64),
                 ("collisions", ctypes.c_int64), ("roulette_kills", ctypes.c_int64),
                 ("waves", ctypes.c_int64), ("inward_fixes", ctypes.c_int64),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("latency", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class gmc_solve_req(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("tau", ctypes.c_void_p),
+                ("c", ctypes.c_void_p), ("source", ctypes.c_void_p),
+                ("n_histories", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+
+
+class gmc_serve_config(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("memory_budget", ctypes.c_size_t)]
+
+
+class gmc_train_config(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int64), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("weight_decay", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 class GMCError(RuntimeError):
@@ -67,11 +83,25 @@ def _load():
         "analog_transmit": [P, i64, P, P, P, P, P, i32, u64, u64, u32, P, P, P],
         "transport_solve": [P, i32, i32, P, P, P, i64, i32, u64, P,
                             ctypes.POINTER(gmc_solve_stats)],
+        "gmc_serve_start": [P, ctypes.POINTER(gmc_serve_config)],
+        "gmc_submit": [P, ctypes.POINTER(gmc_solve_req), ctypes.POINTER(ctypes.c_uint64)],
+        "gmc_poll": [P, u64, P, ctypes.POINTER(gmc_solve_stats)],
+        "gmc_wait": [P, u64, ctypes.c_double, P, ctypes.POINTER(gmc_solve_stats)],
+        "gmc_serve_stop": [P],
+        "gmc_train_data": [P, i64, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, P, P],
+        "gmc_train_begin": [P, i64, P, P, ctypes.POINTER(gmc_train_config)],
+        "gmc_train_steps": [P, i64, P],
+        "gmc_train_grad": [P, i64, P, P, P, P, P, P],
+        "gmc_train_params": [P, P],
+        "gmc_train_commit": [P, ctypes.c_char_p],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    L.gmc_train_param_count.argtypes = []
+    L.gmc_train_param_count.restype = ctypes.c_int64
     L.gmc_status_str.argtypes = [ctypes.c_int]
     L.gmc_status_str.restype = ctypes.c_char_p
     L.gmc_last_error.argtypes = [P]
@@ -200,3 +230,69 @@ def transport_solve(ctx, nx, ny, tau, c, source, n_histories, method, seed, flux
     ctx.check(lib.transport_solve(ctx.handle, nx, ny, _ptr(tau), _ptr(c), _ptr(source),
                                   n_histories, method, seed, _ptr(flux), ctypes.byref(st)))
     return st
+
+
+def gmc_train_data(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
+    return ctx.check(lib.gmc_train_data(ctx.handle, n, seed, tau_lo, tau_hi, c_lo, c_hi,
+                                        _ptr(cond), _ptr(y)))
+
+
+def gmc_train_begin(ctx, n, cond, y, cfg):
+    return ctx.check(lib.gmc_train_begin(ctx.handle, n, _ptr(cond), _ptr(y), ctypes.byref(cfg)))
+
+
+def gmc_train_steps(ctx, n_steps, losses=None):
+    return ctx.check(lib.gmc_train_steps(ctx.handle, n_steps, _ptr(losses)))
+
+
+def gmc_train_grad(ctx, B, cn, x1, x0, t, grad):
+    loss = ctypes.c_double()
+    ctx.check(lib.gmc_train_grad(ctx.handle, B, _ptr(cn), _ptr(x1), _ptr(x0), _ptr(t),
+                                 ctypes.byref(loss), _ptr(grad)))
+    return loss.value
+
+
+def gmc_train_params(ctx, out):
+    return ctx.check(lib.gmc_train_params(ctx.handle, _ptr(out)))
+
+
+def gmc_train_param_count():
+    return int(lib.gmc_train_param_count())
+
+
+def gmc_train_commit(ctx, path=None):
+    return ctx.check(lib.gmc_train_commit(ctx.handle, None if path is None else os.fsencode(path)))
+
+
+def gmc_serve_start(ctx, method, memory_budget):
+    cfg = gmc_serve_config(method=method, memory_budget=memory_budget)
+    return ctx.check(lib.gmc_serve_start(ctx.handle, ctypes.byref(cfg)))
+
+
+def gmc_submit(ctx, nx, ny, tau, c, source, n_histories, seed):
+    """tau, c, source: host float32 arrays of ny*nx cells; returns the ticket."""
+    req = gmc_solve_req(nx=nx, ny=ny, tau=_ptr(tau), c=_ptr(c), source=_ptr(source),
+                        n_histories=n_histories, seed=seed)
+    t = ctypes.c_uint64()
+    ctx.check(lib.gmc_submit(ctx.handle, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def gmc_poll(ctx, ticket, flux):
+    """Returns stats when done, None while the request runs."""
+    st = gmc_solve_stats()
+    s = lib.gmc_poll(ctx.handle, ticket, _ptr(flux), ctypes.byref(st))
+    if s == GMC_EBUSY:
+        return None
+    ctx.check(s)
+    return st
+
+
+def gmc_wait(ctx, ticket, timeout_s, flux):
+    st = gmc_solve_stats()
+    ctx.check(lib.gmc_wait(ctx.handle, ticket, timeout_s, _ptr(flux), ctypes.byref(st)))
+    return st
+
+
+def gmc_serve_stop(ctx):
+    return ctx.check(lib.gmc_serve_stop(ctx.handle))

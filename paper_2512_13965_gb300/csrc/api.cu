@@ -185,12 +185,13 @@ gmc_status gmc_create(gmc_ctx **out, int device) {
 gmc_status gmc_destroy(gmc_ctx *ctx) {
   if (!ctx) return GMC_OK;
   cudaSetDevice(ctx->device);
+  if (ctx->server) server_free(ctx->server);
+  if (ctx->solver) engine_free(ctx->solver);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (auto &b : ctx->stage)
     if (b.ptr) cudaFree(b.ptr);
-  for (auto &b : ctx->solve)
-    if (b.ptr) cudaFree(b.ptr);
   if (ctx->bias1.ptr) cudaFree(ctx->bias1.ptr);
+  if (ctx->train) train_state_free(ctx->train);
   if (ctx->d_f32) cudaFree(ctx->d_f32);
   if (ctx->d_tc) cudaFree(ctx->d_tc);
   if (ctx->d_tc_bias) cudaFree(ctx->d_tc_bias);

@@ -30,6 +30,14 @@ struct NetStats {
 
 // Packed operands of the tensor-core path (built by sampler_tc.cu).
 struct NetTC;
+// Training state (train.cu).
+struct TrainState;
+void train_state_free(TrainState *t);
+// Wave engine of transport_solve and the serving thread (transport.cu).
+class Engine;
+struct Server;
+void engine_free(Engine *e);
+void server_free(Server *s);
 
 struct Buffer {
   void *ptr = nullptr;
@@ -58,12 +66,16 @@ struct gmc_ctx {
   float *d_tc_bias = nullptr;  // per-layer biases for the tensor-core path
   int *d_err = nullptr;        // device error word (bounded waits)
 
+  // training state (gmc_train_begin .. gmc_destroy)
+  gmc::TrainState *train = nullptr;
+
   // staging buffers for host-pointer calls
   gmc::Buffer stage[8];
   // per-evaluation layer-1 bias of the tensor-core sampler
   gmc::Buffer bias1;
-  // transport-solve scratch
-  gmc::Buffer solve[16];
+  // transport_solve engine (kept between calls) and the serving thread
+  gmc::Engine *solver = nullptr;
+  gmc::Server *server = nullptr;
 };
 
 namespace gmc {

@@ -13,12 +13,15 @@
 //   L1: [cn | x_hi | x_lo] (K = 16, BF16) x B1 (N = 256)       -> TMEM
 //       (the time-embedding columns of layer 1 are the same for every row,
 //        so W1[:, emb] emb(t) + b1 is folded into an FP32 per-evaluation bias)
-//   L2..L4: A (128 x 256 BF16, shared memory) x W (256 x 256, streamed in
-//       16 KB chunks of 128 output rows x 64 K) -> TMEM, N = 128 per MMA
+//   L2..L4: A (128 x 256 BF16, shared memory, 128-byte swizzle) x W
+//       (256 x 256, streamed in 16 KB chunks of all 256 output rows x 32 K,
+//       64-byte swizzle) -> TMEM, N = 256 per MMA
 //   L5: A x W5 (N = 16, rows 4..15 zero) -> TMEM columns 0..3
-// Epilogue: SiLU(z) = h + h tanh(h) with h = z/2, written back as the next
-// layer's BF16 operand in the 128-byte-swizzled K-major layout. The ODE
-// state x stays in FP32 registers of the row's epilogue thread.
+// Epilogue: SiLU(z) = h + h tanh(h) with h = z/2 (layers 1-4 are packed with
+// weights and biases halved, so the accumulator holds h), in packed BF16x2,
+// written back as the next layer's BF16 operand in the 128-byte-swizzled
+// K-major layout. The ODE state x stays in FP32 registers of the row's
+// epilogue thread.
 //
 // Roles: warp 0 streams weights, warp 1 owns tensor memory and issues MMAs,
 // warps 2..9 are the epilogue (two threads per row, one per column half).
@@ -39,8 +42,8 @@ using namespace ptx;
 
 constexpr int TM = 128;
 constexpr int NST = 5;                  // weight-chunk stages
-constexpr uint32_t CHUNK = 16384;       // 128 rows x 64 K x 2 bytes
-constexpr int CHUNKS = 8;               // per hidden layer: 4 K-blocks x 2 row halves
+constexpr uint32_t CHUNK = 16384;       // 256 rows x 32 K x 2 bytes
+constexpr int CHUNKS = 8;               // per hidden layer: K in slices of 32
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
 constexpr uint32_t TMEM_COLS = 512;     // two 128 x 256 FP32 accumulators
@@ -80,15 +83,16 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return u;
 }
 
-__device__ __forceinline__ float tanh_approx(float x) {
-  float y;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ float silu_fast(float z) {
-  const float h = 0.5f * z;
-  return fmaf(h, tanh_approx(h), h);
+// SiLU on two pre-activations already halved (the packed weights and biases
+// of layers 1-4 carry a factor 1/2, exact in BF16): with h = z/2,
+// SiLU(z) = z sigmoid(z) = h + h tanh(h). Packed BF16x2: one MUFU op and one
+// FMA for two outputs, already in the operand format of the next layer.
+__device__ __forceinline__ uint32_t silu2_halved(float h0, float h1) {
+  uint32_t h, t, o;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(h1), "f"(h0));
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
+  asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(o) : "r"(h), "r"(t));
+  return o;
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
@@ -130,7 +134,7 @@ __device__ __forceinline__ void write_a1(uint32_t a_base, int r, const float (&c
 
 // bias + SiLU on 32 accumulator columns starting at col0, stored as four
 // 16-byte chunks of the next layer's operand row r.
-__device__ __forceinline__ void epi32(const float (&v)[32], const float *__restrict__ bias,
+__device__ __forceinline__ void epi32(const uint32_t (&v)[32], const float *__restrict__ bias,
                                       int col0, uint32_t a_base, int r) {
   const float4 *b4 = reinterpret_cast<const float4 *>(bias + col0);
   const uint32_t kb_base = a_base + (uint32_t)(col0 >> 6) * 16384u;
@@ -138,12 +142,12 @@ __device__ __forceinline__ void epi32(const float (&v)[32], const float *__restr
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const float4 ba = __ldg(b4 + 2 * j), bb = __ldg(b4 + 2 * j + 1);
-    const float *p = v + 8 * j;
+    const uint32_t *p = v + 8 * j;
     st_shared_v4(sw128(kb_base, r, c0 + j),
-                 pack_bf16x2(silu_fast(p[0] + ba.x), silu_fast(p[1] + ba.y)),
-                 pack_bf16x2(silu_fast(p[2] + ba.z), silu_fast(p[3] + ba.w)),
-                 pack_bf16x2(silu_fast(p[4] + bb.x), silu_fast(p[5] + bb.y)),
-                 pack_bf16x2(silu_fast(p[6] + bb.z), silu_fast(p[7] + bb.w)));
+                 silu2_halved(__uint_as_float(p[0]) + ba.x, __uint_as_float(p[1]) + ba.y),
+                 silu2_halved(__uint_as_float(p[2]) + ba.z, __uint_as_float(p[3]) + ba.w),
+                 silu2_halved(__uint_as_float(p[4]) + bb.x, __uint_as_float(p[5]) + bb.y),
+                 silu2_halved(__uint_as_float(p[6]) + bb.z, __uint_as_float(p[7]) + bb.w));
   }
 }
 
@@ -237,8 +241,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
       bool ok = mbar_wait(&B.res_full, 0, abort);
       if (!ok) fail(B, P.err, 2);
       uint32_t it = 0, aph[2] = {0, 0};
-      const uint32_t id256 = idesc_bf16_m128(256), id128 = idesc_bf16_m128(128),
-                     id16 = idesc_bf16_m128(16);
+      const uint32_t id256 = idesc_bf16_m128(256), id16 = idesc_bf16_m128(16);
       for (int64_t pr = blockIdx.x; pr < npairs && ok; pr += gridDim.x)
         for (int e = 0; e < P.n_eval && ok; ++e)
           for (int L = 0; L < 5 && ok; ++L)
@@ -264,14 +267,14 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
                     break;
                   }
                   tc_fence_after();
-                  const int kb = ch >> 1, nh = ch & 1;
+                  // chunk ch = K columns 32 ch .. 32 ch + 31 of all 256 output rows
+                  const uint32_t a_k = a + (uint32_t)(ch >> 1) * 16384u + (uint32_t)(ch & 1) * 64u;
                   const uint32_t bst = sbase + S_ST + (uint32_t)s * CHUNK;
 #pragma unroll
-                  for (int k = 0; k < 4; ++k)
-                    mma_f16(d + (uint32_t)nh * 128u,
-                            smem_desc(a + (uint32_t)kb * 16384u + (uint32_t)k * 32u, 1024, kSwizzle128B),
-                            smem_desc(bst + (uint32_t)k * 32u, 1024, kSwizzle128B), id128,
-                            (kb | k) != 0);
+                  for (int k = 0; k < 2; ++k)
+                    mma_f16(d, smem_desc(a_k + (uint32_t)k * 32u, 1024, kSwizzle128B),
+                            smem_desc(bst + (uint32_t)k * 32u, 512, kSwizzle64B), id256,
+                            (ch | k) != 0);
                   mma_commit(&B.empty[s]);
                   ++it;
                 }
@@ -341,15 +344,21 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
             const float *bias = L == 0 ? P.bias1 + (size_t)e * 256 : P.bias + L * 256;
             const uint32_t a_base = sbase + (T ? S_A1 : S_A0);
             const uint32_t tcol = tmem + lane_off + (uint32_t)T * 256u + (uint32_t)hf * 128u;
-#pragma unroll
-            for (int jj = 0; jj < 4; jj += 2) {
-              float v0[32], v1[32];
-              tmem_ld32(tcol + (uint32_t)(jj * 32), v0);
-              tmem_ld32(tcol + (uint32_t)(jj * 32 + 32), v1);
-              tmem_wait_ld();
-              epi32(v0, bias, hf * 128 + jj * 32, a_base, r);
-              epi32(v1, bias, hf * 128 + jj * 32 + 32, a_base, r);
-            }
+            // software pipeline: the load of chunk j+1 is in flight while
+            // chunk j is converted and stored
+            uint32_t va[32], vb[32];
+            tmem_ld32_raw(tcol, va);
+            tmem_wait_ld_regs(va);
+            tmem_ld32_raw(tcol + 32u, vb);
+            epi32(va, bias, hf * 128, a_base, r);
+            tmem_wait_ld_regs(vb);
+            tmem_ld32_raw(tcol + 64u, va);
+            epi32(vb, bias, hf * 128 + 32, a_base, r);
+            tmem_wait_ld_regs(va);
+            tmem_ld32_raw(tcol + 96u, vb);
+            epi32(va, bias, hf * 128 + 64, a_base, r);
+            tmem_wait_ld_regs(vb);
+            epi32(vb, bias, hf * 128 + 96, a_base, r);
             fence_proxy_async_smem();
             tc_fence_before();
             __syncwarp();
@@ -368,7 +377,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
           if (hf == 0) {
             float v[4];
             tmem_ld4(tmem + lane_off + (uint32_t)T * 256u, v);
-            tmem_wait_ld();
+            tmem_wait_ld_regs4(v);
 #pragma unroll
             for (int d = 0; d < 4; ++d) v[d] += __ldg(P.bias + 4 * 256 + d);
             float *xin = x[T];
@@ -430,7 +439,7 @@ __global__ void layer1_bias_kernel(const float *__restrict__ w1t, const float *_
                                              : (float)e * h;
   float acc = b1[c];
   for (int j = 0; j < kEmb; ++j) acc = fmaf(w1t[(kCond + kState + j) * kHidden + c], time_embedding(j, t), acc);
-  out[(size_t)e * kHidden + c] = acc;
+  out[(size_t)e * kHidden + c] = 0.5f * acc;  // layers 1-4 carry a factor 1/2
 }
 
 uint16_t bf16_bits(float f) {
@@ -444,6 +453,12 @@ uint16_t bf16_bits(float f) {
 size_t sw128_off(int row, int k) {
   const int c = k >> 3, e = k & 7;
   return (size_t)((row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4) + e * 2);
+}
+
+// element (row, k) of a 64-byte-swizzled K-major block whose rows are 64 B
+size_t sw64_off(int row, int k) {
+  const int c = k >> 3, e = k & 7;
+  return (size_t)((row >> 3) * 512 + (row & 7) * 64 + ((c ^ ((row >> 1) & 3)) << 4) + e * 2);
 }
 
 size_t sw32_off(int row, int k) {
@@ -463,22 +478,21 @@ void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *pack
     const uint16_t u = bf16_bits(v);
     std::memcpy(P + off, &u, 2);
   };
-  // hidden layers W2..W4: chunk (kb, nh) holds output rows nh*128.. and K kb*64..
+  // hidden layers W2..W4: chunk ch holds all 256 output rows and K 32 ch ..
   for (int L = 0; L < 3; ++L)
     for (int ch = 0; ch < CHUNKS; ++ch) {
-      const int kb = ch >> 1, nh = ch & 1;
       const size_t base = OFF_HID + (size_t)(L * CHUNKS + ch) * CHUNK;
-      for (int i = 0; i < 128; ++i)
-        for (int j = 0; j < 64; ++j)
-          put(base + sw128_off(i, j), W[L + 1][(nh * 128 + i) * 256 + kb * 64 + j]);
+      for (int i = 0; i < 256; ++i)
+        for (int j = 0; j < 32; ++j)
+          put(base + sw64_off(i, j), 0.5f * W[L + 1][i * 256 + ch * 32 + j]);
     }
   // layer 1: [cond (5), x (4) for x_hi, x (4) again for x_lo, 0 0 0]
   for (int nrow = 0; nrow < 256; ++nrow) {
     const float *w = &W[0][nrow * 25];
-    for (int k = 0; k < 5; ++k) put(OFF_B1 + sw32_off(nrow, k), w[k]);
+    for (int k = 0; k < 5; ++k) put(OFF_B1 + sw32_off(nrow, k), 0.5f * w[k]);
     for (int k = 0; k < 4; ++k) {
-      put(OFF_B1 + sw32_off(nrow, 5 + k), w[5 + k]);
-      put(OFF_B1 + sw32_off(nrow, 9 + k), w[5 + k]);
+      put(OFF_B1 + sw32_off(nrow, 5 + k), 0.5f * w[5 + k]);
+      put(OFF_B1 + sw32_off(nrow, 9 + k), 0.5f * w[5 + k]);
     }
   }
   // output layer: 16 rows (4 real) x 256 K in four 128-byte-swizzled K-blocks
@@ -487,7 +501,7 @@ void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *pack
       put(OFF_B5 + (size_t)(k >> 6) * 2048 + sw128_off(d, k & 63), W[4][d * 256 + k]);
   for (int i = 0; i < 5 * 256; ++i) bias_host[i] = 0.0f;
   for (int L = 1; L < 4; ++L)
-    for (int c = 0; c < 256; ++c) bias_host[L * 256 + c] = b[L][c];
+    for (int c = 0; c < 256; ++c) bias_host[L * 256 + c] = 0.5f * b[L][c];
   for (int d = 0; d < 4; ++d) bias_host[4 * 256 + d] = b[4][d];
 }
 

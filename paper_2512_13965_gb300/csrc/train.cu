@@ -1,0 +1,564 @@
+// Training of the velocity network by conditional flow matching (Eq. 9) on
+// transmissions generated by the GPU random walk.
+//
+//  gmc_train_data   a11: tau log-uniform, c uniform, xi uniform, sin(theta)
+//                   uniform (Philox tag 5, one block per sample), then the
+//                   implicit-capture walk (flights at rate c) from the left
+//                   face -> targets y = (p, cos theta_out, sin theta_out, ln s).
+//  gmc_train_begin  standardization statistics of the data (FP64 sums), FP32
+//                   master weights copied from the loaded network, AdamW state.
+//  gmc_train_steps  a12 + a13 per step: batch rows drawn with Philox (tag 6):
+//                   sample index, t ~ U(0,1], x0 ~ N(0, I); x_t = (1-t) x0 + t x1,
+//                   target x1 - x0; forward through the MLP keeping
+//                   pre-activations; loss = mean_b ||v - (x1 - x0)||^2;
+//                   hand-derived backward; AdamW (decoupled weight decay).
+//
+// The dense layers run on a tiled FP32 SIMT GEMM with fused epilogues
+// (bias + SiLU forward, SiLU' backward), accumulating in FP32.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "decode.cuh"
+#include "gmc_internal.cuh"
+#include "philox.cuh"
+#include "walk.cuh"
+
+namespace gmc {
+
+constexpr uint32_t kTagData = 5u, kTagTrain = 6u;
+
+// parameter block offsets (floats): W1 [256][32] (columns 25..31 zero), b1,
+// W2, b2, W3, b3, W4, b4 ([256][256], [256]), W5 [4][256], b5 [4]
+constexpr int64_t P_W1 = 0, P_B1 = 8192, P_W2 = P_B1 + 256, P_B2 = P_W2 + 65536,
+                  P_W3 = P_B2 + 256, P_B3 = P_W3 + 65536, P_W4 = P_B3 + 256,
+                  P_B4 = P_W4 + 65536, P_W5 = P_B4 + 256, P_B5 = P_W5 + 1024,
+                  P_TOTAL = P_B5 + 4;
+
+struct TrainState {
+  int64_t n = 0;
+  const float *cond = nullptr, *y = nullptr;
+  float stats[18];
+  gmc_train_config cfg{};
+  int64_t step = 0;
+  float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
+  int64_t B = 0;
+  float *X0 = nullptr, *U = nullptr, *Z[4] = {}, *A[4] = {}, *V = nullptr, *dZ[2] = {},
+        *dV = nullptr;
+  double *loss = nullptr;  // [max steps per call]
+  int64_t loss_cap = 0;
+  double *stat_acc = nullptr;  // 18 sums
+};
+
+namespace {
+
+__global__ void data_kernel(int64_t n, uint64_t seed, float ltau_lo, float ltau_hi, float c_lo,
+                            float c_hi, float *__restrict__ cond, float *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 r = philox_draw(seed, (uint64_t)i, 0u, kTagData);
+  const float ltau = ltau_lo + (ltau_hi - ltau_lo) * u01(r.x);
+  const float tau = expf(ltau);
+  const float c = c_lo + (c_hi - c_lo) * u01(r.y);
+  const float xi = u01(r.z);
+  const float sn = fmaf(2.0f, u01(r.w), -1.0f);
+  const float cs = sqrtf(fmaxf(1.0f - sn * sn, 0.0f));
+  const WalkResult w = walk_cell(tau, c, 1, 0.0f, xi, cs, sn, seed, (uint64_t)i, 1u);
+  cond[i] = xi;
+  cond[n + i] = cs;
+  cond[2 * n + i] = sn;
+  cond[3 * n + i] = ltau;
+  cond[4 * n + i] = c;
+  y[i] = (float)(w.face < 0 ? 0 : w.face) + w.q;
+  y[n + i] = w.ux;
+  y[2 * n + i] = w.uy;
+  y[3 * n + i] = logf(fmaxf(w.s, kSMin));
+}
+
+// sums and sums of squares of the 9 features (FP64)
+__global__ void stats_kernel(int64_t n, const float *__restrict__ cond, const float *__restrict__ y,
+                             double *acc) {
+  __shared__ double sh[18];
+  if (threadIdx.x < 18) sh[threadIdx.x] = 0.0;
+  __syncthreads();
+  double loc[18];
+  for (int k = 0; k < 18; ++k) loc[k] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < 9; ++k) {
+      const double v = k < 5 ? cond[k * n + i] : y[(k - 5) * n + i];
+      loc[k] += v;
+      loc[9 + k] += v * v;
+    }
+  }
+  for (int k = 0; k < 18; ++k) {
+    double v = loc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&sh[k], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < 18) atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
+}
+
+struct Std {
+  float cm[5], cis[5], ym[4], yis[4];
+};
+
+// One batch row: sample index, t, x0 -> X0 row [cn, x_t, emb(t), 0...], U row.
+__global__ void batch_kernel(int64_t B, int64_t n, const float *__restrict__ cond,
+                             const float *__restrict__ y, Std sd, uint64_t seed, int64_t step,
+                             float *__restrict__ X0, float *__restrict__ U) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const uint64_t rid = (uint64_t)step * (uint64_t)B + (uint64_t)b;
+  const uint4 r = philox_draw(seed, rid, 0u, kTagTrain);
+  const int64_t idx = (int64_t)(((uint64_t)r.x * (uint64_t)n) >> 32);
+  const float t = u01(r.y);
+  const float4 z = box_muller4(philox_draw(seed, rid, 1u, kTagTrain));
+  const float x0[4] = {z.x, z.y, z.z, z.w};
+  float *row = X0 + b * 32;
+  for (int k = 0; k < 5; ++k) row[k] = (cond[k * n + idx] - sd.cm[k]) * sd.cis[k];
+  for (int d = 0; d < 4; ++d) {
+    const float x1 = (y[d * n + idx] - sd.ym[d]) * sd.yis[d];
+    row[5 + d] = (1.0f - t) * x0[d] + t * x1;
+    U[b * 4 + d] = x1 - x0[d];
+  }
+  for (int j = 0; j < 16; ++j) row[9 + j] = time_embedding(j, t);
+  for (int k = 25; k < 32; ++k) row[k] = 0.0f;
+}
+
+// Batch rows from explicit inputs (gradient check): cn [B][5], x1, x0 [B][4], t [B].
+__global__ void batch_explicit_kernel(int64_t B, const float *cn, const float *x1,
+                                      const float *x0, const float *tt, float *X0, float *U) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const float t = tt[b];
+  float *row = X0 + b * 32;
+  for (int k = 0; k < 5; ++k) row[k] = cn[b * 5 + k];
+  for (int d = 0; d < 4; ++d) {
+    row[5 + d] = (1.0f - t) * x0[b * 4 + d] + t * x1[b * 4 + d];
+    U[b * 4 + d] = x1[b * 4 + d] - x0[b * 4 + d];
+  }
+  for (int j = 0; j < 16; ++j) row[9 + j] = time_embedding(j, t);
+  for (int k = 25; k < 32; ++k) row[k] = 0.0f;
+}
+
+enum Epi { kEpiStore = 0, kEpiBiasSilu = 1, kEpiBias = 2, kEpiDSilu = 3 };
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// C[M][N] = sum_k A(m,k) B(k,n), A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn].
+// 64x64 tile, 256 threads, 4x4 outputs per thread, K in slices of 16.
+template <int EPI>
+__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float *__restrict__ A,
+                                                   int64_t sam, int64_t sak,
+                                                   const float *__restrict__ Bm, int64_t sbk,
+                                                   int64_t sbn, float *__restrict__ C,
+                                                   const float *__restrict__ bias,
+                                                   float *__restrict__ C2,
+                                                   const float *__restrict__ Zp) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int kk = e & 15, mm = e >> 4;
+      const int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? A[gm * sam + gk * sak] : 0.0f;
+      const int nn = e & 63, kb = e >> 6;
+      const int gn = n0 + nn, gk2 = k0 + kb;
+      Bs[kb][nn] = (gn < N && gk2 < K) ? Bm[gk2 * sbk + gn * sbn] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nn = n0 + tx + 16 * j;
+      if (nn >= N) continue;
+      float v = acc[i][j];
+      const int64_t o = (int64_t)m * N + nn;
+      if (EPI == kEpiBiasSilu) {
+        v += bias[nn];
+        C[o] = v;                       // pre-activation z (kept for backward)
+        C2[o] = v * sigmoidf_(v);       // SiLU(z)
+      } else if (EPI == kEpiBias) {
+        C[o] = v + bias[nn];
+      } else if (EPI == kEpiDSilu) {
+        const float z = Zp[o], s = sigmoidf_(z);
+        C[o] = v * (s * (1.0f + z * (1.0f - s)));
+      } else {
+        C[o] = v;
+      }
+    }
+  }
+}
+
+template <int EPI>
+cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float *A, int64_t sam, int64_t sak,
+                 const float *B, int64_t sbk, int64_t sbn, float *C, const float *bias = nullptr,
+                 float *C2 = nullptr, const float *Zp = nullptr) {
+  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  gemm_kernel<EPI><<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, bias, C2, Zp);
+  return cudaGetLastError();
+}
+
+// loss and dV = 2 (v - u) / B
+__global__ void loss_kernel(int64_t B, const float *__restrict__ V, const float *__restrict__ U,
+                            float *__restrict__ dV, double *loss) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double part = 0.0;
+  if (b < B) {
+    for (int d = 0; d < 4; ++d) {
+      const float r = V[b * 4 + d] - U[b * 4 + d];
+      part += (double)r * r;
+      dV[b * 4 + d] = 2.0f * r / (float)B;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(loss, part / (double)B);
+}
+
+// db[n] = sum_b dZ[b][n]
+__global__ void colsum_kernel(int64_t B, int N, const float *__restrict__ dZ, float *__restrict__ db) {
+  const int n = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int lane_row = threadIdx.x >> 5;  // 8 row groups
+  float acc = 0.0f;
+  if (n < N)
+    for (int64_t b = lane_row; b < B; b += 8) acc += dZ[b * N + n];
+  __shared__ float sh[8][33];
+  sh[lane_row][threadIdx.x & 31] = acc;
+  __syncthreads();
+  if (lane_row == 0 && n < N) {
+    float s = 0.0f;
+    for (int r = 0; r < 8; ++r) s += sh[r][threadIdx.x & 31];
+    db[n] = s;
+  }
+}
+
+__global__ void adamw_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g,
+                             float *__restrict__ m, float *__restrict__ v, float lr, float b1,
+                             float b2, float eps, float wd, float bc1, float bc2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float mh = mi / bc1, vh = vi / bc2;
+  p[i] = p[i] * (1.0f - lr * wd) - lr * mh / (sqrtf(vh) + eps);
+}
+
+inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// forward + loss + backward for the batch already in X0/U; grads overwritten
+cudaError_t fwd_bwd(cudaStream_t s, TrainState &T, double *loss_slot) {
+  const int B = (int)T.B;
+  float *P = T.params, *G = T.grads;
+  const float *W[4] = {P + P_W1, P + P_W2, P + P_W3, P + P_W4};
+  const float *bb[4] = {P + P_B1, P + P_B2, P + P_B3, P + P_B4};
+  cudaError_t e;
+  // forward: Z_l = A_{l-1} W_l^T + b_l, A_l = SiLU(Z_l)
+  e = gemm<kEpiBiasSilu>(s, B, 256, 32, T.X0, 32, 1, W[0], 1, 32, T.Z[0], bb[0], T.A[0]);
+  if (e) return e;
+  for (int l = 1; l < 4; ++l) {
+    e = gemm<kEpiBiasSilu>(s, B, 256, 256, T.A[l - 1], 256, 1, W[l], 1, 256, T.Z[l], bb[l], T.A[l]);
+    if (e) return e;
+  }
+  e = gemm<kEpiBias>(s, B, 4, 256, T.A[3], 256, 1, P + P_W5, 1, 256, T.V, P + P_B5);
+  if (e) return e;
+  loss_kernel<<<nb(B, 256), 256, 0, s>>>(B, T.V, T.U, T.dV, loss_slot);
+  // output layer: dW5 = dV^T A4, db5 = sum dV, dZ4 = (dV W5) * SiLU'(Z4)
+  e = gemm<kEpiStore>(s, 4, 256, B, T.dV, 1, 4, T.A[3], 256, 1, G + P_W5);
+  if (e) return e;
+  colsum_kernel<<<1, 256, 0, s>>>(B, 4, T.dV, G + P_B5);
+  e = gemm<kEpiDSilu>(s, B, 256, 4, T.dV, 4, 1, P + P_W5, 256, 1, T.dZ[0], nullptr, nullptr, T.Z[3]);
+  if (e) return e;
+  int cur = 0;
+  const int64_t wofs[4] = {P_W1, P_W2, P_W3, P_W4}, bofs[4] = {P_B1, P_B2, P_B3, P_B4};
+  for (int l = 3; l >= 0; --l) {
+    const float *dz = T.dZ[cur];
+    const float *ain = l == 0 ? T.X0 : T.A[l - 1];
+    const int kin = l == 0 ? 32 : 256;
+    // dW_l = dZ_l^T A_{l-1}; db_l = column sums of dZ_l
+    e = gemm<kEpiStore>(s, 256, kin, B, dz, 1, 256, ain, kin, 1, G + wofs[l]);
+    if (e) return e;
+    colsum_kernel<<<8, 256, 0, s>>>(B, 256, dz, G + bofs[l]);
+    if (l > 0) {
+      // dZ_{l-1} = (dZ_l W_l) * SiLU'(Z_{l-1})
+      e = gemm<kEpiDSilu>(s, B, 256, 256, dz, 256, 1, P + wofs[l], 256, 1, T.dZ[cur ^ 1], nullptr,
+                          nullptr, T.Z[l - 1]);
+      if (e) return e;
+      cur ^= 1;
+    }
+  }
+  return cudaGetLastError();
+}
+
+void free_train(TrainState *T) {
+  if (!T) return;
+  float *bufs[] = {T->params, T->grads, T->m, T->v, T->X0, T->U, T->V, T->dV, T->Z[0], T->Z[1],
+                   T->Z[2], T->Z[3], T->A[0], T->A[1], T->A[2], T->A[3], T->dZ[0], T->dZ[1]};
+  for (float *b : bufs)
+    if (b) cudaFree(b);
+  if (T->loss) cudaFree(T->loss);
+  if (T->stat_acc) cudaFree(T->stat_acc);
+  delete T;
+}
+
+cudaError_t alloc_batch(TrainState &T, int64_t B) {
+  if (T.B >= B) return cudaSuccess;
+  float **bufs[] = {&T.X0, &T.U, &T.V, &T.dV, &T.Z[0], &T.Z[1], &T.Z[2], &T.Z[3],
+                    &T.A[0], &T.A[1], &T.A[2], &T.A[3], &T.dZ[0], &T.dZ[1]};
+  const int64_t sizes[] = {B * 32, B * 4, B * 4, B * 4, B * 256, B * 256, B * 256, B * 256,
+                           B * 256, B * 256, B * 256, B * 256, B * 256, B * 256};
+  for (int i = 0; i < 14; ++i) {
+    if (*bufs[i]) cudaFree(*bufs[i]);
+    *bufs[i] = nullptr;
+    cudaError_t e = cudaMalloc(bufs[i], sizes[i] * sizeof(float));
+    if (e) return e;
+  }
+  T.B = B;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+void train_state_free(TrainState *T) { free_train(T); }
+
+}  // namespace gmc
+
+using namespace gmc;
+
+extern "C" {
+
+gmc_status gmc_train_data(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, float tau_hi,
+                          float c_lo, float c_hi, float *cond, float *y) {
+  if (!ctx) return GMC_EINVAL;
+  if (n < 0 || (n > 0 && (!cond || !y))) return set_error(ctx, GMC_EINVAL, "gmc_train_data: bad arguments");
+  if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_data: need 0 < tau_lo <= tau_hi, 0 <= c_lo <= c_hi <= 1");
+  if (n == 0) return GMC_OK;
+  if (!is_device_pointer(cond) || !is_device_pointer(y))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_data: cond and y must be device memory");
+  cudaSetDevice(ctx->device);
+  data_kernel<<<nb(n, 128), 128, 0, ctx->stream>>>(n, seed, logf(tau_lo), logf(tau_hi), c_lo, c_hi,
+                                                   cond, y);
+  GMC_CUDA_TRY(ctx, cudaGetLastError());
+  return GMC_OK;
+}
+
+gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const float *y,
+                           const gmc_train_config *cfg) {
+  if (!ctx || !cfg) return GMC_EINVAL;
+  if (n < 2 || !cond || !y) return set_error(ctx, GMC_EINVAL, "gmc_train_begin: need n >= 2 samples");
+  if (cfg->batch < 1 || cfg->batch > (1 << 20) || !(cfg->lr > 0.0))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_begin: batch in [1, 2^20], lr > 0");
+  if (!ctx->has_weights) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_train_begin: load initial weights first");
+  if (!is_device_pointer(cond) || !is_device_pointer(y))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_begin: data must be device memory");
+  cudaSetDevice(ctx->device);
+  if (ctx->train) free_train(ctx->train);
+  TrainState *T = new TrainState();
+  ctx->train = T;
+  T->n = n;
+  T->cond = cond;
+  T->y = y;
+  T->cfg = *cfg;
+  T->step = 0;
+  cudaStream_t s = ctx->stream;
+  GMC_CUDA_TRY(ctx, cudaMalloc(&T->stat_acc, 18 * sizeof(double)));
+  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->stat_acc, 0, 18 * sizeof(double), s));
+  stats_kernel<<<1024, 256, 0, s>>>(n, cond, y, T->stat_acc);
+  GMC_CUDA_TRY(ctx, cudaGetLastError());
+  double acc[18];
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(acc, T->stat_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+  GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  for (int k = 0; k < 9; ++k) {
+    const double mean = acc[k] / n;
+    double var = acc[9 + k] / n - mean * mean;
+    const double sd = var > 1e-12 ? std::sqrt(var) : 1.0;
+    if (k < 5) {
+      T->stats[k] = (float)mean;
+      T->stats[5 + k] = (float)sd;
+    } else {
+      T->stats[10 + (k - 5)] = (float)mean;
+      T->stats[14 + (k - 5)] = (float)sd;
+    }
+  }
+  // master weights from the loaded network
+  std::vector<float> h(P_TOTAL, 0.0f);
+  for (int c = 0; c < 256; ++c)
+    for (int k = 0; k < 25; ++k) h[P_W1 + c * 32 + k] = ctx->host_w[0][c * 25 + k];
+  std::memcpy(&h[P_B1], ctx->host_b[0], 256 * 4);
+  const int64_t wo[3] = {P_W2, P_W3, P_W4}, bo[3] = {P_B2, P_B3, P_B4};
+  for (int l = 0; l < 3; ++l) {
+    std::memcpy(&h[wo[l]], ctx->host_w[l + 1], 65536 * 4);
+    std::memcpy(&h[bo[l]], ctx->host_b[l + 1], 256 * 4);
+  }
+  std::memcpy(&h[P_W5], ctx->host_w[4], 1024 * 4);
+  std::memcpy(&h[P_B5], ctx->host_b[4], 4 * 4);
+  GMC_CUDA_TRY(ctx, cudaMalloc(&T->params, P_TOTAL * 4));
+  GMC_CUDA_TRY(ctx, cudaMalloc(&T->grads, P_TOTAL * 4));
+  GMC_CUDA_TRY(ctx, cudaMalloc(&T->m, P_TOTAL * 4));
+  GMC_CUDA_TRY(ctx, cudaMalloc(&T->v, P_TOTAL * 4));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->params, h.data(), P_TOTAL * 4, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->grads, 0, P_TOTAL * 4, s));
+  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->m, 0, P_TOTAL * 4, s));
+  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->v, 0, P_TOTAL * 4, s));
+  GMC_CUDA_TRY(ctx, alloc_batch(*T, cfg->batch));
+  GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return GMC_OK;
+}
+
+gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses) {
+  if (!ctx) return GMC_EINVAL;
+  TrainState *T = ctx->train;
+  if (!T) return set_error(ctx, GMC_EINVAL, "gmc_train_steps: call gmc_train_begin first");
+  if (n_steps < 0) return set_error(ctx, GMC_EINVAL, "gmc_train_steps: n_steps < 0");
+  if (n_steps == 0) return GMC_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  if (T->loss_cap < n_steps) {
+    if (T->loss) cudaFree(T->loss);
+    T->loss = nullptr;
+    GMC_CUDA_TRY(ctx, cudaMalloc(&T->loss, n_steps * sizeof(double)));
+    T->loss_cap = n_steps;
+  }
+  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->loss, 0, n_steps * sizeof(double), s));
+  Std sd;
+  for (int k = 0; k < 5; ++k) {
+    sd.cm[k] = T->stats[k];
+    sd.cis[k] = 1.0f / T->stats[5 + k];
+  }
+  for (int k = 0; k < 4; ++k) {
+    sd.ym[k] = T->stats[10 + k];
+    sd.yis[k] = 1.0f / T->stats[14 + k];
+  }
+  const gmc_train_config &c = T->cfg;
+  for (int64_t i = 0; i < n_steps; ++i) {
+    batch_kernel<<<nb(T->B, 256), 256, 0, s>>>(T->B, T->n, T->cond, T->y, sd, c.seed, T->step, T->X0, T->U);
+    GMC_CUDA_TRY(ctx, fwd_bwd(s, *T, T->loss + i));
+    ++T->step;
+    const float bc1 = 1.0f - (float)std::pow(c.beta1, (double)T->step);
+    const float bc2 = 1.0f - (float)std::pow(c.beta2, (double)T->step);
+    adamw_kernel<<<nb(P_TOTAL, 256), 256, 0, s>>>(P_TOTAL, T->params, T->grads, T->m, T->v,
+                                                  (float)c.lr, (float)c.beta1, (float)c.beta2,
+                                                  (float)c.eps, (float)c.weight_decay, bc1, bc2);
+    GMC_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  if (losses) {
+    std::vector<double> hl(n_steps);
+    GMC_CUDA_TRY(ctx, cudaMemcpyAsync(hl.data(), T->loss, n_steps * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < n_steps; ++i) losses[i] = (float)hl[i];
+  }
+  return GMC_OK;
+}
+
+gmc_status gmc_train_grad(gmc_ctx *ctx, int64_t B, const float *cn, const float *x1,
+                          const float *x0, const float *t, double *loss, float *grad) {
+  if (!ctx) return GMC_EINVAL;
+  TrainState *T = ctx->train;
+  if (!T) return set_error(ctx, GMC_EINVAL, "gmc_train_grad: call gmc_train_begin first");
+  if (B < 1 || B > T->B || !cn || !x1 || !x0 || !t || !loss || !grad)
+    return set_error(ctx, GMC_EINVAL, "gmc_train_grad: 1 <= B <= batch and non-null arrays");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  float *d;
+  const size_t nbytes = (size_t)B * (5 + 4 + 4 + 1) * 4;
+  GMC_CUDA_TRY(ctx, ensure(ctx->stage[0], nbytes));
+  d = (float *)ctx->stage[0].ptr;
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d, cn, B * 20, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d + B * 5, x1, B * 16, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d + B * 9, x0, B * 16, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d + B * 13, t, B * 4, cudaMemcpyHostToDevice, s));
+  batch_explicit_kernel<<<nb(B, 256), 256, 0, s>>>(B, d, d + B * 5, d + B * 9, d + B * 13, T->X0, T->U);
+  const int64_t saveB = T->B;
+  T->B = B;
+  double *ls;
+  GMC_CUDA_TRY(ctx, ensure(ctx->stage[1], sizeof(double)));
+  ls = (double *)ctx->stage[1].ptr;
+  GMC_CUDA_TRY(ctx, cudaMemsetAsync(ls, 0, sizeof(double), s));
+  cudaError_t e = fwd_bwd(s, *T, ls);
+  T->B = saveB;
+  GMC_CUDA_TRY(ctx, e);
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(loss, ls, sizeof(double), cudaMemcpyDeviceToHost, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(grad, T->grads, P_TOTAL * 4, cudaMemcpyDeviceToHost, s));
+  GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return GMC_OK;
+}
+
+int64_t gmc_train_param_count(void) { return P_TOTAL; }
+
+gmc_status gmc_train_params(gmc_ctx *ctx, float *out) {
+  if (!ctx || !out) return GMC_EINVAL;
+  if (!ctx->train) return set_error(ctx, GMC_EINVAL, "gmc_train_params: call gmc_train_begin first");
+  cudaSetDevice(ctx->device);
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->train->params, P_TOTAL * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return GMC_OK;
+}
+
+gmc_status gmc_train_commit(gmc_ctx *ctx, const char *path) {
+  if (!ctx) return GMC_EINVAL;
+  TrainState *T = ctx->train;
+  if (!T) return set_error(ctx, GMC_EINVAL, "gmc_train_commit: call gmc_train_begin first");
+  cudaSetDevice(ctx->device);
+  std::vector<float> h(P_TOTAL);
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), T->params, P_TOTAL * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  // GMCW version 1 blob
+  std::vector<unsigned char> blob;
+  auto u32 = [&](uint32_t v) { const unsigned char *p = (const unsigned char *)&v; blob.insert(blob.end(), p, p + 4); };
+  auto f32 = [&](const float *v, size_t n) { const unsigned char *p = (const unsigned char *)v; blob.insert(blob.end(), p, p + 4 * n); };
+  blob.insert(blob.end(), {'G', 'M', 'C', 'W'});
+  u32(1); u32(5);
+  const uint32_t dims[6] = {25, 256, 256, 256, 256, 4};
+  for (uint32_t dd : dims) u32(dd);
+  u32(5); u32(4); u32(16); u32(0);
+  f32(T->stats, 18);
+  std::vector<float> w1(256 * 25);
+  for (int c = 0; c < 256; ++c)
+    for (int k = 0; k < 25; ++k) w1[c * 25 + k] = h[P_W1 + c * 32 + k];
+  f32(w1.data(), w1.size());
+  f32(&h[P_B1], 256);
+  f32(&h[P_W2], 65536); f32(&h[P_B2], 256);
+  f32(&h[P_W3], 65536); f32(&h[P_B3], 256);
+  f32(&h[P_W4], 65536); f32(&h[P_B4], 256);
+  f32(&h[P_W5], 1024); f32(&h[P_B5], 4);
+  if (path) {
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return set_error(ctx, GMC_EIO, "cannot write '%s'", path);
+    const size_t wrote = std::fwrite(blob.data(), 1, blob.size(), f);
+    const bool bad = std::fclose(f) != 0 || wrote != blob.size();
+    if (bad) return set_error(ctx, GMC_EIO, "short write to '%s'", path);
+  }
+  TrainState *keep = ctx->train;
+  ctx->train = nullptr;  // loading weights must not drop the training state
+  gmc_status st = gmc_load_weights_buffer(ctx, blob.data(), blob.size());
+  ctx->train = keep;
+  return st;
+}
+
+}  // extern "C"

@@ -1,15 +1,18 @@
-// transport_solve: the four-stage GMC transport algorithm (and the standard
-// MC walk it replaces) as an event loop over waves of in-flight particles.
+// Transport solves: the four-stage GMC transport algorithm (and the standard
+// MC walk it replaces) as an event loop over waves of in-flight particles,
+// with several solves ("requests") sharing one particle bank.
 //
 // Particle bank (structure of arrays, double-buffered, capacity C):
-//   hist u64 (history id = Philox id), cell i32, face i32 (global face the
-//   particle entered through), xi f32 (canonical entry position), gx, gy f32
-//   (global direction), w f32 (weight), ev u32 (next Philox event).
+//   hist u64 (history id = Philox id), slot i32 (request), cell i32, face i32
+//   (global face the particle entered through), xi f32 (canonical entry
+//   position), gx, gy f32 (global direction), w f32 (weight), ev u32 (next
+//   Philox event) -- 40 bytes per particle.
 // One wave:
-//   births   new histories fill free slots: birth point and direction from
-//            Philox (id, 0, tag 4), walked to the first face crossing of the
-//            birth cell with implicit capture (the paper's separate
-//            internal-source network is not built);
+//   births   new histories of every admitted request fill free slots of the
+//            bank (fair share): birth point and direction from Philox
+//            (id, 0, tag 4), walked to the first face crossing of the birth
+//            cell with implicit capture (the paper's separate internal-source
+//            network is not built);
 //   GMC      prep: rotate into the canonical left-entry frame (stage 1),
 //            build the condition and draw z ~ N(0, I) at (id, ev, tag 2);
 //            sampler: the fused flow-ODE kernel (stage 2);
@@ -17,13 +20,23 @@
 //            roulette, cross into the neighbour, compact survivors (stage 4);
 //   ANALOG   one kernel walks each particle through its cell (Eq. 4) and
 //            does stages 3-4 the same way.
-// Tally: FP64 atomics into flux[ny*nx]; Delta w / (V sigma_a) with V = 1.
+// Tallies: per request, FP64 atomics into flux[ny*nx]; Delta w / (V sigma_a)
+// with V = 1. Per-history random numbers depend only on (request seed,
+// history id, event), and sampler rows are independent, so a request's
+// result does not depend on which other requests share its waves (up to the
+// order of FP64 additions).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "decode.cuh"
@@ -32,27 +45,33 @@
 #include "walk.cuh"
 
 namespace gmc {
+
+constexpr int kMaxSlots = 64;
+
 namespace {
 
 struct Bank {
   uint64_t *hist;
-  int32_t *cell, *face;
+  int32_t *slot, *cell, *face;
   float *xi, *gx, *gy, *w;
   uint32_t *ev;
 };
+constexpr size_t kBankBytesPerParticle = 40;
 
 struct DevStats {
   double leaked, absorbed, roulette_net;
   unsigned long long transmissions, collisions, kills, inward;
 };
 
-struct Grid {
+// one admitted request, as the kernels see it
+struct Slot {
   int nx, ny;
   const float *tau, *c;
+  double *flux;
+  uint64_t seed;
 };
 
 struct Rules {
-  uint64_t seed;
   float w_cut, p_survive;
 };
 
@@ -67,23 +86,17 @@ __device__ __forceinline__ void rot(float &ux, float &uy, int k) {
   }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
-__device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Stage 3 and 4 for one finished cell transmission: deposit, attenuate,
-// roulette, cross. Appends the survivor to `out` (warp-aggregated). Every
-// lane of the warp must call this (inactive lanes with active = false).
+// A finished cell transmission of one lane.
 struct Exit {
   bool active;
+  int slot;
   uint64_t hist;
   int cell, gface;   // cell crossed, global exit face
   float q;           // counter-clockwise position on that face
@@ -91,18 +104,21 @@ struct Exit {
   float w, s;        // weight on entry, track length (optical)
   uint32_t ev;       // next Philox event
   uint32_t ncoll;
-  bool inward;
 };
 
-__device__ void finish_transmission(const Exit &x, const Grid &G, const Rules &R, double *flux,
-                                    Bank out, int *out_count, DevStats *st) {
+// Stages 3 and 4: deposit, attenuate, roulette, cross; appends survivors to
+// `out` (warp-aggregated) and counts them per request. Every lane of the
+// warp calls this (inactive lanes with active = false).
+__device__ void finish_transmission(const Exit &x, const Slot *__restrict__ slots, Rules R,
+                                    Bank out, int *out_count, DevStats *st, int *slot_live) {
   double dabs = 0.0, dleak = 0.0, droul = 0.0;
   unsigned long long kills = 0;
   bool keep = false;
   int ncell = 0, nface = 0;
   float w = 0.0f;
   if (x.active) {
-    const float tau = G.tau[x.cell], cc = G.c[x.cell];
+    const Slot S = slots[x.slot];
+    const float tau = S.tau[x.cell], cc = S.c[x.cell];
     const float a = 1.0f - cc;
     float dw;
     double score;
@@ -113,12 +129,12 @@ __device__ void finish_transmission(const Exit &x, const Grid &G, const Rules &R
       dw = 0.0f;
       score = (double)x.w * (double)x.s / (double)tau;
     }
-    atomicAdd(&flux[x.cell], score);
+    atomicAdd(&S.flux[x.cell], score);
     dabs = dw;
     w = x.w - dw;                                           // Eq. 5
     bool alive = true;
     if (w < R.w_cut) {
-      const float u = u01(philox_draw(R.seed, x.hist, x.ev, kTagRoulette).x);
+      const float u = u01(philox_draw(S.seed, x.hist, x.ev, kTagRoulette).x);
       if (u <= R.p_survive) {
         droul = (double)(w / R.p_survive) - (double)w;
         w = w / R.p_survive;
@@ -129,27 +145,27 @@ __device__ void finish_transmission(const Exit &x, const Grid &G, const Rules &R
       }
     }
     if (alive) {
-      const int i = x.cell % G.nx, j = x.cell / G.nx;
+      const int i = x.cell % S.nx, j = x.cell / S.nx;
       const int ni = i + (x.gface == 1) - (x.gface == 3);
       const int nj = j + (x.gface == 2) - (x.gface == 0);
-      if (ni < 0 || ni >= G.nx || nj < 0 || nj >= G.ny) {
+      if (ni < 0 || ni >= S.nx || nj < 0 || nj >= S.ny) {
         dleak = w;
       } else {
         keep = true;
-        ncell = nj * G.nx + ni;
+        ncell = nj * S.nx + ni;
         nface = (x.gface + 2) & 3;
       }
     }
   }
-  // warp-aggregated append of survivors
-  const unsigned mask = __ballot_sync(0xffffffffu, keep);
   const int lane = threadIdx.x & 31;
+  const unsigned mask = __ballot_sync(0xffffffffu, keep);
   int base = 0;
   if (lane == 0 && mask) base = atomicAdd(out_count, __popc(mask));
   base = __shfl_sync(0xffffffffu, base, 0);
   if (keep) {
     const int k = base + __popc(mask & ((1u << lane) - 1u));
     out.hist[k] = x.hist;
+    out.slot[k] = x.slot;
     out.cell[k] = ncell;
     out.face[k] = nface;
     out.xi[k] = x.q;
@@ -158,22 +174,39 @@ __device__ void finish_transmission(const Exit &x, const Grid &G, const Rules &R
     out.w[k] = w;
     out.ev[k] = x.ev;
   }
-  // warp-reduced statistics
-  dabs = warp_sum(dabs);
-  dleak = warp_sum(dleak);
-  droul = warp_sum(droul);
-  const unsigned long long nt = warp_sum_u(x.active ? 1ull : 0ull);
-  const unsigned long long nc = warp_sum_u(x.active ? (unsigned long long)x.ncoll : 0ull);
-  const unsigned long long nk = warp_sum_u(kills);
-  const unsigned long long ni = warp_sum_u(x.active && x.inward ? 1ull : 0ull);
-  if (lane == 0 && nt) {
-    atomicAdd(&st->absorbed, dabs);
-    atomicAdd(&st->leaked, dleak);
-    atomicAdd(&st->roulette_net, droul);
-    atomicAdd(&st->transmissions, nt);
-    atomicAdd(&st->collisions, nc);
-    atomicAdd(&st->kills, nk);
-    atomicAdd(&st->inward, ni);
+  // statistics and survivor counts per request: warp-reduced when every
+  // active lane belongs to the same request (the common case: births of a
+  // request are contiguous and compaction keeps warp order), per lane otherwise
+  const unsigned act = __ballot_sync(0xffffffffu, x.active);
+  if (!act) return;
+  const int lead = __ffs(act) - 1;
+  const int slot0 = __shfl_sync(0xffffffffu, x.slot, lead);
+  const bool uniform = __all_sync(0xffffffffu, !x.active || x.slot == slot0);
+  if (uniform) {
+    dabs = warp_sum(dabs);
+    dleak = warp_sum(dleak);
+    droul = warp_sum(droul);
+    const unsigned long long nc = warp_sum((unsigned long long)(x.active ? x.ncoll : 0u));
+    const unsigned long long nk = warp_sum(kills);
+    if (lane == 0) {
+      DevStats *s = st + slot0;
+      atomicAdd(&s->absorbed, dabs);
+      atomicAdd(&s->leaked, dleak);
+      atomicAdd(&s->roulette_net, droul);
+      atomicAdd(&s->transmissions, (unsigned long long)__popc(act));
+      atomicAdd(&s->collisions, nc);
+      atomicAdd(&s->kills, nk);
+      if (mask) atomicAdd(&slot_live[slot0], __popc(mask));
+    }
+  } else if (x.active) {
+    DevStats *s = st + x.slot;
+    atomicAdd(&s->absorbed, dabs);
+    atomicAdd(&s->leaked, dleak);
+    atomicAdd(&s->roulette_net, droul);
+    atomicAdd(&s->transmissions, 1ull);
+    atomicAdd(&s->collisions, (unsigned long long)x.ncoll);
+    atomicAdd(&s->kills, kills);
+    if (keep) atomicAdd(&slot_live[x.slot], 1);
   }
 }
 
@@ -187,23 +220,24 @@ __device__ __forceinline__ int64_t cdf_search(const double *cdf, int64_t n, doub
   return lo;
 }
 
-// Births of histories first .. first+count-1.
-__global__ void birth_kernel(int64_t first, int64_t count, const double *__restrict__ cdf,
-                             double total, Grid G, Rules R, double *flux, Bank out,
-                             int *out_count, DevStats *st) {
+// Births of histories first .. first+count-1 of the request in `slot`.
+__global__ void birth_kernel(int slot, int64_t first, int64_t count, const double *__restrict__ cdf,
+                             double total, const Slot *__restrict__ slots, Rules R, Bank out,
+                             int *out_count, DevStats *st, int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Exit x;
   x.active = k < count;
-  x.inward = false;
+  x.slot = slot;
   if (x.active) {
+    const Slot S = slots[slot];
     const uint64_t h = (uint64_t)(first + k);
-    const uint4 r = philox_draw(R.seed, h, 0u, kTagBirth);
+    const uint4 r = philox_draw(S.seed, h, 0u, kTagBirth);
     const double u0 = ((double)r.x + 1.0) * (1.0 / 4294967296.0);
-    const int64_t cell = cdf_search(cdf, (int64_t)G.nx * G.ny, u0 * total);
+    const int64_t cell = cdf_search(cdf, (int64_t)S.nx * S.ny, u0 * total);
     float ux, uy;
     sincospif(2.0f * u01(r.w), &uy, &ux);
-    const float tau = G.tau[cell], cc = G.c[cell];
-    const WalkResult wr = walk_cell(tau, cc, 1, u01(r.y), u01(r.z), ux, uy, R.seed, h, 0u);
+    const WalkResult wr = walk_cell(S.tau[cell], S.c[cell], 1, u01(r.y), u01(r.z), ux, uy, S.seed,
+                                    h, 0u);
     x.hist = h;
     x.cell = (int)cell;
     x.gface = wr.face < 0 ? 0 : wr.face;
@@ -215,18 +249,20 @@ __global__ void birth_kernel(int64_t first, int64_t count, const double *__restr
     x.ev = wr.event;
     x.ncoll = wr.ncoll;
   }
-  finish_transmission(x, G, R, flux, out, out_count, st);
+  finish_transmission(x, slots, R, out, out_count, st, slot_live);
 }
 
 // ANALOG: walk each bank particle through its cell in the cell's own
 // (global-oriented) frame, entering at the point its entry face and xi give.
-__global__ void analog_wave_kernel(int64_t live, Bank in, Grid G, Rules R, double *flux, Bank out,
-                                   int *out_count, DevStats *st) {
+__global__ void analog_wave_kernel(int64_t live, Bank in, const Slot *__restrict__ slots, Rules R,
+                                   Bank out, int *out_count, DevStats *st, int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Exit x;
   x.active = k < live;
-  x.inward = false;
+  x.slot = 0;
   if (x.active) {
+    x.slot = in.slot[k];
+    const Slot S = slots[x.slot];
     const int cell = in.cell[k], F = in.face[k];
     const float xi = in.xi[k];
     // point on face F with counter-clockwise parameter 1 - xi
@@ -238,7 +274,7 @@ __global__ void analog_wave_kernel(int64_t live, Bank in, Grid G, Rules R, doubl
       default: X = 0.0f; Y = xi; break;
     }
     const uint64_t h = in.hist[k];
-    const WalkResult wr = walk_cell(G.tau[cell], G.c[cell], 1, X, Y, in.gx[k], in.gy[k], R.seed, h,
+    const WalkResult wr = walk_cell(S.tau[cell], S.c[cell], 1, X, Y, in.gx[k], in.gy[k], S.seed, h,
                                     in.ev[k]);
     x.hist = h;
     x.cell = cell;
@@ -251,23 +287,24 @@ __global__ void analog_wave_kernel(int64_t live, Bank in, Grid G, Rules R, doubl
     x.ev = wr.event;
     x.ncoll = wr.ncoll;
   }
-  finish_transmission(x, G, R, flux, out, out_count, st);
+  finish_transmission(x, slots, R, out, out_count, st, slot_live);
 }
 
 // GMC stage 1 and the noise of stage 2.
-__global__ void gmc_prep_kernel(int64_t live, Bank in, Grid G, uint64_t seed, float *cond,
+__global__ void gmc_prep_kernel(int64_t live, Bank in, const Slot *__restrict__ slots, float *cond,
                                 float *noise) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= live) return;
+  const Slot S = slots[in.slot[k]];
   const int cell = in.cell[k], F = in.face[k];
   float ux = in.gx[k], uy = in.gy[k];
   rot(ux, uy, -((F + 1) & 3));
   cond[k] = in.xi[k];
   cond[live + k] = ux;
   cond[2 * live + k] = uy;
-  cond[3 * live + k] = logf(G.tau[cell]);
-  cond[4 * live + k] = G.c[cell];
-  const float4 z = box_muller4(philox_draw(seed, in.hist[k], in.ev[k], kTagNoise));
+  cond[3 * live + k] = logf(S.tau[cell]);
+  cond[4 * live + k] = S.c[cell];
+  const float4 z = box_muller4(philox_draw(S.seed, in.hist[k], in.ev[k], kTagNoise));
   noise[k] = z.x;
   noise[live + k] = z.y;
   noise[2 * live + k] = z.z;
@@ -275,22 +312,23 @@ __global__ void gmc_prep_kernel(int64_t live, Bank in, Grid G, uint64_t seed, fl
 }
 
 // GMC stages 3 and 4 from the sampler's decoded exits (p, ux, uy, s).
-__global__ void gmc_post_kernel(int64_t live, Bank in, const float *__restrict__ ex, Grid G,
-                                Rules R, double *flux, Bank out, int *out_count, DevStats *st) {
+__global__ void gmc_post_kernel(int64_t live, Bank in, const float *__restrict__ ex,
+                                const Slot *__restrict__ slots, Rules R, Bank out, int *out_count,
+                                DevStats *st, int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Exit x;
   x.active = k < live;
-  x.inward = false;
+  x.slot = 0;
   if (x.active) {
     const int F = in.face[k], r = (F + 1) & 3;
     const float p = ex[k];
     float ux = ex[live + k], uy = ex[2 * live + k];
     const int fc = min((int)p, 3);
+    x.slot = in.slot[k];
     x.hist = in.hist[k];
     x.cell = in.cell[k];
     x.gface = (fc + r) & 3;
     x.q = fminf(fmaxf(p - (float)fc, 0.0f), 1.0f);
-    // the sampler reflected inward directions; count them for the statistics
     rot(ux, uy, r);
     x.gx = ux;
     x.gy = uy;
@@ -299,7 +337,7 @@ __global__ void gmc_post_kernel(int64_t live, Bank in, const float *__restrict__
     x.ev = in.ev[k] + 1u;
     x.ncoll = 0;
   }
-  finish_transmission(x, G, R, flux, out, out_count, st);
+  finish_transmission(x, slots, R, out, out_count, st, slot_live);
 }
 
 inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -308,6 +346,7 @@ Bank carve(void *base, int64_t C) {
   Bank b;
   char *p = (char *)base;
   b.hist = (uint64_t *)p; p += 8 * C;
+  b.slot = (int32_t *)p; p += 4 * C;
   b.cell = (int32_t *)p; p += 4 * C;
   b.face = (int32_t *)p; p += 4 * C;
   b.xi = (float *)p; p += 4 * C;
@@ -318,160 +357,584 @@ Bank carve(void *base, int64_t C) {
   return b;
 }
 
-constexpr size_t kBankBytesPerParticle = 36;
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
+
+// ----------------------------------------------------------------------------
+// Host side: requests, a device-memory pool, the wave engine, the server.
+
+struct Request {
+  uint64_t ticket = 0;
+  int nx = 0, ny = 0;
+  int64_t ncell = 0;
+  std::vector<float> tau, c;
+  std::vector<double> cdf;
+  double total = 0.0;
+  int64_t n_hist = 0;
+  uint64_t seed = 0;
+  int method = GMC_METHOD_ANALOG;
+  // engine state
+  int slot = -1;
+  int64_t next_hist = 0;
+  int live = 0;
+  size_t pool_off = 0, footprint = 0;
+  double *d_cdf = nullptr, *d_flux = nullptr;
+  float *d_tau = nullptr, *d_c = nullptr;
+  // result
+  std::vector<double> flux;
+  gmc_solve_stats st{};
+  gmc_status status = GMC_OK;
+  bool done = false;
+  double t_submit = 0.0, t_done = 0.0;
+  cudaEvent_t ev0 = nullptr;
+};
+
+size_t request_footprint(int64_t ncell) { return 2 * align256(ncell * 4) + 2 * align256(ncell * 8); }
+
+// Validates a solve description and copies it into a Request.
+gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                        const float *source, int64_t n_histories, int method, uint64_t seed,
+                        Request &R) {
+  if (nx < 1 || ny < 1 || (int64_t)nx * ny > (1 << 26))
+    return set_error(ctx, GMC_EINVAL, "solve: grid must be 1..2^26 cells");
+  if (!tau || !c || !source) return set_error(ctx, GMC_EINVAL, "solve: null array");
+  if (n_histories < 0) return set_error(ctx, GMC_EINVAL, "solve: n_histories < 0");
+  if (method != GMC_METHOD_ANALOG && method != GMC_METHOD_GMC)
+    return set_error(ctx, GMC_EINVAL, "solve: unknown method");
+  const int64_t ncell = (int64_t)nx * ny;
+  R.nx = nx;
+  R.ny = ny;
+  R.ncell = ncell;
+  R.tau.assign(tau, tau + ncell);
+  R.c.assign(c, c + ncell);
+  R.cdf.resize(ncell);
+  double acc = 0.0;
+  for (int64_t k = 0; k < ncell; ++k) {
+    if (!(tau[k] > 0.0f) || !std::isfinite(tau[k]) || !(c[k] >= 0.0f && c[k] <= 1.0f))
+      return set_error(ctx, GMC_EINVAL, "solve: cell %lld needs tau > 0, c in [0,1]", (long long)k);
+    if (method == GMC_METHOD_GMC && (tau[k] < 0.05f || tau[k] > 2000.0f || c[k] < 0.4f))
+      return set_error(ctx, GMC_EINVAL,
+                       "solve: cell %lld outside the sampler's range (tau in [0.05, 2000], c >= 0.4)",
+                       (long long)k);
+    if (!(source[k] >= 0.0f) || !std::isfinite(source[k]))
+      return set_error(ctx, GMC_EINVAL, "solve: source must be finite and >= 0");
+    acc += source[k] > 0.0f ? (double)source[k] : 0.0;
+    R.cdf[k] = acc;
+  }
+  if (n_histories > 0 && !(acc > 0.0)) return set_error(ctx, GMC_EINVAL, "solve: zero source");
+  if (method == GMC_METHOD_GMC && !ctx->has_weights)
+    return set_error(ctx, GMC_ENOWEIGHTS, "solve: GMC needs gmc_load_weights");
+  if (method == GMC_METHOD_GMC && ctx->cfg.precision == GMC_FP8)
+    return set_error(ctx, GMC_ENOTIMPL, "solve: FP8 sampler not built");
+  R.total = acc;
+  R.n_hist = n_histories;
+  R.method = method;
+  R.seed = seed;
+  R.footprint = request_footprint(ncell);
+  return GMC_OK;
+}
+
+// First-fit sub-allocator over one device buffer (admission by memory).
+class Pool {
+ public:
+  cudaError_t init(size_t bytes) {
+    bytes_ = align256(bytes);
+    cudaError_t e = cudaMalloc(&base_, bytes_);
+    if (e == cudaSuccess) free_[0] = bytes_;
+    return e;
+  }
+  ~Pool() {
+    if (base_) cudaFree(base_);
+  }
+  size_t capacity() const { return bytes_; }
+  bool alloc(size_t bytes, size_t *off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t noff = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[noff] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  char *base() const { return (char *)base_; }
+
+ private:
+  void *base_ = nullptr;
+  size_t bytes_ = 0;
+  std::map<size_t, size_t> free_;
+};
+
+// The wave engine: every admitted request owns a slot, a pool region (grid,
+// CDF, tally) and its share of the particle bank.
+class Engine {
+ public:
+  Engine(gmc_ctx *ctx, int method, int64_t capacity, size_t pool_bytes, cudaStream_t stream)
+      : ctx_(ctx), method_(method), C_(capacity), pool_bytes_(pool_bytes), s_(stream) {}
+
+  ~Engine() {
+    cudaStreamSynchronize(s_);
+    void *bufs[] = {bank_mem_[0], bank_mem_[1], d_cond_, d_noise_, d_exit_, d_slots_, d_stats_,
+                    d_counts_, d_bias1_};
+    for (void *b : bufs)
+      if (b) cudaFree(b);
+    if (h_counts_) cudaFreeHost(h_counts_);
+  }
+
+  gmc_status init() {
+    GMC_CUDA_TRY(ctx_, pool_.init(pool_bytes_));
+    GMC_CUDA_TRY(ctx_, cudaMalloc(&bank_mem_[0], C_ * kBankBytesPerParticle));
+    GMC_CUDA_TRY(ctx_, cudaMalloc(&bank_mem_[1], C_ * kBankBytesPerParticle));
+    if (method_ == GMC_METHOD_GMC) {
+      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_cond_, C_ * 5 * sizeof(float)));
+      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_noise_, C_ * 4 * sizeof(float)));
+      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_exit_, C_ * 4 * sizeof(float)));
+      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bias1_, 2 * 256 * 256 * sizeof(float)));
+    }
+    GMC_CUDA_TRY(ctx_, cudaMalloc(&d_slots_, kMaxSlots * sizeof(Slot)));
+    GMC_CUDA_TRY(ctx_, cudaMalloc(&d_stats_, kMaxSlots * sizeof(DevStats)));
+    GMC_CUDA_TRY(ctx_, cudaMalloc(&d_counts_, (kMaxSlots + 1) * sizeof(int)));
+    GMC_CUDA_TRY(ctx_, cudaMallocHost(&h_counts_, (kMaxSlots + 1) * sizeof(int)));
+    bank_[0] = carve(bank_mem_[0], C_);
+    bank_[1] = carve(bank_mem_[1], C_);
+    for (auto &r : reqs_) r = nullptr;
+    return GMC_OK;
+  }
+
+  int method() const { return method_; }
+  cudaStream_t stream() const { return s_; }
+  int64_t capacity() const { return C_; }
+  size_t pool_capacity() const { return pool_.capacity(); }
+  bool idle() const { return active_ == 0; }
+  int active() const { return active_; }
+
+  // Admits R if a slot and its pool footprint are free; false otherwise.
+  bool try_admit(Request *R, gmc_status *err) {
+    *err = GMC_OK;
+    if (active_ >= kMaxSlots) return false;
+    size_t off;
+    if (!pool_.alloc(R->footprint, &off)) return false;
+    int slot = -1;
+    for (int k = 0; k < kMaxSlots; ++k)
+      if (!reqs_[k]) {
+        slot = k;
+        break;
+      }
+    char *p = pool_.base() + off;
+    const int64_t n = R->ncell;
+    R->pool_off = off;
+    R->d_tau = (float *)p;
+    R->d_c = (float *)(p + align256(n * 4));
+    R->d_cdf = (double *)(p + 2 * align256(n * 4));
+    R->d_flux = (double *)(p + 2 * align256(n * 4) + align256(n * 8));
+    Slot S{R->nx, R->ny, R->d_tau, R->d_c, R->d_flux, R->seed};
+    cudaError_t e = cudaMemcpyAsync(R->d_tau, R->tau.data(), n * 4, cudaMemcpyHostToDevice, s_);
+    if (!e) e = cudaMemcpyAsync(R->d_c, R->c.data(), n * 4, cudaMemcpyHostToDevice, s_);
+    if (!e) e = cudaMemcpyAsync(R->d_cdf, R->cdf.data(), n * 8, cudaMemcpyHostToDevice, s_);
+    if (!e) e = cudaMemsetAsync(R->d_flux, 0, n * 8, s_);
+    if (!e) e = cudaMemcpyAsync(d_slots_ + slot, &S, sizeof(Slot), cudaMemcpyHostToDevice, s_);
+    if (!e) e = cudaMemsetAsync(d_stats_ + slot, 0, sizeof(DevStats), s_);
+    if (!e) e = cudaStreamSynchronize(s_);  // host vectors and S are read by the copies
+    if (e) {
+      pool_.release(off, R->footprint);
+      *err = cuda_error(ctx_, e, "admitting a solve");
+      return false;
+    }
+    if (!R->ev0) cudaEventCreate(&R->ev0);
+    cudaEventRecord(R->ev0, s_);
+    R->slot = slot;
+    R->next_hist = 0;
+    R->live = 0;
+    reqs_[slot] = R;
+    ++active_;
+    return true;
+  }
+
+  // One wave: births for every request with histories left, one transmission
+  // of every particle in the bank, completion of finished requests.
+  gmc_status step(std::vector<Request *> &completed) {
+    const Rules rules{(float)ctx_->cfg.w_cut, (float)ctx_->cfg.p_survive};
+    int *d_count = d_counts_, *d_slot_live = d_counts_ + 1;
+    // births: fair share of the free bank among requests with histories left
+    int pending = 0;
+    for (auto *R : reqs_)
+      if (R && R->next_hist < R->n_hist) ++pending;
+    int64_t room = C_ - live_;
+    if (pending > 0 && room > 0) {
+      GMC_CUDA_TRY(ctx_, cudaMemcpyAsync(d_count, &live_i_, sizeof(int), cudaMemcpyHostToDevice, s_));
+      GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_slot_live, 0, kMaxSlots * sizeof(int), s_));
+      int left = pending;
+      for (auto *R : reqs_) {
+        if (!R || R->next_hist >= R->n_hist) continue;
+        const int64_t share = room / left;
+        const int64_t m = std::min<int64_t>(share, R->n_hist - R->next_hist);
+        --left;
+        if (m <= 0) continue;
+        room -= m;
+        birth_kernel<<<nblocks(m, 256), 256, 0, s_>>>(R->slot, R->next_hist, m, R->d_cdf, R->total,
+                                                       d_slots_, rules, bank_[cur_], d_count,
+                                                       d_stats_, d_slot_live);
+        GMC_CUDA_TRY(ctx_, cudaGetLastError());
+        R->next_hist += m;
+      }
+      GMC_CUDA_TRY(ctx_, read_counts());
+      live_ = h_counts_[0];
+      for (auto *R : reqs_)
+        if (R) R->live += h_counts_[1 + R->slot];
+    }
+    if (live_ > 0) {
+      ++waves_;
+      const int nxt = cur_ ^ 1;
+      GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_counts_, 0, (kMaxSlots + 1) * sizeof(int), s_));
+      if (method_ == GMC_METHOD_ANALOG) {
+        analog_wave_kernel<<<nblocks(live_, 128), 128, 0, s_>>>(live_, bank_[cur_], d_slots_, rules,
+                                                                bank_[nxt], d_count, d_stats_,
+                                                                d_slot_live);
+        GMC_CUDA_TRY(ctx_, cudaGetLastError());
+      } else {
+        gmc_prep_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_slots_, d_cond_,
+                                                             d_noise_);
+        GMC_CUDA_TRY(ctx_, cudaGetLastError());
+        const gmc_config &cfg = ctx_->cfg;
+        cudaError_t e;
+        if (cfg.precision == GMC_FP32)
+          e = launch_sampler_f32(s_, ctx_->f32, ctx_->stats, live_, d_cond_, d_noise_, 0, 0,
+                                 cfg.steps, cfg.integrator, nullptr, d_exit_);
+        else
+          e = launch_sampler_tc(s_, ctx_->d_tc, ctx_->d_tc_bias, ctx_->f32, ctx_->stats, live_,
+                                d_cond_, d_noise_, 0, 0, cfg.steps, cfg.integrator, nullptr,
+                                d_exit_, ctx_->d_err, d_bias1_);
+        if (e != cudaSuccess) return cuda_error(ctx_, e, "solve: sampler");
+        gmc_post_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_exit_, d_slots_,
+                                                             rules, bank_[nxt], d_count, d_stats_,
+                                                             d_slot_live);
+        GMC_CUDA_TRY(ctx_, cudaGetLastError());
+      }
+      GMC_CUDA_TRY(ctx_, read_counts());
+      live_ = h_counts_[0];
+      for (auto *R : reqs_)
+        if (R) R->live = h_counts_[1 + R->slot];
+      cur_ = nxt;
+      if (method_ == GMC_METHOD_GMC) {
+        gmc_status es = check_device_error(ctx_);
+        if (es != GMC_OK) return es;
+      }
+    }
+    live_i_ = (int)live_;
+    // completions
+    for (int k = 0; k < kMaxSlots; ++k) {
+      Request *R = reqs_[k];
+      if (!R || R->next_hist < R->n_hist || R->live > 0) continue;
+      GMC_CUDA_TRY(ctx_, finish(R));
+      completed.push_back(R);
+      reqs_[k] = nullptr;
+      --active_;
+    }
+    return GMC_OK;
+  }
+
+ private:
+  cudaError_t read_counts() {
+    cudaError_t e = cudaMemcpyAsync(h_counts_, d_counts_, (kMaxSlots + 1) * sizeof(int),
+                                    cudaMemcpyDeviceToHost, s_);
+    if (e) return e;
+    return cudaStreamSynchronize(s_);
+  }
+
+  cudaError_t finish(Request *R) {
+    R->flux.resize(R->ncell);
+    DevStats hs;
+    cudaError_t e = cudaMemcpyAsync(R->flux.data(), R->d_flux, R->ncell * 8, cudaMemcpyDeviceToHost, s_);
+    if (!e) e = cudaMemcpyAsync(&hs, d_stats_ + R->slot, sizeof(hs), cudaMemcpyDeviceToHost, s_);
+    cudaEvent_t e1;
+    cudaEventCreate(&e1);
+    cudaEventRecord(e1, s_);
+    if (!e) e = cudaStreamSynchronize(s_);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, R->ev0, e1);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(R->ev0);
+    R->ev0 = nullptr;
+    pool_.release(R->pool_off, R->footprint);
+    if (e) return e;
+    const double inv = R->n_hist > 0 ? 1.0 / (double)R->n_hist : 0.0;
+    for (auto &f : R->flux) f *= inv;
+    R->st.leaked = hs.leaked;
+    R->st.absorbed = hs.absorbed;
+    R->st.roulette_net = hs.roulette_net;
+    R->st.transmissions = (int64_t)hs.transmissions;
+    R->st.collisions = (int64_t)hs.collisions;
+    R->st.roulette_kills = (int64_t)hs.kills;
+    R->st.waves = waves_;
+    R->st.inward_fixes = (int64_t)hs.inward;
+    R->st.seconds = ms * 1e-3;
+    R->t_done = now_s();
+    R->st.latency = R->t_done - R->t_submit;
+    R->done = true;
+    return cudaSuccess;
+  }
+
+  gmc_ctx *ctx_;
+  int method_;
+  int64_t C_;
+  size_t pool_bytes_;
+  cudaStream_t s_;
+  Pool pool_;
+  void *bank_mem_[2] = {nullptr, nullptr};
+  Bank bank_[2];
+  int cur_ = 0;
+  int64_t live_ = 0;
+  int live_i_ = 0;
+  int64_t waves_ = 0;
+  float *d_cond_ = nullptr, *d_noise_ = nullptr, *d_exit_ = nullptr, *d_bias1_ = nullptr;
+  Slot *d_slots_ = nullptr;
+  DevStats *d_stats_ = nullptr;
+  int *d_counts_ = nullptr;
+  int *h_counts_ = nullptr;
+  Request *reqs_[kMaxSlots];
+  int active_ = 0;
+};
+
+// The server: a worker thread running the engine over admitted requests.
+struct Server {
+  gmc_ctx *ctx = nullptr;
+  std::unique_ptr<Engine> engine;
+  cudaStream_t stream = nullptr;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request *> queue;
+  std::map<uint64_t, std::unique_ptr<Request>> all;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  gmc_status fatal = GMC_OK;
+  int method = 0;
+
+  void run() {
+    cudaSetDevice(ctx->device);
+    std::vector<Request *> done;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        if (!stop && engine->idle() && queue.empty())
+          cv_work.wait_for(lk, std::chrono::milliseconds(50));
+        if (stop) break;
+        while (!queue.empty()) {
+          gmc_status err;
+          if (!engine->try_admit(queue.front(), &err)) {
+            if (err != GMC_OK) {
+              queue.front()->status = err;
+              queue.front()->done = true;
+              queue.pop_front();
+              cv_done.notify_all();
+              continue;
+            }
+            break;  // first-come first-served: wait until memory frees up
+          }
+          queue.pop_front();
+        }
+      }
+      if (engine->idle()) continue;
+      done.clear();
+      const gmc_status st = engine->step(done);
+      std::lock_guard<std::mutex> lk(mu);
+      if (st != GMC_OK) {
+        fatal = st;
+        stop = true;
+        cv_done.notify_all();
+        break;
+      }
+      if (!done.empty()) cv_done.notify_all();
+    }
+  }
+};
+
+void server_free(Server *S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  S->engine.reset();
+  if (S->stream) cudaStreamDestroy(S->stream);
+  delete S;
+}
+
+void engine_free(Engine *E) { delete E; }
+
 }  // namespace gmc
 
 using namespace gmc;
 
-extern "C" gmc_status transport_solve(gmc_ctx *ctx, int nx, int ny, const float *tau,
-                                      const float *c, const float *source, int64_t n_histories,
-                                      int method, uint64_t seed, double *flux,
-                                      gmc_solve_stats *stats) {
+extern "C" {
+
+gmc_status transport_solve(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                           const float *source, int64_t n_histories, int method, uint64_t seed,
+                           double *flux, gmc_solve_stats *stats) {
   if (!ctx) return GMC_EINVAL;
-  if (nx < 1 || ny < 1 || (int64_t)nx * ny > (1 << 26))
-    return set_error(ctx, GMC_EINVAL, "transport_solve: grid must be 1..2^26 cells");
-  if (!tau || !c || !source || !flux) return set_error(ctx, GMC_EINVAL, "transport_solve: null array");
-  if (n_histories < 0) return set_error(ctx, GMC_EINVAL, "transport_solve: n_histories < 0");
-  if (method != GMC_METHOD_ANALOG && method != GMC_METHOD_GMC)
-    return set_error(ctx, GMC_EINVAL, "transport_solve: unknown method");
-  const int64_t ncell = (int64_t)nx * ny;
-  std::vector<double> cdf(ncell);
-  double acc = 0.0;
-  for (int64_t k = 0; k < ncell; ++k) {
-    if (!(tau[k] > 0.0f) || !std::isfinite(tau[k]) || !(c[k] >= 0.0f && c[k] <= 1.0f))
-      return set_error(ctx, GMC_EINVAL, "transport_solve: cell %lld needs tau > 0, c in [0,1]",
-                       (long long)k);
-    if (method == GMC_METHOD_GMC && (tau[k] < 0.05f || tau[k] > 2000.0f || c[k] < 0.4f))
-      return set_error(ctx, GMC_EINVAL,
-                       "transport_solve: cell %lld outside the sampler's range (tau in [0.05, 2000], c >= 0.4)",
-                       (long long)k);
-    if (!(source[k] >= 0.0f) || !std::isfinite(source[k]))
-      return set_error(ctx, GMC_EINVAL, "transport_solve: source must be finite and >= 0");
-    acc += source[k] > 0.0f ? (double)source[k] : 0.0;
-    cdf[k] = acc;
-  }
-  if (n_histories > 0 && !(acc > 0.0)) return set_error(ctx, GMC_EINVAL, "transport_solve: zero source");
-  if (method == GMC_METHOD_GMC && !ctx->has_weights)
-    return set_error(ctx, GMC_ENOWEIGHTS, "transport_solve: GMC needs gmc_load_weights");
-  const gmc_config cfg = ctx->cfg;
-  if (method == GMC_METHOD_GMC && cfg.precision == GMC_FP8)
-    return set_error(ctx, GMC_ENOTIMPL, "transport_solve: FP8 sampler not built");
-  const int64_t C = cfg.bank_capacity;
-
+  if (!flux) return set_error(ctx, GMC_EINVAL, "transport_solve: null flux");
+  Request R;
+  gmc_status st = make_request(ctx, nx, ny, tau, c, source, n_histories, method, seed, R);
+  if (st != GMC_OK) return st;
   cudaSetDevice(ctx->device);
-  cudaStream_t s = ctx->stream;
-  // scratch: grid (tau, c), cdf, flux, stats+counters, two banks, cond, noise, exits
-  GMC_CUDA_TRY(ctx, ensure(ctx->solve[0], (size_t)ncell * 8));
-  GMC_CUDA_TRY(ctx, ensure(ctx->solve[1], (size_t)ncell * 8));
-  GMC_CUDA_TRY(ctx, ensure(ctx->solve[2], (size_t)ncell * 8));
-  GMC_CUDA_TRY(ctx, ensure(ctx->solve[3], sizeof(DevStats) + 64));
-  GMC_CUDA_TRY(ctx, ensure(ctx->solve[4], (size_t)C * kBankBytesPerParticle));
-  GMC_CUDA_TRY(ctx, ensure(ctx->solve[5], (size_t)C * kBankBytesPerParticle));
-  if (method == GMC_METHOD_GMC) {
-    GMC_CUDA_TRY(ctx, ensure(ctx->solve[6], (size_t)C * 5 * 4));
-    GMC_CUDA_TRY(ctx, ensure(ctx->solve[7], (size_t)C * 4 * 4));
-    GMC_CUDA_TRY(ctx, ensure(ctx->solve[8], (size_t)C * 4 * 4));
-    GMC_CUDA_TRY(ctx, ensure(ctx->bias1, (size_t)2 * cfg.steps * 256 * sizeof(float)));
+  const int64_t C = ctx->cfg.bank_capacity;
+  Engine *E = ctx->solver;
+  if (!E || E->method() != method || E->capacity() != C || E->pool_capacity() < R.footprint ||
+      E->stream() != ctx->stream) {
+    if (E) engine_free(E);
+    ctx->solver = nullptr;
+    E = new Engine(ctx, method, C, std::max<size_t>(R.footprint, (size_t)1 << 20), ctx->stream);
+    st = E->init();
+    if (st != GMC_OK) {
+      engine_free(E);
+      return st;
+    }
+    ctx->solver = E;
   }
-  float *d_tau = (float *)ctx->solve[0].ptr;
-  float *d_c = d_tau + ncell;
-  double *d_cdf = (double *)ctx->solve[1].ptr;
-  double *d_flux = (double *)ctx->solve[2].ptr;
-  DevStats *d_st = (DevStats *)ctx->solve[3].ptr;
-  int *d_count = (int *)((char *)ctx->solve[3].ptr + sizeof(DevStats) + 16);
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d_tau, tau, ncell * 4, cudaMemcpyHostToDevice, s));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d_c, c, ncell * 4, cudaMemcpyHostToDevice, s));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d_cdf, cdf.data(), ncell * 8, cudaMemcpyHostToDevice, s));
-  GMC_CUDA_TRY(ctx, cudaMemsetAsync(d_flux, 0, ncell * 8, s));
-  GMC_CUDA_TRY(ctx, cudaMemsetAsync(d_st, 0, sizeof(DevStats) + 64, s));
-
-  Grid G{nx, ny, d_tau, d_c};
-  Rules R{seed, (float)cfg.w_cut, (float)cfg.p_survive};
-  Bank bank[2] = {carve(ctx->solve[4].ptr, C), carve(ctx->solve[5].ptr, C)};
-  int cur = 0;
-  int64_t live = 0, next_hist = 0, waves = 0;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
-  int h_count = 0;
-  for (;;) {
-    // births into the free slots of the current bank
-    const int64_t room = C - live;
-    const int64_t m = std::min(room, n_histories - next_hist);
-    if (m > 0) {
-      GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d_count, &live, 4, cudaMemcpyHostToDevice, s));
-      birth_kernel<<<nblocks(m, 256), 256, 0, s>>>(next_hist, m, d_cdf, acc, G, R, d_flux,
-                                                   bank[cur], d_count, d_st);
-      GMC_CUDA_TRY(ctx, cudaGetLastError());
-      GMC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_count, d_count, 4, cudaMemcpyDeviceToHost, s));
-      GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-      next_hist += m;
-      live = h_count;
-    }
-    if (live == 0) {
-      if (next_hist >= n_histories) break;
-      continue;
-    }
-    ++waves;
-    GMC_CUDA_TRY(ctx, cudaMemsetAsync(d_count, 0, 4, s));
-    const int nxt = cur ^ 1;
-    if (method == GMC_METHOD_ANALOG) {
-      analog_wave_kernel<<<nblocks(live, 128), 128, 0, s>>>(live, bank[cur], G, R, d_flux, bank[nxt],
-                                                           d_count, d_st);
-      GMC_CUDA_TRY(ctx, cudaGetLastError());
-    } else {
-      float *d_cond = (float *)ctx->solve[6].ptr;
-      float *d_noise = (float *)ctx->solve[7].ptr;
-      float *d_exit = (float *)ctx->solve[8].ptr;
-      gmc_prep_kernel<<<nblocks(live, 256), 256, 0, s>>>(live, bank[cur], G, seed, d_cond, d_noise);
-      GMC_CUDA_TRY(ctx, cudaGetLastError());
-      cudaError_t e;
-      if (cfg.precision == GMC_FP32)
-        e = launch_sampler_f32(s, ctx->f32, ctx->stats, live, d_cond, d_noise, seed, 0, cfg.steps,
-                               cfg.integrator, nullptr, d_exit);
-      else
-        e = launch_sampler_tc(s, ctx->d_tc, ctx->d_tc_bias, ctx->f32, ctx->stats, live, d_cond,
-                              d_noise, seed, 0, cfg.steps, cfg.integrator, nullptr, d_exit,
-                              ctx->d_err, (float *)ctx->bias1.ptr);
-      if (e != cudaSuccess) return cuda_error(ctx, e, "transport_solve sampler");
-      gmc_post_kernel<<<nblocks(live, 256), 256, 0, s>>>(live, bank[cur], d_exit, G, R, d_flux,
-                                                         bank[nxt], d_count, d_st);
-      GMC_CUDA_TRY(ctx, cudaGetLastError());
-    }
-    GMC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_count, d_count, 4, cudaMemcpyDeviceToHost, s));
-    GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    live = h_count;
-    cur = nxt;
-    if (method == GMC_METHOD_GMC) {
-      gmc_status es = check_device_error(ctx);
-      if (es != GMC_OK) return es;
+  R.t_submit = now_s();
+  gmc_status err;
+  if (!E->try_admit(&R, &err)) return err != GMC_OK ? err : set_error(ctx, GMC_ENOMEM, "transport_solve: cannot admit");
+  std::vector<Request *> done;
+  while (!R.done) {
+    st = E->step(done);
+    if (st != GMC_OK) {
+      engine_free(E);
+      ctx->solver = nullptr;
+      return st;
     }
   }
-  cudaEventRecord(e1, s);
-  std::vector<double> hf(ncell);
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(hf.data(), d_flux, ncell * 8, cudaMemcpyDeviceToHost, s));
-  DevStats hs;
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(&hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-  GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  float ms = 0.0f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  const double inv = n_histories > 0 ? 1.0 / (double)n_histories : 0.0;
-  for (int64_t k = 0; k < ncell; ++k) flux[k] = hf[k] * inv;
-  if (stats) {
-    stats->leaked = hs.leaked;
-    stats->absorbed = hs.absorbed;
-    stats->roulette_net = hs.roulette_net;
-    stats->transmissions = (int64_t)hs.transmissions;
-    stats->collisions = (int64_t)hs.collisions;
-    stats->roulette_kills = (int64_t)hs.kills;
-    stats->waves = waves;
-    stats->inward_fixes = (int64_t)hs.inward;
-    stats->seconds = ms * 1e-3;
-  }
+  std::memcpy(flux, R.flux.data(), R.ncell * sizeof(double));
+  if (stats) *stats = R.st;
   return check_device_error(ctx);
 }
+
+gmc_status gmc_serve_start(gmc_ctx *ctx, const gmc_serve_config *cfg) {
+  if (!ctx || !cfg) return GMC_EINVAL;
+  if (ctx->server) return set_error(ctx, GMC_EBUSY, "gmc_serve_start: already serving");
+  if (cfg->method != GMC_METHOD_ANALOG && cfg->method != GMC_METHOD_GMC)
+    return set_error(ctx, GMC_EINVAL, "gmc_serve_start: unknown method");
+  if (cfg->memory_budget < ((size_t)1 << 20))
+    return set_error(ctx, GMC_EINVAL, "gmc_serve_start: memory_budget must be >= 1 MiB");
+  if (cfg->method == GMC_METHOD_GMC && !ctx->has_weights)
+    return set_error(ctx, GMC_ENOWEIGHTS, "gmc_serve_start: GMC needs gmc_load_weights");
+  cudaSetDevice(ctx->device);
+  Server *S = new Server();
+  S->ctx = ctx;
+  S->method = cfg->method;
+  cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (e) {
+    delete S;
+    return cuda_error(ctx, e, "gmc_serve_start: stream");
+  }
+  S->engine.reset(new Engine(ctx, cfg->method, ctx->cfg.bank_capacity, cfg->memory_budget, S->stream));
+  gmc_status st = S->engine->init();
+  if (st != GMC_OK) {
+    server_free(S);
+    return st;
+  }
+  S->worker = std::thread([S] { S->run(); });
+  ctx->server = S;
+  return GMC_OK;
+}
+
+gmc_status gmc_submit(gmc_ctx *ctx, const gmc_solve_req *req, uint64_t *ticket) {
+  if (!ctx || !req || !ticket) return GMC_EINVAL;
+  Server *S = ctx->server;
+  if (!S) return set_error(ctx, GMC_EINVAL, "gmc_submit: call gmc_serve_start first");
+  std::unique_ptr<Request> R(new Request());
+  gmc_status st = make_request(ctx, req->nx, req->ny, req->tau, req->c, req->source,
+                               req->n_histories, S->method, req->seed, *R);
+  if (st != GMC_OK) return st;
+  if (R->footprint > S->engine->pool_capacity())
+    return set_error(ctx, GMC_ENOMEM, "gmc_submit: grid needs %zu bytes, budget is %zu",
+                     R->footprint, S->engine->pool_capacity());
+  R->t_submit = now_s();
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->stop) return S->fatal != GMC_OK ? S->fatal : set_error(ctx, GMC_EINVAL, "gmc_submit: server stopped");
+  R->ticket = S->next_ticket++;
+  *ticket = R->ticket;
+  S->queue.push_back(R.get());
+  S->all[R->ticket] = std::move(R);
+  S->cv_work.notify_one();
+  return GMC_OK;
+}
+
+static gmc_status take_result(gmc_ctx *ctx, Server *S, std::map<uint64_t, std::unique_ptr<Request>>::iterator it,
+                              double *flux, gmc_solve_stats *stats) {
+  Request *R = it->second.get();
+  gmc_status st = R->status;
+  if (st == GMC_OK) {
+    if (flux) std::memcpy(flux, R->flux.data(), R->ncell * sizeof(double));
+    if (stats) *stats = R->st;
+  } else {
+    set_error(ctx, st, "request %llu failed", (unsigned long long)R->ticket);
+  }
+  S->all.erase(it);
+  return st;
+}
+
+gmc_status gmc_poll(gmc_ctx *ctx, uint64_t ticket, double *flux, gmc_solve_stats *stats) {
+  if (!ctx) return GMC_EINVAL;
+  Server *S = ctx->server;
+  if (!S) return set_error(ctx, GMC_EINVAL, "gmc_poll: not serving");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return set_error(ctx, GMC_EINVAL, "gmc_poll: unknown ticket %llu", (unsigned long long)ticket);
+  if (!it->second->done) return S->fatal != GMC_OK ? S->fatal : GMC_EBUSY;
+  return take_result(ctx, S, it, flux, stats);
+}
+
+gmc_status gmc_wait(gmc_ctx *ctx, uint64_t ticket, double timeout_s, double *flux,
+                    gmc_solve_stats *stats) {
+  if (!ctx) return GMC_EINVAL;
+  Server *S = ctx->server;
+  if (!S) return set_error(ctx, GMC_EINVAL, "gmc_wait: not serving");
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return set_error(ctx, GMC_EINVAL, "gmc_wait: unknown ticket %llu", (unsigned long long)ticket);
+  Request *R = it->second.get();
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+  while (!R->done && S->fatal == GMC_OK) {
+    if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !R->done)
+      return set_error(ctx, GMC_ETIMEOUT, "gmc_wait: request %llu not done", (unsigned long long)ticket);
+  }
+  if (!R->done) return S->fatal;
+  return take_result(ctx, S, it, flux, stats);
+}
+
+gmc_status gmc_serve_stop(gmc_ctx *ctx) {
+  if (!ctx) return GMC_EINVAL;
+  Server *S = ctx->server;
+  if (!S) return GMC_OK;
+  const gmc_status fatal = S->fatal;
+  server_free(S);
+  ctx->server = nullptr;
+  return fatal;
+}
+
+}  // extern "C"
