@@ -175,9 +175,17 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--workload", default="sampler", choices=["sampler", "solve", "serve"])
+    ap.add_argument("--weights", default=None, help="GMCW file (default: Kaiming seed 1)")
+    ap.add_argument("--histories", type=float, default=1e6)
+    ap.add_argument("--requests", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "solve":
+        return run_solve(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import numpy as np
     import torch
@@ -329,6 +337,118 @@ def analog_extras(g, ctx, torch):
                                         "mean_collisions": flights, "mode": "analog survival",
                                         "position_precision": "fp64 (tau > 64)"}
     return out
+
+
+def _context(args):
+    import torch
+    import synth
+    import paper_2512_13965_gb300 as g
+    torch.cuda.set_device(0)
+    ctx = g.Context(0)
+    if args.weights:
+        g.gmc_load_weights(ctx, args.weights)
+    else:
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "w.bin")
+            synth.write_weights(path, synth.kaiming_weights(1))
+            g.gmc_load_weights(ctx, path)
+    return g, ctx
+
+
+def run_solve(args):
+    """Full transport solve: 128x128 cells, tau logU[0.1,500], c in {0.5, 0.999}
+    per 16x16 block (seed 2), unit source on the central 8x8 cells, vacuum
+    boundaries; GMC (BF16, 16 and 8 Euler steps) against the GPU random walk."""
+    import numpy as np
+    import synth
+    g, ctx = _context(args)
+    tau, c, src = synth.grid_problem(n=128, seed=2)
+    tau, c, src = (np.ascontiguousarray(a.ravel()) for a in (tau, c, src))
+    n = int(args.histories)
+    out = {}
+
+    def solve(method, seed, steps=16):
+        cfg = g.gmc_get_config(ctx)
+        cfg.steps = steps
+        cfg.precision = g.GMC_BF16
+        g.gmc_set_config(ctx, cfg)
+        f = np.zeros(128 * 128)
+        st = g.transport_solve(ctx, 128, 128, tau, c, src, n, method, seed, f)
+        return f, st
+
+    f_mc, st_mc = solve(g.GMC_METHOD_ANALOG, 1)
+    f_mc2, _ = solve(g.GMC_METHOD_ANALOG, 2)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out["analog"] = {"seconds": st_mc.seconds, "transmissions": st_mc.transmissions,
+                     "transmissions_per_s": st_mc.transmissions / st_mc.seconds,
+                     "collisions": st_mc.collisions, "waves": st_mc.waves,
+                     "flux_rel_err_vs_analog_seed2": rel(f_mc2, f_mc)}
+    for steps in (16, 8):
+        f, st = solve(g.GMC_METHOD_GMC, 3, steps)
+        out["gmc_bf16_k%d" % steps] = {"seconds": st.seconds, "transmissions": st.transmissions,
+                                       "transmissions_per_s": st.transmissions / st.seconds,
+                                       "waves": st.waves, "flux_rel_err_vs_analog": rel(f, f_mc)}
+    line = {"metric": METRIC, "workload": "transport solve 128x128, tau logU[0.1,500], c {0.5,0.999} "
+            "16x16 blocks, central 8x8 source, %d histories" % n, "weights": args.weights or "kaiming seed 1 (untrained)",
+            "results": out, "unit": "cell transmissions/s"}
+    print(json.dumps(line))
+    ctx.close()
+
+
+def run_serve(args):
+    """Serving: Poisson stream of solves, grids n x n with n ~ U{16..256},
+    tau logU[0.1,1000], c {0.5,0.999} blocks, histories logU[1e3,1e5];
+    p50/p99 latency and solves/s for GMC BF16 and the analog walk."""
+    import numpy as np
+    import synth
+    g, ctx = _context(args)
+    rng = np.random.default_rng(4)
+    reqs = []
+    for k in range(args.requests):
+        n = int(rng.integers(16, 257))
+        tau, c, src = synth.grid_problem(n=n, seed=1000 + k, tau_range=(0.1, 1000.0),
+                                         block=16, source=max(2, n // 16))
+        hist = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
+        reqs.append((n, np.ascontiguousarray(tau.ravel()), np.ascontiguousarray(c.ravel()),
+                     np.ascontiguousarray(src.ravel()), hist))
+    out = {}
+    for name, method in (("gmc_bf16", g.GMC_METHOD_GMC), ("analog", g.GMC_METHOD_ANALOG)):
+        cfg = g.gmc_get_config(ctx)
+        cfg.steps = 16
+        cfg.bank_capacity = 1 << 20
+        g.gmc_set_config(ctx, cfg)
+        # capacity: the whole stream submitted at once
+        g.gmc_serve_start(ctx, method, 4 << 30)
+        t0 = time.perf_counter()
+        tks = [g.gmc_submit(ctx, n, n, tau, c, src, h, 7 + i) for i, (n, tau, c, src, h) in enumerate(reqs)]
+        for tk, r in zip(tks, reqs):
+            g.gmc_wait(ctx, tk, 600.0, np.zeros(r[0] * r[0]))
+        cap = len(reqs) / (time.perf_counter() - t0)
+        # Poisson arrivals at 0.7 of that capacity
+        gaps = rng.exponential(1.0 / (0.7 * cap), len(reqs))
+        t0 = time.perf_counter()
+        tks = []
+        t_next = t0
+        for i, (n, tau, c, src, h) in enumerate(reqs):
+            t_next += gaps[i]
+            while time.perf_counter() < t_next:
+                time.sleep(0.0002)
+            tks.append(g.gmc_submit(ctx, n, n, tau, c, src, h, 100 + i))
+        lat, trans = [], 0
+        for tk, r in zip(tks, reqs):
+            st = g.gmc_wait(ctx, tk, 600.0, np.zeros(r[0] * r[0]))
+            lat.append(st.latency)
+            trans += st.transmissions
+        wall = time.perf_counter() - t0
+        g.gmc_serve_stop(ctx)
+        out[name] = {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                     "solves_per_s": len(reqs) / wall, "capacity_solves_per_s": cap,
+                     "offered_load": 0.7, "transmissions_per_s": trans / wall}
+    line = {"metric": METRIC, "workload": "serving: %d Poisson-arriving solves, n~U{16..256}, "
+            "tau logU[0.1,1000], histories logU[1e3,1e5]" % len(reqs), "results": out,
+            "weights": args.weights or "kaiming seed 1 (untrained)"}
+    print(json.dumps(line))
+    ctx.close()
 
 
 if __name__ == "__main__":

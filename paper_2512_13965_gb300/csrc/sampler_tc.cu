@@ -24,7 +24,11 @@
 // epilogue thread.
 //
 // Roles: warp 0 streams weights, warp 1 owns tensor memory and issues MMAs,
-// warps 2..9 are the epilogue (two threads per row, one per column half).
+// warps 2..17 are the epilogue (four threads per row, 64 columns each).
+// CTAs run in clusters of two that consume the same weight chunks in the
+// same order: each CTA copies half of every chunk from L2 and multicasts it
+// into both CTAs' stage, so L2 serves each chunk once per pair; a stage is
+// refilled only after both CTAs' MMAs have released it.
 // Every wait is bounded; a timeout sets *err and the CTA drains and exits.
 #include <cuda_bf16.h>
 
@@ -44,8 +48,10 @@ constexpr int TM = 128;
 constexpr int NST = 5;                  // weight-chunk stages
 constexpr uint32_t CHUNK = 16384;       // 256 rows x 32 K x 2 bytes
 constexpr int CHUNKS = 8;               // per hidden layer: K in slices of 32
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;            // four per TMEM lane quadrant, 64 columns each
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
+constexpr int CLUSTER = 2;               // CTAs sharing each weight chunk by multicast
+constexpr uint32_t SLICE = CHUNK / CLUSTER;
 constexpr uint32_t TMEM_COLS = 512;     // two 128 x 256 FP32 accumulators
 
 // packed global operand buffer (bytes)
@@ -110,6 +116,38 @@ __device__ __forceinline__ uint32_t sw128(uint32_t base, int r, int c) {
 // 16 B chunk `c` (0..1) of row `r` in a 32-byte-swizzled block.
 __device__ __forceinline__ uint32_t sw32(uint32_t base, int r, int c) {
   return base + (uint32_t)((r >> 3) * 256 + (r & 7) * 32 + ((c ^ ((r >> 2) & 1)) << 4));
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  // not .aligned: producer and MMA lanes reach this point after divergent loops
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Bulk copy global -> the same shared-memory offset of every CTA in `mask`,
+// completing `bytes` on the barrier at the same offset in each of them.
+__device__ __forceinline__ void bulk_g2s_multicast(void *dst, const void *src, uint32_t bytes,
+                                                   uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+// Arrive on the barrier at the same offset in every CTA of `mask` once this
+// thread's tcgen05 operations have completed.
+__device__ __forceinline__ void mma_commit_multicast(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+      "[%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 
 __device__ void fail(Bars &b, int *err, int code) {
@@ -177,7 +215,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(&B.full[s], 1);
-      mbar_init(&B.empty[s], 1);
+      mbar_init(&B.empty[s], CLUSTER);
     }
     mbar_init(&B.res_full, 1);
     for (int t = 0; t < 2; ++t) {
@@ -194,12 +232,18 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // peers multicast into this CTA's barriers only after they exist
   tc_fence_after();
   const uint32_t tmem = B.tmem_base;
   volatile int *abort = &B.abort;
+  const uint32_t rank = cluster_rank();
+  const uint16_t all_ctas = (uint16_t)((1u << CLUSTER) - 1u);
 
   const int64_t ntiles = (P.n + TM - 1) / TM;
   const int64_t npairs = (ntiles + 1) / 2;
+  // every CTA of a cluster runs the same number of pairs (the chunk stream is
+  // shared); pairs past the end have no valid rows
+  const int64_t n_iter = (npairs + gridDim.x - 1) / gridDim.x;
   const float h = 1.0f / (float)P.steps;
 
   if (warp == 0) {
@@ -210,7 +254,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
       mbar_arrive_expect_tx(&B.res_full, 16384);
       bulk_g2s(sm + S_B1, P.packed + OFF_B1, 8192, &B.res_full);
       bulk_g2s(sm + S_B5, P.packed + OFF_B5, 8192, &B.res_full);
-      for (int64_t pr = blockIdx.x; pr < npairs && ok; pr += gridDim.x)
+      for (int64_t ip = 0; ip < n_iter && ok; ++ip)
         for (int e = 0; e < P.n_eval && ok; ++e)
           for (int L = 0; L < 3 && ok; ++L)
             for (int T = 0; T < 2 && ok; ++T)
@@ -223,8 +267,9 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
                   break;
                 }
                 mbar_arrive_expect_tx(&B.full[s], CHUNK);
-                bulk_g2s(sm + S_ST + s * CHUNK, P.packed + OFF_HID + (size_t)(L * CHUNKS + ch) * CHUNK,
-                         CHUNK, &B.full[s]);
+                bulk_g2s_multicast(sm + S_ST + s * CHUNK + rank * SLICE,
+                                   P.packed + OFF_HID + (size_t)(L * CHUNKS + ch) * CHUNK + rank * SLICE,
+                                   SLICE, &B.full[s], all_ctas);
                 ++it;
               }
       if (!ok) {
@@ -242,7 +287,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
       if (!ok) fail(B, P.err, 2);
       uint32_t it = 0, aph[2] = {0, 0};
       const uint32_t id256 = idesc_bf16_m128(256), id16 = idesc_bf16_m128(16);
-      for (int64_t pr = blockIdx.x; pr < npairs && ok; pr += gridDim.x)
+      for (int64_t ip = 0; ip < n_iter && ok; ++ip)
         for (int e = 0; e < P.n_eval && ok; ++e)
           for (int L = 0; L < 5 && ok; ++L)
             for (int T = 0; T < 2 && ok; ++T) {
@@ -275,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
                     mma_f16(d, smem_desc(a_k + (uint32_t)k * 32u, 1024, kSwizzle128B),
                             smem_desc(bst + (uint32_t)k * 32u, 512, kSwizzle64B), id256,
                             (ch | k) != 0);
-                  mma_commit(&B.empty[s]);
+                  mma_commit_multicast(&B.empty[s], all_ctas);
                   ++it;
                 }
                 if (!ok) break;
@@ -298,13 +343,14 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     }
   } else {
     // ---------------- epilogue ----------------
-    const int q = warp & 3, hf = (warp - 2) >> 2;
+    const int q = warp & 3, hf = (warp - 2) >> 2;  // lane quadrant, column quarter
     const int r = 32 * q + lane;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
     float cn[2][kCond], x[2][4], xm[2][4];
     uint32_t dph[2] = {0, 0};
     bool ok = true;
-    for (int64_t pr = blockIdx.x; pr < npairs && ok; pr += gridDim.x) {
+    for (int64_t ip = 0; ip < n_iter && ok; ++ip) {
+      const int64_t pr = blockIdx.x + ip * gridDim.x;
       for (int T = 0; T < 2; ++T) {
         const int64_t g = (2 * pr + T) * TM + r;
         const bool valid = g < P.n;
@@ -343,22 +389,16 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
             tc_fence_after();
             const float *bias = L == 0 ? P.bias1 + (size_t)e * 256 : P.bias + L * 256;
             const uint32_t a_base = sbase + (T ? S_A1 : S_A0);
-            const uint32_t tcol = tmem + lane_off + (uint32_t)T * 256u + (uint32_t)hf * 128u;
-            // software pipeline: the load of chunk j+1 is in flight while
-            // chunk j is converted and stored
+            const uint32_t tcol = tmem + lane_off + (uint32_t)T * 256u + (uint32_t)hf * 64u;
+            // the load of the second 32 columns is in flight while the first
+            // are converted and stored
             uint32_t va[32], vb[32];
             tmem_ld32_raw(tcol, va);
             tmem_wait_ld_regs(va);
             tmem_ld32_raw(tcol + 32u, vb);
-            epi32(va, bias, hf * 128, a_base, r);
+            epi32(va, bias, hf * 64, a_base, r);
             tmem_wait_ld_regs(vb);
-            tmem_ld32_raw(tcol + 64u, va);
-            epi32(vb, bias, hf * 128 + 32, a_base, r);
-            tmem_wait_ld_regs(va);
-            tmem_ld32_raw(tcol + 96u, vb);
-            epi32(va, bias, hf * 128 + 64, a_base, r);
-            tmem_wait_ld_regs(vb);
-            epi32(vb, bias, hf * 128 + 96, a_base, r);
+            epi32(vb, bias, hf * 64 + 32, a_base, r);
             fence_proxy_async_smem();
             tc_fence_before();
             __syncwarp();
@@ -422,6 +462,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
 
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // no peer multicasts into this CTA's barriers after it exits
   tc_fence_after();
   if (warp == 1) {
     __syncwarp();
@@ -523,7 +564,10 @@ cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const flo
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = (n + TM - 1) / TM, npairs = (ntiles + 1) / 2;
-  const int grid = (int)(npairs < sms ? npairs : sms);
+  int64_t g = npairs < sms ? npairs : sms;
+  g = (g + CLUSTER - 1) / CLUSTER * CLUSTER;
+  if (g > sms / CLUSTER * CLUSTER) g = sms / CLUSTER * CLUSTER;
+  const int grid = (int)g;
   Params p;
   p.packed = (const unsigned char *)packed;
   p.bias = bias;
@@ -540,7 +584,32 @@ cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const flo
   p.y_raw = y_raw;
   p.exitp = exit;
   p.err = err;
-  sampler_tc_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(p);
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  lc.blockDim = dim3(THREADS);
+  lc.dynamicSmemBytes = SMEM_BYTES;
+  lc.stream = stream;
+  // a persistent grid must be co-resident: at most the clusters that fit
+  static int max_clusters = -1;
+  if (max_clusters < 0) {
+    lc.gridDim = dim3((unsigned)(sms / CLUSTER * CLUSTER));
+    int mc = 0;
+    if (cudaOccupancyMaxActiveClusters(&mc, sampler_tc_kernel, &lc) != cudaSuccess || mc < 1) {
+      cudaGetLastError();
+      mc = sms / CLUSTER;
+    }
+    max_clusters = mc;
+  }
+  const int grid_fit = grid < max_clusters * CLUSTER ? grid : max_clusters * CLUSTER;
+  lc.gridDim = dim3((unsigned)grid_fit);
+  e = cudaLaunchKernelEx(&lc, sampler_tc_kernel, p);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -1,0 +1,81 @@
+"""Train the GMC velocity network on the GPU and write a GMCW weight file.
+
+    python -m paper_2512_13965_gb300.train --out weights.bin \\
+        [--samples 16777216] [--steps 20000] [--batch 8192] [--lr 1e-3]
+
+Data: `gmc_train_data` (implicit-capture random walks, tau log-uniform in
+[0.1, 1000], c uniform in [0.5, 0.999]); objective: conditional flow
+matching (Eq. 9) with AdamW; everything runs in libgmc.so. The network
+starts from Kaiming-normal weights drawn by `synth` (seed --init-seed).
+Prints one JSON line per report interval (loss, samples/s).
+"""
+import argparse
+import json
+import os
+import sys
+import tempfile
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--samples", type=int, default=1 << 24)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--weight-decay", type=float, default=0.01)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--init-seed", type=int, default=1)
+    ap.add_argument("--tau", type=float, nargs=2, default=(0.1, 1000.0))
+    ap.add_argument("--c", type=float, nargs=2, default=(0.5, 0.999))
+    ap.add_argument("--report", type=int, default=1000)
+    ap.add_argument("--device", type=int, default=0)
+    args = ap.parse_args(argv)
+
+    import numpy as np
+    import torch
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import synth
+    from . import _abi as g
+
+    torch.cuda.set_device(args.device)
+    ctx = g.Context(args.device)
+    stream = torch.cuda.Stream()
+    g.gmc_set_stream(ctx, stream)
+    with tempfile.TemporaryDirectory() as d:
+        init = os.path.join(d, "init.bin")
+        synth.write_weights(init, synth.kaiming_weights(args.init_seed))
+        g.gmc_load_weights(ctx, init)
+    n = args.samples
+    with torch.cuda.stream(stream):
+        cond = torch.empty(5, n, device="cuda")
+        y = torch.empty(4, n, device="cuda")
+    t0 = time.perf_counter()
+    g.gmc_train_data(ctx, n, args.seed, args.tau[0], args.tau[1], args.c[0], args.c[1], cond, y)
+    g.gmc_synchronize(ctx)
+    t_data = time.perf_counter() - t0
+    print(json.dumps({"phase": "data", "samples": n, "seconds": t_data}), flush=True)
+    cfg = g.gmc_train_config(batch=args.batch, lr=args.lr, beta1=0.9, beta2=0.999, eps=1e-8,
+                             weight_decay=args.weight_decay, seed=args.seed + 1000)
+    g.gmc_train_begin(ctx, n, cond, y, cfg)
+    done = 0
+    while done < args.steps:
+        k = min(args.report, args.steps - done)
+        losses = np.zeros(k, np.float32)
+        t1 = time.perf_counter()
+        g.gmc_train_steps(ctx, k, losses)
+        dt = time.perf_counter() - t1
+        done += k
+        print(json.dumps({"phase": "train", "step": done, "loss": float(losses[-min(k, 100):].mean()),
+                          "rows_per_s": k * args.batch / dt}), flush=True)
+    g.gmc_train_commit(ctx, args.out)
+    print(json.dumps({"phase": "done", "out": args.out, "steps": done}), flush=True)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
