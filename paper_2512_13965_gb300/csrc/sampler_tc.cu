@@ -282,16 +282,29 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
+    // The issuing thread shares its scheduler with busy epilogue warps, so the
+    // loop is kept lean: descriptors are built once and advanced by constant
+    // offsets (the start-address field counts 16-byte units), the chunk loop
+    // is unrolled, and a stage that has already landed costs one try_wait.
     if (lane == 0) {
       bool ok = mbar_wait(&B.res_full, 0, abort);
       if (!ok) fail(B, P.err, 2);
-      uint32_t it = 0, aph[2] = {0, 0};
+      uint32_t aph[2] = {0, 0};
+      uint32_t stage = 0, sph = 0;  // next weight stage and its phase parity
       const uint32_t id256 = idesc_bf16_m128(256), id16 = idesc_bf16_m128(16);
+      const uint64_t dA[2] = {smem_desc(sbase + S_A0, 1024, kSwizzle128B),
+                              smem_desc(sbase + S_A1, 1024, kSwizzle128B)};
+      const uint64_t dA1[2] = {smem_desc(sbase + S_A0, 256, kSwizzle32B),
+                               smem_desc(sbase + S_A1, 256, kSwizzle32B)};
+      const uint64_t dB1 = smem_desc(sbase + S_B1, 256, kSwizzle32B);
+      const uint64_t dB5 = smem_desc(sbase + S_B5, 1024, kSwizzle128B);
+      const uint64_t dST = smem_desc(sbase + S_ST, 512, kSwizzle64B);
       for (int64_t ip = 0; ip < n_iter && ok; ++ip)
         for (int e = 0; e < P.n_eval && ok; ++e)
           for (int L = 0; L < 5 && ok; ++L)
             for (int T = 0; T < 2 && ok; ++T) {
-              if (!mbar_wait(&B.a_ready[T], aph[T] & 1u, abort)) {
+              if (!mbar_try_wait(&B.a_ready[T], aph[T] & 1u) &&
+                  !mbar_wait(&B.a_ready[T], aph[T] & 1u, abort)) {
                 fail(B, P.err, 3);
                 ok = false;
                 break;
@@ -299,39 +312,38 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
               ++aph[T];
               tc_fence_after();
               const uint32_t d = tmem + (uint32_t)T * 256u;
-              const uint32_t a = sbase + (T ? S_A1 : S_A0);
               if (L == 0) {
-                mma_f16(d, smem_desc(a, 256, kSwizzle32B), smem_desc(sbase + S_B1, 256, kSwizzle32B),
-                        id256, 0);
+                mma_f16(d, dA1[T], dB1, id256, 0);
               } else if (L < 4) {
+                const uint64_t a0 = dA[T];
+#pragma unroll
                 for (int ch = 0; ch < CHUNKS; ++ch) {
-                  const int s = it % NST;
-                  if (!mbar_wait(&B.full[s], (it / NST) & 1u, abort)) {
+                  if (!mbar_try_wait(&B.full[stage], sph) && !mbar_wait(&B.full[stage], sph, abort)) {
                     fail(B, P.err, 4);
                     ok = false;
                     break;
                   }
                   tc_fence_after();
-                  // chunk ch = K columns 32 ch .. 32 ch + 31 of all 256 output rows
-                  const uint32_t a_k = a + (uint32_t)(ch >> 1) * 16384u + (uint32_t)(ch & 1) * 64u;
-                  const uint32_t bst = sbase + S_ST + (uint32_t)s * CHUNK;
-#pragma unroll
-                  for (int k = 0; k < 2; ++k)
-                    mma_f16(d, smem_desc(a_k + (uint32_t)k * 32u, 1024, kSwizzle128B),
-                            smem_desc(bst + (uint32_t)k * 32u, 512, kSwizzle64B), id256,
-                            (ch | k) != 0);
-                  mma_commit_multicast(&B.empty[s], all_ctas);
-                  ++it;
+                  // chunk ch = K columns 32 ch .. 32 ch + 31 of all 256 output rows:
+                  // A at K-block ch/2, byte 64 (ch%2) of its rows; B at stage `stage`
+                  const uint64_t a_ch = a0 + (uint64_t)((ch >> 1) * 1024 + (ch & 1) * 4);
+                  const uint64_t b_ch = dST + (uint64_t)(stage * (CHUNK >> 4));
+                  mma_f16(d, a_ch, b_ch, id256, ch != 0);
+                  mma_f16(d, a_ch + 2u, b_ch + 2u, id256, 1u);
+                  mma_commit_multicast(&B.empty[stage], all_ctas);
+                  if (++stage == NST) {
+                    stage = 0;
+                    sph ^= 1u;
+                  }
                 }
                 if (!ok) break;
               } else {
+                const uint64_t a0 = dA[T];
 #pragma unroll
                 for (int kb = 0; kb < 4; ++kb)
 #pragma unroll
                   for (int k = 0; k < 4; ++k)
-                    mma_f16(d, smem_desc(a + (uint32_t)kb * 16384u + (uint32_t)k * 32u, 1024, kSwizzle128B),
-                            smem_desc(sbase + S_B5 + (uint32_t)kb * 2048u + (uint32_t)k * 32u, 1024,
-                                      kSwizzle128B),
+                    mma_f16(d, a0 + (uint64_t)(kb * 1024 + k * 2), dB5 + (uint64_t)(kb * 128 + k * 2),
                             id16, (kb | k) != 0);
               }
               mma_commit(&B.mma_done[T]);
