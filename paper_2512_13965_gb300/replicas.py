@@ -1,0 +1,41 @@
+"""Replica (data-parallel) runs of a transport solve over several processes.
+
+Histories are independent, so a solve of N histories splits into W replicas
+with no exchange during the run: replica r simulates its share of the
+histories with its own Philox seed (seed_for(seed, r)), and the per-source-
+particle fluxes combine as the history-weighted mean
+    phi = sum_r n_r phi_r / sum_r n_r.
+The one collective is that final FP64 sum (torch.distributed all_reduce on
+whatever backend the process group uses). Nothing here computes a step of
+the method; the per-replica solve is transport_solve.
+"""
+import numpy as np
+
+
+def shard(n_histories, world, rank):
+    """Histories of replica `rank` out of `world` (the first n % world get one more)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank/world")
+    base, extra = divmod(int(n_histories), world)
+    return base + (1 if rank < extra else 0)
+
+
+def seed_for(seed, rank):
+    """Philox key of replica `rank`: distinct per replica, equal to `seed` for rank 0."""
+    return (int(seed) + 0x9E3779B97F4A7C15 * int(rank)) & 0xFFFFFFFFFFFFFFFF
+
+
+def combine(flux, n_local, group=None):
+    """History-weighted mean of the replicas' flux arrays (FP64 all_reduce).
+
+    flux: numpy array (this replica's flux per source particle),
+    n_local: this replica's history count. Returns the combined flux.
+    """
+    import torch
+    import torch.distributed as dist
+    t = torch.from_numpy(np.ascontiguousarray(flux, dtype=np.float64) * float(n_local)).reshape(-1)
+    t = torch.cat([t, torch.tensor([float(n_local)], dtype=torch.float64)])
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    total = t[-1].item()
+    return (t[:-1] / total).numpy().reshape(np.shape(flux))
