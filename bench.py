@@ -175,7 +175,7 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--workload", default="sampler", choices=["sampler", "solve", "serve"])
+    ap.add_argument("--workload", default="sampler", choices=["sampler", "solve", "serve", "sweep"])
     ap.add_argument("--weights", default=None, help="GMCW file (default: Kaiming seed 1)")
     ap.add_argument("--histories", type=float, default=1e6)
     ap.add_argument("--requests", type=int, default=200)
@@ -186,6 +186,8 @@ def main():
         return run_solve(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
 
     import numpy as np
     import torch
@@ -391,6 +393,63 @@ def run_solve(args):
     line = {"metric": METRIC, "workload": "transport solve 128x128, tau logU[0.1,500], c {0.5,0.999} "
             "16x16 blocks, central 8x8 source, %d histories" % n, "weights": args.weights or "kaiming seed 1 (untrained)",
             "results": out, "unit": "cell transmissions/s"}
+    print(json.dumps(line))
+    ctx.close()
+
+
+def run_sweep(args):
+    """Cost per cell transmission against optical thickness (the paper's
+    computational-scaling study): the GPU random walk in a purely scattering
+    cell (implicit capture, c = 1) for tau from 0.1 to 1000, against the
+    GMC sampler (BF16, 16 and 8 Euler steps), 2^20 transmissions each."""
+    import numpy as np
+    import torch
+    import synth
+    g, ctx = _context(args)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    g.gmc_set_stream(ctx, stream)
+    n = 1 << 20
+    e = synth.cell_entries(n, 9)
+    xi, cs, sn = (torch.from_numpy(e[k]).cuda() for k in ("xi", "cos", "sin"))
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    ex = torch.empty(4, n, device="cuda")
+    nc = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / reps * 1e-3
+
+    rows = []
+    for tau in (0.1, 0.3, 1, 3, 10, 30, 100, 300, 1000):
+        tt = torch.full((n,), float(tau), device="cuda")
+        cc = torch.ones(n, device="cuda")
+        sec = timed(lambda: g.analog_transmit(ctx, n, xi, cs, sn, tt, cc, g.GMC_ABSORB_IMPLICIT, 3, 0, 0,
+                                              st, ex, nc), reps=1 if tau >= 300 else 3)
+        rows.append({"tau": tau, "analog_transmissions_per_s": n / sec,
+                     "mean_collisions": float(nc.double().mean().item())})
+    cond_h, _, _ = synth.sampler_conditions(n, 1)
+    cond = torch.from_numpy(cond_h).cuda()
+    gmc = {}
+    for k in (16, 8):
+        sec = timed(lambda: g.gmc_transmit(ctx, n, cond, None, 5, 0, k, g.GMC_EULER, g.GMC_BF16, None, ex))
+        gmc["bf16_k%d" % k] = n / sec
+    cross = None
+    for r in rows:
+        if r["analog_transmissions_per_s"] < gmc["bf16_k16"]:
+            cross = r["tau"]
+            break
+    line = {"metric": METRIC, "workload": "tau sweep, pure scattering cell, 2^20 transmissions per point",
+            "analog": rows, "gmc": gmc, "crossover_tau_k16": cross,
+            "note": "analog positions in FP64 above tau = 64"}
     print(json.dumps(line))
     ctx.close()
 

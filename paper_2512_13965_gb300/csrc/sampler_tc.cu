@@ -14,8 +14,8 @@
 //       (the time-embedding columns of layer 1 are the same for every row,
 //        so W1[:, emb] emb(t) + b1 is folded into an FP32 per-evaluation bias)
 //   L2..L4: A (128 x 256 BF16, shared memory, 128-byte swizzle) x W
-//       (256 x 256, streamed in 16 KB chunks of all 256 output rows x 32 K,
-//       64-byte swizzle) -> TMEM, N = 256 per MMA
+//       (256 x 256, streamed in chunks of all 256 output rows x CHUNK_K)
+//       -> TMEM, N = 256 per MMA
 //   L5: A x W5 (N = 16, rows 4..15 zero) -> TMEM columns 0..3
 // Epilogue: SiLU(z) = h + h tanh(h) with h = z/2 (layers 1-4 are packed with
 // weights and biases halved, so the accumulator holds h), in packed BF16x2,
@@ -24,7 +24,7 @@
 // epilogue thread.
 //
 // Roles: warp 0 streams weights, warp 1 owns tensor memory and issues MMAs,
-// warps 2..17 are the epilogue (four threads per row, 64 columns each).
+// warps 2.. are the epilogue (EPI_WARPS / 4 threads per row).
 // CTAs run in clusters of two that consume the same weight chunks in the
 // same order: each CTA copies half of every chunk from L2 and multicasts it
 // into both CTAs' stage, so L2 serves each chunk once per pair; a stage is
@@ -45,11 +45,27 @@ namespace {
 using namespace ptx;
 
 constexpr int TM = 128;
-constexpr int NST = 5;                  // weight-chunk stages
-constexpr uint32_t CHUNK = 16384;       // 256 rows x 32 K x 2 bytes
-constexpr int CHUNKS = 8;               // per hidden layer: K in slices of 32
-constexpr int EPI_WARPS = 16;            // four per TMEM lane quadrant, 64 columns each
+#ifndef GMC_TC_CHUNK_K
+#define GMC_TC_CHUNK_K 32
+#endif
+#ifndef GMC_TC_EPI_WARPS
+#define GMC_TC_EPI_WARPS 16
+#endif
+// Weight chunk: all 256 output rows x CHUNK_K inputs, K-major; 32 -> 64-byte
+// swizzle (16 KB), 64 -> 128-byte swizzle (32 KB).
+constexpr int CHUNK_K = GMC_TC_CHUNK_K;
+constexpr uint32_t CHUNK = 256u * CHUNK_K * 2u;
+constexpr int CHUNKS = 256 / CHUNK_K;             // per hidden layer
+constexpr int MMAS_PER_CHUNK = CHUNK_K / 16;
+constexpr uint32_t CHUNK_SWIZZLE = CHUNK_K == 32 ? 4u /* 64B */ : 2u /* 128B */;
+constexpr uint32_t CHUNK_SBO = CHUNK_K == 32 ? 512u : 1024u;
+constexpr int NST = (81920 / CHUNK) > 5 ? 5 : (int)(81920 / CHUNK);  // stages in 80 KB
+constexpr int EPI_WARPS = GMC_TC_EPI_WARPS;      // a multiple of 4 (TMEM lane quadrants)
+constexpr int EPI_COLS = 256 / (EPI_WARPS / 4);   // accumulator columns per epilogue thread
+constexpr int EPI_CH = EPI_COLS / 32;             // 32-column TMEM loads per thread
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
+static_assert(CHUNK_K == 32 || CHUNK_K == 64, "chunk K");
+static_assert(EPI_WARPS == 8 || EPI_WARPS == 16, "epilogue warps");
 constexpr int CLUSTER = 2;               // CTAs sharing each weight chunk by multicast
 constexpr uint32_t SLICE = CHUNK / CLUSTER;
 constexpr uint32_t TMEM_COLS = 512;     // two 128 x 256 FP32 accumulators
@@ -65,7 +81,7 @@ constexpr uint32_t S_A0 = 0;                     // tile X operand, 64 KB
 constexpr uint32_t S_A1 = 65536;                 // tile Y operand, 64 KB
 constexpr uint32_t S_B1 = 131072;                // 8 KB
 constexpr uint32_t S_B5 = 139264;                // 8 KB
-constexpr uint32_t S_ST = 147456;                // NST x 16 KB
+constexpr uint32_t S_ST = 147456;                // NST weight stages
 constexpr uint32_t S_BAR = S_ST + NST * CHUNK;   // barriers and flags
 constexpr uint32_t S_TOTAL = S_BAR + 256;
 constexpr uint32_t SMEM_BYTES = S_TOTAL + 1024;  // + alignment slack
@@ -298,7 +314,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
                                smem_desc(sbase + S_A1, 256, kSwizzle32B)};
       const uint64_t dB1 = smem_desc(sbase + S_B1, 256, kSwizzle32B);
       const uint64_t dB5 = smem_desc(sbase + S_B5, 1024, kSwizzle128B);
-      const uint64_t dST = smem_desc(sbase + S_ST, 512, kSwizzle64B);
+      const uint64_t dST = smem_desc(sbase + S_ST, CHUNK_SBO, CHUNK_SWIZZLE);
       for (int64_t ip = 0; ip < n_iter && ok; ++ip)
         for (int e = 0; e < P.n_eval && ok; ++e)
           for (int L = 0; L < 5 && ok; ++L)
@@ -324,12 +340,15 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
                     break;
                   }
                   tc_fence_after();
-                  // chunk ch = K columns 32 ch .. 32 ch + 31 of all 256 output rows:
-                  // A at K-block ch/2, byte 64 (ch%2) of its rows; B at stage `stage`
-                  const uint64_t a_ch = a0 + (uint64_t)((ch >> 1) * 1024 + (ch & 1) * 4);
+                  // chunk ch = K columns CHUNK_K ch .. of all 256 output rows: A at
+                  // K-block (CHUNK_K ch)/64, byte 2 (CHUNK_K ch % 64) of its rows
+                  const int k0 = ch * CHUNK_K;
+                  const uint64_t a_ch = a0 + (uint64_t)((k0 >> 6) * 1024 + ((k0 & 63) >> 3));
                   const uint64_t b_ch = dST + (uint64_t)(stage * (CHUNK >> 4));
-                  mma_f16(d, a_ch, b_ch, id256, ch != 0);
-                  mma_f16(d, a_ch + 2u, b_ch + 2u, id256, 1u);
+#pragma unroll
+                  for (int k = 0; k < MMAS_PER_CHUNK; ++k)
+                    mma_f16(d, a_ch + (uint64_t)(2 * k), b_ch + (uint64_t)(2 * k), id256,
+                            (ch | k) != 0);
                   mma_commit_multicast(&B.empty[stage], all_ctas);
                   if (++stage == NST) {
                     stage = 0;
@@ -401,16 +420,18 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
             tc_fence_after();
             const float *bias = L == 0 ? P.bias1 + (size_t)e * 256 : P.bias + L * 256;
             const uint32_t a_base = sbase + (T ? S_A1 : S_A0);
-            const uint32_t tcol = tmem + lane_off + (uint32_t)T * 256u + (uint32_t)hf * 64u;
-            // the load of the second 32 columns is in flight while the first
-            // are converted and stored
-            uint32_t va[32], vb[32];
-            tmem_ld32_raw(tcol, va);
-            tmem_wait_ld_regs(va);
-            tmem_ld32_raw(tcol + 32u, vb);
-            epi32(va, bias, hf * 64, a_base, r);
-            tmem_wait_ld_regs(vb);
-            epi32(vb, bias, hf * 64 + 32, a_base, r);
+            const uint32_t tcol = tmem + lane_off + (uint32_t)T * 256u + (uint32_t)(hf * EPI_COLS);
+            // the load of the next 32 columns is in flight while the current
+            // ones are converted and stored
+            uint32_t buf[2][32];
+            tmem_ld32_raw(tcol, buf[0]);
+            tmem_wait_ld_regs(buf[0]);
+#pragma unroll
+            for (int j = 0; j < EPI_CH; ++j) {
+              if (j + 1 < EPI_CH) tmem_ld32_raw(tcol + 32u * (uint32_t)(j + 1), buf[(j + 1) & 1]);
+              epi32(buf[j & 1], bias, hf * EPI_COLS + 32 * j, a_base, r);
+              if (j + 1 < EPI_CH) tmem_wait_ld_regs(buf[(j + 1) & 1]);
+            }
             fence_proxy_async_smem();
             tc_fence_before();
             __syncwarp();
@@ -531,13 +552,14 @@ void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *pack
     const uint16_t u = bf16_bits(v);
     std::memcpy(P + off, &u, 2);
   };
-  // hidden layers W2..W4: chunk ch holds all 256 output rows and K 32 ch ..
+  // hidden layers W2..W4: chunk ch holds all 256 output rows and K CHUNK_K ch ..
   for (int L = 0; L < 3; ++L)
     for (int ch = 0; ch < CHUNKS; ++ch) {
       const size_t base = OFF_HID + (size_t)(L * CHUNKS + ch) * CHUNK;
       for (int i = 0; i < 256; ++i)
-        for (int j = 0; j < 32; ++j)
-          put(base + sw64_off(i, j), 0.5f * W[L + 1][i * 256 + ch * 32 + j]);
+        for (int j = 0; j < CHUNK_K; ++j)
+          put(base + (CHUNK_K == 32 ? sw64_off(i, j) : sw128_off(i, j)),
+              0.5f * W[L + 1][i * 256 + ch * CHUNK_K + j]);
     }
   // layer 1: [cond (5), x (4) for x_hi, x (4) again for x_lo, 0 0 0]
   for (int nrow = 0; nrow < 256; ++nrow) {
