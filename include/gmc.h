@@ -60,7 +60,10 @@ typedef enum gmc_status {
 } gmc_status;
 
 typedef enum gmc_precision { GMC_FP32 = 0, GMC_BF16 = 1, GMC_FP8 = 2 } gmc_precision;
-typedef enum gmc_integrator { GMC_EULER = 0, GMC_MIDPOINT = 1 } gmc_integrator;
+/* Fixed-step integrators of Eq. 8 with h = 1/K, t_k = k h: explicit Euler,
+   explicit midpoint, classical Runge-Kutta (four evaluations per step; the
+   solver the paper times). */
+typedef enum gmc_integrator { GMC_EULER = 0, GMC_MIDPOINT = 1, GMC_RK4 = 2 } gmc_integrator;
 typedef enum gmc_absorb_mode { GMC_ABSORB_ANALOG = 0, GMC_ABSORB_IMPLICIT = 1 } gmc_absorb_mode;
 typedef enum gmc_method { GMC_METHOD_ANALOG = 0, GMC_METHOD_GMC = 1 } gmc_method;
 
@@ -165,10 +168,10 @@ gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float 
  * only at start-up). Same arguments and results as gmc_transmit with
  * precision GMC_BF16, except:
  *  - every array must be device memory (host pointers give GMC_EINVAL);
- *  - steps must be in [1, 256]: the layer-1 bias table lives in a static
- *    512 KiB device array (512 network evaluations), held by every GPU that
- *    loads the library until the process exits; larger values give
- *    GMC_EINVAL;
+ *  - steps must be in [1, 256] (Euler, midpoint) or [1, 128] (RK4): the
+ *    layer-1 bias table lives in a static 512 KiB device array (512 network
+ *    evaluations), held by every GPU that loads the library until the
+ *    process exits; larger values give GMC_EINVAL;
  *  - the first call on a device resolves that array's address (and may load
  *    the library's device code); make it before any stream capture;
  *  - all calls on a device share the array: calls whose kernels overlap on

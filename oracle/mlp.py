@@ -3,8 +3,8 @@ infrastructure only).
 
 What it computes, in the paper's order:
   * Eq. 8 -- a sample is x(1) of dx/dt = v_theta(x, t), x(0) ~ N(0, I),
-    integrated from t = 0 to 1 with a fixed number of steps (the paper times a
-    fixed-step ODE; here explicit Euler or the explicit midpoint rule).
+    integrated from t = 0 to 1 with a fixed number of steps (explicit Euler,
+    the explicit midpoint rule, or classical RK4, which the paper times).
   * Eq. 10 / Eq. 11 -- the condition c is the entry state and cell in optical
     coordinates and the state x is the exit state y = (p_exit, Omega_exit, s).
     This build uses a square cell and directions on the unit circle, so
@@ -110,6 +110,10 @@ def integrate(vfun, x0, steps, integrator="euler"):
 
     Euler:    x_{k+1} = x_k + h v(x_k, t_k)
     midpoint: x_{k+1} = x_k + h v(x_k + (h/2) v(x_k, t_k), t_k + h/2)
+    rk4:      k1 = v(x_k, t_k), k2 = v(x_k + (h/2) k1, t_k + h/2),
+              k3 = v(x_k + (h/2) k2, t_k + h/2), k4 = v(x_k + h k3, t_k + h),
+              x_{k+1} = x_k + (h/6)(k1 + 2 k2 + 2 k3 + k4)   (classical Runge-Kutta,
+              the fixed-step solver the paper times)
     with h = 1/steps and t_k = k h.
     """
     x = np.array(x0, dtype=np.float64)
@@ -121,6 +125,12 @@ def integrate(vfun, x0, steps, integrator="euler"):
         elif integrator == "midpoint":
             xm = x + 0.5 * h * vfun(x, t)
             x = x + h * vfun(xm, t + 0.5 * h)
+        elif integrator == "rk4":
+            k1 = vfun(x, t)
+            k2 = vfun(x + 0.5 * h * k1, t + 0.5 * h)
+            k3 = vfun(x + 0.5 * h * k2, t + 0.5 * h)
+            k4 = vfun(x + h * k3, t + h)
+            x = x + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
         else:
             raise ValueError(integrator)
     return x

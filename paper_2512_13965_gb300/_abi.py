@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libgmc.so")
 GMC_OK, GMC_EINVAL, GMC_ENOMEM, GMC_ECUDA, GMC_ETIMEOUT = 0, -1, -2, -3, -4
 GMC_EFORMAT, GMC_ENOTIMPL, GMC_EBUSY, GMC_ENOWEIGHTS, GMC_EIO = -5, -6, -7, -8, -9
 GMC_FP32, GMC_BF16, GMC_FP8 = 0, 1, 2
-GMC_EULER, GMC_MIDPOINT = 0, 1
+GMC_EULER, GMC_MIDPOINT, GMC_RK4 = 0, 1, 2
 GMC_ABSORB_ANALOG, GMC_ABSORB_IMPLICIT = 0, 1
 GMC_METHOD_ANALOG, GMC_METHOD_GMC = 0, 1
 

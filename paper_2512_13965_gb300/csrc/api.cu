@@ -224,7 +224,7 @@ gmc_status gmc_set_config(gmc_ctx *ctx, const gmc_config *cfg) {
   if (!ctx || !cfg) return GMC_EINVAL;
   if (cfg->steps < 1 || cfg->steps > 256)
     return set_error(ctx, GMC_EINVAL, "steps must be in [1, 256], got %d", cfg->steps);
-  if (cfg->integrator != GMC_EULER && cfg->integrator != GMC_MIDPOINT)
+  if (cfg->integrator != GMC_EULER && cfg->integrator != GMC_MIDPOINT && cfg->integrator != GMC_RK4)
     return set_error(ctx, GMC_EINVAL, "unknown integrator %d", cfg->integrator);
   if (cfg->precision < GMC_FP32 || cfg->precision > GMC_FP8)
     return set_error(ctx, GMC_EINVAL, "unknown precision %d", cfg->precision);
@@ -383,7 +383,7 @@ gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float 
   if (n == 0) return GMC_OK;
   if (!cond || (!y_raw && !exit)) return set_error(ctx, GMC_EINVAL, "gmc_transmit: null array");
   if (steps < 1 || steps > 256) return set_error(ctx, GMC_EINVAL, "gmc_transmit: steps in [1,256]");
-  if (integrator != GMC_EULER && integrator != GMC_MIDPOINT)
+  if (integrator != GMC_EULER && integrator != GMC_MIDPOINT && integrator != GMC_RK4)
     return set_error(ctx, GMC_EINVAL, "gmc_transmit: unknown integrator");
   if (!ctx->has_weights) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_transmit: no weights loaded");
   if (precision == GMC_FP8) return set_error(ctx, GMC_ENOTIMPL, "gmc_transmit: FP8 not built");
@@ -405,7 +405,7 @@ gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float 
                                          (float *)a_y.dev, (float *)a_exit.dev));
   } else {
     if (!ctx->d_tc) return set_error(ctx, GMC_ENOTIMPL, "gmc_transmit: BF16 path not built");
-    GMC_CUDA_TRY(ctx, ensure(ctx->bias1, (size_t)2 * steps * 256 * sizeof(float)));
+    GMC_CUDA_TRY(ctx, ensure(ctx->bias1, (size_t)4 * steps * 256 * sizeof(float)));
     cudaError_t e = launch_sampler_tc(ctx->stream, ctx->d_tc, ctx->d_tc_bias, ctx->f32, ctx->stats,
                                       n, (const float *)a_cond.dev, (const float *)a_noise.dev,
                                       seed, id0, steps, integrator, (float *)a_y.dev,

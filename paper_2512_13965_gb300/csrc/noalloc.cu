@@ -12,8 +12,8 @@
 // The only scratch the sampler needs beyond its inputs and outputs is the
 // per-evaluation layer-1 bias table (W1[:, emb] emb(t_e) + b1, FP32,
 // 256 floats per network evaluation). Here it lives in a file-scope device
-// array sized for 512 evaluations (256 Euler steps, or 256 midpoint steps),
-// 512 KiB, which every GPU that loads the library holds until the process
+// array sized for 512 evaluations (256 Euler or midpoint steps, 128 RK4
+// steps), 512 KiB, which every GPU that loads the library holds until the process
 // exits. All calls on a device share that one array: two calls whose
 // kernels overlap on the GPU (different streams, or different host threads)
 // race on it and must be serialized by the caller. Each call rewrites every
@@ -67,13 +67,15 @@ extern "C" gmc_status gmc_transmit_noalloc(gmc_ctx *ctx, int64_t n, const float 
                                            int steps, int integrator, float *y_raw, float *exit) {
   if (!ctx) return GMC_EINVAL;
   if (n < 0) return set_error(ctx, GMC_EINVAL, "gmc_transmit_noalloc: n < 0");
-  if (steps < 1 || steps > kNoallocMaxSteps)
-    return set_error(ctx, GMC_EINVAL,
-                     "gmc_transmit_noalloc: steps must be in [1, %d] (the static scratch holds %d "
-                     "layer-1 bias rows), got %d",
-                     kNoallocMaxSteps, kNoallocMaxEvals, steps);
-  if (integrator != GMC_EULER && integrator != GMC_MIDPOINT)
+  if (integrator != GMC_EULER && integrator != GMC_MIDPOINT && integrator != GMC_RK4)
     return set_error(ctx, GMC_EINVAL, "gmc_transmit_noalloc: unknown integrator");
+  const int evals_per_step = integrator == GMC_RK4 ? 4 : (integrator == GMC_MIDPOINT ? 2 : 1);
+  const int max_steps = integrator == GMC_RK4 ? kNoallocMaxEvals / 4 : kNoallocMaxSteps;
+  if (steps < 1 || steps > max_steps)
+    return set_error(ctx, GMC_EINVAL,
+                     "gmc_transmit_noalloc: steps must be in [1, %d] for this integrator (the "
+                     "static scratch holds %d layer-1 bias rows, %d per step), got %d",
+                     max_steps, kNoallocMaxEvals, evals_per_step, steps);
   if (!ctx->has_weights || !ctx->d_tc)
     return set_error(ctx, GMC_ENOWEIGHTS, "gmc_transmit_noalloc: no weights loaded");
   if (n == 0) return GMC_OK;

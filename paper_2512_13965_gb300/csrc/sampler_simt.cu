@@ -24,6 +24,7 @@ struct Smem {
   float wc[KC][kHidden];
   float x[R][4];
   float xm[R][4];
+  float ka[R][4];
   float v[R][4];
   float cn[R][kCond];
   float emb[kEmb];
@@ -157,21 +158,31 @@ __global__ void __launch_bounds__(THREADS) sampler_f32_kernel(
   }
   __syncthreads();
   const float h = 1.0f / (float)steps;
+  const int rr = tid >> 2, dd = tid & 3;
   for (int k = 0; k < steps; ++k) {
     const float t = (float)k * h;
     velocity(s, net, s.x, t);
     if (integrator == GMC_MIDPOINT) {
-      {
-        const int r = tid >> 2, d = tid & 3;
-        s.xm[r][d] = fmaf(0.5f * h, s.v[r][d], s.x[r][d]);
-      }
+      s.xm[rr][dd] = fmaf(0.5f * h, s.v[rr][dd], s.x[rr][dd]);
       __syncthreads();
       velocity(s, net, s.xm, t + 0.5f * h);
+    } else if (integrator == GMC_RK4) {
+      // k1 .. k4 accumulate into ka = k1 + 2 k2 + 2 k3 + k4
+      s.ka[rr][dd] = s.v[rr][dd];
+      s.xm[rr][dd] = fmaf(0.5f * h, s.v[rr][dd], s.x[rr][dd]);
+      __syncthreads();
+      velocity(s, net, s.xm, t + 0.5f * h);
+      s.ka[rr][dd] = fmaf(2.0f, s.v[rr][dd], s.ka[rr][dd]);
+      s.xm[rr][dd] = fmaf(0.5f * h, s.v[rr][dd], s.x[rr][dd]);
+      __syncthreads();
+      velocity(s, net, s.xm, t + 0.5f * h);
+      s.ka[rr][dd] = fmaf(2.0f, s.v[rr][dd], s.ka[rr][dd]);
+      s.xm[rr][dd] = fmaf(h, s.v[rr][dd], s.x[rr][dd]);
+      __syncthreads();
+      velocity(s, net, s.xm, t + h);
+      s.v[rr][dd] = (s.ka[rr][dd] + s.v[rr][dd]) * (1.0f / 6.0f);
     }
-    {
-      const int r = tid >> 2, d = tid & 3;
-      s.x[r][d] = fmaf(h, s.v[r][d], s.x[r][d]);
-    }
+    s.x[rr][dd] = fmaf(h, s.v[rr][dd], s.x[rr][dd]);
     __syncthreads();
   }
   if (tid < R) {

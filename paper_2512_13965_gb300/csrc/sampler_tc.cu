@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     const int q = warp & 3, hf = (warp - 2) >> 2;  // lane quadrant, column quarter
     const int r = 32 * q + lane;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    float cn[2][kCond], x[2][4], xm[2][4];
+    float cn[2][kCond], x[2][4], xm[2][4], ka[2][4];
     uint32_t dph[2] = {0, 0};
     bool ok = true;
     for (int64_t ip = 0; ip < n_iter && ok; ++ip) {
@@ -458,6 +458,21 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
 #pragma unroll
               for (int d = 0; d < 4; ++d) xm[T][d] = fmaf(0.5f * h, v[d], x[T][d]);
               xin = xm[T];
+            } else if (P.integrator == GMC_RK4) {
+              // evaluation e % 4 = i gives k_{i+1}; ka = k1 + 2 k2 + 2 k3 + k4
+              const int i = e & 3;
+              if (i == 3) {
+#pragma unroll
+                for (int d = 0; d < 4; ++d) x[T][d] = fmaf(h * (1.0f / 6.0f), ka[T][d] + v[d], x[T][d]);
+              } else {
+                const float wgt = i == 0 ? 1.0f : 2.0f, hs = i == 2 ? h : 0.5f * h;
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                  ka[T][d] = i == 0 ? v[d] : fmaf(wgt, v[d], ka[T][d]);
+                  xm[T][d] = fmaf(hs, v[d], x[T][d]);
+                }
+                xin = xm[T];
+              }
             } else {
 #pragma unroll
               for (int d = 0; d < 4; ++d) x[T][d] = fmaf(h, v[d], x[T][d]);
@@ -509,8 +524,15 @@ __global__ void layer1_bias_kernel(const float *__restrict__ w1t, const float *_
   const int e = blockIdx.x, c = threadIdx.x;
   if (e >= n_eval) return;
   const float h = 1.0f / (float)steps;
-  const float t = integrator == GMC_MIDPOINT ? (float)(e >> 1) * h + (float)(e & 1) * 0.5f * h
-                                             : (float)e * h;
+  float t;
+  if (integrator == GMC_MIDPOINT) {
+    t = (float)(e >> 1) * h + (float)(e & 1) * 0.5f * h;
+  } else if (integrator == GMC_RK4) {
+    const int i = e & 3;  // stage times t_k, t_k + h/2, t_k + h/2, t_k + h
+    t = (float)(e >> 2) * h + (i == 0 ? 0.0f : (i == 3 ? h : 0.5f * h));
+  } else {
+    t = (float)e * h;
+  }
   float acc = b1[c];
   for (int j = 0; j < kEmb; ++j) acc = fmaf(w1t[(kCond + kState + j) * kHidden + c], time_embedding(j, t), acc);
   out[(size_t)e * kHidden + c] = 0.5f * acc;  // layers 1-4 carry a factor 1/2
@@ -586,7 +608,7 @@ cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const flo
                               int integrator, float *y_raw, float *exit, int *err,
                               float *bias1_scratch) {
   if (n <= 0) return cudaSuccess;
-  const int n_eval = integrator == GMC_MIDPOINT ? 2 * steps : steps;
+  const int n_eval = integrator == GMC_RK4 ? 4 * steps : (integrator == GMC_MIDPOINT ? 2 * steps : steps);
   layer1_bias_kernel<<<n_eval, kHidden, 0, stream>>>(f32.w1t, f32.b1, steps, integrator, n_eval,
                                                      bias1_scratch);
   cudaError_t e = cudaGetLastError();

@@ -512,7 +512,7 @@ class Engine {
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_cond_, C_ * 5 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_noise_, C_ * 4 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_exit_, C_ * 4 * sizeof(float)));
-      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bias1_, 2 * 256 * 256 * sizeof(float)));
+      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bias1_, 4 * 256 * 256 * sizeof(float)));
     }
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_slots_, kMaxSlots * sizeof(Slot)));
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_stats_, kMaxSlots * sizeof(DevStats)));

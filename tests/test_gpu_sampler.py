@@ -169,3 +169,26 @@ def test_bf16_full_size_sampled(gpu_ctx, net):
     err = np.abs(y[:, idx] - expect)
     assert err.max() < BF16_MAX
     assert np.all(np.isfinite(y))
+
+
+@pytest.mark.parametrize("steps", [1, 4, 12])
+def test_fp32_rk4_parity(gpu_ctx, net, steps):
+    # classical RK4, the fixed-step solver the paper times (12 steps)
+    import paper_2512_13965_gb300 as g
+    n = 700
+    cond, _, _ = synth.sampler_conditions(n, 70 + steps)
+    z = synth.gaussian_noise(n, 80 + steps)
+    y, _ = _run(gpu_ctx, cond, z, steps, g.GMC_RK4, g.GMC_FP32)
+    expect = oracle.mlp.sample(net, cond, z, steps, "rk4")
+    assert np.abs(y - expect).max() < FP32_TOL
+
+
+def test_bf16_rk4_bound(gpu_ctx, net):
+    import paper_2512_13965_gb300 as g
+    n = 3000
+    cond, _, _ = synth.sampler_conditions(n, 91)
+    z = synth.gaussian_noise(n, 92)
+    y, _ = _bf16_or_skip(gpu_ctx, cond, z, 12, integ=g.GMC_RK4)
+    expect = oracle.mlp.sample(net, cond, z, 12, "rk4")
+    err = np.abs(y - expect)
+    assert err.max() < BF16_MAX and np.quantile(err, 0.999) < BF16_P999

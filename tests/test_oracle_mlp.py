@@ -122,13 +122,28 @@ def test_condition_and_time_columns(tmp_path):
 @pytest.mark.parametrize("steps", [1, 5, 16])
 def test_integrators_on_linear_field(steps):
     # dx/dt = a x: Euler gives (1 + a h)^K x0, the midpoint rule
-    # (1 + a h + (a h)^2 / 2)^K x0.
+    # (1 + a h + (a h)^2 / 2)^K x0, classical RK4 the degree-4 Taylor
+    # polynomial of exp(a h) to the power K.
     a, h = -0.8, 1.0 / steps
     x0 = np.array([[1.0, -2.0, 0.5, 3.0]])
     ye = mlp.integrate(lambda x, t: a * x, x0, steps, "euler")
     ym = mlp.integrate(lambda x, t: a * x, x0, steps, "midpoint")
-    np.testing.assert_allclose(ye, (1 + a * h) ** steps * x0, rtol=1e-14)
-    np.testing.assert_allclose(ym, (1 + a * h + 0.5 * (a * h) ** 2) ** steps * x0, rtol=1e-14)
+    yr = mlp.integrate(lambda x, t: a * x, x0, steps, "rk4")
+    z = a * h
+    np.testing.assert_allclose(ye, (1 + z) ** steps * x0, rtol=1e-14)
+    np.testing.assert_allclose(ym, (1 + z + 0.5 * z ** 2) ** steps * x0, rtol=1e-14)
+    np.testing.assert_allclose(yr, (1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24) ** steps * x0,
+                               rtol=1e-13)
+
+
+def test_rk4_on_time_field_is_simpson():
+    # dx/dt = f(t): RK4 reduces to Simpson's rule per step.
+    K = 5
+    f = lambda t: np.exp(np.sin(3 * t))
+    y = mlp.integrate(lambda x, t: f(t) + 0 * x, np.zeros((1, 1)), K, "rk4")
+    h = 1.0 / K
+    expect = sum(h / 6 * (f(k * h) + 4 * f(k * h + h / 2) + f(k * h + h)) for k in range(K))
+    assert abs(y[0, 0] - expect) < 1e-14
 
 
 def test_integrators_on_time_field():
