@@ -369,9 +369,10 @@ def run_solve(args):
     n = int(args.histories)
     out = {}
 
-    def solve(method, seed, steps=16):
+    def solve(method, seed, steps=16, integ=0):
         cfg = g.gmc_get_config(ctx)
         cfg.steps = steps
+        cfg.integrator = integ
         cfg.precision = g.GMC_BF16
         g.gmc_set_config(ctx, cfg)
         f = np.zeros(128 * 128)
@@ -385,11 +386,14 @@ def run_solve(args):
                      "transmissions_per_s": st_mc.transmissions / st_mc.seconds,
                      "collisions": st_mc.collisions, "waves": st_mc.waves,
                      "flux_rel_err_vs_analog_seed2": rel(f_mc2, f_mc)}
-    for steps in (16, 8):
-        f, st = solve(g.GMC_METHOD_GMC, 3, steps)
-        out["gmc_bf16_k%d" % steps] = {"seconds": st.seconds, "transmissions": st.transmissions,
-                                       "transmissions_per_s": st.transmissions / st.seconds,
-                                       "waves": st.waves, "flux_rel_err_vs_analog": rel(f, f_mc)}
+    names = {g.GMC_EULER: "euler", g.GMC_MIDPOINT: "midpoint", g.GMC_RK4: "rk4"}
+    for integ, steps in ((g.GMC_EULER, 16), (g.GMC_EULER, 8), (g.GMC_MIDPOINT, 8), (g.GMC_RK4, 4),
+                         (g.GMC_RK4, 12)):
+        f, st = solve(g.GMC_METHOD_GMC, 3, steps, integ)
+        out["gmc_bf16_%s%d" % (names[integ], steps)] = {
+            "seconds": st.seconds, "transmissions": st.transmissions,
+            "transmissions_per_s": st.transmissions / st.seconds, "waves": st.waves,
+            "flux_rel_err_vs_analog": rel(f, f_mc)}
     line = {"metric": METRIC, "workload": "transport solve 128x128, tau logU[0.1,500], c {0.5,0.999} "
             "16x16 blocks, central 8x8 source, %d histories" % n, "weights": args.weights or "kaiming seed 1 (untrained)",
             "results": out, "unit": "cell transmissions/s"}

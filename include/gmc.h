@@ -313,6 +313,9 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
  * losses: host [n_steps] float, nullable (blocking when given).
  */
 gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses);
+/* Learning rate of later gmc_train_steps calls (a schedule is a sequence of
+   calls); AdamW moments and the step count carry over. */
+gmc_status gmc_train_set_lr(gmc_ctx *ctx, double lr);
 /*
  * Loss and gradient of Eq. 9 at the current master weights for an explicit
  * batch (host arrays): cn [B][5] standardized conditions, x1 [B][4]

@@ -92,6 +92,7 @@ def _load():
                            ctypes.c_float, P, P],
         "gmc_train_begin": [P, i64, P, P, ctypes.POINTER(gmc_train_config)],
         "gmc_train_steps": [P, i64, P],
+        "gmc_train_set_lr": [P, ctypes.c_double],
         "gmc_train_grad": [P, i64, P, P, P, P, P, P],
         "gmc_train_params": [P, P],
         "gmc_train_commit": [P, ctypes.c_char_p],
@@ -243,6 +244,10 @@ def gmc_train_begin(ctx, n, cond, y, cfg):
 
 def gmc_train_steps(ctx, n_steps, losses=None):
     return ctx.check(lib.gmc_train_steps(ctx.handle, n_steps, _ptr(losses)))
+
+
+def gmc_train_set_lr(ctx, lr):
+    return ctx.check(lib.gmc_train_set_lr(ctx.handle, lr))
 
 
 def gmc_train_grad(ctx, B, cn, x1, x0, t, grad):

@@ -511,6 +511,14 @@ gmc_status gmc_train_grad(gmc_ctx *ctx, int64_t B, const float *cn, const float 
 
 int64_t gmc_train_param_count(void) { return P_TOTAL; }
 
+gmc_status gmc_train_set_lr(gmc_ctx *ctx, double lr) {
+  if (!ctx) return GMC_EINVAL;
+  if (!ctx->train) return set_error(ctx, GMC_EINVAL, "gmc_train_set_lr: call gmc_train_begin first");
+  if (!(lr > 0.0)) return set_error(ctx, GMC_EINVAL, "gmc_train_set_lr: lr must be > 0");
+  ctx->train->cfg.lr = lr;
+  return GMC_OK;
+}
+
 gmc_status gmc_train_params(gmc_ctx *ctx, float *out) {
   if (!ctx || !out) return GMC_EINVAL;
   if (!ctx->train) return set_error(ctx, GMC_EINVAL, "gmc_train_params: call gmc_train_begin first");

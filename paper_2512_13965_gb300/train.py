@@ -1,11 +1,13 @@
 """Train the GMC velocity network on the GPU and write a GMCW weight file.
 
     python -m paper_2512_13965_gb300.train --out weights.bin \\
-        [--samples 16777216] [--steps 20000] [--batch 8192] [--lr 1e-3]
+        [--samples 16777216] [--steps 20000] [--batch 8192] [--lr 1e-3] \\
+        [--lr-min 1e-5] [--warmup 500]
 
 Data: `gmc_train_data` (implicit-capture random walks, tau log-uniform in
 [0.1, 1000], c uniform in [0.5, 0.999]); objective: conditional flow
-matching (Eq. 9) with AdamW; everything runs in libgmc.so. The network
+matching (Eq. 9) with AdamW, learning rate warmed up linearly and then
+decayed along a cosine to --lr-min; everything runs in libgmc.so. The network
 starts from Kaiming-normal weights drawn by `synth` (seed --init-seed).
 Prints one JSON line per report interval (loss, samples/s).
 """
@@ -24,6 +26,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-min", type=float, default=1e-5)
+    ap.add_argument("--warmup", type=int, default=500)
+    ap.add_argument("--chunk", type=int, default=100, help="steps per learning-rate update")
     ap.add_argument("--weight-decay", type=float, default=0.01)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--init-seed", type=int, default=1)
@@ -62,16 +67,31 @@ def main(argv=None):
     cfg = g.gmc_train_config(batch=args.batch, lr=args.lr, beta1=0.9, beta2=0.999, eps=1e-8,
                              weight_decay=args.weight_decay, seed=args.seed + 1000)
     g.gmc_train_begin(ctx, n, cond, y, cfg)
+    import math
+
+    def lr_at(step):
+        if step < args.warmup:
+            return args.lr * (step + 1) / args.warmup
+        f = (step - args.warmup) / max(1, args.steps - args.warmup)
+        return args.lr_min + 0.5 * (args.lr - args.lr_min) * (1 + math.cos(math.pi * min(f, 1.0)))
+
     done = 0
+    recent = []
+    t1 = time.perf_counter()
     while done < args.steps:
-        k = min(args.report, args.steps - done)
+        k = min(args.chunk, args.steps - done)
+        g.gmc_train_set_lr(ctx, lr_at(done))
         losses = np.zeros(k, np.float32)
-        t1 = time.perf_counter()
         g.gmc_train_steps(ctx, k, losses)
-        dt = time.perf_counter() - t1
+        recent.extend(losses.tolist())
         done += k
-        print(json.dumps({"phase": "train", "step": done, "loss": float(losses[-min(k, 100):].mean()),
-                          "rows_per_s": k * args.batch / dt}), flush=True)
+        if done % args.report == 0 or done == args.steps:
+            dt = time.perf_counter() - t1
+            print(json.dumps({"phase": "train", "step": done, "lr": lr_at(done - 1),
+                              "loss": float(np.mean(recent[-100:])),
+                              "rows_per_s": len(recent) * args.batch / dt}), flush=True)
+            recent = []
+            t1 = time.perf_counter()
     g.gmc_train_commit(ctx, args.out)
     print(json.dumps({"phase": "done", "out": args.out, "steps": done}), flush=True)
     ctx.close()
