@@ -172,13 +172,15 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gmc", choices=["gmc", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--workload", default="sampler", choices=["sampler", "solve", "serve", "sweep"])
+    ap.add_argument("--workload", default="sampler", choices=["sampler", "solve", "serve", "sweep", "heldout"])
     ap.add_argument("--weights", default=None, help="GMCW file (default: Kaiming seed 1)")
     ap.add_argument("--histories", type=float, default=1e6)
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--solve-variants", default=None,
+                    help="comma list for --workload solve, e.g. analog,gmc_bf16_rk412 (default: all)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -188,6 +190,8 @@ def main():
         return run_serve(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "heldout":
+        return run_heldout(args)
 
     import numpy as np
     import torch
@@ -200,7 +204,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prec = g.GMC_BF16 if args.precision == "bf16" else g.GMC_FP32
+    prec = {"bf16": g.GMC_BF16, "fp8": g.GMC_FP8, "fp32": g.GMC_FP32}[args.precision]
 
     ctx = g.Context(local)
     # one explicit stream for the library and for the timing events
@@ -276,6 +280,13 @@ def main():
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16"], "unit": "TFLOP/s",
                 "frac": achieved / pk["bf16"], "traffic": None,
                 "peak_source": pk["src"] + " bf16 burst", "kernel": "sampler_tc_kernel"}
+    elif prec == g.GMC_FP8:
+        # 97% of the flops run in E4M3: the FP8 dense rate is twice BF16's
+        fp8 = 2.0 * pk["bf16"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": fp8, "unit": "TFLOP/s",
+                "frac": achieved / fp8, "traffic": None,
+                "peak_source": pk["src"] + " bf16 burst x 2 (nominal fp8/bf16 ratio)",
+                "kernel": "sampler_tc_kernel<fp8>"}
     else:
         # FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
         alu = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -291,7 +302,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "cell transmissions/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16" if prec == g.GMC_BF16 else "f32", "data": "synthetic",
+                "dtype": {g.GMC_BF16: "bf16", g.GMC_FP8: "e4m3+bf16", g.GMC_FP32: "f32"}[prec],
+                "data": "synthetic",
                 "config": {"workload": WORKLOAD, "batch": BATCH, "ode_steps": ODE_STEPS,
                            "integrator": "euler", "precision": args.precision,
                            "l2": "flushed between steps (256 MiB write)",
@@ -360,7 +372,8 @@ def _context(args):
 def run_solve(args):
     """Full transport solve: 128x128 cells, tau logU[0.1,500], c in {0.5, 0.999}
     per 16x16 block (seed 2), unit source on the central 8x8 cells, vacuum
-    boundaries; GMC (BF16, 16 and 8 Euler steps) against the GPU random walk."""
+    boundaries; GMC (BF16 and FP8; Euler, midpoint and RK4) against the GPU
+    random walk."""
     import numpy as np
     import synth
     g, ctx = _context(args)
@@ -369,31 +382,48 @@ def run_solve(args):
     n = int(args.histories)
     out = {}
 
-    def solve(method, seed, steps=16, integ=0):
+    def solve(method, seed, steps=16, integ=0, prec=None, n_hist=None):
         cfg = g.gmc_get_config(ctx)
         cfg.steps = steps
         cfg.integrator = integ
-        cfg.precision = g.GMC_BF16
+        cfg.precision = g.GMC_BF16 if prec is None else prec
         g.gmc_set_config(ctx, cfg)
         f = np.zeros(128 * 128)
-        st = g.transport_solve(ctx, 128, 128, tau, c, src, n, method, seed, f)
+        st = g.transport_solve(ctx, 128, 128, tau, c, src, n if n_hist is None else n_hist, method,
+                               seed, f)
         return f, st
 
-    f_mc, st_mc = solve(g.GMC_METHOD_ANALOG, 1)
-    f_mc2, _ = solve(g.GMC_METHOD_ANALOG, 2)
+    # the analog reference: two independent runs of n/2 histories, averaged
+    # (= one run of n); their difference gives the statistical floor, which
+    # for two independent n-history runs is sqrt(1/2) of theirs
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    out["analog"] = {"seconds": st_mc.seconds, "transmissions": st_mc.transmissions,
-                     "transmissions_per_s": st_mc.transmissions / st_mc.seconds,
-                     "collisions": st_mc.collisions, "waves": st_mc.waves,
-                     "flux_rel_err_vs_analog_seed2": rel(f_mc2, f_mc)}
+    want = None if args.solve_variants is None else set(args.solve_variants.split(","))
+    f_mc = None
+    if want is None or "analog" in want:
+        n_half = n // 2
+        f_a, st_a = solve(g.GMC_METHOD_ANALOG, 1, n_hist=n_half)
+        f_b, st_b = solve(g.GMC_METHOD_ANALOG, 2, n_hist=n - n_half)
+        f_mc = 0.5 * (f_a + f_b)
+        secs = st_a.seconds + st_b.seconds
+        trans = st_a.transmissions + st_b.transmissions
+        out["analog"] = {"seconds": secs, "transmissions": trans, "transmissions_per_s": trans / secs,
+                         "collisions": st_a.collisions + st_b.collisions,
+                         "waves": st_a.waves + st_b.waves,
+                         "floor_rel_err_half_vs_half": rel(f_a, f_b),
+                         "floor_rel_err_at_n": rel(f_a, f_b) / np.sqrt(2.0)}
     names = {g.GMC_EULER: "euler", g.GMC_MIDPOINT: "midpoint", g.GMC_RK4: "rk4"}
-    for integ, steps in ((g.GMC_EULER, 16), (g.GMC_EULER, 8), (g.GMC_MIDPOINT, 8), (g.GMC_RK4, 4),
-                         (g.GMC_RK4, 12)):
-        f, st = solve(g.GMC_METHOD_GMC, 3, steps, integ)
-        out["gmc_bf16_%s%d" % (names[integ], steps)] = {
-            "seconds": st.seconds, "transmissions": st.transmissions,
-            "transmissions_per_s": st.transmissions / st.seconds, "waves": st.waves,
-            "flux_rel_err_vs_analog": rel(f, f_mc)}
+    for prec, integ, steps in ((g.GMC_BF16, g.GMC_EULER, 16), (g.GMC_BF16, g.GMC_EULER, 8),
+                               (g.GMC_BF16, g.GMC_MIDPOINT, 8), (g.GMC_BF16, g.GMC_RK4, 4),
+                               (g.GMC_BF16, g.GMC_RK4, 12), (g.GMC_FP8, g.GMC_EULER, 16),
+                               (g.GMC_FP8, g.GMC_EULER, 8), (g.GMC_FP8, g.GMC_RK4, 12)):
+        pname = "bf16" if prec == g.GMC_BF16 else "fp8"
+        key = "gmc_%s_%s%d" % (pname, names[integ], steps)
+        if want is not None and key not in want:
+            continue
+        f, st = solve(g.GMC_METHOD_GMC, 3, steps, integ, prec)
+        out[key] = {"seconds": st.seconds, "transmissions": st.transmissions,
+                    "transmissions_per_s": st.transmissions / st.seconds, "waves": st.waves,
+                    "flux_rel_err_vs_analog": None if f_mc is None else rel(f, f_mc)}
     line = {"metric": METRIC, "workload": "transport solve 128x128, tau logU[0.1,500], c {0.5,0.999} "
             "16x16 blocks, central 8x8 source, %d histories" % n, "weights": args.weights or "kaiming seed 1 (untrained)",
             "results": out, "unit": "cell transmissions/s"}
@@ -458,10 +488,84 @@ def run_sweep(args):
     ctx.close()
 
 
+def run_heldout(args):
+    """Distributional error of the sampler at 20 held-out (tau, c) pairs:
+    tau in {0.3, 3, 30, 300, 900} x c in {0.55, 0.75, 0.9, 0.99}, 1e5 entries
+    each (xi uniform, cosine-weighted inward direction). Per output (p, cos,
+    sin, ln s): the 1-D Wasserstein distance and the mean and variance of GMC
+    with the given weights and with the untrained (Kaiming seed 1) network,
+    against the GPU implicit-capture walk (the law the network learns), and
+    the distance between two independent walks (the statistical floor)."""
+    import numpy as np
+    import torch
+    import synth
+    if not args.weights:
+        raise SystemExit("--workload heldout needs --weights (a trained GMCW file)")
+    g, ctx = _context(args)
+    args_u = argparse.Namespace(**vars(args))
+    args_u.weights = None
+    _, ctx_u = _context(args_u)
+    n = 100000
+    e = synth.cell_entries(n, 2024)
+    xi, cs, sn = (torch.from_numpy(e[k]).cuda() for k in ("xi", "cos", "sin"))
+    names = ("p", "cos", "sin", "ln_s")
+
+    def outputs(ex):
+        a = ex.cpu().numpy().astype(np.float64)
+        a[3] = np.log(a[3])
+        return a
+
+    def w1(a, b):
+        return float(np.mean(np.abs(np.sort(a) - np.sort(b))))
+
+    rows = []
+    samplers = (("gmc_rk4_12", ctx, g.GMC_RK4, 12), ("gmc_euler16", ctx, g.GMC_EULER, 16),
+                ("untrained_euler16", ctx_u, g.GMC_EULER, 16))
+    for tau in (0.3, 3.0, 30.0, 300.0, 900.0):
+        for c in (0.55, 0.75, 0.9, 0.99):
+            tt = torch.full((n,), tau, device="cuda")
+            cc = torch.full((n,), c, device="cuda")
+            st = torch.empty(n, dtype=torch.int32, device="cuda")
+            ref = []
+            for seed in (11, 12):
+                ex = torch.empty(4, n, device="cuda")
+                g.analog_transmit(ctx, n, xi, cs, sn, tt, cc, g.GMC_ABSORB_IMPLICIT, seed, 0, 1, st, ex)
+                ref.append(outputs(ex))
+            cond = torch.stack([xi, cs, sn, torch.log(tt), cc])
+            row = {"tau": tau, "c": c}
+            row["floor_w1"] = [w1(ref[1][k], ref[0][k]) for k in range(4)]
+            row["analog_mean"] = [float(ref[0][k].mean()) for k in range(4)]
+            row["analog_var"] = [float(ref[0][k].var()) for k in range(4)]
+            for name, cx, integ, steps in samplers:
+                ex = torch.empty(4, n, device="cuda")
+                g.gmc_transmit(cx, n, cond, None, 31, 0, steps, integ, g.GMC_BF16, None, ex)
+                o = outputs(ex)
+                row[name + "_w1"] = [w1(o[k], ref[0][k]) for k in range(4)]
+                row[name + "_mean"] = [float(o[k].mean()) for k in range(4)]
+                row[name + "_var"] = [float(o[k].var()) for k in range(4)]
+            rows.append(row)
+    summ = {}
+    for name, _, _, _ in samplers:
+        r = np.array([[row[name + "_w1"][k] / max(row["floor_w1"][k], 1e-12) for k in range(4)]
+                      for row in rows])
+        summ[name] = {"median_w1_over_floor": dict(zip(names, np.median(r, axis=0).tolist())),
+                      "max_w1_over_floor": dict(zip(names, r.max(axis=0).tolist()))}
+    won = sum(all(row["gmc_rk4_12_w1"][k] < row["untrained_euler16_w1"][k] for k in range(4))
+              for row in rows)
+    line = {"metric": "1-D Wasserstein distance to the implicit-capture walk at 20 held-out (tau, c) pairs",
+            "workload": "held-out evaluation, 1e5 entries per pair, outputs " + ", ".join(names),
+            "weights": args.weights, "precision": "bf16", "summary": summ,
+            "pairs_trained_beats_untrained_on_all_outputs": won, "rows": rows}
+    print(json.dumps(line))
+    ctx_u.close()
+    ctx.close()
+
+
 def run_serve(args):
     """Serving: Poisson stream of solves, grids n x n with n ~ U{16..256},
     tau logU[0.1,1000], c {0.5,0.999} blocks, histories logU[1e3,1e5];
-    p50/p99 latency and solves/s for GMC BF16 and the analog walk."""
+    p50/p99 latency and solves/s for GMC (RK4, 12 steps; BF16 and FP8) and the
+    analog walk."""
     import numpy as np
     import synth
     g, ctx = _context(args)
@@ -475,9 +579,15 @@ def run_serve(args):
         reqs.append((n, np.ascontiguousarray(tau.ravel()), np.ascontiguousarray(c.ravel()),
                      np.ascontiguousarray(src.ravel()), hist))
     out = {}
-    for name, method in (("gmc_bf16", g.GMC_METHOD_GMC), ("analog", g.GMC_METHOD_ANALOG)):
+    # GMC with the integrator that reaches the analog floor on the 128^2
+    # solve (RK4, 12 steps), in BF16 and FP8, against the analog walk
+    for name, method, prec in (("gmc_bf16_rk4_12", g.GMC_METHOD_GMC, g.GMC_BF16),
+                               ("gmc_fp8_rk4_12", g.GMC_METHOD_GMC, g.GMC_FP8),
+                               ("analog", g.GMC_METHOD_ANALOG, g.GMC_BF16)):
         cfg = g.gmc_get_config(ctx)
-        cfg.steps = 16
+        cfg.steps = 12
+        cfg.integrator = g.GMC_RK4
+        cfg.precision = prec
         cfg.bank_capacity = 1 << 20
         g.gmc_set_config(ctx, cfg)
         # capacity: the whole stream submitted at once

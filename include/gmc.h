@@ -148,7 +148,10 @@ gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes
  *          ids id0+i, event 0, tag 2.
  *  steps   ODE steps K >= 1 (h = 1/K, t_k = k h); integrator gmc_integrator.
  *  precision gmc_precision: FP32 (SIMT, FP32 throughout), BF16 (tcgen05
- *          tensor cores, BF16 operands, FP32 accumulation and state).
+ *          tensor cores, BF16 operands, FP32 accumulation and state), FP8
+ *          (as BF16, but the three 256 x 256 layers take E4M3 weights with one
+ *          FP32 scale per output channel and E4M3 inputs; the paper fixes no
+ *          precision, this is a reduced-precision variant of Eq. 8's v_theta).
  *  y_raw   [4][n] float, nullable: standardized x(1).
  *  exit    [4][n] float, nullable: decoded exit state in the canonical frame:
  *          p in [0,4) (wrapped), exit direction (ux, uy) made unit and
@@ -282,6 +285,9 @@ typedef struct gmc_train_config {
     double eps;          /* e.g. 1e-8 */
     double weight_decay; /* decoupled weight decay, e.g. 0.01 */
     uint64_t seed;       /* Philox key of the batch draws (tag 6) */
+    int precision;       /* GMC_FP32: SIMT FP32 GEMMs; GMC_BF16: tcgen05 GEMMs with BF16
+                            operands and FP32 accumulation (master weights, moments,
+                            activations and gradients stay FP32) */
 } gmc_train_config;
 
 /*

@@ -20,6 +20,13 @@ What it computes, in the paper's order:
 Matrix products use numpy's matmul in float64 (a library primitive); nothing
 is blocked, fused or reordered beyond the definitions above.
 
+The paper fixes no reduced precision. For an 8-bit path this module also
+defines the quantized network such a path evaluates (quantized_e4m3): the
+three 256 x 256 layers take E4M3 weights with one FP32 scale per output row
+(s_c = max_k |W[c,k]| / 448) and E4M3 inputs with unit scale; everything
+else stays as above, in FP64. It is the same network up to those roundings,
+so the FP64 results stay the reference for the size of the 8-bit error.
+
 Weight file ("GMCW" version 1, little-endian):
   char magic[4] = "GMCW"; u32 version; u32 n_layers = 5; u32 dims[6];
   u32 n_cond, n_state, n_emb, flags;
@@ -95,12 +102,48 @@ def standardize_cond(net, cond):
     return ((cond.T - net.cond_mean) / net.cond_std)
 
 
+def round_e4m3(a):
+    """Nearest value of the FP8 E4M3 format, ties to an even significand,
+    saturating at +-448.
+
+    E4M3 (OCP 8-bit floating point): sign, 4 exponent bits with bias 7, 3
+    significand bits, no infinities. Normal values (1 + m/8) 2^(e-7) for
+    e = 1..15 (e = 15, m = 7 is NaN, so 448 = 1.75 * 2^8 is the largest);
+    subnormal values m/8 * 2^-6. In the binade [2^E, 2^(E+1)) the spacing is
+    2^(E-3); below 2^-6 it is 2^-9.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    m = np.minimum(np.abs(a), 448.0)
+    _, ex = np.frexp(np.maximum(m, 2.0 ** -6))  # m = f 2^ex with f in [0.5, 1)
+    q = np.ldexp(1.0, ex - 1 - 3)                # spacing in m's binade
+    r = np.round(m / q) * q                       # numpy rounds halves to even
+    return np.copysign(np.minimum(r, 448.0), a)
+
+
+def quantized_e4m3(net):
+    """The network an E4M3 path evaluates (see the module note): W2..W4 rows
+    replaced by s_c round_e4m3(W[c,:] / s_c) with s_c = max_k |W[c,k]| / 448
+    (1 for an all-zero row), and the inputs of those layers rounded to E4M3.
+    """
+    W = [w.copy() for w in net.W]
+    for l in (1, 2, 3):
+        amax = np.abs(W[l]).max(axis=1)
+        sc = np.where(amax > 0, amax / 448.0, 1.0)[:, None]
+        W[l] = round_e4m3(W[l] / sc) * sc
+    q = Net(W, net.b, net.cond_mean, net.cond_std, net.y_mean, net.y_std)
+    q.e4m3_inputs = True
+    return q
+
+
 def velocity(net, cn, x, t):
     """v_theta(x, t | c): cn [B,5] standardized condition, x [B,4], t scalar or [B]."""
     B = x.shape[0]
     t = np.broadcast_to(np.asarray(t, dtype=np.float64), (B,))
     h = np.concatenate([cn, x, time_embedding(t)], axis=1)
+    e4m3 = getattr(net, "e4m3_inputs", False)
     for l in range(4):
+        if e4m3 and l >= 1:
+            h = round_e4m3(h)
         h = silu(h @ net.W[l].T + net.b[l])
     return h @ net.W[4].T + net.b[4]
 

@@ -52,7 +52,8 @@ class gmc_serve_config(ctypes.Structure):
 class gmc_train_config(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int64), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
                 ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
-                ("weight_decay", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("weight_decay", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int)]
 
 
 class GMCError(RuntimeError):

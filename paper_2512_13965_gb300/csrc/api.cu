@@ -195,6 +195,8 @@ gmc_status gmc_destroy(gmc_ctx *ctx) {
   if (ctx->d_f32) cudaFree(ctx->d_f32);
   if (ctx->d_tc) cudaFree(ctx->d_tc);
   if (ctx->d_tc_bias) cudaFree(ctx->d_tc_bias);
+  if (ctx->d_tc8) cudaFree(ctx->d_tc8);
+  if (ctx->d_tc8_scale) cudaFree(ctx->d_tc8_scale);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   delete ctx;
@@ -343,16 +345,22 @@ gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes
   ctx->f32.w5 = d; d += 4 * 256;
   ctx->f32.b5 = d;
 
-  // packed operands of the tensor-core path
-  const size_t tcb = tc_packed_bytes();
-  if (tcb > 0) {
-    std::vector<unsigned char> packed(tcb);
-    std::vector<float> bias(5 * 256, 0.0f);
+  // packed operands of the tensor-core path (BF16 and FP8 variants)
+  {
+    const size_t tcb = tc_packed_bytes(false), tcb8 = tc_packed_bytes(true);
+    std::vector<unsigned char> packed(tcb), packed8(tcb8);
+    std::vector<float> bias(5 * 256, 0.0f), scale(3 * 256, 0.0f);
     tc_pack_host(ctx->host_w, ctx->host_b, packed.data(), bias.data());
+    tc_pack_host_fp8(ctx->host_w, ctx->host_b, packed8.data(), bias.data(), scale.data());
     if (!ctx->d_tc) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_tc, tcb));
+    if (!ctx->d_tc8) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_tc8, tcb8));
     if (!ctx->d_tc_bias) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_tc_bias, 5 * 256 * sizeof(float)));
+    if (!ctx->d_tc8_scale) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_tc8_scale, 3 * 256 * sizeof(float)));
     GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_tc, packed.data(), tcb, cudaMemcpyHostToDevice));
+    GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_tc8, packed8.data(), tcb8, cudaMemcpyHostToDevice));
     GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_tc_bias, bias.data(), 5 * 256 * sizeof(float),
+                                 cudaMemcpyHostToDevice));
+    GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_tc8_scale, scale.data(), 3 * 256 * sizeof(float),
                                  cudaMemcpyHostToDevice));
     ctx->tc_bytes = tcb;
   }
@@ -386,8 +394,7 @@ gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float 
   if (integrator != GMC_EULER && integrator != GMC_MIDPOINT && integrator != GMC_RK4)
     return set_error(ctx, GMC_EINVAL, "gmc_transmit: unknown integrator");
   if (!ctx->has_weights) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_transmit: no weights loaded");
-  if (precision == GMC_FP8) return set_error(ctx, GMC_ENOTIMPL, "gmc_transmit: FP8 not built");
-  if (precision != GMC_FP32 && precision != GMC_BF16)
+  if (precision != GMC_FP32 && precision != GMC_BF16 && precision != GMC_FP8)
     return set_error(ctx, GMC_EINVAL, "gmc_transmit: unknown precision");
   cudaSetDevice(ctx->device);
   Arg a_cond, a_noise, a_y, a_exit;
@@ -404,13 +411,13 @@ gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float 
                                          (const float *)a_noise.dev, seed, id0, steps, integrator,
                                          (float *)a_y.dev, (float *)a_exit.dev));
   } else {
-    if (!ctx->d_tc) return set_error(ctx, GMC_ENOTIMPL, "gmc_transmit: BF16 path not built");
+    const bool fp8 = precision == GMC_FP8;
     GMC_CUDA_TRY(ctx, ensure(ctx->bias1, (size_t)4 * steps * 256 * sizeof(float)));
-    cudaError_t e = launch_sampler_tc(ctx->stream, ctx->d_tc, ctx->d_tc_bias, ctx->f32, ctx->stats,
-                                      n, (const float *)a_cond.dev, (const float *)a_noise.dev,
-                                      seed, id0, steps, integrator, (float *)a_y.dev,
-                                      (float *)a_exit.dev, ctx->d_err, (float *)ctx->bias1.ptr);
-    if (e == cudaErrorNotSupported) return set_error(ctx, GMC_ENOTIMPL, "gmc_transmit: BF16 path not built");
+    cudaError_t e = launch_sampler_tc(ctx->stream, fp8 ? ctx->d_tc8 : ctx->d_tc, ctx->d_tc_bias,
+                                      ctx->f32, ctx->stats, n, (const float *)a_cond.dev,
+                                      (const float *)a_noise.dev, seed, id0, steps, integrator,
+                                      (float *)a_y.dev, (float *)a_exit.dev, ctx->d_err,
+                                      (float *)ctx->bias1.ptr, fp8 ? ctx->d_tc8_scale : nullptr);
     if (e != cudaSuccess) return cuda_error(ctx, e, "launch_sampler_tc");
   }
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, a_y));

@@ -64,6 +64,8 @@ struct gmc_ctx {
   void *d_tc = nullptr;  // packed BF16 operands
   size_t tc_bytes = 0;
   float *d_tc_bias = nullptr;  // per-layer biases for the tensor-core path
+  void *d_tc8 = nullptr;       // packed operands of the FP8 variant (E4M3 W2..W4)
+  float *d_tc8_scale = nullptr;  // [3][256] per-output-channel scales of W2..W4, halved
   int *d_err = nullptr;        // device error word (bounded waits)
 
   // training state (gmc_train_begin .. gmc_destroy)
@@ -108,14 +110,30 @@ cudaError_t launch_analog(cudaStream_t stream, int64_t n, const float *xi, const
                           uint64_t seed, uint64_t id0, uint32_t event0, int32_t *status,
                           float *exit, uint32_t *ncoll);
 
-// Tensor-core sampler (sampler_tc.cu).
-size_t tc_packed_bytes();
+// BF16 tensor-core GEMM of the training step (train_tc.cu):
+// C[m][n] = epi(sum_k A[m sam + k sak] B[n sbn + k sbk]), FP32 in and out,
+// N <= 256. With splits > 1 (kTgStore only) the K range is cut into slices
+// written to `ws` (splits x M x N floats at most ws_floats) and summed into C
+// in slice order.
+enum { kTgStore = 0, kTgBiasSilu = 1, kTgBias = 2, kTgDSilu = 3 };
+cudaError_t tgemm(cudaStream_t st, int epi, int M, int N, int K, const float *A, int64_t sam,
+                  int64_t sak, const float *B, int64_t sbn, int64_t sbk, float *C,
+                  const float *bias, float *C2, const float *Zp, int splits, float *ws,
+                  size_t ws_floats, int *err);
+
+// Tensor-core sampler (sampler_tc.cu). The BF16 and FP8 variants share the
+// bias vector ([5][256]); the FP8 one also takes per-channel weight scales.
+size_t tc_packed_bytes(bool fp8);
 void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
                   float *bias_host);
+void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
+                      float *bias_host, float *scale_host);
+// packed: from tc_pack_host (fp8_scale null) or tc_pack_host_fp8 (fp8_scale =
+// its [3][256] scales on the device).
 cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const float *bias,
                               const NetF32 &f32, const NetStats &st, int64_t n, const float *cond,
                               const float *noise, uint64_t seed, uint64_t id0, int steps,
                               int integrator, float *y_raw, float *exit, int *err,
-                              float *bias1_scratch);
+                              float *bias1_scratch, const float *fp8_scale);
 
 }  // namespace gmc

@@ -90,7 +90,8 @@ extern "C" gmc_status gmc_transmit_noalloc(gmc_ctx *ctx, int64_t n, const float 
   gmc_status st = scratch_address(ctx, &scratch);
   if (st != GMC_OK) return st;
   e = launch_sampler_tc(ctx->stream, ctx->d_tc, ctx->d_tc_bias, ctx->f32, ctx->stats, n, cond,
-                        noise, seed, id0, steps, integrator, y_raw, exit, ctx->d_err, scratch);
+                        noise, seed, id0, steps, integrator, y_raw, exit, ctx->d_err, scratch,
+                        nullptr);
   if (e != cudaSuccess) return cuda_error(ctx, e, "gmc_transmit_noalloc launch");
   return GMC_OK;
 }

@@ -30,7 +30,20 @@
 // into both CTAs' stage, so L2 serves each chunk once per pair; a stage is
 // refilled only after both CTAs' MMAs have released it.
 // Every wait is bounded; a timeout sets *err and the CTA drains and exits.
+//
+// FP8 variant (template argument FP8): the three 256 x 256 layers (97% of the
+// FLOPs) run as kind::f8f6f4 MMAs on E4M3 operands. Each output row c of
+// W2..W4 is stored as E4M3 codes of W[c][:] / s_c with s_c = max_k |W[c][k]| / 448
+// (per-output-channel scale, FP32), and the epilogue applies h = acc s_c / 2
+// + b_c / 2 in one FMA. Activations entering layers 2-4 are E4M3 with unit
+// scale (SiLU outputs are >= -0.279 and far below E4M3's 448). Layer 1 keeps
+// BF16 operands (the ODE state enters through them) and layer 4's epilogue
+// writes BF16, so layer 5 (the velocity) is the same BF16 MMA as above.
+// A 16 KB weight chunk then holds 64 inputs instead of 32; byte offsets in
+// the operand rows are the same, so descriptors advance identically.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <cstring>
 
@@ -55,7 +68,6 @@ constexpr int TM = 128;
 // swizzle (16 KB), 64 -> 128-byte swizzle (32 KB).
 constexpr int CHUNK_K = GMC_TC_CHUNK_K;
 constexpr uint32_t CHUNK = 256u * CHUNK_K * 2u;
-constexpr int CHUNKS = 256 / CHUNK_K;             // per hidden layer
 constexpr int MMAS_PER_CHUNK = CHUNK_K / 16;
 constexpr uint32_t CHUNK_SWIZZLE = CHUNK_K == 32 ? 4u /* 64B */ : 2u /* 128B */;
 constexpr uint32_t CHUNK_SBO = CHUNK_K == 32 ? 512u : 1024u;
@@ -69,12 +81,18 @@ static_assert(EPI_WARPS == 8 || EPI_WARPS == 16, "epilogue warps");
 constexpr int CLUSTER = 2;               // CTAs sharing each weight chunk by multicast
 constexpr uint32_t SLICE = CHUNK / CLUSTER;
 constexpr uint32_t TMEM_COLS = 512;     // two 128 x 256 FP32 accumulators
+constexpr int ROW_BYTES = CHUNK_K * 2;  // bytes of one output row in a weight chunk
 
-// packed global operand buffer (bytes)
-constexpr size_t OFF_HID = 0;                    // [layer 0..2][chunk 0..7] x 16 KB
-constexpr size_t OFF_B1 = 3 * CHUNKS * CHUNK;    // 256 rows x 32 B, 32-byte swizzle
-constexpr size_t OFF_B5 = OFF_B1 + 8192;         // 4 K-blocks x 16 rows x 128 B
-constexpr size_t PACKED = OFF_B5 + 8192;
+// packed global operand buffer (bytes): hidden-layer chunks, then the BF16
+// operands of layers 1 and 5
+template <bool FP8>
+struct Packed {
+  static constexpr int NCH = 256 * (FP8 ? 1 : 2) / ROW_BYTES;  // chunks per hidden layer
+  static constexpr size_t OFF_HID = 0;                  // [layer 0..2][chunk] x CHUNK
+  static constexpr size_t OFF_B1 = 3 * (size_t)NCH * CHUNK;  // 256 rows x 32 B, 32-byte swizzle
+  static constexpr size_t OFF_B5 = OFF_B1 + 8192;      // 4 K-blocks x 16 rows x 128 B
+  static constexpr size_t BYTES = OFF_B5 + 8192;
+};
 
 // shared memory (offsets from a 1024-byte aligned base)
 constexpr uint32_t S_A0 = 0;                     // tile X operand, 64 KB
@@ -115,6 +133,21 @@ __device__ __forceinline__ uint32_t silu2_halved(float h0, float h1) {
   asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
   asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(o) : "r"(h), "r"(t));
   return o;
+}
+
+// As silu2_halved, rounded to two E4M3 codes (low byte from h0): the SiLU in
+// packed FP16 (11-bit significand, so the E4M3 rounding sees an accurate
+// value), then one saturating conversion.
+__device__ __forceinline__ uint32_t silu2_halved_e4m3(float h0, float h1) {
+  const __half2 hh = __floats2half2_rn(h0, h1);
+  uint32_t h, t, o;
+  memcpy(&h, &hh, 4);
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
+  asm("fma.rn.f16x2 %0, %1, %2, %1;" : "=r"(o) : "r"(h), "r"(t));
+  __half2_raw raw;
+  raw.x = (unsigned short)(o & 0xFFFFu);
+  raw.y = (unsigned short)(o >> 16);
+  return (uint32_t)__nv_cvt_halfraw2_to_fp8x2(raw, __NV_SATFINITE, __NV_E4M3);
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
@@ -186,22 +219,79 @@ __device__ __forceinline__ void write_a1(uint32_t a_base, int r, const float (&c
                pack_bf16x2(lo[3], 0.0f), pack_bf16x2(0.0f, 0.0f));
 }
 
-// bias + SiLU on 32 accumulator columns starting at col0, stored as four
-// 16-byte chunks of the next layer's operand row r.
+// Halved pre-activations of 4 accumulator columns: acc + bias, or with
+// SCALED (an FP8 layer) acc * scale + bias.
+template <bool SCALED>
+__device__ __forceinline__ float4 pre4(const uint32_t *p, const float4 *b4, const float4 *s4, int q) {
+  const float4 b = __ldg(b4 + q);
+  float4 z;
+  if constexpr (SCALED) {
+    const float4 sc = __ldg(s4 + q);
+    z.x = fmaf(__uint_as_float(p[0]), sc.x, b.x);
+    z.y = fmaf(__uint_as_float(p[1]), sc.y, b.y);
+    z.z = fmaf(__uint_as_float(p[2]), sc.z, b.z);
+    z.w = fmaf(__uint_as_float(p[3]), sc.w, b.w);
+  } else {
+    z.x = __uint_as_float(p[0]) + b.x;
+    z.y = __uint_as_float(p[1]) + b.y;
+    z.z = __uint_as_float(p[2]) + b.z;
+    z.w = __uint_as_float(p[3]) + b.w;
+  }
+  return z;
+}
+
+// bias (and scale) + SiLU on 32 accumulator columns starting at col0,
+// stored into the next layer's operand row r: BF16 (four 16-byte chunks of
+// a 64-column K-block) or, with OUT8, E4M3 (two 16-byte chunks of a
+// 128-column K-block). Both K-blocks have 128-byte rows, 128-byte swizzle.
+template <bool SCALED, bool OUT8>
 __device__ __forceinline__ void epi32(const uint32_t (&v)[32], const float *__restrict__ bias,
-                                      int col0, uint32_t a_base, int r) {
+                                      const float *__restrict__ scale, int col0, uint32_t a_base,
+                                      int r) {
   const float4 *b4 = reinterpret_cast<const float4 *>(bias + col0);
-  const uint32_t kb_base = a_base + (uint32_t)(col0 >> 6) * 16384u;
-  const int c0 = (col0 & 63) >> 3;
+  const float4 *s4 = SCALED ? reinterpret_cast<const float4 *>(scale + col0) : nullptr;
+  if constexpr (OUT8) {
+    const uint32_t kb_base = a_base + (uint32_t)(col0 >> 7) * 16384u;
+    const int c0 = (col0 & 127) >> 4;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float4 ba = __ldg(b4 + 2 * j), bb = __ldg(b4 + 2 * j + 1);
-    const uint32_t *p = v + 8 * j;
-    st_shared_v4(sw128(kb_base, r, c0 + j),
-                 silu2_halved(__uint_as_float(p[0]) + ba.x, __uint_as_float(p[1]) + ba.y),
-                 silu2_halved(__uint_as_float(p[2]) + ba.z, __uint_as_float(p[3]) + ba.w),
-                 silu2_halved(__uint_as_float(p[4]) + bb.x, __uint_as_float(p[5]) + bb.y),
-                 silu2_halved(__uint_as_float(p[6]) + bb.z, __uint_as_float(p[7]) + bb.w));
+    for (int j = 0; j < 2; ++j) {
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int q = 4 * j + i;
+        const float4 z = pre4<SCALED>(v + 4 * q, b4, s4, q);
+        w[i] = silu2_halved_e4m3(z.x, z.y) | (silu2_halved_e4m3(z.z, z.w) << 16);
+      }
+      st_shared_v4(sw128(kb_base, r, c0 + j), w[0], w[1], w[2], w[3]);
+    }
+  } else {
+    const uint32_t kb_base = a_base + (uint32_t)(col0 >> 6) * 16384u;
+    const int c0 = (col0 & 63) >> 3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 za = pre4<SCALED>(v + 8 * j, b4, s4, 2 * j);
+      const float4 zb = pre4<SCALED>(v + 8 * j + 4, b4, s4, 2 * j + 1);
+      st_shared_v4(sw128(kb_base, r, c0 + j), silu2_halved(za.x, za.y), silu2_halved(za.z, za.w),
+                   silu2_halved(zb.x, zb.y), silu2_halved(zb.z, zb.w));
+    }
+  }
+}
+
+// One epilogue thread's EPI_COLS columns of a 128 x 256 accumulator: the
+// load of the next 32 columns is in flight while the current ones are
+// converted and stored.
+template <bool SCALED, bool OUT8>
+__device__ __forceinline__ void epi_layer(uint32_t tcol, const float *__restrict__ bias,
+                                          const float *__restrict__ scale, int col0,
+                                          uint32_t a_base, int r) {
+  uint32_t buf[2][32];
+  tmem_ld32_raw(tcol, buf[0]);
+  tmem_wait_ld_regs(buf[0]);
+#pragma unroll
+  for (int j = 0; j < EPI_CH; ++j) {
+    if (j + 1 < EPI_CH) tmem_ld32_raw(tcol + 32u * (uint32_t)(j + 1), buf[(j + 1) & 1]);
+    epi32<SCALED, OUT8>(buf[j & 1], bias, scale, col0 + 32 * j, a_base, r);
+    if (j + 1 < EPI_CH) tmem_wait_ld_regs(buf[(j + 1) & 1]);
   }
 }
 
@@ -209,6 +299,7 @@ struct Params {
   const unsigned char *packed;
   const float *bias;    // [5][256]: rows 1..3 = b2..b4, row 4 = b5
   const float *bias1;   // [n_eval][256]: W1[:, emb] emb(t_e) + b1
+  const float *scale;   // FP8 only: [3][256] per-output-channel scales of W2..W4, halved
   NetStats st;
   int64_t n;
   const float *cond;
@@ -219,7 +310,10 @@ struct Params {
   int *err;
 };
 
+template <bool FP8>
 __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
+  using PK = Packed<FP8>;
+  constexpr int NCH = PK::NCH;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (raw_addr & 1023u)) & 1023u;
@@ -268,13 +362,13 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
       uint32_t it = 0;
       bool ok = true;
       mbar_arrive_expect_tx(&B.res_full, 16384);
-      bulk_g2s(sm + S_B1, P.packed + OFF_B1, 8192, &B.res_full);
-      bulk_g2s(sm + S_B5, P.packed + OFF_B5, 8192, &B.res_full);
+      bulk_g2s(sm + S_B1, P.packed + PK::OFF_B1, 8192, &B.res_full);
+      bulk_g2s(sm + S_B5, P.packed + PK::OFF_B5, 8192, &B.res_full);
       for (int64_t ip = 0; ip < n_iter && ok; ++ip)
         for (int e = 0; e < P.n_eval && ok; ++e)
           for (int L = 0; L < 3 && ok; ++L)
             for (int T = 0; T < 2 && ok; ++T)
-              for (int ch = 0; ch < CHUNKS; ++ch) {
+              for (int ch = 0; ch < NCH; ++ch) {
                 const int s = it % NST;
                 const uint32_t round = it / NST;
                 if (!mbar_wait(&B.empty[s], (round & 1u) ^ 1u, abort)) {
@@ -284,7 +378,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
                 }
                 mbar_arrive_expect_tx(&B.full[s], CHUNK);
                 bulk_g2s_multicast(sm + S_ST + s * CHUNK + rank * SLICE,
-                                   P.packed + OFF_HID + (size_t)(L * CHUNKS + ch) * CHUNK + rank * SLICE,
+                                   P.packed + PK::OFF_HID + (size_t)(L * NCH + ch) * CHUNK + rank * SLICE,
                                    SLICE, &B.full[s], all_ctas);
                 ++it;
               }
@@ -308,6 +402,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
       uint32_t aph[2] = {0, 0};
       uint32_t stage = 0, sph = 0;  // next weight stage and its phase parity
       const uint32_t id256 = idesc_bf16_m128(256), id16 = idesc_bf16_m128(16);
+      const uint32_t idh = FP8 ? idesc_e4m3_m128(256) : id256;  // hidden layers
       const uint64_t dA[2] = {smem_desc(sbase + S_A0, 1024, kSwizzle128B),
                               smem_desc(sbase + S_A1, 1024, kSwizzle128B)};
       const uint64_t dA1[2] = {smem_desc(sbase + S_A0, 256, kSwizzle32B),
@@ -333,22 +428,29 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
               } else if (L < 4) {
                 const uint64_t a0 = dA[T];
 #pragma unroll
-                for (int ch = 0; ch < CHUNKS; ++ch) {
+                for (int ch = 0; ch < NCH; ++ch) {
                   if (!mbar_try_wait(&B.full[stage], sph) && !mbar_wait(&B.full[stage], sph, abort)) {
                     fail(B, P.err, 4);
                     ok = false;
                     break;
                   }
                   tc_fence_after();
-                  // chunk ch = K columns CHUNK_K ch .. of all 256 output rows: A at
-                  // K-block (CHUNK_K ch)/64, byte 2 (CHUNK_K ch % 64) of its rows
-                  const int k0 = ch * CHUNK_K;
-                  const uint64_t a_ch = a0 + (uint64_t)((k0 >> 6) * 1024 + ((k0 & 63) >> 3));
+                  // chunk ch = operand bytes ROW_BYTES ch .. of all 256 output
+                  // rows (CHUNK_K BF16 or 2 CHUNK_K E4M3 inputs): A at K-block
+                  // (ROW_BYTES ch)/128, byte (ROW_BYTES ch) % 128 of its rows;
+                  // each MMA takes 32 bytes of K
+                  const int kb = ch * ROW_BYTES;
+                  const uint64_t a_ch = a0 + (uint64_t)((kb >> 7) * 1024 + ((kb & 127) >> 4));
                   const uint64_t b_ch = dST + (uint64_t)(stage * (CHUNK >> 4));
 #pragma unroll
-                  for (int k = 0; k < MMAS_PER_CHUNK; ++k)
-                    mma_f16(d, a_ch + (uint64_t)(2 * k), b_ch + (uint64_t)(2 * k), id256,
-                            (ch | k) != 0);
+                  for (int k = 0; k < MMAS_PER_CHUNK; ++k) {
+                    if constexpr (FP8)
+                      mma_f8(d, a_ch + (uint64_t)(2 * k), b_ch + (uint64_t)(2 * k), idh,
+                             (ch | k) != 0);
+                    else
+                      mma_f16(d, a_ch + (uint64_t)(2 * k), b_ch + (uint64_t)(2 * k), idh,
+                              (ch | k) != 0);
+                  }
                   mma_commit_multicast(&B.empty[stage], all_ctas);
                   if (++stage == NST) {
                     stage = 0;
@@ -421,16 +523,18 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
             const float *bias = L == 0 ? P.bias1 + (size_t)e * 256 : P.bias + L * 256;
             const uint32_t a_base = sbase + (T ? S_A1 : S_A0);
             const uint32_t tcol = tmem + lane_off + (uint32_t)T * 256u + (uint32_t)(hf * EPI_COLS);
-            // the load of the next 32 columns is in flight while the current
-            // ones are converted and stored
-            uint32_t buf[2][32];
-            tmem_ld32_raw(tcol, buf[0]);
-            tmem_wait_ld_regs(buf[0]);
-#pragma unroll
-            for (int j = 0; j < EPI_CH; ++j) {
-              if (j + 1 < EPI_CH) tmem_ld32_raw(tcol + 32u * (uint32_t)(j + 1), buf[(j + 1) & 1]);
-              epi32(buf[j & 1], bias, hf * EPI_COLS + 32 * j, a_base, r);
-              if (j + 1 < EPI_CH) tmem_wait_ld_regs(buf[(j + 1) & 1]);
+            const int col0 = hf * EPI_COLS;
+            if constexpr (FP8) {
+              // layer 1 (BF16 MMA) and layers 2-3 feed E4M3 operands; layer 4
+              // feeds the BF16 operand of layer 5
+              if (L == 0)
+                epi_layer<false, true>(tcol, bias, nullptr, col0, a_base, r);
+              else if (L < 3)
+                epi_layer<true, true>(tcol, bias, P.scale + (L - 1) * 256, col0, a_base, r);
+              else
+                epi_layer<true, false>(tcol, bias, P.scale + 2 * 256, col0, a_base, r);
+            } else {
+              epi_layer<false, false>(tcol, bias, nullptr, col0, a_base, r);
             }
             fence_proxy_async_smem();
             tc_fence_before();
@@ -551,95 +655,126 @@ size_t sw128_off(int row, int k) {
   return (size_t)((row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4) + e * 2);
 }
 
-// element (row, k) of a 64-byte-swizzled K-major block whose rows are 64 B
-size_t sw64_off(int row, int k) {
-  const int c = k >> 3, e = k & 7;
-  return (size_t)((row >> 3) * 512 + (row & 7) * 64 + ((c ^ ((row >> 1) & 3)) << 4) + e * 2);
-}
-
 size_t sw32_off(int row, int k) {
   const int c = k >> 3, e = k & 7;
   return (size_t)((row >> 3) * 256 + (row & 7) * 32 + ((c ^ ((row >> 2) & 1)) << 4) + e * 2);
 }
 
-}  // namespace
+// byte b of row `row` in a weight chunk (ROW_BYTES-byte rows: 64-byte swizzle
+// for 64, 128-byte swizzle for 128)
+size_t chunk_byte_off(int row, int b) {
+  const int c = b >> 4, e = b & 15;
+  if (ROW_BYTES == 64)
+    return (size_t)((row >> 3) * 512 + (row & 7) * 64 + ((c ^ ((row >> 1) & 3)) << 4) + e);
+  return (size_t)((row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4) + e);
+}
 
-size_t tc_packed_bytes() { return PACKED; }
+// Value of the E4M3 code k (0..126, sign clear): subnormal k/8 2^-6 for an
+// exponent field of 0, else (1 + m/8) 2^(e-7); 126 is the largest, 448.
+double e4m3_value(int k) {
+  const int e = k >> 3, m = k & 7;
+  return e == 0 ? std::ldexp(m / 8.0, -6) : std::ldexp(1.0 + m / 8.0, e - 7);
+}
 
-void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
-                  float *bias_host) {
-  unsigned char *P = (unsigned char *)packed_host;
-  std::memset(P, 0, PACKED);
+// Round to the nearest E4M3 value, ties to the even code, saturating at 448.
+uint8_t e4m3_bits(double x) {
+  const uint8_t sign = std::signbit(x) ? 0x80 : 0x00;
+  const double a = std::fabs(x);
+  if (!(a < 448.0)) return (uint8_t)(sign | 126);
+  int lo = 0, hi = 126;  // e4m3_value(lo) <= a < e4m3_value(hi)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (e4m3_value(mid) <= a) lo = mid;
+    else hi = mid;
+  }
+  const double dl = a - e4m3_value(lo), dh = e4m3_value(hi) - a;
+  const int k = dl < dh ? lo : (dh < dl ? hi : ((lo & 1) ? hi : lo));
+  return (uint8_t)(sign | k);
+}
+
+// Layers 1 and 5 (BF16 in both variants) and the per-layer bias vectors.
+void pack_b1_b5_bias(const float (*W)[256 * 256], const float (*b)[256], unsigned char *P,
+                     size_t off_b1, size_t off_b5, float *bias_host) {
   auto put = [&](size_t off, float v) {
     const uint16_t u = bf16_bits(v);
     std::memcpy(P + off, &u, 2);
   };
-  // hidden layers W2..W4: chunk ch holds all 256 output rows and K CHUNK_K ch ..
-  for (int L = 0; L < 3; ++L)
-    for (int ch = 0; ch < CHUNKS; ++ch) {
-      const size_t base = OFF_HID + (size_t)(L * CHUNKS + ch) * CHUNK;
-      for (int i = 0; i < 256; ++i)
-        for (int j = 0; j < CHUNK_K; ++j)
-          put(base + (CHUNK_K == 32 ? sw64_off(i, j) : sw128_off(i, j)),
-              0.5f * W[L + 1][i * 256 + ch * CHUNK_K + j]);
-    }
   // layer 1: [cond (5), x (4) for x_hi, x (4) again for x_lo, 0 0 0]
   for (int nrow = 0; nrow < 256; ++nrow) {
     const float *w = &W[0][nrow * 25];
-    for (int k = 0; k < 5; ++k) put(OFF_B1 + sw32_off(nrow, k), 0.5f * w[k]);
+    for (int k = 0; k < 5; ++k) put(off_b1 + sw32_off(nrow, k), 0.5f * w[k]);
     for (int k = 0; k < 4; ++k) {
-      put(OFF_B1 + sw32_off(nrow, 5 + k), 0.5f * w[5 + k]);
-      put(OFF_B1 + sw32_off(nrow, 9 + k), 0.5f * w[5 + k]);
+      put(off_b1 + sw32_off(nrow, 5 + k), 0.5f * w[5 + k]);
+      put(off_b1 + sw32_off(nrow, 9 + k), 0.5f * w[5 + k]);
     }
   }
   // output layer: 16 rows (4 real) x 256 K in four 128-byte-swizzled K-blocks
   for (int d = 0; d < 4; ++d)
     for (int k = 0; k < 256; ++k)
-      put(OFF_B5 + (size_t)(k >> 6) * 2048 + sw128_off(d, k & 63), W[4][d * 256 + k]);
+      put(off_b5 + (size_t)(k >> 6) * 2048 + sw128_off(d, k & 63), W[4][d * 256 + k]);
   for (int i = 0; i < 5 * 256; ++i) bias_host[i] = 0.0f;
   for (int L = 1; L < 4; ++L)
     for (int c = 0; c < 256; ++c) bias_host[L * 256 + c] = 0.5f * b[L][c];
   for (int d = 0; d < 4; ++d) bias_host[4 * 256 + d] = b[4][d];
 }
 
-cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const float *bias,
-                              const NetF32 &f32, const NetStats &st, int64_t n, const float *cond,
-                              const float *noise, uint64_t seed, uint64_t id0, int steps,
-                              int integrator, float *y_raw, float *exit, int *err,
-                              float *bias1_scratch) {
-  if (n <= 0) return cudaSuccess;
-  const int n_eval = integrator == GMC_RK4 ? 4 * steps : (integrator == GMC_MIDPOINT ? 2 * steps : steps);
-  layer1_bias_kernel<<<n_eval, kHidden, 0, stream>>>(f32.w1t, f32.b1, steps, integrator, n_eval,
-                                                     bias1_scratch);
-  cudaError_t e = cudaGetLastError();
+}  // namespace
+
+size_t tc_packed_bytes(bool fp8) { return fp8 ? Packed<true>::BYTES : Packed<false>::BYTES; }
+
+void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
+                  float *bias_host) {
+  using PK = Packed<false>;
+  unsigned char *P = (unsigned char *)packed_host;
+  std::memset(P, 0, PK::BYTES);
+  // hidden layers W2..W4: chunk ch holds all 256 output rows and K CHUNK_K ch ..
+  for (int L = 0; L < 3; ++L)
+    for (int ch = 0; ch < PK::NCH; ++ch) {
+      const size_t base = PK::OFF_HID + (size_t)(L * PK::NCH + ch) * CHUNK;
+      for (int i = 0; i < 256; ++i)
+        for (int j = 0; j < CHUNK_K; ++j) {
+          const uint16_t u = bf16_bits(0.5f * W[L + 1][i * 256 + ch * CHUNK_K + j]);
+          std::memcpy(P + base + chunk_byte_off(i, 2 * j), &u, 2);
+        }
+    }
+  pack_b1_b5_bias(W, b, P, PK::OFF_B1, PK::OFF_B5, bias_host);
+}
+
+void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
+                      float *bias_host, float *scale_host) {
+  using PK = Packed<true>;
+  unsigned char *P = (unsigned char *)packed_host;
+  std::memset(P, 0, PK::BYTES);
+  // hidden layers W2..W4: row c as E4M3 codes of W[c][:] / s_c, s_c = amax / 448;
+  // chunk ch holds all 256 output rows and K ROW_BYTES ch ..
+  for (int L = 0; L < 3; ++L)
+    for (int i = 0; i < 256; ++i) {
+      const float *w = &W[L + 1][i * 256];
+      double amax = 0.0;
+      for (int k = 0; k < 256; ++k) amax = std::fmax(amax, std::fabs((double)w[k]));
+      const double sc = amax > 0.0 ? amax / 448.0 : 1.0;
+      scale_host[L * 256 + i] = (float)(0.5 * sc);  // layers 2-4 carry a factor 1/2
+      for (int k = 0; k < 256; ++k) {
+        const int ch = k / ROW_BYTES, j = k % ROW_BYTES;
+        P[PK::OFF_HID + (size_t)(L * PK::NCH + ch) * CHUNK + chunk_byte_off(i, j)] =
+            e4m3_bits((double)w[k] / sc);
+      }
+    }
+  pack_b1_b5_bias(W, b, P, PK::OFF_B1, PK::OFF_B5, bias_host);
+}
+
+namespace {
+template <bool FP8>
+cudaError_t launch_tc(cudaStream_t stream, const Params &p, int sms) {
+  auto kernel = sampler_tc_kernel<FP8>;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(sampler_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SMEM_BYTES);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t ntiles = (n + TM - 1) / TM, npairs = (ntiles + 1) / 2;
+  const int64_t ntiles = (p.n + TM - 1) / TM, npairs = (ntiles + 1) / 2;
   int64_t g = npairs < sms ? npairs : sms;
   g = (g + CLUSTER - 1) / CLUSTER * CLUSTER;
   if (g > sms / CLUSTER * CLUSTER) g = sms / CLUSTER * CLUSTER;
   const int grid = (int)g;
-  Params p;
-  p.packed = (const unsigned char *)packed;
-  p.bias = bias;
-  p.bias1 = bias1_scratch;
-  p.st = st;
-  p.n = n;
-  p.cond = cond;
-  p.noise = noise;
-  p.seed = seed;
-  p.id0 = id0;
-  p.steps = steps;
-  p.integrator = integrator;
-  p.n_eval = n_eval;
-  p.y_raw = y_raw;
-  p.exitp = exit;
-  p.err = err;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -656,7 +791,7 @@ cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const flo
   if (max_clusters < 0) {
     lc.gridDim = dim3((unsigned)(sms / CLUSTER * CLUSTER));
     int mc = 0;
-    if (cudaOccupancyMaxActiveClusters(&mc, sampler_tc_kernel, &lc) != cudaSuccess || mc < 1) {
+    if (cudaOccupancyMaxActiveClusters(&mc, kernel, &lc) != cudaSuccess || mc < 1) {
       cudaGetLastError();
       mc = sms / CLUSTER;
     }
@@ -664,9 +799,44 @@ cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const flo
   }
   const int grid_fit = grid < max_clusters * CLUSTER ? grid : max_clusters * CLUSTER;
   lc.gridDim = dim3((unsigned)grid_fit);
-  e = cudaLaunchKernelEx(&lc, sampler_tc_kernel, p);
+  e = cudaLaunchKernelEx(&lc, kernel, p);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const float *bias,
+                              const NetF32 &f32, const NetStats &st, int64_t n, const float *cond,
+                              const float *noise, uint64_t seed, uint64_t id0, int steps,
+                              int integrator, float *y_raw, float *exit, int *err,
+                              float *bias1_scratch, const float *fp8_scale) {
+  if (n <= 0) return cudaSuccess;
+  const int n_eval = integrator == GMC_RK4 ? 4 * steps : (integrator == GMC_MIDPOINT ? 2 * steps : steps);
+  layer1_bias_kernel<<<n_eval, kHidden, 0, stream>>>(f32.w1t, f32.b1, steps, integrator, n_eval,
+                                                     bias1_scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  Params p;
+  p.packed = (const unsigned char *)packed;
+  p.bias = bias;
+  p.bias1 = bias1_scratch;
+  p.scale = fp8_scale;
+  p.st = st;
+  p.n = n;
+  p.cond = cond;
+  p.noise = noise;
+  p.seed = seed;
+  p.id0 = id0;
+  p.steps = steps;
+  p.integrator = integrator;
+  p.n_eval = n_eval;
+  p.y_raw = y_raw;
+  p.exitp = exit;
+  p.err = err;
+  return fp8_scale ? launch_tc<true>(stream, p, sms) : launch_tc<false>(stream, p, sms);
 }
 
 }  // namespace gmc

@@ -117,6 +117,18 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64
 
 // Arrive on `bar` once every tcgen05 operation issued so far by this thread
 // has completed.
+// Same as mma_f16 for 8-bit operands (kind::f8f6f4; the operand types come
+// from the instruction descriptor): D (+)= A B with A and B E4M3, D FP32.
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                      uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -188,6 +200,14 @@ __device__ __forceinline__ void tmem_wait_ld_regs4(float (&v)[4]) {
 }
 
 // Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, M = 128.
+// kind::f8f6f4 instruction descriptor: A and B E4M3 (type code 0), D FP32.
+__host__ __device__ constexpr uint32_t idesc_e4m3_m128(uint32_t n) {
+  return (1u << 4)            // D format: F32
+         | (0u << 7)          // A format: E4M3
+         | (0u << 10)         // B format: E4M3
+         | ((n >> 3) << 17)   // N / 8
+         | ((128u >> 4) << 24);  // M / 16
+}
 __host__ __device__ constexpr uint32_t idesc_bf16_m128(uint32_t n) {
   return (1u << 4)            // D format: F32
          | (1u << 7)          // A format: BF16

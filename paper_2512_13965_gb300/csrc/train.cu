@@ -13,8 +13,10 @@
 //                   pre-activations; loss = mean_b ||v - (x1 - x0)||^2;
 //                   hand-derived backward; AdamW (decoupled weight decay).
 //
-// The dense layers run on a tiled FP32 SIMT GEMM with fused epilogues
-// (bias + SiLU forward, SiLU' backward), accumulating in FP32.
+// The dense layers run either on tcgen05 tensor cores with BF16 operands
+// (train_tc.cu; the default of the command-line trainer) or on a tiled FP32
+// SIMT GEMM, both with fused epilogues (bias + SiLU forward, SiLU' backward)
+// and FP32 accumulation; master weights and AdamW moments are FP32 in both.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -50,6 +52,9 @@ struct TrainState {
   double *loss = nullptr;  // [max steps per call]
   int64_t loss_cap = 0;
   double *stat_acc = nullptr;  // 18 sums
+  float *ws = nullptr;         // split-K slices of the weight-gradient GEMMs (tensor-core path)
+  size_t ws_floats = 0;
+  int *err = nullptr;          // device error word of the context
 };
 
 namespace {
@@ -315,6 +320,62 @@ cudaError_t fwd_bwd(cudaStream_t s, TrainState &T, double *loss_slot) {
   return cudaGetLastError();
 }
 
+// The same step with the GEMMs on tensor cores (BF16 operands, FP32
+// accumulation). Weight gradients reduce over the batch in `splits` slices of
+// at least 256 rows, summed in a fixed order.
+cudaError_t fwd_bwd_tc(cudaStream_t s, TrainState &T, double *loss_slot) {
+  const int B = (int)T.B;
+  float *P = T.params, *G = T.grads;
+  const float *W[4] = {P + P_W1, P + P_W2, P + P_W3, P + P_W4};
+  const float *bb[4] = {P + P_B1, P + P_B2, P + P_B3, P + P_B4};
+  int splits = B / 256;
+  splits = splits < 1 ? 1 : (splits > 32 ? 32 : splits);
+  cudaError_t e;
+#define TG_TRY(...)                \
+  do {                             \
+    e = tgemm(__VA_ARGS__);        \
+    if (e != cudaSuccess) return e; \
+  } while (0)
+  // forward: Z_l = A_{l-1} W_l^T + b_l, A_l = SiLU(Z_l); B(n,k) = W_l[n][k]
+  TG_TRY(s, kTgBiasSilu, B, 256, 32, T.X0, 32, 1, W[0], 32, 1, T.Z[0], bb[0], T.A[0], nullptr, 1,
+         nullptr, 0, T.err);
+  for (int l = 1; l < 4; ++l)
+    TG_TRY(s, kTgBiasSilu, B, 256, 256, T.A[l - 1], 256, 1, W[l], 256, 1, T.Z[l], bb[l], T.A[l],
+           nullptr, 1, nullptr, 0, T.err);
+  TG_TRY(s, kTgBias, B, 4, 256, T.A[3], 256, 1, P + P_W5, 256, 1, T.V, P + P_B5, nullptr, nullptr, 1,
+         nullptr, 0, T.err);
+  loss_kernel<<<nb(B, 256), 256, 0, s>>>(B, T.V, T.U, T.dV, loss_slot);
+  // dW5 = dV^T A4 (contraction over the batch), db5, dZ4 = (dV W5) * SiLU'(Z4)
+  TG_TRY(s, kTgStore, 4, 256, B, T.dV, 1, 4, T.A[3], 1, 256, G + P_W5, nullptr, nullptr, nullptr,
+         splits, T.ws, T.ws_floats, T.err);
+  colsum_kernel<<<1, 256, 0, s>>>(B, 4, T.dV, G + P_B5);
+  TG_TRY(s, kTgDSilu, B, 256, 4, T.dV, 4, 1, P + P_W5, 1, 256, T.dZ[0], nullptr, nullptr, T.Z[3], 1,
+         nullptr, 0, T.err);
+  int cur = 0;
+  const int64_t wofs[4] = {P_W1, P_W2, P_W3, P_W4}, bofs[4] = {P_B1, P_B2, P_B3, P_B4};
+  for (int l = 3; l >= 0; --l) {
+    const float *dz = T.dZ[cur];
+    const float *ain = l == 0 ? T.X0 : T.A[l - 1];
+    const int kin = l == 0 ? 32 : 256;
+    // dW_l[m][n] = sum_b dZ_l[b][m] A_{l-1}[b][n]
+    TG_TRY(s, kTgStore, 256, kin, B, dz, 1, 256, ain, 1, kin, G + wofs[l], nullptr, nullptr, nullptr,
+           splits, T.ws, T.ws_floats, T.err);
+    colsum_kernel<<<8, 256, 0, s>>>(B, 256, dz, G + bofs[l]);
+    if (l > 0) {
+      // dZ_{l-1}[b][n] = SiLU'(Z_{l-1}[b][n]) sum_k dZ_l[b][k] W_l[k][n]
+      TG_TRY(s, kTgDSilu, B, 256, 256, dz, 256, 1, P + wofs[l], 1, 256, T.dZ[cur ^ 1], nullptr,
+             nullptr, T.Z[l - 1], 1, nullptr, 0, T.err);
+      cur ^= 1;
+    }
+  }
+#undef TG_TRY
+  return cudaGetLastError();
+}
+
+cudaError_t step_grads(cudaStream_t s, TrainState &T, double *loss_slot) {
+  return T.cfg.precision == GMC_BF16 ? fwd_bwd_tc(s, T, loss_slot) : fwd_bwd(s, T, loss_slot);
+}
+
 void free_train(TrainState *T) {
   if (!T) return;
   float *bufs[] = {T->params, T->grads, T->m, T->v, T->X0, T->U, T->V, T->dV, T->Z[0], T->Z[1],
@@ -323,6 +384,7 @@ void free_train(TrainState *T) {
     if (b) cudaFree(b);
   if (T->loss) cudaFree(T->loss);
   if (T->stat_acc) cudaFree(T->stat_acc);
+  if (T->ws) cudaFree(T->ws);
   delete T;
 }
 
@@ -374,6 +436,8 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
   if (n < 2 || !cond || !y) return set_error(ctx, GMC_EINVAL, "gmc_train_begin: need n >= 2 samples");
   if (cfg->batch < 1 || cfg->batch > (1 << 20) || !(cfg->lr > 0.0))
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: batch in [1, 2^20], lr > 0");
+  if (cfg->precision != GMC_FP32 && cfg->precision != GMC_BF16)
+    return set_error(ctx, GMC_EINVAL, "gmc_train_begin: precision must be GMC_FP32 or GMC_BF16");
   if (!ctx->has_weights) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_train_begin: load initial weights first");
   if (!is_device_pointer(cond) || !is_device_pointer(y))
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: data must be device memory");
@@ -427,6 +491,11 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
   GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->m, 0, P_TOTAL * 4, s));
   GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->v, 0, P_TOTAL * 4, s));
   GMC_CUDA_TRY(ctx, alloc_batch(*T, cfg->batch));
+  T->err = ctx->d_err;
+  if (cfg->precision == GMC_BF16) {
+    T->ws_floats = (size_t)32 * 256 * 256;  // 32 split-K slices of a 256 x 256 gradient
+    GMC_CUDA_TRY(ctx, cudaMalloc(&T->ws, T->ws_floats * sizeof(float)));
+  }
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   return GMC_OK;
 }
@@ -458,7 +527,7 @@ gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses) {
   const gmc_train_config &c = T->cfg;
   for (int64_t i = 0; i < n_steps; ++i) {
     batch_kernel<<<nb(T->B, 256), 256, 0, s>>>(T->B, T->n, T->cond, T->y, sd, c.seed, T->step, T->X0, T->U);
-    GMC_CUDA_TRY(ctx, fwd_bwd(s, *T, T->loss + i));
+    GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i));
     ++T->step;
     const float bc1 = 1.0f - (float)std::pow(c.beta1, (double)T->step);
     const float bc2 = 1.0f - (float)std::pow(c.beta2, (double)T->step);
@@ -472,6 +541,7 @@ gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses) {
     GMC_CUDA_TRY(ctx, cudaMemcpyAsync(hl.data(), T->loss, n_steps * sizeof(double), cudaMemcpyDeviceToHost, s));
     GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     for (int64_t i = 0; i < n_steps; ++i) losses[i] = (float)hl[i];
+    return check_device_error(ctx);
   }
   return GMC_OK;
 }
@@ -500,13 +570,13 @@ gmc_status gmc_train_grad(gmc_ctx *ctx, int64_t B, const float *cn, const float 
   GMC_CUDA_TRY(ctx, ensure(ctx->stage[1], sizeof(double)));
   ls = (double *)ctx->stage[1].ptr;
   GMC_CUDA_TRY(ctx, cudaMemsetAsync(ls, 0, sizeof(double), s));
-  cudaError_t e = fwd_bwd(s, *T, ls);
+  cudaError_t e = step_grads(s, *T, ls);
   T->B = saveB;
   GMC_CUDA_TRY(ctx, e);
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(loss, ls, sizeof(double), cudaMemcpyDeviceToHost, s));
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(grad, T->grads, P_TOTAL * 4, cudaMemcpyDeviceToHost, s));
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  return GMC_OK;
+  return check_device_error(ctx);
 }
 
 int64_t gmc_train_param_count(void) { return P_TOTAL; }

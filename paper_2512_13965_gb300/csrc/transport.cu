@@ -429,8 +429,6 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
   if (n_histories > 0 && !(acc > 0.0)) return set_error(ctx, GMC_EINVAL, "solve: zero source");
   if (method == GMC_METHOD_GMC && !ctx->has_weights)
     return set_error(ctx, GMC_ENOWEIGHTS, "solve: GMC needs gmc_load_weights");
-  if (method == GMC_METHOD_GMC && ctx->cfg.precision == GMC_FP8)
-    return set_error(ctx, GMC_ENOTIMPL, "solve: FP8 sampler not built");
   R.total = acc;
   R.n_hist = n_histories;
   R.method = method;
@@ -623,10 +621,13 @@ class Engine {
         if (cfg.precision == GMC_FP32)
           e = launch_sampler_f32(s_, ctx_->f32, ctx_->stats, live_, d_cond_, d_noise_, 0, 0,
                                  cfg.steps, cfg.integrator, nullptr, d_exit_);
-        else
-          e = launch_sampler_tc(s_, ctx_->d_tc, ctx_->d_tc_bias, ctx_->f32, ctx_->stats, live_,
-                                d_cond_, d_noise_, 0, 0, cfg.steps, cfg.integrator, nullptr,
-                                d_exit_, ctx_->d_err, d_bias1_);
+        else {
+          const bool fp8 = cfg.precision == GMC_FP8;
+          e = launch_sampler_tc(s_, fp8 ? ctx_->d_tc8 : ctx_->d_tc, ctx_->d_tc_bias, ctx_->f32,
+                                ctx_->stats, live_, d_cond_, d_noise_, 0, 0, cfg.steps,
+                                cfg.integrator, nullptr, d_exit_, ctx_->d_err, d_bias1_,
+                                fp8 ? ctx_->d_tc8_scale : nullptr);
+        }
         if (e != cudaSuccess) return cuda_error(ctx_, e, "solve: sampler");
         gmc_post_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_exit_, d_slots_,
                                                              rules, bank_[nxt], d_count, d_stats_,

@@ -7,7 +7,9 @@
 Data: `gmc_train_data` (implicit-capture random walks, tau log-uniform in
 [0.1, 1000], c uniform in [0.5, 0.999]); objective: conditional flow
 matching (Eq. 9) with AdamW, learning rate warmed up linearly and then
-decayed along a cosine to --lr-min; everything runs in libgmc.so. The network
+decayed along a cosine to --lr-min; everything runs in libgmc.so, the GEMMs
+on tensor cores with BF16 operands and FP32 accumulation and master weights
+(--precision fp32 selects the FP32 SIMT GEMMs). The network
 starts from Kaiming-normal weights drawn by `synth` (seed --init-seed).
 Prints one JSON line per report interval (loss, samples/s).
 """
@@ -36,6 +38,8 @@ def main(argv=None):
     ap.add_argument("--c", type=float, nargs=2, default=(0.5, 0.999))
     ap.add_argument("--report", type=int, default=1000)
     ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"],
+                    help="GEMM operands: bf16 (tensor cores) or fp32 (SIMT)")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -65,7 +69,8 @@ def main(argv=None):
     t_data = time.perf_counter() - t0
     print(json.dumps({"phase": "data", "samples": n, "seconds": t_data}), flush=True)
     cfg = g.gmc_train_config(batch=args.batch, lr=args.lr, beta1=0.9, beta2=0.999, eps=1e-8,
-                             weight_decay=args.weight_decay, seed=args.seed + 1000)
+                             weight_decay=args.weight_decay, seed=args.seed + 1000,
+                             precision=g.GMC_BF16 if args.precision == "bf16" else g.GMC_FP32)
     g.gmc_train_begin(ctx, n, cond, y, cfg)
     import math
 

@@ -192,3 +192,56 @@ def test_bf16_rk4_bound(gpu_ctx, net):
     expect = oracle.mlp.sample(net, cond, z, 12, "rk4")
     err = np.abs(y - expect)
     assert err.max() < BF16_MAX and np.quantile(err, 0.999) < BF16_P999
+
+
+# FP8 path: E4M3 weights (per-output-channel scales) and inputs for layers
+# 2-4. Two references: the FP64 network (the size of the 8-bit error, a
+# measured bound like BF16's) and the oracle's quantized network
+# (oracle.mlp.quantized_e4m3: the same roundings of weights and layer inputs
+# in FP64), which the GPU must track much more closely -- what remains is
+# accumulation order, the BF16 layers 1 and 5, and E4M3 rounding decisions
+# flipped by the FP16 SiLU.
+FP8_MAX, FP8_P999 = 2.0, 1.0
+FP8Q_MAX, FP8Q_P999 = 1.0, 0.3
+
+
+def _fp8_check(ctx, net, n, steps, integ, iname, seed):
+    import paper_2512_13965_gb300 as g
+    cond, _, _ = synth.sampler_conditions(n, seed)
+    z = synth.gaussian_noise(n, seed + 1)
+    y, _ = _run(ctx, cond, z, steps, integ, g.GMC_FP8)
+    assert np.all(np.isfinite(y))
+    e = np.abs(y - oracle.mlp.sample(net, cond, z, steps, iname))
+    eq = np.abs(y - oracle.mlp.sample(oracle.mlp.quantized_e4m3(net), cond, z, steps, iname))
+    assert e.max() < FP8_MAX, e.max()
+    assert eq.max() < FP8Q_MAX, eq.max()
+    if n > 1000:
+        assert np.quantile(e, 0.999) < FP8_P999
+        assert np.quantile(eq, 0.999) < FP8Q_P999
+        # it is the quantized network that the path evaluates
+        assert np.median(eq) < 0.5 * np.median(e)
+    return e, eq
+
+
+@pytest.mark.parametrize("n", [1, 129, 8192 + 77])
+def test_fp8_euler16_bound(gpu_ctx, net, n):
+    _fp8_check(gpu_ctx, net, n, 16, 0, "euler", 500 + n)
+
+
+def test_fp8_midpoint_and_rk4_bound(gpu_ctx, net):
+    import paper_2512_13965_gb300 as g
+    _fp8_check(gpu_ctx, net, 2000, 8, g.GMC_MIDPOINT, "midpoint", 71)
+    _fp8_check(gpu_ctx, net, 2000, 12, g.GMC_RK4, "rk4", 73)
+
+
+def test_fp8_full_size_sampled(gpu_ctx, net):
+    import paper_2512_13965_gb300 as g
+    n = 1 << 20
+    cond, _, _ = synth.sampler_conditions(n, 1)
+    z = synth.gaussian_noise(n, 3)
+    y, _ = _run(gpu_ctx, cond, z, 16, g.GMC_EULER, g.GMC_FP8)
+    assert np.all(np.isfinite(y))
+    idx = np.concatenate([np.random.default_rng(2).choice(n, 1024, replace=False), [0, n - 1]])
+    q = oracle.mlp.quantized_e4m3(net)
+    eq = np.abs(y[:, idx] - oracle.mlp.sample(q, cond[:, idx], z[:, idx], 16, "euler"))
+    assert eq.max() < FP8Q_MAX

@@ -178,3 +178,59 @@ def test_training_gain(gpu_ctx, trainer, tmp_path):
             b = before[(tau, c)][k] if k != 3 else np.log(before[(tau, c)][3])
             a = after[k] if k != 3 else np.log(after[3])
             assert oracle.stats.w1(a, ref[k]) < oracle.stats.w1(b, ref[k]), (tau, c, k)
+
+
+# BF16 tensor-core training step: the same gradient with BF16 MMA operands
+# (FP32 accumulation, FP32 master weights). The bound is stated per layer
+# relative to the layer's largest gradient entry, from the arithmetic: one
+# BF16 rounding (2^-9 relative) of each operand, accumulated over K terms of
+# mixed sign, then carried through four layers of backward.
+BF16_GRAD_REL = 3e-2
+
+
+def _begin_bf16(ctx, trainer):
+    import paper_2512_13965_gb300 as g
+    c = trainer["cfg"]
+    cfg = g.gmc_train_config(batch=c.batch, lr=c.lr, beta1=c.beta1, beta2=c.beta2, eps=c.eps,
+                             weight_decay=c.weight_decay, seed=c.seed, precision=g.GMC_BF16)
+    g.gmc_train_begin(ctx, trainer["n"], trainer["cond"], trainer["y"], cfg)
+    return cfg
+
+
+@pytest.mark.parametrize("B", [64, 300, 2048])
+def test_gradient_bf16_tensor_cores(gpu_ctx, trainer, B):
+    import paper_2512_13965_gb300 as g
+    _begin_bf16(gpu_ctx, trainer)
+    rng = np.random.default_rng(B)
+    cn = rng.standard_normal((B, 5)).astype(np.float32)
+    x1 = rng.standard_normal((B, 4)).astype(np.float32)
+    x0 = rng.standard_normal((B, 4)).astype(np.float32)
+    t = rng.random(B).astype(np.float32)
+    P = g.gmc_train_param_count()
+    grad = np.zeros(P, np.float32)
+    loss = g.gmc_train_grad(gpu_ctx, B, cn, x1, x0, t, grad)
+    params = np.zeros(P, np.float32)
+    g.gmc_train_params(gpu_ctx, params)
+    W, b = _oracle_params(params)
+    ref_loss, gW, gb = oracle.train.cfm_loss_grad(W, b, cn.astype(np.float64), x1.astype(np.float64),
+                                                  x0.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - ref_loss) < 1e-2 * max(1.0, abs(ref_loss))
+    GW, Gb = _oracle_params(grad)
+    for l in range(5):
+        scale = max(np.abs(gW[l]).max(), 1e-12)
+        assert np.abs(GW[l] - gW[l]).max() < BF16_GRAD_REL * scale, ("W", l)
+        bs = max(np.abs(gb[l]).max(), 1e-12)
+        assert np.abs(Gb[l] - gb[l]).max() < BF16_GRAD_REL * bs, ("b", l)
+        # and far from an unrelated gradient: the error is a small part
+        assert np.linalg.norm(GW[l] - gW[l]) < 0.05 * np.linalg.norm(gW[l]), ("W norm", l)
+    assert np.all(grad[:256 * 32].reshape(256, 32)[:, 25:] == 0)
+
+
+def test_training_bf16_reduces_loss(gpu_ctx, trainer):
+    import paper_2512_13965_gb300 as g
+    _begin_bf16(gpu_ctx, trainer)
+    steps = 400
+    losses = np.zeros(steps, np.float32)
+    g.gmc_train_steps(gpu_ctx, steps, losses)
+    assert np.all(np.isfinite(losses))
+    assert losses[-50:].mean() < 0.8 * losses[:20].mean()

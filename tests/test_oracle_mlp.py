@@ -187,3 +187,75 @@ def test_decode_destandardizes(tmp_path):
     assert d["face"][0] == 2 and abs(d["q"][0] - 0.5) < 1e-15
     np.testing.assert_allclose([d["ux"][0], d["uy"][0]], [0.6, 0.8])
     assert abs(d["s"][0] - 1.0) < 1e-15
+
+
+def _e4m3_values():
+    # every non-negative finite E4M3 value, from the format's definition:
+    # zero, subnormals m/8 2^-6, normals (1 + m/8) 2^(e-7) up to 448
+    v = [0.0] + [m / 8 * 2.0 ** -6 for m in range(1, 8)]
+    v += [(1 + m / 8) * 2.0 ** (e - 7) for e in range(1, 16) for m in range(8)]
+    return np.array(v[:-1])  # e = 15, m = 7 is NaN
+
+
+def test_round_e4m3_format_values():
+    v = _e4m3_values()
+    assert v.size == 127 and v[-1] == 448.0 and np.all(np.diff(v) > 0)
+    np.testing.assert_array_equal(mlp.round_e4m3(v), v)
+    np.testing.assert_array_equal(mlp.round_e4m3(-v), -v)
+    # midpoints go to the neighbour with the even code (code = index here)
+    mid = 0.5 * (v[:-1] + v[1:])
+    even = np.where(np.arange(v.size - 1) % 2 == 0, v[:-1], v[1:])
+    np.testing.assert_array_equal(mlp.round_e4m3(mid), even)
+    # just off the midpoint: nearest
+    np.testing.assert_array_equal(mlp.round_e4m3(mid * (1 - 1e-9)), v[:-1])
+    np.testing.assert_array_equal(mlp.round_e4m3(mid * (1 + 1e-9)), v[1:])
+    # saturation
+    np.testing.assert_array_equal(mlp.round_e4m3([449.0, 1e6, -1e30]), [448.0, 448.0, -448.0])
+
+
+def test_round_e4m3_matches_torch_cast():
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8_e4m3fn")
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(200000) * np.exp(rng.uniform(-14, 7, 200000))
+    x = np.clip(x, -448, 448)
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(mlp.round_e4m3(x), ref)
+
+
+def test_quantized_e4m3_weights(tmp_path):
+    o = _load(tmp_path, synth.kaiming_weights(1))
+    q = mlp.quantized_e4m3(o)
+    for l in (0, 4):
+        np.testing.assert_array_equal(q.W[l], o.W[l])
+    for l in (1, 2, 3):
+        sc = np.abs(o.W[l]).max(axis=1, keepdims=True) / 448.0
+        err = np.abs(q.W[l] - o.W[l])
+        # half a spacing: 2^-4 relative in the normal range, 2^-10 s below it
+        assert np.all(err <= np.maximum(np.abs(o.W[l]) / 16, sc * 2.0 ** -10) * (1 + 1e-12))
+        # each row's largest weight maps to 448 and is kept (up to the
+        # rounding of the division and multiplication by s_c)
+        i = np.arange(256), np.abs(o.W[l]).argmax(axis=1)
+        np.testing.assert_allclose(q.W[l][i], o.W[l][i], rtol=1e-15)
+
+
+def test_quantized_e4m3_single_path(tmp_path):
+    # the chain of test_single_path_through_the_network: its weights are
+    # exact in E4M3 after scaling (row max 1 -> 448), so only the inputs of
+    # layers 2-4 are rounded: x_0(1) = x_0 + silu(r(silu(r(silu(r(silu(a x_0)))))))
+    net = _zero_net()
+    a = float(np.float32(0.7))
+    net["W"][0][0, 5] = a
+    for l in (1, 2, 3):
+        net["W"][l][0, 0] = 1.0
+    net["W"][4][0, 0] = 1.0
+    q = mlp.quantized_e4m3(_load(tmp_path, net))
+    cond, _, _ = synth.sampler_conditions(8, 5)
+    z = synth.gaussian_noise(8, 6)
+    y = mlp.sample(q, cond, z, 1, "euler")
+    r = lambda u: float(mlp.round_e4m3(u))
+    for i in range(8):
+        x0 = float(z[0, i])
+        expect = x0 + _silu(r(_silu(r(_silu(r(_silu(a * x0)))))))
+        assert abs(y[0, i] - expect) < 1e-14
