@@ -505,6 +505,12 @@ def run_heldout(args):
     args_u = argparse.Namespace(**vars(args))
     args_u.weights = None
     _, ctx_u = _context(args_u)
+    # one stream for torch and the library: inputs made by torch, outputs read
+    # by torch, in stream order (a null stream would select the context's own)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    for cx in (ctx, ctx_u):
+        g.gmc_set_stream(cx, stream)
     n = 100000
     e = synth.cell_entries(n, 2024)
     xi, cs, sn = (torch.from_numpy(e[k]).cuda() for k in ("xi", "cos", "sin"))

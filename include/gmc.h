@@ -87,7 +87,7 @@ typedef struct gmc_solve_stats {
     int64_t transmissions;  /* cell transmissions, births included */
     int64_t collisions;     /* scatterings simulated by random walks */
     int64_t roulette_kills; /* histories ended by roulette */
-    int64_t waves;          /* event waves of the particle loop */
+    int64_t waves;          /* event waves of the particle loop while the solve was admitted */
     int64_t inward_fixes;   /* sampled exit directions that pointed into the cell */
     double seconds;         /* device time from admission to the last wave */
     double latency;         /* host wall time from submission to completion */
@@ -95,7 +95,9 @@ typedef struct gmc_solve_stats {
 
 /* ---- context ------------------------------------------------------------ */
 
-/* Creates a context on CUDA device `device` with its own stream. */
+/* Creates a context on CUDA device `device` with its own stream (a blocking
+   stream: ordered with work on the legacy default stream, not with other
+   non-blocking streams; pass those with gmc_set_stream). */
 gmc_status gmc_create(gmc_ctx **out, int device);
 /* Frees the context and every device buffer it owns. Null is accepted. */
 gmc_status gmc_destroy(gmc_ctx *ctx);

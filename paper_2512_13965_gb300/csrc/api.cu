@@ -170,7 +170,9 @@ gmc_status gmc_create(gmc_ctx **out, int device) {
   ctx->device = device;
   ctx->cfg = default_config();
   cudaError_t e = cudaSetDevice(device);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+  // a blocking stream: ordered with work on the legacy default stream, so
+  // buffers a caller fills there are ready before the library reads them
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamDefault);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int) * 4);
   if (e != cudaSuccess) {

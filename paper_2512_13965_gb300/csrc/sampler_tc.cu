@@ -72,8 +72,14 @@ constexpr int MMAS_PER_CHUNK = CHUNK_K / 16;
 constexpr uint32_t CHUNK_SWIZZLE = CHUNK_K == 32 ? 4u /* 64B */ : 2u /* 128B */;
 constexpr uint32_t CHUNK_SBO = CHUNK_K == 32 ? 512u : 1024u;
 constexpr int NST = (81920 / CHUNK) > 5 ? 5 : (int)(81920 / CHUNK);  // stages in 80 KB
-constexpr int EPI_WARPS = GMC_TC_EPI_WARPS;      // a multiple of 4 (TMEM lane quadrants)
-constexpr int EPI_COLS = 256 / (EPI_WARPS / 4);   // accumulator columns per epilogue thread
+#ifndef GMC_TC_SPLIT_TILES
+#define GMC_TC_SPLIT_TILES 0  // measured on GB300: 1 is 8 % slower (6.65 vs 6.13 ms per 2^20 x 16 steps)
+#endif
+constexpr int EPI_WARPS = GMC_TC_EPI_WARPS;      // a multiple of 8 (2 groups x TMEM lane quadrants)
+constexpr bool SPLIT_TILES = GMC_TC_SPLIT_TILES != 0;  // one epilogue group per tile
+constexpr int TPW = SPLIT_TILES ? 1 : 2;          // tiles served by each epilogue warp
+constexpr int GROUP_WARPS = SPLIT_TILES ? EPI_WARPS / 2 : EPI_WARPS;  // warps per tile
+constexpr int EPI_COLS = 256 / (GROUP_WARPS / 4);  // accumulator columns per epilogue thread
 constexpr int EPI_CH = EPI_COLS / 32;             // 32-column TMEM loads per thread
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
 static_assert(CHUNK_K == 32 || CHUNK_K == 64, "chunk K");
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     }
     mbar_init(&B.res_full, 1);
     for (int t = 0; t < 2; ++t) {
-      mbar_init(&B.a_ready[t], EPI_WARPS);
+      mbar_init(&B.a_ready[t], GROUP_WARPS);
       mbar_init(&B.mma_done[t], 1);
     }
     mbar_init(&B.drain, 1);
@@ -476,35 +482,45 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     }
   } else {
     // ---------------- epilogue ----------------
-    const int q = warp & 3, hf = (warp - 2) >> 2;  // lane quadrant, column quarter
+    // SPLIT_TILES: warps 2 .. 2+GROUP-1 serve tile X and the rest tile Y, so
+    // one group converts its accumulator while the other waits for its MMA;
+    // otherwise every epilogue warp serves both tiles in turn.
+    const int ew = warp - 2;
+    const int t0 = SPLIT_TILES ? ew / GROUP_WARPS : 0;  // first tile of this warp
+    const int q = warp & 3;                             // TMEM lane quadrant of the warp
+    const int hf = (ew % GROUP_WARPS) >> 2;             // column part within the group
     const int r = 32 * q + lane;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    float cn[2][kCond], x[2][4], xm[2][4], ka[2][4];
-    uint32_t dph[2] = {0, 0};
+    float cn[TPW][kCond], x[TPW][4], xm[TPW][4], ka[TPW][4];
+    uint32_t dph[TPW];
+#pragma unroll
+    for (int tt = 0; tt < TPW; ++tt) dph[tt] = 0;
     bool ok = true;
     for (int64_t ip = 0; ip < n_iter && ok; ++ip) {
       const int64_t pr = blockIdx.x + ip * gridDim.x;
-      for (int T = 0; T < 2; ++T) {
+#pragma unroll
+      for (int tt = 0; tt < TPW; ++tt) {
+        const int T = t0 + tt;
         const int64_t g = (2 * pr + T) * TM + r;
         const bool valid = g < P.n;
         if (hf == 0) {
 #pragma unroll
           for (int k = 0; k < kCond; ++k)
-            cn[T][k] = valid ? (P.cond[k * P.n + g] - P.st.cond_mean[k]) * P.st.cond_inv_std[k] : 0.0f;
+            cn[tt][k] = valid ? (P.cond[k * P.n + g] - P.st.cond_mean[k]) * P.st.cond_inv_std[k] : 0.0f;
           if (!valid) {
 #pragma unroll
-            for (int d = 0; d < 4; ++d) x[T][d] = 0.0f;
+            for (int d = 0; d < 4; ++d) x[tt][d] = 0.0f;
           } else if (P.noise) {
 #pragma unroll
-            for (int d = 0; d < 4; ++d) x[T][d] = P.noise[d * P.n + g];
+            for (int d = 0; d < 4; ++d) x[tt][d] = P.noise[d * P.n + g];
           } else {
             const float4 z = box_muller4(philox_draw(P.seed, P.id0 + (uint64_t)g, 0u, kTagNoise));
-            x[T][0] = z.x;
-            x[T][1] = z.y;
-            x[T][2] = z.z;
-            x[T][3] = z.w;
+            x[tt][0] = z.x;
+            x[tt][1] = z.y;
+            x[tt][2] = z.z;
+            x[tt][3] = z.w;
           }
-          write_a1(sbase + (T ? S_A1 : S_A0), r, cn[T], x[T]);
+          write_a1(sbase + (T ? S_A1 : S_A0), r, cn[tt], x[tt]);
           fence_proxy_async_smem();
         }
         __syncwarp();
@@ -512,13 +528,15 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
       }
       for (int e = 0; e < P.n_eval && ok; ++e) {
         for (int L = 0; L < 4 && ok; ++L)
-          for (int T = 0; T < 2; ++T) {
-            if (!mbar_wait(&B.mma_done[T], dph[T] & 1u, abort)) {
+#pragma unroll
+          for (int tt = 0; tt < TPW; ++tt) {
+            const int T = t0 + tt;
+            if (!mbar_wait(&B.mma_done[T], dph[tt] & 1u, abort)) {
               fail(B, P.err, 5);
               ok = false;
               break;
             }
-            ++dph[T];
+            ++dph[tt];
             tc_fence_after();
             const float *bias = L == 0 ? P.bias1 + (size_t)e * 256 : P.bias + L * 256;
             const uint32_t a_base = sbase + (T ? S_A1 : S_A0);
@@ -543,13 +561,15 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
           }
         if (!ok) break;
         const bool last = e == P.n_eval - 1;
-        for (int T = 0; T < 2; ++T) {
-          if (!mbar_wait(&B.mma_done[T], dph[T] & 1u, abort)) {
+#pragma unroll
+        for (int tt = 0; tt < TPW; ++tt) {
+          const int T = t0 + tt;
+          if (!mbar_wait(&B.mma_done[T], dph[tt] & 1u, abort)) {
             fail(B, P.err, 6);
             ok = false;
             break;
           }
-          ++dph[T];
+          ++dph[tt];
           tc_fence_after();
           if (hf == 0) {
             float v[4];
@@ -557,33 +577,33 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
             tmem_wait_ld_regs4(v);
 #pragma unroll
             for (int d = 0; d < 4; ++d) v[d] += __ldg(P.bias + 4 * 256 + d);
-            float *xin = x[T];
+            float *xin = x[tt];
             if (P.integrator == GMC_MIDPOINT && (e & 1) == 0) {
 #pragma unroll
-              for (int d = 0; d < 4; ++d) xm[T][d] = fmaf(0.5f * h, v[d], x[T][d]);
-              xin = xm[T];
+              for (int d = 0; d < 4; ++d) xm[tt][d] = fmaf(0.5f * h, v[d], x[tt][d]);
+              xin = xm[tt];
             } else if (P.integrator == GMC_RK4) {
               // evaluation e % 4 = i gives k_{i+1}; ka = k1 + 2 k2 + 2 k3 + k4
               const int i = e & 3;
               if (i == 3) {
 #pragma unroll
-                for (int d = 0; d < 4; ++d) x[T][d] = fmaf(h * (1.0f / 6.0f), ka[T][d] + v[d], x[T][d]);
+                for (int d = 0; d < 4; ++d) x[tt][d] = fmaf(h * (1.0f / 6.0f), ka[tt][d] + v[d], x[tt][d]);
               } else {
                 const float wgt = i == 0 ? 1.0f : 2.0f, hs = i == 2 ? h : 0.5f * h;
 #pragma unroll
                 for (int d = 0; d < 4; ++d) {
-                  ka[T][d] = i == 0 ? v[d] : fmaf(wgt, v[d], ka[T][d]);
-                  xm[T][d] = fmaf(hs, v[d], x[T][d]);
+                  ka[tt][d] = i == 0 ? v[d] : fmaf(wgt, v[d], ka[tt][d]);
+                  xm[tt][d] = fmaf(hs, v[d], x[tt][d]);
                 }
-                xin = xm[T];
+                xin = xm[tt];
               }
             } else {
 #pragma unroll
-              for (int d = 0; d < 4; ++d) x[T][d] = fmaf(h, v[d], x[T][d]);
+              for (int d = 0; d < 4; ++d) x[tt][d] = fmaf(h, v[d], x[tt][d]);
             }
             if (!last) {
               float xi[4] = {xin[0], xin[1], xin[2], xin[3]};
-              write_a1(sbase + (T ? S_A1 : S_A0), r, cn[T], xi);
+              write_a1(sbase + (T ? S_A1 : S_A0), r, cn[tt], xi);
               fence_proxy_async_smem();
             }
           }
@@ -595,11 +615,11 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
             if (g < P.n) {
               if (P.y_raw) {
 #pragma unroll
-                for (int d = 0; d < 4; ++d) P.y_raw[d * P.n + g] = x[T][d];
+                for (int d = 0; d < 4; ++d) P.y_raw[d * P.n + g] = x[tt][d];
               }
               if (P.exitp) {
                 bool inward;
-                const float4 o = decode_exit(x[T][0], x[T][1], x[T][2], x[T][3], P.st, &inward);
+                const float4 o = decode_exit(x[tt][0], x[tt][1], x[tt][2], x[tt][3], P.st, &inward);
                 P.exitp[g] = o.x;
                 P.exitp[P.n + g] = o.y;
                 P.exitp[2 * P.n + g] = o.z;

@@ -382,6 +382,7 @@ struct Request {
   int slot = -1;
   int64_t next_hist = 0;
   int live = 0;
+  int64_t wave0 = 0;  // engine wave count at admission
   size_t pool_off = 0, footprint = 0;
   double *d_cdf = nullptr, *d_flux = nullptr;
   float *d_tau = nullptr, *d_c = nullptr;
@@ -566,6 +567,7 @@ class Engine {
     R->slot = slot;
     R->next_hist = 0;
     R->live = 0;
+    R->wave0 = waves_;
     reqs_[slot] = R;
     ++active_;
     return true;
@@ -689,7 +691,7 @@ class Engine {
     R->st.transmissions = (int64_t)hs.transmissions;
     R->st.collisions = (int64_t)hs.collisions;
     R->st.roulette_kills = (int64_t)hs.kills;
-    R->st.waves = waves_;
+    R->st.waves = waves_ - R->wave0;
     R->st.inward_fixes = (int64_t)hs.inward;
     R->st.seconds = ms * 1e-3;
     R->t_done = now_s();

@@ -2,9 +2,10 @@
 weights and noise.
 
 FP32 path: within 1e-4 absolute per output (the contract's FP32 bound).
-BF16 path: the bound derived from the arithmetic (BF16 operands with 8-bit
-significands, FP32 accumulation, K steps): max abs error 0.25 and p99.9 0.1
-on standardized outputs after 16 steps, for Kaiming random weights.
+BF16 path: max abs error 0.1 and p99.9 0.06 on standardized outputs, for
+Kaiming random weights (measured on GB300 over 8192 rows: max 0.042-0.048,
+p99.9 0.030-0.038 for Euler 16 and 8, midpoint 8 and RK4 12 -- BF16
+operands with 8-bit significands, FP32 accumulation).
 """
 import numpy as np
 import pytest
@@ -16,7 +17,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-4
-BF16_MAX, BF16_P999 = 0.25, 0.1
+BF16_MAX, BF16_P999 = 0.1, 0.06
 
 
 @pytest.fixture(scope="module")
@@ -201,8 +202,12 @@ def test_bf16_rk4_bound(gpu_ctx, net):
 # in FP64), which the GPU must track much more closely -- what remains is
 # accumulation order, the BF16 layers 1 and 5, and E4M3 rounding decisions
 # flipped by the FP16 SiLU.
-FP8_MAX, FP8_P999 = 2.0, 1.0
-FP8Q_MAX, FP8Q_P999 = 1.0, 0.3
+# measured on GB300, 8192 rows, Kaiming weights, Euler 16/8, midpoint 8, RK4 12:
+# against FP64 max 0.19-0.26, p99.9 0.15-0.18; against the quantized network
+# max 0.07-0.20, p99.9 0.04-0.10 (and the quantized network itself differs from
+# FP64 by max 0.21-0.25): the bounds keep a factor of about 2.
+FP8_MAX, FP8_P999 = 0.5, 0.3
+FP8Q_MAX, FP8Q_P999 = 0.4, 0.2
 
 
 def _fp8_check(ctx, net, n, steps, integ, iname, seed):

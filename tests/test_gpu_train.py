@@ -226,8 +226,9 @@ def test_gradient_bf16_tensor_cores(gpu_ctx, trainer, B):
     assert np.all(grad[:256 * 32].reshape(256, 32)[:, 25:] == 0)
 
 
-def test_training_bf16_reduces_loss(gpu_ctx, trainer):
+def test_training_bf16_reduces_loss(gpu_ctx, trainer, kaiming_file):
     import paper_2512_13965_gb300 as g
+    g.gmc_load_weights(gpu_ctx, kaiming_file)  # start untrained (earlier tests commit weights)
     _begin_bf16(gpu_ctx, trainer)
     steps = 400
     losses = np.zeros(steps, np.float32)
