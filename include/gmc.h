@@ -77,6 +77,9 @@ typedef struct gmc_config {
     double w_cut;          /* roulette threshold on the particle weight; default 1e-4 */
     double p_survive;      /* roulette survival probability; default 0.1 */
     int64_t bank_capacity; /* particles in flight per wave in transport_solve; default 2^21 */
+    int flights_per_wave;  /* random-walk flights a particle takes per wave of transport_solve
+                              before it waits for the next wave (births, and every walk of
+                              GMC_METHOD_ANALOG); results do not depend on it; default 512 */
 } gmc_config;
 
 /* Per-solve counters (all weights per history-weight unit, not normalized). */

@@ -112,6 +112,7 @@ gmc_config default_config() {
   c.w_cut = 1e-4;
   c.p_survive = 0.1;
   c.bank_capacity = (int64_t)1 << 21;
+  c.flights_per_wave = 512;
   return c;
 }
 
@@ -236,6 +237,8 @@ gmc_status gmc_set_config(gmc_ctx *ctx, const gmc_config *cfg) {
     return set_error(ctx, GMC_EINVAL, "need w_cut >= 0 and p_survive in (0, 1]");
   if (cfg->bank_capacity < 1024 || cfg->bank_capacity > ((int64_t)1 << 28))
     return set_error(ctx, GMC_EINVAL, "bank_capacity must be in [1024, 2^28]");
+  if (cfg->flights_per_wave < 1)
+    return set_error(ctx, GMC_EINVAL, "flights_per_wave must be >= 1");
   ctx->cfg = *cfg;
   return GMC_OK;
 }

@@ -2,24 +2,32 @@
 // MC walk it replaces) as an event loop over waves of in-flight particles,
 // with several solves ("requests") sharing one particle bank.
 //
-// Particle bank (structure of arrays, double-buffered, capacity C):
-//   hist u64 (history id = Philox id), slot i32 (request), cell i32, face i32
-//   (global face the particle entered through), xi f32 (canonical entry
-//   position), gx, gy f32 (global direction), w f32 (weight), ev u32 (next
-//   Philox event) -- 40 bytes per particle.
+// Particle banks (structure of arrays, double-buffered, capacity C each):
+//   face bank: particles entering a cell through a face -- hist u64 (history
+//     id = Philox id), slot i32 (request), cell i32, face i32 (global face the
+//     particle entered through), xi f32 (canonical entry position), gx, gy f32
+//     (global direction), w f32 (weight), ev u32 (next Philox event): 40 B;
+//   inside bank: random walks in progress inside a cell -- position and track
+//     length (f64, in the precision the cell walks in), direction, weight,
+//     next Philox event, collisions so far: 64 B.
 // One wave:
-//   births   new histories of every admitted request fill free slots of the
-//            bank (fair share): birth point and direction from Philox
-//            (id, 0, tag 4), walked to the first face crossing of the birth
-//            cell with implicit capture (the paper's separate internal-source
-//            network is not built);
-//   GMC      prep: rotate into the canonical left-entry frame (stage 1),
-//            build the condition and draw z ~ N(0, I) at (id, ev, tag 2);
-//            sampler: the fused flow-ODE kernel (stage 2);
+//   births   new histories of every admitted request fill free room of the
+//            banks (fair share): birth point and direction from Philox
+//            (id, 0, tag 4) start a walk in the inside bank (the paper's
+//            separate internal-source network is not built);
+//   inside   every walk in progress takes up to flights_per_wave more
+//            flights of the implicit-capture walk (Eq. 4); a walk that leaves
+//            its cell does stages 3-4 below, the others stay in the bank, so
+//            no wave waits for the longest walk;
+//   GMC      face particles -- prep: rotate into the canonical left-entry
+//            frame (stage 1), build the condition and draw z ~ N(0, I) at
+//            (id, ev, tag 2); sampler: the fused flow-ODE kernel (stage 2);
 //            post: attenuate and tally (stage 3, Eq. 5-7), rotate back,
 //            roulette, cross into the neighbour, compact survivors (stage 4);
-//   ANALOG   one kernel walks each particle through its cell (Eq. 4) and
-//            does stages 3-4 the same way.
+//   ANALOG   face particles start their walk through the cell (Eq. 4), up
+//            to flights_per_wave flights, then as for the inside bank.
+// A resumed walk draws the same random numbers as an uninterrupted one, so
+// the cap changes no result.
 // Tallies: per request, FP64 atomics into flux[ny*nx]; Delta w / (V sigma_a)
 // with V = 1. Per-history random numbers depend only on (request seed,
 // history id, event), and sampler rows are independent, so a request's
@@ -57,6 +65,16 @@ struct Bank {
   uint32_t *ev;
 };
 constexpr size_t kBankBytesPerParticle = 40;
+
+// Walks in progress inside a cell.
+struct IBank {
+  uint64_t *hist;
+  double *x, *y, *s;
+  int32_t *slot, *cell;
+  float *ux, *uy, *w;
+  uint32_t *ev, *ncoll;
+};
+constexpr size_t kIBankBytesPerParticle = 64;
 
 struct DevStats {
   double leaked, absorbed, roulette_net;
@@ -210,6 +228,40 @@ __device__ void finish_transmission(const Exit &x, const Slot *__restrict__ slot
   }
 }
 
+// Appends the lanes with `keep` set to the inside bank (warp-aggregated) and
+// counts them per request. Every lane of the warp must call it.
+__device__ void append_inside(bool keep, int slot, uint64_t hist, int cell, const WalkState &ws,
+                              float w, IBank out, int *count, int *slot_live) {
+  const int lane = threadIdx.x & 31;
+  const unsigned mask = __ballot_sync(0xffffffffu, keep);
+  if (!mask) return;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(count, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (keep) {
+    const int k = base + __popc(mask & ((1u << lane) - 1u));
+    out.hist[k] = hist;
+    out.x[k] = ws.x;
+    out.y[k] = ws.y;
+    out.s[k] = ws.s;
+    out.slot[k] = slot;
+    out.cell[k] = cell;
+    out.ux[k] = ws.ux;
+    out.uy[k] = ws.uy;
+    out.w[k] = w;
+    out.ev[k] = ws.event;
+    out.ncoll[k] = ws.ncoll;
+  }
+  const int lead = __ffs(mask) - 1;
+  const int slot0 = __shfl_sync(0xffffffffu, slot, lead);
+  const bool uniform = __all_sync(0xffffffffu, !keep || slot == slot0);
+  if (uniform) {
+    if (lane == 0) atomicAdd(&slot_live[slot0], __popc(mask));
+  } else if (keep) {
+    atomicAdd(&slot_live[slot], 1);
+  }
+}
+
 __device__ __forceinline__ int64_t cdf_search(const double *cdf, int64_t n, double target) {
   int64_t lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -220,50 +272,101 @@ __device__ __forceinline__ int64_t cdf_search(const double *cdf, int64_t n, doub
   return lo;
 }
 
-// Births of histories first .. first+count-1 of the request in `slot`.
+// Births of histories first .. first+count-1 of the request in `slot`: a
+// walk starting at the birth point (walked by the next wave).
 __global__ void birth_kernel(int slot, int64_t first, int64_t count, const double *__restrict__ cdf,
-                             double total, const Slot *__restrict__ slots, Rules R, Bank out,
-                             int *out_count, DevStats *st, int *slot_live) {
+                             double total, const Slot *__restrict__ slots, IBank out, int *in_count,
+                             int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  Exit x;
-  x.active = k < count;
-  x.slot = slot;
-  if (x.active) {
+  const bool keep = k < count;
+  WalkState ws{};
+  int cell = 0;
+  uint64_t h = 0;
+  if (keep) {
     const Slot S = slots[slot];
-    const uint64_t h = (uint64_t)(first + k);
+    h = (uint64_t)(first + k);
     const uint4 r = philox_draw(S.seed, h, 0u, kTagBirth);
     const double u0 = ((double)r.x + 1.0) * (1.0 / 4294967296.0);
-    const int64_t cell = cdf_search(cdf, (int64_t)S.nx * S.ny, u0 * total);
+    cell = (int)cdf_search(cdf, (int64_t)S.nx * S.ny, u0 * total);
     float ux, uy;
     sincospif(2.0f * u01(r.w), &uy, &ux);
-    const WalkResult wr = walk_cell(S.tau[cell], S.c[cell], 1, u01(r.y), u01(r.z), ux, uy, S.seed,
-                                    h, 0u);
-    x.hist = h;
-    x.cell = (int)cell;
-    x.gface = wr.face < 0 ? 0 : wr.face;
-    x.q = wr.q;
-    x.gx = wr.ux;
-    x.gy = wr.uy;
-    x.w = 1.0f;
-    x.s = wr.s;
-    x.ev = wr.event;
-    x.ncoll = wr.ncoll;
+    ws = walk_start(S.tau[cell], u01(r.y), u01(r.z), ux, uy, 0u);
   }
-  finish_transmission(x, slots, R, out, out_count, st, slot_live);
+  append_inside(keep, slot, h, cell, ws, 1.0f, out, in_count, slot_live);
 }
 
-// ANALOG: walk each bank particle through its cell in the cell's own
-// (global-oriented) frame, entering at the point its entry face and xi give.
-__global__ void analog_wave_kernel(int64_t live, Bank in, const Slot *__restrict__ slots, Rules R,
-                                   Bank out, int *out_count, DevStats *st, int *slot_live) {
+// Ends or parks one lane's walk: an exit (or absorption) becomes the Exit of
+// stages 3-4, a walk cut by the flight cap goes back to the inside bank.
+__device__ __forceinline__ void settle(const WalkResult &wr, const WalkState &ws, int slot,
+                                       uint64_t h, int cell, float w, Exit &x, bool &park) {
+  park = wr.status == kTruncated && ws.ncoll < kMaxFlights;
+  x.active = !park;
+  x.slot = slot;
+  x.hist = h;
+  x.cell = cell;
+  x.gface = wr.face < 0 ? 0 : wr.face;
+  x.q = wr.q;
+  x.gx = wr.ux;
+  x.gy = wr.uy;
+  x.w = w;
+  x.s = wr.s;
+  x.ev = wr.event;
+  x.ncoll = wr.ncoll;
+}
+
+// Up to `cap` more flights of every walk in progress.
+__global__ void inside_walk_kernel(int64_t live, IBank in, const Slot *__restrict__ slots, Rules R,
+                                   uint32_t cap, Bank out, int *out_count, IBank iout,
+                                   int *in_count, DevStats *st, int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Exit x;
-  x.active = k < live;
+  x.active = false;
   x.slot = 0;
-  if (x.active) {
-    x.slot = in.slot[k];
-    const Slot S = slots[x.slot];
-    const int cell = in.cell[k], F = in.face[k];
+  bool park = false;
+  WalkState ws{};
+  int slot = 0, cell = 0;
+  uint64_t h = 0;
+  float w = 0.0f;
+  if (k < live) {
+    slot = in.slot[k];
+    const Slot S = slots[slot];
+    cell = in.cell[k];
+    h = in.hist[k];
+    w = in.w[k];
+    ws.x = in.x[k];
+    ws.y = in.y[k];
+    ws.s = in.s[k];
+    ws.ux = in.ux[k];
+    ws.uy = in.uy[k];
+    ws.event = in.ev[k];
+    ws.ncoll = in.ncoll[k];
+    const WalkResult wr = walk_cell_resume(S.tau[cell], S.c[cell], 1, ws, cap, S.seed, h);
+    settle(wr, ws, slot, h, cell, w, x, park);
+  }
+  finish_transmission(x, slots, R, out, out_count, st, slot_live);
+  append_inside(park, slot, h, cell, ws, w, iout, in_count, slot_live);
+}
+
+// ANALOG: start the walk of each face particle through its cell in the
+// cell's own (global-oriented) frame, entering at the point its entry face
+// and xi give; up to `cap` flights, then as inside_walk_kernel.
+__global__ void analog_wave_kernel(int64_t live, Bank in, const Slot *__restrict__ slots, Rules R,
+                                   uint32_t cap, Bank out, int *out_count, IBank iout,
+                                   int *in_count, DevStats *st, int *slot_live) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Exit x;
+  x.active = false;
+  x.slot = 0;
+  bool park = false;
+  WalkState ws{};
+  int slot = 0, cell = 0;
+  uint64_t h = 0;
+  float w = 0.0f;
+  if (k < live) {
+    slot = in.slot[k];
+    const Slot S = slots[slot];
+    cell = in.cell[k];
+    const int F = in.face[k];
     const float xi = in.xi[k];
     // point on face F with counter-clockwise parameter 1 - xi
     float X, Y;
@@ -273,21 +376,15 @@ __global__ void analog_wave_kernel(int64_t live, Bank in, const Slot *__restrict
       case 2: X = xi; Y = 1.0f; break;
       default: X = 0.0f; Y = xi; break;
     }
-    const uint64_t h = in.hist[k];
-    const WalkResult wr = walk_cell(S.tau[cell], S.c[cell], 1, X, Y, in.gx[k], in.gy[k], S.seed, h,
-                                    in.ev[k]);
-    x.hist = h;
-    x.cell = cell;
-    x.gface = wr.face < 0 ? 0 : wr.face;
-    x.q = wr.q;
-    x.gx = wr.ux;
-    x.gy = wr.uy;
-    x.w = in.w[k];
-    x.s = wr.s;
-    x.ev = wr.event;
-    x.ncoll = wr.ncoll;
+    h = in.hist[k];
+    w = in.w[k];
+    const float tau = S.tau[cell];
+    ws = walk_start(tau, X, Y, in.gx[k], in.gy[k], in.ev[k]);
+    const WalkResult wr = walk_cell_resume(tau, S.c[cell], 1, ws, cap, S.seed, h);
+    settle(wr, ws, slot, h, cell, w, x, park);
   }
   finish_transmission(x, slots, R, out, out_count, st, slot_live);
+  append_inside(park, slot, h, cell, ws, w, iout, in_count, slot_live);
 }
 
 // GMC stage 1 and the noise of stage 2.
@@ -354,6 +451,23 @@ Bank carve(void *base, int64_t C) {
   b.gy = (float *)p; p += 4 * C;
   b.w = (float *)p; p += 4 * C;
   b.ev = (uint32_t *)p;
+  return b;
+}
+
+IBank carve_inside(void *base, int64_t C) {
+  IBank b;
+  char *p = (char *)base;
+  b.hist = (uint64_t *)p; p += 8 * C;
+  b.x = (double *)p; p += 8 * C;
+  b.y = (double *)p; p += 8 * C;
+  b.s = (double *)p; p += 8 * C;
+  b.slot = (int32_t *)p; p += 4 * C;
+  b.cell = (int32_t *)p; p += 4 * C;
+  b.ux = (float *)p; p += 4 * C;
+  b.uy = (float *)p; p += 4 * C;
+  b.w = (float *)p; p += 4 * C;
+  b.ev = (uint32_t *)p; p += 4 * C;
+  b.ncoll = (uint32_t *)p;
   return b;
 }
 
@@ -496,8 +610,8 @@ class Engine {
 
   ~Engine() {
     cudaStreamSynchronize(s_);
-    void *bufs[] = {bank_mem_[0], bank_mem_[1], d_cond_, d_noise_, d_exit_, d_slots_, d_stats_,
-                    d_counts_, d_bias1_};
+    void *bufs[] = {bank_mem_[0], bank_mem_[1], ibank_mem_[0], ibank_mem_[1], d_cond_, d_noise_,
+                    d_exit_, d_slots_, d_stats_, d_counts_, d_bias1_};
     for (void *b : bufs)
       if (b) cudaFree(b);
     if (h_counts_) cudaFreeHost(h_counts_);
@@ -507,6 +621,8 @@ class Engine {
     GMC_CUDA_TRY(ctx_, pool_.init(pool_bytes_));
     GMC_CUDA_TRY(ctx_, cudaMalloc(&bank_mem_[0], C_ * kBankBytesPerParticle));
     GMC_CUDA_TRY(ctx_, cudaMalloc(&bank_mem_[1], C_ * kBankBytesPerParticle));
+    GMC_CUDA_TRY(ctx_, cudaMalloc(&ibank_mem_[0], C_ * kIBankBytesPerParticle));
+    GMC_CUDA_TRY(ctx_, cudaMalloc(&ibank_mem_[1], C_ * kIBankBytesPerParticle));
     if (method_ == GMC_METHOD_GMC) {
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_cond_, C_ * 5 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_noise_, C_ * 4 * sizeof(float)));
@@ -515,10 +631,12 @@ class Engine {
     }
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_slots_, kMaxSlots * sizeof(Slot)));
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_stats_, kMaxSlots * sizeof(DevStats)));
-    GMC_CUDA_TRY(ctx_, cudaMalloc(&d_counts_, (kMaxSlots + 1) * sizeof(int)));
-    GMC_CUDA_TRY(ctx_, cudaMallocHost(&h_counts_, (kMaxSlots + 1) * sizeof(int)));
+    GMC_CUDA_TRY(ctx_, cudaMalloc(&d_counts_, kCounts * sizeof(int)));
+    GMC_CUDA_TRY(ctx_, cudaMallocHost(&h_counts_, kCounts * sizeof(int)));
     bank_[0] = carve(bank_mem_[0], C_);
     bank_[1] = carve(bank_mem_[1], C_);
+    ibank_[0] = carve_inside(ibank_mem_[0], C_);
+    ibank_[1] = carve_inside(ibank_mem_[1], C_);
     for (auto &r : reqs_) r = nullptr;
     return GMC_OK;
   }
@@ -573,18 +691,22 @@ class Engine {
     return true;
   }
 
-  // One wave: births for every request with histories left, one transmission
-  // of every particle in the bank, completion of finished requests.
+  // One wave: births for every request with histories left, one step of
+  // every particle in the banks (a transmission of each face particle, up to
+  // flights_per_wave flights of each walk in progress), completion of
+  // finished requests.
   gmc_status step(std::vector<Request *> &completed) {
     const Rules rules{(float)ctx_->cfg.w_cut, (float)ctx_->cfg.p_survive};
-    int *d_count = d_counts_, *d_slot_live = d_counts_ + 1;
-    // births: fair share of the free bank among requests with histories left
+    const uint32_t cap = (uint32_t)ctx_->cfg.flights_per_wave;
+    int *d_face = d_counts_, *d_in = d_counts_ + 1, *d_slot_live = d_counts_ + 2;
+    // births: fair share of the free room among requests with histories left
     int pending = 0;
     for (auto *R : reqs_)
       if (R && R->next_hist < R->n_hist) ++pending;
-    int64_t room = C_ - live_;
+    int64_t room = C_ - live_ - live_in_;
     if (pending > 0 && room > 0) {
-      GMC_CUDA_TRY(ctx_, cudaMemcpyAsync(d_count, &live_i_, sizeof(int), cudaMemcpyHostToDevice, s_));
+      in0_ = (int)live_in_;
+      GMC_CUDA_TRY(ctx_, cudaMemcpyAsync(d_in, &in0_, sizeof(int), cudaMemcpyHostToDevice, s_));
       GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_slot_live, 0, kMaxSlots * sizeof(int), s_));
       int left = pending;
       for (auto *R : reqs_) {
@@ -595,26 +717,31 @@ class Engine {
         if (m <= 0) continue;
         room -= m;
         birth_kernel<<<nblocks(m, 256), 256, 0, s_>>>(R->slot, R->next_hist, m, R->d_cdf, R->total,
-                                                       d_slots_, rules, bank_[cur_], d_count,
-                                                       d_stats_, d_slot_live);
+                                                       d_slots_, ibank_[cin_], d_in, d_slot_live);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
         R->next_hist += m;
       }
       GMC_CUDA_TRY(ctx_, read_counts());
-      live_ = h_counts_[0];
+      live_in_ = h_counts_[1];
       for (auto *R : reqs_)
-        if (R) R->live += h_counts_[1 + R->slot];
+        if (R) R->live += h_counts_[2 + R->slot];
     }
-    if (live_ > 0) {
+    if (live_ + live_in_ > 0) {
       ++waves_;
-      const int nxt = cur_ ^ 1;
-      GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_counts_, 0, (kMaxSlots + 1) * sizeof(int), s_));
-      if (method_ == GMC_METHOD_ANALOG) {
-        analog_wave_kernel<<<nblocks(live_, 128), 128, 0, s_>>>(live_, bank_[cur_], d_slots_, rules,
-                                                                bank_[nxt], d_count, d_stats_,
-                                                                d_slot_live);
+      const int nxt = cur_ ^ 1, nin = cin_ ^ 1;
+      GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_counts_, 0, kCounts * sizeof(int), s_));
+      if (live_in_ > 0) {
+        inside_walk_kernel<<<nblocks(live_in_, 128), 128, 0, s_>>>(
+            live_in_, ibank_[cin_], d_slots_, rules, cap, bank_[nxt], d_face, ibank_[nin], d_in,
+            d_stats_, d_slot_live);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
-      } else {
+      }
+      if (live_ > 0 && method_ == GMC_METHOD_ANALOG) {
+        analog_wave_kernel<<<nblocks(live_, 128), 128, 0, s_>>>(live_, bank_[cur_], d_slots_, rules,
+                                                                cap, bank_[nxt], d_face, ibank_[nin],
+                                                                d_in, d_stats_, d_slot_live);
+        GMC_CUDA_TRY(ctx_, cudaGetLastError());
+      } else if (live_ > 0) {
         gmc_prep_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_slots_, d_cond_,
                                                              d_noise_);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
@@ -632,21 +759,22 @@ class Engine {
         }
         if (e != cudaSuccess) return cuda_error(ctx_, e, "solve: sampler");
         gmc_post_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_exit_, d_slots_,
-                                                             rules, bank_[nxt], d_count, d_stats_,
+                                                             rules, bank_[nxt], d_face, d_stats_,
                                                              d_slot_live);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
       }
       GMC_CUDA_TRY(ctx_, read_counts());
       live_ = h_counts_[0];
+      live_in_ = h_counts_[1];
       for (auto *R : reqs_)
-        if (R) R->live = h_counts_[1 + R->slot];
+        if (R) R->live = h_counts_[2 + R->slot];
       cur_ = nxt;
+      cin_ = nin;
       if (method_ == GMC_METHOD_GMC) {
         gmc_status es = check_device_error(ctx_);
         if (es != GMC_OK) return es;
       }
     }
-    live_i_ = (int)live_;
     // completions
     for (int k = 0; k < kMaxSlots; ++k) {
       Request *R = reqs_[k];
@@ -661,7 +789,7 @@ class Engine {
 
  private:
   cudaError_t read_counts() {
-    cudaError_t e = cudaMemcpyAsync(h_counts_, d_counts_, (kMaxSlots + 1) * sizeof(int),
+    cudaError_t e = cudaMemcpyAsync(h_counts_, d_counts_, kCounts * sizeof(int),
                                     cudaMemcpyDeviceToHost, s_);
     if (e) return e;
     return cudaStreamSynchronize(s_);
@@ -706,11 +834,14 @@ class Engine {
   size_t pool_bytes_;
   cudaStream_t s_;
   Pool pool_;
-  void *bank_mem_[2] = {nullptr, nullptr};
+  // counters: [0] face bank, [1] inside bank, [2 ..] live particles per slot
+  static constexpr int kCounts = kMaxSlots + 2;
+  void *bank_mem_[2] = {nullptr, nullptr}, *ibank_mem_[2] = {nullptr, nullptr};
   Bank bank_[2];
-  int cur_ = 0;
-  int64_t live_ = 0;
-  int live_i_ = 0;
+  IBank ibank_[2];
+  int cur_ = 0, cin_ = 0;
+  int64_t live_ = 0, live_in_ = 0;
+  int in0_ = 0;  // host source of the inside-bank count copied before births
   int64_t waves_ = 0;
   float *d_cond_ = nullptr, *d_noise_ = nullptr, *d_exit_ = nullptr, *d_bias1_ = nullptr;
   Slot *d_slots_ = nullptr;

@@ -31,19 +31,23 @@ struct WalkResult {
   uint32_t event;   // next unused Philox event
 };
 
+// Up to max_flights flights of a walk in progress: position (x, y), track
+// length s, direction, next Philox event and collision count are read and
+// updated in place. Status kExited / kAbsorbed ends the walk; kTruncated means
+// max_flights were taken and the walk resumes from the updated state, drawing
+// exactly the random numbers an uninterrupted walk would.
 template <typename T>
-__device__ __forceinline__ WalkResult walk_box(T tau, float c, int implicit, T x, T y, float ux,
-                                               float uy, uint64_t seed, uint64_t id,
-                                               uint32_t event) {
+__device__ __forceinline__ WalkResult walk_box_from(T tau, float c, int implicit, T &x, T &y, T &s,
+                                                    float &ux, float &uy, uint32_t &event,
+                                                    uint32_t &ncoll, uint32_t max_flights,
+                                                    uint64_t seed, uint64_t id) {
   const float rate = implicit ? c : 1.0f;
   const T inf = (T)INFINITY;
-  T s = 0;
-  uint32_t ncoll = 0;
   WalkResult w;
   w.status = kTruncated;
   w.face = -1;
   w.q = 0.0f;
-  for (uint32_t it = 0; it < kMaxFlights; ++it) {
+  for (uint32_t it = 0; it < max_flights; ++it) {
     const uint4 r = philox_draw(seed, id, event, kTagWalk);
     ++event;
     const T d = rate > 0.0f ? (T)(-logf(u01(r.x)) / rate) : inf;
@@ -90,6 +94,70 @@ __device__ __forceinline__ WalkResult walk_box(T tau, float c, int implicit, T x
   w.s = (float)s;
   w.ncoll = ncoll;
   w.event = event;
+  return w;
+}
+
+template <typename T>
+__device__ __forceinline__ WalkResult walk_box(T tau, float c, int implicit, T x, T y, float ux,
+                                               float uy, uint64_t seed, uint64_t id,
+                                               uint32_t event) {
+  T s = 0;
+  uint32_t ncoll = 0;
+  return walk_box_from(tau, c, implicit, x, y, s, ux, uy, event, ncoll, kMaxFlights, seed, id);
+}
+
+// A walk in progress inside a cell, in optical units. Positions and track
+// length hold values of the precision the cell walks in (float below
+// kTau64, double above), so a resumed walk continues bit for bit.
+struct WalkState {
+  double x, y, s;
+  float ux, uy;
+  uint32_t event, ncoll;
+};
+
+// Start of a walk at the point (X, Y) in normalized cell coordinates.
+__device__ __forceinline__ WalkState walk_start(float tau, float X, float Y, float ux, float uy,
+                                                uint32_t event) {
+  WalkState st;
+  if (tau > kTau64) {
+    st.x = (double)X * (double)tau;
+    st.y = (double)Y * (double)tau;
+  } else {
+    st.x = (double)(X * tau);
+    st.y = (double)(Y * tau);
+  }
+  st.s = 0.0;
+  st.ux = ux;
+  st.uy = uy;
+  st.event = event;
+  st.ncoll = 0;
+  return st;
+}
+
+// Up to max_flights more flights of the walk in `st` (updated in place); a
+// walk whose total collisions reach kMaxFlights ends as kTruncated with
+// face -1 regardless of max_flights.
+__device__ __forceinline__ WalkResult walk_cell_resume(float tau, float c, int implicit,
+                                                       WalkState &st, uint32_t max_flights,
+                                                       uint64_t seed, uint64_t id) {
+  const uint32_t left = st.ncoll < kMaxFlights ? kMaxFlights - st.ncoll : 0u;
+  const uint32_t cap = max_flights < left ? max_flights : left;
+  WalkResult w;
+  if (tau > kTau64) {
+    double x = st.x, y = st.y, s = st.s;
+    w = walk_box_from<double>((double)tau, c, implicit, x, y, s, st.ux, st.uy, st.event, st.ncoll,
+                              cap, seed, id);
+    st.x = x;
+    st.y = y;
+    st.s = s;
+  } else {
+    float x = (float)st.x, y = (float)st.y, s = (float)st.s;
+    w = walk_box_from<float>(tau, c, implicit, x, y, s, st.ux, st.uy, st.event, st.ncoll, cap, seed,
+                             id);
+    st.x = x;
+    st.y = y;
+    st.s = s;
+  }
   return w;
 }
 

@@ -138,3 +138,26 @@ def test_solve_edge_cases(gpu_ctx, kaiming_net):
     # BF16 rows are independent) up to FP64 summation order
     np.testing.assert_allclose(f1, f2, rtol=1e-9, atol=1e-12)
     assert s1["transmissions"] == s2["transmissions"]
+
+
+@pytest.mark.parametrize("method", ["analog", "gmc"])
+def test_flight_cap_changes_no_result(gpu_ctx, kaiming_net, method):
+    # Walks cut at flights_per_wave resume with the same random numbers, so the
+    # flux is the same for any cap up to the order of the FP64 tally additions;
+    # thick cells (FP64 positions) and thin ones both appear.
+    import paper_2512_13965_gb300 as g
+    m = g.GMC_METHOD_ANALOG if method == "analog" else g.GMC_METHOD_GMC
+    tau, c, src = synth.grid_problem(n=12, seed=33, tau_range=(0.1, 300.0), block=4, source=4)
+    out = []
+    for cap in (1 << 20, 512, 3):
+        _set(gpu_ctx, bank_capacity=1 << 14, flights_per_wave=cap, precision=g.GMC_FP32, steps=4)
+        f, st = _solve(gpu_ctx, tau, c, src, 3000, m, 17)
+        out.append((f, st))
+    _set(gpu_ctx, flights_per_wave=512)
+    f0, s0 = out[0]
+    for f, st in out[1:]:
+        np.testing.assert_allclose(f, f0, rtol=1e-9, atol=1e-12 * np.abs(f0).max())
+        assert st["transmissions"] == s0["transmissions"]
+        assert st["collisions"] == s0["collisions"]
+        assert st["roulette_kills"] == s0["roulette_kills"]
+    assert out[2][1]["waves"] > out[0][1]["waves"]  # the cap did cut walks
