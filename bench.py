@@ -177,6 +177,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--workload", default="sampler", choices=["sampler", "solve", "serve", "sweep", "heldout"])
     ap.add_argument("--weights", default=None, help="GMCW file (default: Kaiming seed 1)")
+    ap.add_argument("--internal-weights", default=None,
+                    help="GMCW file of the internal-source model (solve/serve: births sampled by it)")
     ap.add_argument("--histories", type=float, default=1e6)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--solve-variants", default=None,
@@ -359,6 +361,8 @@ def _context(args):
     import paper_2512_13965_gb300 as g
     torch.cuda.set_device(0)
     ctx = g.Context(0)
+    if getattr(args, "internal_weights", None):
+        g.gmc_load_internal_weights(ctx, args.internal_weights)
     if args.weights:
         g.gmc_load_weights(ctx, args.weights)
     else:
@@ -426,6 +430,7 @@ def run_solve(args):
                     "flux_rel_err_vs_analog": None if f_mc is None else rel(f, f_mc)}
     line = {"metric": METRIC, "workload": "transport solve 128x128, tau logU[0.1,500], c {0.5,0.999} "
             "16x16 blocks, central 8x8 source, %d histories" % n, "weights": args.weights or "kaiming seed 1 (untrained)",
+            "births": ("internal model " + args.internal_weights) if args.internal_weights else "random walk",
             "results": out, "unit": "cell transmissions/s"}
     print(json.dumps(line))
     ctx.close()

@@ -146,6 +146,20 @@ gmc_status gmc_load_weights(gmc_ctx *ctx, const char *path);
 gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes);
 
 /*
+ * Internal (volumetric-source) model: the second network of the method
+ * (section "Network Architecture and Inputs": an internal model for particles
+ * born inside a cell, a boundary model for particles crossing between cells).
+ * Same GMCW layout; its condition is (X, Y, ln tau, c, d) for a birth at
+ * (X, Y) in [0,1]^2 of the cell, d = min(X, Y, 1 - X, 1 - Y), and its state the
+ * exit (p, cos, sin, ln s) in the cell's own frame. The birth direction is
+ * isotropic and not a condition: the network samples the exit marginalized
+ * over it. When loaded, GMC solves sample births with it (births otherwise
+ * take the random walk). Errors as gmc_load_weights.
+ */
+gmc_status gmc_load_internal_weights(gmc_ctx *ctx, const char *path);
+gmc_status gmc_load_internal_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes);
+
+/*
  * Samples n exit states (Eq. 8, Eq. 11) with the loaded network.
  *  cond    [5][n] float: xi, cos theta_in, sin theta_in, ln tau, c (raw,
  *          standardized inside with the file's cond_mean / cond_std).
@@ -167,6 +181,11 @@ gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes
 gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
                         uint64_t seed, uint64_t id0, int steps, int integrator, int precision,
                         float *y_raw, float *exit);
+/* gmc_transmit with the internal model: cond [5][n] = (X, Y, ln tau, c, d) as
+   above, exits in the cell's own frame; GMC_ENOWEIGHTS if none is loaded. */
+gmc_status gmc_sample_internal(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
+                               uint64_t seed, uint64_t id0, int steps, int integrator,
+                               int precision, float *y_raw, float *exit);
 
 /*
  * gmc_transmit without any device allocation during the call (the paper has
@@ -306,6 +325,16 @@ typedef struct gmc_train_config {
  */
 gmc_status gmc_train_data(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, float tau_hi,
                           float c_lo, float c_hi, float *cond, float *y);
+/*
+ * Training data of the internal model: for sample i, Philox block (i, 0, tag 7)
+ * gives ln tau uniform in [ln tau_lo, ln tau_hi], c uniform in [c_lo, c_hi],
+ * X and Y uniform; (i, 1, tag 7) the isotropic birth direction; the
+ * implicit-capture walk from (X, Y) draws from event 2 on.
+ * cond [5][n] = (X, Y, ln tau, c, min(X, Y, 1 - X, 1 - Y)), y [4][n] =
+ * (p, cos, sin, ln s) in the cell's own frame: device memory.
+ */
+gmc_status gmc_train_data_internal(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo,
+                                   float tau_hi, float c_lo, float c_hi, float *cond, float *y);
 /*
  * Starts training on the device dataset (cond, y as gmc_train_data writes;
  * the caller keeps them alive while training). Standardization statistics

@@ -15,7 +15,8 @@
     4. rotate the exit back to global coordinates and cross into the
        neighbour; stop at the domain edge, roulette below the weight cutoff.
   Births in a source cell are walked to their first face crossing with the
-  random walk (the paper's separate internal-source model is not built).
+  random walk, or, given an internal sampler (the paper's internal model for
+  volumetric sources), their exit from the birth cell is sampled by it.
 
 Global faces use the same counter-clockwise numbering as a cell in its own
 frame: 0 = south (y-), 1 = east (x+), 2 = north (y+), 3 = west (x-). A
@@ -139,8 +140,48 @@ def walk_sampler(seed):
     return f
 
 
-def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max_waves=100000):
-    """Event-based GMC solve; tau, c, src are [ny, nx]. Returns (flux, stats)."""
+def internal_condition(X, Y, tau, c):
+    """Condition of the internal model for births at (X, Y) in [0,1]^2 of a cell:
+    (X, Y, ln tau, c, distance to the nearest face in cell units) -> [5, B]."""
+    X, Y, tau, c = (np.asarray(a, dtype=np.float64) for a in (X, Y, tau, c))
+    d = np.minimum(np.minimum(X, Y), np.minimum(1.0 - X, 1.0 - Y))
+    return np.stack([X, Y, np.log(tau), c, d])
+
+
+def mlp_internal_sampler(net, steps, integrator, seed):
+    """Births with the internal model: exit (cell frame) from the flow ODE with
+    noise at (id, 0, TAG_NOISE); the next event is 1."""
+    def f(X, Y, tau, c, ids, u_angle):
+        cond = internal_condition(X, Y, tau, c)
+        ids = np.asarray(ids, np.uint64)
+        z = rng.normals_for(seed, ids, np.zeros(ids.size, np.uint32), rng.TAG_NOISE)
+        d = mlp.decode(net, mlp.sample(net, cond, z, steps, integrator))
+        return d["face"], d["q"], d["ux"], d["uy"], d["s"], np.ones(ids.size, np.uint32)
+    return f
+
+
+def walk_internal_sampler(seed):
+    """Births walked exactly as the random-walk solve does: direction from the
+    birth draw, implicit-capture walk from event 0."""
+    def f(X, Y, tau, c, ids, u_angle):
+        out = [np.zeros(len(ids)) for _ in range(5)] + [np.zeros(len(ids), np.uint32)]
+        for k in range(len(ids)):
+            ang = 2.0 * np.pi * u_angle[k]
+            r = walk_one(tau[k], c[k], MODE_IMPLICIT, X[k] * tau[k], Y[k] * tau[k], np.cos(ang),
+                         np.sin(ang), seed, int(ids[k]), 0)
+            for a, v in zip(out, (r["face"], r["q"], r["ux"], r["uy"], r["s"], r["event"])):
+                a[k] = v
+        return out[0].astype(np.int64), out[1], out[2], out[3], out[4], out[5]
+    return f
+
+
+def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max_waves=100000,
+              internal=None):
+    """Event-based GMC solve; tau, c, src are [ny, nx]. Returns (flux, stats).
+
+    internal: sampler of births (mlp_internal_sampler / walk_internal_sampler),
+    or None to walk every birth with walk_one.
+    """
     tau = np.asarray(tau, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)
     ny, nx = tau.shape
@@ -154,9 +195,25 @@ def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max
     ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
     cells = np.searchsorted(cdf, ub[0] * total, side="left")
 
-    # Births: walk from the birth point to the first face crossing (cell frame).
+    # Births: walk from the birth point to the first face crossing (cell frame),
+    # or sample that exit with the internal model.
     live = {k: [] for k in ("id", "i", "j", "F", "xi", "gx", "gy", "w", "ev")}
-    for h in range(n_hist):
+    if internal is not None:
+        face, q, ux, uy, s, ev = internal(ub[1], ub[2], tf[cells], cf[cells], ids, ub[3])
+        for h in range(n_hist):
+            k = int(cells[h])
+            st[3] += 1
+            dw, score = deposit(1.0, s[h], tf[k], cf[k])
+            flux[k] += score
+            st[1] += dw
+            w = 1.0 - dw
+            w, alive = _roulette(seed, np.array([h], np.uint64), np.array([ev[h]], np.uint32),
+                                 np.array([w]), w_cut, p_survive, st)
+            if not alive[0]:
+                continue
+            _advance_one(live, h, k % nx, k // nx, int(face[h]), q[h], ux[h], uy[h], w[0],
+                         int(ev[h]), nx, ny, st)
+    for h in range(n_hist if internal is None else 0):
         k = int(cells[h])
         i, j = k % nx, k // nx
         t, cc = tf[k], cf[k]

@@ -79,6 +79,9 @@ def _load():
         "gmc_normals": [P, i64, u64, u64, u32, u32, P],
         "gmc_load_weights": [P, ctypes.c_char_p],
         "gmc_load_weights_buffer": [P, P, sz],
+        "gmc_load_internal_weights": [P, ctypes.c_char_p],
+        "gmc_load_internal_weights_buffer": [P, P, sz],
+        "gmc_sample_internal": [P, i64, P, P, u64, u64, i32, i32, i32, P, P],
         "gmc_transmit": [P, i64, P, P, u64, u64, i32, i32, i32, P, P],
         "gmc_transmit_noalloc": [P, i64, P, P, u64, u64, i32, i32, P, P],
         "analog_transmit": [P, i64, P, P, P, P, P, i32, u64, u64, u32, P, P, P],
@@ -91,6 +94,8 @@ def _load():
         "gmc_serve_stop": [P],
         "gmc_train_data": [P, i64, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            ctypes.c_float, P, P],
+        "gmc_train_data_internal": [P, i64, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, P, P],
         "gmc_train_begin": [P, i64, P, P, ctypes.POINTER(gmc_train_config)],
         "gmc_train_steps": [P, i64, P],
         "gmc_train_set_lr": [P, ctypes.c_double],
@@ -210,6 +215,22 @@ def gmc_load_weights_buffer(ctx, blob):
     return ctx.check(lib.gmc_load_weights_buffer(ctx.handle, ctypes.addressof(buf), len(blob)))
 
 
+def gmc_load_internal_weights(ctx, path):
+    return ctx.check(lib.gmc_load_internal_weights(ctx.handle, os.fsencode(path)))
+
+
+def gmc_load_internal_weights_buffer(ctx, blob):
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    return ctx.check(lib.gmc_load_internal_weights_buffer(ctx.handle, ctypes.addressof(buf),
+                                                          len(blob)))
+
+
+def gmc_sample_internal(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw, exit):
+    return ctx.check(lib.gmc_sample_internal(ctx.handle, n, _ptr(cond), _ptr(noise), seed, id0,
+                                             steps, integrator, precision, _ptr(y_raw),
+                                             _ptr(exit)))
+
+
 def gmc_transmit(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw, exit):
     return ctx.check(lib.gmc_transmit(ctx.handle, n, _ptr(cond), _ptr(noise), seed, id0, steps,
                                       integrator, precision, _ptr(y_raw), _ptr(exit)))
@@ -237,6 +258,11 @@ def transport_solve(ctx, nx, ny, tau, c, source, n_histories, method, seed, flux
 def gmc_train_data(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
     return ctx.check(lib.gmc_train_data(ctx.handle, n, seed, tau_lo, tau_hi, c_lo, c_hi,
                                         _ptr(cond), _ptr(y)))
+
+
+def gmc_train_data_internal(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
+    return ctx.check(lib.gmc_train_data_internal(ctx.handle, n, seed, tau_lo, tau_hi, c_lo, c_hi,
+                                                 _ptr(cond), _ptr(y)))
 
 
 def gmc_train_begin(ctx, n, cond, y, cfg):

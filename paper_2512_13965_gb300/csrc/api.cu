@@ -195,11 +195,16 @@ gmc_status gmc_destroy(gmc_ctx *ctx) {
     if (b.ptr) cudaFree(b.ptr);
   if (ctx->bias1.ptr) cudaFree(ctx->bias1.ptr);
   if (ctx->train) train_state_free(ctx->train);
-  if (ctx->d_f32) cudaFree(ctx->d_f32);
-  if (ctx->d_tc) cudaFree(ctx->d_tc);
-  if (ctx->d_tc_bias) cudaFree(ctx->d_tc_bias);
-  if (ctx->d_tc8) cudaFree(ctx->d_tc8);
-  if (ctx->d_tc8_scale) cudaFree(ctx->d_tc8_scale);
+  if (ctx->net.d_f32) cudaFree(ctx->net.d_f32);
+  if (ctx->net.d_tc) cudaFree(ctx->net.d_tc);
+  if (ctx->net.d_tc_bias) cudaFree(ctx->net.d_tc_bias);
+  if (ctx->net.d_tc8) cudaFree(ctx->net.d_tc8);
+  if (ctx->net.d_tc8_scale) cudaFree(ctx->net.d_tc8_scale);
+  if (ctx->internal.d_f32) cudaFree(ctx->internal.d_f32);
+  if (ctx->internal.d_tc) cudaFree(ctx->internal.d_tc);
+  if (ctx->internal.d_tc_bias) cudaFree(ctx->internal.d_tc_bias);
+  if (ctx->internal.d_tc8) cudaFree(ctx->internal.d_tc8);
+  if (ctx->internal.d_tc8_scale) cudaFree(ctx->internal.d_tc8_scale);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   delete ctx;
@@ -273,8 +278,11 @@ gmc_status gmc_normals(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uin
   return GMC_OK;
 }
 
-gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes) {
-  if (!ctx || !blob) return set_error(ctx, GMC_EINVAL, "gmc_load_weights_buffer: null argument");
+}  // extern "C"
+
+namespace gmc {
+// Parses a GMCW version 1 blob into N and uploads its FP32, BF16 and FP8 copies.
+gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   static const uint32_t dims_ok[6] = {25, 256, 256, 256, 256, 4};
   Reader rd{(const unsigned char *)blob, nbytes};
   if (nbytes < 4 || std::memcmp(blob, "GMCW", 4) != 0)
@@ -293,7 +301,7 @@ gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes
   float st[18];
   if (!rd.f32(st, 18)) return set_error(ctx, GMC_EFORMAT, "weight file: truncated statistics");
   for (int l = 0; l < 5; ++l) {
-    if (!rd.f32(ctx->host_w[l], (size_t)dims[l + 1] * dims[l]) || !rd.f32(ctx->host_b[l], dims[l + 1]))
+    if (!rd.f32(N.host_w[l], (size_t)dims[l + 1] * dims[l]) || !rd.f32(N.host_b[l], dims[l + 1]))
       return set_error(ctx, GMC_EFORMAT, "weight file: truncated layer %d", l);
   }
   if (rd.off != nbytes) return set_error(ctx, GMC_EFORMAT, "weight file: trailing bytes");
@@ -324,81 +332,120 @@ gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes
   float *w5 = p; p += 4 * 256;
   float *b5 = p; p += 4;
   for (int c = 0; c < 256; ++c)
-    for (int k = 0; k < 25; ++k) w1t[k * 256 + c] = ctx->host_w[0][c * 25 + k];
-  std::memcpy(b1, ctx->host_b[0], 256 * 4);
+    for (int k = 0; k < 25; ++k) w1t[k * 256 + c] = N.host_w[0][c * 25 + k];
+  std::memcpy(b1, N.host_b[0], 256 * 4);
   for (int l = 0; l < 3; ++l) {
     for (int c = 0; c < 256; ++c)
-      for (int k = 0; k < 256; ++k) wt[l][k * 256 + c] = ctx->host_w[l + 1][c * 256 + k];
-    std::memcpy(bt[l], ctx->host_b[l + 1], 256 * 4);
+      for (int k = 0; k < 256; ++k) wt[l][k * 256 + c] = N.host_w[l + 1][c * 256 + k];
+    std::memcpy(bt[l], N.host_b[l + 1], 256 * 4);
   }
-  std::memcpy(w5, ctx->host_w[4], 4 * 256 * 4);
-  std::memcpy(b5, ctx->host_b[4], 4 * 4);
+  std::memcpy(w5, N.host_w[4], 4 * 256 * 4);
+  std::memcpy(b5, N.host_b[4], 4 * 4);
 
   cudaSetDevice(ctx->device);
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  if (!ctx->d_f32) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_f32, total * sizeof(float)));
-  GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_f32, h.data(), total * sizeof(float), cudaMemcpyHostToDevice));
-  float *d = ctx->d_f32;
-  ctx->f32.w1t = d; d += n1;
-  ctx->f32.b1 = d; d += 256;
-  ctx->f32.w2t = d; d += nh;
-  ctx->f32.b2 = d; d += 256;
-  ctx->f32.w3t = d; d += nh;
-  ctx->f32.b3 = d; d += 256;
-  ctx->f32.w4t = d; d += nh;
-  ctx->f32.b4 = d; d += 256;
-  ctx->f32.w5 = d; d += 4 * 256;
-  ctx->f32.b5 = d;
+  if (!N.d_f32) GMC_CUDA_TRY(ctx, cudaMalloc(&N.d_f32, total * sizeof(float)));
+  GMC_CUDA_TRY(ctx, cudaMemcpy(N.d_f32, h.data(), total * sizeof(float), cudaMemcpyHostToDevice));
+  float *d = N.d_f32;
+  N.f32.w1t = d; d += n1;
+  N.f32.b1 = d; d += 256;
+  N.f32.w2t = d; d += nh;
+  N.f32.b2 = d; d += 256;
+  N.f32.w3t = d; d += nh;
+  N.f32.b3 = d; d += 256;
+  N.f32.w4t = d; d += nh;
+  N.f32.b4 = d; d += 256;
+  N.f32.w5 = d; d += 4 * 256;
+  N.f32.b5 = d;
 
   // packed operands of the tensor-core path (BF16 and FP8 variants)
   {
     const size_t tcb = tc_packed_bytes(false), tcb8 = tc_packed_bytes(true);
     std::vector<unsigned char> packed(tcb), packed8(tcb8);
     std::vector<float> bias(5 * 256, 0.0f), scale(3 * 256, 0.0f);
-    tc_pack_host(ctx->host_w, ctx->host_b, packed.data(), bias.data());
-    tc_pack_host_fp8(ctx->host_w, ctx->host_b, packed8.data(), bias.data(), scale.data());
-    if (!ctx->d_tc) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_tc, tcb));
-    if (!ctx->d_tc8) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_tc8, tcb8));
-    if (!ctx->d_tc_bias) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_tc_bias, 5 * 256 * sizeof(float)));
-    if (!ctx->d_tc8_scale) GMC_CUDA_TRY(ctx, cudaMalloc(&ctx->d_tc8_scale, 3 * 256 * sizeof(float)));
-    GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_tc, packed.data(), tcb, cudaMemcpyHostToDevice));
-    GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_tc8, packed8.data(), tcb8, cudaMemcpyHostToDevice));
-    GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_tc_bias, bias.data(), 5 * 256 * sizeof(float),
+    tc_pack_host(N.host_w, N.host_b, packed.data(), bias.data());
+    tc_pack_host_fp8(N.host_w, N.host_b, packed8.data(), bias.data(), scale.data());
+    if (!N.d_tc) GMC_CUDA_TRY(ctx, cudaMalloc(&N.d_tc, tcb));
+    if (!N.d_tc8) GMC_CUDA_TRY(ctx, cudaMalloc(&N.d_tc8, tcb8));
+    if (!N.d_tc_bias) GMC_CUDA_TRY(ctx, cudaMalloc(&N.d_tc_bias, 5 * 256 * sizeof(float)));
+    if (!N.d_tc8_scale) GMC_CUDA_TRY(ctx, cudaMalloc(&N.d_tc8_scale, 3 * 256 * sizeof(float)));
+    GMC_CUDA_TRY(ctx, cudaMemcpy(N.d_tc, packed.data(), tcb, cudaMemcpyHostToDevice));
+    GMC_CUDA_TRY(ctx, cudaMemcpy(N.d_tc8, packed8.data(), tcb8, cudaMemcpyHostToDevice));
+    GMC_CUDA_TRY(ctx, cudaMemcpy(N.d_tc_bias, bias.data(), 5 * 256 * sizeof(float),
                                  cudaMemcpyHostToDevice));
-    GMC_CUDA_TRY(ctx, cudaMemcpy(ctx->d_tc8_scale, scale.data(), 3 * 256 * sizeof(float),
+    GMC_CUDA_TRY(ctx, cudaMemcpy(N.d_tc8_scale, scale.data(), 3 * 256 * sizeof(float),
                                  cudaMemcpyHostToDevice));
-    ctx->tc_bytes = tcb;
+    N.tc_bytes = tcb;
   }
-  ctx->stats = ns;
-  ctx->has_weights = true;
+  N.stats = ns;
+  N.loaded = true;
   return GMC_OK;
 }
 
-gmc_status gmc_load_weights(gmc_ctx *ctx, const char *path) {
-  if (!ctx || !path) return set_error(ctx, GMC_EINVAL, "gmc_load_weights: null argument");
+
+// Reads a whole file; false (with the context error set) on failure.
+bool read_file(gmc_ctx *ctx, const char *path, std::vector<unsigned char> &blob, gmc_status *st) {
   FILE *f = std::fopen(path, "rb");
-  if (!f) return set_error(ctx, GMC_EIO, "cannot open weight file '%s'", path);
-  std::vector<unsigned char> blob;
+  if (!f) {
+    *st = set_error(ctx, GMC_EIO, "cannot open weight file '%s'", path);
+    return false;
+  }
   unsigned char buf[1 << 16];
   size_t got;
   while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) blob.insert(blob.end(), buf, buf + got);
   const bool err = std::ferror(f) != 0;
   std::fclose(f);
-  if (err) return set_error(ctx, GMC_EIO, "read error on '%s'", path);
-  return gmc_load_weights_buffer(ctx, blob.data(), blob.size());
+  if (err) {
+    *st = set_error(ctx, GMC_EIO, "read error on '%s'", path);
+    return false;
+  }
+  return true;
 }
 
-gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
-                        uint64_t seed, uint64_t id0, int steps, int integrator, int precision,
-                        float *y_raw, float *exit) {
-  if (!ctx) return GMC_EINVAL;
+}  // namespace gmc
+
+extern "C" {
+
+gmc_status gmc_load_weights(gmc_ctx *ctx, const char *path) {
+  if (!ctx || !path) return set_error(ctx, GMC_EINVAL, "gmc_load_weights: null argument");
+  std::vector<unsigned char> blob;
+  gmc_status st;
+  if (!read_file(ctx, path, blob, &st)) return st;
+  return load_net(ctx, ctx->net, blob.data(), blob.size());
+}
+
+gmc_status gmc_load_internal_weights(gmc_ctx *ctx, const char *path) {
+  if (!ctx || !path) return set_error(ctx, GMC_EINVAL, "gmc_load_internal_weights: null argument");
+  std::vector<unsigned char> blob;
+  gmc_status st;
+  if (!read_file(ctx, path, blob, &st)) return st;
+  return load_net(ctx, ctx->internal, blob.data(), blob.size());
+}
+
+gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes) {
+  if (!ctx || !blob) return set_error(ctx, GMC_EINVAL, "gmc_load_weights_buffer: null argument");
+  return load_net(ctx, ctx->net, blob, nbytes);
+}
+
+gmc_status gmc_load_internal_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes) {
+  if (!ctx || !blob) return set_error(ctx, GMC_EINVAL, "gmc_load_internal_weights_buffer: null argument");
+  return load_net(ctx, ctx->internal, blob, nbytes);
+}
+
+}  // extern "C"
+
+namespace gmc {
+// gmc_transmit with network N (the boundary or the internal model).
+gmc_status transmit_net(gmc_ctx *ctx, const NetDev &N, int64_t n, const float *cond,
+                        const float *noise, uint64_t seed, uint64_t id0, int steps, int integrator,
+                        int precision, float *y_raw, float *exit) {
   if (n < 0) return set_error(ctx, GMC_EINVAL, "gmc_transmit: n < 0");
   if (n == 0) return GMC_OK;
   if (!cond || (!y_raw && !exit)) return set_error(ctx, GMC_EINVAL, "gmc_transmit: null array");
   if (steps < 1 || steps > 256) return set_error(ctx, GMC_EINVAL, "gmc_transmit: steps in [1,256]");
   if (integrator != GMC_EULER && integrator != GMC_MIDPOINT && integrator != GMC_RK4)
     return set_error(ctx, GMC_EINVAL, "gmc_transmit: unknown integrator");
-  if (!ctx->has_weights) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_transmit: no weights loaded");
+  if (!N.loaded) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_transmit: no weights loaded for this model");
   if (precision != GMC_FP32 && precision != GMC_BF16 && precision != GMC_FP8)
     return set_error(ctx, GMC_EINVAL, "gmc_transmit: unknown precision");
   cudaSetDevice(ctx->device);
@@ -412,17 +459,17 @@ gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float 
   GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 2, a_y));
   GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 3, a_exit));
   if (precision == GMC_FP32) {
-    GMC_CUDA_TRY(ctx, launch_sampler_f32(ctx->stream, ctx->f32, ctx->stats, n, (const float *)a_cond.dev,
+    GMC_CUDA_TRY(ctx, launch_sampler_f32(ctx->stream, N.f32, N.stats, n, (const float *)a_cond.dev,
                                          (const float *)a_noise.dev, seed, id0, steps, integrator,
                                          (float *)a_y.dev, (float *)a_exit.dev));
   } else {
     const bool fp8 = precision == GMC_FP8;
     GMC_CUDA_TRY(ctx, ensure(ctx->bias1, (size_t)4 * steps * 256 * sizeof(float)));
-    cudaError_t e = launch_sampler_tc(ctx->stream, fp8 ? ctx->d_tc8 : ctx->d_tc, ctx->d_tc_bias,
-                                      ctx->f32, ctx->stats, n, (const float *)a_cond.dev,
+    cudaError_t e = launch_sampler_tc(ctx->stream, fp8 ? N.d_tc8 : N.d_tc, N.d_tc_bias,
+                                      N.f32, N.stats, n, (const float *)a_cond.dev,
                                       (const float *)a_noise.dev, seed, id0, steps, integrator,
                                       (float *)a_y.dev, (float *)a_exit.dev, ctx->d_err,
-                                      (float *)ctx->bias1.ptr, fp8 ? ctx->d_tc8_scale : nullptr);
+                                      (float *)ctx->bias1.ptr, fp8 ? N.d_tc8_scale : nullptr);
     if (e != cudaSuccess) return cuda_error(ctx, e, "launch_sampler_tc");
   }
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, a_y));
@@ -432,6 +479,26 @@ gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float 
     return check_device_error(ctx);
   }
   return GMC_OK;
+}
+
+}  // namespace gmc
+
+extern "C" {
+
+gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
+                        uint64_t seed, uint64_t id0, int steps, int integrator, int precision,
+                        float *y_raw, float *exit) {
+  if (!ctx) return GMC_EINVAL;
+  return transmit_net(ctx, ctx->net, n, cond, noise, seed, id0, steps, integrator, precision,
+                      y_raw, exit);
+}
+
+gmc_status gmc_sample_internal(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
+                               uint64_t seed, uint64_t id0, int steps, int integrator,
+                               int precision, float *y_raw, float *exit) {
+  if (!ctx) return GMC_EINVAL;
+  return transmit_net(ctx, ctx->internal, n, cond, noise, seed, id0, steps, integrator, precision,
+                      y_raw, exit);
 }
 
 gmc_status analog_transmit(gmc_ctx *ctx, int64_t n, const float *xi, const float *cos_in,

@@ -44,6 +44,23 @@ struct Buffer {
   size_t bytes = 0;
 };
 
+// One loaded velocity network: host copy of the file's layers, the FP32
+// transposed block of the SIMT path, and the packed BF16 and FP8 operands of
+// the tensor-core path.
+struct NetDev {
+  bool loaded = false;
+  float host_w[5][256 * 256];  // W_l[out][in] as in the file (unused tail for small layers)
+  float host_b[5][256];
+  NetStats stats{};
+  float *d_f32 = nullptr;  // FP32 transposed block
+  NetF32 f32{};
+  void *d_tc = nullptr;  // packed BF16 operands
+  size_t tc_bytes = 0;
+  float *d_tc_bias = nullptr;    // per-layer biases for the tensor-core path
+  void *d_tc8 = nullptr;         // packed operands of the FP8 variant (E4M3 W2..W4)
+  float *d_tc8_scale = nullptr;  // [3][256] per-output-channel scales of W2..W4, halved
+};
+
 }  // namespace gmc
 
 struct gmc_ctx {
@@ -54,19 +71,11 @@ struct gmc_ctx {
   gmc_config cfg{};
   std::mutex mu;
 
-  // weights
-  bool has_weights = false;
-  float host_w[5][256 * 256];  // unused tail for small layers
-  float host_b[5][256];
-  gmc::NetStats stats{};
-  float *d_f32 = nullptr;  // FP32 transposed block
-  gmc::NetF32 f32{};
-  void *d_tc = nullptr;  // packed BF16 operands
-  size_t tc_bytes = 0;
-  float *d_tc_bias = nullptr;  // per-layer biases for the tensor-core path
-  void *d_tc8 = nullptr;       // packed operands of the FP8 variant (E4M3 W2..W4)
-  float *d_tc8_scale = nullptr;  // [3][256] per-output-channel scales of W2..W4, halved
-  int *d_err = nullptr;        // device error word (bounded waits)
+  // networks: the boundary model (cell transmissions, gmc_load_weights) and
+  // the internal model (births inside a source cell, gmc_load_internal_weights)
+  gmc::NetDev net;
+  gmc::NetDev internal;
+  int *d_err = nullptr;  // device error word (bounded waits)
 
   // training state (gmc_train_begin .. gmc_destroy)
   gmc::TrainState *train = nullptr;

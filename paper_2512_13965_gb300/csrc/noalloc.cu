@@ -76,7 +76,7 @@ extern "C" gmc_status gmc_transmit_noalloc(gmc_ctx *ctx, int64_t n, const float 
                      "gmc_transmit_noalloc: steps must be in [1, %d] for this integrator (the "
                      "static scratch holds %d layer-1 bias rows, %d per step), got %d",
                      max_steps, kNoallocMaxEvals, evals_per_step, steps);
-  if (!ctx->has_weights || !ctx->d_tc)
+  if (!ctx->net.loaded || !ctx->net.d_tc)
     return set_error(ctx, GMC_ENOWEIGHTS, "gmc_transmit_noalloc: no weights loaded");
   if (n == 0) return GMC_OK;
   if (!cond || (!y_raw && !exit)) return set_error(ctx, GMC_EINVAL, "gmc_transmit_noalloc: null array");
@@ -89,7 +89,7 @@ extern "C" gmc_status gmc_transmit_noalloc(gmc_ctx *ctx, int64_t n, const float 
   float *scratch = nullptr;
   gmc_status st = scratch_address(ctx, &scratch);
   if (st != GMC_OK) return st;
-  e = launch_sampler_tc(ctx->stream, ctx->d_tc, ctx->d_tc_bias, ctx->f32, ctx->stats, n, cond,
+  e = launch_sampler_tc(ctx->stream, ctx->net.d_tc, ctx->net.d_tc_bias, ctx->net.f32, ctx->net.stats, n, cond,
                         noise, seed, id0, steps, integrator, y_raw, exit, ctx->d_err, scratch,
                         nullptr);
   if (e != cudaSuccess) return cuda_error(ctx, e, "gmc_transmit_noalloc launch");

@@ -30,7 +30,7 @@
 
 namespace gmc {
 
-constexpr uint32_t kTagData = 5u, kTagTrain = 6u;
+constexpr uint32_t kTagData = 5u, kTagTrain = 6u, kTagDataInternal = 7u;
 
 // parameter block offsets (floats): W1 [256][32] (columns 25..31 zero), b1,
 // W2, b2, W3, b3, W4, b4 ([256][256], [256]), W5 [4][256], b5 [4]
@@ -76,6 +76,36 @@ __global__ void data_kernel(int64_t n, uint64_t seed, float ltau_lo, float ltau_
   cond[2 * n + i] = sn;
   cond[3 * n + i] = ltau;
   cond[4 * n + i] = c;
+  y[i] = (float)(w.face < 0 ? 0 : w.face) + w.q;
+  y[n + i] = w.ux;
+  y[2 * n + i] = w.uy;
+  y[3 * n + i] = logf(fmaxf(w.s, kSMin));
+}
+
+// Training data of the internal (volumetric-source) model: a birth at a
+// uniform point (X, Y) of the cell with an isotropic direction, walked with
+// implicit capture to its exit. Philox block (i, 0, tag 7): ln tau, c, X, Y;
+// (i, 1, tag 7): the direction; the walk draws from event 2 on.
+// cond = (X, Y, ln tau, c, min(X, Y, 1 - X, 1 - Y)); y = (p, ux, uy, ln s)
+// in the cell's own frame (p counter-clockwise from corner (0, 0)).
+__global__ void internal_data_kernel(int64_t n, uint64_t seed, float ltau_lo, float ltau_hi,
+                                     float c_lo, float c_hi, float *__restrict__ cond,
+                                     float *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 r = philox_draw(seed, (uint64_t)i, 0u, kTagDataInternal);
+  const float ltau = ltau_lo + (ltau_hi - ltau_lo) * u01(r.x);
+  const float tau = expf(ltau);
+  const float c = c_lo + (c_hi - c_lo) * u01(r.y);
+  const float X = u01(r.z), Y = u01(r.w);
+  float ux, uy;
+  sincospif(2.0f * u01(philox_draw(seed, (uint64_t)i, 1u, kTagDataInternal).x), &uy, &ux);
+  const WalkResult w = walk_cell(tau, c, 1, X, Y, ux, uy, seed, (uint64_t)i, 2u);
+  cond[i] = X;
+  cond[n + i] = Y;
+  cond[2 * n + i] = ltau;
+  cond[3 * n + i] = c;
+  cond[4 * n + i] = fminf(fminf(X, Y), fminf(1.0f - X, 1.0f - Y));
   y[i] = (float)(w.face < 0 ? 0 : w.face) + w.q;
   y[n + i] = w.ux;
   y[2 * n + i] = w.uy;
@@ -430,6 +460,24 @@ gmc_status gmc_train_data(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, 
   return GMC_OK;
 }
 
+gmc_status gmc_train_data_internal(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo,
+                                   float tau_hi, float c_lo, float c_hi, float *cond, float *y) {
+  if (!ctx) return GMC_EINVAL;
+  if (n < 0 || (n > 0 && (!cond || !y)))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_data_internal: bad arguments");
+  if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
+    return set_error(ctx, GMC_EINVAL,
+                     "gmc_train_data_internal: need 0 < tau_lo <= tau_hi, 0 <= c_lo <= c_hi <= 1");
+  if (n == 0) return GMC_OK;
+  if (!is_device_pointer(cond) || !is_device_pointer(y))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_data_internal: cond and y must be device memory");
+  cudaSetDevice(ctx->device);
+  internal_data_kernel<<<nb(n, 128), 128, 0, ctx->stream>>>(n, seed, logf(tau_lo), logf(tau_hi), c_lo,
+                                                            c_hi, cond, y);
+  GMC_CUDA_TRY(ctx, cudaGetLastError());
+  return GMC_OK;
+}
+
 gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const float *y,
                            const gmc_train_config *cfg) {
   if (!ctx || !cfg) return GMC_EINVAL;
@@ -438,7 +486,7 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: batch in [1, 2^20], lr > 0");
   if (cfg->precision != GMC_FP32 && cfg->precision != GMC_BF16)
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: precision must be GMC_FP32 or GMC_BF16");
-  if (!ctx->has_weights) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_train_begin: load initial weights first");
+  if (!ctx->net.loaded) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_train_begin: load initial weights first");
   if (!is_device_pointer(cond) || !is_device_pointer(y))
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: data must be device memory");
   cudaSetDevice(ctx->device);
@@ -473,15 +521,15 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
   // master weights from the loaded network
   std::vector<float> h(P_TOTAL, 0.0f);
   for (int c = 0; c < 256; ++c)
-    for (int k = 0; k < 25; ++k) h[P_W1 + c * 32 + k] = ctx->host_w[0][c * 25 + k];
-  std::memcpy(&h[P_B1], ctx->host_b[0], 256 * 4);
+    for (int k = 0; k < 25; ++k) h[P_W1 + c * 32 + k] = ctx->net.host_w[0][c * 25 + k];
+  std::memcpy(&h[P_B1], ctx->net.host_b[0], 256 * 4);
   const int64_t wo[3] = {P_W2, P_W3, P_W4}, bo[3] = {P_B2, P_B3, P_B4};
   for (int l = 0; l < 3; ++l) {
-    std::memcpy(&h[wo[l]], ctx->host_w[l + 1], 65536 * 4);
-    std::memcpy(&h[bo[l]], ctx->host_b[l + 1], 256 * 4);
+    std::memcpy(&h[wo[l]], ctx->net.host_w[l + 1], 65536 * 4);
+    std::memcpy(&h[bo[l]], ctx->net.host_b[l + 1], 256 * 4);
   }
-  std::memcpy(&h[P_W5], ctx->host_w[4], 1024 * 4);
-  std::memcpy(&h[P_B5], ctx->host_b[4], 4 * 4);
+  std::memcpy(&h[P_W5], ctx->net.host_w[4], 1024 * 4);
+  std::memcpy(&h[P_B5], ctx->net.host_b[4], 4 * 4);
   GMC_CUDA_TRY(ctx, cudaMalloc(&T->params, P_TOTAL * 4));
   GMC_CUDA_TRY(ctx, cudaMalloc(&T->grads, P_TOTAL * 4));
   GMC_CUDA_TRY(ctx, cudaMalloc(&T->m, P_TOTAL * 4));

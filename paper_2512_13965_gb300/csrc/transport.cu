@@ -12,9 +12,13 @@
 //     next Philox event, collisions so far: 64 B.
 // One wave:
 //   births   new histories of every admitted request fill free room of the
-//            banks (fair share): birth point and direction from Philox
-//            (id, 0, tag 4) start a walk in the inside bank (the paper's
-//            separate internal-source network is not built);
+//            banks (fair share), birth cell and point from Philox (id, 0,
+//            tag 4). GMC with an internal (volumetric-source) network loaded:
+//            one batch of the internal model samples every birth's exit from
+//            its cell (condition X, Y, ln tau, c and the distance to the
+//            nearest face; noise at (id, 0, tag 2)), then stages 3-4 as below.
+//            Otherwise (and for ANALOG) the birth direction from the same draw
+//            starts a random walk in the inside bank;
 //   inside   every walk in progress takes up to flights_per_wave more
 //            flights of the implicit-capture walk (Eq. 4); a walk that leaves
 //            its cell does stages 3-4 below, the others stay in the bank, so
@@ -347,6 +351,67 @@ __global__ void inside_walk_kernel(int64_t live, IBank in, const Slot *__restric
   append_inside(park, slot, h, cell, ws, w, iout, in_count, slot_live);
 }
 
+// GMC births with the internal model, stage 1: rows base .. base+count-1 of
+// the birth batch (row stride M): history, request and cell, the internal
+// condition (X, Y, ln tau, c, min(X, Y, 1 - X, 1 - Y)) and z ~ N(0, I) at
+// (id, 0, tag 2). Birth point and cell are those of birth_kernel.
+__global__ void birth_gmc_kernel(int slot, int64_t first, int64_t count, int64_t base, int64_t M,
+                                 const double *__restrict__ cdf, double total,
+                                 const Slot *__restrict__ slots, uint64_t *bhist, int32_t *bslot,
+                                 int32_t *bcell, float *cond, float *noise) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const Slot S = slots[slot];
+  const uint64_t h = (uint64_t)(first + k);
+  const uint4 r = philox_draw(S.seed, h, 0u, kTagBirth);
+  const double u0 = ((double)r.x + 1.0) * (1.0 / 4294967296.0);
+  const int cell = (int)cdf_search(cdf, (int64_t)S.nx * S.ny, u0 * total);
+  const float X = u01(r.y), Y = u01(r.z);
+  const int64_t row = base + k;
+  bhist[row] = h;
+  bslot[row] = slot;
+  bcell[row] = cell;
+  cond[row] = X;
+  cond[M + row] = Y;
+  cond[2 * M + row] = logf(S.tau[cell]);
+  cond[3 * M + row] = S.c[cell];
+  cond[4 * M + row] = fminf(fminf(X, Y), fminf(1.0f - X, 1.0f - Y));
+  const float4 z = box_muller4(philox_draw(S.seed, h, 0u, kTagNoise));
+  noise[row] = z.x;
+  noise[M + row] = z.y;
+  noise[2 * M + row] = z.z;
+  noise[3 * M + row] = z.w;
+}
+
+// GMC births, stages 3-4 from the internal model's decoded exits (p, ux, uy,
+// s), which are already in the cell's own (global-oriented) frame.
+__global__ void birth_gmc_post_kernel(int64_t M, const uint64_t *__restrict__ bhist,
+                                      const int32_t *__restrict__ bslot,
+                                      const int32_t *__restrict__ bcell, const float *__restrict__ ex,
+                                      const Slot *__restrict__ slots, Rules R, Bank out,
+                                      int *out_count, DevStats *st, int *slot_live) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Exit x;
+  x.active = k < M;
+  x.slot = 0;
+  if (x.active) {
+    const float p = ex[k];
+    const int fc = min((int)p, 3);
+    x.slot = bslot[k];
+    x.hist = bhist[k];
+    x.cell = bcell[k];
+    x.gface = fc;
+    x.q = fminf(fmaxf(p - (float)fc, 0.0f), 1.0f);
+    x.gx = ex[M + k];
+    x.gy = ex[2 * M + k];
+    x.w = 1.0f;
+    x.s = ex[3 * M + k];
+    x.ev = 1u;  // event 0 held the birth draw and the noise
+    x.ncoll = 0;
+  }
+  finish_transmission(x, slots, R, out, out_count, st, slot_live);
+}
+
 // ANALOG: start the walk of each face particle through its cell in the
 // cell's own (global-oriented) frame, entering at the point its entry face
 // and xi give; up to `cap` flights, then as inside_walk_kernel.
@@ -542,7 +607,7 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
     R.cdf[k] = acc;
   }
   if (n_histories > 0 && !(acc > 0.0)) return set_error(ctx, GMC_EINVAL, "solve: zero source");
-  if (method == GMC_METHOD_GMC && !ctx->has_weights)
+  if (method == GMC_METHOD_GMC && !ctx->net.loaded)
     return set_error(ctx, GMC_ENOWEIGHTS, "solve: GMC needs gmc_load_weights");
   R.total = acc;
   R.n_hist = n_histories;
@@ -611,7 +676,7 @@ class Engine {
   ~Engine() {
     cudaStreamSynchronize(s_);
     void *bufs[] = {bank_mem_[0], bank_mem_[1], ibank_mem_[0], ibank_mem_[1], d_cond_, d_noise_,
-                    d_exit_, d_slots_, d_stats_, d_counts_, d_bias1_};
+                    d_exit_, d_slots_, d_stats_, d_counts_, d_bias1_, d_bmeta_};
     for (void *b : bufs)
       if (b) cudaFree(b);
     if (h_counts_) cudaFreeHost(h_counts_);
@@ -628,6 +693,7 @@ class Engine {
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_noise_, C_ * 4 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_exit_, C_ * 4 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bias1_, 4 * 256 * 256 * sizeof(float)));
+      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bmeta_, C_ * 16));  // birth batch: hist, slot, cell
     }
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_slots_, kMaxSlots * sizeof(Slot)));
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_stats_, kMaxSlots * sizeof(DevStats)));
@@ -704,7 +770,10 @@ class Engine {
     for (auto *R : reqs_)
       if (R && R->next_hist < R->n_hist) ++pending;
     int64_t room = C_ - live_ - live_in_;
-    if (pending > 0 && room > 0) {
+    if (pending > 0 && room > 0 && method_ == GMC_METHOD_GMC && ctx_->internal.loaded) {
+      const gmc_status sb = births_internal(pending, room, rules);
+      if (sb != GMC_OK) return sb;
+    } else if (pending > 0 && room > 0) {
       in0_ = (int)live_in_;
       GMC_CUDA_TRY(ctx_, cudaMemcpyAsync(d_in, &in0_, sizeof(int), cudaMemcpyHostToDevice, s_));
       GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_slot_live, 0, kMaxSlots * sizeof(int), s_));
@@ -745,19 +814,8 @@ class Engine {
         gmc_prep_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_slots_, d_cond_,
                                                              d_noise_);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
-        const gmc_config &cfg = ctx_->cfg;
-        cudaError_t e;
-        if (cfg.precision == GMC_FP32)
-          e = launch_sampler_f32(s_, ctx_->f32, ctx_->stats, live_, d_cond_, d_noise_, 0, 0,
-                                 cfg.steps, cfg.integrator, nullptr, d_exit_);
-        else {
-          const bool fp8 = cfg.precision == GMC_FP8;
-          e = launch_sampler_tc(s_, fp8 ? ctx_->d_tc8 : ctx_->d_tc, ctx_->d_tc_bias, ctx_->f32,
-                                ctx_->stats, live_, d_cond_, d_noise_, 0, 0, cfg.steps,
-                                cfg.integrator, nullptr, d_exit_, ctx_->d_err, d_bias1_,
-                                fp8 ? ctx_->d_tc8_scale : nullptr);
-        }
-        if (e != cudaSuccess) return cuda_error(ctx_, e, "solve: sampler");
+        gmc_status es = sample(ctx_->net, live_);
+        if (es != GMC_OK) return es;
         gmc_post_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_exit_, d_slots_,
                                                              rules, bank_[nxt], d_face, d_stats_,
                                                              d_slot_live);
@@ -788,6 +846,72 @@ class Engine {
   }
 
  private:
+  // Stage 2 on `rows` rows of d_cond_ / d_noise_ into d_exit_ with network N.
+  gmc_status sample(const NetDev &N, int64_t rows) {
+    const gmc_config &cfg = ctx_->cfg;
+    cudaError_t e;
+    if (cfg.precision == GMC_FP32)
+      e = launch_sampler_f32(s_, N.f32, N.stats, rows, d_cond_, d_noise_, 0, 0, cfg.steps,
+                             cfg.integrator, nullptr, d_exit_);
+    else {
+      const bool fp8 = cfg.precision == GMC_FP8;
+      e = launch_sampler_tc(s_, fp8 ? N.d_tc8 : N.d_tc, N.d_tc_bias, N.f32, N.stats, rows, d_cond_,
+                            d_noise_, 0, 0, cfg.steps, cfg.integrator, nullptr, d_exit_,
+                            ctx_->d_err, d_bias1_, fp8 ? N.d_tc8_scale : nullptr);
+    }
+    if (e != cudaSuccess) return cuda_error(ctx_, e, "solve: sampler");
+    return GMC_OK;
+  }
+
+  // Births of this wave through the internal model: every request's share of
+  // the free room is sampled in one batch, tallied in its birth cell and
+  // appended to the face bank, so it crosses its first face in this wave.
+  gmc_status births_internal(int pending, int64_t room, const Rules &rules) {
+    std::vector<std::pair<Request *, int64_t>> plan;
+    int64_t M = 0;
+    int left = pending;
+    for (auto *R : reqs_) {
+      if (!R || R->next_hist >= R->n_hist) continue;
+      const int64_t share = room / left;
+      const int64_t m = std::min<int64_t>(share, R->n_hist - R->next_hist);
+      --left;
+      if (m <= 0) continue;
+      room -= m;
+      plan.emplace_back(R, m);
+      M += m;
+    }
+    if (M == 0) return GMC_OK;
+    uint64_t *bhist = (uint64_t *)d_bmeta_;
+    int32_t *bslot = (int32_t *)((char *)d_bmeta_ + 8 * C_);
+    int32_t *bcell = (int32_t *)((char *)d_bmeta_ + 12 * C_);
+    int64_t base = 0;
+    for (auto &pm : plan) {
+      Request *R = pm.first;
+      const int64_t m = pm.second;
+      birth_gmc_kernel<<<nblocks(m, 256), 256, 0, s_>>>(R->slot, R->next_hist, m, base, M, R->d_cdf,
+                                                         R->total, d_slots_, bhist, bslot, bcell,
+                                                         d_cond_, d_noise_);
+      GMC_CUDA_TRY(ctx_, cudaGetLastError());
+      R->next_hist += m;
+      base += m;
+    }
+    gmc_status st = sample(ctx_->internal, M);
+    if (st != GMC_OK) return st;
+    in0_ = (int)live_;
+    int *d_face = d_counts_, *d_slot_live = d_counts_ + 2;
+    GMC_CUDA_TRY(ctx_, cudaMemcpyAsync(d_face, &in0_, sizeof(int), cudaMemcpyHostToDevice, s_));
+    GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_slot_live, 0, kMaxSlots * sizeof(int), s_));
+    birth_gmc_post_kernel<<<nblocks(M, 256), 256, 0, s_>>>(M, bhist, bslot, bcell, d_exit_, d_slots_,
+                                                           rules, bank_[cur_], d_face, d_stats_,
+                                                           d_slot_live);
+    GMC_CUDA_TRY(ctx_, cudaGetLastError());
+    GMC_CUDA_TRY(ctx_, read_counts());
+    live_ = h_counts_[0];
+    for (auto *R : reqs_)
+      if (R) R->live += h_counts_[2 + R->slot];
+    return check_device_error(ctx_);
+  }
+
   cudaError_t read_counts() {
     cudaError_t e = cudaMemcpyAsync(h_counts_, d_counts_, kCounts * sizeof(int),
                                     cudaMemcpyDeviceToHost, s_);
@@ -844,6 +968,7 @@ class Engine {
   int in0_ = 0;  // host source of the inside-bank count copied before births
   int64_t waves_ = 0;
   float *d_cond_ = nullptr, *d_noise_ = nullptr, *d_exit_ = nullptr, *d_bias1_ = nullptr;
+  void *d_bmeta_ = nullptr;
   Slot *d_slots_ = nullptr;
   DevStats *d_stats_ = nullptr;
   int *d_counts_ = nullptr;
@@ -974,7 +1099,7 @@ gmc_status gmc_serve_start(gmc_ctx *ctx, const gmc_serve_config *cfg) {
     return set_error(ctx, GMC_EINVAL, "gmc_serve_start: unknown method");
   if (cfg->memory_budget < ((size_t)1 << 20))
     return set_error(ctx, GMC_EINVAL, "gmc_serve_start: memory_budget must be >= 1 MiB");
-  if (cfg->method == GMC_METHOD_GMC && !ctx->has_weights)
+  if (cfg->method == GMC_METHOD_GMC && !ctx->net.loaded)
     return set_error(ctx, GMC_ENOWEIGHTS, "gmc_serve_start: GMC needs gmc_load_weights");
   cudaSetDevice(ctx->device);
   Server *S = new Server();

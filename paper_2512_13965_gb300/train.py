@@ -4,8 +4,10 @@
         [--samples 16777216] [--steps 20000] [--batch 8192] [--lr 1e-3] \\
         [--lr-min 1e-5] [--warmup 500]
 
-Data: `gmc_train_data` (implicit-capture random walks, tau log-uniform in
-[0.1, 1000], c uniform in [0.5, 0.999]); objective: conditional flow
+Data: `gmc_train_data` (implicit-capture random walks from the left face,
+tau log-uniform in [0.1, 1000], c uniform in [0.5, 0.999]) or, with
+--model internal, `gmc_train_data_internal` (walks from a uniform point inside
+the cell, for the internal-source model); objective: conditional flow
 matching (Eq. 9) with AdamW, learning rate warmed up linearly and then
 decayed along a cosine to --lr-min; everything runs in libgmc.so, the GEMMs
 on tensor cores with BF16 operands and FP32 accumulation and master weights
@@ -38,6 +40,9 @@ def main(argv=None):
     ap.add_argument("--c", type=float, nargs=2, default=(0.5, 0.999))
     ap.add_argument("--report", type=int, default=1000)
     ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--model", default="boundary", choices=["boundary", "internal"],
+                    help="boundary: cell transmissions from the left face; internal: births "
+                         "inside a cell (volumetric source)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"],
                     help="GEMM operands: bf16 (tensor cores) or fp32 (SIMT)")
     args = ap.parse_args(argv)
@@ -64,7 +69,8 @@ def main(argv=None):
         cond = torch.empty(5, n, device="cuda")
         y = torch.empty(4, n, device="cuda")
     t0 = time.perf_counter()
-    g.gmc_train_data(ctx, n, args.seed, args.tau[0], args.tau[1], args.c[0], args.c[1], cond, y)
+    data = g.gmc_train_data if args.model == "boundary" else g.gmc_train_data_internal
+    data(ctx, n, args.seed, args.tau[0], args.tau[1], args.c[0], args.c[1], cond, y)
     g.gmc_synchronize(ctx)
     t_data = time.perf_counter() - t0
     print(json.dumps({"phase": "data", "samples": n, "seconds": t_data}), flush=True)

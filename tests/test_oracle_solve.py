@@ -120,3 +120,26 @@ def test_sigma_bar_decays_as_inverse_sqrt_n():
         sb.append(ostats.sigma_bar(runs))
     slope = np.polyfit(np.log([1000, 4000, 16000]), np.log(sb), 1)[0]
     assert -0.62 < slope < -0.38, (slope, sb)
+
+
+def test_internal_walk_births_reproduce_walked_births():
+    # Births through the internal-model path with the exact walk as the
+    # "model" (birth direction from the birth draw, walk from event 0) are the
+    # walked births history by history: identical flux, leakage, absorption.
+    tau, c, src = synth.grid_problem(n=8, seed=21, tau_range=(0.1, 20.0), block=4, source=2)
+    a, sa = T.solve_gmc(tau, c, src, 2000, 5, T.walk_sampler(5))
+    b, sb = T.solve_gmc(tau, c, src, 2000, 5, T.walk_sampler(5),
+                        internal=T.walk_internal_sampler(5))
+    np.testing.assert_array_equal(a, b)
+    for k in ("leak", "absorbed", "roulette_net", "transmissions", "roulette_kills"):
+        assert sa[k] == sb[k], k
+
+
+def test_internal_condition():
+    X = np.array([0.1, 0.9, 0.5, 0.3])
+    Y = np.array([0.4, 0.2, 0.5, 0.99])
+    cond = T.internal_condition(X, Y, np.array([2.0, 3.0, 4.0, 5.0]), np.array([0.5] * 4))
+    np.testing.assert_allclose(cond[0], X)
+    np.testing.assert_allclose(cond[1], Y)
+    np.testing.assert_allclose(cond[2], np.log([2.0, 3.0, 4.0, 5.0]))
+    np.testing.assert_allclose(cond[4], [0.1, 0.1, 0.5, 0.01])
