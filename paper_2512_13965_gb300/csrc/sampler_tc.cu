@@ -80,7 +80,15 @@ constexpr bool SPLIT_TILES = GMC_TC_SPLIT_TILES != 0;  // one epilogue group per
 constexpr int TPW = SPLIT_TILES ? 1 : 2;          // tiles served by each epilogue warp
 constexpr int GROUP_WARPS = SPLIT_TILES ? EPI_WARPS / 2 : EPI_WARPS;  // warps per tile
 constexpr int EPI_COLS = 256 / (GROUP_WARPS / 4);  // accumulator columns per epilogue thread
-constexpr int EPI_CH = EPI_COLS / 32;             // 32-column TMEM loads per thread
+#ifndef GMC_TC_EPI_CW
+#define GMC_TC_EPI_CW 32
+#endif
+#ifndef GMC_TC_EPI_CW8
+#define GMC_TC_EPI_CW8 16
+#endif
+constexpr int EPI_CW = GMC_TC_EPI_CW;    // accumulator columns per TMEM load, BF16 variant
+constexpr int EPI_CW8 = GMC_TC_EPI_CW8;  // the same for the FP8 variant (more live registers)
+static_assert((EPI_CW == 16 || EPI_CW == 32) && (EPI_CW8 == 16 || EPI_CW8 == 32), "TMEM load width");
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
 static_assert(CHUNK_K == 32 || CHUNK_K == 64, "chunk K");
 static_assert(EPI_WARPS == 8 || EPI_WARPS == 16, "epilogue warps");
@@ -283,21 +291,63 @@ __device__ __forceinline__ void epi32(const uint32_t (&v)[32], const float *__re
   }
 }
 
-// One epilogue thread's EPI_COLS columns of a 128 x 256 accumulator: the
-// load of the next 32 columns is in flight while the current ones are
-// converted and stored.
+// bias (and scale) + SiLU on 16 accumulator columns starting at col0 (a
+// multiple of 16): one 16-byte E4M3 chunk, or with !OUT8 two BF16 chunks.
 template <bool SCALED, bool OUT8>
+__device__ __forceinline__ void epi16(const uint32_t (&v)[16], const float *__restrict__ bias,
+                                      const float *__restrict__ scale, int col0, uint32_t a_base,
+                                      int r) {
+  const float4 *b4 = reinterpret_cast<const float4 *>(bias + col0);
+  const float4 *s4 = SCALED ? reinterpret_cast<const float4 *>(scale + col0) : nullptr;
+  if constexpr (OUT8) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 z = pre4<SCALED>(v + 4 * q, b4, s4, q);
+      w[q] = silu2_halved_e4m3(z.x, z.y) | (silu2_halved_e4m3(z.z, z.w) << 16);
+    }
+    st_shared_v4(sw128(a_base + (uint32_t)(col0 >> 7) * 16384u, r, (col0 & 127) >> 4), w[0], w[1],
+                 w[2], w[3]);
+  } else {
+    const uint32_t kb_base = a_base + (uint32_t)(col0 >> 6) * 16384u;
+    const int c0 = (col0 & 63) >> 3;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float4 za = pre4<SCALED>(v + 8 * j, b4, s4, 2 * j);
+      const float4 zb = pre4<SCALED>(v + 8 * j + 4, b4, s4, 2 * j + 1);
+      st_shared_v4(sw128(kb_base, r, c0 + j), silu2_halved(za.x, za.y), silu2_halved(za.z, za.w),
+                   silu2_halved(zb.x, zb.y), silu2_halved(zb.z, zb.w));
+    }
+  }
+}
+
+// One epilogue thread's EPI_COLS columns of a 128 x 256 accumulator: the
+// load of the next 32 (CW = 32) or 16 (CW = 16, fewer live registers)
+// columns is in flight while the current ones are converted and stored.
+template <bool SCALED, bool OUT8, int CW = 32>
 __device__ __forceinline__ void epi_layer(uint32_t tcol, const float *__restrict__ bias,
                                           const float *__restrict__ scale, int col0,
                                           uint32_t a_base, int r) {
-  uint32_t buf[2][32];
-  tmem_ld32_raw(tcol, buf[0]);
-  tmem_wait_ld_regs(buf[0]);
+  constexpr int NCH = EPI_COLS / CW;
+  uint32_t buf[2][CW];
+  if constexpr (CW == 32) {
+    tmem_ld32_raw(tcol, buf[0]);
+    tmem_wait_ld_regs(buf[0]);
+  } else {
+    tmem_ld16_raw(tcol, buf[0]);
+    tmem_wait_ld_regs16(buf[0]);
+  }
 #pragma unroll
-  for (int j = 0; j < EPI_CH; ++j) {
-    if (j + 1 < EPI_CH) tmem_ld32_raw(tcol + 32u * (uint32_t)(j + 1), buf[(j + 1) & 1]);
-    epi32<SCALED, OUT8>(buf[j & 1], bias, scale, col0 + 32 * j, a_base, r);
-    if (j + 1 < EPI_CH) tmem_wait_ld_regs(buf[(j + 1) & 1]);
+  for (int j = 0; j < NCH; ++j) {
+    if constexpr (CW == 32) {
+      if (j + 1 < NCH) tmem_ld32_raw(tcol + 32u * (uint32_t)(j + 1), buf[(j + 1) & 1]);
+      epi32<SCALED, OUT8>(buf[j & 1], bias, scale, col0 + 32 * j, a_base, r);
+      if (j + 1 < NCH) tmem_wait_ld_regs(buf[(j + 1) & 1]);
+    } else {
+      if (j + 1 < NCH) tmem_ld16_raw(tcol + 16u * (uint32_t)(j + 1), buf[(j + 1) & 1]);
+      epi16<SCALED, OUT8>(buf[j & 1], bias, scale, col0 + 16 * j, a_base, r);
+      if (j + 1 < NCH) tmem_wait_ld_regs16(buf[(j + 1) & 1]);
+    }
   }
 }
 
@@ -546,13 +596,13 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
               // layer 1 (BF16 MMA) and layers 2-3 feed E4M3 operands; layer 4
               // feeds the BF16 operand of layer 5
               if (L == 0)
-                epi_layer<false, true>(tcol, bias, nullptr, col0, a_base, r);
+                epi_layer<false, true, EPI_CW8>(tcol, bias, nullptr, col0, a_base, r);
               else if (L < 3)
-                epi_layer<true, true>(tcol, bias, P.scale + (L - 1) * 256, col0, a_base, r);
+                epi_layer<true, true, EPI_CW8>(tcol, bias, P.scale + (L - 1) * 256, col0, a_base, r);
               else
-                epi_layer<true, false>(tcol, bias, P.scale + 2 * 256, col0, a_base, r);
+                epi_layer<true, false, EPI_CW8>(tcol, bias, P.scale + 2 * 256, col0, a_base, r);
             } else {
-              epi_layer<false, false>(tcol, bias, nullptr, col0, a_base, r);
+              epi_layer<false, false, EPI_CW>(tcol, bias, nullptr, col0, a_base, r);
             }
             fence_proxy_async_smem();
             tc_fence_before();
