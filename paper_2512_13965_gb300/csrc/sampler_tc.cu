@@ -366,7 +366,9 @@ struct Params {
   int *err;
 };
 
-template <bool FP8>
+// INTEG: the integrator (GMC_EULER, GMC_MIDPOINT, GMC_RK4) as a compile-time
+// choice, so an Euler kernel holds no midpoint or RK4 state in registers.
+template <bool FP8, int INTEG>
 __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
   using PK = Packed<FP8>;
   constexpr int NCH = PK::NCH;
@@ -628,11 +630,11 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
 #pragma unroll
             for (int d = 0; d < 4; ++d) v[d] += __ldg(P.bias + 4 * 256 + d);
             float *xin = x[tt];
-            if (P.integrator == GMC_MIDPOINT && (e & 1) == 0) {
+            if (INTEG == GMC_MIDPOINT && (e & 1) == 0) {
 #pragma unroll
               for (int d = 0; d < 4; ++d) xm[tt][d] = fmaf(0.5f * h, v[d], x[tt][d]);
               xin = xm[tt];
-            } else if (P.integrator == GMC_RK4) {
+            } else if (INTEG == GMC_RK4) {
               // evaluation e % 4 = i gives k_{i+1}; ka = k1 + 2 k2 + 2 k3 + k4
               const int i = e & 3;
               if (i == 3) {
@@ -834,9 +836,9 @@ void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *
 }
 
 namespace {
-template <bool FP8>
+template <bool FP8, int INTEG>
 cudaError_t launch_tc(cudaStream_t stream, const Params &p, int sms) {
-  auto kernel = sampler_tc_kernel<FP8>;
+  auto kernel = sampler_tc_kernel<FP8, INTEG>;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
@@ -906,7 +908,14 @@ cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const flo
   p.y_raw = y_raw;
   p.exitp = exit;
   p.err = err;
-  return fp8_scale ? launch_tc<true>(stream, p, sms) : launch_tc<false>(stream, p, sms);
+  if (fp8_scale) {
+    if (integrator == GMC_RK4) return launch_tc<true, GMC_RK4>(stream, p, sms);
+    if (integrator == GMC_MIDPOINT) return launch_tc<true, GMC_MIDPOINT>(stream, p, sms);
+    return launch_tc<true, GMC_EULER>(stream, p, sms);
+  }
+  if (integrator == GMC_RK4) return launch_tc<false, GMC_RK4>(stream, p, sms);
+  if (integrator == GMC_MIDPOINT) return launch_tc<false, GMC_MIDPOINT>(stream, p, sms);
+  return launch_tc<false, GMC_EULER>(stream, p, sms);
 }
 
 }  // namespace gmc
