@@ -279,8 +279,11 @@ def main():
     flops = BATCH * (FLOPS_PER_STEP * ODE_STEPS + FLOPS_COND)
     achieved = flops / avg_s / 1e12
     if prec == g.GMC_BF16:
+        # DRAM read + write bytes of one launch of this kernel (BF16, Euler, 2^20 rows x
+        # 16 steps), from ncu dram__bytes_read.sum + dram__bytes_write.sum
+        traffic = 21479936 + 512 if ODE_STEPS == 16 and BATCH == 1 << 20 else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16"], "unit": "TFLOP/s",
-                "frac": achieved / pk["bf16"], "traffic": None,
+                "frac": achieved / pk["bf16"], "traffic": traffic, "traffic_unit": "bytes per launch",
                 "peak_source": pk["src"] + " bf16 burst", "kernel": "sampler_tc_kernel"}
     elif prec == g.GMC_FP8:
         # 97% of the flops run in E4M3: the FP8 dense rate is twice BF16's
@@ -417,7 +420,8 @@ def run_solve(args):
                          "floor_rel_err_at_n": rel(f_a, f_b) / np.sqrt(2.0)}
     names = {g.GMC_EULER: "euler", g.GMC_MIDPOINT: "midpoint", g.GMC_RK4: "rk4"}
     for prec, integ, steps in ((g.GMC_BF16, g.GMC_EULER, 16), (g.GMC_BF16, g.GMC_EULER, 8),
-                               (g.GMC_BF16, g.GMC_MIDPOINT, 8), (g.GMC_BF16, g.GMC_RK4, 4),
+                               (g.GMC_BF16, g.GMC_MIDPOINT, 8), (g.GMC_BF16, g.GMC_MIDPOINT, 12),
+                               (g.GMC_BF16, g.GMC_RK4, 4), (g.GMC_BF16, g.GMC_RK4, 6),
                                (g.GMC_BF16, g.GMC_RK4, 12), (g.GMC_FP8, g.GMC_EULER, 16),
                                (g.GMC_FP8, g.GMC_EULER, 8), (g.GMC_FP8, g.GMC_RK4, 12)):
         pname = "bf16" if prec == g.GMC_BF16 else "fp8"
