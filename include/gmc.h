@@ -98,6 +98,16 @@ typedef struct gmc_solve_stats {
 
 /* ---- context ------------------------------------------------------------ */
 
+/*
+ * Failure-path self-test (no counterpart in the paper): one device thread
+ * waits on an mbarrier that nothing arrives at, using the bounded wait of the
+ * tensor-core kernels, gives up after limit_ms (0 < limit_ms <= 2000) and sets
+ * the device error word. Returns what every blocking call returns after a
+ * wait gave up: GMC_ETIMEOUT, with the error word cleared and the context
+ * usable. Blocking.
+ */
+gmc_status gmc_selftest_wait(gmc_ctx *ctx, double limit_ms);
+
 /* Creates a context on CUDA device `device` with its own stream (a blocking
    stream: ordered with work on the legacy default stream, not with other
    non-blocking streams; pass those with gmc_set_stream). */

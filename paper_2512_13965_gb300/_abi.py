@@ -102,6 +102,7 @@ def _load():
         "gmc_train_grad": [P, i64, P, P, P, P, P, P],
         "gmc_train_params": [P, P],
         "gmc_train_commit": [P, ctypes.c_char_p],
+        "gmc_selftest_wait": [P, ctypes.c_double],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -328,3 +329,8 @@ def gmc_wait(ctx, ticket, timeout_s, flux):
 
 def gmc_serve_stop(ctx):
     return ctx.check(lib.gmc_serve_stop(ctx.handle))
+
+
+def gmc_selftest_wait(ctx, limit_ms):
+    """Returns the status of the bounded-wait self-test (GMC_ETIMEOUT expected)."""
+    return lib.gmc_selftest_wait(ctx.handle, float(limit_ms))
