@@ -389,11 +389,12 @@ def run_solve(args):
     n = int(args.histories)
     out = {}
 
-    def solve(method, seed, steps=16, integ=0, prec=None, n_hist=None):
+    def solve(method, seed, steps=16, integ=0, prec=None, n_hist=None, min_tau=0.0):
         cfg = g.gmc_get_config(ctx)
         cfg.steps = steps
         cfg.integrator = integ
         cfg.precision = g.GMC_BF16 if prec is None else prec
+        cfg.gmc_min_tau = min_tau
         g.gmc_set_config(ctx, cfg)
         f = np.zeros(128 * 128)
         st = g.transport_solve(ctx, 128, 128, tau, c, src, n if n_hist is None else n_hist, method,
@@ -431,6 +432,18 @@ def run_solve(args):
         f, st = solve(g.GMC_METHOD_GMC, 3, steps, integ, prec)
         out[key] = {"seconds": st.seconds, "transmissions": st.transmissions,
                     "transmissions_per_s": st.transmissions / st.seconds, "waves": st.waves,
+                    "flux_rel_err_vs_analog": None if f_mc is None else rel(f, f_mc)}
+    # GMC only in cells thicker than tau = 64 (where the walk switches to FP64
+    # positions and one transmission costs more than the network); thinner
+    # cells and their births by the random walk
+    for integ, steps in ((g.GMC_MIDPOINT, 8), (g.GMC_RK4, 12)):
+        key = "hybrid64_bf16_%s%d" % (names[integ], steps)
+        if want is not None and key not in want:
+            continue
+        f, st = solve(g.GMC_METHOD_GMC, 3, steps, integ, g.GMC_BF16, min_tau=64.0)
+        out[key] = {"seconds": st.seconds, "transmissions": st.transmissions,
+                    "transmissions_per_s": st.transmissions / st.seconds, "waves": st.waves,
+                    "collisions": st.collisions,
                     "flux_rel_err_vs_analog": None if f_mc is None else rel(f, f_mc)}
     line = {"metric": METRIC, "workload": "transport solve 128x128, tau logU[0.1,500], c {0.5,0.999} "
             "16x16 blocks, central 8x8 source, %d histories" % n, "weights": args.weights or "kaiming seed 1 (untrained)",

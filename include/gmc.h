@@ -80,6 +80,11 @@ typedef struct gmc_config {
     int flights_per_wave;  /* random-walk flights a particle takes per wave of transport_solve
                               before it waits for the next wave (births, and every walk of
                               GMC_METHOD_ANALOG); results do not depend on it; default 512 */
+    double gmc_min_tau;    /* GMC solves only: cells with tau below this are crossed (and
+                              their births walked) by the random walk instead of the
+                              networks, so GMC runs where one network evaluation costs less
+                              than the walk's flights; 0 (default) = every cell by GMC, as
+                              in the paper */
 } gmc_config;
 
 /* Per-solve counters (all weights per history-weight unit, not normalized). */

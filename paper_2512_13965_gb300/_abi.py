@@ -25,7 +25,8 @@ GMC_METHOD_ANALOG, GMC_METHOD_GMC = 0, 1
 class gmc_config(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("integrator", ctypes.c_int), ("precision", ctypes.c_int),
                 ("w_cut", ctypes.c_double), ("p_survive", ctypes.c_double),
-                ("bank_capacity", ctypes.c_int64), ("flights_per_wave", ctypes.c_int)]
+                ("bank_capacity", ctypes.c_int64), ("flights_per_wave", ctypes.c_int),
+                ("gmc_min_tau", ctypes.c_double)]
 
 
 class gmc_solve_stats(ctypes.Structure):

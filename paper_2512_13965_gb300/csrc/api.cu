@@ -113,6 +113,7 @@ gmc_config default_config() {
   c.p_survive = 0.1;
   c.bank_capacity = (int64_t)1 << 21;
   c.flights_per_wave = 512;
+  c.gmc_min_tau = 0.0;
   return c;
 }
 
@@ -244,6 +245,7 @@ gmc_status gmc_set_config(gmc_ctx *ctx, const gmc_config *cfg) {
     return set_error(ctx, GMC_EINVAL, "bank_capacity must be in [1024, 2^28]");
   if (cfg->flights_per_wave < 1)
     return set_error(ctx, GMC_EINVAL, "flights_per_wave must be >= 1");
+  if (!(cfg->gmc_min_tau >= 0.0)) return set_error(ctx, GMC_EINVAL, "gmc_min_tau must be >= 0");
   ctx->cfg = *cfg;
   return GMC_OK;
 }

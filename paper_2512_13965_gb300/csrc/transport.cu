@@ -97,6 +97,17 @@ struct Rules {
   float w_cut, p_survive;
 };
 
+// Where stage 4 appends the survivors: the face bank, or, for a destination
+// cell thinner than min_tau in a GMC solve that walks thin cells (0: never),
+// the bank of face particles the random walk transmits.
+struct Route {
+  Bank out;
+  int *count;
+  Bank thin;
+  int *thin_count;
+  float min_tau;
+};
+
 // rotate (ux, uy) by k quarter turns counter-clockwise
 __device__ __forceinline__ void rot(float &ux, float &uy, int k) {
   const float a = ux, b = uy;
@@ -131,11 +142,24 @@ struct Exit {
 // Stages 3 and 4: deposit, attenuate, roulette, cross; appends survivors to
 // `out` (warp-aggregated) and counts them per request. Every lane of the
 // warp calls this (inactive lanes with active = false).
+__device__ __forceinline__ void put_face(Bank out, int k, const Exit &x, int ncell, int nface,
+                                         float w) {
+  out.hist[k] = x.hist;
+  out.slot[k] = x.slot;
+  out.cell[k] = ncell;
+  out.face[k] = nface;
+  out.xi[k] = x.q;
+  out.gx[k] = x.gx;
+  out.gy[k] = x.gy;
+  out.w[k] = w;
+  out.ev[k] = x.ev;
+}
+
 __device__ void finish_transmission(const Exit &x, const Slot *__restrict__ slots, Rules R,
-                                    Bank out, int *out_count, DevStats *st, int *slot_live) {
+                                    const Route &rt, DevStats *st, int *slot_live) {
   double dabs = 0.0, dleak = 0.0, droul = 0.0;
   unsigned long long kills = 0;
-  bool keep = false;
+  bool keep = false, thin = false;
   int ncell = 0, nface = 0;
   float w = 0.0f;
   if (x.active) {
@@ -176,26 +200,22 @@ __device__ void finish_transmission(const Exit &x, const Slot *__restrict__ slot
         keep = true;
         ncell = nj * S.nx + ni;
         nface = (x.gface + 2) & 3;
+        thin = rt.min_tau > 0.0f && S.tau[ncell] < rt.min_tau;
       }
     }
   }
   const int lane = threadIdx.x & 31;
-  const unsigned mask = __ballot_sync(0xffffffffu, keep);
-  int base = 0;
-  if (lane == 0 && mask) base = atomicAdd(out_count, __popc(mask));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (keep) {
-    const int k = base + __popc(mask & ((1u << lane) - 1u));
-    out.hist[k] = x.hist;
-    out.slot[k] = x.slot;
-    out.cell[k] = ncell;
-    out.face[k] = nface;
-    out.xi[k] = x.q;
-    out.gx[k] = x.gx;
-    out.gy[k] = x.gy;
-    out.w[k] = w;
-    out.ev[k] = x.ev;
-  }
+  const unsigned below = (1u << lane) - 1u;
+  const unsigned mask_f = __ballot_sync(0xffffffffu, keep && !thin);
+  const unsigned mask_t = __ballot_sync(0xffffffffu, keep && thin);
+  const unsigned mask = mask_f | mask_t;
+  int base_f = 0, base_t = 0;
+  if (lane == 0 && mask_f) base_f = atomicAdd(rt.count, __popc(mask_f));
+  if (lane == 0 && mask_t) base_t = atomicAdd(rt.thin_count, __popc(mask_t));
+  base_f = __shfl_sync(0xffffffffu, base_f, 0);
+  base_t = __shfl_sync(0xffffffffu, base_t, 0);
+  if (keep && !thin) put_face(rt.out, base_f + __popc(mask_f & below), x, ncell, nface, w);
+  if (keep && thin) put_face(rt.thin, base_t + __popc(mask_t & below), x, ncell, nface, w);
   // statistics and survivor counts per request: warp-reduced when every
   // active lane belongs to the same request (the common case: births of a
   // request are contiguous and compaction keeps warp order), per lane otherwise
@@ -320,8 +340,8 @@ __device__ __forceinline__ void settle(const WalkResult &wr, const WalkState &ws
 
 // Up to `cap` more flights of every walk in progress.
 __global__ void inside_walk_kernel(int64_t live, IBank in, const Slot *__restrict__ slots, Rules R,
-                                   uint32_t cap, Bank out, int *out_count, IBank iout,
-                                   int *in_count, DevStats *st, int *slot_live) {
+                                   uint32_t cap, Route rt, IBank iout, int *in_count, DevStats *st,
+                                   int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Exit x;
   x.active = false;
@@ -347,40 +367,56 @@ __global__ void inside_walk_kernel(int64_t live, IBank in, const Slot *__restric
     const WalkResult wr = walk_cell_resume(S.tau[cell], S.c[cell], 1, ws, cap, S.seed, h);
     settle(wr, ws, slot, h, cell, w, x, park);
   }
-  finish_transmission(x, slots, R, out, out_count, st, slot_live);
+  finish_transmission(x, slots, R, rt, st, slot_live);
   append_inside(park, slot, h, cell, ws, w, iout, in_count, slot_live);
 }
 
 // GMC births with the internal model, stage 1: rows base .. base+count-1 of
 // the birth batch (row stride M): history, request and cell, the internal
 // condition (X, Y, ln tau, c, min(X, Y, 1 - X, 1 - Y)) and z ~ N(0, I) at
-// (id, 0, tag 2). Birth point and cell are those of birth_kernel.
+// (id, 0, tag 2). Birth point and cell are those of birth_kernel. A birth in
+// a cell thinner than min_tau starts a random walk in the inside bank
+// instead (direction from the same draw) and its batch row is marked unused.
 __global__ void birth_gmc_kernel(int slot, int64_t first, int64_t count, int64_t base, int64_t M,
                                  const double *__restrict__ cdf, double total,
                                  const Slot *__restrict__ slots, uint64_t *bhist, int32_t *bslot,
-                                 int32_t *bcell, float *cond, float *noise) {
+                                 int32_t *bcell, float *cond, float *noise, float min_tau,
+                                 IBank iout, int *in_count, int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= count) return;
-  const Slot S = slots[slot];
-  const uint64_t h = (uint64_t)(first + k);
-  const uint4 r = philox_draw(S.seed, h, 0u, kTagBirth);
-  const double u0 = ((double)r.x + 1.0) * (1.0 / 4294967296.0);
-  const int cell = (int)cdf_search(cdf, (int64_t)S.nx * S.ny, u0 * total);
-  const float X = u01(r.y), Y = u01(r.z);
-  const int64_t row = base + k;
-  bhist[row] = h;
-  bslot[row] = slot;
-  bcell[row] = cell;
-  cond[row] = X;
-  cond[M + row] = Y;
-  cond[2 * M + row] = logf(S.tau[cell]);
-  cond[3 * M + row] = S.c[cell];
-  cond[4 * M + row] = fminf(fminf(X, Y), fminf(1.0f - X, 1.0f - Y));
-  const float4 z = box_muller4(philox_draw(S.seed, h, 0u, kTagNoise));
-  noise[row] = z.x;
-  noise[M + row] = z.y;
-  noise[2 * M + row] = z.z;
-  noise[3 * M + row] = z.w;
+  bool walk = false;
+  WalkState ws{};
+  int cell = 0;
+  uint64_t h = 0;
+  if (k < count) {
+    const Slot S = slots[slot];
+    h = (uint64_t)(first + k);
+    const uint4 r = philox_draw(S.seed, h, 0u, kTagBirth);
+    const double u0 = ((double)r.x + 1.0) * (1.0 / 4294967296.0);
+    cell = (int)cdf_search(cdf, (int64_t)S.nx * S.ny, u0 * total);
+    const float X = u01(r.y), Y = u01(r.z);
+    const float tau = S.tau[cell];
+    const int64_t row = base + k;
+    bhist[row] = h;
+    bcell[row] = cell;
+    walk = tau < min_tau;
+    bslot[row] = walk ? -1 : slot;
+    cond[row] = X;
+    cond[M + row] = Y;
+    cond[2 * M + row] = logf(tau);
+    cond[3 * M + row] = S.c[cell];
+    cond[4 * M + row] = fminf(fminf(X, Y), fminf(1.0f - X, 1.0f - Y));
+    const float4 z = box_muller4(philox_draw(S.seed, h, 0u, kTagNoise));
+    noise[row] = z.x;
+    noise[M + row] = z.y;
+    noise[2 * M + row] = z.z;
+    noise[3 * M + row] = z.w;
+    if (walk) {
+      float ux, uy;
+      sincospif(2.0f * u01(r.w), &uy, &ux);
+      ws = walk_start(tau, X, Y, ux, uy, 0u);
+    }
+  }
+  append_inside(walk, slot, h, cell, ws, 1.0f, iout, in_count, slot_live);
 }
 
 // GMC births, stages 3-4 from the internal model's decoded exits (p, ux, uy,
@@ -388,11 +424,11 @@ __global__ void birth_gmc_kernel(int slot, int64_t first, int64_t count, int64_t
 __global__ void birth_gmc_post_kernel(int64_t M, const uint64_t *__restrict__ bhist,
                                       const int32_t *__restrict__ bslot,
                                       const int32_t *__restrict__ bcell, const float *__restrict__ ex,
-                                      const Slot *__restrict__ slots, Rules R, Bank out,
-                                      int *out_count, DevStats *st, int *slot_live) {
+                                      const Slot *__restrict__ slots, Rules R, Route rt,
+                                      DevStats *st, int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Exit x;
-  x.active = k < M;
+  x.active = k < M && bslot[k] >= 0;  // rows of walked births are unused
   x.slot = 0;
   if (x.active) {
     const float p = ex[k];
@@ -409,15 +445,15 @@ __global__ void birth_gmc_post_kernel(int64_t M, const uint64_t *__restrict__ bh
     x.ev = 1u;  // event 0 held the birth draw and the noise
     x.ncoll = 0;
   }
-  finish_transmission(x, slots, R, out, out_count, st, slot_live);
+  finish_transmission(x, slots, R, rt, st, slot_live);
 }
 
 // ANALOG: start the walk of each face particle through its cell in the
 // cell's own (global-oriented) frame, entering at the point its entry face
 // and xi give; up to `cap` flights, then as inside_walk_kernel.
 __global__ void analog_wave_kernel(int64_t live, Bank in, const Slot *__restrict__ slots, Rules R,
-                                   uint32_t cap, Bank out, int *out_count, IBank iout,
-                                   int *in_count, DevStats *st, int *slot_live) {
+                                   uint32_t cap, Route rt, IBank iout, int *in_count, DevStats *st,
+                                   int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Exit x;
   x.active = false;
@@ -448,7 +484,7 @@ __global__ void analog_wave_kernel(int64_t live, Bank in, const Slot *__restrict
     const WalkResult wr = walk_cell_resume(tau, S.c[cell], 1, ws, cap, S.seed, h);
     settle(wr, ws, slot, h, cell, w, x, park);
   }
-  finish_transmission(x, slots, R, out, out_count, st, slot_live);
+  finish_transmission(x, slots, R, rt, st, slot_live);
   append_inside(park, slot, h, cell, ws, w, iout, in_count, slot_live);
 }
 
@@ -475,8 +511,8 @@ __global__ void gmc_prep_kernel(int64_t live, Bank in, const Slot *__restrict__ 
 
 // GMC stages 3 and 4 from the sampler's decoded exits (p, ux, uy, s).
 __global__ void gmc_post_kernel(int64_t live, Bank in, const float *__restrict__ ex,
-                                const Slot *__restrict__ slots, Rules R, Bank out, int *out_count,
-                                DevStats *st, int *slot_live) {
+                                const Slot *__restrict__ slots, Rules R, Route rt, DevStats *st,
+                                int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Exit x;
   x.active = k < live;
@@ -499,7 +535,7 @@ __global__ void gmc_post_kernel(int64_t live, Bank in, const float *__restrict__
     x.ev = in.ev[k] + 1u;
     x.ncoll = 0;
   }
-  finish_transmission(x, slots, R, out, out_count, st, slot_live);
+  finish_transmission(x, slots, R, rt, st, slot_live);
 }
 
 inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -675,8 +711,9 @@ class Engine {
 
   ~Engine() {
     cudaStreamSynchronize(s_);
-    void *bufs[] = {bank_mem_[0], bank_mem_[1], ibank_mem_[0], ibank_mem_[1], d_cond_, d_noise_,
-                    d_exit_, d_slots_, d_stats_, d_counts_, d_bias1_, d_bmeta_};
+    void *bufs[] = {bank_mem_[0], bank_mem_[1], ibank_mem_[0], ibank_mem_[1], tbank_mem_[0],
+                    tbank_mem_[1], d_cond_, d_noise_, d_exit_, d_slots_, d_stats_, d_counts_,
+                    d_bias1_, d_bmeta_};
     for (void *b : bufs)
       if (b) cudaFree(b);
     if (h_counts_) cudaFreeHost(h_counts_);
@@ -694,6 +731,8 @@ class Engine {
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_exit_, C_ * 4 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bias1_, 4 * 256 * 256 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bmeta_, C_ * 16));  // birth batch: hist, slot, cell
+      GMC_CUDA_TRY(ctx_, cudaMalloc(&tbank_mem_[0], C_ * kBankBytesPerParticle));
+      GMC_CUDA_TRY(ctx_, cudaMalloc(&tbank_mem_[1], C_ * kBankBytesPerParticle));
     }
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_slots_, kMaxSlots * sizeof(Slot)));
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_stats_, kMaxSlots * sizeof(DevStats)));
@@ -703,6 +742,9 @@ class Engine {
     bank_[1] = carve(bank_mem_[1], C_);
     ibank_[0] = carve_inside(ibank_mem_[0], C_);
     ibank_[1] = carve_inside(ibank_mem_[1], C_);
+    // the thin-cell face banks exist for GMC solves only; ANALOG routes nothing there
+    tbank_[0] = carve(tbank_mem_[0] ? tbank_mem_[0] : bank_mem_[0], C_);
+    tbank_[1] = carve(tbank_mem_[1] ? tbank_mem_[1] : bank_mem_[1], C_);
     for (auto &r : reqs_) r = nullptr;
     return GMC_OK;
   }
@@ -764,19 +806,19 @@ class Engine {
   gmc_status step(std::vector<Request *> &completed) {
     const Rules rules{(float)ctx_->cfg.w_cut, (float)ctx_->cfg.p_survive};
     const uint32_t cap = (uint32_t)ctx_->cfg.flights_per_wave;
-    int *d_face = d_counts_, *d_in = d_counts_ + 1, *d_slot_live = d_counts_ + 2;
+    const float min_tau = method_ == GMC_METHOD_GMC ? (float)ctx_->cfg.gmc_min_tau : 0.0f;
+    int *d_face = d_counts_, *d_in = d_counts_ + 1, *d_thin = d_counts_ + 2,
+        *d_slot_live = d_counts_ + 3;
     // births: fair share of the free room among requests with histories left
     int pending = 0;
     for (auto *R : reqs_)
       if (R && R->next_hist < R->n_hist) ++pending;
-    int64_t room = C_ - live_ - live_in_;
+    int64_t room = C_ - live_ - live_in_ - live_thin_;
     if (pending > 0 && room > 0 && method_ == GMC_METHOD_GMC && ctx_->internal.loaded) {
-      const gmc_status sb = births_internal(pending, room, rules);
+      const gmc_status sb = births_internal(pending, room, rules, min_tau);
       if (sb != GMC_OK) return sb;
     } else if (pending > 0 && room > 0) {
-      in0_ = (int)live_in_;
-      GMC_CUDA_TRY(ctx_, cudaMemcpyAsync(d_in, &in0_, sizeof(int), cudaMemcpyHostToDevice, s_));
-      GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_slot_live, 0, kMaxSlots * sizeof(int), s_));
+      GMC_CUDA_TRY(ctx_, set_counts());
       int left = pending;
       for (auto *R : reqs_) {
         if (!R || R->next_hist >= R->n_hist) continue;
@@ -793,22 +835,29 @@ class Engine {
       GMC_CUDA_TRY(ctx_, read_counts());
       live_in_ = h_counts_[1];
       for (auto *R : reqs_)
-        if (R) R->live += h_counts_[2 + R->slot];
+        if (R) R->live += h_counts_[3 + R->slot];
     }
-    if (live_ + live_in_ > 0) {
+    if (live_ + live_in_ + live_thin_ > 0) {
       ++waves_;
-      const int nxt = cur_ ^ 1, nin = cin_ ^ 1;
+      const int nxt = cur_ ^ 1, nin = cin_ ^ 1, ntn = ctn_ ^ 1;
+      const Route route{bank_[nxt], d_face, tbank_[ntn], d_thin, min_tau};
       GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_counts_, 0, kCounts * sizeof(int), s_));
       if (live_in_ > 0) {
         inside_walk_kernel<<<nblocks(live_in_, 128), 128, 0, s_>>>(
-            live_in_, ibank_[cin_], d_slots_, rules, cap, bank_[nxt], d_face, ibank_[nin], d_in,
-            d_stats_, d_slot_live);
+            live_in_, ibank_[cin_], d_slots_, rules, cap, route, ibank_[nin], d_in, d_stats_,
+            d_slot_live);
+        GMC_CUDA_TRY(ctx_, cudaGetLastError());
+      }
+      if (live_thin_ > 0) {  // face particles of thin cells in a GMC solve: random walk
+        analog_wave_kernel<<<nblocks(live_thin_, 128), 128, 0, s_>>>(
+            live_thin_, tbank_[ctn_], d_slots_, rules, cap, route, ibank_[nin], d_in, d_stats_,
+            d_slot_live);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
       }
       if (live_ > 0 && method_ == GMC_METHOD_ANALOG) {
         analog_wave_kernel<<<nblocks(live_, 128), 128, 0, s_>>>(live_, bank_[cur_], d_slots_, rules,
-                                                                cap, bank_[nxt], d_face, ibank_[nin],
-                                                                d_in, d_stats_, d_slot_live);
+                                                                cap, route, ibank_[nin], d_in,
+                                                                d_stats_, d_slot_live);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
       } else if (live_ > 0) {
         gmc_prep_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_slots_, d_cond_,
@@ -817,17 +866,18 @@ class Engine {
         gmc_status es = sample(ctx_->net, live_);
         if (es != GMC_OK) return es;
         gmc_post_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_exit_, d_slots_,
-                                                             rules, bank_[nxt], d_face, d_stats_,
-                                                             d_slot_live);
+                                                             rules, route, d_stats_, d_slot_live);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
       }
       GMC_CUDA_TRY(ctx_, read_counts());
       live_ = h_counts_[0];
       live_in_ = h_counts_[1];
+      live_thin_ = h_counts_[2];
       for (auto *R : reqs_)
-        if (R) R->live = h_counts_[2 + R->slot];
+        if (R) R->live = h_counts_[3 + R->slot];
       cur_ = nxt;
       cin_ = nin;
+      ctn_ = ntn;
       if (method_ == GMC_METHOD_GMC) {
         gmc_status es = check_device_error(ctx_);
         if (es != GMC_OK) return es;
@@ -865,8 +915,9 @@ class Engine {
 
   // Births of this wave through the internal model: every request's share of
   // the free room is sampled in one batch, tallied in its birth cell and
-  // appended to the face bank, so it crosses its first face in this wave.
-  gmc_status births_internal(int pending, int64_t room, const Rules &rules) {
+  // appended to the face banks, so it crosses its first face in this wave;
+  // births in cells thinner than min_tau start random walks instead.
+  gmc_status births_internal(int pending, int64_t room, const Rules &rules, float min_tau) {
     std::vector<std::pair<Request *, int64_t>> plan;
     int64_t M = 0;
     int left = pending;
@@ -884,32 +935,45 @@ class Engine {
     uint64_t *bhist = (uint64_t *)d_bmeta_;
     int32_t *bslot = (int32_t *)((char *)d_bmeta_ + 8 * C_);
     int32_t *bcell = (int32_t *)((char *)d_bmeta_ + 12 * C_);
+    int *d_face = d_counts_, *d_in = d_counts_ + 1, *d_thin = d_counts_ + 2,
+        *d_slot_live = d_counts_ + 3;
+    GMC_CUDA_TRY(ctx_, set_counts());
     int64_t base = 0;
     for (auto &pm : plan) {
       Request *R = pm.first;
       const int64_t m = pm.second;
       birth_gmc_kernel<<<nblocks(m, 256), 256, 0, s_>>>(R->slot, R->next_hist, m, base, M, R->d_cdf,
                                                          R->total, d_slots_, bhist, bslot, bcell,
-                                                         d_cond_, d_noise_);
+                                                         d_cond_, d_noise_, min_tau, ibank_[cin_],
+                                                         d_in, d_slot_live);
       GMC_CUDA_TRY(ctx_, cudaGetLastError());
       R->next_hist += m;
       base += m;
     }
     gmc_status st = sample(ctx_->internal, M);
     if (st != GMC_OK) return st;
-    in0_ = (int)live_;
-    int *d_face = d_counts_, *d_slot_live = d_counts_ + 2;
-    GMC_CUDA_TRY(ctx_, cudaMemcpyAsync(d_face, &in0_, sizeof(int), cudaMemcpyHostToDevice, s_));
-    GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_slot_live, 0, kMaxSlots * sizeof(int), s_));
+    const Route route{bank_[cur_], d_face, tbank_[ctn_], d_thin, min_tau};
     birth_gmc_post_kernel<<<nblocks(M, 256), 256, 0, s_>>>(M, bhist, bslot, bcell, d_exit_, d_slots_,
-                                                           rules, bank_[cur_], d_face, d_stats_,
-                                                           d_slot_live);
+                                                           rules, route, d_stats_, d_slot_live);
     GMC_CUDA_TRY(ctx_, cudaGetLastError());
     GMC_CUDA_TRY(ctx_, read_counts());
     live_ = h_counts_[0];
+    live_in_ = h_counts_[1];
+    live_thin_ = h_counts_[2];
     for (auto *R : reqs_)
-      if (R) R->live += h_counts_[2 + R->slot];
+      if (R) R->live += h_counts_[3 + R->slot];
     return check_device_error(ctx_);
+  }
+
+  // Bank counters <- current live counts, survivor counts per slot <- 0 (for
+  // births appending to the current banks).
+  cudaError_t set_counts() {
+    init_[0] = (int)live_;
+    init_[1] = (int)live_in_;
+    init_[2] = (int)live_thin_;
+    cudaError_t e = cudaMemcpyAsync(d_counts_, init_, 3 * sizeof(int), cudaMemcpyHostToDevice, s_);
+    if (e) return e;
+    return cudaMemsetAsync(d_counts_ + 3, 0, kMaxSlots * sizeof(int), s_);
   }
 
   cudaError_t read_counts() {
@@ -958,14 +1022,16 @@ class Engine {
   size_t pool_bytes_;
   cudaStream_t s_;
   Pool pool_;
-  // counters: [0] face bank, [1] inside bank, [2 ..] live particles per slot
-  static constexpr int kCounts = kMaxSlots + 2;
-  void *bank_mem_[2] = {nullptr, nullptr}, *ibank_mem_[2] = {nullptr, nullptr};
-  Bank bank_[2];
+  // counters: [0] face bank, [1] inside bank, [2] thin-cell face bank,
+  // [3 ..] live particles per slot
+  static constexpr int kCounts = kMaxSlots + 3;
+  void *bank_mem_[2] = {nullptr, nullptr}, *ibank_mem_[2] = {nullptr, nullptr},
+       *tbank_mem_[2] = {nullptr, nullptr};
+  Bank bank_[2], tbank_[2];
   IBank ibank_[2];
-  int cur_ = 0, cin_ = 0;
-  int64_t live_ = 0, live_in_ = 0;
-  int in0_ = 0;  // host source of the inside-bank count copied before births
+  int cur_ = 0, cin_ = 0, ctn_ = 0;
+  int64_t live_ = 0, live_in_ = 0, live_thin_ = 0;
+  int init_[3] = {0, 0, 0};  // host source of the counters copied before births
   int64_t waves_ = 0;
   float *d_cond_ = nullptr, *d_noise_ = nullptr, *d_exit_ = nullptr, *d_bias1_ = nullptr;
   void *d_bmeta_ = nullptr;

@@ -106,3 +106,23 @@ def test_gmc_solve_with_internal_births_matches_oracle(ictx, kaiming_file):
     assert abs(st["transmissions"] - so["transmissions"]) < 0.02 * so["transmissions"]
     assert abs(st["absorbed"] + st["leaked"] - st["roulette_net"] - n) < 1e-4 * n
     assert st["collisions"] == 0  # no birth was walked
+
+
+def test_hybrid_with_internal_model_all_thin_equals_analog(ictx):
+    # with the internal model loaded, births in thin cells are walked too
+    import paper_2512_13965_gb300 as g
+    tau, c, src = synth.grid_problem(n=12, seed=36, tau_range=(0.1, 120.0), block=4, source=4)
+    ny, nx = tau.shape
+    args = [np.ascontiguousarray(a, np.float32).ravel() for a in (tau, c, src)]
+    out = {}
+    for name, method, mt in (("analog", g.GMC_METHOD_ANALOG, 0.0), ("hybrid", g.GMC_METHOD_GMC, 1e30)):
+        _set(ictx, bank_capacity=1 << 14, precision=g.GMC_FP32, steps=4, gmc_min_tau=mt)
+        f = np.zeros(ny * nx)
+        st = g.transport_solve(ictx, nx, ny, *args, 3000, method, 29, f).as_dict()
+        out[name] = (f, st)
+    _set(ictx, gmc_min_tau=0.0)
+    fa, sa = out["analog"]
+    fh, sh = out["hybrid"]
+    np.testing.assert_allclose(fh, fa, rtol=1e-9, atol=1e-12 * np.abs(fa).max())
+    for k in ("transmissions", "collisions", "roulette_kills"):
+        assert sh[k] == sa[k], k

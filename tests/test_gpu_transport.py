@@ -161,3 +161,52 @@ def test_flight_cap_changes_no_result(gpu_ctx, kaiming_net, method):
         assert st["collisions"] == s0["collisions"]
         assert st["roulette_kills"] == s0["roulette_kills"]
     assert out[2][1]["waves"] > out[0][1]["waves"]  # the cap did cut walks
+
+
+def test_hybrid_all_thin_equals_analog(gpu_ctx, kaiming_net):
+    # gmc_min_tau above every cell: a GMC solve walks every cell, drawing the
+    # same random numbers as the analog solve, so the two agree history by
+    # history (up to the order of the FP64 tally additions)
+    import paper_2512_13965_gb300 as g
+    tau, c, src = synth.grid_problem(n=12, seed=35, tau_range=(0.1, 120.0), block=4, source=4)
+    _set(gpu_ctx, bank_capacity=1 << 14, precision=g.GMC_FP32, steps=4, gmc_min_tau=0.0)
+    fa, sa = _solve(gpu_ctx, tau, c, src, 4000, g.GMC_METHOD_ANALOG, 23)
+    _set(gpu_ctx, gmc_min_tau=1e30)
+    fh, sh = _solve(gpu_ctx, tau, c, src, 4000, g.GMC_METHOD_GMC, 23)
+    _set(gpu_ctx, gmc_min_tau=0.0)
+    np.testing.assert_allclose(fh, fa, rtol=1e-9, atol=1e-12 * np.abs(fa).max())
+    for k in ("transmissions", "collisions", "roulette_kills"):
+        assert sh[k] == sa[k], k
+
+
+def _hybrid_sampler(net, steps, seed, min_tau):
+    mlp = OT.mlp_sampler(net, steps, "euler", seed)
+    walk = OT.walk_sampler(seed)
+
+    def f(xi, cx, cy, t, cc, ids, events):
+        thin = np.asarray(t) < min_tau
+        out = [np.zeros(len(ids)) for _ in range(5)] + [np.zeros(len(ids), np.uint32)]
+        for sel, fn in ((thin, walk), (~thin, mlp)):
+            if sel.any():
+                res = fn(np.asarray(xi)[sel], np.asarray(cx)[sel], np.asarray(cy)[sel],
+                         np.asarray(t)[sel], np.asarray(cc)[sel], np.asarray(ids)[sel],
+                         np.asarray(events)[sel])
+                for a, v in zip(out, res):
+                    a[sel] = v
+        return out[0].astype(np.int64), out[1], out[2], out[3], out[4], out[5]
+    return f
+
+
+def test_hybrid_solve_matches_oracle(gpu_ctx, kaiming_net):
+    # cells thinner than 2 walked, thicker ones sampled (FP32 network)
+    import paper_2512_13965_gb300 as g
+    _set(gpu_ctx, precision=g.GMC_FP32, steps=4, integrator=g.GMC_EULER, bank_capacity=4096,
+         gmc_min_tau=2.0)
+    tau, c, src = synth.grid_problem(n=8, seed=31, tau_range=(0.1, 8.0), block=4, source=2)
+    n = 1500
+    fg, sg = _solve(gpu_ctx, tau, c, src, n, g.GMC_METHOD_GMC, 9)
+    _set(gpu_ctx, gmc_min_tau=0.0)
+    fo, so = OT.solve_gmc(tau, c, src, n, 9, _hybrid_sampler(kaiming_net, 4, 9, 2.0))
+    assert _rel_l2(fg, fo) < 0.03
+    assert abs(sg["transmissions"] - so["transmissions"]) < 0.02 * so["transmissions"]
+    assert sg["collisions"] > 0
