@@ -7,7 +7,7 @@ What it computes, in the paper's order:
     the explicit midpoint rule, or classical RK4, which the paper times).
   * Eq. 10 / Eq. 11 -- the condition c is the entry state and cell in optical
     coordinates and the state x is the exit state y = (p_exit, Omega_exit, s).
-    This build uses a square cell and directions on the unit circle, so
+    Here the cell is a square and directions lie on the unit circle, so
     c = (xi_in, cos theta_in, sin theta_in, ln tau, c_scat) and
     y = (p, cos theta_out, sin theta_out, ln s).
   * v_theta is a plain feed-forward network: input [c_std (5), x (4),
