@@ -181,6 +181,8 @@ def main():
                     help="GMCW file of the internal-source model (solve/serve: births sampled by it)")
     ap.add_argument("--histories", type=float, default=1e6)
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--hist-range", type=float, nargs=2, default=(1e3, 1e5),
+                    help="serve: histories per request, log-uniform in [lo, hi]")
     ap.add_argument("--solve-variants", default=None,
                     help="comma list for --workload solve, e.g. analog,gmc_bf16_rk412 (default: all)")
     args = ap.parse_args()
@@ -592,8 +594,8 @@ def run_heldout(args):
 def run_serve(args):
     """Serving: Poisson stream of solves, grids n x n with n ~ U{16..256},
     tau logU[0.1,1000], c {0.5,0.999} blocks, histories logU[1e3,1e5];
-    p50/p99 latency and solves/s for GMC (RK4, 12 steps; BF16 and FP8) and the
-    analog walk."""
+    p50/p99 latency and solves/s for GMC (RK4, 12 steps; BF16, FP8, and the hybrid
+    with cells thinner than tau = 64 walked) and the analog walk."""
     import numpy as np
     import synth
     g, ctx = _context(args)
@@ -603,19 +605,21 @@ def run_serve(args):
         n = int(rng.integers(16, 257))
         tau, c, src = synth.grid_problem(n=n, seed=1000 + k, tau_range=(0.1, 1000.0),
                                          block=16, source=max(2, n // 16))
-        hist = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
+        hist = int(np.exp(rng.uniform(np.log(args.hist_range[0]), np.log(args.hist_range[1]))))
         reqs.append((n, np.ascontiguousarray(tau.ravel()), np.ascontiguousarray(c.ravel()),
                      np.ascontiguousarray(src.ravel()), hist))
     out = {}
     # GMC with the integrator that reaches the analog floor on the 128^2
     # solve (RK4, 12 steps), in BF16 and FP8, against the analog walk
-    for name, method, prec in (("gmc_bf16_rk4_12", g.GMC_METHOD_GMC, g.GMC_BF16),
-                               ("gmc_fp8_rk4_12", g.GMC_METHOD_GMC, g.GMC_FP8),
-                               ("analog", g.GMC_METHOD_ANALOG, g.GMC_BF16)):
+    for name, method, prec, min_tau in (("gmc_bf16_rk4_12", g.GMC_METHOD_GMC, g.GMC_BF16, 0.0),
+                                        ("gmc_fp8_rk4_12", g.GMC_METHOD_GMC, g.GMC_FP8, 0.0),
+                                        ("hybrid64_bf16_rk4_12", g.GMC_METHOD_GMC, g.GMC_BF16, 64.0),
+                                        ("analog", g.GMC_METHOD_ANALOG, g.GMC_BF16, 0.0)):
         cfg = g.gmc_get_config(ctx)
         cfg.steps = 12
         cfg.integrator = g.GMC_RK4
         cfg.precision = prec
+        cfg.gmc_min_tau = min_tau
         cfg.bank_capacity = 1 << 20
         g.gmc_set_config(ctx, cfg)
         # capacity: the whole stream submitted at once
@@ -646,7 +650,9 @@ def run_serve(args):
                      "solves_per_s": len(reqs) / wall, "capacity_solves_per_s": cap,
                      "offered_load": 0.7, "transmissions_per_s": trans / wall}
     line = {"metric": METRIC, "workload": "serving: %d Poisson-arriving solves, n~U{16..256}, "
-            "tau logU[0.1,1000], histories logU[1e3,1e5]" % len(reqs), "results": out,
+            "tau logU[0.1,1000], histories logU[%g,%g]" % (len(reqs), args.hist_range[0],
+                                                          args.hist_range[1]), "results": out,
+            "births": ("internal model " + args.internal_weights) if args.internal_weights else "random walk",
             "weights": args.weights or "kaiming seed 1 (untrained)"}
     print(json.dumps(line))
     ctx.close()
