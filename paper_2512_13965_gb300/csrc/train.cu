@@ -53,6 +53,7 @@ struct TrainState {
   int64_t loss_cap = 0;
   double *stat_acc = nullptr;  // 18 sums
   float *ws = nullptr;         // split-K slices of the weight-gradient GEMMs (tensor-core path)
+  float *colpart = nullptr;    // partial column sums of the bias gradients
   size_t ws_floats = 0;
   int *err = nullptr;          // device error word of the context
 };
@@ -273,21 +274,44 @@ __global__ void loss_kernel(int64_t B, const float *__restrict__ V, const float 
   if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(loss, part / (double)B);
 }
 
-// db[n] = sum_b dZ[b][n]
-__global__ void colsum_kernel(int64_t B, int N, const float *__restrict__ dZ, float *__restrict__ db) {
-  const int n = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int lane_row = threadIdx.x >> 5;  // 8 row groups
+// db[n] = sum_b dZ[b][n] in two passes: blocks of kColRows rows give partial
+// sums (grid: column groups of 32 x row blocks), then one thread per column
+// adds the partials in block order (a fixed order: deterministic).
+constexpr int kColRows = 128;
+
+__global__ void colsum_partial_kernel(int64_t B, int N, const float *__restrict__ dZ,
+                                      float *__restrict__ partial) {
+  const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;  // 8 row groups
+  const int n = blockIdx.x * 32 + lane;
+  const int64_t b0 = (int64_t)blockIdx.y * kColRows;
+  const int64_t b1 = b0 + kColRows < B ? b0 + kColRows : B;
   float acc = 0.0f;
   if (n < N)
-    for (int64_t b = lane_row; b < B; b += 8) acc += dZ[b * N + n];
+    for (int64_t b = b0 + rg; b < b1; b += 8) acc += dZ[b * N + n];
   __shared__ float sh[8][33];
-  sh[lane_row][threadIdx.x & 31] = acc;
+  sh[rg][lane] = acc;
   __syncthreads();
-  if (lane_row == 0 && n < N) {
-    float s = 0.0f;
-    for (int r = 0; r < 8; ++r) s += sh[r][threadIdx.x & 31];
-    db[n] = s;
+  if (rg == 0 && n < N) {
+    float t = 0.0f;
+    for (int r = 0; r < 8; ++r) t += sh[r][lane];
+    partial[(int64_t)blockIdx.y * N + n] = t;
   }
+}
+
+__global__ void colsum_final_kernel(int P, int N, const float *__restrict__ partial,
+                                    float *__restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float t = 0.0f;
+  for (int p = 0; p < P; ++p) t += partial[(int64_t)p * N + n];
+  db[n] = t;
+}
+
+cudaError_t colsum(cudaStream_t s, int64_t B, int N, const float *dZ, float *partial, float *db) {
+  const int P = (int)((B + kColRows - 1) / kColRows);
+  colsum_partial_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)P), 256, 0, s>>>(B, N, dZ, partial);
+  colsum_final_kernel<<<(N + 255) / 256, 256, 0, s>>>(P, N, partial, db);
+  return cudaGetLastError();
 }
 
 __global__ void adamw_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g,
@@ -326,7 +350,8 @@ cudaError_t fwd_bwd(cudaStream_t s, TrainState &T, double *loss_slot) {
   // output layer: dW5 = dV^T A4, db5 = sum dV, dZ4 = (dV W5) * SiLU'(Z4)
   e = gemm<kEpiStore>(s, 4, 256, B, T.dV, 1, 4, T.A[3], 256, 1, G + P_W5);
   if (e) return e;
-  colsum_kernel<<<1, 256, 0, s>>>(B, 4, T.dV, G + P_B5);
+  e = colsum(s, B, 4, T.dV, T.colpart, G + P_B5);
+  if (e) return e;
   e = gemm<kEpiDSilu>(s, B, 256, 4, T.dV, 4, 1, P + P_W5, 256, 1, T.dZ[0], nullptr, nullptr, T.Z[3]);
   if (e) return e;
   int cur = 0;
@@ -338,7 +363,8 @@ cudaError_t fwd_bwd(cudaStream_t s, TrainState &T, double *loss_slot) {
     // dW_l = dZ_l^T A_{l-1}; db_l = column sums of dZ_l
     e = gemm<kEpiStore>(s, 256, kin, B, dz, 1, 256, ain, kin, 1, G + wofs[l]);
     if (e) return e;
-    colsum_kernel<<<8, 256, 0, s>>>(B, 256, dz, G + bofs[l]);
+    e = colsum(s, B, 256, dz, T.colpart, G + bofs[l]);
+    if (e) return e;
     if (l > 0) {
       // dZ_{l-1} = (dZ_l W_l) * SiLU'(Z_{l-1})
       e = gemm<kEpiDSilu>(s, B, 256, 256, dz, 256, 1, P + wofs[l], 256, 1, T.dZ[cur ^ 1], nullptr,
@@ -378,7 +404,8 @@ cudaError_t fwd_bwd_tc(cudaStream_t s, TrainState &T, double *loss_slot) {
   // dW5 = dV^T A4 (contraction over the batch), db5, dZ4 = (dV W5) * SiLU'(Z4)
   TG_TRY(s, kTgStore, 4, 256, B, T.dV, 1, 4, T.A[3], 1, 256, G + P_W5, nullptr, nullptr, nullptr,
          splits, T.ws, T.ws_floats, T.err);
-  colsum_kernel<<<1, 256, 0, s>>>(B, 4, T.dV, G + P_B5);
+  e = colsum(s, B, 4, T.dV, T.colpart, G + P_B5);
+  if (e) return e;
   TG_TRY(s, kTgDSilu, B, 256, 4, T.dV, 4, 1, P + P_W5, 1, 256, T.dZ[0], nullptr, nullptr, T.Z[3], 1,
          nullptr, 0, T.err);
   int cur = 0;
@@ -390,7 +417,8 @@ cudaError_t fwd_bwd_tc(cudaStream_t s, TrainState &T, double *loss_slot) {
     // dW_l[m][n] = sum_b dZ_l[b][m] A_{l-1}[b][n]
     TG_TRY(s, kTgStore, 256, kin, B, dz, 1, 256, ain, 1, kin, G + wofs[l], nullptr, nullptr, nullptr,
            splits, T.ws, T.ws_floats, T.err);
-    colsum_kernel<<<8, 256, 0, s>>>(B, 256, dz, G + bofs[l]);
+    e = colsum(s, B, 256, dz, T.colpart, G + bofs[l]);
+    if (e) return e;
     if (l > 0) {
       // dZ_{l-1}[b][n] = SiLU'(Z_{l-1}[b][n]) sum_k dZ_l[b][k] W_l[k][n]
       TG_TRY(s, kTgDSilu, B, 256, 256, dz, 256, 1, P + wofs[l], 1, 256, T.dZ[cur ^ 1], nullptr,
@@ -415,6 +443,7 @@ void free_train(TrainState *T) {
   if (T->loss) cudaFree(T->loss);
   if (T->stat_acc) cudaFree(T->stat_acc);
   if (T->ws) cudaFree(T->ws);
+  if (T->colpart) cudaFree(T->colpart);
   delete T;
 }
 
@@ -430,6 +459,10 @@ cudaError_t alloc_batch(TrainState &T, int64_t B) {
     cudaError_t e = cudaMalloc(bufs[i], sizes[i] * sizeof(float));
     if (e) return e;
   }
+  if (T.colpart) cudaFree(T.colpart);
+  T.colpart = nullptr;
+  cudaError_t e = cudaMalloc(&T.colpart, ((B + kColRows - 1) / kColRows) * 256 * sizeof(float));
+  if (e) return e;
   T.B = B;
   return cudaSuccess;
 }
