@@ -124,7 +124,7 @@ def deposit(w, s, tau, c):
 
 def mlp_sampler(net, steps, integrator, seed):
     """Stage 2 with the flow ODE: noise at (id, event, TAG_NOISE), one event used."""
-    def f(xi, cos_c, sin_c, tau, c, ids, events):
+    def f(xi, cos_c, sin_c, tau, c, ids, events, rot=None):
         cond = np.stack([xi, cos_c, sin_c, np.log(tau), c])
         z = rng.normals_for(seed, ids, events, rng.TAG_NOISE)
         d = mlp.decode(net, mlp.sample(net, cond, z, steps, integrator))
@@ -134,7 +134,7 @@ def mlp_sampler(net, steps, integrator, seed):
 
 def walk_sampler(seed):
     """Stage 2 replaced by the implicit-capture random walk in the canonical frame."""
-    def f(xi, cos_c, sin_c, tau, c, ids, events):
+    def f(xi, cos_c, sin_c, tau, c, ids, events, rot=None):
         r = transmit(xi, cos_c, sin_c, tau, c, MODE_IMPLICIT, seed, ids=ids, events=events)
         return r["face"], r["q"], r["ux"], r["uy"], r["s"], r["events"]
     return f
@@ -173,6 +173,39 @@ def walk_internal_sampler(seed):
                 a[k] = v
         return out[0].astype(np.int64), out[1], out[2], out[3], out[4], out[5]
     return f
+
+
+def walk_sampler_global(seed):
+    """Stage 2 replaced by the implicit-capture walk in the cell's own (global)
+    frame, as a random-walk solve takes it: entry face F = (rot - 1) mod 4 at
+    counter-clockwise parameter 1 - xi, global direction rot(canonical, rot);
+    the exit is returned in the canonical frame (face - rot, same q, direction
+    rotated back)."""
+    def f(xi, cos_c, sin_c, tau, c, ids, events, rot=None):
+        n = len(ids)
+        face = np.zeros(n, np.int64)
+        out = [np.zeros(n) for _ in range(4)]
+        ev = np.zeros(n, np.uint32)
+        for k in range(n):
+            r = int(rot[k])
+            F = (r - 1) % 4
+            x = float(xi[k])
+            X, Y = {0: (1.0 - x, 0.0), 1: (1.0, 1.0 - x), 2: (x, 1.0), 3: (0.0, x)}[F]
+            gx, gy = rot_dir(cos_c[k], sin_c[k], r)
+            w = walk_one(tau[k], c[k], MODE_IMPLICIT, X * tau[k], Y * tau[k], gx, gy, seed,
+                         int(ids[k]), int(events[k]))
+            face[k] = (w["face"] - r) % 4
+            ux, uy = rot_dir(w["ux"], w["uy"], -r)
+            out[0][k], out[1][k], out[2][k], out[3][k] = w["q"], ux, uy, w["s"]
+            ev[k] = w["event"]
+        return face, out[0], out[1], out[2], out[3], ev
+    return f
+
+
+def rot_dir(ux, uy, k):
+    """Scalar form of rot."""
+    rx, ry = rot(np.array([ux]), np.array([uy]), k)
+    return float(rx[0]), float(ry[0])
 
 
 def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max_waves=100000,
@@ -247,7 +280,7 @@ def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max
         t, cc = tf[cell], cf[cell]
         rr = np.mod(L["F"] + 1, 4)
         cx, cy = rot(L["gx"], L["gy"], -rr)
-        face, q, ux, uy, s, ev = sampler(L["xi"], cx, cy, t, cc, L["id"], L["ev"])
+        face, q, ux, uy, s, ev = sampler(L["xi"], cx, cy, t, cc, L["id"], L["ev"], rot=rr)
         st[3] += cell.size
         dw, score = deposit(L["w"], s, t, cc)
         np.add.at(flux, cell, score)

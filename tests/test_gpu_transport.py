@@ -180,17 +180,19 @@ def test_hybrid_all_thin_equals_analog(gpu_ctx, kaiming_net):
 
 
 def _hybrid_sampler(net, steps, seed, min_tau):
+    # the network in thick cells; in thin cells the walk in the cell's own
+    # frame, drawing what the GPU's random-walk kernel draws
     mlp = OT.mlp_sampler(net, steps, "euler", seed)
-    walk = OT.walk_sampler(seed)
+    walk = OT.walk_sampler_global(seed)
 
-    def f(xi, cx, cy, t, cc, ids, events):
+    def f(xi, cx, cy, t, cc, ids, events, rot=None):
         thin = np.asarray(t) < min_tau
         out = [np.zeros(len(ids)) for _ in range(5)] + [np.zeros(len(ids), np.uint32)]
         for sel, fn in ((thin, walk), (~thin, mlp)):
             if sel.any():
                 res = fn(np.asarray(xi)[sel], np.asarray(cx)[sel], np.asarray(cy)[sel],
                          np.asarray(t)[sel], np.asarray(cc)[sel], np.asarray(ids)[sel],
-                         np.asarray(events)[sel])
+                         np.asarray(events)[sel], rot=np.asarray(rot)[sel])
                 for a, v in zip(out, res):
                     a[sel] = v
         return out[0].astype(np.int64), out[1], out[2], out[3], out[4], out[5]
