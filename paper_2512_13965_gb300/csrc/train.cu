@@ -298,19 +298,24 @@ __global__ void colsum_partial_kernel(int64_t B, int N, const float *__restrict_
   }
 }
 
+// One warp per column: lane l adds partials l, l + 32, ..., then a fixed
+// shuffle tree combines the lanes (the same order on every run).
 __global__ void colsum_final_kernel(int P, int N, const float *__restrict__ partial,
                                     float *__restrict__ db) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
+  const int n = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (n >= N) return;  // whole warps leave together
   float t = 0.0f;
-  for (int p = 0; p < P; ++p) t += partial[(int64_t)p * N + n];
-  db[n] = t;
+  for (int p = lane; p < P; p += 32) t += partial[(int64_t)p * N + n];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (lane == 0) db[n] = t;
 }
 
 cudaError_t colsum(cudaStream_t s, int64_t B, int N, const float *dZ, float *partial, float *db) {
   const int P = (int)((B + kColRows - 1) / kColRows);
   colsum_partial_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)P), 256, 0, s>>>(B, N, dZ, partial);
-  colsum_final_kernel<<<(N + 255) / 256, 256, 0, s>>>(P, N, partial, db);
+  colsum_final_kernel<<<(N * 32 + 255) / 256, 256, 0, s>>>(P, N, partial, db);
   return cudaGetLastError();
 }
 

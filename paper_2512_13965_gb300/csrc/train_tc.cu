@@ -63,37 +63,45 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
 }
 
 // ROWS x 64 operand chunk (rows row0.., K k0..) into shared memory as BF16.
-// Work item = (row r, 8-column group c); out-of-range entries are zero.
+// Work item = (row r, 8-column group c); out-of-range entries are zero. Each
+// thread first issues the loads of all its items, then converts and stores
+// them, so a chunk costs about one memory latency, not one per item.
 template <int ROWS>
 __device__ __forceinline__ void stage(uint32_t sbase, const float *__restrict__ P, int64_t s_row,
                                       int64_t s_k, int row0, int nrows, int k0, int kend) {
   constexpr int ITEMS = ROWS * 8;
+  constexpr int PER = (ITEMS + TG_THREADS - 1) / TG_THREADS;
   const bool kcontig = s_k == 1;
-  for (int i = threadIdx.x; i < ITEMS; i += TG_THREADS) {
-    int r, c;
-    if (kcontig) {
-      r = i >> 3;
-      c = i & 7;
-    } else {
-      r = i % ROWS;
-      c = i / ROWS;
-    }
+  float v[PER][8];
+#pragma unroll
+  for (int it = 0; it < PER; ++it) {
+    const int i = threadIdx.x + it * TG_THREADS;
+    const int r = kcontig ? (i >> 3) : (i % ROWS);
+    const int c = kcontig ? (i & 7) : (i / ROWS);
     const int gr = row0 + r, gk = k0 + 8 * c;
-    float v[8];
     const float *src = P + (int64_t)gr * s_row + (int64_t)gk * s_k;
-    if (gr < nrows && kcontig && gk + 8 <= kend && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
+    if (i < ITEMS && gr < nrows && kcontig && gk + 8 <= kend &&
+        ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
       const float4 a = __ldg(reinterpret_cast<const float4 *>(src));
       const float4 b = __ldg(reinterpret_cast<const float4 *>(src) + 1);
-      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      v[it][0] = a.x; v[it][1] = a.y; v[it][2] = a.z; v[it][3] = a.w;
+      v[it][4] = b.x; v[it][5] = b.y; v[it][6] = b.z; v[it][7] = b.w;
     } else {
 #pragma unroll
       for (int j = 0; j < 8; ++j)
-        v[j] = (gr < nrows && gk + j < kend) ? __ldg(P + (int64_t)gr * s_row + (int64_t)(gk + j) * s_k)
-                                             : 0.0f;
+        v[it][j] = (i < ITEMS && gr < nrows && gk + j < kend)
+                       ? __ldg(P + (int64_t)gr * s_row + (int64_t)(gk + j) * s_k)
+                       : 0.0f;
     }
-    sts128(sw128_addr(sbase, r, c), bf16x2(v[0], v[1]), bf16x2(v[2], v[3]), bf16x2(v[4], v[5]),
-           bf16x2(v[6], v[7]));
+  }
+#pragma unroll
+  for (int it = 0; it < PER; ++it) {
+    const int i = threadIdx.x + it * TG_THREADS;
+    if (i >= ITEMS) break;
+    const int r = kcontig ? (i >> 3) : (i % ROWS);
+    const int c = kcontig ? (i & 7) : (i / ROWS);
+    sts128(sw128_addr(sbase, r, c), bf16x2(v[it][0], v[it][1]), bf16x2(v[it][2], v[it][3]),
+           bf16x2(v[it][4], v[it][5]), bf16x2(v[it][6], v[it][7]));
   }
 }
 
