@@ -1,30 +1,42 @@
 // BF16 tensor-core flow-ODE sampler (Eq. 8) for sm_103a: tcgen05 MMA with
-// FP32 accumulators in tensor memory, weights streamed by bulk async copies.
+// FP32 accumulators in tensor memory, the hidden activations kept in tensor
+// memory as the next layer's A operand, weights streamed by bulk async copies.
 //
 // Work unit: a tile of 128 particles. One persistent CTA per SM owns two
-// tiles (X, Y) at a time and runs all K steps of both, ping-ponging them so
-// that the tensor core computes one tile's layer while the epilogue warps
-// turn the other tile's accumulator into the next layer's operand:
+// tiles (X, Y) at a time and runs all K steps of both. Every layer is computed
+// as two N = 128 halves, each into one of two 128-column FP32 accumulators
+// (P, Q); epilogue group 0 converts every P, group 1 every Q, so the tensor
+// core computes one half while each group turns its previous half into
+// activations:
 //
-//   MMA warp:      L1(X) L1(Y) L2(X) L2(Y) ... L5(X) L5(Y) | next evaluation
-//   epilogue warps:       E1(X) E1(Y) E2(X) ...              (bias, SiLU, BF16)
+//   MMA warp:  X.P   X.Q   Y.P   Y.Q | next layer X.P ...
+//   group 0:         E(X.P)      E(Y.P)        (SiLU, BF16)
+//   group 1:               E(X.Q)      E(Y.Q)
+//
+// Tensor memory (512 columns): A_X, A_Y (cols 0-127, 128-255): the 128 x 256
+// BF16 operand of each tile (row m in lane m, two K values per column); P, Q
+// (256-383, 384-511): accumulators. The epilogue reads its accumulator half
+// into registers, releases it at once, and writes the activations back to A_T
+// with tcgen05.st once the tile's second half has finished reading A_T: no
+// shared-memory traffic for activations.
 //
 // Per evaluation of v_theta and tile (M = 128 rows):
-//   L1: [cn | x_hi | x_lo] (K = 16, BF16) x B1 (N = 256)       -> TMEM
+//   L1: [x_hi | x_lo | cn | 1 1 0] (K = 16, BF16, shared memory) x B1 -> P, Q
 //       (the time-embedding columns of layer 1 are the same for every row,
 //        so W1[:, emb] emb(t) + b1 is folded into an FP32 per-evaluation bias)
-//   L2..L4: A (128 x 256 BF16, shared memory, 128-byte swizzle) x W
-//       (256 x 256, streamed in chunks of all 256 output rows x CHUNK_K)
-//       -> TMEM, N = 256 per MMA
-//   L5: A x W5 (N = 16, rows 4..15 zero) -> TMEM columns 0..3
+//   L2..L4: A_T (tensor memory) x W (shared memory, streamed in chunks of
+//       128 output rows x 128 bytes of K) -> P, Q
+//   L5: A_T x W5 (N = 16, rows 4..15 zero) -> P (tile X) or Q (tile Y)
 // Epilogue: SiLU(z) = h + h tanh(h) with h = z/2 (layers 1-4 are packed with
-// weights and biases halved, so the accumulator holds h), in packed BF16x2,
-// written back as the next layer's BF16 operand in the 128-byte-swizzled
-// K-major layout. The ODE state x stays in FP32 registers of the row's
-// epilogue thread.
+// weights and biases halved, so the accumulator holds h), in packed BF16x2.
+// The biases of layers 2-4 enter the accumulator through one extra K = 16 MMA
+// (two constant-1 columns of the layer-1 operand against the bias split into
+// BF16 hi + lo); layer 1's bias, which depends on t, is added in the epilogue.
+// The ODE state x of tile T stays in FP32 registers of group T's threads.
 //
 // Roles: warp 0 streams weights, warp 1 owns tensor memory and issues MMAs,
-// warps 2.. are the epilogue (EPI_WARPS / 4 threads per row).
+// warps 2..17 are the epilogue: two groups of 8 warps, two threads per row and
+// half, each loading its 64 columns at once and converting them in 16-column pieces.
 // CTAs run in clusters of two that consume the same weight chunks in the
 // same order: each CTA copies half of every chunk from L2 and multicasts it
 // into both CTAs' stage, so L2 serves each chunk once per pair; a stage is
@@ -36,11 +48,11 @@
 // W2..W4 is stored as E4M3 codes of W[c][:] / s_c with s_c = max_k |W[c][k]| / 448
 // (per-output-channel scale, FP32), and the epilogue applies h = acc s_c / 2
 // + b_c / 2 in one FMA. Activations entering layers 2-4 are E4M3 with unit
-// scale (SiLU outputs are >= -0.279 and far below E4M3's 448). Layer 1 keeps
-// BF16 operands (the ODE state enters through them) and layer 4's epilogue
-// writes BF16, so layer 5 (the velocity) is the same BF16 MMA as above.
-// A 16 KB weight chunk then holds 64 inputs instead of 32; byte offsets in
-// the operand rows are the same, so descriptors advance identically.
+// scale (SiLU outputs are >= -0.279 and far below E4M3's 448), four per
+// tensor-memory column. Layer 1 keeps BF16 operands (the ODE state enters
+// through them) and layer 4's epilogue writes BF16, so layer 5 (the velocity)
+// is the same BF16 MMA as above. A 16 KB weight chunk then holds 128 inputs
+// instead of 64; a K step is 32 bytes (8 A columns) in both variants.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -58,72 +70,59 @@ namespace {
 using namespace ptx;
 
 constexpr int TM = 128;
-#ifndef GMC_TC_CHUNK_K
-#define GMC_TC_CHUNK_K 32
-#endif
-#ifndef GMC_TC_EPI_WARPS
-#define GMC_TC_EPI_WARPS 16
-#endif
-// Weight chunk: all 256 output rows x CHUNK_K inputs, K-major; 32 -> 64-byte
-// swizzle (16 KB), 64 -> 128-byte swizzle (32 KB).
-constexpr int CHUNK_K = GMC_TC_CHUNK_K;
-constexpr uint32_t CHUNK = 256u * CHUNK_K * 2u;
-constexpr int MMAS_PER_CHUNK = CHUNK_K / 16;
-constexpr uint32_t CHUNK_SWIZZLE = CHUNK_K == 32 ? 4u /* 64B */ : 2u /* 128B */;
-constexpr uint32_t CHUNK_SBO = CHUNK_K == 32 ? 512u : 1024u;
-constexpr int NST = (81920 / CHUNK) > 5 ? 5 : (int)(81920 / CHUNK);  // stages in 80 KB
-#ifndef GMC_TC_SPLIT_TILES
-#define GMC_TC_SPLIT_TILES 0  // measured on GB300: 1 is 8 % slower (6.65 vs 6.13 ms per 2^20 x 16 steps)
-#endif
-constexpr int EPI_WARPS = GMC_TC_EPI_WARPS;      // a multiple of 8 (2 groups x TMEM lane quadrants)
-constexpr bool SPLIT_TILES = GMC_TC_SPLIT_TILES != 0;  // one epilogue group per tile
-constexpr int TPW = SPLIT_TILES ? 1 : 2;          // tiles served by each epilogue warp
-constexpr int GROUP_WARPS = SPLIT_TILES ? EPI_WARPS / 2 : EPI_WARPS;  // warps per tile
-constexpr int EPI_COLS = 256 / (GROUP_WARPS / 4);  // accumulator columns per epilogue thread
-#ifndef GMC_TC_EPI_CW
-#define GMC_TC_EPI_CW 32
-#endif
-#ifndef GMC_TC_EPI_CW8
-#define GMC_TC_EPI_CW8 16
-#endif
-constexpr int EPI_CW = GMC_TC_EPI_CW;    // accumulator columns per TMEM load, BF16 variant
-constexpr int EPI_CW8 = GMC_TC_EPI_CW8;  // the same for the FP8 variant (more live registers)
-static_assert((EPI_CW == 16 || EPI_CW == 32) && (EPI_CW8 == 16 || EPI_CW8 == 32), "TMEM load width");
+constexpr int EPI_WARPS = 16;                 // two groups of 8, one per 128 output columns
+constexpr int GROUP_WARPS = EPI_WARPS / 2;    // 2 per TMEM lane quadrant, 64 columns each
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
-static_assert(CHUNK_K == 32 || CHUNK_K == 64, "chunk K");
-static_assert(EPI_WARPS == 8 || EPI_WARPS == 16, "epilogue warps");
-constexpr int CLUSTER = 2;               // CTAs sharing each weight chunk by multicast
+constexpr int NH = 128;                       // output columns of one epilogue group
+constexpr int CLUSTER = 2;                    // CTAs sharing each weight chunk by multicast
+// Weight chunk: all 256 output rows x 128 bytes of K (64 BF16 or 128 E4M3
+// inputs), K-major, 128-byte swizzle; 32 KB.
+constexpr uint32_t CHUNK = 256u * 128u;
 constexpr uint32_t SLICE = CHUNK / CLUSTER;
-constexpr uint32_t TMEM_COLS = 512;     // two 128 x 256 FP32 accumulators
-constexpr int ROW_BYTES = CHUNK_K * 2;  // bytes of one output row in a weight chunk
+constexpr int MMAS_PER_CHUNK = 4;             // 32 bytes of K per MMA
+#ifndef GMC_TC_STAGES
+#define GMC_TC_STAGES 5
+#endif
+constexpr int NST = GMC_TC_STAGES;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t COL_A = 0;                 // + 128 T: operand of tile T
+constexpr uint32_t COL_D = 256;               // the 128 x 256 FP32 accumulator
 
 // packed global operand buffer (bytes): hidden-layer chunks, then the BF16
 // operands of layers 1 and 5
 template <bool FP8>
 struct Packed {
-  static constexpr int NCH = 256 * (FP8 ? 1 : 2) / ROW_BYTES;  // chunks per hidden layer
+  static constexpr int NCH = 256 * (FP8 ? 1 : 2) / 128;  // chunks per hidden layer
   static constexpr size_t OFF_HID = 0;                  // [layer 0..2][chunk] x CHUNK
   static constexpr size_t OFF_B1 = 3 * (size_t)NCH * CHUNK;  // 256 rows x 32 B, 32-byte swizzle
-  static constexpr size_t OFF_B5 = OFF_B1 + 8192;      // 4 K-blocks x 16 rows x 128 B
-  static constexpr size_t BYTES = OFF_B5 + 8192;
+  static constexpr size_t OFF_B5 = OFF_B1 + 8192;       // 4 K-blocks x 16 rows x 128 B
+  // BF16 only: biases of layers 2-4 as one block per layer of 256 rows x 32 B
+  // (32-byte swizzle), K = 16 with the bias in columns 13 (BF16 value) and 14
+  // (BF16 remainder), the others zero
+  static constexpr size_t OFF_BIAS = OFF_B5 + 8192;
+  static constexpr size_t BYTES = OFF_BIAS + 24576;
 };
 
 // shared memory (offsets from a 1024-byte aligned base)
-constexpr uint32_t S_A0 = 0;                     // tile X operand, 64 KB
-constexpr uint32_t S_A1 = 65536;                 // tile Y operand, 64 KB
-constexpr uint32_t S_B1 = 131072;                // 8 KB
-constexpr uint32_t S_B5 = 139264;                // 8 KB
-constexpr uint32_t S_ST = 147456;                // NST weight stages
+constexpr uint32_t S_A1 = 0;                     // layer-1 operands of tiles X, Y: 2 x 4 KB
+constexpr uint32_t S_B1 = 8192;                  // 8 KB
+constexpr uint32_t S_B5 = 16384;                 // 8 KB
+constexpr uint32_t S_BIAS = 24576;               // 24 KB (BF16 variant)
+constexpr uint32_t S_ST = 49152;                 // NST weight stages
 constexpr uint32_t S_BAR = S_ST + NST * CHUNK;   // barriers and flags
 constexpr uint32_t S_TOTAL = S_BAR + 256;
 constexpr uint32_t SMEM_BYTES = S_TOTAL + 1024;  // + alignment slack
+// More than half of the SM's shared memory, so no second CTA (which would
+// wait for the 512 tensor-memory columns this one holds) shares the SM.
+static_assert(SMEM_BYTES > 116 * 1024 && SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
 
 struct Bars {
   uint64_t full[NST];
   uint64_t empty[NST];
   uint64_t res_full;
-  uint64_t a_ready[2];
-  uint64_t mma_done[2];
+  uint64_t ar[2][2];    // [T][g]: group g's part of tile T's next operand written
+  uint64_t dfull;       // accumulator computed (MMA commit)
+  uint64_t dfree;       // accumulator read out (all epilogue warps)
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
@@ -171,11 +170,6 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                : "memory");
 }
 
-// 16 B chunk `c` (0..7) of row `r` in a 128-byte-swizzled K-block.
-__device__ __forceinline__ uint32_t sw128(uint32_t base, int r, int c) {
-  return base + (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
-}
-
 // 16 B chunk `c` (0..1) of row `r` in a 32-byte-swizzled block.
 __device__ __forceinline__ uint32_t sw32(uint32_t base, int r, int c) {
   return base + (uint32_t)((r >> 3) * 256 + (r & 7) * 32 + ((c ^ ((r >> 2) & 1)) << 4));
@@ -203,12 +197,14 @@ __device__ __forceinline__ void bulk_g2s_multicast(void *dst, const void *src, u
       : "memory");
 }
 
-// Arrive on the barrier at the same offset in every CTA of `mask` once this
-// thread's tcgen05 operations have completed.
-__device__ __forceinline__ void mma_commit_multicast(uint64_t *bar, uint16_t mask) {
+// Arrive on the barrier at the same offset in every CTA of `mask` once the
+// tcgen05 operations issued so far have completed (warp-wide, one lane issues).
+__device__ __forceinline__ void mma_commit_multicast_w(uint64_t *bar, uint16_t mask) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
-      "[%0], %1;" ::"r"(smem_u32(bar)),
+      "{\n\t.reg .pred e;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+      "[%0], %1;\n\t}" ::"r"(smem_u32(bar)),
       "h"(mask)
       : "memory");
 }
@@ -218,19 +214,24 @@ __device__ void fail(Bars &b, int *err, int code) {
   atomicExch(err, code);
 }
 
-// Layer-1 operand row: [cn0..cn4, x_hi0..3, x_lo0..3, 0, 0, 0] in BF16.
-__device__ __forceinline__ void write_a1(uint32_t a_base, int r, const float (&cn)[kCond],
-                                        const float (&x)[4]) {
+// Layer-1 operand row: [x_hi0..3, x_lo0..3 | cn0..cn4, 1, 1, 0] in BF16. The
+// normalized condition (second 16 bytes) is written once per tile; every
+// evaluation rewrites only the ODE state (first 16 bytes). Layer 1's weights
+// are zero in columns 13-14; the bias blocks of layers 2-4 use them.
+__device__ __forceinline__ void write_a1_cond(uint32_t a_base, int r, const float (&cn)[kCond]) {
+  st_shared_v4(sw32(a_base, r, 1), pack_bf16x2(cn[0], cn[1]), pack_bf16x2(cn[2], cn[3]),
+               pack_bf16x2(cn[4], 1.0f), pack_bf16x2(1.0f, 0.0f));
+}
+
+__device__ __forceinline__ void write_a1_x(uint32_t a_base, int r, const float (&x)[4]) {
   float hi[4], lo[4];
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
     hi[d] = __bfloat162float(__float2bfloat16_rn(x[d]));
     lo[d] = x[d] - hi[d];
   }
-  st_shared_v4(sw32(a_base, r, 0), pack_bf16x2(cn[0], cn[1]), pack_bf16x2(cn[2], cn[3]),
-               pack_bf16x2(cn[4], hi[0]), pack_bf16x2(hi[1], hi[2]));
-  st_shared_v4(sw32(a_base, r, 1), pack_bf16x2(hi[3], lo[0]), pack_bf16x2(lo[1], lo[2]),
-               pack_bf16x2(lo[3], 0.0f), pack_bf16x2(0.0f, 0.0f));
+  st_shared_v4(sw32(a_base, r, 0), pack_bf16x2(hi[0], hi[1]), pack_bf16x2(hi[2], hi[3]),
+               pack_bf16x2(lo[0], lo[1]), pack_bf16x2(lo[2], lo[3]));
 }
 
 // Halved pre-activations of 4 accumulator columns: acc + bias, or with
@@ -254,101 +255,62 @@ __device__ __forceinline__ float4 pre4(const uint32_t *p, const float4 *b4, cons
   return z;
 }
 
-// bias (and scale) + SiLU on 32 accumulator columns starting at col0,
-// stored into the next layer's operand row r: BF16 (four 16-byte chunks of
-// a 64-column K-block) or, with OUT8, E4M3 (two 16-byte chunks of a
-// 128-column K-block). Both K-blocks have 128-byte rows, 128-byte swizzle.
-template <bool SCALED, bool OUT8>
-__device__ __forceinline__ void epi32(const uint32_t (&v)[32], const float *__restrict__ bias,
-                                      const float *__restrict__ scale, int col0, uint32_t a_base,
-                                      int r) {
-  const float4 *b4 = reinterpret_cast<const float4 *>(bias + col0);
-  const float4 *s4 = SCALED ? reinterpret_cast<const float4 *>(scale + col0) : nullptr;
-  if constexpr (OUT8) {
-    const uint32_t kb_base = a_base + (uint32_t)(col0 >> 7) * 16384u;
-    const int c0 = (col0 & 127) >> 4;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      uint32_t w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int q = 4 * j + i;
-        const float4 z = pre4<SCALED>(v + 4 * q, b4, s4, q);
-        w[i] = silu2_halved_e4m3(z.x, z.y) | (silu2_halved_e4m3(z.z, z.w) << 16);
-      }
-      st_shared_v4(sw128(kb_base, r, c0 + j), w[0], w[1], w[2], w[3]);
-    }
-  } else {
-    const uint32_t kb_base = a_base + (uint32_t)(col0 >> 6) * 16384u;
-    const int c0 = (col0 & 63) >> 3;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float4 za = pre4<SCALED>(v + 8 * j, b4, s4, 2 * j);
-      const float4 zb = pre4<SCALED>(v + 8 * j + 4, b4, s4, 2 * j + 1);
-      st_shared_v4(sw128(kb_base, r, c0 + j), silu2_halved(za.x, za.y), silu2_halved(za.z, za.w),
-                   silu2_halved(zb.x, zb.y), silu2_halved(zb.z, zb.w));
-    }
-  }
-}
 
-// bias (and scale) + SiLU on 16 accumulator columns starting at col0 (a
-// multiple of 16): one 16-byte E4M3 chunk, or with !OUT8 two BF16 chunks.
-template <bool SCALED, bool OUT8>
-__device__ __forceinline__ void epi16(const uint32_t (&v)[16], const float *__restrict__ bias,
-                                      const float *__restrict__ scale, int col0, uint32_t a_base,
-                                      int r) {
-  const float4 *b4 = reinterpret_cast<const float4 *>(bias + col0);
-  const float4 *s4 = SCALED ? reinterpret_cast<const float4 *>(scale + col0) : nullptr;
-  if constexpr (OUT8) {
-    uint32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float4 z = pre4<SCALED>(v + 4 * q, b4, s4, q);
-      w[q] = silu2_halved_e4m3(z.x, z.y) | (silu2_halved_e4m3(z.z, z.w) << 16);
-    }
-    st_shared_v4(sw128(a_base + (uint32_t)(col0 >> 7) * 16384u, r, (col0 & 127) >> 4), w[0], w[1],
-                 w[2], w[3]);
-  } else {
-    const uint32_t kb_base = a_base + (uint32_t)(col0 >> 6) * 16384u;
-    const int c0 = (col0 & 63) >> 3;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const float4 za = pre4<SCALED>(v + 8 * j, b4, s4, 2 * j);
-      const float4 zb = pre4<SCALED>(v + 8 * j + 4, b4, s4, 2 * j + 1);
-      st_shared_v4(sw128(kb_base, r, c0 + j), silu2_halved(za.x, za.y), silu2_halved(za.z, za.w),
-                   silu2_halved(zb.x, zb.y), silu2_halved(zb.z, zb.w));
-    }
-  }
-}
+// Epilogue pre-activation modes: the bias already in the accumulator (BF16
+// layers 2-4, whose bias enters through the MMA), bias added here (layer 1,
+// whose bias depends on t), or per-channel scale and bias (FP8 layers 2-4).
+enum : int { kPreNone = 0, kPreBias = 1, kPreScaleBias = 2 };
 
-// One epilogue thread's EPI_COLS columns of a 128 x 256 accumulator: the
-// load of the next 32 (CW = 32) or 16 (CW = 16, fewer live registers)
-// columns is in flight while the current ones are converted and stored.
-template <bool SCALED, bool OUT8, int CW = 32>
-__device__ __forceinline__ void epi_layer(uint32_t tcol, const float *__restrict__ bias,
-                                          const float *__restrict__ scale, int col0,
-                                          uint32_t a_base, int r) {
-  constexpr int NCH = EPI_COLS / CW;
-  uint32_t buf[2][CW];
-  if constexpr (CW == 32) {
-    tmem_ld32_raw(tcol, buf[0]);
-    tmem_wait_ld_regs(buf[0]);
-  } else {
-    tmem_ld16_raw(tcol, buf[0]);
-    tmem_wait_ld_regs16(buf[0]);
-  }
+// SiLU of one thread's 16 accumulator columns starting at col0, packed as the
+// next layer's operand: 8 BF16x2 words or, with OUT8, 4 words of four E4M3
+// codes (low byte first).
+template <int MODE, bool OUT8>
+__device__ __forceinline__ void silu16(const uint32_t *v, const float *__restrict__ bias,
+                                       const float *__restrict__ scale, int col0, uint32_t (&w)[8]) {
+  const float4 *b4 = reinterpret_cast<const float4 *>(bias + col0);
+  const float4 *s4 = reinterpret_cast<const float4 *>(scale + col0);
 #pragma unroll
-  for (int j = 0; j < NCH; ++j) {
-    if constexpr (CW == 32) {
-      if (j + 1 < NCH) tmem_ld32_raw(tcol + 32u * (uint32_t)(j + 1), buf[(j + 1) & 1]);
-      epi32<SCALED, OUT8>(buf[j & 1], bias, scale, col0 + 32 * j, a_base, r);
-      if (j + 1 < NCH) tmem_wait_ld_regs(buf[(j + 1) & 1]);
+  for (int q = 0; q < 4; ++q) {
+    float4 z;
+    if constexpr (MODE == kPreNone) {
+      z = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                      __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
     } else {
-      if (j + 1 < NCH) tmem_ld16_raw(tcol + 16u * (uint32_t)(j + 1), buf[(j + 1) & 1]);
-      epi16<SCALED, OUT8>(buf[j & 1], bias, scale, col0 + 16 * j, a_base, r);
-      if (j + 1 < NCH) tmem_wait_ld_regs16(buf[(j + 1) & 1]);
+      z = pre4<MODE == kPreScaleBias>(v + 4 * q, b4, s4, q);
+    }
+    if constexpr (OUT8) {
+      w[q] = silu2_halved_e4m3(z.x, z.y) | (silu2_halved_e4m3(z.z, z.w) << 16);
+    } else {
+      w[2 * q] = silu2_halved(z.x, z.y);
+      w[2 * q + 1] = silu2_halved(z.z, z.w);
     }
   }
+}
+
+// One 16-column piece of layer L's epilogue: activations of accumulator
+// columns col0.. (of 256) written into this thread's row of A_T. BF16: K =
+// col0 at column col0 / 2; E4M3 (FP8 layers 1-3): column col0 / 4.
+template <bool FP8>
+__device__ __forceinline__ void epi_piece(int L, const uint32_t *v, const float *bias,
+                                          const float *scale, int col0, uint32_t a_row) {
+  uint32_t w[8];
+  if constexpr (FP8) {
+    if (L < 3) {
+      if (L == 0)
+        silu16<kPreBias, true>(v, bias, nullptr, col0, w);
+      else
+        silu16<kPreScaleBias, true>(v, bias, scale + (L - 1) * 256, col0, w);
+      tmem_st4(a_row + (uint32_t)(col0 >> 2), w);
+      return;
+    }
+    silu16<kPreScaleBias, false>(v, bias, scale + 2 * 256, col0, w);
+  } else {
+    if (L == 0)
+      silu16<kPreBias, false>(v, bias, nullptr, col0, w);
+    else
+      silu16<kPreNone, false>(v, bias, nullptr, col0, w);
+  }
+  tmem_st8(a_row + (uint32_t)(col0 >> 1), w);
 }
 
 struct Params {
@@ -387,9 +349,11 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     }
     mbar_init(&B.res_full, 1);
     for (int t = 0; t < 2; ++t) {
-      mbar_init(&B.a_ready[t], GROUP_WARPS);
-      mbar_init(&B.mma_done[t], 1);
+      mbar_init(&B.ar[t][0], GROUP_WARPS);
+      mbar_init(&B.ar[t][1], GROUP_WARPS);
     }
+    mbar_init(&B.dfull, 1);
+    mbar_init(&B.dfree, EPI_WARPS);
     mbar_init(&B.drain, 1);
     B.abort = 0;
     fence_mbar_init();
@@ -419,27 +383,30 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
-      mbar_arrive_expect_tx(&B.res_full, 16384);
+      mbar_arrive_expect_tx(&B.res_full, 16384 + (FP8 ? 0 : 24576));
       bulk_g2s(sm + S_B1, P.packed + PK::OFF_B1, 8192, &B.res_full);
       bulk_g2s(sm + S_B5, P.packed + PK::OFF_B5, 8192, &B.res_full);
+      if (!FP8) bulk_g2s(sm + S_BIAS, P.packed + PK::OFF_BIAS, 24576, &B.res_full);
+      // the MMA warp's order: per hidden layer and tile, its chunks
       for (int64_t ip = 0; ip < n_iter && ok; ++ip)
         for (int e = 0; e < P.n_eval && ok; ++e)
           for (int L = 0; L < 3 && ok; ++L)
             for (int T = 0; T < 2 && ok; ++T)
-              for (int ch = 0; ch < NCH; ++ch) {
-                const int s = it % NST;
-                const uint32_t round = it / NST;
-                if (!mbar_wait(&B.empty[s], (round & 1u) ^ 1u, abort)) {
-                  fail(B, P.err, 1);
-                  ok = false;
-                  break;
+                for (int ch = 0; ch < NCH; ++ch) {
+                  const int s = it % NST;
+                  const uint32_t round = it / NST;
+                  if (!mbar_wait(&B.empty[s], (round & 1u) ^ 1u, abort)) {
+                    fail(B, P.err, 1);
+                    ok = false;
+                    break;
+                  }
+                  mbar_arrive_expect_tx(&B.full[s], CHUNK);
+                  bulk_g2s_multicast(
+                      sm + S_ST + s * CHUNK + rank * SLICE,
+                      P.packed + PK::OFF_HID + (size_t)(L * NCH + ch) * CHUNK + rank * SLICE,
+                      SLICE, &B.full[s], all_ctas);
+                  ++it;
                 }
-                mbar_arrive_expect_tx(&B.full[s], CHUNK);
-                bulk_g2s_multicast(sm + S_ST + s * CHUNK + rank * SLICE,
-                                   P.packed + PK::OFF_HID + (size_t)(L * NCH + ch) * CHUNK + rank * SLICE,
-                                   SLICE, &B.full[s], all_ctas);
-                ++it;
-              }
       if (!ok) {
         // drain: every issued copy lands before the CTA exits
         int never = 0;
@@ -450,66 +417,83 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    // The issuing thread shares its scheduler with busy epilogue warps, so the
-    // loop is kept lean: descriptors are built once and advanced by constant
-    // offsets (the start-address field counts 16-byte units), the chunk loop
-    // is unrolled, and a stage that has already landed costs one try_wait.
-    if (lane == 0) {
-      bool ok = mbar_wait(&B.res_full, 0, abort);
-      if (!ok) fail(B, P.err, 2);
-      uint32_t aph[2] = {0, 0};
+    // The whole warp runs the loop with warp-uniform values, and one elected
+    // lane issues each tcgen05 instruction, so descriptors and addresses stay
+    // uniform and an MMA issues in a few cycles. Descriptors are built once
+    // and advanced by constant offsets (the start-address field counts 16-byte
+    // units); a barrier phase that has already completed costs one try_wait.
+    {
+      // every lane waits (and acquires); the result is made warp-uniform
+      auto wwait = [&](uint64_t *bar, uint32_t parity) {
+        const bool r = mbar_try_wait(bar, parity) || mbar_wait(bar, parity, abort);
+        return __all_sync(0xffffffffu, r);
+      };
+      bool ok = wwait(&B.res_full, 0);
+      if (!ok && lane == 0) fail(B, P.err, 2);
+      uint32_t aph[2][2] = {{0, 0}, {0, 0}}, fph = 0;
       uint32_t stage = 0, sph = 0;  // next weight stage and its phase parity
-      const uint32_t id256 = idesc_bf16_m128(256), id16 = idesc_bf16_m128(16);
-      const uint32_t idh = FP8 ? idesc_e4m3_m128(256) : id256;  // hidden layers
-      const uint64_t dA[2] = {smem_desc(sbase + S_A0, 1024, kSwizzle128B),
-                              smem_desc(sbase + S_A1, 1024, kSwizzle128B)};
-      const uint64_t dA1[2] = {smem_desc(sbase + S_A0, 256, kSwizzle32B),
-                               smem_desc(sbase + S_A1, 256, kSwizzle32B)};
+      const uint32_t idn = idesc_bf16_m128(256), id16 = idesc_bf16_m128(16);
+      const uint32_t idh = FP8 ? idesc_e4m3_m128(256) : idn;  // hidden layers
+      const uint64_t dA1[2] = {smem_desc(sbase + S_A1, 256, kSwizzle32B),
+                               smem_desc(sbase + S_A1 + 4096, 256, kSwizzle32B)};
       const uint64_t dB1 = smem_desc(sbase + S_B1, 256, kSwizzle32B);
       const uint64_t dB5 = smem_desc(sbase + S_B5, 1024, kSwizzle128B);
-      const uint64_t dST = smem_desc(sbase + S_ST, CHUNK_SBO, CHUNK_SWIZZLE);
+      const uint64_t dBias = smem_desc(sbase + S_BIAS, 256, kSwizzle32B);
+      const uint64_t dST = smem_desc(sbase + S_ST, 1024, kSwizzle128B);
+      auto wait_ar = [&](int T, int g) {
+        if (!wwait(&B.ar[T][g], aph[T][g] & 1u)) {
+          if (lane == 0) fail(B, P.err, 3);
+          return false;
+        }
+        ++aph[T][g];
+        return true;
+      };
       for (int64_t ip = 0; ip < n_iter && ok; ++ip)
         for (int e = 0; e < P.n_eval && ok; ++e)
           for (int L = 0; L < 5 && ok; ++L)
             for (int T = 0; T < 2 && ok; ++T) {
-              if (!mbar_try_wait(&B.a_ready[T], aph[T] & 1u) &&
-                  !mbar_wait(&B.a_ready[T], aph[T] & 1u, abort)) {
-                fail(B, P.err, 3);
+              // layer 1 reads the tile's shared-memory operand, written by the
+              // group that owns the tile's ODE state; later layers read A_T,
+              // written half by each group
+              if (L == 0) ok = wait_ar(T, T);
+              else ok = wait_ar(T, 0) && wait_ar(T, 1);
+              if (!ok) break;
+              if (!wwait(&B.dfree, (fph & 1u) ^ 1u)) {
+                if (lane == 0) fail(B, P.err, 7);
                 ok = false;
                 break;
               }
-              ++aph[T];
+              ++fph;
               tc_fence_after();
-              const uint32_t d = tmem + (uint32_t)T * 256u;
+              const uint32_t d = tmem + COL_D;
+              const uint32_t a = tmem + COL_A + 128u * (uint32_t)T;
               if (L == 0) {
-                mma_f16(d, dA1[T], dB1, id256, 0);
+                mma_f16_w(d, dA1[T], dB1, idn, 0);
               } else if (L < 4) {
-                const uint64_t a0 = dA[T];
+                // BF16: D = bias first (the two constant-1 columns of the
+                // tile's layer-1 operand times the bias block's hi/lo columns)
+                if (!FP8) mma_f16_w(d, dA1[T], dBias + (uint64_t)((L - 1) * 512), idn, 0);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
-                  if (!mbar_try_wait(&B.full[stage], sph) && !mbar_wait(&B.full[stage], sph, abort)) {
-                    fail(B, P.err, 4);
+                  if (!wwait(&B.full[stage], sph)) {
+                    if (lane == 0) fail(B, P.err, 4);
                     ok = false;
                     break;
                   }
                   tc_fence_after();
-                  // chunk ch = operand bytes ROW_BYTES ch .. of all 256 output
-                  // rows (CHUNK_K BF16 or 2 CHUNK_K E4M3 inputs): A at K-block
-                  // (ROW_BYTES ch)/128, byte (ROW_BYTES ch) % 128 of its rows;
-                  // each MMA takes 32 bytes of K
-                  const int kb = ch * ROW_BYTES;
-                  const uint64_t a_ch = a0 + (uint64_t)((kb >> 7) * 1024 + ((kb & 127) >> 4));
+                  // chunk ch = operand bytes 128 ch .. of all 256 output rows;
+                  // each MMA takes 32 bytes of K = 8 columns of A_T
                   const uint64_t b_ch = dST + (uint64_t)(stage * (CHUNK >> 4));
 #pragma unroll
                   for (int k = 0; k < MMAS_PER_CHUNK; ++k) {
+                    const uint32_t a_k = a + (uint32_t)(32 * ch + 8 * k);
+                    const uint32_t acc = FP8 ? (uint32_t)((ch | k) != 0) : 1u;
                     if constexpr (FP8)
-                      mma_f8(d, a_ch + (uint64_t)(2 * k), b_ch + (uint64_t)(2 * k), idh,
-                             (ch | k) != 0);
+                      mma_ts_f8_w(d, a_k, b_ch + (uint64_t)(2 * k), idh, acc);
                     else
-                      mma_f16(d, a_ch + (uint64_t)(2 * k), b_ch + (uint64_t)(2 * k), idh,
-                              (ch | k) != 0);
+                      mma_ts_f16_w(d, a_k, b_ch + (uint64_t)(2 * k), idh, acc);
                   }
-                  mma_commit_multicast(&B.empty[stage], all_ctas);
+                  mma_commit_multicast_w(&B.empty[stage], all_ctas);
                   if (++stage == NST) {
                     stage = 0;
                     sph ^= 1u;
@@ -517,165 +501,174 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
                 }
                 if (!ok) break;
               } else {
-                const uint64_t a0 = dA[T];
+                // velocity: K = 256 BF16 = 16 MMAs of 8 columns; B5 in four
+                // 2 KB K-blocks of 128-byte rows
 #pragma unroll
-                for (int kb = 0; kb < 4; ++kb)
-#pragma unroll
-                  for (int k = 0; k < 4; ++k)
-                    mma_f16(d, a0 + (uint64_t)(kb * 1024 + k * 2), dB5 + (uint64_t)(kb * 128 + k * 2),
-                            id16, (kb | k) != 0);
+                for (int j = 0; j < 16; ++j)
+                  mma_ts_f16_w(d, a + (uint32_t)(8 * j), dB5 + (uint64_t)((j >> 2) * 128 + (j & 3) * 2),
+                             id16, j != 0);
               }
-              mma_commit(&B.mma_done[T]);
+              mma_commit_w(&B.dfull);
             }
       // all issued MMAs complete before tensor memory is released
-      mma_commit(&B.drain);
+      mma_commit_w(&B.drain);
       int never = 0;
       mbar_wait(&B.drain, 0, &never, 1000000000ull);
     }
   } else {
     // ---------------- epilogue ----------------
-    // SPLIT_TILES: warps 2 .. 2+GROUP-1 serve tile X and the rest tile Y, so
-    // one group converts its accumulator while the other waits for its MMA;
-    // otherwise every epilogue warp serves both tiles in turn.
+    // Group g (8 warps) converts accumulator columns 128 g .. 128 g + 127 of
+    // every layer of both tiles and owns the ODE state of tile g; within a
+    // group, warp w serves TMEM lane quadrant w % 4 (rows 32 q ..) and
+    // columns 64 p .. 64 p + 63 of the group's 128.
     const int ew = warp - 2;
-    const int t0 = SPLIT_TILES ? ew / GROUP_WARPS : 0;  // first tile of this warp
-    const int q = warp & 3;                             // TMEM lane quadrant of the warp
-    const int hf = (ew % GROUP_WARPS) >> 2;             // column part within the group
+    const int g = ew / GROUP_WARPS;
+    const int p = (ew >> 2) & 1;
+    const int q = warp & 3;
     const int r = 32 * q + lane;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    float cn[TPW][kCond], x[TPW][4], xm[TPW][4], ka[TPW][4];
-    uint32_t dph[TPW];
-#pragma unroll
-    for (int tt = 0; tt < TPW; ++tt) dph[tt] = 0;
+    const bool owner = p == 0;  // holds the ODE state of tile g's rows
+    float x[4], xm[4], ka[4];
+    uint32_t dph = 0;
     bool ok = true;
     for (int64_t ip = 0; ip < n_iter && ok; ++ip) {
       const int64_t pr = blockIdx.x + ip * gridDim.x;
-#pragma unroll
-      for (int tt = 0; tt < TPW; ++tt) {
-        const int T = t0 + tt;
-        const int64_t g = (2 * pr + T) * TM + r;
-        const bool valid = g < P.n;
-        if (hf == 0) {
+      {
+        const int T = g;
+        const int64_t gi = (2 * pr + T) * TM + r;
+        const bool valid = gi < P.n;
+        if (owner) {
+          float cn[kCond];
 #pragma unroll
           for (int k = 0; k < kCond; ++k)
-            cn[tt][k] = valid ? (P.cond[k * P.n + g] - P.st.cond_mean[k]) * P.st.cond_inv_std[k] : 0.0f;
+            cn[k] = valid ? (P.cond[k * P.n + gi] - P.st.cond_mean[k]) * P.st.cond_inv_std[k] : 0.0f;
           if (!valid) {
 #pragma unroll
-            for (int d = 0; d < 4; ++d) x[tt][d] = 0.0f;
+            for (int d = 0; d < 4; ++d) x[d] = 0.0f;
           } else if (P.noise) {
 #pragma unroll
-            for (int d = 0; d < 4; ++d) x[tt][d] = P.noise[d * P.n + g];
+            for (int d = 0; d < 4; ++d) x[d] = P.noise[d * P.n + gi];
           } else {
-            const float4 z = box_muller4(philox_draw(P.seed, P.id0 + (uint64_t)g, 0u, kTagNoise));
-            x[tt][0] = z.x;
-            x[tt][1] = z.y;
-            x[tt][2] = z.z;
-            x[tt][3] = z.w;
+            const float4 z = box_muller4(philox_draw(P.seed, P.id0 + (uint64_t)gi, 0u, kTagNoise));
+            x[0] = z.x;
+            x[1] = z.y;
+            x[2] = z.z;
+            x[3] = z.w;
           }
-          write_a1(sbase + (T ? S_A1 : S_A0), r, cn[tt], x[tt]);
+          write_a1_cond(sbase + S_A1 + (uint32_t)T * 4096u, r, cn);
+          write_a1_x(sbase + S_A1 + (uint32_t)T * 4096u, r, x);
           fence_proxy_async_smem();
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&B.a_ready[T]);
+        if (lane == 0) mbar_arrive(&B.ar[T][g]);
       }
       for (int e = 0; e < P.n_eval && ok; ++e) {
         for (int L = 0; L < 4 && ok; ++L)
 #pragma unroll
-          for (int tt = 0; tt < TPW; ++tt) {
-            const int T = t0 + tt;
-            if (!mbar_wait(&B.mma_done[T], dph[tt] & 1u, abort)) {
+          for (int T = 0; T < 2; ++T) {
+            const float *bias = L == 0 ? P.bias1 + (size_t)e * 256 : P.bias + L * 256;
+            const uint32_t a_row = tmem + lane_off + COL_A + 128u * (uint32_t)T;
+            const uint32_t d_col = tmem + lane_off + COL_D + (uint32_t)(NH * g + 64 * p);
+            const int col0 = NH * g + 64 * p;  // of the layer's 256 outputs
+            if (!mbar_wait(&B.dfull, dph & 1u, abort)) {
               fail(B, P.err, 5);
               ok = false;
               break;
             }
-            ++dph[tt];
+            ++dph;
             tc_fence_after();
-            const float *bias = L == 0 ? P.bias1 + (size_t)e * 256 : P.bias + L * 256;
-            const uint32_t a_base = sbase + (T ? S_A1 : S_A0);
-            const uint32_t tcol = tmem + lane_off + (uint32_t)T * 256u + (uint32_t)(hf * EPI_COLS);
-            const int col0 = hf * EPI_COLS;
-            if constexpr (FP8) {
-              // layer 1 (BF16 MMA) and layers 2-3 feed E4M3 operands; layer 4
-              // feeds the BF16 operand of layer 5
-              if (L == 0)
-                epi_layer<false, true, EPI_CW8>(tcol, bias, nullptr, col0, a_base, r);
-              else if (L < 3)
-                epi_layer<true, true, EPI_CW8>(tcol, bias, P.scale + (L - 1) * 256, col0, a_base, r);
-              else
-                epi_layer<true, false, EPI_CW8>(tcol, bias, P.scale + 2 * 256, col0, a_base, r);
-            } else {
-              epi_layer<false, false, EPI_CW>(tcol, bias, nullptr, col0, a_base, r);
-            }
-            fence_proxy_async_smem();
+            // the whole 64-column slice comes into registers first, so the
+            // accumulator is released after one load latency; the MMA that
+            // read A_T has completed, so the activations overwrite it at once
+            uint32_t va[32], vb[32];
+            tmem_ld32_raw(d_col, va);
+            tmem_ld32_raw(d_col + 32u, vb);
+            tmem_wait_ld_regs(va);
+            tmem_wait_ld_regs(vb);
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&B.a_ready[T]);
+            if (lane == 0) mbar_arrive(&B.dfree);  // the MMA may overwrite the accumulator now
+            epi_piece<FP8>(L, va, bias, P.scale, col0, a_row);
+            epi_piece<FP8>(L, va + 16, bias, P.scale, col0 + 16, a_row);
+            epi_piece<FP8>(L, vb, bias, P.scale, col0 + 32, a_row);
+            epi_piece<FP8>(L, vb + 16, bias, P.scale, col0 + 48, a_row);
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&B.ar[T][g]);
+            if (!ok) break;
           }
         if (!ok) break;
         const bool last = e == P.n_eval - 1;
 #pragma unroll
-        for (int tt = 0; tt < TPW; ++tt) {
-          const int T = t0 + tt;
-          if (!mbar_wait(&B.mma_done[T], dph[tt] & 1u, abort)) {
+        for (int T = 0; T < 2; ++T) {
+          // the velocity of tile T: columns 0-3, read by the group owning T
+          if (!mbar_wait(&B.dfull, dph & 1u, abort)) {
             fail(B, P.err, 6);
             ok = false;
             break;
           }
-          ++dph[tt];
+          ++dph;
           tc_fence_after();
-          if (hf == 0) {
-            float v[4];
-            tmem_ld4(tmem + lane_off + (uint32_t)T * 256u, v);
+          const bool mine = owner && g == T;
+          float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          if (mine) {
+            tmem_ld4(tmem + lane_off + COL_D, v);
             tmem_wait_ld_regs4(v);
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&B.dfree);
+          if (g != T) continue;
+          if (mine) {
 #pragma unroll
             for (int d = 0; d < 4; ++d) v[d] += __ldg(P.bias + 4 * 256 + d);
-            float *xin = x[tt];
+            float *xin = x;
             if (INTEG == GMC_MIDPOINT && (e & 1) == 0) {
 #pragma unroll
-              for (int d = 0; d < 4; ++d) xm[tt][d] = fmaf(0.5f * h, v[d], x[tt][d]);
-              xin = xm[tt];
+              for (int d = 0; d < 4; ++d) xm[d] = fmaf(0.5f * h, v[d], x[d]);
+              xin = xm;
             } else if (INTEG == GMC_RK4) {
               // evaluation e % 4 = i gives k_{i+1}; ka = k1 + 2 k2 + 2 k3 + k4
               const int i = e & 3;
               if (i == 3) {
 #pragma unroll
-                for (int d = 0; d < 4; ++d) x[tt][d] = fmaf(h * (1.0f / 6.0f), ka[tt][d] + v[d], x[tt][d]);
+                for (int d = 0; d < 4; ++d) x[d] = fmaf(h * (1.0f / 6.0f), ka[d] + v[d], x[d]);
               } else {
                 const float wgt = i == 0 ? 1.0f : 2.0f, hs = i == 2 ? h : 0.5f * h;
 #pragma unroll
                 for (int d = 0; d < 4; ++d) {
-                  ka[tt][d] = i == 0 ? v[d] : fmaf(wgt, v[d], ka[tt][d]);
-                  xm[tt][d] = fmaf(hs, v[d], x[tt][d]);
+                  ka[d] = i == 0 ? v[d] : fmaf(wgt, v[d], ka[d]);
+                  xm[d] = fmaf(hs, v[d], x[d]);
                 }
-                xin = xm[tt];
+                xin = xm;
               }
             } else {
 #pragma unroll
-              for (int d = 0; d < 4; ++d) x[tt][d] = fmaf(h, v[d], x[tt][d]);
+              for (int d = 0; d < 4; ++d) x[d] = fmaf(h, v[d], x[d]);
             }
             if (!last) {
               float xi[4] = {xin[0], xin[1], xin[2], xin[3]};
-              write_a1(sbase + (T ? S_A1 : S_A0), r, cn[tt], xi);
+              write_a1_x(sbase + S_A1 + (uint32_t)T * 4096u, r, xi);
               fence_proxy_async_smem();
             }
           }
-          tc_fence_before();
           __syncwarp();
-          if (!last && lane == 0) mbar_arrive(&B.a_ready[T]);
-          if (last && hf == 0) {
-            const int64_t g = (2 * pr + T) * TM + r;
-            if (g < P.n) {
+          if (!last && lane == 0) mbar_arrive(&B.ar[T][g]);
+          if (last && owner) {
+            const int64_t gi = (2 * pr + T) * TM + r;
+            if (gi < P.n) {
               if (P.y_raw) {
 #pragma unroll
-                for (int d = 0; d < 4; ++d) P.y_raw[d * P.n + g] = x[tt][d];
+                for (int d = 0; d < 4; ++d) P.y_raw[d * P.n + gi] = x[d];
               }
               if (P.exitp) {
                 bool inward;
-                const float4 o = decode_exit(x[tt][0], x[tt][1], x[tt][2], x[tt][3], P.st, &inward);
-                P.exitp[g] = o.x;
-                P.exitp[P.n + g] = o.y;
-                P.exitp[2 * P.n + g] = o.z;
-                P.exitp[3 * P.n + g] = o.w;
+                const float4 o = decode_exit(x[0], x[1], x[2], x[3], P.st, &inward);
+                P.exitp[gi] = o.x;
+                P.exitp[P.n + gi] = o.y;
+                P.exitp[2 * P.n + gi] = o.z;
+                P.exitp[3 * P.n + gi] = o.w;
               }
             }
           }
@@ -732,12 +725,10 @@ size_t sw32_off(int row, int k) {
   return (size_t)((row >> 3) * 256 + (row & 7) * 32 + ((c ^ ((row >> 2) & 1)) << 4) + e * 2);
 }
 
-// byte b of row `row` in a weight chunk (ROW_BYTES-byte rows: 64-byte swizzle
-// for 64, 128-byte swizzle for 128)
+// byte b (0..127) of row `row` (0..255) in a weight chunk: 128-byte rows,
+// 128-byte swizzle
 size_t chunk_byte_off(int row, int b) {
   const int c = b >> 4, e = b & 15;
-  if (ROW_BYTES == 64)
-    return (size_t)((row >> 3) * 512 + (row & 7) * 64 + ((c ^ ((row >> 1) & 3)) << 4) + e);
   return (size_t)((row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4) + e);
 }
 
@@ -771,14 +762,14 @@ void pack_b1_b5_bias(const float (*W)[256 * 256], const float (*b)[256], unsigne
     const uint16_t u = bf16_bits(v);
     std::memcpy(P + off, &u, 2);
   };
-  // layer 1: [cond (5), x (4) for x_hi, x (4) again for x_lo, 0 0 0]
+  // layer 1: [x (4) for x_hi, x (4) again for x_lo, cond (5), 0 0 0]
   for (int nrow = 0; nrow < 256; ++nrow) {
     const float *w = &W[0][nrow * 25];
-    for (int k = 0; k < 5; ++k) put(off_b1 + sw32_off(nrow, k), 0.5f * w[k]);
     for (int k = 0; k < 4; ++k) {
-      put(off_b1 + sw32_off(nrow, 5 + k), 0.5f * w[5 + k]);
-      put(off_b1 + sw32_off(nrow, 9 + k), 0.5f * w[5 + k]);
+      put(off_b1 + sw32_off(nrow, k), 0.5f * w[5 + k]);
+      put(off_b1 + sw32_off(nrow, 4 + k), 0.5f * w[5 + k]);
     }
+    for (int k = 0; k < 5; ++k) put(off_b1 + sw32_off(nrow, 8 + k), 0.5f * w[k]);
   }
   // output layer: 16 rows (4 real) x 256 K in four 128-byte-swizzled K-blocks
   for (int d = 0; d < 4; ++d)
@@ -799,17 +790,32 @@ void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *pack
   using PK = Packed<false>;
   unsigned char *P = (unsigned char *)packed_host;
   std::memset(P, 0, PK::BYTES);
-  // hidden layers W2..W4: chunk ch holds all 256 output rows and K CHUNK_K ch ..
+  // hidden layers W2..W4: chunk ch holds all 256 output rows and inputs
+  // 64 ch .. 64 ch + 63
   for (int L = 0; L < 3; ++L)
     for (int ch = 0; ch < PK::NCH; ++ch) {
       const size_t base = PK::OFF_HID + (size_t)(L * PK::NCH + ch) * CHUNK;
       for (int i = 0; i < 256; ++i)
-        for (int j = 0; j < CHUNK_K; ++j) {
-          const uint16_t u = bf16_bits(0.5f * W[L + 1][i * 256 + ch * CHUNK_K + j]);
+        for (int j = 0; j < 64; ++j) {
+          const uint16_t u = bf16_bits(0.5f * W[L + 1][i * 256 + 64 * ch + j]);
           std::memcpy(P + base + chunk_byte_off(i, 2 * j), &u, 2);
         }
     }
   pack_b1_b5_bias(W, b, P, PK::OFF_B1, PK::OFF_B5, bias_host);
+  // bias blocks of layers 2-4: b/2 = hi + lo, both BF16, against the two
+  // constant-1 columns of the layer-1 operand
+  for (int L = 0; L < 3; ++L)
+    for (int c = 0; c < 256; ++c) {
+      const float v = 0.5f * b[L + 1][c];
+      const uint16_t hi = bf16_bits(v);
+      float hif;
+      const uint32_t hb = (uint32_t)hi << 16;
+      std::memcpy(&hif, &hb, 4);
+      const uint16_t lo = bf16_bits(v - hif);
+      const size_t base = PK::OFF_BIAS + (size_t)L * 8192;
+      std::memcpy(P + base + sw32_off(c, 13), &hi, 2);
+      std::memcpy(P + base + sw32_off(c, 14), &lo, 2);
+    }
 }
 
 void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
@@ -818,7 +824,7 @@ void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *
   unsigned char *P = (unsigned char *)packed_host;
   std::memset(P, 0, PK::BYTES);
   // hidden layers W2..W4: row c as E4M3 codes of W[c][:] / s_c, s_c = amax / 448;
-  // chunk ch holds all 256 output rows and K ROW_BYTES ch ..
+  // chunk ch holds all 256 output rows and inputs 128 ch ..
   for (int L = 0; L < 3; ++L)
     for (int i = 0; i < 256; ++i) {
       const float *w = &W[L + 1][i * 256];
@@ -827,7 +833,7 @@ void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *
       const double sc = amax > 0.0 ? amax / 448.0 : 1.0;
       scale_host[L * 256 + i] = (float)(0.5 * sc);  // layers 2-4 carry a factor 1/2
       for (int k = 0; k < 256; ++k) {
-        const int ch = k / ROW_BYTES, j = k % ROW_BYTES;
+        const int ch = k >> 7, j = k & 127;
         P[PK::OFF_HID + (size_t)(L * PK::NCH + ch) * CHUNK + chunk_byte_off(i, j)] =
             e4m3_bits((double)w[k] / sc);
       }
