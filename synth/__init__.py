@@ -74,6 +74,20 @@ def kaiming_weights(seed=1):
             "y_mean": np.zeros(4, np.float32), "y_std": np.ones(4, np.float32)}
 
 
+def biased_weights(seed=7, bias_std=0.3):
+    """Kaiming-normal weights with N(0, bias_std^2) biases and a non-identity
+    standardization (condition and output means and standard deviations of
+    the size a trained network's data statistics have)."""
+    net = kaiming_weights(seed)
+    g = generator(seed + 1000)
+    net["b"] = [(g.standard_normal(len(b)) * bias_std).astype(np.float32) for b in net["b"]]
+    net["cond_mean"] = g.uniform(-1.0, 1.0, 5).astype(np.float32)
+    net["cond_std"] = g.uniform(0.5, 2.0, 5).astype(np.float32)
+    net["y_mean"] = g.uniform(-0.5, 0.5, 4).astype(np.float32)
+    net["y_std"] = g.uniform(0.3, 1.5, 4).astype(np.float32)
+    return net
+
+
 def write_weights(path, net):
     """Write a dict like `kaiming_weights()` returns as a GMCW version-1 file."""
     with open(path, "wb") as f:
