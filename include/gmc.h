@@ -27,10 +27,12 @@
  *  - Array arguments are structure-of-arrays, row k of an [m][n] array
  *    starting at element k*n. Unless a parameter says "host", array pointers
  *    may be device pointers (the call runs asynchronously on the context's
- *    stream) or host pointers (the call copies inputs in and results out
- *    through context-owned device buffers and returns when results are on
- *    the host). The caller owns every buffer it passes; the context owns its
- *    weights, particle banks and scratch.
+ *    stream) or host pointers (the call returns when results are on the
+ *    host): page-locked host memory (cudaHostAlloc, cudaHostRegister) is
+ *    read and written in place by the kernels over the CPU-GPU link; other
+ *    host memory is copied in and out through context-owned device buffers.
+ *    The caller owns every buffer it passes; the context owns its weights,
+ *    particle banks and scratch.
  *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with counter
  *    (id_lo, id_hi, event, tag) and key (seed_lo, seed_hi); tags: 1 walk
  *    flights, 2 flow-ODE noise, 3 roulette, 4 births, 5 training data,

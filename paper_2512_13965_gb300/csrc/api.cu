@@ -63,19 +63,37 @@ cudaError_t ensure(Buffer &b, size_t bytes) {
 
 namespace {
 
-// One array argument of a batched call: device pointers pass through, host
-// pointers are staged through a context buffer.
+// One array argument of a batched call: device pointers pass through;
+// page-locked host memory (cudaHostAlloc / cudaHostRegister) is read and
+// written in place by the kernels over the CPU-GPU link (mapped); other host
+// memory is staged through a context buffer (host).
 struct Arg {
   const void *user = nullptr;
   void *dev = nullptr;
   size_t bytes = 0;
   bool host = false;
+  bool mapped = false;
 };
+
+// Device address of page-locked host memory, or null for anything else.
+void *mapped_host_pointer(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
 
 cudaError_t stage_in(gmc_ctx *ctx, int slot, Arg &a) {
   if (!a.user) return cudaSuccess;
   if (is_device_pointer(a.user)) {
     a.dev = const_cast<void *>(a.user);
+    return cudaSuccess;
+  }
+  if (void *m = mapped_host_pointer(a.user)) {
+    a.dev = m;
+    a.mapped = true;
     return cudaSuccess;
   }
   a.host = true;
@@ -89,6 +107,11 @@ cudaError_t stage_out_prepare(gmc_ctx *ctx, int slot, Arg &a) {
   if (!a.user) return cudaSuccess;
   if (is_device_pointer(a.user)) {
     a.dev = const_cast<void *>(a.user);
+    return cudaSuccess;
+  }
+  if (void *m = mapped_host_pointer(a.user)) {
+    a.dev = m;
+    a.mapped = true;
     return cudaSuccess;
   }
   a.host = true;
@@ -261,7 +284,7 @@ gmc_status gmc_philox(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uint
   GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 0, o));
   GMC_CUDA_TRY(ctx, launch_philox(ctx->stream, n, seed, id0, event, tag, (uint32_t *)o.dev));
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o));
-  if (o.host) GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (o.host || o.mapped) GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return GMC_OK;
 }
 
@@ -276,7 +299,7 @@ gmc_status gmc_normals(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uin
   GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 0, o));
   GMC_CUDA_TRY(ctx, launch_normals(ctx->stream, n, seed, id0, event, tag, (float *)o.dev));
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o));
-  if (o.host) GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (o.host || o.mapped) GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return GMC_OK;
 }
 
@@ -476,7 +499,8 @@ gmc_status transmit_net(gmc_ctx *ctx, const NetDev &N, int64_t n, const float *c
   }
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, a_y));
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, a_exit));
-  if (a_cond.host || a_noise.host || a_y.host || a_exit.host) {
+  if (a_cond.host || a_noise.host || a_y.host || a_exit.host || a_cond.mapped || a_noise.mapped ||
+      a_y.mapped || a_exit.mapped) {
     GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return check_device_error(ctx);
   }
@@ -536,8 +560,9 @@ gmc_status analog_transmit(gmc_ctx *ctx, int64_t n, const float *xi, const float
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_status));
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_exit));
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_ncoll));
-  bool host = o_status.host || o_exit.host || o_ncoll.host;
-  for (auto &a : in) host = host || a.host;
+  bool host = o_status.host || o_exit.host || o_ncoll.host || o_status.mapped || o_exit.mapped ||
+              o_ncoll.mapped;
+  for (auto &a : in) host = host || a.host || a.mapped;
   if (host) GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return GMC_OK;
 }
