@@ -175,7 +175,8 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--workload", default="sampler", choices=["sampler", "solve", "serve", "sweep", "heldout"])
+    ap.add_argument("--workload", default="sampler",
+                    choices=["sampler", "solve", "hohlraum", "serve", "sweep", "heldout"])
     ap.add_argument("--weights", default=None, help="GMCW file (default: Kaiming seed 1)")
     ap.add_argument("--internal-weights", default=None,
                     help="GMCW file of the internal-source model (solve/serve: births sampled by it)")
@@ -188,7 +189,7 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "solve":
+    if args.workload in ("solve", "hohlraum"):
         return run_solve(args)
     if args.workload == "serve":
         return run_serve(args)
@@ -379,15 +380,30 @@ def _context(args):
 
 
 def run_solve(args):
-    """Full transport solve: 128x128 cells, tau logU[0.1,500], c in {0.5, 0.999}
-    per 16x16 block (seed 2), unit source on the central 8x8 cells, vacuum
-    boundaries; GMC (BF16 and FP8; Euler, midpoint and RK4) against the GPU
-    random walk."""
+    """Full transport solve, GMC (BF16 and FP8; Euler, midpoint and RK4; hybrid)
+    against the GPU random walk. --workload solve: 128x128 cells, tau
+    logU[0.1,500], c in {0.5, 0.999} per 16x16 block (seed 2), unit source on
+    the central 8x8 cells, vacuum boundaries. --workload hohlraum: the
+    hohlraum-like boundary-source problem (64x64 cells, five materials, the
+    entrance hole driven from the left boundary)."""
     import numpy as np
     import synth
     g, ctx = _context(args)
-    tau, c, src = synth.grid_problem(n=128, seed=2)
-    tau, c, src = (np.ascontiguousarray(a.ravel()) for a in (tau, c, src))
+    hohl = args.workload == "hohlraum"
+    if hohl:
+        N = 64
+        tau, c, wall = synth.hohlraum_problem(N)
+        tau, c = (np.ascontiguousarray(a.ravel()) for a in (tau, c))
+        src = np.ascontiguousarray(wall)
+        desc = ("hohlraum-like boundary source 64x64: gas (tau 0.2, c 1), wall (200, 0.6), window "
+                "(0.5, 1), ablator (20, 0.9), fuel (2, 0.99); entrance rows 16-47 driven from x = 0")
+    else:
+        N = 128
+        tau, c, src = synth.grid_problem(n=N, seed=2)
+        tau, c, src = (np.ascontiguousarray(a.ravel()) for a in (tau, c, src))
+        desc = ("transport solve 128x128, tau logU[0.1,500], c {0.5,0.999} 16x16 blocks, central "
+                "8x8 source")
+    solve_fn = g.transport_solve_wall if hohl else g.transport_solve
     n = int(args.histories)
     out = {}
 
@@ -398,9 +414,8 @@ def run_solve(args):
         cfg.precision = g.GMC_BF16 if prec is None else prec
         cfg.gmc_min_tau = min_tau
         g.gmc_set_config(ctx, cfg)
-        f = np.zeros(128 * 128)
-        st = g.transport_solve(ctx, 128, 128, tau, c, src, n if n_hist is None else n_hist, method,
-                               seed, f)
+        f = np.zeros(N * N)
+        st = solve_fn(ctx, N, N, tau, c, src, n if n_hist is None else n_hist, method, seed, f)
         return f, st
 
     # the analog reference: two independent runs of n/2 histories, averaged
@@ -447,9 +462,10 @@ def run_solve(args):
                     "transmissions_per_s": st.transmissions / st.seconds, "waves": st.waves,
                     "collisions": st.collisions,
                     "flux_rel_err_vs_analog": None if f_mc is None else rel(f, f_mc)}
-    line = {"metric": METRIC, "workload": "transport solve 128x128, tau logU[0.1,500], c {0.5,0.999} "
-            "16x16 blocks, central 8x8 source, %d histories" % n, "weights": args.weights or "kaiming seed 1 (untrained)",
-            "births": ("internal model " + args.internal_weights) if args.internal_weights else "random walk",
+    line = {"metric": METRIC, "workload": "%s, %d histories" % (desc, n),
+            "weights": args.weights or "kaiming seed 1 (untrained)",
+            "births": "on the left boundary (no birth walk)" if hohl else (
+                ("internal model " + args.internal_weights) if args.internal_weights else "random walk"),
             "results": out, "unit": "cell transmissions/s"}
     print(json.dumps(line))
     ctx.close()

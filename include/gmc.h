@@ -274,6 +274,22 @@ gmc_status transport_solve(gmc_ctx *ctx, int nx, int ny, const float *tau, const
                            const float *source, int64_t n_histories, int method, uint64_t seed,
                            double *flux, gmc_solve_stats *stats);
 
+/*
+ * As transport_solve with a surface source on the left boundary (x = 0)
+ * instead of a volumetric one: history h (Philox draw (h, 0, tag 4) =
+ * (u0, u1, u2, u3)) enters boundary row j, the first whose cumulative
+ * strength reaches u0 * sum(wall), through the west face of cell (0, j) at
+ * height j + u1, with sin(theta) = 2 u2 - 1 against the inward normal (the
+ * cosine law of an isotropic radiance seen through the boundary), weight 1;
+ * its first cell crossing is a transmission of the chosen method. This is the
+ * boundary-source problem of the paper's experiments (a driven wall).
+ *  wall  host [ny] float, relative strengths (>= 0, not all zero).
+ * Other arguments, the result and blocking as for transport_solve.
+ */
+gmc_status transport_solve_wall(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                                const float *wall, int64_t n_histories, int method, uint64_t seed,
+                                double *flux, gmc_solve_stats *stats);
+
 /* ---- serving: continuous batching of transport solves ---------------------- */
 
 /* One transport solve (arguments of transport_solve; arrays are host memory

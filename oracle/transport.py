@@ -208,12 +208,31 @@ def rot_dir(ux, uy, k):
     return float(rx[0]), float(ry[0])
 
 
+def wall_births(wall, n_hist, seed):
+    """Histories of an isotropic surface source on the left boundary (x = 0),
+    from the birth draw (id, 0, TAG_BIRTH) = (u0, u1, u2, u3): boundary cell
+    row j with probability wall[j] / sum(wall) (first row whose cumulative
+    strength reaches u0 * total), entry point y = j + u1 on the cell's left
+    face, and the cosine law for the direction (the flux of an isotropic
+    radiance through a surface): sin(theta) = 2 u2 - 1, cos(theta) =
+    sqrt(1 - sin^2) > 0. Returns (j, xi, gx, gy) per history."""
+    cdf = np.cumsum(np.maximum(np.asarray(wall, dtype=np.float64), 0.0))
+    ids = np.arange(n_hist, dtype=np.uint64)
+    ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
+    j = np.searchsorted(cdf, ub[0] * cdf[-1], side="left")
+    sn = 2.0 * ub[2] - 1.0
+    return j, ub[1], np.sqrt(np.maximum(1.0 - sn * sn, 0.0)), sn
+
+
 def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max_waves=100000,
-              internal=None):
+              internal=None, wall=None):
     """Event-based GMC solve; tau, c, src are [ny, nx]. Returns (flux, stats).
 
     internal: sampler of births (mlp_internal_sampler / walk_internal_sampler),
     or None to walk every birth with walk_one.
+    wall: [ny] strengths of a surface source on the left boundary instead of
+    the volumetric source src (see wall_births); each history enters its
+    boundary cell through the west face with weight 1 and next event 0.
     """
     tau = np.asarray(tau, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)
@@ -221,17 +240,26 @@ def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max
     tf, cf = tau.ravel(), c.ravel()
     flux = np.zeros(ny * nx, dtype=np.float64)
     st = np.zeros(6, dtype=np.float64)
-    srcf = np.maximum(np.asarray(src, dtype=np.float64).ravel(), 0.0)
-    cdf = np.cumsum(srcf)
-    total = cdf[-1]
-    ids = np.arange(n_hist, dtype=np.uint64)
-    ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
-    cells = np.searchsorted(cdf, ub[0] * total, side="left")
+    live = {k: [] for k in ("id", "i", "j", "F", "xi", "gx", "gy", "w", "ev")}
+    if wall is not None:
+        j, xi, gx, gy = wall_births(wall, n_hist, seed)
+        for h in range(n_hist):
+            for k, v in (("id", h), ("i", 0), ("j", int(j[h])), ("F", 3), ("xi", xi[h]),
+                         ("gx", gx[h]), ("gy", gy[h]), ("w", 1.0), ("ev", 0)):
+                live[k].append(v)
+        n_src = 0
+    else:
+        n_src = n_hist
+        srcf = np.maximum(np.asarray(src, dtype=np.float64).ravel(), 0.0)
+        cdf = np.cumsum(srcf)
+        total = cdf[-1]
+        ids = np.arange(n_hist, dtype=np.uint64)
+        ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
+        cells = np.searchsorted(cdf, ub[0] * total, side="left")
 
     # Births: walk from the birth point to the first face crossing (cell frame),
     # or sample that exit with the internal model.
-    live = {k: [] for k in ("id", "i", "j", "F", "xi", "gx", "gy", "w", "ev")}
-    if internal is not None:
+    if internal is not None and n_src > 0:
         face, q, ux, uy, s, ev = internal(ub[1], ub[2], tf[cells], cf[cells], ids, ub[3])
         for h in range(n_hist):
             k = int(cells[h])
@@ -246,7 +274,7 @@ def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max
                 continue
             _advance_one(live, h, k % nx, k // nx, int(face[h]), q[h], ux[h], uy[h], w[0],
                          int(ev[h]), nx, ny, st)
-    for h in range(n_hist if internal is None else 0):
+    for h in range(n_src if internal is None else 0):
         k = int(cells[h])
         i, j = k % nx, k // nx
         t, cc = tf[k], cf[k]

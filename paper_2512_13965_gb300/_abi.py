@@ -88,6 +88,8 @@ def _load():
         "analog_transmit": [P, i64, P, P, P, P, P, i32, u64, u64, u32, P, P, P],
         "transport_solve": [P, i32, i32, P, P, P, i64, i32, u64, P,
                             ctypes.POINTER(gmc_solve_stats)],
+        "transport_solve_wall": [P, i32, i32, P, P, P, i64, i32, u64, P,
+                                 ctypes.POINTER(gmc_solve_stats)],
         "gmc_serve_start": [P, ctypes.POINTER(gmc_serve_config)],
         "gmc_submit": [P, ctypes.POINTER(gmc_solve_req), ctypes.POINTER(ctypes.c_uint64)],
         "gmc_poll": [P, u64, P, ctypes.POINTER(gmc_solve_stats)],
@@ -254,6 +256,13 @@ def transport_solve(ctx, nx, ny, tau, c, source, n_histories, method, seed, flux
     st = stats if stats is not None else gmc_solve_stats()
     ctx.check(lib.transport_solve(ctx.handle, nx, ny, _ptr(tau), _ptr(c), _ptr(source),
                                   n_histories, method, seed, _ptr(flux), ctypes.byref(st)))
+    return st
+
+
+def transport_solve_wall(ctx, nx, ny, tau, c, wall, n_histories, method, seed, flux, stats=None):
+    st = stats if stats is not None else gmc_solve_stats()
+    ctx.check(lib.transport_solve_wall(ctx.handle, nx, ny, _ptr(tau), _ptr(c), _ptr(wall),
+                                       n_histories, method, seed, _ptr(flux), ctypes.byref(st)))
     return st
 
 

@@ -319,6 +319,35 @@ __global__ void birth_kernel(int slot, int64_t first, int64_t count, const doubl
   append_inside(keep, slot, h, cell, ws, 1.0f, out, in_count, slot_live);
 }
 
+// Births of a surface source on the left boundary (x = 0): history h of the
+// request in `slot` draws (u0, u1, u2, -) at (h, 0, tag 4), enters boundary
+// row j (the first whose cumulative wall strength reaches u0 total) through
+// the west face of cell (0, j) at canonical position xi = u1, with the cosine
+// law for its direction, sin theta = 2 u2 - 1 (an isotropic radiance seen
+// through the boundary), and joins the face bank at base + k with weight 1.
+__global__ void birth_wall_kernel(int slot, int64_t first, int64_t count,
+                                  const double *__restrict__ cdf, double total,
+                                  const Slot *__restrict__ slots, Bank out, int64_t base) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const Slot S = slots[slot];
+  const uint64_t h = (uint64_t)(first + k);
+  const uint4 r = philox_draw(S.seed, h, 0u, kTagBirth);
+  const double u0 = ((double)r.x + 1.0) * (1.0 / 4294967296.0);
+  const int j = (int)cdf_search(cdf, (int64_t)S.ny, u0 * total);
+  const float sn = 2.0f * u01(r.z) - 1.0f;
+  const int64_t o = base + k;
+  out.hist[o] = h;
+  out.slot[o] = slot;
+  out.cell[o] = j * S.nx;
+  out.face[o] = 3;
+  out.xi[o] = u01(r.y);
+  out.gx[o] = sqrtf(fmaxf(1.0f - sn * sn, 0.0f));
+  out.gy[o] = sn;
+  out.w[o] = 1.0f;
+  out.ev[o] = 0u;
+}
+
 // Ends or parks one lane's walk: an exit (or absorption) becomes the Exit of
 // stages 3-4, a walk cut by the flight cap goes back to the inside bank.
 __device__ __forceinline__ void settle(const WalkResult &wr, const WalkState &ws, int slot,
@@ -593,6 +622,7 @@ struct Request {
   int64_t n_hist = 0;
   uint64_t seed = 0;
   int method = GMC_METHOD_ANALOG;
+  bool wall = false;  // source on the left boundary (cdf over the ny rows)
   // engine state
   int slot = -1;
   int64_t next_hist = 0;
@@ -613,9 +643,11 @@ struct Request {
 size_t request_footprint(int64_t ncell) { return 2 * align256(ncell * 4) + 2 * align256(ncell * 8); }
 
 // Validates a solve description and copies it into a Request.
+// wall: `source` holds ny strengths of a surface source on the left boundary
+// instead of ny*nx volumetric strengths.
 gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
                         const float *source, int64_t n_histories, int method, uint64_t seed,
-                        Request &R) {
+                        Request &R, bool wall = false) {
   if (nx < 1 || ny < 1 || (int64_t)nx * ny > (1 << 26))
     return set_error(ctx, GMC_EINVAL, "solve: grid must be 1..2^26 cells");
   if (!tau || !c || !source) return set_error(ctx, GMC_EINVAL, "solve: null array");
@@ -637,11 +669,19 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
       return set_error(ctx, GMC_EINVAL,
                        "solve: cell %lld outside the sampler's range (tau in [0.05, 2000], c >= 0.4)",
                        (long long)k);
+    if (wall) continue;
     if (!(source[k] >= 0.0f) || !std::isfinite(source[k]))
       return set_error(ctx, GMC_EINVAL, "solve: source must be finite and >= 0");
     acc += source[k] > 0.0f ? (double)source[k] : 0.0;
     R.cdf[k] = acc;
   }
+  for (int j = 0; wall && j < ny; ++j) {
+    if (!(source[j] >= 0.0f) || !std::isfinite(source[j]))
+      return set_error(ctx, GMC_EINVAL, "solve: wall source must be finite and >= 0");
+    acc += source[j] > 0.0f ? (double)source[j] : 0.0;
+    R.cdf[j] = acc;
+  }
+  R.wall = wall;
   if (n_histories > 0 && !(acc > 0.0)) return set_error(ctx, GMC_EINVAL, "solve: zero source");
   if (method == GMC_METHOD_GMC && !ctx->net.loaded)
     return set_error(ctx, GMC_ENOWEIGHTS, "solve: GMC needs gmc_load_weights");
@@ -810,10 +850,27 @@ class Engine {
     int *d_face = d_counts_, *d_in = d_counts_ + 1, *d_thin = d_counts_ + 2,
         *d_slot_live = d_counts_ + 3;
     // births: fair share of the free room among requests with histories left
-    int pending = 0;
+    int pending = 0, pending_wall = 0;
     for (auto *R : reqs_)
-      if (R && R->next_hist < R->n_hist) ++pending;
+      if (R && R->next_hist < R->n_hist) ++(R->wall ? pending_wall : pending);
     int64_t room = C_ - live_ - live_in_ - live_thin_;
+    if (pending_wall > 0 && room > 0) {
+      // surface-source births enter the current face bank directly
+      int left = pending + pending_wall;
+      for (auto *R : reqs_) {
+        if (!R || !R->wall || R->next_hist >= R->n_hist) continue;
+        const int64_t m = std::min<int64_t>(room / left, R->n_hist - R->next_hist);
+        --left;
+        if (m <= 0) continue;
+        birth_wall_kernel<<<nblocks(m, 256), 256, 0, s_>>>(R->slot, R->next_hist, m, R->d_cdf,
+                                                            R->total, d_slots_, bank_[cur_], live_);
+        GMC_CUDA_TRY(ctx_, cudaGetLastError());
+        live_ += m;
+        R->live += (int)m;
+        R->next_hist += m;
+        room -= m;
+      }
+    }
     if (pending > 0 && room > 0 && method_ == GMC_METHOD_GMC && ctx_->internal.loaded) {
       const gmc_status sb = births_internal(pending, room, rules, min_tau);
       if (sb != GMC_OK) return sb;
@@ -821,7 +878,7 @@ class Engine {
       GMC_CUDA_TRY(ctx_, set_counts());
       int left = pending;
       for (auto *R : reqs_) {
-        if (!R || R->next_hist >= R->n_hist) continue;
+        if (!R || R->wall || R->next_hist >= R->n_hist) continue;
         const int64_t share = room / left;
         const int64_t m = std::min<int64_t>(share, R->n_hist - R->next_hist);
         --left;
@@ -922,7 +979,7 @@ class Engine {
     int64_t M = 0;
     int left = pending;
     for (auto *R : reqs_) {
-      if (!R || R->next_hist >= R->n_hist) continue;
+      if (!R || R->wall || R->next_hist >= R->n_hist) continue;
       const int64_t share = room / left;
       const int64_t m = std::min<int64_t>(share, R->n_hist - R->next_hist);
       --left;
@@ -1118,13 +1175,14 @@ using namespace gmc;
 
 extern "C" {
 
-gmc_status transport_solve(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
-                           const float *source, int64_t n_histories, int method, uint64_t seed,
-                           double *flux, gmc_solve_stats *stats) {
+namespace {
+gmc_status solve_one(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                     const float *source, int64_t n_histories, int method, uint64_t seed,
+                     double *flux, gmc_solve_stats *stats, bool wall) {
   if (!ctx) return GMC_EINVAL;
   if (!flux) return set_error(ctx, GMC_EINVAL, "transport_solve: null flux");
   Request R;
-  gmc_status st = make_request(ctx, nx, ny, tau, c, source, n_histories, method, seed, R);
+  gmc_status st = make_request(ctx, nx, ny, tau, c, source, n_histories, method, seed, R, wall);
   if (st != GMC_OK) return st;
   cudaSetDevice(ctx->device);
   const int64_t C = ctx->cfg.bank_capacity;
@@ -1156,6 +1214,19 @@ gmc_status transport_solve(gmc_ctx *ctx, int nx, int ny, const float *tau, const
   std::memcpy(flux, R.flux.data(), R.ncell * sizeof(double));
   if (stats) *stats = R.st;
   return check_device_error(ctx);
+}
+}  // namespace
+
+gmc_status transport_solve(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                           const float *source, int64_t n_histories, int method, uint64_t seed,
+                           double *flux, gmc_solve_stats *stats) {
+  return solve_one(ctx, nx, ny, tau, c, source, n_histories, method, seed, flux, stats, false);
+}
+
+gmc_status transport_solve_wall(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                                const float *wall, int64_t n_histories, int method, uint64_t seed,
+                                double *flux, gmc_solve_stats *stats) {
+  return solve_one(ctx, nx, ny, tau, c, wall, n_histories, method, seed, flux, stats, true);
 }
 
 gmc_status gmc_serve_start(gmc_ctx *ctx, const gmc_serve_config *cfg) {

@@ -117,3 +117,35 @@ def grid_problem(n=128, seed=2, tau_range=(0.1, 500.0), c_values=(0.5, 0.999), b
     src[a:a + source, a:a + source] = 1.0
     src /= src.sum()
     return tau.astype(np.float32), c.astype(np.float32), src.astype(np.float32)
+
+
+# Material classes of the hohlraum-like boundary-source problem: (tau, c).
+HOHLRAUM_MATERIALS = {"gas": (0.2, 1.0), "wall": (200.0, 0.6), "window": (0.5, 1.0),
+                      "ablator": (20.0, 0.9), "fuel": (2.0, 0.99)}
+
+
+def hohlraum_problem(n=64):
+    """Hohlraum-like boundary-source problem on n x n unit cells with five
+    material classes (HOHLRAUM_MATERIALS): a wall frame n/16 cells thick, open
+    on the left between rows n/4 and 3n/4 (the entrance hole, filled with the
+    window material); a capsule of radius n/6 at the centre (an ablator shell
+    two cells thick around the fuel); gas elsewhere. The source drives the
+    entrance hole from the left boundary. Returns tau [n, n], c [n, n]
+    (float32, row = y index) and the left-boundary strengths wall [n]."""
+    t = max(1, n // 16)
+    lo, hi = n // 4, (3 * n) // 4
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n))  # ii: x index, jj: y index
+    mat = np.full((n, n), "gas", dtype=object)
+    frame = (jj < t) | (jj >= n - t) | (ii >= n - t) | (ii < t)
+    mat[frame] = "wall"
+    mat[(ii < t) & (jj >= lo) & (jj < hi)] = "window"
+    r = np.hypot(ii + 0.5 - n / 2.0, jj + 0.5 - n / 2.0)
+    R = n / 6.0
+    mat[r < R] = "ablator"
+    mat[r < R - 2.0] = "fuel"
+    tau = np.vectorize(lambda m: HOHLRAUM_MATERIALS[m][0])(mat).astype(np.float32)
+    c = np.vectorize(lambda m: HOHLRAUM_MATERIALS[m][1])(mat).astype(np.float32)
+    wall = np.zeros(n, dtype=np.float32)
+    wall[lo:hi] = 1.0
+    return tau, c, wall
+

@@ -212,3 +212,85 @@ def test_hybrid_solve_matches_oracle(gpu_ctx, kaiming_net):
     assert _rel_l2(fg, fo) < 0.03
     assert abs(sg["transmissions"] - so["transmissions"]) < 0.02 * so["transmissions"]
     assert sg["collisions"] > 0
+
+
+# --- surface source on the left boundary (transport_solve_wall) --------------
+
+def _solve_wall(ctx, tau, c, wall, n, method, seed):
+    import paper_2512_13965_gb300 as g
+    ny, nx = tau.shape
+    flux = np.zeros(ny * nx, dtype=np.float64)
+    st = g.transport_solve_wall(ctx, nx, ny, np.ascontiguousarray(tau, np.float32).ravel(),
+                                np.ascontiguousarray(c, np.float32).ravel(),
+                                np.ascontiguousarray(wall, np.float32), n, method, seed, flux)
+    return flux.reshape(ny, nx), st.as_dict()
+
+
+def _wall_strengths(ny, seed):
+    w = synth.generator(seed).uniform(0.0, 1.0, ny).astype(np.float32)
+    w[: ny // 4] = 0.0  # part of the wall does not emit
+    return w
+
+
+def test_wall_analog_solve_matches_oracle(gpu_ctx):
+    import paper_2512_13965_gb300 as g
+    _set(gpu_ctx, bank_capacity=1 << 14)
+    tau, c, _ = synth.grid_problem(n=8, seed=41, tau_range=(0.1, 5.0), block=4, source=2)
+    wall = _wall_strengths(8, 42)
+    n = 8000
+    fg, sg = _solve_wall(gpu_ctx, tau, c, wall, n, g.GMC_METHOD_ANALOG, 6)
+    fo, so = OT.solve_gmc(tau, c, None, n, 6, OT.walk_sampler_global(6), wall=wall)
+    assert _rel_l2(fg, fo) < 0.02
+    assert abs(sg["leaked"] - so["leak"]) < 0.01 * n
+    assert abs(sg["transmissions"] - so["transmissions"]) < 0.01 * so["transmissions"]
+    assert abs(sg["absorbed"] + sg["leaked"] - sg["roulette_net"] - n) < 1e-4 * n
+    # rows of the first column that do not emit still see flux from their neighbours,
+    # and the flux falls away from the wall on average
+    assert fg[:, 0].mean() > fg[:, -1].mean()
+
+
+def test_wall_gmc_solve_fp32_matches_oracle_loop(gpu_ctx, kaiming_net):
+    import paper_2512_13965_gb300 as g
+    _set(gpu_ctx, precision=g.GMC_FP32, steps=4, integrator=g.GMC_EULER, bank_capacity=4096)
+    tau, c, _ = synth.grid_problem(n=8, seed=43, tau_range=(0.1, 5.0), block=4, source=2)
+    wall = _wall_strengths(8, 44)
+    n = 1500
+    fg, sg = _solve_wall(gpu_ctx, tau, c, wall, n, g.GMC_METHOD_GMC, 10)
+    fo, so = OT.solve_gmc(tau, c, None, n, 10, OT.mlp_sampler(kaiming_net, 4, "euler", 10), wall=wall)
+    assert _rel_l2(fg, fo) < 0.03
+    assert abs(sg["leaked"] - so["leak"]) < 0.02 * n
+    assert abs(sg["transmissions"] - so["transmissions"]) < 0.02 * so["transmissions"]
+
+
+@pytest.mark.parametrize("tau,c", [(0.5, 0.0), (2.0, 0.0), (3.0, 1.0)])
+def test_wall_single_cell_closed_forms(gpu_ctx, tau, c):
+    # one cell lit from the left: pure absorber (c = 0) -> (1 - P_unc) / tau,
+    # pure scatterer (c = 1) -> pi / 4 (mean path pi tau / 4 of a Lambertian
+    # inflow); the spread per history comes from the oracle's walks
+    import paper_2512_13965_gb300 as g
+    from test_oracle_walk import uncollided_by_face
+    _set(gpu_ctx, bank_capacity=1 << 16)
+    n = 1 << 18
+    f, st = _solve_wall(gpu_ctx, np.full((1, 1), tau), np.full((1, 1), c), [1.0], n,
+                        g.GMC_METHOD_ANALOG, 8)
+    j, xi, gx, gy = OT.wall_births([1.0], 4000, 9)
+    r = OT.transmit(xi, gx, gy, np.full(4000, tau), np.full(4000, c), OT.MODE_IMPLICIT, 9,
+                    ids=np.arange(4000, dtype=np.uint64), events=np.zeros(4000, np.uint32))
+    per = (r["s"] / tau) if c == 1.0 else (-np.expm1(-r["s"]) / tau)
+    expect = math.pi / 4 if c == 1.0 else (1.0 - uncollided_by_face(tau).sum()) / tau
+    assert abs(f[0, 0] - expect) < 4 * per.std() / math.sqrt(n) + 1e-6
+    if c == 1.0:
+        assert st["absorbed"] == 0.0 and abs(st["leaked"] - n) < 1e-6 * n
+
+
+def test_wall_source_errors(gpu_ctx):
+    import paper_2512_13965_gb300 as g
+    tau = np.ones((2, 2), np.float32)
+    with pytest.raises(g.GMCError) as e:
+        _solve_wall(gpu_ctx, tau, np.full((2, 2), 0.9, np.float32), [0.0, 0.0], 10,
+                    g.GMC_METHOD_ANALOG, 1)
+    assert e.value.status == g.GMC_EINVAL
+    with pytest.raises(g.GMCError) as e:
+        _solve_wall(gpu_ctx, tau, np.full((2, 2), 0.9, np.float32), [1.0, float("nan")], 10,
+                    g.GMC_METHOD_ANALOG, 1)
+    assert e.value.status == g.GMC_EINVAL

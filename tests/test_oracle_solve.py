@@ -3,9 +3,11 @@ GMC loop)."""
 import math
 
 import numpy as np
-from scipy import integrate
+import pytest
+from scipy import integrate, stats as sstats
 
 import synth
+from test_oracle_walk import uncollided_by_face
 from oracle import stats as ostats
 from oracle import transport as T
 
@@ -156,3 +158,55 @@ def test_global_frame_walk_sampler_is_the_mc_solve():
     np.testing.assert_allclose(b, a, rtol=1e-12, atol=1e-15)
     for k in ("leak", "absorbed", "transmissions", "roulette_kills"):
         assert abs(sa[k] - sb[k]) <= 1e-9 * max(1.0, abs(sa[k])), k
+
+
+# --- surface source on the left boundary ------------------------------------
+
+def _wall_single_cell(tau, c, n, seed):
+    """Per-history track lengths of a one-cell problem with the wall source
+    (the canonical walk from the births' entry states), and the solve."""
+    j, xi, gx, gy = T.wall_births([1.0], n, seed)
+    assert np.all(j == 0) and np.all(gx > 0)
+    r = T.transmit(xi, gx, gy, np.full(n, tau), np.full(n, c), T.MODE_IMPLICIT, seed,
+                   ids=np.arange(n, dtype=np.uint64), events=np.zeros(n, np.uint32))
+    flux, st = T.solve_gmc(np.full((1, 1), tau), np.full((1, 1), c), None, n, seed,
+                           T.walk_sampler_global(seed), wall=[1.0])
+    return r["s"], float(flux[0, 0]), st
+
+
+def test_wall_source_entry_law():
+    # u2 -> sin(theta) uniform in (-1, 1]: the cosine law; u1 -> xi uniform;
+    # the row follows the strengths
+    j, xi, gx, gy = T.wall_births([1.0, 0.0, 3.0], 40000, 12)
+    assert set(np.unique(j)) == {0, 2}
+    assert abs(np.mean(j == 2) - 0.75) < 4 * math.sqrt(0.75 * 0.25 / 40000)
+    assert np.allclose(gx * gx + gy * gy, 1.0) and np.all(gx >= 0)
+    for a in (xi, 0.5 * (gy + 1.0)):
+        assert sstats.kstest(a, "uniform").pvalue > 1e-3
+
+
+@pytest.mark.parametrize("tau", [0.5, 2.0])
+def test_wall_source_pure_absorber_closed_form(tau):
+    # c = 0 with implicit capture: no collisions, each history crosses the cell
+    # on a straight chord of optical length s and deposits 1 - e^{-s}, so the
+    # flux is (1 - P_unc) / tau with P_unc the uncollided transmission of the
+    # same entry law (the closed form of the walk tests).
+    n = 20000
+    s, flux, st = _wall_single_cell(tau, 0.0, n, 3)
+    per = -np.expm1(-s) / tau
+    assert flux == pytest.approx(per.mean(), rel=1e-12)
+    expect = (1.0 - uncollided_by_face(tau).sum()) / tau
+    assert abs(per.mean() - expect) < 4 * per.std() / math.sqrt(n)
+    assert st["transmissions"] == n
+
+
+def test_wall_source_pure_scatterer_mean_path():
+    # c = 1: nothing is absorbed, every history leaks, and the mean track length
+    # of a Lambertian inflow is pi tau / 4 for any tau (the path-length
+    # invariance), so the flux of the one-cell problem is pi / 4.
+    n, tau = 20000, 3.0
+    s, flux, st = _wall_single_cell(tau, 1.0, n, 4)
+    per = s / tau
+    assert flux == pytest.approx(per.mean(), rel=1e-12)
+    assert abs(per.mean() - math.pi / 4) < 4 * per.std() / math.sqrt(n)
+    assert st["leak"] == pytest.approx(n, rel=1e-12) and st["absorbed"] == 0.0
