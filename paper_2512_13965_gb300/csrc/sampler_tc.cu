@@ -3,30 +3,28 @@
 // memory as the next layer's A operand, weights streamed by bulk async copies.
 //
 // Work unit: a tile of 128 particles. One persistent CTA per SM owns two
-// tiles (X, Y) at a time and runs all K steps of both. Every layer is computed
-// as two N = 128 halves, each into one of two 128-column FP32 accumulators
-// (P, Q); epilogue group 0 converts every P, group 1 every Q, so the tensor
-// core computes one half while each group turns its previous half into
-// activations:
+// tiles (X, Y) at a time and runs all K steps of both, alternating them: the
+// tensor core computes one tile's layer while the epilogue warps turn the
+// other tile's previous layer into activations:
 //
-//   MMA warp:  X.P   X.Q   Y.P   Y.Q | next layer X.P ...
-//   group 0:         E(X.P)      E(Y.P)        (SiLU, BF16)
-//   group 1:               E(X.Q)      E(Y.Q)
+//   MMA warp:   L(X)   L(Y)   L+1(X)   L+1(Y) ...
+//   epilogue:          E(X)   E(Y)     E(X)  ...     (SiLU, BF16)
 //
 // Tensor memory (512 columns): A_X, A_Y (cols 0-127, 128-255): the 128 x 256
-// BF16 operand of each tile (row m in lane m, two K values per column); P, Q
-// (256-383, 384-511): accumulators. The epilogue reads its accumulator half
-// into registers, releases it at once, and writes the activations back to A_T
-// with tcgen05.st once the tile's second half has finished reading A_T: no
-// shared-memory traffic for activations.
+// BF16 operand of each tile (row m in lane m, two K values per column); D
+// (256-511): one 128 x 256 FP32 accumulator that the tiles use in turn. The
+// epilogue reads the accumulator into registers and releases it at once (the
+// other tile's MMAs may start), then writes the activations back to A_T with
+// tcgen05.st: no shared-memory traffic for activations. Two accumulators would
+// not fit beside the two operands.
 //
 // Per evaluation of v_theta and tile (M = 128 rows):
-//   L1: [x_hi | x_lo | cn | 1 1 0] (K = 16, BF16, shared memory) x B1 -> P, Q
+//   L1: [x_hi | x_lo | cn | 1 1 0] (K = 16, BF16, shared memory) x B1 -> D
 //       (the time-embedding columns of layer 1 are the same for every row,
 //        so W1[:, emb] emb(t) + b1 is folded into an FP32 per-evaluation bias)
 //   L2..L4: A_T (tensor memory) x W (shared memory, streamed in chunks of
-//       128 output rows x 128 bytes of K) -> P, Q
-//   L5: A_T x W5 (N = 16, rows 4..15 zero) -> P (tile X) or Q (tile Y)
+//       all 256 output rows x 128 bytes of K) -> D, N = 256 per MMA
+//   L5: A_T x W5 (N = 16, rows 4..15 zero) -> D columns 0..15
 // Epilogue: SiLU(z) = h + h tanh(h) with h = z/2 (layers 1-4 are packed with
 // weights and biases halved, so the accumulator holds h), in packed BF16x2.
 // The biases of layers 2-4 enter the accumulator through one extra K = 16 MMA
@@ -35,8 +33,10 @@
 // The ODE state x of tile T stays in FP32 registers of group T's threads.
 //
 // Roles: warp 0 streams weights, warp 1 owns tensor memory and issues MMAs,
-// warps 2..17 are the epilogue: two groups of 8 warps, two threads per row and
-// half, each loading its 64 columns at once and converting them in 16-column pieces.
+// warps 2..17 are the epilogue: two groups of 8 warps (group g: accumulator
+// columns 128 g .. 128 g + 127, and the ODE state of tile g), two threads per
+// row and group, each loading its 64 columns at once and converting them in
+// 16-column pieces.
 // CTAs run in clusters of two that consume the same weight chunks in the
 // same order: each CTA copies half of every chunk from L2 and multicasts it
 // into both CTAs' stage, so L2 serves each chunk once per pair; a stage is
@@ -51,7 +51,7 @@
 // scale (SiLU outputs are >= -0.279 and far below E4M3's 448), four per
 // tensor-memory column. Layer 1 keeps BF16 operands (the ODE state enters
 // through them) and layer 4's epilogue writes BF16, so layer 5 (the velocity)
-// is the same BF16 MMA as above. A 16 KB weight chunk then holds 128 inputs
+// is the same BF16 MMA as above. A 32 KB weight chunk then holds 128 inputs
 // instead of 64; a K step is 32 bytes (8 A columns) in both variants.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
