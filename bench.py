@@ -176,7 +176,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--workload", default="sampler",
-                    choices=["sampler", "solve", "hohlraum", "serve", "sweep", "heldout"])
+                    choices=["sampler", "solve", "hohlraum", "serve", "sweep", "heldout", "sigma"])
     ap.add_argument("--weights", default=None, help="GMCW file (default: Kaiming seed 1)")
     ap.add_argument("--internal-weights", default=None,
                     help="GMCW file of the internal-source model (solve/serve: births sampled by it)")
@@ -191,6 +191,8 @@ def main():
         return run_reference(args)
     if args.workload in ("solve", "hohlraum"):
         return run_solve(args)
+    if args.workload == "sigma":
+        return run_sigma(args)
     if args.workload == "serve":
         return run_serve(args)
     if args.workload == "sweep":
@@ -468,6 +470,48 @@ def run_solve(args):
                 ("internal model " + args.internal_weights) if args.internal_weights else "random walk"),
             "results": out, "unit": "cell transmissions/s"}
     print(json.dumps(line))
+    ctx.close()
+
+
+def run_sigma(args):
+    """Statistical convergence of the 128x128 solve (the solve workload's grid):
+    the cell-averaged run-to-run standard deviation of the flux over K = 5
+    independent runs, sigma_bar(N) = mean over cells of the sample standard
+    deviation (Eq. 12), at N = 1e5, 1e6, 1e7 histories, for the random walk,
+    GMC (BF16, midpoint 8) and the hybrid; the log-log slope should be -1/2."""
+    import numpy as np
+    import synth
+    g, ctx = _context(args)
+    tau, c, src = synth.grid_problem(n=128, seed=2)
+    tau, c, src = (np.ascontiguousarray(a.ravel()) for a in (tau, c, src))
+    Ns = [int(1e5), int(1e6), int(1e7)]
+    K = 5
+    methods = {"analog": (g.GMC_METHOD_ANALOG, 0.0), "gmc_bf16_midpoint8": (g.GMC_METHOD_GMC, 0.0),
+               "hybrid64_bf16_midpoint8": (g.GMC_METHOD_GMC, 64.0)}
+    out = {}
+    for name, (method, min_tau) in methods.items():
+        cfg = g.gmc_get_config(ctx)
+        cfg.steps, cfg.integrator, cfg.precision, cfg.gmc_min_tau = 8, g.GMC_MIDPOINT, g.GMC_BF16, min_tau
+        g.gmc_set_config(ctx, cfg)
+        rows = []
+        for n in Ns:
+            runs, secs = [], 0.0
+            for k in range(K):
+                f = np.zeros(128 * 128)
+                st = g.transport_solve(ctx, 128, 128, tau, c, src, n, method, 1000 + 17 * k, f)
+                runs.append(f)
+                secs += st.seconds
+            runs = np.asarray(runs)
+            sd = np.sqrt(((runs - runs.mean(0)) ** 2).sum(0) / (K - 1))
+            rows.append({"histories": n, "sigma_bar": float(sd.mean()), "seconds_per_run": secs / K})
+        x = np.log([r["histories"] for r in rows])
+        y = np.log([r["sigma_bar"] for r in rows])
+        out[name] = {"runs": rows, "slope": float(np.polyfit(x, y, 1)[0])}
+    print(json.dumps({"metric": "sigma_bar(N), Eq. 12, K = %d runs" % K,
+                      "workload": "transport solve 128x128 (solve workload grid)",
+                      "weights": args.weights or "kaiming seed 1 (untrained)",
+                      "births": ("internal model " + args.internal_weights) if args.internal_weights
+                      else "random walk", "results": out}))
     ctx.close()
 
 
