@@ -210,3 +210,21 @@ def test_wall_source_pure_scatterer_mean_path():
     assert flux == pytest.approx(per.mean(), rel=1e-12)
     assert abs(per.mean() - math.pi / 4) < 4 * per.std() / math.sqrt(n)
     assert st["leak"] == pytest.approx(n, rel=1e-12) and st["absorbed"] == 0.0
+
+
+def test_hohlraum_layout():
+    # five material classes where the layout puts them; the source drives the
+    # entrance rows, which are window cells on the left boundary
+    n = 64
+    tau, c, wall = synth.hohlraum_problem(n)
+    mats = {m: (t, cc) for m, (t, cc) in synth.HOHLRAUM_MATERIALS.items()}
+    assert {(float(a), float(b)) for a, b in zip(tau.ravel(), c.ravel())} == \
+        {(float(np.float32(t)), float(np.float32(cc))) for t, cc in mats.values()}
+    t_wall, t_win = np.float32(mats["wall"][0]), np.float32(mats["window"][0])
+    assert np.all(tau[0, :] == t_wall) and np.all(tau[-1, :] == t_wall) and np.all(tau[:, -1] == t_wall)
+    lit = np.flatnonzero(wall > 0)
+    assert lit.min() == n // 4 and lit.max() == 3 * n // 4 - 1
+    assert np.all(tau[lit, 0] == t_win) and np.all(tau[np.flatnonzero(wall == 0)[4:-4], 0] == t_wall)
+    centre = tau[n // 2, n // 2]
+    assert centre == np.float32(mats["fuel"][0])
+    assert np.allclose(tau, tau[::-1, :])  # mirror symmetry about the horizontal axis
