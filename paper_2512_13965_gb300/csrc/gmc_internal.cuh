@@ -14,6 +14,7 @@ namespace gmc {
 
 constexpr int kCond = 5, kState = 4, kEmb = 16, kIn = kCond + kState + kEmb, kHidden = 256;
 constexpr int kIn1Pad = 32;  // layer-1 input padded to 32 columns
+constexpr int kMaxDevices = 64;  // per-device launch caches (attributes, occupancy)
 constexpr float kSMin = 1e-7f;
 
 // FP32 network, transposed for the SIMT path: w1t [32][256] (rows 25..31

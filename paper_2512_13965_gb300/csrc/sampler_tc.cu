@@ -57,6 +57,7 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <atomic>
 #include <cstring>
 
 #include "decode.cuh"
@@ -865,8 +866,12 @@ cudaError_t launch_tc(cudaStream_t stream, const Params &p, int sms) {
   lc.dynamicSmemBytes = SMEM_BYTES;
   lc.stream = stream;
   // a persistent grid must be co-resident: at most the clusters that fit
-  static int max_clusters = -1;
-  if (max_clusters < 0) {
+  // (queried once per device)
+  static std::atomic<int> cached[kMaxDevices];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int max_clusters = (dev >= 0 && dev < kMaxDevices) ? cached[dev].load(std::memory_order_relaxed) : 0;
+  if (max_clusters < 1) {
     lc.gridDim = dim3((unsigned)(sms / CLUSTER * CLUSTER));
     int mc = 0;
     if (cudaOccupancyMaxActiveClusters(&mc, kernel, &lc) != cudaSuccess || mc < 1) {
@@ -874,6 +879,7 @@ cudaError_t launch_tc(cudaStream_t stream, const Params &p, int sms) {
       mc = sms / CLUSTER;
     }
     max_clusters = mc;
+    if (dev >= 0 && dev < kMaxDevices) cached[dev].store(mc, std::memory_order_relaxed);
   }
   const int grid_fit = grid < max_clusters * CLUSTER ? grid : max_clusters * CLUSTER;
   lc.gridDim = dim3((unsigned)grid_fit);

@@ -17,6 +17,7 @@
 // Every wait is bounded; a timeout sets the context's device error word.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstring>
 
 #include "gmc_internal.cuh"
@@ -267,12 +268,15 @@ __global__ void splitk_reduce_kernel(int64_t n, int S, const float *__restrict__
 template <int BN, int EPI>
 cudaError_t launch_bn(cudaStream_t st, const TgParams &p, int splits) {
   constexpr size_t smem = 2 * ((size_t)A_BYTES + (size_t)BN * 128) + 64 + 1024;
-  static bool attr = false;
-  if (!attr) {
+  // the attribute is per device: set it once on each device this process uses
+  static std::atomic<bool> attr[kMaxDevices];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kMaxDevices || !attr[dev].load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(tgemm_kernel<BN, EPI>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    if (dev >= 0 && dev < kMaxDevices) attr[dev].store(true, std::memory_order_release);
   }
   dim3 grid((unsigned)((p.M + 127) / 128), (unsigned)((p.N + BN - 1) / BN), (unsigned)splits);
   tgemm_kernel<BN, EPI><<<grid, TG_THREADS, smem, st>>>(p);
