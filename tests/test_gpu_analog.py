@@ -138,3 +138,23 @@ def test_edge_sizes_and_errors(gpu_ctx):
     g.analog_transmit(gpu_ctx, 0, z, z, z, z, z, 0, 0, 0, 0, st, ex)
     with pytest.raises(g.GMCError):
         g.analog_transmit(gpu_ctx, 1, z, z, z, z, z, 7, 0, 0, 0, st, ex)
+
+
+def test_pinned_host_buffers_in_place(gpu_ctx):
+    """Page-locked host arrays are read and written in place by the walk
+    kernel: outputs equal those from device arrays bit for bit."""
+    import paper_2512_13965_gb300 as g
+    n = 20000 + 3
+    e = synth.cell_entries(n, 77)
+    ref = _gpu(gpu_ctx, e, 2.0, 0.9, g.GMC_ABSORB_IMPLICIT, seed=5)
+    p = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+    st = torch.full((n,), -7, dtype=torch.int32).pin_memory()
+    ex = torch.full((4, n), float("nan")).pin_memory()
+    nc = torch.zeros(n, dtype=torch.int32).pin_memory()
+    g.analog_transmit(gpu_ctx, n, p(e["xi"]), p(e["cos"]), p(e["sin"]), p(np.full(n, 2.0)),
+                      p(np.full(n, 0.9)), g.GMC_ABSORB_IMPLICIT, 5, 0, 0, st, ex, nc)
+    exn = ex.numpy().astype(np.float64)
+    assert np.array_equal(st.numpy(), ref["status"])
+    assert np.array_equal(exn[0], ref["p"]) and np.array_equal(exn[3], ref["s"])
+    assert np.array_equal(exn[1], ref["ux"]) and np.array_equal(exn[2], ref["uy"])
+    assert np.array_equal(nc.numpy().view(np.uint32).astype(np.int64), ref["ncoll"])
