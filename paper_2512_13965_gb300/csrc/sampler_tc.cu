@@ -46,8 +46,8 @@
 // FP8 variant (template argument FP8): the three 256 x 256 layers (97% of the
 // FLOPs) run as kind::f8f6f4 MMAs on E4M3 operands. Each output row c of
 // W2..W4 is stored as E4M3 codes of W[c][:] / s_c with s_c = max_k |W[c][k]| / 448
-// (per-output-channel scale, FP32), and the epilogue applies h = acc s_c / 2
-// + b_c / 2 in one FMA. Activations entering layers 2-4 are E4M3 with unit
+// (per-output-channel scale, FP32); the bias enters the accumulator as b_c / s_c
+// through the bias MMA, and the epilogue applies h = acc s_c / 2. Activations entering layers 2-4 are E4M3 with unit
 // scale (SiLU outputs are >= -0.279 and far below E4M3's 448), four per
 // tensor-memory column. Layer 1 keeps BF16 operands (the ODE state enters
 // through them) and layer 4's epilogue writes BF16, so layer 5 (the velocity)
@@ -97,9 +97,10 @@ struct Packed {
   static constexpr size_t OFF_HID = 0;                  // [layer 0..2][chunk] x CHUNK
   static constexpr size_t OFF_B1 = 3 * (size_t)NCH * CHUNK;  // 256 rows x 32 B, 32-byte swizzle
   static constexpr size_t OFF_B5 = OFF_B1 + 8192;       // 4 K-blocks x 16 rows x 128 B
-  // BF16 only: biases of layers 2-4 as one block per layer of 256 rows x 32 B
-  // (32-byte swizzle), K = 16 with the bias in columns 13 (BF16 value) and 14
-  // (BF16 remainder), the others zero
+  // biases of layers 2-4 as one block per layer of 256 rows x 32 B (32-byte
+  // swizzle), K = 16 with the bias in columns 13 (BF16 value) and 14 (BF16
+  // remainder), the others zero: b/2 (BF16 variant) or b/s_c (FP8 variant,
+  // whose epilogue multiplies the accumulator by s_c/2)
   static constexpr size_t OFF_BIAS = OFF_B5 + 8192;
   static constexpr size_t BYTES = OFF_BIAS + 24576;
 };
@@ -235,32 +236,19 @@ __device__ __forceinline__ void write_a1_x(uint32_t a_base, int r, const float (
                pack_bf16x2(lo[0], lo[1]), pack_bf16x2(lo[2], lo[3]));
 }
 
-// Halved pre-activations of 4 accumulator columns: acc + bias, or with
-// SCALED (an FP8 layer) acc * scale + bias.
-template <bool SCALED>
-__device__ __forceinline__ float4 pre4(const uint32_t *p, const float4 *b4, const float4 *s4, int q) {
+// Halved pre-activations of 4 accumulator columns: acc + bias.
+__device__ __forceinline__ float4 pre4(const uint32_t *p, const float4 *b4, int q) {
   const float4 b = __ldg(b4 + q);
-  float4 z;
-  if constexpr (SCALED) {
-    const float4 sc = __ldg(s4 + q);
-    z.x = fmaf(__uint_as_float(p[0]), sc.x, b.x);
-    z.y = fmaf(__uint_as_float(p[1]), sc.y, b.y);
-    z.z = fmaf(__uint_as_float(p[2]), sc.z, b.z);
-    z.w = fmaf(__uint_as_float(p[3]), sc.w, b.w);
-  } else {
-    z.x = __uint_as_float(p[0]) + b.x;
-    z.y = __uint_as_float(p[1]) + b.y;
-    z.z = __uint_as_float(p[2]) + b.z;
-    z.w = __uint_as_float(p[3]) + b.w;
-  }
-  return z;
+  return make_float4(__uint_as_float(p[0]) + b.x, __uint_as_float(p[1]) + b.y,
+                     __uint_as_float(p[2]) + b.z, __uint_as_float(p[3]) + b.w);
 }
 
 
-// Epilogue pre-activation modes: the bias already in the accumulator (BF16
-// layers 2-4, whose bias enters through the MMA), bias added here (layer 1,
-// whose bias depends on t), or per-channel scale and bias (FP8 layers 2-4).
-enum : int { kPreNone = 0, kPreBias = 1, kPreScaleBias = 2 };
+// Epilogue pre-activation modes: the bias already in the accumulator (layers
+// 2-4, whose biases enter through the MMA), bias added here (layer 1, whose
+// bias depends on t), or a per-channel scale (FP8 layers 2-4, bias already in
+// the accumulator in units of that scale).
+enum : int { kPreNone = 0, kPreBias = 1, kPreScale = 2 };
 
 // SiLU of one thread's 16 accumulator columns starting at col0, packed as the
 // next layer's operand: 8 BF16x2 words or, with OUT8, 4 words of four E4M3
@@ -277,7 +265,13 @@ __device__ __forceinline__ void silu16(const uint32_t *v, const float *__restric
       z = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
                       __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
     } else {
-      z = pre4<MODE == kPreScaleBias>(v + 4 * q, b4, s4, q);
+      if constexpr (MODE == kPreScale) {
+        const float4 sc = __ldg(s4 + q);
+        z = make_float4(__uint_as_float(v[4 * q]) * sc.x, __uint_as_float(v[4 * q + 1]) * sc.y,
+                        __uint_as_float(v[4 * q + 2]) * sc.z, __uint_as_float(v[4 * q + 3]) * sc.w);
+      } else {
+        z = pre4(v + 4 * q, b4, q);
+      }
     }
     if constexpr (OUT8) {
       w[q] = silu2_halved_e4m3(z.x, z.y) | (silu2_halved_e4m3(z.z, z.w) << 16);
@@ -300,11 +294,11 @@ __device__ __forceinline__ void epi_piece(int L, const uint32_t *v, const float 
       if (L == 0)
         silu16<kPreBias, true>(v, bias, nullptr, col0, w);
       else
-        silu16<kPreScaleBias, true>(v, bias, scale + (L - 1) * 256, col0, w);
+        silu16<kPreScale, true>(v, bias, scale + (L - 1) * 256, col0, w);
       tmem_st4(a_row + (uint32_t)(col0 >> 2), w);
       return;
     }
-    silu16<kPreScaleBias, false>(v, bias, scale + 2 * 256, col0, w);
+    silu16<kPreScale, false>(v, bias, scale + 2 * 256, col0, w);
   } else {
     if (L == 0)
       silu16<kPreBias, false>(v, bias, nullptr, col0, w);
@@ -384,10 +378,10 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
-      mbar_arrive_expect_tx(&B.res_full, 16384 + (FP8 ? 0 : 24576));
+      mbar_arrive_expect_tx(&B.res_full, 16384 + 24576);
       bulk_g2s(sm + S_B1, P.packed + PK::OFF_B1, 8192, &B.res_full);
       bulk_g2s(sm + S_B5, P.packed + PK::OFF_B5, 8192, &B.res_full);
-      if (!FP8) bulk_g2s(sm + S_BIAS, P.packed + PK::OFF_BIAS, 24576, &B.res_full);
+      bulk_g2s(sm + S_BIAS, P.packed + PK::OFF_BIAS, 24576, &B.res_full);
       // the MMA warp's order: per hidden layer and tile, its chunks
       for (int64_t ip = 0; ip < n_iter && ok; ++ip)
         for (int e = 0; e < P.n_eval && ok; ++e)
@@ -471,9 +465,10 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
               if (L == 0) {
                 mma_f16_w(d, dA1[T], dB1, idn, 0);
               } else if (L < 4) {
-                // BF16: D = bias first (the two constant-1 columns of the
-                // tile's layer-1 operand times the bias block's hi/lo columns)
-                if (!FP8) mma_f16_w(d, dA1[T], dBias + (uint64_t)((L - 1) * 512), idn, 0);
+                // D = bias first (the two constant-1 columns of the tile's
+                // layer-1 operand times the bias block's hi/lo columns; a BF16
+                // MMA also in the FP8 variant, whose MMAs then accumulate)
+                mma_f16_w(d, dA1[T], dBias + (uint64_t)((L - 1) * 512), idn, 0);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
                   if (!wwait(&B.full[stage], sph)) {
@@ -488,7 +483,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
 #pragma unroll
                   for (int k = 0; k < MMAS_PER_CHUNK; ++k) {
                     const uint32_t a_k = a + (uint32_t)(32 * ch + 8 * k);
-                    const uint32_t acc = FP8 ? (uint32_t)((ch | k) != 0) : 1u;
+                    const uint32_t acc = 1u;
                     if constexpr (FP8)
                       mma_ts_f8_w(d, a_k, b_ch + (uint64_t)(2 * k), idh, acc);
                     else
@@ -838,6 +833,15 @@ void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *
         P[PK::OFF_HID + (size_t)(L * PK::NCH + ch) * CHUNK + chunk_byte_off(i, j)] =
             e4m3_bits((double)w[k] / sc);
       }
+      // bias block: b / s_c as BF16 hi + lo (the epilogue scales by s_c / 2)
+      const float v = (float)((double)b[L + 1][i] / sc);
+      const uint16_t hi = bf16_bits(v);
+      float hif;
+      const uint32_t hb = (uint32_t)hi << 16;
+      std::memcpy(&hif, &hb, 4);
+      const uint16_t lo = bf16_bits(v - hif);
+      std::memcpy(P + PK::OFF_BIAS + (size_t)L * 8192 + sw32_off(i, 13), &hi, 2);
+      std::memcpy(P + PK::OFF_BIAS + (size_t)L * 8192 + sw32_off(i, 14), &lo, 2);
     }
   pack_b1_b5_bias(W, b, P, PK::OFF_B1, PK::OFF_B5, bias_host);
 }
