@@ -47,5 +47,7 @@ typedef struct {
 
 void orc_walk_box(double tau, double c, int mode, double x, double y, double ux, double uy,
                   uint64_t seed, uint64_t id, uint32_t event0, orc_walk_result *res);
+void orc_walk_rect(double tx, double ty, double c, int mode, double x, double y, double ux,
+                   double uy, uint64_t seed, uint64_t id, uint32_t event0, orc_walk_result *res);
 
 #endif

@@ -72,6 +72,29 @@ def transmit(xi, cos_in, sin_in, tau, c, mode, seed, ids=None, events=None, id0=
     return out
 
 
+def transmit_rect(xi, cos_in, sin_in, tx, ty, c, mode, seed, ids=None, events=None):
+    """transmit for rectangular cells (geometry variant): optical width tx,
+    height ty, entry on the left face at y = xi ty; q normalized per face.
+    Per-particle Philox ids (default 0..n-1) and first events (default 0)."""
+    xi, cos_in, sin_in, tx, ty, c = (_c(a, np.float64) for a in (xi, cos_in, sin_in, tx, ty, c))
+    n = xi.shape[0]
+    ids = _c(np.arange(n) if ids is None else ids, np.uint64)
+    events = _c(np.zeros(n) if events is None else events, np.uint32)
+    out = {k: np.zeros(n, dtype=np.float64) for k in ("q", "ux", "uy", "s")}
+    status = np.zeros(n, dtype=np.int32)
+    face = np.zeros(n, dtype=np.int32)
+    ncoll = np.zeros(n, dtype=np.int64)
+    ev = np.zeros(n, dtype=np.uint32)
+    lib().orc_transmit_rect_ids(n, xi.ctypes.data, cos_in.ctypes.data, sin_in.ctypes.data,
+                                tx.ctypes.data, ty.ctypes.data, c.ctypes.data, mode, seed,
+                                ids.ctypes.data, events.ctypes.data, status.ctypes.data,
+                                face.ctypes.data, out["q"].ctypes.data, out["ux"].ctypes.data,
+                                out["uy"].ctypes.data, out["s"].ctypes.data, ncoll.ctypes.data,
+                                ev.ctypes.data)
+    out.update(status=status, face=face, ncoll=ncoll, events=ev)
+    return out
+
+
 def walk_one(tau, c, mode, x, y, ux, uy, seed, pid, event0):
     """One random walk from an arbitrary point (cell frame, optical units)."""
     status = ctypes.c_int32()

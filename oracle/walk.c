@@ -162,3 +162,101 @@ void orc_transmit_ids(int64_t n, const double *xi, const double *cos_in, const d
         event_out[i] = r.event;
     }
 }
+
+/*
+ * The same walk in a rectangular cell (the geometry variant with unequal
+ * sides): optical width tx along x, height ty along y; exits report q along
+ * the face normalized to [0,1) (counter-clockwise, as for the square), so
+ * p = face + q stays in [0,4). tx = ty = tau is exactly orc_walk_box.
+ */
+static void exit_point_rect(double tx, double ty, int face, double x, double y,
+                            orc_walk_result *res)
+{
+    double q;
+    switch (face) {
+    case 0: q = x / tx; y = 0.0; break;
+    case 1: q = y / ty; x = tx; break;
+    case 2: q = (tx - x) / tx; y = ty; break;
+    default: q = (ty - y) / ty; x = 0.0; break;
+    }
+    if (q < 0.0) q = 0.0;
+    if (q > 1.0) q = 1.0;
+    res->face = face;
+    res->q = q;
+    res->x = x;
+    res->y = y;
+}
+
+void orc_walk_rect(double tx, double ty, double c, int mode, double x, double y, double ux,
+                   double uy, uint64_t seed, uint64_t id, uint32_t event0, orc_walk_result *res)
+{
+    const double rate = (mode == ORC_MODE_IMPLICIT) ? c : 1.0;
+    uint32_t event = event0;
+    double s = 0.0;
+    int64_t ncoll = 0;
+    for (;;) {
+        double u[4];
+        orc_uniform4(seed, id, event, ORC_TAG_WALK, u);
+        ++event;
+        double d = (rate > 0.0) ? -log(u[0]) / rate : INFINITY;
+        double dbx = INFINITY, dby = INFINITY;
+        if (ux > 0.0) dbx = (tx - x) / ux;
+        else if (ux < 0.0) dbx = -x / ux;
+        if (uy > 0.0) dby = (ty - y) / uy;
+        else if (uy < 0.0) dby = -y / uy;
+        double db = dbx <= dby ? dbx : dby;
+        if (d >= db) {
+            s += db;
+            double xe = x + db * ux, ye = y + db * uy;
+            int face = (dbx <= dby) ? (ux > 0.0 ? 1 : 3) : (uy > 0.0 ? 2 : 0);
+            exit_point_rect(tx, ty, face, xe, ye, res);
+            res->status = ORC_EXITED;
+            res->ux = ux;
+            res->uy = uy;
+            break;
+        }
+        s += d;
+        x += d * ux;
+        y += d * uy;
+        ++ncoll;
+        if (mode == ORC_MODE_ANALOG && u[1] > c) {
+            res->status = ORC_ABSORBED;
+            res->face = -1;
+            res->q = 0.0;
+            res->x = x;
+            res->y = y;
+            res->ux = ux;
+            res->uy = uy;
+            break;
+        }
+        double phi = ORC_TWO_PI * u[2];
+        ux = cos(phi);
+        uy = sin(phi);
+    }
+    res->s = s;
+    res->ncoll = ncoll;
+    res->event = event;
+}
+
+/* Canonical-frame transmission through rectangles: particle i enters the
+   left face at y = xi[i]*ty[i]; otherwise as orc_transmit_ids. */
+void orc_transmit_rect_ids(int64_t n, const double *xi, const double *cos_in,
+                           const double *sin_in, const double *tx, const double *ty,
+                           const double *c, int mode, uint64_t seed, const uint64_t *ids,
+                           const uint32_t *events, int32_t *status, int32_t *face, double *q,
+                           double *ux, double *uy, double *s, int64_t *ncoll, uint32_t *event_out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        orc_walk_result r;
+        orc_walk_rect(tx[i], ty[i], c[i], mode, 0.0, xi[i] * ty[i], cos_in[i], sin_in[i], seed,
+                      ids[i], events[i], &r);
+        status[i] = r.status;
+        face[i] = r.face;
+        q[i] = r.q;
+        ux[i] = r.ux;
+        uy[i] = r.uy;
+        s[i] = r.s;
+        ncoll[i] = r.ncoll;
+        event_out[i] = r.event;
+    }
+}
