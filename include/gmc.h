@@ -249,6 +249,20 @@ gmc_status analog_transmit(gmc_ctx *ctx, int64_t n, const float *xi, const float
                            uint64_t seed, uint64_t id0, uint32_t event0, int32_t *status,
                            float *exit, uint32_t *ncoll);
 
+/*
+ * As analog_transmit for rectangular cells (the geometry variant with unequal
+ * sides): cell i has optical width tau_x[i] along x and height tau_y[i] along
+ * the entry face; the particle enters the left face at height
+ * xi[i] * tau_y[i]. The exit position q is normalized along the exit face
+ * (p = face + q in [0,4) as for the square cell), s is the track length in
+ * optical units. tau_x = tau_y = tau is analog_transmit's walk.
+ *  tau_x, tau_y  [n] float (> 0). Other arguments as analog_transmit.
+ */
+gmc_status analog_transmit_rect(gmc_ctx *ctx, int64_t n, const float *xi, const float *cos_in,
+                                const float *sin_in, const float *tau_x, const float *tau_y,
+                                const float *c, int mode, uint64_t seed, uint64_t id0,
+                                uint32_t event0, int32_t *status, float *exit, uint32_t *ncoll);
+
 /* ---- transport solve (the four-stage transport algorithm) ----------------- */
 
 /*

@@ -82,7 +82,7 @@ struct gmc_ctx {
   gmc::TrainState *train = nullptr;
 
   // staging buffers for host-pointer calls
-  gmc::Buffer stage[8];
+  gmc::Buffer stage[9];
   // per-evaluation layer-1 bias of the tensor-core sampler
   gmc::Buffer bias1;
   // transport_solve engine (kept between calls) and the serving thread
@@ -119,6 +119,10 @@ cudaError_t launch_analog(cudaStream_t stream, int64_t n, const float *xi, const
                           const float *sin_in, const float *tau, const float *c, int mode,
                           uint64_t seed, uint64_t id0, uint32_t event0, int32_t *status,
                           float *exit, uint32_t *ncoll);
+cudaError_t launch_analog_rect(cudaStream_t stream, int64_t n, const float *xi, const float *cos_in,
+                               const float *sin_in, const float *tx, const float *ty,
+                               const float *c, int mode, uint64_t seed, uint64_t id0,
+                               uint32_t event0, int32_t *status, float *exit, uint32_t *ncoll);
 
 // BF16 tensor-core GEMM of the training step (train_tc.cu):
 // C[m][n] = epi(sum_k A[m sam + k sak] B[n sbn + k sbk]), FP32 in and out,

@@ -161,6 +161,69 @@ __device__ __forceinline__ WalkResult walk_cell_resume(float tau, float c, int i
   return w;
 }
 
+// The walk in a rectangular cell of optical width tx and height ty (the
+// geometry variant with unequal sides), from (x, y) to its end; q is
+// normalized along the exit face, as for the square, which tx = ty gives.
+template <typename T>
+__device__ __forceinline__ WalkResult walk_rect(T tx, T ty, float c, int implicit, T x, T y,
+                                                float ux, float uy, uint64_t seed, uint64_t id,
+                                                uint32_t event) {
+  const float rate = implicit ? c : 1.0f;
+  const T inf = (T)INFINITY;
+  T s = 0;
+  uint32_t ncoll = 0;
+  WalkResult w;
+  w.status = kTruncated;
+  w.face = -1;
+  w.q = 0.0f;
+  for (uint32_t it = 0; it < kMaxFlights; ++it) {
+    const uint4 r = philox_draw(seed, id, event, kTagWalk);
+    ++event;
+    const T d = rate > 0.0f ? (T)(-logf(u01(r.x)) / rate) : inf;
+    T dbx = inf, dby = inf;
+    if (ux > 0.0f) dbx = (tx - x) / (T)ux;
+    else if (ux < 0.0f) dbx = -x / (T)ux;
+    if (uy > 0.0f) dby = (ty - y) / (T)uy;
+    else if (uy < 0.0f) dby = -y / (T)uy;
+    const bool xface = dbx <= dby;
+    T db = xface ? dbx : dby;
+    if (db < (T)0) db = (T)0;
+    if (d >= db) {
+      s += db;
+      int face;
+      T qn;
+      if (xface) {
+        face = ux > 0.0f ? 1 : 3;
+        const T along = y + db * (T)uy;
+        qn = face == 1 ? along / ty : (ty - along) / ty;
+      } else {
+        face = uy > 0.0f ? 2 : 0;
+        const T along = x + db * (T)ux;
+        qn = face == 0 ? along / tx : (tx - along) / tx;
+      }
+      w.status = kExited;
+      w.face = face;
+      w.q = fminf(fmaxf((float)qn, 0.0f), 1.0f);
+      break;
+    }
+    s += d;
+    x += d * (T)ux;
+    y += d * (T)uy;
+    ++ncoll;
+    if (!implicit && u01(r.y) > c) {
+      w.status = kAbsorbed;
+      break;
+    }
+    sincospif(2.0f * u01(r.z), &uy, &ux);
+  }
+  w.ux = ux;
+  w.uy = uy;
+  w.s = (float)s;
+  w.ncoll = ncoll;
+  w.event = event;
+  return w;
+}
+
 // Walk from a point given in normalized cell coordinates (X, Y in [0,1]),
 // picking the position precision from the cell's optical size.
 __device__ __forceinline__ WalkResult walk_cell(float tau, float c, int implicit, float X, float Y,
