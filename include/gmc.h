@@ -250,9 +250,10 @@ gmc_status analog_transmit(gmc_ctx *ctx, int64_t n, const float *xi, const float
                            float *exit, uint32_t *ncoll);
 
 /*
- * As analog_transmit for rectangular cells (the geometry variant with unequal
- * sides): cell i has optical width tau_x[i] along x and height tau_y[i] along
- * the entry face; the particle enters the left face at height
+ * As analog_transmit for rectangular cells (the random walk of section "Monte
+ * Carlo Method", Eq. 4, in the paper's cell of width W and height H, here with
+ * unequal optical sides): cell i has optical width tau_x[i] along x and
+ * height tau_y[i] along the entry face; the particle enters the left face at height
  * xi[i] * tau_y[i]. The exit position q is normalized along the exit face
  * (p = face + q in [0,4) as for the square cell), s is the track length in
  * optical units. tau_x = tau_y = tau is analog_transmit's walk.
