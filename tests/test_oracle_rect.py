@@ -115,3 +115,20 @@ def test_implicit_law_depends_on_c_times_sides():
     assert same
     assert np.allclose(b["s"], c * a["s"], rtol=1e-9, atol=1e-12)
     assert np.allclose(a["q"], b["q"], rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("c", [0.0, 0.5, 0.99])
+def test_mean_path_invariance_whole_boundary(c):
+    # isotropic inflow over the whole boundary (each face in proportion to its
+    # length, cosine law): the mean track length is pi A / P = pi tx ty / (2
+    # (tx + ty)) for any scattering rate (implicit capture; Blanco-Fournier).
+    # Entering a horizontal face is entering the left face of the cell turned
+    # by a quarter, tx <-> ty.
+    n, tx, ty = 200000, 2.5, 0.8
+    xi, cs, sn = _entries(n, 305)
+    vertical = np.random.default_rng(5).random(n) < ty / (tx + ty)
+    w = np.where(vertical, tx, ty)
+    h = np.where(vertical, ty, tx)
+    r = T.transmit_rect(xi, cs, sn, w, h, np.full(n, c), T.MODE_IMPLICIT, 7)
+    expect = math.pi * tx * ty / (2.0 * (tx + ty))
+    assert abs(r["s"].mean() - expect) < 4 * r["s"].std() / math.sqrt(n), (r["s"].mean(), expect)
