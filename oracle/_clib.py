@@ -59,6 +59,8 @@ def lib():
                                        P, P, P, P, P]
             L.orc_transmit_rect_ids.argtypes = [i64, P, P, P, P, P, P, i32, u64, P, P,
                                                 P, P, P, P, P, P, P, P]
+            L.orc_transmit_xy_ids.argtypes = [i64, P, P, P, P, P, P, P, i32, i32, u64, P, P,
+                                              P, P, P, P, P, P, P, P, P]
             L.orc_solve_analog.argtypes = [i32, i32, P, P, P, i64, u64, dbl, dbl, P, P]
             L.orc_solve_analog.restype = i32
             _lib = L

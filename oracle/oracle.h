@@ -5,7 +5,8 @@
  * Conventions (stated by specification; the CUDA path implements them in
  * code of its own):
  *  - A cell is the square [0,tau]^2 in optical coordinates (sigma_t = 1,
- *    lengths in total mean free paths). Directions lie on the unit circle.
+ *    lengths in total mean free paths). Directions lie on the unit circle,
+ *    except in the x-y geometry walk, whose directions are 3-D unit vectors.
  *  - Faces are numbered counter-clockwise from the corner (0,0):
  *    0 = bottom (y=0), 1 = right (x=tau), 2 = top (y=tau), 3 = left (x=0).
  *    A point on face f has a counter-clockwise parameter q in [0,1]:
@@ -49,5 +50,8 @@ void orc_walk_box(double tau, double c, int mode, double x, double y, double ux,
                   uint64_t seed, uint64_t id, uint32_t event0, orc_walk_result *res);
 void orc_walk_rect(double tx, double ty, double c, int mode, double x, double y, double ux,
                    double uy, uint64_t seed, uint64_t id, uint32_t event0, orc_walk_result *res);
+void orc_walk_xy(double tx, double ty, double c, int mode, int sphere, double x, double y,
+                 double ux, double uy, double uz, uint64_t seed, uint64_t id, uint32_t event0,
+                 orc_walk_result *res, double *uz_out);
 
 #endif

@@ -95,6 +95,34 @@ def transmit_rect(xi, cos_in, sin_in, tx, ty, c, mode, seed, ids=None, events=No
     return out
 
 
+def transmit_xy(xi, ux_in, uy_in, uz_in, tx, ty, c, mode, seed, ids=None, events=None,
+                sphere=True):
+    """Transmission in x-y geometry (geometry variant: the cell is the
+    cross-section of an infinite prism, directions are 3-D unit vectors, s is
+    the 3-D track length): entry on the left face at y = xi ty with direction
+    (ux_in, uy_in, uz_in); scattering isotropic on the sphere (on the circle
+    with sphere=False, which is transmit_rect draw for draw). The exit
+    direction's projection (ux, uy) lies in the unit disk."""
+    xi, ux_in, uy_in, uz_in, tx, ty, c = (_c(a, np.float64)
+                                          for a in (xi, ux_in, uy_in, uz_in, tx, ty, c))
+    n = xi.shape[0]
+    ids = _c(np.arange(n) if ids is None else ids, np.uint64)
+    events = _c(np.zeros(n) if events is None else events, np.uint32)
+    out = {k: np.zeros(n, dtype=np.float64) for k in ("q", "ux", "uy", "uz", "s")}
+    status = np.zeros(n, dtype=np.int32)
+    face = np.zeros(n, dtype=np.int32)
+    ncoll = np.zeros(n, dtype=np.int64)
+    ev = np.zeros(n, dtype=np.uint32)
+    lib().orc_transmit_xy_ids(n, xi.ctypes.data, ux_in.ctypes.data, uy_in.ctypes.data,
+                              uz_in.ctypes.data, tx.ctypes.data, ty.ctypes.data, c.ctypes.data,
+                              mode, int(bool(sphere)), seed, ids.ctypes.data, events.ctypes.data,
+                              status.ctypes.data, face.ctypes.data, out["q"].ctypes.data,
+                              out["ux"].ctypes.data, out["uy"].ctypes.data, out["uz"].ctypes.data,
+                              out["s"].ctypes.data, ncoll.ctypes.data, ev.ctypes.data)
+    out.update(status=status, face=face, ncoll=ncoll, events=ev)
+    return out
+
+
 def walk_one(tau, c, mode, x, y, ux, uy, seed, pid, event0):
     """One random walk from an arbitrary point (cell frame, optical units)."""
     status = ctypes.c_int32()

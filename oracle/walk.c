@@ -260,3 +260,96 @@ void orc_transmit_rect_ids(int64_t n, const double *xi, const double *cos_in,
         event_out[i] = r.event;
     }
 }
+
+/*
+ * The walk in x-y geometry (the geometry variant in which the cell is the
+ * cross-section of an infinite prism and directions are 3-D; the paper
+ * encodes them by their projection on the unit disk): the direction is the
+ * unit vector (ux, uy, uz), the particle's position moves in the plane by
+ * d (ux, uy) over a flight of 3-D length d, and the track length s is 3-D.
+ * Faces, q and the flight draws are those of orc_walk_rect. A scattering
+ * draws the new direction isotropically on the sphere: azimuth 2 pi u2 and
+ * polar cosine uz = 2 u3 - 1 (u3 is the fourth uniform of the flight's draw);
+ * with sphere = 0 it stays on the circle (uz = 0) and the walk is
+ * orc_walk_rect draw for draw.
+ */
+void orc_walk_xy(double tx, double ty, double c, int mode, int sphere, double x, double y,
+                 double ux, double uy, double uz, uint64_t seed, uint64_t id, uint32_t event0,
+                 orc_walk_result *res, double *uz_out)
+{
+    const double rate = (mode == ORC_MODE_IMPLICIT) ? c : 1.0;
+    uint32_t event = event0;
+    double s = 0.0;
+    int64_t ncoll = 0;
+    for (;;) {
+        double u[4];
+        orc_uniform4(seed, id, event, ORC_TAG_WALK, u);
+        ++event;
+        double d = (rate > 0.0) ? -log(u[0]) / rate : INFINITY;
+        double dbx = INFINITY, dby = INFINITY;
+        if (ux > 0.0) dbx = (tx - x) / ux;
+        else if (ux < 0.0) dbx = -x / ux;
+        if (uy > 0.0) dby = (ty - y) / uy;
+        else if (uy < 0.0) dby = -y / uy;
+        double db = dbx <= dby ? dbx : dby;
+        if (d >= db) {
+            s += db;
+            double xe = x + db * ux, ye = y + db * uy;
+            int face = (dbx <= dby) ? (ux > 0.0 ? 1 : 3) : (uy > 0.0 ? 2 : 0);
+            exit_point_rect(tx, ty, face, xe, ye, res);
+            res->status = ORC_EXITED;
+            break;
+        }
+        s += d;
+        x += d * ux;
+        y += d * uy;
+        ++ncoll;
+        if (mode == ORC_MODE_ANALOG && u[1] > c) {
+            res->status = ORC_ABSORBED;
+            res->face = -1;
+            res->q = 0.0;
+            res->x = x;
+            res->y = y;
+            break;
+        }
+        double phi = ORC_TWO_PI * u[2];
+        double r = 1.0;
+        uz = 0.0;
+        if (sphere) {
+            uz = 2.0 * u[3] - 1.0;
+            r = sqrt(1.0 - uz * uz);
+        }
+        ux = r * cos(phi);
+        uy = r * sin(phi);
+    }
+    res->ux = ux;
+    res->uy = uy;
+    res->s = s;
+    res->ncoll = ncoll;
+    res->event = event;
+    *uz_out = uz;
+}
+
+/* Canonical-frame transmission in x-y geometry: particle i enters the left
+   face at y = xi[i]*ty[i] with the 3-D direction (ux_in, uy_in, uz_in)[i]. */
+void orc_transmit_xy_ids(int64_t n, const double *xi, const double *ux_in, const double *uy_in,
+                         const double *uz_in, const double *tx, const double *ty,
+                         const double *c, int mode, int sphere, uint64_t seed,
+                         const uint64_t *ids, const uint32_t *events, int32_t *status,
+                         int32_t *face, double *q, double *ux, double *uy, double *uz, double *s,
+                         int64_t *ncoll, uint32_t *event_out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        orc_walk_result r;
+        orc_walk_xy(tx[i], ty[i], c[i], mode, sphere, 0.0, xi[i] * ty[i], ux_in[i], uy_in[i],
+                    uz_in[i], seed, ids[i], events[i], &r, &uz[i]);
+        status[i] = r.status;
+        face[i] = r.face;
+        q[i] = r.q;
+        ux[i] = r.ux;
+        uy[i] = r.uy;
+        s[i] = r.s;
+        ncoll[i] = r.ncoll;
+        event_out[i] = r.event;
+    }
+}

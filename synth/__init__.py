@@ -10,6 +10,8 @@ Workload recipes (the paper's geometries and data are not available, so each
 input is drawn from the distributions the workload names):
   * cell entries: xi ~ U[0,1), sin(theta) ~ U(-1,1) (an inward direction with
     cosine-weighted density on the entry face), cos(theta) = sqrt(1 - sin^2);
+  * x-y geometry entries: xi ~ U[0,1), the cosine to the face normal is
+    sqrt(U[0,1)) and the azimuth about it U[0, 2 pi) (3-D cosine law);
   * sampler conditions: tau log-uniform in [0.1, 1000], c uniform in
     [0.5, 0.999], entries as above; condition vector
     (xi, cos theta, sin theta, ln tau, c);
@@ -38,6 +40,19 @@ def cell_entries(n, seed):
     cs = np.sqrt(np.maximum(1.0 - sn * sn, 0.0))
     return {"xi": xi.astype(np.float32), "cos": cs.astype(np.float32),
             "sin": sn.astype(np.float32)}
+
+
+def cell_entries_xy(n, seed):
+    """Entry states on the left face with 3-D directions (x-y geometry):
+    xi ~ U[0,1), cosine to the face normal ux = sqrt(U[0,1)) (the cosine-law
+    inflow of an isotropic flux), azimuth about the normal U[0, 2 pi):
+    dict of float64 arrays xi, ux, uy, uz."""
+    g = generator(seed)
+    xi = g.random(n)
+    mu = np.sqrt(g.random(n))
+    phi = g.uniform(0.0, 2.0 * np.pi, n)
+    r = np.sqrt(np.maximum(1.0 - mu * mu, 0.0))
+    return {"xi": xi, "ux": mu, "uy": r * np.cos(phi), "uz": r * np.sin(phi)}
 
 
 def materials(n, seed, tau_range=(0.1, 1000.0), c_range=(0.5, 0.999)):
