@@ -16,6 +16,9 @@ What it computes, in the paper's order:
   * Decoding (the fourth stage of the transport algorithm): destandardize,
     wrap p into [0,4), split it into face and position, renormalize the
     direction, make it point out of the exit face, s = exp(ln s).
+    decode_disk is the decoding of x-y geometry, whose directions are 3-D and
+    enter the network by their projection on the unit disk: the projection
+    is pulled back into the disk instead of onto the circle.
 
 Matrix products use numpy's matmul in float64 (a library primitive); nothing
 is blocked, fused or reordered beyond the definitions above.
@@ -215,3 +218,36 @@ def decode(net, y_raw):
     uy = np.where(inward, uy - 2.0 * dot * n_out[:, 1], uy)
     s = np.maximum(np.exp(y[:, 3]), S_MIN)
     return {"face": face, "q": q, "ux": ux, "uy": uy, "s": s, "inward": inward}
+
+
+def decode_disk(net, y_raw):
+    """Standardized ODE output [4, B] -> exit state for x-y geometry, where
+    (y1, y2) is the projection of a 3-D unit direction on the unit disk.
+
+    face, q and s as in decode; the projection is scaled back onto the unit
+    circle when it falls outside the disk, its component along the exit
+    face's normal is reflected when it points inward, and one with no outward
+    component left (parallel to the face, or zero) becomes the outward
+    normal. uz is the out-of-plane magnitude sqrt(1 - ux^2 - uy^2) (its sign
+    does not enter a walk in the plane).
+    """
+    y = np.asarray(y_raw, dtype=np.float64).T * net.y_std + net.y_mean
+    p = np.mod(y[:, 0], 4.0)
+    face = np.minimum(np.floor(p), 3.0).astype(np.int64)
+    q = np.clip(p - face, 0.0, 1.0)
+    ux, uy = y[:, 1].copy(), y[:, 2].copy()
+    norm = np.hypot(ux, uy)
+    big = norm > 1.0
+    ux = np.where(big, ux / np.where(big, norm, 1.0), ux)
+    uy = np.where(big, uy / np.where(big, norm, 1.0), uy)
+    n_out = OUTWARD[face]
+    dot = ux * n_out[:, 0] + uy * n_out[:, 1]
+    inward = dot < 0.0
+    ux = np.where(inward, ux - 2.0 * dot * n_out[:, 0], ux)
+    uy = np.where(inward, uy - 2.0 * dot * n_out[:, 1], uy)
+    flat = dot == 0.0
+    ux = np.where(flat, n_out[:, 0], ux)
+    uy = np.where(flat, n_out[:, 1], uy)
+    uz = np.sqrt(np.maximum(1.0 - ux * ux - uy * uy, 0.0))
+    s = np.maximum(np.exp(y[:, 3]), S_MIN)
+    return {"face": face, "q": q, "ux": ux, "uy": uy, "uz": uz, "s": s, "inward": inward}

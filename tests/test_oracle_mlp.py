@@ -178,6 +178,36 @@ def test_decode_rules(tmp_path):
     np.testing.assert_allclose(d["s"], [2.0, 1.0, mlp.S_MIN, math.e])
 
 
+def test_decode_disk_rules(tmp_path):
+    # x-y geometry: the projected direction stays inside the unit disk
+    net = _zero_net()
+    net["y_mean"] = np.array([0, 0, 0, 0], np.float32)
+    net["y_std"] = np.array([1, 1, 1, 1], np.float32)
+    o = _load(tmp_path, net)
+    y = np.array([
+        [1.5, 0.3, 0.4, 0.0],      # right face, inside the disk: kept
+        [1.5, 3.0, 4.0, 0.0],      # outside the disk: back onto the circle
+        [1.5, -0.3, 0.4, 0.0],     # inward: reflected
+        [1.5, 0.0, 0.5, 0.0],      # parallel to the face: outward normal
+        [0.25, 0.0, 0.0, 0.0],     # zero on the bottom face: outward normal
+        [2.5, -0.6, -0.8, 0.0],    # top face, on the circle, inward: reflected
+        [-0.5, -0.28, -0.96, 0.0], # wraps to the left face, unit, outward
+    ]).T
+    d = mlp.decode_disk(o, y)
+    np.testing.assert_array_equal(d["face"], [1, 1, 1, 1, 0, 2, 3])
+    ex = np.array([[0.3, 0.4], [0.6, 0.8], [0.3, 0.4], [1.0, 0.0], [0.0, -1.0],
+                   [-0.6, 0.8], [-0.28, -0.96]])
+    np.testing.assert_allclose(np.stack([d["ux"], d["uy"]], 1), ex, atol=1e-15)
+    np.testing.assert_allclose(d["uz"], [math.sqrt(0.75), 0, math.sqrt(0.75), 0, 0, 0, 0],
+                               atol=1e-7)
+    np.testing.assert_array_equal(d["inward"], [False, False, True, False, False, True, False])
+    # on the circle the disk decode is the circle decode
+    f = mlp.decode(o, y[:, [1, 5, 6]])
+    g = mlp.decode_disk(o, y[:, [1, 5, 6]])
+    for k in ("face", "q", "ux", "uy", "s"):
+        np.testing.assert_allclose(f[k], g[k], atol=1e-15)
+
+
 def test_decode_destandardizes(tmp_path):
     net = _zero_net()
     net["y_mean"] = np.array([2.0, 0.0, 0.0, 1.0], np.float32)
