@@ -23,7 +23,8 @@
  *
  * Conventions:
  *  - Every call returns a gmc_status; nothing throws across the ABI. On error
- *    gmc_last_error(ctx) describes the failure.
+ *    gmc_last_error(ctx) describes the failure (the returned string is the
+ *    calling thread's copy, valid until its next gmc_last_error call).
  *  - Array arguments are structure-of-arrays, row k of an [m][n] array
  *    starting at element k*n. Unless a parameter says "host", array pointers
  *    may be device pointers (the call runs asynchronously on the context's
@@ -128,7 +129,8 @@ gmc_status gmc_set_stream(gmc_ctx *ctx, void *cuda_stream);
 gmc_status gmc_synchronize(gmc_ctx *ctx);
 gmc_status gmc_get_config(const gmc_ctx *ctx, gmc_config *out);
 /* Validates and applies `cfg` (steps in [1, 256], w_cut >= 0,
-   p_survive in (0, 1], bank_capacity in [1024, 2^28]). */
+   p_survive in (0, 1], bank_capacity in [1024, 2^28]); GMC_EBUSY while the
+   server (gmc_serve_start) runs. */
 gmc_status gmc_set_config(gmc_ctx *ctx, const gmc_config *cfg);
 const char *gmc_status_str(gmc_status s);
 const char *gmc_last_error(const gmc_ctx *ctx);
@@ -155,8 +157,10 @@ gmc_status gmc_normals(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uin
  * f32 W[out][in], f32 b[out]. The network input is [standardized condition
  * (5), state x (4), emb(t) (16)] with emb(t) = [sin(2^j pi t)]_{j<8},
  * [cos(2^j pi t)]_{j<8}; hidden layers use SiLU. Returns GMC_EIO if the file
- * cannot be read, GMC_EFORMAT on any layout mismatch. The FP32 weights are
- * kept and the BF16 / FP8 packed copies are derived from them.
+ * cannot be read, GMC_EFORMAT on any layout mismatch (the network loaded
+ * before, if any, is then kept unchanged), GMC_EBUSY while the server runs.
+ * The FP32 weights are kept and the BF16 / FP8 packed copies are derived
+ * from them.
  */
 gmc_status gmc_load_weights(gmc_ctx *ctx, const char *path);
 /* Same, from a host buffer holding the file's bytes. */
@@ -331,7 +335,7 @@ typedef struct gmc_serve_config {
  * memory budget and one of 64 request slots is free. Its result equals that
  * of transport_solve alone (same random numbers; only the order of FP64
  * additions differs). The server uses its own stream and buffers; loading
- * weights or changing the configuration while it runs is not supported.
+ * weights and gmc_set_config return GMC_EBUSY while it runs.
  */
 gmc_status gmc_serve_start(gmc_ctx *ctx, const gmc_serve_config *cfg);
 /* Queues a solve; *ticket identifies it. GMC_ENOMEM if the request alone
@@ -418,7 +422,8 @@ gmc_status gmc_train_grad(gmc_ctx *ctx, int64_t B, const float *cn, const float 
 gmc_status gmc_train_params(gmc_ctx *ctx, float *out);
 int64_t gmc_train_param_count(void);
 /* Makes the trained network (with its standardization) the sampler's
-   network; also writes it as a GMCW file when `path` is not null. */
+   network; also writes it as a GMCW file when `path` is not null.
+   GMC_EBUSY, with nothing written, while the server runs. */
 gmc_status gmc_train_commit(gmc_ctx *ctx, const char *path);
 
 #ifdef __cplusplus

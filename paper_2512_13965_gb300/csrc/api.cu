@@ -4,7 +4,9 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "gmc_internal.cuh"
@@ -18,6 +20,7 @@ gmc_status set_error(gmc_ctx *ctx, gmc_status s, const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
+    std::lock_guard<std::mutex> lk(ctx->err_mu);
     ctx->last_error = buf;
   }
   return s;
@@ -180,7 +183,14 @@ const char *gmc_status_str(gmc_status s) {
   return "GMC_UNKNOWN";
 }
 
-const char *gmc_last_error(const gmc_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+const char *gmc_last_error(const gmc_ctx *ctx) {
+  if (!ctx) return "null context";
+  // a copy per calling thread: the serving thread may replace the message
+  thread_local std::string copy;
+  std::lock_guard<std::mutex> lk(ctx->err_mu);
+  copy = ctx->last_error;
+  return copy.c_str();
+}
 
 gmc_status gmc_create(gmc_ctx **out, int device) {
   if (!out) return GMC_EINVAL;
@@ -256,6 +266,7 @@ gmc_status gmc_get_config(const gmc_ctx *ctx, gmc_config *out) {
 
 gmc_status gmc_set_config(gmc_ctx *ctx, const gmc_config *cfg) {
   if (!ctx || !cfg) return GMC_EINVAL;
+  if (ctx->server) return set_error(ctx, GMC_EBUSY, "gmc_set_config: the server is running");
   if (cfg->steps < 1 || cfg->steps > 256)
     return set_error(ctx, GMC_EINVAL, "steps must be in [1, 256], got %d", cfg->steps);
   if (cfg->integrator != GMC_EULER && cfg->integrator != GMC_MIDPOINT && cfg->integrator != GMC_RK4)
@@ -307,8 +318,11 @@ gmc_status gmc_normals(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uin
 
 namespace gmc {
 // Parses a GMCW version 1 blob into N and uploads its FP32, BF16 and FP8 copies.
+// Nothing of N changes unless the blob parses; N stays marked unloaded from
+// the first change until every device copy is in place.
 gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   static const uint32_t dims_ok[6] = {25, 256, 256, 256, 256, 4};
+  if (ctx->server) return set_error(ctx, GMC_EBUSY, "loading weights: the server is running");
   Reader rd{(const unsigned char *)blob, nbytes};
   if (nbytes < 4 || std::memcmp(blob, "GMCW", 4) != 0)
     return set_error(ctx, GMC_EFORMAT, "weight file: bad magic");
@@ -325,8 +339,10 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
       return set_error(ctx, GMC_EFORMAT, "weight file: layer dims must be 25-256-256-256-256-4");
   float st[18];
   if (!rd.f32(st, 18)) return set_error(ctx, GMC_EFORMAT, "weight file: truncated statistics");
+  const size_t wl = sizeof(N.host_w[0]) / sizeof(float), bl = sizeof(N.host_b[0]) / sizeof(float);
+  std::vector<float> tw(5 * wl, 0.0f), tb(5 * bl, 0.0f);
   for (int l = 0; l < 5; ++l) {
-    if (!rd.f32(N.host_w[l], (size_t)dims[l + 1] * dims[l]) || !rd.f32(N.host_b[l], dims[l + 1]))
+    if (!rd.f32(&tw[l * wl], (size_t)dims[l + 1] * dims[l]) || !rd.f32(&tb[l * bl], dims[l + 1]))
       return set_error(ctx, GMC_EFORMAT, "weight file: truncated layer %d", l);
   }
   if (rd.off != nbytes) return set_error(ctx, GMC_EFORMAT, "weight file: trailing bytes");
@@ -335,6 +351,11 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   for (int k = 0; k < 18; ++k)
     if (!std::isfinite(st[k])) return set_error(ctx, GMC_EFORMAT, "weight file: non-finite statistics");
 
+  N.loaded = false;
+  for (int l = 0; l < 5; ++l) {
+    std::memcpy(N.host_w[l], &tw[l * wl], wl * sizeof(float));
+    std::memcpy(N.host_b[l], &tb[l * bl], bl * sizeof(float));
+  }
   NetStats ns;
   for (int k = 0; k < 5; ++k) {
     ns.cond_mean[k] = st[k];

@@ -69,8 +69,8 @@ struct gmc_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
   std::string last_error;
+  mutable std::mutex err_mu;  // last_error is also written by the serving thread
   gmc_config cfg{};
-  std::mutex mu;
 
   // networks: the boundary model (cell transmissions, gmc_load_weights) and
   // the internal model (births inside a source cell, gmc_load_internal_weights)

@@ -688,6 +688,7 @@ gmc_status gmc_train_commit(gmc_ctx *ctx, const char *path) {
   if (!ctx) return GMC_EINVAL;
   TrainState *T = ctx->train;
   if (!T) return set_error(ctx, GMC_EINVAL, "gmc_train_commit: call gmc_train_begin first");
+  if (ctx->server) return set_error(ctx, GMC_EBUSY, "gmc_train_commit: the server is running");
   cudaSetDevice(ctx->device);
   std::vector<float> h(P_TOTAL);
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), T->params, P_TOTAL * 4, cudaMemcpyDeviceToHost, ctx->stream));
