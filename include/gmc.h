@@ -268,6 +268,27 @@ gmc_status analog_transmit_rect(gmc_ctx *ctx, int64_t n, const float *xi, const 
                                 const float *c, int mode, uint64_t seed, uint64_t id0,
                                 uint32_t event0, int32_t *status, float *exit, uint32_t *ncoll);
 
+/*
+ * As analog_transmit_rect in x-y geometry (the paper's encoding of a
+ * direction by its projection on the unit disk, section "Network
+ * Architecture and Inputs"; the walk of section "Monte Carlo Method", Eq. 4):
+ * the cell is the cross-section of an infinite prism and directions are 3-D
+ * unit vectors, given and returned by their projection (ux, uy) on the
+ * plane; a flight of 3-D length d moves the particle by d (ux, uy); a
+ * scattering draws the direction isotropically on the sphere (azimuth
+ * 2 pi u2, polar cosine 2 u3 - 1 from the flight's Philox block); s is the
+ * 3-D track length. The out-of-plane component is +-sqrt(1 - ux^2 - uy^2);
+ * its sign does not enter the walk.
+ *  ux_in, uy_in  [n] float: entry direction's projection, ux_in > 0,
+ *                ux_in^2 + uy_in^2 <= 1.
+ *  exit          [4][n] float: p (or -1), projected exit direction ux, uy,
+ *                s. Other arguments as analog_transmit_rect.
+ */
+gmc_status analog_transmit_xy(gmc_ctx *ctx, int64_t n, const float *xi, const float *ux_in,
+                              const float *uy_in, const float *tau_x, const float *tau_y,
+                              const float *c, int mode, uint64_t seed, uint64_t id0,
+                              uint32_t event0, int32_t *status, float *exit, uint32_t *ncoll);
+
 /* ---- transport solve (the four-stage transport algorithm) ----------------- */
 
 /*

@@ -87,6 +87,7 @@ def _load():
         "gmc_transmit_noalloc": [P, i64, P, P, u64, u64, i32, i32, P, P],
         "analog_transmit": [P, i64, P, P, P, P, P, i32, u64, u64, u32, P, P, P],
         "analog_transmit_rect": [P, i64, P, P, P, P, P, P, i32, u64, u64, u32, P, P, P],
+        "analog_transmit_xy": [P, i64, P, P, P, P, P, P, i32, u64, u64, u32, P, P, P],
         "transport_solve": [P, i32, i32, P, P, P, i64, i32, u64, P,
                             ctypes.POINTER(gmc_solve_stats)],
         "transport_solve_wall": [P, i32, i32, P, P, P, i64, i32, u64, P,
@@ -258,6 +259,13 @@ def analog_transmit_rect(ctx, n, xi, cos_in, sin_in, tau_x, tau_y, c, mode, seed
     return ctx.check(lib.analog_transmit_rect(ctx.handle, n, _ptr(xi), _ptr(cos_in), _ptr(sin_in),
                                               _ptr(tau_x), _ptr(tau_y), _ptr(c), mode, seed, id0,
                                               event0, _ptr(status), _ptr(exit), _ptr(ncoll)))
+
+
+def analog_transmit_xy(ctx, n, xi, ux_in, uy_in, tau_x, tau_y, c, mode, seed, id0, event0,
+                       status, exit, ncoll=None):
+    return ctx.check(lib.analog_transmit_xy(ctx.handle, n, _ptr(xi), _ptr(ux_in), _ptr(uy_in),
+                                            _ptr(tau_x), _ptr(tau_y), _ptr(c), mode, seed, id0,
+                                            event0, _ptr(status), _ptr(exit), _ptr(ncoll)))
 
 
 def transport_solve(ctx, nx, ny, tau, c, source, n_histories, method, seed, flux, stats=None):

@@ -530,6 +530,54 @@ gmc_status transmit_net(gmc_ctx *ctx, const NetDev &N, int64_t n, const float *c
 
 }  // namespace gmc
 
+namespace gmc {
+using Walk6Launch = cudaError_t (*)(cudaStream_t, int64_t, const float *, const float *,
+                                    const float *, const float *, const float *, const float *,
+                                    int, uint64_t, uint64_t, uint32_t, int32_t *, float *,
+                                    uint32_t *);
+
+// Marshalling of the batched walks with six per-particle inputs (rectangular
+// cells, x-y geometry): staging, launch, copies back.
+static gmc_status walk6(gmc_ctx *ctx, const char *name, Walk6Launch launch, int64_t n,
+                        const float *const ins[6], int mode, uint64_t seed, uint64_t id0,
+                        uint32_t event0, int32_t *status, float *exit, uint32_t *ncoll) {
+  if (!ctx) return GMC_EINVAL;
+  if (n < 0) return set_error(ctx, GMC_EINVAL, "%s: n < 0", name);
+  if (n == 0) return GMC_OK;
+  for (int k = 0; k < 6; ++k)
+    if (!ins[k]) return set_error(ctx, GMC_EINVAL, "%s: null array", name);
+  if (!status || !exit) return set_error(ctx, GMC_EINVAL, "%s: null array", name);
+  if (mode != GMC_ABSORB_ANALOG && mode != GMC_ABSORB_IMPLICIT)
+    return set_error(ctx, GMC_EINVAL, "%s: unknown mode", name);
+  cudaSetDevice(ctx->device);
+  Arg in[6], o_status, o_exit, o_ncoll;
+  for (int k = 0; k < 6; ++k) {
+    in[k].user = ins[k];
+    in[k].bytes = (size_t)n * 4;
+    GMC_CUDA_TRY(ctx, stage_in(ctx, k, in[k]));
+  }
+  o_status.user = status; o_status.bytes = (size_t)n * 4;
+  o_exit.user = exit; o_exit.bytes = (size_t)n * 16;
+  o_ncoll.user = ncoll; o_ncoll.bytes = (size_t)n * 4;
+  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 6, o_status));
+  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 7, o_exit));
+  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 8, o_ncoll));
+  GMC_CUDA_TRY(ctx, launch(ctx->stream, n, (const float *)in[0].dev, (const float *)in[1].dev,
+                           (const float *)in[2].dev, (const float *)in[3].dev,
+                           (const float *)in[4].dev, (const float *)in[5].dev, mode, seed, id0,
+                           event0, (int32_t *)o_status.dev, (float *)o_exit.dev,
+                           (uint32_t *)o_ncoll.dev));
+  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_status));
+  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_exit));
+  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_ncoll));
+  bool host = o_status.host || o_exit.host || o_ncoll.host || o_status.mapped || o_exit.mapped ||
+              o_ncoll.mapped;
+  for (auto &a : in) host = host || a.host || a.mapped;
+  if (host) GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return GMC_OK;
+}
+}  // namespace gmc
+
 extern "C" {
 
 gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
@@ -592,41 +640,18 @@ gmc_status analog_transmit_rect(gmc_ctx *ctx, int64_t n, const float *xi, const 
                                 const float *sin_in, const float *tau_x, const float *tau_y,
                                 const float *c, int mode, uint64_t seed, uint64_t id0,
                                 uint32_t event0, int32_t *status, float *exit, uint32_t *ncoll) {
-  if (!ctx) return GMC_EINVAL;
-  if (n < 0) return set_error(ctx, GMC_EINVAL, "analog_transmit_rect: n < 0");
-  if (n == 0) return GMC_OK;
-  if (!xi || !cos_in || !sin_in || !tau_x || !tau_y || !c || !status || !exit)
-    return set_error(ctx, GMC_EINVAL, "analog_transmit_rect: null array");
-  if (mode != GMC_ABSORB_ANALOG && mode != GMC_ABSORB_IMPLICIT)
-    return set_error(ctx, GMC_EINVAL, "analog_transmit_rect: unknown mode");
-  cudaSetDevice(ctx->device);
-  Arg in[6], o_status, o_exit, o_ncoll;
-  const float *ins[6] = {xi, cos_in, sin_in, tau_x, tau_y, c};
-  for (int k = 0; k < 6; ++k) {
-    in[k].user = ins[k];
-    in[k].bytes = (size_t)n * 4;
-    GMC_CUDA_TRY(ctx, stage_in(ctx, k, in[k]));
-  }
-  o_status.user = status; o_status.bytes = (size_t)n * 4;
-  o_exit.user = exit; o_exit.bytes = (size_t)n * 16;
-  o_ncoll.user = ncoll; o_ncoll.bytes = (size_t)n * 4;
-  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 6, o_status));
-  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 7, o_exit));
-  GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 8, o_ncoll));
-  GMC_CUDA_TRY(ctx, launch_analog_rect(ctx->stream, n, (const float *)in[0].dev,
-                                       (const float *)in[1].dev, (const float *)in[2].dev,
-                                       (const float *)in[3].dev, (const float *)in[4].dev,
-                                       (const float *)in[5].dev, mode, seed, id0, event0,
-                                       (int32_t *)o_status.dev, (float *)o_exit.dev,
-                                       (uint32_t *)o_ncoll.dev));
-  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_status));
-  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_exit));
-  GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_ncoll));
-  bool host = o_status.host || o_exit.host || o_ncoll.host || o_status.mapped || o_exit.mapped ||
-              o_ncoll.mapped;
-  for (auto &a : in) host = host || a.host || a.mapped;
-  if (host) GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  return GMC_OK;
+  const float *in[6] = {xi, cos_in, sin_in, tau_x, tau_y, c};
+  return walk6(ctx, "analog_transmit_rect", launch_analog_rect, n, in, mode, seed, id0, event0,
+               status, exit, ncoll);
+}
+
+gmc_status analog_transmit_xy(gmc_ctx *ctx, int64_t n, const float *xi, const float *ux_in,
+                              const float *uy_in, const float *tau_x, const float *tau_y,
+                              const float *c, int mode, uint64_t seed, uint64_t id0,
+                              uint32_t event0, int32_t *status, float *exit, uint32_t *ncoll) {
+  const float *in[6] = {xi, ux_in, uy_in, tau_x, tau_y, c};
+  return walk6(ctx, "analog_transmit_xy", launch_analog_xy, n, in, mode, seed, id0, event0,
+               status, exit, ncoll);
 }
 
 }  // extern "C"

@@ -123,6 +123,10 @@ cudaError_t launch_analog_rect(cudaStream_t stream, int64_t n, const float *xi, 
                                const float *sin_in, const float *tx, const float *ty,
                                const float *c, int mode, uint64_t seed, uint64_t id0,
                                uint32_t event0, int32_t *status, float *exit, uint32_t *ncoll);
+cudaError_t launch_analog_xy(cudaStream_t stream, int64_t n, const float *xi, const float *ux_in,
+                             const float *uy_in, const float *tx, const float *ty, const float *c,
+                             int mode, uint64_t seed, uint64_t id0, uint32_t event0,
+                             int32_t *status, float *exit, uint32_t *ncoll);
 
 // BF16 tensor-core GEMM of the training step (train_tc.cu):
 // C[m][n] = epi(sum_k A[m sam + k sak] B[n sbn + k sbk]), FP32 in and out,

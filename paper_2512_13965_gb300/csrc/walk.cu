@@ -68,6 +68,32 @@ __global__ void analog_rect_kernel(int64_t n, const float *__restrict__ xi,
   if (ncoll) ncoll[i] = w.ncoll;
 }
 
+// x-y geometry: entry on the left face at y = xi * ty with the projected
+// direction (ux_in, uy_in); exits report the projected direction.
+__global__ void analog_xy_kernel(int64_t n, const float *__restrict__ xi,
+                                 const float *__restrict__ ux_in, const float *__restrict__ uy_in,
+                                 const float *__restrict__ tx, const float *__restrict__ ty,
+                                 const float *__restrict__ c, int mode, uint64_t seed,
+                                 uint64_t id0, uint32_t event0, int32_t *__restrict__ status,
+                                 float *__restrict__ exitp, uint32_t *__restrict__ ncoll) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int implicit = mode == GMC_ABSORB_IMPLICIT;
+  const float a = tx[i], b = ty[i];
+  const WalkResult w =
+      fmaxf(a, b) > kTau64
+          ? walk_xy<double>((double)a, (double)b, c[i], implicit, 0.0, (double)xi[i] * b,
+                            ux_in[i], uy_in[i], seed, id0 + (uint64_t)i, event0)
+          : walk_xy<float>(a, b, c[i], implicit, 0.0f, xi[i] * b, ux_in[i], uy_in[i], seed,
+                           id0 + (uint64_t)i, event0);
+  status[i] = w.status;
+  exitp[i] = w.status == kExited ? (float)w.face + w.q : -1.0f;
+  exitp[n + i] = w.ux;
+  exitp[2 * n + i] = w.uy;
+  exitp[3 * n + i] = w.s;
+  if (ncoll) ncoll[i] = w.ncoll;
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -105,6 +131,17 @@ cudaError_t launch_analog_rect(cudaStream_t stream, int64_t n, const float *xi, 
   analog_rect_kernel<<<blocks_for(n, 128), 128, 0, stream>>>(n, xi, cos_in, sin_in, tx, ty, c, mode,
                                                               seed, id0, event0, status, exit,
                                                               ncoll);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_analog_xy(cudaStream_t stream, int64_t n, const float *xi, const float *ux_in,
+                             const float *uy_in, const float *tx, const float *ty, const float *c,
+                             int mode, uint64_t seed, uint64_t id0, uint32_t event0,
+                             int32_t *status, float *exit, uint32_t *ncoll) {
+  if (n <= 0) return cudaSuccess;
+  analog_xy_kernel<<<blocks_for(n, 128), 128, 0, stream>>>(n, xi, ux_in, uy_in, tx, ty, c, mode,
+                                                            seed, id0, event0, status, exit,
+                                                            ncoll);
   return cudaGetLastError();
 }
 

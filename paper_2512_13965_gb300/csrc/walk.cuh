@@ -224,6 +224,78 @@ __device__ __forceinline__ WalkResult walk_rect(T tx, T ty, float c, int implici
   return w;
 }
 
+// The walk in x-y geometry (the geometry variant in which the cell is the
+// cross-section of an infinite prism and directions are 3-D): (ux, uy) is
+// the direction's projection on the plane (a point of the unit disk), a
+// flight of 3-D length d moves the position by d (ux, uy), s is the 3-D
+// track length, and a scattering draws the direction isotropically on the
+// sphere, polar cosine 2 u3 - 1 from the flight's fourth uniform and
+// azimuth 2 pi u2. Faces and q as walk_rect.
+template <typename T>
+__device__ __forceinline__ WalkResult walk_xy(T tx, T ty, float c, int implicit, T x, T y,
+                                              float ux, float uy, uint64_t seed, uint64_t id,
+                                              uint32_t event) {
+  const float rate = implicit ? c : 1.0f;
+  const T inf = (T)INFINITY;
+  T s = 0;
+  uint32_t ncoll = 0;
+  WalkResult w;
+  w.status = kTruncated;
+  w.face = -1;
+  w.q = 0.0f;
+  for (uint32_t it = 0; it < kMaxFlights; ++it) {
+    const uint4 r = philox_draw(seed, id, event, kTagWalk);
+    ++event;
+    const T d = rate > 0.0f ? (T)(-logf(u01(r.x)) / rate) : inf;
+    T dbx = inf, dby = inf;
+    if (ux > 0.0f) dbx = (tx - x) / (T)ux;
+    else if (ux < 0.0f) dbx = -x / (T)ux;
+    if (uy > 0.0f) dby = (ty - y) / (T)uy;
+    else if (uy < 0.0f) dby = -y / (T)uy;
+    const bool xface = dbx <= dby;
+    T db = xface ? dbx : dby;
+    if (db < (T)0) db = (T)0;
+    if (d >= db) {
+      s += db;
+      int face;
+      T qn;
+      if (xface) {
+        face = ux > 0.0f ? 1 : 3;
+        const T along = y + db * (T)uy;
+        qn = face == 1 ? along / ty : (ty - along) / ty;
+      } else {
+        face = uy > 0.0f ? 2 : 0;
+        const T along = x + db * (T)ux;
+        qn = face == 0 ? along / tx : (tx - along) / tx;
+      }
+      w.status = kExited;
+      w.face = face;
+      w.q = fminf(fmaxf((float)qn, 0.0f), 1.0f);
+      break;
+    }
+    s += d;
+    x += d * (T)ux;
+    y += d * (T)uy;
+    ++ncoll;
+    if (!implicit && u01(r.y) > c) {
+      w.status = kAbsorbed;
+      break;
+    }
+    float sp, cp;
+    sincospif(2.0f * u01(r.z), &sp, &cp);
+    const float mu = 2.0f * u01(r.w) - 1.0f;
+    const float rr = sqrtf(fmaxf(1.0f - mu * mu, 0.0f));
+    ux = rr * cp;
+    uy = rr * sp;
+  }
+  w.ux = ux;
+  w.uy = uy;
+  w.s = (float)s;
+  w.ncoll = ncoll;
+  w.event = event;
+  return w;
+}
+
 // Walk from a point given in normalized cell coordinates (X, Y in [0,1]),
 // picking the position precision from the cell's optical size.
 __device__ __forceinline__ WalkResult walk_cell(float tau, float c, int implicit, float X, float Y,
