@@ -176,7 +176,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--workload", default="sampler",
-                    choices=["sampler", "solve", "hohlraum", "serve", "sweep", "heldout", "sigma"])
+                    choices=["sampler", "solve", "hohlraum", "serve", "sweep", "heldout", "sigma",
+                             "walks"])
     ap.add_argument("--weights", default=None, help="GMCW file (default: Kaiming seed 1)")
     ap.add_argument("--internal-weights", default=None,
                     help="GMCW file of the internal-source model (solve/serve: births sampled by it)")
@@ -199,6 +200,8 @@ def main():
         return run_sweep(args)
     if args.workload == "heldout":
         return run_heldout(args)
+    if args.workload == "walks":
+        return run_walks(args)
 
     import numpy as np
     import torch
@@ -512,6 +515,66 @@ def run_sigma(args):
                       "weights": args.weights or "kaiming seed 1 (untrained)",
                       "births": ("internal model " + args.internal_weights) if args.internal_weights
                       else "random walk", "results": out}))
+    ctx.close()
+
+
+def run_walks(args):
+    """The random walk in its three cell geometries on one batch: 2^22 entries
+    with the sampler workload's (tau, c) law (tau logU[0.1, 1000], c U[0.5,
+    0.999]), implicit capture; square cells (analog_transmit), rectangles of
+    sides (tau, tau / 2) (analog_transmit_rect) and x-y geometry with 3-D
+    directions in square prisms (analog_transmit_xy, 3-D cosine-law entries).
+    Cell transmissions/s and flights/s, median of --steps timed launches after
+    --warmup, L2 flushed (256 MiB write) before each."""
+    import numpy as np
+    import torch
+    import synth
+    g, ctx = _context(args)
+    n = 1 << 22
+    tau, c = synth.materials(n, 21)
+    e2 = synth.cell_entries(n, 22)
+    e3 = synth.cell_entries_xy(n, 23)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    tau_d, half_d, c_d = d(tau), d(tau * 0.5), d(c)
+    xi2, cs2, sn2 = d(e2["xi"]), d(e2["cos"]), d(e2["sin"])
+    xi3, ux3, uy3 = d(e3["xi"]), d(e3["ux"]), d(e3["uy"])
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    ex = torch.empty(4, n, device="cuda")
+    nc = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    imp = g.GMC_ABSORB_IMPLICIT
+    calls = {
+        "square": lambda s: g.analog_transmit(ctx, n, xi2, cs2, sn2, tau_d, c_d, imp, s, 0, 0, st,
+                                              ex, nc),
+        "rect_2to1": lambda s: g.analog_transmit_rect(ctx, n, xi2, cs2, sn2, tau_d, half_d, c_d,
+                                                      imp, s, 0, 0, st, ex, nc),
+        "xy_3d_square_prism": lambda s: g.analog_transmit_xy(ctx, n, xi3, ux3, uy3, tau_d, tau_d,
+                                                             c_d, imp, s, 0, 0, st, ex, nc),
+    }
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, call in calls.items():
+        times = []
+        for k in range(args.warmup + args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            call(100 + k)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(t0.elapsed_time(t1))
+        ms = statistics.median(times)
+        flights = float(nc.double().sum().item())
+        out[name] = {"ms": ms, "transmissions_per_s": n / (ms * 1e-3),
+                     "flights_per_s": flights / (ms * 1e-3), "mean_flights": flights / n,
+                     "mean_s": float(ex[3].double().mean().item())}
+    print(json.dumps({"metric": "cell transmissions/s of the random walk", "unit": "cell transmissions/s",
+                      "workload": "2^22 entries, tau logU[0.1,1000], c U[0.5,0.999], implicit capture",
+                      "steps": args.steps, "warmup": args.warmup, "l2": "flushed (256 MiB write)",
+                      "results": out}))
     ctx.close()
 
 
