@@ -191,6 +191,63 @@ def walk_sampler(seed):
     return f
 
 
+def equivalent_condition(tau, c, tau_range=(0.1, 1000.0), c_range=(0.5, 0.999)):
+    """Scattering-equivalent condition of cells (tau, c) inside a network's
+    training box [tau_lo, tau_hi] x [c_lo, c_hi].
+
+    The implicit-capture walk (MC section, Eq. 4; absorption applied
+    afterwards as exp(-(1 - c) s), Eq. 5) draws flights at rate c in a cell of
+    side tau, which is the walk at rate 1 in a cell of side c tau with every
+    length divided by c: exits depend on the scattering thickness c tau only,
+    and track lengths scale as 1 / c. A cell (tau', c') with c' tau' = c tau
+    therefore has the same exit law, and s = s' c' / c. c' is c moved into
+    [c_lo, c_hi] and [c tau / tau_hi, c tau / tau_lo]; cells inside the box
+    keep (tau, c). Returns (tau', c', ok); ok is False where no equivalent
+    exists (c tau outside [c_lo tau_lo, c_hi tau_hi], c = 0 included), and
+    those cells keep (tau, c)."""
+    tau = np.asarray(tau, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
+    (t_lo, t_hi), (c_lo, c_hi) = tau_range, c_range
+    w = c * tau
+    lo = np.maximum(c_lo, w / t_hi)
+    hi = np.minimum(c_hi, w / t_lo)
+    ok = (w > 0.0) & (lo <= hi)
+    inside = (tau >= t_lo) & (tau <= t_hi) & (c >= c_lo) & (c <= c_hi)
+    ok = ok | inside
+    cp = np.where(inside, c, np.where(ok, np.clip(c, lo, np.maximum(lo, hi)), c))
+    tp = np.where(inside | ~ok, tau, np.clip(w / np.where(ok, cp, 1.0), t_lo, t_hi))
+    return tp, cp, ok
+
+
+def equivalent_sampler(sampler, fallback, tau_range=(0.1, 1000.0), c_range=(0.5, 0.999)):
+    """Stage 2 for grids whose cells leave the network's training box: each
+    particle is sampled by `sampler` at its cell's scattering-equivalent
+    condition (equivalent_condition) and its track length scaled by c' / c;
+    particles in cells without an equivalent go to `fallback` (the random
+    walk) at their own (tau, c). Inside the box this is `sampler` itself."""
+    def f(xi, cos_c, sin_c, tau, c, ids, events, rot=None):
+        xi, cos_c, sin_c, tau, c = (np.asarray(a, dtype=np.float64)
+                                    for a in (xi, cos_c, sin_c, tau, c))
+        ids = np.asarray(ids, dtype=np.uint64)
+        events = np.asarray(events, dtype=np.uint32)
+        tp, cp, ok = equivalent_condition(tau, c, tau_range, c_range)
+        n = xi.shape[0]
+        face = np.zeros(n, np.int64)
+        q, ux, uy, s = (np.zeros(n) for _ in range(4))
+        ev = np.zeros(n, np.uint32)
+        for sel, fn, tt, cc in ((ok, sampler, tp, cp), (~ok, fallback, tau, c)):
+            k = np.nonzero(sel)[0]
+            if k.size == 0:
+                continue
+            r = None if rot is None else np.asarray(rot)[k]
+            fa, qa, uxa, uya, sa, eva = fn(xi[k], cos_c[k], sin_c[k], tt[k], cc[k], ids[k],
+                                           events[k], rot=r)
+            face[k], q[k], ux[k], uy[k], ev[k] = fa, qa, uxa, uya, eva
+            s[k] = np.asarray(sa) * (cc[k] / c[k]) if fn is sampler else sa
+        return face, q, ux, uy, s, ev
+    return f
+
+
 def internal_condition(X, Y, tau, c):
     """Condition of the internal model for births at (X, Y) in [0,1]^2 of a cell:
     (X, Y, ln tau, c, distance to the nearest face in cell units) -> [5, B]."""

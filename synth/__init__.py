@@ -19,7 +19,10 @@ input is drawn from the distributions the workload names):
     N(0, 2 / fan_in), zero biases, identity standardization;
   * grid: n x n cells, tau log-uniform in [0.1, 500], c drawn from
     {0.5, 0.999} per 16 x 16 block, unit source spread over the central 8 x 8
-    cells.
+    cells;
+  * the paper's two benchmarks with their printed cross sections (lattice
+    and linearized hohlraum, 112 x 112 meshes); their layouts are only in
+    figures that are not available, so the arrangements are stand-ins.
 """
 import struct
 
@@ -164,3 +167,62 @@ def hohlraum_problem(n=64):
     wall[lo:hi] = 1.0
     return tau, c, wall
 
+
+
+# Cross sections (sigma_a, sigma_s) in cm^-1 of the paper's benchmarks
+# (section "Benchmark Performance"). Each cell of side h gets tau = sigma_t h
+# and c = sigma_s / sigma_t.
+LATTICE_XS = {"background": (0.0, 1.0), "absorber": (9.5, 0.5)}
+PAPER_HOHLRAUM_XS = {"wall": (50.0, 50.0), "stripe": (5.0, 95.0), "frame": (10.0, 90.0),
+                     "absorber": (95.0, 5.0), "vacuum": (0.0, 5.0)}
+
+
+def _optical(xs, mat, h):
+    sa = np.vectorize(lambda m: xs[m][0])(mat)
+    ss = np.vectorize(lambda m: xs[m][1])(mat)
+    st = sa + ss
+    return (st * h).astype(np.float32), (ss / st).astype(np.float32)
+
+
+def paper_lattice_problem(n=112):
+    """The lattice benchmark's materials on a 7 x 7 cm square, n x n cells
+    (n a multiple of 7): scattering background, absorbers (LATTICE_XS) and an
+    isotropic volumetric source in the central 1 x 1 cm square. The absorber
+    arrangement (a periodic array in the paper, whose figure is not
+    available) is a stand-in: the 1 x 1 cm squares (a, b) of the inner 5 x 5
+    with a + b even, the source square (3, 3) excepted. Returns tau, c, src
+    [n, n] (float32, row = y index; src sums to 1)."""
+    if n % 7:
+        raise ValueError("n must be a multiple of 7")
+    u = n // 7
+    a = np.arange(n) // u
+    A, B = np.meshgrid(a, a)  # A: x square, B: y square
+    mat = np.full((n, n), "background", dtype=object)
+    inner = (A >= 1) & (A <= 5) & (B >= 1) & (B <= 5)
+    mat[inner & ((A + B) % 2 == 0) & ~((A == 3) & (B == 3))] = "absorber"
+    tau, c = _optical(LATTICE_XS, mat, 7.0 / n)
+    src = ((A == 3) & (B == 3)).astype(np.float64)
+    return tau, c, (src / src.sum()).astype(np.float32)
+
+
+def paper_hohlraum_problem(n=112):
+    """The linearized hohlraum's materials on a 1.3 x 1.3 cm square, n x n
+    cells (PAPER_HOHLRAUM_XS), driven by an isotropic surface source over the
+    whole left boundary. The arrangement (in a figure that is not available)
+    is a stand-in, mirror-symmetric about y = 0.65 cm: absorbing walls along
+    the top, bottom and right (0.1 cm thick); stripes covering the left
+    boundary outside the entrance 0.4 < y < 0.9 cm (0.1 cm thick); a square
+    absorber of half-width 0.2 cm at the centre inside a frame 0.1 cm wide;
+    near-vacuum elsewhere. Returns tau, c [n, n] (float32, row = y index)
+    and the left-boundary strengths wall [n]."""
+    h = 1.3 / n
+    x = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(x, x)
+    mat = np.full((n, n), "vacuum", dtype=object)
+    d = np.maximum(np.abs(X - 0.65), np.abs(Y - 0.65))
+    mat[d < 0.3] = "frame"
+    mat[d < 0.2] = "absorber"
+    mat[(X < 0.1) & ((Y < 0.4) | (Y > 0.9))] = "stripe"
+    mat[(X > 1.2) | (Y < 0.1) | (Y > 1.2)] = "wall"
+    tau, c = _optical(PAPER_HOHLRAUM_XS, mat, h)
+    return tau, c, np.ones(n, dtype=np.float32)
