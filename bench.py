@@ -177,7 +177,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--workload", default="sampler",
                     choices=["sampler", "solve", "hohlraum", "serve", "sweep", "heldout", "sigma",
-                             "walks"])
+                             "walks", "paper"])
     ap.add_argument("--weights", default=None, help="GMCW file (default: Kaiming seed 1)")
     ap.add_argument("--internal-weights", default=None,
                     help="GMCW file of the internal-source model (solve/serve: births sampled by it)")
@@ -202,6 +202,8 @@ def main():
         return run_heldout(args)
     if args.workload == "walks":
         return run_walks(args)
+    if args.workload == "paper":
+        return run_paper(args)
 
     import numpy as np
     import torch
@@ -515,6 +517,40 @@ def run_sigma(args):
                       "weights": args.weights or "kaiming seed 1 (untrained)",
                       "births": ("internal model " + args.internal_weights) if args.internal_weights
                       else "random walk", "results": out}))
+    ctx.close()
+
+
+def run_paper(args):
+    """Random-walk solves of the paper's two benchmark problems with their
+    printed cross sections (stand-in layouts): the lattice (112 x 112 cells,
+    central volumetric source) and the linearized hohlraum (112 x 112 cells,
+    surface source on the left boundary). --histories per solve, two seeds
+    each: solve time, transmissions/s and the run-to-run flux difference
+    ||phi_1 - phi_2|| / ||phi_1|| (the statistical floor of the flux error)."""
+    import numpy as np
+    import synth
+    g, ctx = _context(args)
+    n_hist = int(args.histories)
+    problems = {"lattice": (synth.paper_lattice_problem(112), g.transport_solve),
+                "hohlraum": (synth.paper_hohlraum_problem(112), g.transport_solve_wall)}
+    out = {}
+    for name, ((tau, c, src), solve) in problems.items():
+        tau, c, src = (np.ascontiguousarray(a.ravel()) for a in (tau, c, src))
+        fl, secs, trans = [], [], []
+        for seed in (11, 12):
+            f = np.zeros(112 * 112)
+            st = solve(ctx, 112, 112, tau, c, src, n_hist, g.GMC_METHOD_ANALOG, seed, f)
+            fl.append(f)
+            secs.append(st.seconds)
+            trans.append(st.transmissions)
+        floor = float(np.linalg.norm(fl[0] - fl[1]) / np.linalg.norm(fl[0]))
+        out[name] = {"method": "analog", "histories": n_hist, "seconds": secs,
+                     "transmissions": trans,
+                     "transmissions_per_s": float(np.mean(trans) / np.mean(secs)),
+                     "flux_floor": floor}
+    print(json.dumps({"metric": "random-walk solves of the paper's benchmark problems",
+                      "workload": "lattice and linearized hohlraum, 112x112 cells, printed cross "
+                                  "sections, stand-in layouts", "results": out}))
     ctx.close()
 
 
