@@ -129,6 +129,29 @@ def status_name(s):
     return lib.gmc_status_str(int(s)).decode()
 
 
+def _arr(x, itemsize, count, name):
+    """_ptr after checking what the call will touch: `count` elements of
+    `itemsize` bytes (the header's layout for that argument). A mismatch
+    raises GMCError(GMC_EINVAL) before anything runs: the library itself
+    cannot see a buffer's size, and a short or wider-typed buffer would be
+    read or written past its end. None and raw integer addresses pass as
+    they are (the library rejects a null array it needs)."""
+    if x is None or isinstance(x, int):
+        return _ptr(x)
+    if hasattr(x, "data_ptr"):
+        size, have = x.element_size(), x.numel()
+    elif isinstance(x, np.ndarray):
+        size, have = x.itemsize, x.size
+    else:
+        return _ptr(x)
+    if size != itemsize:
+        raise GMCError(GMC_EINVAL, "%s: elements of %d bytes expected, got %d"
+                       % (name, itemsize, size))
+    if count > 0 and have < count:
+        raise GMCError(GMC_EINVAL, "%s: %d elements needed, buffer has %d" % (name, count, have))
+    return _ptr(x)
+
+
 def _ptr(x):
     if x is None:
         return None
@@ -154,6 +177,7 @@ class Context:
         if s != GMC_OK:
             raise GMCError(s, "gmc_create(device=%d) failed" % device)
         self.handle = h
+        self.cells = {}  # grid size of each queued serving ticket
 
     def check(self, s):
         if s != GMC_OK:
@@ -174,6 +198,26 @@ class Context:
     @property
     def _as_parameter_(self):
         return self.handle
+
+
+def _sampler_args(n, cond, noise):
+    return _arr(cond, 4, 5 * n, "cond"), _arr(noise, 4, 4 * n, "noise")
+
+
+def _sampler_out(n, y_raw, exit):
+    return _arr(y_raw, 4, 4 * n, "y_raw"), _arr(exit, 4, 4 * n, "exit")
+
+
+def _walk_in(n, **arrays):
+    return [_arr(v, 4, n, k) for k, v in arrays.items()]
+
+
+def _walk_out(n, status, exit, ncoll):
+    return _arr(status, 4, n, "status"), _arr(exit, 4, 4 * n, "exit"), _arr(ncoll, 4, n, "ncoll")
+
+
+def _grid(m, tau, c):
+    return _arr(tau, 4, m, "tau"), _arr(c, 4, m, "c")
 
 
 def gmc_create(device=0):
@@ -205,11 +249,13 @@ def gmc_set_config(ctx, cfg):
 
 
 def gmc_philox(ctx, n, seed, id0, event, tag, out):
-    return ctx.check(lib.gmc_philox(ctx.handle, n, seed, id0, event, tag, _ptr(out)))
+    return ctx.check(lib.gmc_philox(ctx.handle, n, seed, id0, event, tag,
+                                    _arr(out, 4, 4 * n, "out")))
 
 
 def gmc_normals(ctx, n, seed, id0, event, tag, out):
-    return ctx.check(lib.gmc_normals(ctx.handle, n, seed, id0, event, tag, _ptr(out)))
+    return ctx.check(lib.gmc_normals(ctx.handle, n, seed, id0, event, tag,
+                                     _arr(out, 4, 4 * n, "out")))
 
 
 def gmc_load_weights(ctx, path):
@@ -232,72 +278,80 @@ def gmc_load_internal_weights_buffer(ctx, blob):
 
 
 def gmc_sample_internal(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw, exit):
-    return ctx.check(lib.gmc_sample_internal(ctx.handle, n, _ptr(cond), _ptr(noise), seed, id0,
-                                             steps, integrator, precision, _ptr(y_raw),
-                                             _ptr(exit)))
+    return ctx.check(lib.gmc_sample_internal(ctx.handle, n, *_sampler_args(n, cond, noise),
+                                             seed, id0, steps, integrator, precision,
+                                             *_sampler_out(n, y_raw, exit)))
 
 
 def gmc_transmit(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw, exit):
-    return ctx.check(lib.gmc_transmit(ctx.handle, n, _ptr(cond), _ptr(noise), seed, id0, steps,
-                                      integrator, precision, _ptr(y_raw), _ptr(exit)))
+    return ctx.check(lib.gmc_transmit(ctx.handle, n, *_sampler_args(n, cond, noise), seed, id0,
+                                      steps, integrator, precision,
+                                      *_sampler_out(n, y_raw, exit)))
 
 
 def gmc_transmit_noalloc(ctx, n, cond, noise, seed, id0, steps, integrator, y_raw, exit):
-    return ctx.check(lib.gmc_transmit_noalloc(ctx.handle, n, _ptr(cond), _ptr(noise), seed, id0,
-                                              steps, integrator, _ptr(y_raw), _ptr(exit)))
+    return ctx.check(lib.gmc_transmit_noalloc(ctx.handle, n, *_sampler_args(n, cond, noise),
+                                              seed, id0, steps, integrator,
+                                              *_sampler_out(n, y_raw, exit)))
 
 
 def analog_transmit(ctx, n, xi, cos_in, sin_in, tau, c, mode, seed, id0, event0, status, exit,
                     ncoll=None):
-    return ctx.check(lib.analog_transmit(ctx.handle, n, _ptr(xi), _ptr(cos_in), _ptr(sin_in),
-                                         _ptr(tau), _ptr(c), mode, seed, id0, event0,
-                                         _ptr(status), _ptr(exit), _ptr(ncoll)))
+    ins = _walk_in(n, xi=xi, cos_in=cos_in, sin_in=sin_in, tau=tau, c=c)
+    return ctx.check(lib.analog_transmit(ctx.handle, n, *ins, mode, seed, id0, event0,
+                                         *_walk_out(n, status, exit, ncoll)))
 
 
 def analog_transmit_rect(ctx, n, xi, cos_in, sin_in, tau_x, tau_y, c, mode, seed, id0, event0,
                          status, exit, ncoll=None):
-    return ctx.check(lib.analog_transmit_rect(ctx.handle, n, _ptr(xi), _ptr(cos_in), _ptr(sin_in),
-                                              _ptr(tau_x), _ptr(tau_y), _ptr(c), mode, seed, id0,
-                                              event0, _ptr(status), _ptr(exit), _ptr(ncoll)))
+    ins = _walk_in(n, xi=xi, cos_in=cos_in, sin_in=sin_in, tau_x=tau_x, tau_y=tau_y, c=c)
+    return ctx.check(lib.analog_transmit_rect(ctx.handle, n, *ins, mode, seed, id0, event0,
+                                              *_walk_out(n, status, exit, ncoll)))
 
 
 def analog_transmit_xy(ctx, n, xi, ux_in, uy_in, tau_x, tau_y, c, mode, seed, id0, event0,
                        status, exit, ncoll=None):
-    return ctx.check(lib.analog_transmit_xy(ctx.handle, n, _ptr(xi), _ptr(ux_in), _ptr(uy_in),
-                                            _ptr(tau_x), _ptr(tau_y), _ptr(c), mode, seed, id0,
-                                            event0, _ptr(status), _ptr(exit), _ptr(ncoll)))
+    ins = _walk_in(n, xi=xi, ux_in=ux_in, uy_in=uy_in, tau_x=tau_x, tau_y=tau_y, c=c)
+    return ctx.check(lib.analog_transmit_xy(ctx.handle, n, *ins, mode, seed, id0, event0,
+                                            *_walk_out(n, status, exit, ncoll)))
 
 
 def transport_solve(ctx, nx, ny, tau, c, source, n_histories, method, seed, flux, stats=None):
     st = stats if stats is not None else gmc_solve_stats()
-    ctx.check(lib.transport_solve(ctx.handle, nx, ny, _ptr(tau), _ptr(c), _ptr(source),
-                                  n_histories, method, seed, _ptr(flux), ctypes.byref(st)))
+    m = max(nx, 0) * max(ny, 0)
+    ctx.check(lib.transport_solve(ctx.handle, nx, ny, *_grid(m, tau, c), _arr(source, 4, m, "source"),
+                                  n_histories, method, seed, _arr(flux, 8, m, "flux"),
+                                  ctypes.byref(st)))
     return st
 
 
 def transport_solve_wall(ctx, nx, ny, tau, c, wall, n_histories, method, seed, flux, stats=None):
     st = stats if stats is not None else gmc_solve_stats()
-    ctx.check(lib.transport_solve_wall(ctx.handle, nx, ny, _ptr(tau), _ptr(c), _ptr(wall),
-                                       n_histories, method, seed, _ptr(flux), ctypes.byref(st)))
+    m = max(nx, 0) * max(ny, 0)
+    ctx.check(lib.transport_solve_wall(ctx.handle, nx, ny, *_grid(m, tau, c),
+                                       _arr(wall, 4, max(ny, 0), "wall"), n_histories, method,
+                                       seed, _arr(flux, 8, m, "flux"), ctypes.byref(st)))
     return st
 
 
 def gmc_train_data(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
     return ctx.check(lib.gmc_train_data(ctx.handle, n, seed, tau_lo, tau_hi, c_lo, c_hi,
-                                        _ptr(cond), _ptr(y)))
+                                        _arr(cond, 4, 5 * n, "cond"), _arr(y, 4, 4 * n, "y")))
 
 
 def gmc_train_data_internal(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
     return ctx.check(lib.gmc_train_data_internal(ctx.handle, n, seed, tau_lo, tau_hi, c_lo, c_hi,
-                                                 _ptr(cond), _ptr(y)))
+                                                 _arr(cond, 4, 5 * n, "cond"),
+                                                 _arr(y, 4, 4 * n, "y")))
 
 
 def gmc_train_begin(ctx, n, cond, y, cfg):
-    return ctx.check(lib.gmc_train_begin(ctx.handle, n, _ptr(cond), _ptr(y), ctypes.byref(cfg)))
+    return ctx.check(lib.gmc_train_begin(ctx.handle, n, _arr(cond, 4, 5 * n, "cond"),
+                                         _arr(y, 4, 4 * n, "y"), ctypes.byref(cfg)))
 
 
 def gmc_train_steps(ctx, n_steps, losses=None):
-    return ctx.check(lib.gmc_train_steps(ctx.handle, n_steps, _ptr(losses)))
+    return ctx.check(lib.gmc_train_steps(ctx.handle, n_steps, _arr(losses, 4, n_steps, "losses")))
 
 
 def gmc_train_set_lr(ctx, lr):
@@ -306,13 +360,16 @@ def gmc_train_set_lr(ctx, lr):
 
 def gmc_train_grad(ctx, B, cn, x1, x0, t, grad):
     loss = ctypes.c_double()
-    ctx.check(lib.gmc_train_grad(ctx.handle, B, _ptr(cn), _ptr(x1), _ptr(x0), _ptr(t),
-                                 ctypes.byref(loss), _ptr(grad)))
+    P = gmc_train_param_count()
+    ctx.check(lib.gmc_train_grad(ctx.handle, B, _arr(cn, 4, 5 * B, "cn"), _arr(x1, 4, 4 * B, "x1"),
+                                 _arr(x0, 4, 4 * B, "x0"), _arr(t, 4, B, "t"),
+                                 ctypes.byref(loss), _arr(grad, 4, P, "grad")))
     return loss.value
 
 
 def gmc_train_params(ctx, out):
-    return ctx.check(lib.gmc_train_params(ctx.handle, _ptr(out)))
+    return ctx.check(lib.gmc_train_params(ctx.handle,
+                                          _arr(out, 4, gmc_train_param_count(), "out")))
 
 
 def gmc_train_param_count():
@@ -330,26 +387,33 @@ def gmc_serve_start(ctx, method, memory_budget):
 
 def gmc_submit(ctx, nx, ny, tau, c, source, n_histories, seed):
     """tau, c, source: host float32 arrays of ny*nx cells; returns the ticket."""
-    req = gmc_solve_req(nx=nx, ny=ny, tau=_ptr(tau), c=_ptr(c), source=_ptr(source),
+    m = max(nx, 0) * max(ny, 0)
+    gt, gc = _grid(m, tau, c)
+    req = gmc_solve_req(nx=nx, ny=ny, tau=gt, c=gc, source=_arr(source, 4, m, "source"),
                         n_histories=n_histories, seed=seed)
     t = ctypes.c_uint64()
     ctx.check(lib.gmc_submit(ctx.handle, ctypes.byref(req), ctypes.byref(t)))
+    ctx.cells[t.value] = m
     return t.value
 
 
 def gmc_poll(ctx, ticket, flux):
     """Returns stats when done, None while the request runs."""
     st = gmc_solve_stats()
-    s = lib.gmc_poll(ctx.handle, ticket, _ptr(flux), ctypes.byref(st))
+    s = lib.gmc_poll(ctx.handle, ticket, _arr(flux, 8, ctx.cells.get(ticket, 0), "flux"),
+                     ctypes.byref(st))
     if s == GMC_EBUSY:
         return None
     ctx.check(s)
+    ctx.cells.pop(ticket, None)
     return st
 
 
 def gmc_wait(ctx, ticket, timeout_s, flux):
     st = gmc_solve_stats()
-    ctx.check(lib.gmc_wait(ctx.handle, ticket, timeout_s, _ptr(flux), ctypes.byref(st)))
+    ctx.check(lib.gmc_wait(ctx.handle, ticket, timeout_s,
+                           _arr(flux, 8, ctx.cells.get(ticket, 0), "flux"), ctypes.byref(st)))
+    ctx.cells.pop(ticket, None)
     return st
 
 

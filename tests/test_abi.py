@@ -50,3 +50,33 @@ def test_status_strings_and_null_handling(libgmc):
     assert _abi.lib.gmc_destroy(None) == 0
     assert _abi.lib.gmc_synchronize(None) == _abi.GMC_EINVAL
     assert _abi.lib.gmc_transmit(None, 1, None, None, 0, 0, 1, 0, 0, None, None) == _abi.GMC_EINVAL
+
+
+def test_binding_checks_buffer_sizes_and_types(libgmc):
+    # The binding checks every array against the layout the call touches
+    # before the library runs; nothing here reaches a GPU.
+    import numpy as np
+    import torch
+    from paper_2512_13965_gb300 import _abi
+    n = 10
+    ok = np.zeros((4, n), np.float32)
+    assert _abi._arr(ok, 4, 4 * n, "exit") == ok.ctypes.data
+    assert _abi._arr(None, 4, 4 * n, "exit") is None
+    assert _abi._arr(torch.zeros(5, n), 4, 5 * n, "cond") is not None
+    for bad, why in ((np.zeros((4, n), np.float64), "bytes"), (np.zeros((3, n), np.float32), "needed"),
+                     (torch.zeros(4, n, dtype=torch.float16), "bytes")):
+        with pytest.raises(_abi.GMCError) as e:
+            _abi._arr(bad, 4, 4 * n, "exit")
+        assert e.value.status == _abi.GMC_EINVAL and why in str(e.value)
+    # the wrappers apply it: a float64 grid is refused before any call is made
+    ctx = object.__new__(_abi.Context)
+    ctx.handle, ctx.cells = None, {}
+    with pytest.raises(_abi.GMCError) as e:
+        _abi.transport_solve(ctx, 4, 4, np.ones(16), np.ones(16, np.float32),
+                             np.ones(16, np.float32), 10, 0, 1, np.zeros(16))
+    assert "tau" in str(e.value)
+    with pytest.raises(_abi.GMCError) as e:
+        _abi.analog_transmit(ctx, n, *[np.zeros(n, np.float32)] * 5, 0, 0, 0, 0,
+                             np.zeros(n, np.int32), np.zeros((4, n - 1), np.float32))
+    assert "exit" in str(e.value)
+    ctx.handle = None
