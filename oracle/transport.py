@@ -123,6 +123,22 @@ def transmit_xy(xi, ux_in, uy_in, uz_in, tx, ty, c, mode, seed, ids=None, events
     return out
 
 
+def training_pairs_xy(xi, ux_in, uy_in, tau, c, seed, ids=None):
+    """Training pairs of the boundary model in x-y geometry ("Network
+    Architecture and Inputs": pure-scattering walks from the entry face, the
+    direction encoded by its projection on the unit disk): condition
+    (xi, ux_in, uy_in, ln tau, c) [5, n] and target (p, ux, uy, ln s) [4, n]
+    of the implicit-capture 3-D walk, p = face + q. The out-of-plane entry
+    component is sqrt(1 - ux_in^2 - uy_in^2) (its sign does not enter)."""
+    xi, ux_in, uy_in, tau, c = (np.asarray(a, dtype=np.float64)
+                                for a in (xi, ux_in, uy_in, tau, c))
+    uz_in = np.sqrt(np.maximum(1.0 - ux_in * ux_in - uy_in * uy_in, 0.0))
+    r = transmit_xy(xi, ux_in, uy_in, uz_in, tau, tau, c, MODE_IMPLICIT, seed, ids=ids)
+    cond = np.stack([xi, ux_in, uy_in, np.log(tau), c])
+    y = np.stack([r["face"] + r["q"], r["ux"], r["uy"], np.log(r["s"])])
+    return cond, y
+
+
 def walk_one(tau, c, mode, x, y, ux, uy, seed, pid, event0):
     """One random walk from an arbitrary point (cell frame, optical units)."""
     status = ctypes.c_int32()

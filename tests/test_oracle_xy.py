@@ -7,7 +7,8 @@ scattering ratio; a thin slab's uncollided transmission is 2 E3(tau) with mean
 exit cosine E4/E3; the slab's rotation symmetry about its normal makes the
 exit y and z direction components equally distributed (isotropy on the
 sphere); collisions average c times the track length; implicit capture
-depends on (c tx, c ty) only."""
+depends on (c tx, c ty) only; training pairs decode back to the walk's
+exits."""
 import math
 
 import numpy as np
@@ -90,7 +91,7 @@ def test_slab_uncollided_transmission(tx):
 
 
 @pytest.mark.parametrize("tx", [2.0])
-def test_slab_slab_mean_track_and_rotation_symmetry(tx):
+def test_slab_mean_track_and_rotation_symmetry(tx):
     # in a slab the inflow and the walk are symmetric under rotations about
     # the normal (x axis), so the exit y and z components share a law; the
     # mean track is 4 V / S = 2 tx per unit area; collisions average c s
@@ -140,3 +141,26 @@ def test_implicit_law_depends_on_c_times_sides():
     assert np.allclose(0.9 * a["s"], b["s"], rtol=1e-9)
     for k in ("ux", "uy", "uz"):
         assert np.allclose(a[k], b[k], atol=1e-12)
+
+
+def test_training_pairs_round_trip_through_the_disk_decode(tmp_path):
+    # targets encode the walk's exit; decoding them with identity statistics
+    # gives the exit back (face, q, projected direction, s, |uz|)
+    from oracle import mlp
+    n = 20000
+    e = synth.cell_entries_xy(n, 405)
+    tau, c = synth.materials(n, 406)
+    cond, y = T.training_pairs_xy(e["xi"], e["ux"], e["uy"], tau, c, 9)
+    assert cond.shape == (5, n) and y.shape == (4, n)
+    assert np.allclose(cond[3], np.log(tau.astype(np.float64)))
+    r = T.transmit_xy(e["xi"], e["ux"], e["uy"], e["uz"], tau, tau, c, T.MODE_IMPLICIT, 9)
+    p = str(tmp_path / "w.bin")
+    synth.write_weights(p, synth.kaiming_weights(1))
+    net = mlp.read_weights(p)
+    d = mlp.decode_disk(net, y)
+    assert np.array_equal(d["face"], r["face"])
+    assert np.allclose(d["q"], r["q"], atol=1e-12)
+    assert np.allclose(d["ux"], r["ux"], atol=1e-12) and np.allclose(d["uy"], r["uy"], atol=1e-12)
+    assert np.allclose(d["uz"], np.abs(r["uz"]), atol=1e-6)
+    assert np.allclose(d["s"], r["s"], rtol=1e-12)
+    assert not d["inward"].any()
