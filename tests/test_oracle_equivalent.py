@@ -125,11 +125,33 @@ def test_paper_hohlraum_layout():
     n = 112
     tau, c, wall = synth.paper_hohlraum_problem(n)
     h = 1.3 / n
-    cls = {k: (s + a) for k, (a, s) in synth.PAPER_HOHLRAUM_XS.items()}
+    assert len(synth.PAPER_HOHLRAUM_XS) == 5
     for name, (sa, ss) in synth.PAPER_HOHLRAUM_XS.items():
         m = np.isclose(c, ss / (sa + ss))
         assert m.any(), name
         assert np.allclose(tau[m], (sa + ss) * h), name
     assert np.array_equal(c, c[::-1]) and np.array_equal(tau, tau[::-1])
     assert wall.shape == (n,) and (wall == 1.0).all()
-    assert len(cls) == 5
+
+
+def test_generators_carry_the_printed_cross_sections():
+    # tests/golden/paper_benchmark_cross_sections.txt holds the printed values
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_benchmark_cross_sections.txt")
+    rows = []
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            prob, region, sa, ss, side, mesh = line.split()
+            rows.append((prob, region, float(sa), float(ss), float(side), int(mesh)))
+    assert len(rows) == 7
+    tables = {"lattice": synth.LATTICE_XS, "hohlraum": synth.PAPER_HOHLRAUM_XS}
+    gens = {"lattice": synth.paper_lattice_problem, "hohlraum": synth.paper_hohlraum_problem}
+    for prob, region, sa, ss, side, mesh in rows:
+        assert tables[prob][region] == (sa, ss), (prob, region)
+        tau, c = gens[prob](mesh)[:2]
+        st = sa + ss
+        m = np.isclose(tau, st * side / mesh, rtol=1e-6) & np.isclose(c, ss / st, rtol=1e-6)
+        assert m.any(), (prob, region)
+    for prob, table in tables.items():
+        assert set(table) == {r for p, r, *_ in rows if p == prob}
