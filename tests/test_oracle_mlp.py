@@ -289,3 +289,21 @@ def test_quantized_e4m3_single_path(tmp_path):
         x0 = float(z[0, i])
         expect = x0 + _silu(r(_silu(r(_silu(r(_silu(a * x0)))))))
         assert abs(y[0, i] - expect) < 1e-14
+
+
+def test_evaluation_counts_and_times():
+    # the paper's timed solver, RK4 with 12 fixed steps, makes 48 network
+    # evaluations per sample; Euler K and midpoint 2K; every evaluation time
+    # lies in [0, 1] on the step's nodes (t_k, t_k + h/2, t_k + h)
+    for integ, steps, count in (("rk4", 12, 48), ("euler", 16, 16), ("midpoint", 8, 16)):
+        seen = []
+
+        def v(x, t):
+            seen.append(t)
+            return 0.0 * x
+
+        mlp.integrate(v, np.zeros((1, 4)), steps, integ)
+        assert len(seen) == count, integ
+        h = 1.0 / steps
+        nodes = {round(k * h / 2, 12) for k in range(2 * steps + 1)}
+        assert all(0.0 <= t <= 1.0 and round(t, 12) in nodes for t in seen)
