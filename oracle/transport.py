@@ -123,6 +123,20 @@ def transmit_xy(xi, ux_in, uy_in, uz_in, tx, ty, c, mode, seed, ids=None, events
     return out
 
 
+def training_pairs_rect(xi, cos_in, sin_in, tau_x, tau_y, c, seed, ids=None):
+    """Training pairs of a boundary model for rectangular cells (geometry
+    variant with unequal sides): condition (xi, cos, sin, ln tau_x, c,
+    ln(tau_y / tau_x)) [6, n], the aspect ratio as the sixth input, and
+    target (p, cos_out, sin_out, ln s) [4, n] of the implicit-capture walk in
+    the rectangle, p = face + q with q normalized per face."""
+    xi, cos_in, sin_in, tau_x, tau_y, c = (np.asarray(a, dtype=np.float64)
+                                           for a in (xi, cos_in, sin_in, tau_x, tau_y, c))
+    r = transmit_rect(xi, cos_in, sin_in, tau_x, tau_y, c, MODE_IMPLICIT, seed, ids=ids)
+    cond = np.stack([xi, cos_in, sin_in, np.log(tau_x), c, np.log(tau_y / tau_x)])
+    y = np.stack([r["face"] + r["q"], r["ux"], r["uy"], np.log(r["s"])])
+    return cond, y
+
+
 def training_pairs_xy(xi, ux_in, uy_in, tau, c, seed, ids=None):
     """Training pairs of the boundary model in x-y geometry ("Network
     Architecture and Inputs": pure-scattering walks from the entry face, the

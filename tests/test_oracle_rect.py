@@ -1,8 +1,10 @@
 """Pins for the oracle's random walk in rectangular cells (the geometry
 variant with unequal sides): a width tx = height ty reduces it to the square
 walk history by history; the uncollided transmission per face and the mean
-uncollided chord follow by quadrature; outcomes partition; top and bottom are
-mirror images; implicit capture depends on (c tx, c ty) only."""
+uncollided chord follow by quadrature; the mean track over the whole boundary
+is pi A / P; outcomes partition; top and bottom are mirror images; implicit
+capture depends on (c tx, c ty) only; training pairs decode back to the
+walk's exits."""
 import math
 
 import numpy as np
@@ -132,3 +134,28 @@ def test_mean_path_invariance_whole_boundary(c):
     r = T.transmit_rect(xi, cs, sn, w, h, np.full(n, c), T.MODE_IMPLICIT, 7)
     expect = math.pi * tx * ty / (2.0 * (tx + ty))
     assert abs(r["s"].mean() - expect) < 4 * r["s"].std() / math.sqrt(n), (r["s"].mean(), expect)
+
+
+def test_training_pairs_round_trip_through_the_decode(tmp_path):
+    # the aspect ratio is the sixth condition; targets decode back to the
+    # rectangle walk's exits; equal sides give aspect 0 and the square walk
+    from oracle import mlp
+    n = 20000
+    xi, cs, sn = _entries(n, 307)
+    tx, c = synth.materials(n, 308)
+    ty = tx * np.exp(np.random.default_rng(9).uniform(-2.0, 2.0, n))
+    cond, y = T.training_pairs_rect(xi, cs, sn, tx, ty, c, 4)
+    assert cond.shape == (6, n) and y.shape == (4, n)
+    assert np.allclose(np.exp(cond[5]) * np.exp(cond[3]), ty.astype(np.float64), rtol=1e-6)
+    r = T.transmit_rect(xi, cs, sn, tx, ty, c, T.MODE_IMPLICIT, 4)
+    p = str(tmp_path / "w.bin")
+    synth.write_weights(p, synth.kaiming_weights(1))
+    d = mlp.decode(mlp.read_weights(p), y)
+    assert np.array_equal(d["face"], r["face"])
+    assert np.allclose(d["q"], r["q"], atol=1e-12)
+    assert np.allclose(d["ux"], r["ux"], atol=1e-12) and np.allclose(d["uy"], r["uy"], atol=1e-12)
+    assert np.allclose(d["s"], r["s"], rtol=1e-12)
+    c2, y2 = T.training_pairs_rect(xi, cs, sn, tx, tx, c, 4)
+    sq = T.transmit(xi, cs, sn, tx, c, T.MODE_IMPLICIT, 4)
+    assert not c2[5].any()
+    assert np.array_equal(y2[0], sq["face"] + sq["q"]) and np.array_equal(y2[3], np.log(sq["s"]))
