@@ -155,3 +155,23 @@ def test_generators_carry_the_printed_cross_sections():
         assert m.any(), (prob, region)
     for prob, table in tables.items():
         assert set(table) == {r for p, r, *_ in rows if p == prob}
+
+
+def test_network_solve_at_equivalent_conditions_balances_weight(tmp_path):
+    # the network (FP64 oracle, random weights) at equivalent conditions, the
+    # walk where none exists: implicit capture keeps the weight balance exact
+    # (deposited + leaked - roulette changes = histories) and the Eq. 7
+    # tally equals the deposit over sigma_a, whatever the sampler returns
+    from oracle import mlp
+    p = str(tmp_path / "w.bin")
+    synth.write_weights(p, synth.biased_weights(7))
+    net = mlp.read_weights(p)
+    tau, c, src = synth.paper_lattice_problem(7)  # absorbers c tau = 0.5
+    tau[0, :3] = 0.02  # c tau = 0.02: no equivalent, walked
+    n = 200
+    f = T.equivalent_sampler(T.mlp_sampler(net, 2, "euler", 3), T.walk_sampler(3), *BOX)
+    flux, st = T.solve_gmc(tau, c, src, n, 3, f, max_waves=5000)
+    assert abs(st["absorbed"] + st["leak"] - st["roulette_net"] - n) < 1e-8 * n
+    sig_a = (1.0 - c.astype(np.float64)) * tau.astype(np.float64)
+    assert abs(np.sum(flux * sig_a) * n - st["absorbed"]) < 1e-8 * n
+    assert st["transmissions"] > n
