@@ -442,6 +442,22 @@ gmc_status gmc_train_grad(gmc_ctx *ctx, int64_t B, const float *cn, const float 
 /* Copies the FP32 master weights (layout of gmc_train_grad) to host `out`. */
 gmc_status gmc_train_params(gmc_ctx *ctx, float *out);
 int64_t gmc_train_param_count(void);
+/*
+ * Training checkpoint (host memory): the FP32 master weights, AdamW's first
+ * and second moments, the step count, the hyperparameters (learning rate as
+ * last set, betas, eps, weight decay, seed) and the standardization
+ * statistics. gmc_train_state_size gives the size in bytes (a header plus
+ * 3 gmc_train_param_count() floats). gmc_train_save_state writes a
+ * checkpoint into `blob` (exactly that many bytes). gmc_train_load_state
+ * restores one into the training state of gmc_train_begin, which must have
+ * been called on the same dataset with the same batch and precision
+ * (GMC_EINVAL otherwise; GMC_EFORMAT for a blob that is not a checkpoint).
+ * Step k's batch is drawn from Philox at (seed, k), so steps after a restore
+ * continue the saved run exactly.
+ */
+gmc_status gmc_train_state_size(const gmc_ctx *ctx, size_t *bytes);
+gmc_status gmc_train_save_state(gmc_ctx *ctx, void *blob, size_t nbytes);
+gmc_status gmc_train_load_state(gmc_ctx *ctx, const void *blob, size_t nbytes);
 /* Makes the trained network (with its standardization) the sampler's
    network; also writes it as a GMCW file when `path` is not null.
    GMC_EBUSY, with nothing written, while the server runs. */

@@ -107,6 +107,9 @@ def _load():
         "gmc_train_grad": [P, i64, P, P, P, P, P, P],
         "gmc_train_params": [P, P],
         "gmc_train_commit": [P, ctypes.c_char_p],
+        "gmc_train_state_size": [P, ctypes.POINTER(ctypes.c_size_t)],
+        "gmc_train_save_state": [P, P, sz],
+        "gmc_train_load_state": [P, P, sz],
         "gmc_selftest_wait": [P, ctypes.c_double],
     }
     for name, args in sig.items():
@@ -374,6 +377,25 @@ def gmc_train_params(ctx, out):
 
 def gmc_train_param_count():
     return int(lib.gmc_train_param_count())
+
+
+def gmc_train_state_size(ctx):
+    n = ctypes.c_size_t()
+    ctx.check(lib.gmc_train_state_size(ctx.handle, ctypes.byref(n)))
+    return n.value
+
+
+def gmc_train_save_state(ctx):
+    """Returns the training checkpoint as bytes."""
+    n = gmc_train_state_size(ctx)
+    buf = ctypes.create_string_buffer(n)
+    ctx.check(lib.gmc_train_save_state(ctx.handle, ctypes.addressof(buf), n))
+    return buf.raw
+
+
+def gmc_train_load_state(ctx, blob):
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    return ctx.check(lib.gmc_train_load_state(ctx.handle, ctypes.addressof(buf), len(blob)))
 
 
 def gmc_train_commit(ctx, path=None):

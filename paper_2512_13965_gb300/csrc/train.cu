@@ -684,6 +684,97 @@ gmc_status gmc_train_params(gmc_ctx *ctx, float *out) {
   return GMC_OK;
 }
 
+// Training checkpoint: header, then the FP32 master weights, Adam's first
+// and second moments (P floats each). The batch of step k draws its rows from
+// Philox at (seed, k), so restoring these and the step count resumes the run
+// exactly where it stopped.
+struct TrainCkpt {
+  char magic[4];
+  uint32_t version;
+  int64_t params, step, batch;
+  int32_t precision, reserved;
+  double lr, beta1, beta2, eps, weight_decay;
+  uint64_t seed;
+  float stats[18];
+};
+
+gmc_status gmc_train_state_size(const gmc_ctx *ctx, size_t *bytes) {
+  if (!ctx || !bytes) return GMC_EINVAL;
+  *bytes = sizeof(TrainCkpt) + 3 * (size_t)P_TOTAL * sizeof(float);
+  return GMC_OK;
+}
+
+gmc_status gmc_train_save_state(gmc_ctx *ctx, void *blob, size_t nbytes) {
+  if (!ctx) return GMC_EINVAL;
+  TrainState *T = ctx->train;
+  if (!T) return set_error(ctx, GMC_EINVAL, "gmc_train_save_state: call gmc_train_begin first");
+  size_t need = 0;
+  gmc_train_state_size(ctx, &need);
+  if (!blob || nbytes != need)
+    return set_error(ctx, GMC_EINVAL, "gmc_train_save_state: need a host buffer of %zu bytes", need);
+  TrainCkpt h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "GMCT", 4);
+  h.version = 1;
+  h.params = P_TOTAL;
+  h.step = T->step;
+  h.batch = T->cfg.batch;
+  h.precision = T->cfg.precision;
+  h.lr = T->cfg.lr;
+  h.beta1 = T->cfg.beta1;
+  h.beta2 = T->cfg.beta2;
+  h.eps = T->cfg.eps;
+  h.weight_decay = T->cfg.weight_decay;
+  h.seed = T->cfg.seed;
+  std::memcpy(h.stats, T->stats, sizeof(h.stats));
+  unsigned char *out = (unsigned char *)blob;
+  std::memcpy(out, &h, sizeof(h));
+  float *body = (float *)(out + sizeof(h));
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(body, T->params, P_TOTAL * 4, cudaMemcpyDeviceToHost, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(body + P_TOTAL, T->m, P_TOTAL * 4, cudaMemcpyDeviceToHost, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(body + 2 * P_TOTAL, T->v, P_TOTAL * 4, cudaMemcpyDeviceToHost, s));
+  GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return check_device_error(ctx);
+}
+
+gmc_status gmc_train_load_state(gmc_ctx *ctx, const void *blob, size_t nbytes) {
+  if (!ctx) return GMC_EINVAL;
+  TrainState *T = ctx->train;
+  if (!T) return set_error(ctx, GMC_EINVAL, "gmc_train_load_state: call gmc_train_begin first");
+  size_t need = 0;
+  gmc_train_state_size(ctx, &need);
+  if (!blob || nbytes != need)
+    return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: a checkpoint is %zu bytes", need);
+  TrainCkpt h;
+  std::memcpy(&h, blob, sizeof(h));
+  if (std::memcmp(h.magic, "GMCT", 4) != 0 || h.version != 1 || h.params != P_TOTAL)
+    return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: not a version-1 training checkpoint");
+  if (h.batch != T->cfg.batch || h.precision != T->cfg.precision || h.step < 0)
+    return set_error(ctx, GMC_EINVAL,
+                     "gmc_train_load_state: begin training with the checkpoint's batch and precision");
+  for (int k = 0; k < 18; ++k)
+    if (!std::isfinite(h.stats[k]) || (((k >= 5 && k < 10) || k >= 14) && !(h.stats[k] > 0.0f)))
+      return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: bad standardization statistics");
+  const float *body = (const float *)((const unsigned char *)blob + sizeof(h));
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->params, body, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->m, body + P_TOTAL, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->v, body + 2 * P_TOTAL, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  T->step = h.step;
+  T->cfg.lr = h.lr;
+  T->cfg.beta1 = h.beta1;
+  T->cfg.beta2 = h.beta2;
+  T->cfg.eps = h.eps;
+  T->cfg.weight_decay = h.weight_decay;
+  T->cfg.seed = h.seed;
+  std::memcpy(T->stats, h.stats, sizeof(h.stats));
+  return GMC_OK;
+}
+
 gmc_status gmc_train_commit(gmc_ctx *ctx, const char *path) {
   if (!ctx) return GMC_EINVAL;
   TrainState *T = ctx->train;

@@ -1,0 +1,67 @@
+"""Training checkpoint and resume (gmc_train_save_state / gmc_train_load_state):
+a run stopped after k steps, saved, restored into a fresh training state and
+continued ends where the uninterrupted run ends (bit for bit when two
+uninterrupted runs agree bit for bit, else within their spread); malformed
+checkpoints and a mismatched batch are refused."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_resume_continues_the_run(gpu_ctx, kaiming_file):
+    import torch
+    import paper_2512_13965_gb300 as g
+    ctx = g.Context(0)
+    try:
+        g.gmc_load_weights(ctx, kaiming_file)
+        n = 1 << 16
+        cond = torch.empty(5, n, device="cuda")
+        y = torch.empty(4, n, device="cuda")
+        g.gmc_train_data(ctx, n, 3, 0.1, 1000.0, 0.5, 0.999, cond, y)
+        torch.cuda.synchronize()
+        cfg = g.gmc_train_config(batch=1024, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                                 weight_decay=0.01, seed=5)
+        P = g.gmc_train_param_count()
+
+        def run(k1, k2, resume):
+            g.gmc_train_begin(ctx, n, cond, y, cfg)
+            g.gmc_train_steps(ctx, k1)
+            g.gmc_train_set_lr(ctx, 5e-4)
+            if resume:
+                blob = g.gmc_train_save_state(ctx)
+                assert len(blob) == g.gmc_train_state_size(ctx)
+                g.gmc_train_begin(ctx, n, cond, y, cfg)  # step 0, initial weights, lr 1e-3
+                g.gmc_train_load_state(ctx, blob)
+            g.gmc_train_steps(ctx, k2)
+            p = np.zeros(P, np.float32)
+            g.gmc_train_params(ctx, p)
+            return p
+
+        a = run(4, 6, False)
+        a2 = run(4, 6, False)
+        b = run(4, 6, True)
+        spread = float(np.abs(a - a2).max())
+        if spread == 0.0:
+            assert np.array_equal(a, b)
+        else:
+            assert np.abs(b - a).max() <= 10.0 * spread
+        assert np.abs(a - run(0, 0, False)).max() > 1e-4  # the steps moved the weights
+
+        blob = g.gmc_train_save_state(ctx)
+        with pytest.raises(g.GMCError) as e:
+            g.gmc_train_load_state(ctx, blob[:-4])
+        assert e.value.status == g.GMC_EFORMAT
+        bad = bytearray(blob)
+        bad[0:4] = b"XXXX"
+        with pytest.raises(g.GMCError) as e:
+            g.gmc_train_load_state(ctx, bytes(bad))
+        assert e.value.status == g.GMC_EFORMAT
+        other = g.gmc_train_config(batch=512, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                                   weight_decay=0.01, seed=5)
+        g.gmc_train_begin(ctx, n, cond, y, other)
+        with pytest.raises(g.GMCError) as e:
+            g.gmc_train_load_state(ctx, blob)
+        assert e.value.status == g.GMC_EINVAL
+    finally:
+        ctx.close()
