@@ -8,8 +8,57 @@ particle fluxes combine as the history-weighted mean
 The one collective is that final FP64 sum (torch.distributed all_reduce on
 whatever backend the process group uses). Nothing here computes a step of
 the method; the per-replica solve is transport_solve.
+
+Failure detection happens on the host, before the collective: every replica
+publishes its outcome in the process group's key-value store (report), and
+await_replicas waits, with a bound, until every replica has reported. A
+replica that failed, or that left without reporting, raises ReplicaFailure
+on the others instead of leaving them blocked in the all_reduce.
 """
+import datetime
+import time
+
 import numpy as np
+
+
+class ReplicaFailure(RuntimeError):
+    """One or more replicas failed or did not report before the combination."""
+
+    def __init__(self, failed, missing):
+        parts = ["replica %d failed: %s" % (r, m) for r, m in failed]
+        parts += ["replica %d did not report" % r for r in missing]
+        super().__init__("; ".join(parts))
+        self.failed = failed
+        self.missing = missing
+
+
+def _key(rank):
+    return "gmc_replica/%d" % rank
+
+
+def report(store, rank, ok=True, message=""):
+    """Publishes replica `rank`'s outcome (a torch.distributed Store)."""
+    store.set(_key(rank), "ok" if ok else "fail:" + str(message))
+
+
+def await_replicas(store, world, timeout_s):
+    """Waits until all `world` replicas have reported, at most timeout_s
+    seconds in total; raises ReplicaFailure naming the replicas that reported
+    a failure or did not report in time."""
+    deadline = time.monotonic() + float(timeout_s)
+    failed, missing = [], []
+    for r in range(world):
+        left = max(deadline - time.monotonic(), 0.001)
+        try:
+            store.wait([_key(r)], datetime.timedelta(seconds=left))
+        except Exception:  # the store's timeout error
+            missing.append(r)
+            continue
+        v = store.get(_key(r)).decode()
+        if v != "ok":
+            failed.append((r, v[len("fail:"):]))
+    if failed or missing:
+        raise ReplicaFailure(failed, missing)
 
 
 def shard(n_histories, world, rank):

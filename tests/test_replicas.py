@@ -1,8 +1,11 @@
-"""Replica runs over two gloo processes on CPU: sharding and the FP64
-combination of per-replica fluxes (the oracle solve stands in for each
-replica's transport_solve)."""
+"""Replica runs over gloo processes on CPU: sharding, the FP64 combination
+of per-replica fluxes (the oracle solve stands in for each replica's
+transport_solve), and failure detection before the combination (a replica
+that reports a failure, or leaves without reporting, is named on the others,
+which never enter the collective)."""
 import os
 import socket
+import time
 
 import numpy as np
 import pytest
@@ -77,3 +80,76 @@ def test_two_replicas_combine_to_weighted_mean():
     tau, c, src = synth.grid_problem(n=8, seed=3, tau_range=(0.1, 4.0), block=4, source=2)
     single, _ = T.solve_analog(tau, c, src, n0, 11)
     np.testing.assert_array_equal(f0, single)
+
+
+def _worker_failure(rank, world, port, mode, q):
+    # rank 1 fails (reports it) or leaves silently; the others must learn of
+    # it on the host and never enter the collective
+    import datetime
+    import torch.distributed as dist
+    R = _load_replicas()
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0,
+                          timeout=datetime.timedelta(seconds=60))
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=world)
+    if rank == 1:
+        if mode == "raise":
+            try:
+                raise RuntimeError("solver error")
+            except RuntimeError as ex:
+                R.report(store, rank, ok=False, message=str(ex))
+            q.put((rank, "reported", 0.0))
+            return
+        q.put((rank, "left", 0.0))
+        q.close()
+        q.join_thread()  # deliver the message before the abrupt exit
+        os._exit(3)
+    from oracle import transport as T
+    tau, c, src = synth.grid_problem(n=4, seed=3, tau_range=(0.1, 2.0), block=2, source=2)
+    f, _ = T.solve_analog(tau, c, src, 100, R.seed_for(11, rank))
+    R.report(store, rank)
+    t0 = time.monotonic()
+    try:
+        R.await_replicas(store, world, 5.0)
+        R.combine(f, 100)
+        q.put((rank, "combined", time.monotonic() - t0))
+    except R.ReplicaFailure as ex:
+        q.put((rank, "detected: " + str(ex), time.monotonic() - t0))
+
+
+@pytest.mark.parametrize("mode", ["raise", "leave"])
+def test_replica_failure_is_detected_before_the_combination(mode):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = 3
+    procs = [ctx.Process(target=_worker_failure, args=(r, world, port, mode, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {r: (msg, dt) for r, msg, dt in [q.get(timeout=120) for _ in procs]}
+    for p in procs:
+        p.join(timeout=60)
+    assert procs[0].exitcode == 0 and procs[2].exitcode == 0
+    for r in (0, 2):
+        msg, dt = res[r]
+        if mode == "raise":
+            assert msg == "detected: replica 1 failed: solver error", msg
+            assert dt < 5.0
+        else:
+            assert msg == "detected: replica 1 did not report", msg
+            assert 4.0 < dt < 30.0
+
+
+def test_all_replicas_reporting_pass_the_check():
+    import datetime
+    import torch.distributed as dist
+    R = _load_replicas()
+    port = _free_port()
+    store = dist.TCPStore("127.0.0.1", port, 1, True, timeout=datetime.timedelta(seconds=10))
+    for r in range(3):
+        R.report(store, r)
+    R.await_replicas(store, 3, 1.0)
+    R.report(store, 1, ok=False, message="x")
+    with pytest.raises(R.ReplicaFailure) as e:
+        R.await_replicas(store, 3, 1.0)
+    assert e.value.failed == [(1, "x")] and e.value.missing == []
