@@ -13,7 +13,11 @@ Failure detection happens on the host, before the collective: every replica
 publishes its outcome in the process group's key-value store (report), and
 await_replicas waits, with a bound, until every replica has reported. A
 replica that failed, or that left without reporting, raises ReplicaFailure
-on the others instead of leaving them blocked in the all_reduce.
+on the others instead of leaving them blocked in the all_reduce. Outcomes
+are keyed by a solve id that every replica of one solve passes alike (a
+counter of the solves the group has run, say), so an outcome left in the
+store by an earlier solve never stands in for the current one; `forget`
+removes one solve's keys once it is combined.
 """
 import datetime
 import time
@@ -32,33 +36,44 @@ class ReplicaFailure(RuntimeError):
         self.missing = missing
 
 
-def _key(rank):
-    return "gmc_replica/%d" % rank
+def _key(solve_id, rank):
+    return "gmc_replica/%s/%d" % (solve_id, rank)
 
 
-def report(store, rank, ok=True, message=""):
-    """Publishes replica `rank`'s outcome (a torch.distributed Store)."""
-    store.set(_key(rank), "ok" if ok else "fail:" + str(message))
+def report(store, rank, solve_id, ok=True, message=""):
+    """Publishes replica `rank`'s outcome of solve `solve_id` (a
+    torch.distributed Store)."""
+    store.set(_key(solve_id, rank), "ok" if ok else "fail:" + str(message))
 
 
-def await_replicas(store, world, timeout_s):
-    """Waits until all `world` replicas have reported, at most timeout_s
-    seconds in total; raises ReplicaFailure naming the replicas that reported
-    a failure or did not report in time."""
+def await_replicas(store, world, solve_id, timeout_s):
+    """Waits until all `world` replicas have reported their outcome of solve
+    `solve_id`, at most timeout_s seconds in total; raises ReplicaFailure
+    naming the replicas that reported a failure or did not report in time."""
     deadline = time.monotonic() + float(timeout_s)
     failed, missing = [], []
     for r in range(world):
         left = max(deadline - time.monotonic(), 0.001)
         try:
-            store.wait([_key(r)], datetime.timedelta(seconds=left))
+            store.wait([_key(solve_id, r)], datetime.timedelta(seconds=left))
         except Exception:  # the store's timeout error
             missing.append(r)
             continue
-        v = store.get(_key(r)).decode()
+        v = store.get(_key(solve_id, r)).decode()
         if v != "ok":
             failed.append((r, v[len("fail:"):]))
     if failed or missing:
         raise ReplicaFailure(failed, missing)
+
+
+def forget(store, world, solve_id):
+    """Deletes the outcomes of solve `solve_id` (one replica calls it after
+    the combination; keys that are absent are skipped)."""
+    for r in range(world):
+        try:
+            store.delete_key(_key(solve_id, r))
+        except Exception:  # a store without delete_key keeps them: ids never repeat
+            pass
 
 
 def shard(n_histories, world, rank):

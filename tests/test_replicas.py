@@ -96,7 +96,7 @@ def _worker_failure(rank, world, port, mode, q):
             try:
                 raise RuntimeError("solver error")
             except RuntimeError as ex:
-                R.report(store, rank, ok=False, message=str(ex))
+                R.report(store, rank, 0, ok=False, message=str(ex))
             q.put((rank, "reported", 0.0))
             return
         q.put((rank, "left", 0.0))
@@ -106,10 +106,10 @@ def _worker_failure(rank, world, port, mode, q):
     from oracle import transport as T
     tau, c, src = synth.grid_problem(n=4, seed=3, tau_range=(0.1, 2.0), block=2, source=2)
     f, _ = T.solve_analog(tau, c, src, 100, R.seed_for(11, rank))
-    R.report(store, rank)
+    R.report(store, rank, 0)
     t0 = time.monotonic()
     try:
-        R.await_replicas(store, world, 5.0)
+        R.await_replicas(store, world, 0, 5.0)
         R.combine(f, 100)
         q.put((rank, "combined", time.monotonic() - t0))
     except R.ReplicaFailure as ex:
@@ -147,9 +147,68 @@ def test_all_replicas_reporting_pass_the_check():
     port = _free_port()
     store = dist.TCPStore("127.0.0.1", port, 1, True, timeout=datetime.timedelta(seconds=10))
     for r in range(3):
-        R.report(store, r)
-    R.await_replicas(store, 3, 1.0)
-    R.report(store, 1, ok=False, message="x")
+        R.report(store, r, 7)
+    R.await_replicas(store, 3, 7, 1.0)
+    R.report(store, 1, 7, ok=False, message="x")
     with pytest.raises(R.ReplicaFailure) as e:
-        R.await_replicas(store, 3, 1.0)
+        R.await_replicas(store, 3, 7, 1.0)
     assert e.value.failed == [(1, "x")] and e.value.missing == []
+    # the outcomes of solve 7 say nothing about solve 8
+    R.report(store, 0, 8)
+    with pytest.raises(R.ReplicaFailure) as e:
+        R.await_replicas(store, 3, 8, 0.5)
+    assert e.value.failed == [] and e.value.missing == [1, 2]
+    R.forget(store, 3, 7)
+    assert not store.check(["gmc_replica/7/0"]) and store.check(["gmc_replica/8/0"])
+
+
+def _worker_second_solve(rank, world, port, q):
+    # two solves in a row on one process group: every replica completes the
+    # first; in the second, rank 1 leaves without reporting. Its "ok" from the
+    # first solve must not satisfy the check of the second.
+    import datetime
+    import torch.distributed as dist
+    R = _load_replicas()
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0,
+                          timeout=datetime.timedelta(seconds=60))
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=world)
+    from oracle import transport as T
+    tau, c, src = synth.grid_problem(n=4, seed=3, tau_range=(0.1, 2.0), block=2, source=2)
+    out = []
+    for solve_id in (0, 1):
+        if rank == 1 and solve_id == 1:
+            q.put((rank, ["left"], 0.0))
+            q.close()
+            q.join_thread()
+            os._exit(3)
+        f, _ = T.solve_analog(tau, c, src, 50, R.seed_for(11 + solve_id, rank))
+        R.report(store, rank, solve_id)
+        t0 = time.monotonic()
+        try:
+            R.await_replicas(store, world, solve_id, 4.0)
+            R.combine(f, 50)
+            out.append("combined")
+        except R.ReplicaFailure as ex:
+            out.append("detected: " + str(ex))
+            q.put((rank, out, time.monotonic() - t0))
+            return
+    q.put((rank, out, 0.0))
+
+
+def test_stale_outcome_of_an_earlier_solve_does_not_hide_a_failure():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = 3
+    procs = [ctx.Process(target=_worker_second_solve, args=(r, world, port, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {r: (out, dt) for r, out, dt in [q.get(timeout=120) for _ in procs]}
+    for p in procs:
+        p.join(timeout=60)
+    assert procs[0].exitcode == 0 and procs[2].exitcode == 0
+    for r in (0, 2):
+        out, dt = res[r]
+        assert out == ["combined", "detected: replica 1 did not report"], out
+        assert 3.0 < dt < 30.0
