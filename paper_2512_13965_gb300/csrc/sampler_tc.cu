@@ -37,10 +37,10 @@
 // columns 128 g .. 128 g + 127, and the ODE state of tile g), two threads per
 // row and group, each loading its 64 columns at once and converting them in
 // 16-column pieces.
-// CTAs run in clusters of two that consume the same weight chunks in the
-// same order: each CTA copies half of every chunk from L2 and multicasts it
-// into both CTAs' stage, so L2 serves each chunk once per pair; a stage is
-// refilled only after both CTAs' MMAs have released it.
+// Each CTA streams every weight chunk from L2 into its own stages with a
+// plain bulk copy (the whole network is 424 KB, L2-resident); a stage is
+// refilled once this CTA's MMAs have released it. CTAs never wait on one
+// another.
 // Every wait is bounded; a timeout sets *err and the CTA drains and exits.
 //
 // FP8 variant (template argument FP8): the three 256 x 256 layers (97% of the
@@ -57,7 +57,6 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
-#include <atomic>
 #include <cstring>
 
 #include "decode.cuh"
@@ -75,11 +74,9 @@ constexpr int EPI_WARPS = 16;                 // two groups of 8, one per 128 ou
 constexpr int GROUP_WARPS = EPI_WARPS / 2;    // 2 per TMEM lane quadrant, 64 columns each
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
 constexpr int NH = 128;                       // output columns of one epilogue group
-constexpr int CLUSTER = 2;                    // CTAs sharing each weight chunk by multicast
 // Weight chunk: all 256 output rows x 128 bytes of K (64 BF16 or 128 E4M3
 // inputs), K-major, 128-byte swizzle; 32 KB.
 constexpr uint32_t CHUNK = 256u * 128u;
-constexpr uint32_t SLICE = CHUNK / CLUSTER;
 constexpr int MMAS_PER_CHUNK = 4;             // 32 bytes of K per MMA
 #ifndef GMC_TC_STAGES
 #define GMC_TC_STAGES 5
@@ -175,40 +172,6 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 // 16 B chunk `c` (0..1) of row `r` in a 32-byte-swizzled block.
 __device__ __forceinline__ uint32_t sw32(uint32_t base, int r, int c) {
   return base + (uint32_t)((r >> 3) * 256 + (r & 7) * 32 + ((c ^ ((r >> 2) & 1)) << 4));
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  // not .aligned: producer and MMA lanes reach this point after divergent loops
-  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-}
-
-// Bulk copy global -> the same shared-memory offset of every CTA in `mask`,
-// completing `bytes` on the barrier at the same offset in each of them.
-__device__ __forceinline__ void bulk_g2s_multicast(void *dst, const void *src, uint32_t bytes,
-                                                   uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-      "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-// Arrive on the barrier at the same offset in every CTA of `mask` once the
-// tcgen05 operations issued so far have completed (warp-wide, one lane issues).
-__device__ __forceinline__ void mma_commit_multicast_w(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "{\n\t.reg .pred e;\n\t"
-      "elect.sync _|e, 0xffffffff;\n\t"
-      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
-      "[%0], %1;\n\t}" ::"r"(smem_u32(bar)),
-      "h"(mask)
-      : "memory");
 }
 
 __device__ void fail(Bars &b, int *err, int code) {
@@ -340,7 +303,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(&B.full[s], 1);
-      mbar_init(&B.empty[s], CLUSTER);
+      mbar_init(&B.empty[s], 1);
     }
     mbar_init(&B.res_full, 1);
     for (int t = 0; t < 2; ++t) {
@@ -359,18 +322,16 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
   }
   tc_fence_before();
   __syncthreads();
-  cluster_sync();  // peers multicast into this CTA's barriers only after they exist
   tc_fence_after();
   const uint32_t tmem = B.tmem_base;
   volatile int *abort = &B.abort;
-  const uint32_t rank = cluster_rank();
-  const uint16_t all_ctas = (uint16_t)((1u << CLUSTER) - 1u);
 
   const int64_t ntiles = (P.n + TM - 1) / TM;
   const int64_t npairs = (ntiles + 1) / 2;
-  // every CTA of a cluster runs the same number of pairs (the chunk stream is
-  // shared); pairs past the end have no valid rows
-  const int64_t n_iter = (npairs + gridDim.x - 1) / gridDim.x;
+  // tile pairs blockIdx.x, blockIdx.x + gridDim.x, ... (grid <= npairs); the
+  // last pair may hold one tile, or rows past n, which are computed on zeros
+  // and not stored
+  const int64_t n_iter = (npairs - blockIdx.x + gridDim.x - 1) / gridDim.x;
   const float h = 1.0f / (float)P.steps;
 
   if (warp == 0) {
@@ -396,10 +357,8 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
                     break;
                   }
                   mbar_arrive_expect_tx(&B.full[s], CHUNK);
-                  bulk_g2s_multicast(
-                      sm + S_ST + s * CHUNK + rank * SLICE,
-                      P.packed + PK::OFF_HID + (size_t)(L * NCH + ch) * CHUNK + rank * SLICE,
-                      SLICE, &B.full[s], all_ctas);
+                  bulk_g2s(sm + S_ST + s * CHUNK, P.packed + PK::OFF_HID + (size_t)(L * NCH + ch) * CHUNK,
+                           CHUNK, &B.full[s]);
                   ++it;
                 }
       if (!ok) {
@@ -489,7 +448,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
                     else
                       mma_ts_f16_w(d, a_k, b_ch + (uint64_t)(2 * k), idh, acc);
                   }
-                  mma_commit_multicast_w(&B.empty[stage], all_ctas);
+                  mma_commit_w(&B.empty[stage]);
                   if (++stage == NST) {
                     stage = 0;
                     sph ^= 1u;
@@ -675,7 +634,6 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
 
   tc_fence_before();
   __syncthreads();
-  cluster_sync();  // no peer multicasts into this CTA's barriers after it exits
   tc_fence_after();
   if (warp == 1) {
     __syncwarp();
@@ -853,42 +811,11 @@ cudaError_t launch_tc(cudaStream_t stream, const Params &p, int sms) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
+  // one persistent CTA per SM (its shared memory and 512 tensor-memory
+  // columns keep a second one off the SM), never more CTAs than tile pairs
   const int64_t ntiles = (p.n + TM - 1) / TM, npairs = (ntiles + 1) / 2;
-  int64_t g = npairs < sms ? npairs : sms;
-  g = (g + CLUSTER - 1) / CLUSTER * CLUSTER;
-  if (g > sms / CLUSTER * CLUSTER) g = sms / CLUSTER * CLUSTER;
-  const int grid = (int)g;
-  cudaLaunchConfig_t lc = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CLUSTER;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  lc.attrs = attr;
-  lc.numAttrs = 1;
-  lc.blockDim = dim3(THREADS);
-  lc.dynamicSmemBytes = SMEM_BYTES;
-  lc.stream = stream;
-  // a persistent grid must be co-resident: at most the clusters that fit
-  // (queried once per device)
-  static std::atomic<int> cached[kMaxDevices];
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int max_clusters = (dev >= 0 && dev < kMaxDevices) ? cached[dev].load(std::memory_order_relaxed) : 0;
-  if (max_clusters < 1) {
-    lc.gridDim = dim3((unsigned)(sms / CLUSTER * CLUSTER));
-    int mc = 0;
-    if (cudaOccupancyMaxActiveClusters(&mc, kernel, &lc) != cudaSuccess || mc < 1) {
-      cudaGetLastError();
-      mc = sms / CLUSTER;
-    }
-    max_clusters = mc;
-    if (dev >= 0 && dev < kMaxDevices) cached[dev].store(mc, std::memory_order_relaxed);
-  }
-  const int grid_fit = grid < max_clusters * CLUSTER ? grid : max_clusters * CLUSTER;
-  lc.gridDim = dim3((unsigned)grid_fit);
-  e = cudaLaunchKernelEx(&lc, kernel, p);
-  if (e != cudaSuccess) return e;
+  const int grid = (int)(npairs < sms ? npairs : sms);
+  kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(p);
   return cudaGetLastError();
 }
 }  // namespace
