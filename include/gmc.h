@@ -32,6 +32,8 @@
  *    host): page-locked host memory (cudaHostAlloc, cudaHostRegister) is
  *    read and written in place by the kernels over the CPU-GPU link; other
  *    host memory is copied in and out through context-owned device buffers.
+ *    Device memory must belong to the context's GPU (or be managed memory):
+ *    another GPU's memory gives GMC_EINVAL before any kernel runs.
  *    The caller owns every buffer it passes; the context owns its weights,
  *    particle banks and scratch.
  *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with counter
@@ -215,7 +217,8 @@ gmc_status gmc_sample_internal(gmc_ctx *ctx, int64_t n, const float *cond, const
  * latency-critical loop or graph-recording section, or hosts that allocate
  * only at start-up). Same arguments and results as gmc_transmit with
  * precision GMC_BF16, except:
- *  - every array must be device memory (host pointers give GMC_EINVAL);
+ *  - every array must be device memory of the context's GPU, or managed
+ *    memory (host pointers and other GPUs' memory give GMC_EINVAL);
  *  - steps must be in [1, 256] (Euler, midpoint) or [1, 128] (RK4): the
  *    layer-1 bias table lives in a static 512 KiB device array (512 network
  *    evaluations), held by every GPU that loads the library until the
@@ -452,6 +455,9 @@ int64_t gmc_train_param_count(void);
  * restores one into the training state of gmc_train_begin, which must have
  * been called on the same dataset with the same batch and precision
  * (GMC_EINVAL otherwise; GMC_EFORMAT for a blob that is not a checkpoint).
+ * The checkpoint records the dataset's size and its standardization
+ * statistics, which gmc_train_begin recomputes from the data: other data (a
+ * different size, or statistics that differ in any bit) gives GMC_EINVAL.
  * Step k's batch is drawn from Philox at (seed, k), so steps after a restore
  * continue the saved run exactly.
  */

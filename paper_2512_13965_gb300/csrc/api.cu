@@ -29,17 +29,23 @@ gmc_status set_error(gmc_ctx *ctx, gmc_status s, const char *fmt, ...) {
 gmc_status cuda_error(gmc_ctx *ctx, cudaError_t e, const char *what) {
   if (e == cudaErrorMemoryAllocation)
     return set_error(ctx, GMC_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorInvalidDevicePointer)  // stage_in / stage_out_prepare: another GPU's memory
+    return set_error(ctx, GMC_EINVAL, "%s: an array is device memory of another GPU than the "
+                     "context's", what);
   return set_error(ctx, GMC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-bool is_device_pointer(const void *p) {
-  if (!p) return false;
+PtrKind pointer_kind(const void *p, int ctx_device) {
   cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return kPtrHost;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return classify_pointer((int)a.type, a.device, ctx_device, a.devicePointer != nullptr);
+}
+
+bool is_device_pointer(const void *p, int ctx_device) {
+  return p && pointer_kind(p, ctx_device) == kPtrDevice;
 }
 
 gmc_status check_device_error(gmc_ctx *ctx) {
@@ -88,17 +94,32 @@ void *mapped_host_pointer(const void *p) {
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// Device memory of the context's GPU and managed memory pass through,
+// page-locked host memory is used in place; another GPU's memory is refused
+// with cudaErrorInvalidDevicePointer (cuda_error turns it into GMC_EINVAL).
+cudaError_t stage_direct(gmc_ctx *ctx, Arg &a, bool *done) {
+  *done = true;
+  switch (pointer_kind(a.user, ctx->device)) {
+    case kPtrDevice: a.dev = const_cast<void *>(a.user); return cudaSuccess;
+    case kPtrOtherDevice: return cudaErrorInvalidDevicePointer;
+    case kPtrMappedHost:
+      if (void *m = mapped_host_pointer(a.user)) {
+        a.dev = m;
+        a.mapped = true;
+        return cudaSuccess;
+      }
+      break;
+    case kPtrHost: break;
+  }
+  *done = false;
+  return cudaSuccess;
+}
+
 cudaError_t stage_in(gmc_ctx *ctx, int slot, Arg &a) {
   if (!a.user) return cudaSuccess;
-  if (is_device_pointer(a.user)) {
-    a.dev = const_cast<void *>(a.user);
-    return cudaSuccess;
-  }
-  if (void *m = mapped_host_pointer(a.user)) {
-    a.dev = m;
-    a.mapped = true;
-    return cudaSuccess;
-  }
+  bool done = false;
+  cudaError_t d = stage_direct(ctx, a, &done);
+  if (done) return d;
   a.host = true;
   cudaError_t e = ensure(ctx->stage[slot], a.bytes);
   if (e != cudaSuccess) return e;
@@ -108,15 +129,9 @@ cudaError_t stage_in(gmc_ctx *ctx, int slot, Arg &a) {
 
 cudaError_t stage_out_prepare(gmc_ctx *ctx, int slot, Arg &a) {
   if (!a.user) return cudaSuccess;
-  if (is_device_pointer(a.user)) {
-    a.dev = const_cast<void *>(a.user);
-    return cudaSuccess;
-  }
-  if (void *m = mapped_host_pointer(a.user)) {
-    a.dev = m;
-    a.mapped = true;
-    return cudaSuccess;
-  }
+  bool done = false;
+  cudaError_t d = stage_direct(ctx, a, &done);
+  if (done) return d;
   a.host = true;
   cudaError_t e = ensure(ctx->stage[slot], a.bytes);
   if (e != cudaSuccess) return e;

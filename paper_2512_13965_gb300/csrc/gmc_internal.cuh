@@ -9,6 +9,7 @@
 #include <string>
 
 #include "../../include/gmc.h"
+#include "ptr_kind.h"
 
 namespace gmc {
 
@@ -94,7 +95,9 @@ namespace gmc {
 
 gmc_status set_error(gmc_ctx *ctx, gmc_status s, const char *fmt, ...);
 gmc_status cuda_error(gmc_ctx *ctx, cudaError_t e, const char *what);
-bool is_device_pointer(const void *p);
+// Device memory of GPU ctx_device, or managed memory (not another GPU's memory).
+bool is_device_pointer(const void *p, int ctx_device);
+PtrKind pointer_kind(const void *p, int ctx_device);
 // Reads and clears the device error word (set by bounded waits that gave up).
 gmc_status check_device_error(gmc_ctx *ctx);
 // Grows buffer `b` to at least `bytes` (never shrinks).

@@ -82,10 +82,11 @@ extern "C" gmc_status gmc_transmit_noalloc(gmc_ctx *ctx, int64_t n, const float 
   if (!cond || (!y_raw && !exit)) return set_error(ctx, GMC_EINVAL, "gmc_transmit_noalloc: null array");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_error(ctx, e, "cudaSetDevice");
-  // host pointers would need staging buffers: only device memory is accepted
-  if (!is_device_pointer(cond) || (noise && !is_device_pointer(noise)) ||
-      (y_raw && !is_device_pointer(y_raw)) || (exit && !is_device_pointer(exit)))
-    return set_error(ctx, GMC_EINVAL, "gmc_transmit_noalloc: every array must be device memory");
+  // host pointers would need staging buffers: only device memory of the
+  // context's GPU (or managed memory) is accepted
+  if (!is_device_pointer(cond, ctx->device) || (noise && !is_device_pointer(noise, ctx->device)) ||
+      (y_raw && !is_device_pointer(y_raw, ctx->device)) || (exit && !is_device_pointer(exit, ctx->device)))
+    return set_error(ctx, GMC_EINVAL, "gmc_transmit_noalloc: every array must be device memory of the context's GPU");
   float *scratch = nullptr;
   gmc_status st = scratch_address(ctx, &scratch);
   if (st != GMC_OK) return st;

@@ -80,3 +80,44 @@ def test_binding_checks_buffer_sizes_and_types(libgmc):
                              np.zeros(n, np.int32), np.zeros((4, n - 1), np.float32))
     assert "exit" in str(e.value)
     ctx.handle = None
+
+
+def test_pointer_classification_rejects_another_gpus_memory(tmp_path):
+    # The rule every array argument goes through (csrc/ptr_kind.h), compiled
+    # into a host-only program: device memory of the context's GPU and managed
+    # memory are used directly, another GPU's memory is refused, page-locked
+    # host memory with a device address is used in place, other host memory is
+    # staged. The memory-type codes are checked against the CUDA runtime's
+    # enum, from its header alone (no GPU, no CUDA library call).
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    inc = "/usr/local/cuda/include"
+    if not gxx or not os.path.exists(os.path.join(inc, "driver_types.h")):
+        pytest.skip("needs g++ and the CUDA headers")
+    src = tmp_path / "t.cpp"
+    src.write_text(r'''
+#include <driver_types.h>
+#include "ptr_kind.h"
+using namespace gmc;
+static_assert(cudaMemoryTypeUnregistered == 0 && cudaMemoryTypeHost == 1 &&
+              cudaMemoryTypeDevice == 2 && cudaMemoryTypeManaged == 3, "cudaMemoryType codes");
+int main() {
+  int bad = 0;
+  bad += classify_pointer(cudaMemoryTypeDevice, 0, 0, true) != kPtrDevice;
+  bad += classify_pointer(cudaMemoryTypeDevice, 3, 3, true) != kPtrDevice;
+  bad += classify_pointer(cudaMemoryTypeDevice, 1, 0, true) != kPtrOtherDevice;
+  bad += classify_pointer(cudaMemoryTypeDevice, 0, 1, true) != kPtrOtherDevice;
+  bad += classify_pointer(cudaMemoryTypeManaged, 1, 0, true) != kPtrDevice;
+  bad += classify_pointer(cudaMemoryTypeHost, 0, 0, true) != kPtrMappedHost;
+  bad += classify_pointer(cudaMemoryTypeHost, 0, 0, false) != kPtrHost;
+  bad += classify_pointer(cudaMemoryTypeUnregistered, -2, 0, false) != kPtrHost;
+  return bad;
+}
+''')
+    exe = tmp_path / "t"
+    r = subprocess.run([gxx, "-std=c++17", "-I", inc, "-I",
+                        os.path.join(ROOT, "paper_2512_13965_gb300", "csrc"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([str(exe)]).returncode == 0
