@@ -489,7 +489,7 @@ gmc_status gmc_train_data(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, 
   if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data: need 0 < tau_lo <= tau_hi, 0 <= c_lo <= c_hi <= 1");
   if (n == 0) return GMC_OK;
-  if (!is_device_pointer(cond) || !is_device_pointer(y))
+  if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data: cond and y must be device memory");
   cudaSetDevice(ctx->device);
   data_kernel<<<nb(n, 128), 128, 0, ctx->stream>>>(n, seed, logf(tau_lo), logf(tau_hi), c_lo, c_hi,
@@ -507,7 +507,7 @@ gmc_status gmc_train_data_internal(gmc_ctx *ctx, int64_t n, uint64_t seed, float
     return set_error(ctx, GMC_EINVAL,
                      "gmc_train_data_internal: need 0 < tau_lo <= tau_hi, 0 <= c_lo <= c_hi <= 1");
   if (n == 0) return GMC_OK;
-  if (!is_device_pointer(cond) || !is_device_pointer(y))
+  if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data_internal: cond and y must be device memory");
   cudaSetDevice(ctx->device);
   internal_data_kernel<<<nb(n, 128), 128, 0, ctx->stream>>>(n, seed, logf(tau_lo), logf(tau_hi), c_lo,
@@ -525,7 +525,7 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
   if (cfg->precision != GMC_FP32 && cfg->precision != GMC_BF16)
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: precision must be GMC_FP32 or GMC_BF16");
   if (!ctx->net.loaded) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_train_begin: load initial weights first");
-  if (!is_device_pointer(cond) || !is_device_pointer(y))
+  if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: data must be device memory");
   cudaSetDevice(ctx->device);
   if (ctx->train) free_train(ctx->train);
@@ -688,10 +688,14 @@ gmc_status gmc_train_params(gmc_ctx *ctx, float *out) {
 // and second moments (P floats each). The batch of step k draws its rows from
 // Philox at (seed, k), so restoring these and the step count resumes the run
 // exactly where it stopped.
+// The dataset is identified by its size n and its 18 FP64-accumulated
+// standardization statistics (stored as FP32), which gmc_train_begin
+// recomputes from the data: a checkpoint restores only into a training state
+// begun on data with the same n and bit-identical statistics.
 struct TrainCkpt {
   char magic[4];
   uint32_t version;
-  int64_t params, step, batch;
+  int64_t params, step, batch, n;
   int32_t precision, reserved;
   double lr, beta1, beta2, eps, weight_decay;
   uint64_t seed;
@@ -715,10 +719,11 @@ gmc_status gmc_train_save_state(gmc_ctx *ctx, void *blob, size_t nbytes) {
   TrainCkpt h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "GMCT", 4);
-  h.version = 1;
+  h.version = 2;
   h.params = P_TOTAL;
   h.step = T->step;
   h.batch = T->cfg.batch;
+  h.n = T->n;
   h.precision = T->cfg.precision;
   h.lr = T->cfg.lr;
   h.beta1 = T->cfg.beta1;
@@ -749,14 +754,19 @@ gmc_status gmc_train_load_state(gmc_ctx *ctx, const void *blob, size_t nbytes) {
     return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: a checkpoint is %zu bytes", need);
   TrainCkpt h;
   std::memcpy(&h, blob, sizeof(h));
-  if (std::memcmp(h.magic, "GMCT", 4) != 0 || h.version != 1 || h.params != P_TOTAL)
-    return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: not a version-1 training checkpoint");
-  if (h.batch != T->cfg.batch || h.precision != T->cfg.precision || h.step < 0)
-    return set_error(ctx, GMC_EINVAL,
-                     "gmc_train_load_state: begin training with the checkpoint's batch and precision");
+  if (std::memcmp(h.magic, "GMCT", 4) != 0 || h.version != 2 || h.params != P_TOTAL)
+    return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: not a version-2 training checkpoint");
   for (int k = 0; k < 18; ++k)
     if (!std::isfinite(h.stats[k]) || (((k >= 5 && k < 10) || k >= 14) && !(h.stats[k] > 0.0f)))
       return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: bad standardization statistics");
+  if (h.batch != T->cfg.batch || h.precision != T->cfg.precision || h.step < 0)
+    return set_error(ctx, GMC_EINVAL,
+                     "gmc_train_load_state: begin training with the checkpoint's batch and precision");
+  if (h.n != T->n || std::memcmp(h.stats, T->stats, sizeof(h.stats)) != 0)
+    return set_error(ctx, GMC_EINVAL,
+                     "gmc_train_load_state: the checkpoint was saved on other data (size %lld, "
+                     "or different statistics) than this training state's (size %lld)",
+                     (long long)h.n, (long long)T->n);
   const float *body = (const float *)((const unsigned char *)blob + sizeof(h));
   cudaSetDevice(ctx->device);
   cudaStream_t s = ctx->stream;
@@ -771,7 +781,6 @@ gmc_status gmc_train_load_state(gmc_ctx *ctx, const void *blob, size_t nbytes) {
   T->cfg.eps = h.eps;
   T->cfg.weight_decay = h.weight_decay;
   T->cfg.seed = h.seed;
-  std::memcpy(T->stats, h.stats, sizeof(h.stats));
   return GMC_OK;
 }
 

@@ -2,7 +2,8 @@
 a run stopped after k steps, saved, restored into a fresh training state and
 continued ends where the uninterrupted run ends (bit for bit when two
 uninterrupted runs agree bit for bit, else within their spread); malformed
-checkpoints and a mismatched batch are refused."""
+checkpoints, a mismatched batch and a checkpoint saved on other data are
+refused."""
 import numpy as np
 import pytest
 
@@ -63,5 +64,22 @@ def test_resume_continues_the_run(gpu_ctx, kaiming_file):
         with pytest.raises(g.GMCError) as e:
             g.gmc_train_load_state(ctx, blob)
         assert e.value.status == g.GMC_EINVAL
+        # the same batch and precision on other data: a smaller prefix of the
+        # dataset (other n), then a dataset of the same size drawn with another seed
+        half_c = cond[:, : n // 2].contiguous()
+        half_y = y[:, : n // 2].contiguous()
+        g.gmc_train_begin(ctx, n // 2, half_c, half_y, cfg)
+        with pytest.raises(g.GMCError) as e:
+            g.gmc_train_load_state(ctx, blob)
+        assert e.value.status == g.GMC_EINVAL
+        cond2 = torch.empty(5, n, device="cuda")
+        y2 = torch.empty(4, n, device="cuda")
+        g.gmc_train_data(ctx, n, 4, 0.1, 1000.0, 0.5, 0.999, cond2, y2)
+        g.gmc_train_begin(ctx, n, cond2, y2, cfg)
+        with pytest.raises(g.GMCError) as e:
+            g.gmc_train_load_state(ctx, blob)
+        assert e.value.status == g.GMC_EINVAL
+        g.gmc_train_begin(ctx, n, cond, y, cfg)
+        g.gmc_train_load_state(ctx, blob)  # the original data is accepted again
     finally:
         ctx.close()
