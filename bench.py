@@ -34,6 +34,12 @@ HIDDEN = 256
 FLOPS_PER_STEP = 2 * (4 * HIDDEN + 3 * HIDDEN * HIDDEN + HIDDEN * 4)
 FLOPS_COND = 2 * 5 * HIDDEN
 METRIC = "cell transmissions/s GMC vs analog MC at flux err <=1%; p99 latency"
+# networks trained by the package's own trainer (commands in the weights folder)
+TRAINED_BOUNDARY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_boundary.bin")
+TRAINED_INTERNAL = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_internal.bin")
+# stated GMC-vs-analog relative L2 flux error at 1e7 histories, per precision
+# of the network (the metric's condition is the BF16 one, 1 %)
+FLUX_ERR_BOUND = {"bf16": 0.01, "fp8": 0.02}
 WORKLOAD = ("GMC sampler inference: 25-256x4-4 SiLU velocity MLP, Kaiming-normal seed 1, "
             "16 Euler steps, batch 2^20, tau logU[0.1,1000], c U[0.5,0.999]")
 
@@ -178,9 +184,15 @@ def main():
     ap.add_argument("--workload", default="sampler",
                     choices=["sampler", "solve", "hohlraum", "serve", "sweep", "heldout", "sigma",
                              "walks", "paper"])
-    ap.add_argument("--weights", default=None, help="GMCW file (default: Kaiming seed 1)")
+    ap.add_argument("--weights", default=None,
+                    help="GMCW file of the boundary model for the solve, serve, sigma, sweep and "
+                         "heldout workloads (default: the package's trained network; 'kaiming': "
+                         "untrained Kaiming-normal seed 1)")
     ap.add_argument("--internal-weights", default=None,
-                    help="GMCW file of the internal-source model (solve/serve: births sampled by it)")
+                    help="GMCW file of the internal-source model (solve/serve: births sampled by "
+                         "it; default: the package's trained network; 'none': births walked)")
+    ap.add_argument("--serve-leg-requests", type=int, default=40,
+                    help="requests of the short serving leg in the default line")
     ap.add_argument("--histories", type=float, default=1e6)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--hist-range", type=float, nargs=2, default=(1e3, 1e5),
@@ -312,6 +324,8 @@ def main():
     extras = {}
     if not args.no_extras:
         extras = analog_extras(g, ctx, torch)
+        if world == 1:
+            extras.update(headline_extras(args))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "cell transmissions/s", "n_gpus": world,
@@ -368,22 +382,172 @@ def analog_extras(g, ctx, torch):
     return out
 
 
+def _weights(args):
+    """(boundary, internal) weight files of a solve-level workload: the
+    package's trained networks unless the flags say otherwise."""
+    b = TRAINED_BOUNDARY if args.weights is None else args.weights
+    i = getattr(args, "internal_weights", None)
+    i = TRAINED_INTERNAL if i is None else (None if i == "none" else i)
+    return b, i
+
+
 def _context(args):
     import torch
     import synth
     import paper_2512_13965_gb300 as g
     torch.cuda.set_device(0)
     ctx = g.Context(0)
-    if getattr(args, "internal_weights", None):
-        g.gmc_load_internal_weights(ctx, args.internal_weights)
-    if args.weights:
-        g.gmc_load_weights(ctx, args.weights)
+    bw, iw = _weights(args)
+    args.weights, args.internal_weights = bw, iw
+    if iw:
+        g.gmc_load_internal_weights(ctx, iw)
+    if bw != "kaiming":
+        g.gmc_load_weights(ctx, bw)
     else:
         with tempfile.TemporaryDirectory() as d:
             path = os.path.join(d, "w.bin")
             synth.write_weights(path, synth.kaiming_weights(1))
             g.gmc_load_weights(ctx, path)
     return g, ctx
+
+
+def _rel(a, b):
+    import numpy as np
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def solve_cfg4(g, ctx, n_hist, variants):
+    """The 128x128 transport solve (tau logU[0.1,500], c {0.5,0.999} per 16x16
+    block, seed 2; central 8x8 source; vacuum boundaries): the GPU random walk
+    as two independent runs of n/2 histories (averaged: the reference flux;
+    their difference / sqrt(2): the statistical floor of an n-history run),
+    then each GMC variant (precision, integrator, steps) with n histories.
+    Device time per solve from CUDA events around the whole solve."""
+    import numpy as np
+    import synth
+    N = 128
+    tau, c, src = synth.grid_problem(n=N, seed=2)
+    tau, c, src = (np.ascontiguousarray(a.ravel()) for a in (tau, c, src))
+
+    def solve(method, seed, n, prec=None, integ=0, steps=16):
+        cfg = g.gmc_get_config(ctx)
+        cfg.steps, cfg.integrator = steps, integ
+        cfg.precision = g.GMC_BF16 if prec is None else prec
+        cfg.gmc_min_tau = 0.0
+        g.gmc_set_config(ctx, cfg)
+        f = np.zeros(N * N)
+        st = g.transport_solve(ctx, N, N, tau, c, src, n, method, seed, f)
+        return f, st
+
+    half = n_hist // 2
+    f_a, st_a = solve(g.GMC_METHOD_ANALOG, 1, half)
+    f_b, st_b = solve(g.GMC_METHOD_ANALOG, 2, n_hist - half)
+    f_mc = 0.5 * (f_a + f_b)
+    secs = st_a.seconds + st_b.seconds
+    trans = st_a.transmissions + st_b.transmissions
+    out = {"analog": {"seconds": secs, "transmissions": trans, "transmissions_per_s": trans / secs,
+                      "collisions": st_a.collisions + st_b.collisions,
+                      "flux_floor_at_n": _rel(f_a, f_b) / np.sqrt(2.0)}}
+    names = {g.GMC_EULER: "euler", g.GMC_MIDPOINT: "midpoint", g.GMC_RK4: "rk4"}
+    for prec, integ, steps in variants:
+        pname = "bf16" if prec == g.GMC_BF16 else "fp8"
+        key = "gmc_%s_%s%d" % (pname, names[integ], steps)
+        f, st = solve(g.GMC_METHOD_GMC, 3, n_hist, prec, integ, steps)
+        err = _rel(f, f_mc)
+        out[key] = {"seconds": st.seconds, "transmissions": st.transmissions,
+                    "transmissions_per_s": st.transmissions / st.seconds,
+                    "flux_rel_err_vs_analog": err, "flux_err_bound": FLUX_ERR_BOUND[pname],
+                    "within_bound": err <= FLUX_ERR_BOUND[pname],
+                    "solve_speedup_vs_analog": secs / st.seconds,
+                    "transmission_rate_vs_analog": (st.transmissions / st.seconds) / (trans / secs)}
+    return out
+
+
+def serve_stream(g, ctx, reqs, method, prec, integ, steps, rng, load=0.7, min_tau=0.0):
+    """One serving run: the capacity of the server (the whole stream submitted
+    at once), then the same requests arriving as a Poisson stream at `load`
+    of that capacity; latency = completion - submission per request."""
+    import numpy as np
+    cfg = g.gmc_get_config(ctx)
+    cfg.steps, cfg.integrator, cfg.precision, cfg.gmc_min_tau = steps, integ, prec, min_tau
+    cfg.bank_capacity = 1 << 20
+    g.gmc_set_config(ctx, cfg)
+    g.gmc_serve_start(ctx, method, 4 << 30)
+    try:
+        t0 = time.perf_counter()
+        tks = [g.gmc_submit(ctx, n, n, tau, c, src, h, 7 + i) for i, (n, tau, c, src, h) in enumerate(reqs)]
+        for tk, r in zip(tks, reqs):
+            g.gmc_wait(ctx, tk, 1800.0, np.zeros(r[0] * r[0]))
+        cap = len(reqs) / (time.perf_counter() - t0)
+        gaps = rng.exponential(1.0 / (load * cap), len(reqs))
+        t0 = time.perf_counter()
+        tks = []
+        t_next = t0
+        for i, (n, tau, c, src, h) in enumerate(reqs):
+            t_next += gaps[i]
+            while time.perf_counter() < t_next:
+                time.sleep(0.0002)
+            tks.append(g.gmc_submit(ctx, n, n, tau, c, src, h, 100000 + i))
+        lat, trans = [], 0
+        for tk, r in zip(tks, reqs):
+            st = g.gmc_wait(ctx, tk, 1800.0, np.zeros(r[0] * r[0]))
+            lat.append(st.latency)
+            trans += st.transmissions
+        wall = time.perf_counter() - t0
+    finally:
+        g.gmc_serve_stop(ctx)
+    return {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "solves_per_s": len(reqs) / wall, "capacity_solves_per_s": cap, "offered_load": load,
+            "transmissions_per_s": trans / wall}
+
+
+def serve_requests(n_req, hist_range, seed=4):
+    """Serving stream requests: grids n x n with n ~ U{16..256}, tau
+    logU[0.1,1000], c {0.5,0.999} per 16x16 block, a central source of n/16
+    cells a side, histories log-uniform in hist_range."""
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n_req):
+        n = int(rng.integers(16, 257))
+        tau, c, src = synth.grid_problem(n=n, seed=1000 + k, tau_range=(0.1, 1000.0),
+                                         block=16, source=max(2, n // 16))
+        hist = int(np.exp(rng.uniform(np.log(hist_range[0]), np.log(hist_range[1]))))
+        reqs.append((n, np.ascontiguousarray(tau.ravel()), np.ascontiguousarray(c.ravel()),
+                     np.ascontiguousarray(src.ravel()), hist))
+    return reqs, rng
+
+
+def headline_extras(args):
+    """The solve-level headline on the trained networks: the 128x128 solve at
+    1e7 histories (analog vs GMC BF16 midpoint 8, FP8 midpoint 8 and BF16 RK4
+    12) and a short Poisson serving leg (GMC FP8 midpoint 8 vs analog)."""
+    import numpy as np
+    import paper_2512_13965_gb300 as g
+    ctx = g.Context(0)
+    try:
+        g.gmc_load_weights(ctx, TRAINED_BOUNDARY)
+        g.gmc_load_internal_weights(ctx, TRAINED_INTERNAL)
+        n = int(1e7)
+        solve = solve_cfg4(g, ctx, n, ((g.GMC_BF16, g.GMC_MIDPOINT, 8), (g.GMC_FP8, g.GMC_MIDPOINT, 8),
+                                       (g.GMC_BF16, g.GMC_RK4, 12)))
+        out = {"solve_cfg4": {"workload": "transport solve 128x128, tau logU[0.1,500], c {0.5,0.999} "
+                              "16x16 blocks (seed 2), central 8x8 source, vacuum, %d histories" % n,
+                              "networks": "trained (package weights folder): boundary and internal "
+                              "models, births sampled by the internal model",
+                              "results": solve}}
+        reqs, rng = serve_requests(args.serve_leg_requests, (1e4, 1e6))
+        leg = {}
+        for name, method, prec in (("gmc_fp8_midpoint8", g.GMC_METHOD_GMC, g.GMC_FP8),
+                                   ("analog", g.GMC_METHOD_ANALOG, g.GMC_BF16)):
+            leg[name] = serve_stream(g, ctx, reqs, method, prec, g.GMC_MIDPOINT, 8, rng)
+        out["serve_leg"] = {"workload": "%d Poisson-arriving solves, n~U{16..256}, tau logU[0.1,1000], "
+                            "histories logU[1e4,1e6], offered load 0.7 of measured capacity"
+                            % len(reqs), "results": leg}
+    finally:
+        ctx.close()
+    return out
 
 
 def run_solve(args):
@@ -470,7 +634,7 @@ def run_solve(args):
                     "collisions": st.collisions,
                     "flux_rel_err_vs_analog": None if f_mc is None else rel(f, f_mc)}
     line = {"metric": METRIC, "workload": "%s, %d histories" % (desc, n),
-            "weights": args.weights or "kaiming seed 1 (untrained)",
+            "weights": args.weights,
             "births": "on the left boundary (no birth walk)" if hohl else (
                 ("internal model " + args.internal_weights) if args.internal_weights else "random walk"),
             "results": out, "unit": "cell transmissions/s"}
@@ -514,19 +678,23 @@ def run_sigma(args):
         out[name] = {"runs": rows, "slope": float(np.polyfit(x, y, 1)[0])}
     print(json.dumps({"metric": "sigma_bar(N), Eq. 12, K = %d runs" % K,
                       "workload": "transport solve 128x128 (solve workload grid)",
-                      "weights": args.weights or "kaiming seed 1 (untrained)",
+                      "weights": args.weights,
                       "births": ("internal model " + args.internal_weights) if args.internal_weights
                       else "random walk", "results": out}))
     ctx.close()
 
 
 def run_paper(args):
-    """Random-walk solves of the paper's two benchmark problems with their
-    printed cross sections (stand-in layouts): the lattice (112 x 112 cells,
-    central volumetric source) and the linearized hohlraum (112 x 112 cells,
-    surface source on the left boundary). --histories per solve, two seeds
-    each: solve time, transmissions/s and the run-to-run flux difference
-    ||phi_1 - phi_2|| / ||phi_1|| (the statistical floor of the flux error)."""
+    """Solves of the paper's two benchmark problems with their printed cross
+    sections (stand-in layouts): the lattice (112 x 112 cells, central
+    volumetric source) and the linearized hohlraum (112 x 112 cells, surface
+    source on the left boundary). Every cell is thin (tau <= 1.16) and most
+    leave the networks' training box (c = 1 scatterers, c = 0.05 absorbers):
+    GMC samples them at their scattering-equivalent condition and walks the
+    cells that have none. --histories per solve: the random walk with two
+    seeds (its run-to-run difference is the statistical floor), then GMC
+    (trained networks, BF16, midpoint 8 and RK4 12); solve time,
+    transmissions/s and the flux error against the walk."""
     import numpy as np
     import synth
     g, ctx = _context(args)
@@ -535,23 +703,58 @@ def run_paper(args):
                 "hohlraum": (synth.paper_hohlraum_problem(112), g.transport_solve_wall)}
     out = {}
     for name, ((tau, c, src), solve) in problems.items():
+        n_equiv, n_walk, n_inside = _equivalent_summary(tau, c)
         tau, c, src = (np.ascontiguousarray(a.ravel()) for a in (tau, c, src))
+
+        def run(method, seed, prec=g.GMC_BF16, integ=g.GMC_MIDPOINT, steps=8):
+            cfg = g.gmc_get_config(ctx)
+            cfg.precision, cfg.integrator, cfg.steps, cfg.gmc_min_tau = prec, integ, steps, 0.0
+            g.gmc_set_config(ctx, cfg)
+            f = np.zeros(112 * 112)
+            st = solve(ctx, 112, 112, tau, c, src, n_hist, method, seed, f)
+            return f, st
+
         fl, secs, trans = [], [], []
         for seed in (11, 12):
-            f = np.zeros(112 * 112)
-            st = solve(ctx, 112, 112, tau, c, src, n_hist, g.GMC_METHOD_ANALOG, seed, f)
+            f, st = run(g.GMC_METHOD_ANALOG, seed)
             fl.append(f)
             secs.append(st.seconds)
             trans.append(st.transmissions)
-        floor = float(np.linalg.norm(fl[0] - fl[1]) / np.linalg.norm(fl[0]))
-        out[name] = {"method": "analog", "histories": n_hist, "seconds": secs,
-                     "transmissions": trans,
-                     "transmissions_per_s": float(np.mean(trans) / np.mean(secs)),
-                     "flux_floor": floor}
-    print(json.dumps({"metric": "random-walk solves of the paper's benchmark problems",
+        f_mc = 0.5 * (fl[0] + fl[1])
+        res = {"analog": {"histories": n_hist, "seconds": secs, "transmissions": trans,
+                          "transmissions_per_s": float(np.mean(trans) / np.mean(secs)),
+                          "flux_floor_at_n": _rel(fl[0], fl[1]) / np.sqrt(2.0)},
+               "cells": {"outside_box_sampled_at_equivalent": n_equiv, "walked_no_equivalent": n_walk,
+                         "inside_box": n_inside}}
+        for key, integ, steps in (("gmc_bf16_midpoint8", g.GMC_MIDPOINT, 8),
+                                  ("gmc_bf16_rk412", g.GMC_RK4, 12)):
+            f, st = run(g.GMC_METHOD_GMC, 13, integ=integ, steps=steps)
+            res[key] = {"seconds": st.seconds, "transmissions": st.transmissions,
+                        "transmissions_per_s": st.transmissions / st.seconds,
+                        "collisions_of_walked_cells": st.collisions,
+                        "flux_rel_err_vs_analog": _rel(f, f_mc),
+                        "solve_speedup_vs_analog": float(np.mean(secs)) / st.seconds}
+        out[name] = res
+    print(json.dumps({"metric": "solves of the paper's benchmark problems, GMC vs the random walk",
                       "workload": "lattice and linearized hohlraum, 112x112 cells, printed cross "
-                                  "sections, stand-in layouts", "results": out}))
+                                  "sections, stand-in layouts, %d histories" % n_hist,
+                      "weights": args.weights, "internal_weights": args.internal_weights,
+                      "results": out}))
     ctx.close()
+
+
+def _equivalent_summary(tau, c, box=((0.1, 1000.0), (0.5, 0.999))):
+    """Cell counts: outside the training box with an equivalent condition,
+    without one (walked), inside (host arithmetic of the same reading as the
+    solve)."""
+    import numpy as np
+    tau = np.asarray(tau, np.float64)
+    c = np.asarray(c, np.float64)
+    (t_lo, t_hi), (c_lo, c_hi) = box
+    inside = (tau >= t_lo) & (tau <= t_hi) & (c >= c_lo) & (c <= c_hi)
+    w = c * tau
+    ok = inside | ((w > 0) & (np.maximum(c_lo, w / t_hi) <= np.minimum(c_hi, w / t_lo)))
+    return int((ok & ~inside).sum()), int((~ok).sum()), int(inside.sum())
 
 
 def run_walks(args):
@@ -682,11 +885,12 @@ def run_heldout(args):
     import numpy as np
     import torch
     import synth
-    if not args.weights:
-        raise SystemExit("--workload heldout needs --weights (a trained GMCW file)")
+    if args.weights == "kaiming":
+        raise SystemExit("--workload heldout compares a trained network with the untrained one")
     g, ctx = _context(args)
     args_u = argparse.Namespace(**vars(args))
-    args_u.weights = None
+    args_u.weights = "kaiming"
+    args_u.internal_weights = "none"
     _, ctx_u = _context(args_u)
     # one stream for torch and the library: inputs made by torch, outputs read
     # by torch, in stream order (a null stream would select the context's own)
@@ -751,68 +955,22 @@ def run_heldout(args):
 
 
 def run_serve(args):
-    """Serving: Poisson stream of solves, grids n x n with n ~ U{16..256},
-    tau logU[0.1,1000], c {0.5,0.999} blocks, histories logU[1e3,1e5];
-    p50/p99 latency and solves/s for GMC (RK4, 12 steps; BF16, FP8, and the hybrid
-    with cells thinner than tau = 64 walked) and the analog walk."""
-    import numpy as np
-    import synth
+    """Serving: Poisson stream of solves (serve_requests: grids n x n with
+    n ~ U{16..256}, tau logU[0.1,1000], c {0.5,0.999} blocks, histories
+    log-uniform in --hist-range); p50/p99 latency and solves/s for GMC FP8
+    and BF16 (midpoint, 8 steps) and the analog walk."""
     g, ctx = _context(args)
-    rng = np.random.default_rng(4)
-    reqs = []
-    for k in range(args.requests):
-        n = int(rng.integers(16, 257))
-        tau, c, src = synth.grid_problem(n=n, seed=1000 + k, tau_range=(0.1, 1000.0),
-                                         block=16, source=max(2, n // 16))
-        hist = int(np.exp(rng.uniform(np.log(args.hist_range[0]), np.log(args.hist_range[1]))))
-        reqs.append((n, np.ascontiguousarray(tau.ravel()), np.ascontiguousarray(c.ravel()),
-                     np.ascontiguousarray(src.ravel()), hist))
+    reqs, rng = serve_requests(args.requests, args.hist_range)
     out = {}
-    # GMC with the integrator that reaches the analog floor on the 128^2
-    # solve (RK4, 12 steps), in BF16 and FP8, against the analog walk
-    for name, method, prec, min_tau in (("gmc_bf16_rk4_12", g.GMC_METHOD_GMC, g.GMC_BF16, 0.0),
-                                        ("gmc_fp8_rk4_12", g.GMC_METHOD_GMC, g.GMC_FP8, 0.0),
-                                        ("hybrid64_bf16_rk4_12", g.GMC_METHOD_GMC, g.GMC_BF16, 64.0),
-                                        ("analog", g.GMC_METHOD_ANALOG, g.GMC_BF16, 0.0)):
-        cfg = g.gmc_get_config(ctx)
-        cfg.steps = 12
-        cfg.integrator = g.GMC_RK4
-        cfg.precision = prec
-        cfg.gmc_min_tau = min_tau
-        cfg.bank_capacity = 1 << 20
-        g.gmc_set_config(ctx, cfg)
-        # capacity: the whole stream submitted at once
-        g.gmc_serve_start(ctx, method, 4 << 30)
-        t0 = time.perf_counter()
-        tks = [g.gmc_submit(ctx, n, n, tau, c, src, h, 7 + i) for i, (n, tau, c, src, h) in enumerate(reqs)]
-        for tk, r in zip(tks, reqs):
-            g.gmc_wait(ctx, tk, 600.0, np.zeros(r[0] * r[0]))
-        cap = len(reqs) / (time.perf_counter() - t0)
-        # Poisson arrivals at 0.7 of that capacity
-        gaps = rng.exponential(1.0 / (0.7 * cap), len(reqs))
-        t0 = time.perf_counter()
-        tks = []
-        t_next = t0
-        for i, (n, tau, c, src, h) in enumerate(reqs):
-            t_next += gaps[i]
-            while time.perf_counter() < t_next:
-                time.sleep(0.0002)
-            tks.append(g.gmc_submit(ctx, n, n, tau, c, src, h, 100 + i))
-        lat, trans = [], 0
-        for tk, r in zip(tks, reqs):
-            st = g.gmc_wait(ctx, tk, 600.0, np.zeros(r[0] * r[0]))
-            lat.append(st.latency)
-            trans += st.transmissions
-        wall = time.perf_counter() - t0
-        g.gmc_serve_stop(ctx)
-        out[name] = {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                     "solves_per_s": len(reqs) / wall, "capacity_solves_per_s": cap,
-                     "offered_load": 0.7, "transmissions_per_s": trans / wall}
+    for name, method, prec in (("gmc_fp8_midpoint8", g.GMC_METHOD_GMC, g.GMC_FP8),
+                               ("gmc_bf16_midpoint8", g.GMC_METHOD_GMC, g.GMC_BF16),
+                               ("analog", g.GMC_METHOD_ANALOG, g.GMC_BF16)):
+        out[name] = serve_stream(g, ctx, reqs, method, prec, g.GMC_MIDPOINT, 8, rng)
     line = {"metric": METRIC, "workload": "serving: %d Poisson-arriving solves, n~U{16..256}, "
             "tau logU[0.1,1000], histories logU[%g,%g]" % (len(reqs), args.hist_range[0],
                                                           args.hist_range[1]), "results": out,
             "births": ("internal model " + args.internal_weights) if args.internal_weights else "random walk",
-            "weights": args.weights or "kaiming seed 1 (untrained)"}
+            "weights": args.weights}
     print(json.dumps(line))
     ctx.close()
 

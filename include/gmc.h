@@ -71,6 +71,12 @@ typedef enum gmc_precision { GMC_FP32 = 0, GMC_BF16 = 1, GMC_FP8 = 2 } gmc_preci
 typedef enum gmc_integrator { GMC_EULER = 0, GMC_MIDPOINT = 1, GMC_RK4 = 2 } gmc_integrator;
 typedef enum gmc_absorb_mode { GMC_ABSORB_ANALOG = 0, GMC_ABSORB_IMPLICIT = 1 } gmc_absorb_mode;
 typedef enum gmc_method { GMC_METHOD_ANALOG = 0, GMC_METHOD_GMC = 1 } gmc_method;
+/* Kernel of the BF16 tensor-core sampler (results agree within the BF16
+   bound; the FP8 path always uses the tile kernel): GMC_KERNEL_TILE, one
+   CTA per SM running two M = 128 tiles with one accumulator; GMC_KERNEL_PAIR,
+   clusters of two CTAs running M = 256 tiles (tcgen05 cta_group::2) with two
+   accumulators per CTA. */
+typedef enum gmc_sampler_kernel { GMC_KERNEL_TILE = 0, GMC_KERNEL_PAIR = 1 } gmc_sampler_kernel;
 
 typedef struct gmc_ctx gmc_ctx;
 
@@ -90,6 +96,21 @@ typedef struct gmc_config {
                               networks, so GMC runs where one network evaluation costs less
                               than the walk's flights; 0 (default) = every cell by GMC, as
                               in the paper */
+    /* GMC solves: the box of (tau, c) the networks were trained on (both
+       models; defaults [0.1, 1000] x [0.5, 0.999], the trainer's). The
+       networks learn the implicit-capture walk, whose exits depend on the
+       scattering thickness c tau alone and whose track lengths scale as 1/c
+       (section "Monte Carlo Method", Eq. 4-5). A cell outside the box is
+       sampled at the in-box condition (tau', c') with c' tau' = c tau (c'
+       the value in [c_lo, c_hi] nearest c that keeps tau' in the box) and
+       its sampled track length multiplied by c'/c; a cell whose c tau lies
+       outside [c_lo tau_lo, c_hi tau_hi] (c = 0 included) has no such
+       condition and is crossed, and its births walked, by the random walk.
+       Need 0 < net_tau_lo <= net_tau_hi, 0 < net_c_lo <= net_c_hi <= 1. */
+    double net_tau_lo, net_tau_hi;
+    double net_c_lo, net_c_hi;
+    int sampler_kernel;    /* gmc_sampler_kernel of BF16 sampling (gmc_transmit, solves,
+                              gmc_transmit_noalloc); default GMC_KERNEL_TILE */
 } gmc_config;
 
 /* Per-solve counters (all weights per history-weight unit, not normalized). */

@@ -278,6 +278,36 @@ def equivalent_sampler(sampler, fallback, tau_range=(0.1, 1000.0), c_range=(0.5,
     return f
 
 
+def equivalent_internal_sampler(internal, fallback, tau_range=(0.1, 1000.0),
+                                c_range=(0.5, 0.999)):
+    """Births for grids whose cells leave the internal model's training box:
+    the same reading as equivalent_sampler. A birth at the normalized point
+    (X, Y) of a cell (tau, c) walks, in cell units, exactly as a birth at
+    (X, Y) of a cell (tau', c') with c' tau' = c tau (flights at rate c in
+    side tau are flights at rate c' in side tau', every length times c'/c),
+    so births in cells with an equivalent are sampled by `internal` at
+    (tau', c') with s scaled by c'/c; births in cells without one go to
+    `fallback` (the walk) at their own (tau, c)."""
+    def f(X, Y, tau, c, ids, u_angle):
+        X, Y, tau, c = (np.asarray(a, dtype=np.float64) for a in (X, Y, tau, c))
+        ids = np.asarray(ids, dtype=np.uint64)
+        u_angle = np.asarray(u_angle, dtype=np.float64)
+        tp, cp, ok = equivalent_condition(tau, c, tau_range, c_range)
+        n = X.shape[0]
+        face = np.zeros(n, np.int64)
+        q, ux, uy, s = (np.zeros(n) for _ in range(4))
+        ev = np.zeros(n, np.uint32)
+        for sel, fn, tt, cc in ((ok, internal, tp, cp), (~ok, fallback, tau, c)):
+            k = np.nonzero(sel)[0]
+            if k.size == 0:
+                continue
+            fa, qa, uxa, uya, sa, eva = fn(X[k], Y[k], tt[k], cc[k], ids[k], u_angle[k])
+            face[k], q[k], ux[k], uy[k], ev[k] = fa, qa, uxa, uya, eva
+            s[k] = np.asarray(sa) * (cc[k] / c[k]) if fn is internal else sa
+        return face, q, ux, uy, s, ev
+    return f
+
+
 def internal_condition(X, Y, tau, c):
     """Condition of the internal model for births at (X, Y) in [0,1]^2 of a cell:
     (X, Y, ln tau, c, distance to the nearest face in cell units) -> [5, B]."""

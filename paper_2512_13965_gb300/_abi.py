@@ -26,7 +26,10 @@ class gmc_config(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("integrator", ctypes.c_int), ("precision", ctypes.c_int),
                 ("w_cut", ctypes.c_double), ("p_survive", ctypes.c_double),
                 ("bank_capacity", ctypes.c_int64), ("flights_per_wave", ctypes.c_int),
-                ("gmc_min_tau", ctypes.c_double)]
+                ("gmc_min_tau", ctypes.c_double),
+                ("net_tau_lo", ctypes.c_double), ("net_tau_hi", ctypes.c_double),
+                ("net_c_lo", ctypes.c_double), ("net_c_hi", ctypes.c_double),
+                ("sampler_kernel", ctypes.c_int)]
 
 
 class gmc_solve_stats(ctypes.Structure):

@@ -155,6 +155,11 @@ gmc_config default_config() {
   c.bank_capacity = (int64_t)1 << 21;
   c.flights_per_wave = 512;
   c.gmc_min_tau = 0.0;
+  c.net_tau_lo = 0.1;
+  c.net_tau_hi = 1000.0;
+  c.net_c_lo = 0.5;
+  c.net_c_hi = 0.999;
+  c.sampler_kernel = GMC_KERNEL_TILE;
   return c;
 }
 
@@ -243,6 +248,7 @@ gmc_status gmc_destroy(gmc_ctx *ctx) {
   for (auto &b : ctx->stage)
     if (b.ptr) cudaFree(b.ptr);
   if (ctx->bias1.ptr) cudaFree(ctx->bias1.ptr);
+  if (ctx->walk_next.ptr) cudaFree(ctx->walk_next.ptr);
   if (ctx->train) train_state_free(ctx->train);
   if (ctx->net.d_f32) cudaFree(ctx->net.d_f32);
   if (ctx->net.d_tc) cudaFree(ctx->net.d_tc);
@@ -295,6 +301,12 @@ gmc_status gmc_set_config(gmc_ctx *ctx, const gmc_config *cfg) {
   if (cfg->flights_per_wave < 1)
     return set_error(ctx, GMC_EINVAL, "flights_per_wave must be >= 1");
   if (!(cfg->gmc_min_tau >= 0.0)) return set_error(ctx, GMC_EINVAL, "gmc_min_tau must be >= 0");
+  if (!(cfg->net_tau_lo > 0.0 && cfg->net_tau_hi >= cfg->net_tau_lo && std::isfinite(cfg->net_tau_hi)) ||
+      !(cfg->net_c_lo > 0.0 && cfg->net_c_hi >= cfg->net_c_lo && cfg->net_c_hi <= 1.0))
+    return set_error(ctx, GMC_EINVAL,
+                     "need 0 < net_tau_lo <= net_tau_hi (finite), 0 < net_c_lo <= net_c_hi <= 1");
+  if (cfg->sampler_kernel != GMC_KERNEL_TILE && cfg->sampler_kernel != GMC_KERNEL_PAIR)
+    return set_error(ctx, GMC_EINVAL, "unknown sampler_kernel %d", cfg->sampler_kernel);
   ctx->cfg = *cfg;
   return GMC_OK;
 }
@@ -530,7 +542,8 @@ gmc_status transmit_net(gmc_ctx *ctx, const NetDev &N, int64_t n, const float *c
                                       N.f32, N.stats, n, (const float *)a_cond.dev,
                                       (const float *)a_noise.dev, seed, id0, steps, integrator,
                                       (float *)a_y.dev, (float *)a_exit.dev, ctx->d_err,
-                                      (float *)ctx->bias1.ptr, fp8 ? N.d_tc8_scale : nullptr);
+                                      (float *)ctx->bias1.ptr, fp8 ? N.d_tc8_scale : nullptr,
+                                      ctx->cfg.sampler_kernel);
     if (e != cudaSuccess) return cuda_error(ctx, e, "launch_sampler_tc");
   }
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, a_y));
@@ -636,11 +649,13 @@ gmc_status analog_transmit(gmc_ctx *ctx, int64_t n, const float *xi, const float
   GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 5, o_status));
   GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 6, o_exit));
   GMC_CUDA_TRY(ctx, stage_out_prepare(ctx, 7, o_ncoll));
+  GMC_CUDA_TRY(ctx, ensure(ctx->walk_next, sizeof(unsigned long long)));
   GMC_CUDA_TRY(ctx, launch_analog(ctx->stream, n, (const float *)in[0].dev, (const float *)in[1].dev,
                                   (const float *)in[2].dev, (const float *)in[3].dev,
                                   (const float *)in[4].dev, mode, seed, id0, event0,
                                   (int32_t *)o_status.dev, (float *)o_exit.dev,
-                                  (uint32_t *)o_ncoll.dev));
+                                  (uint32_t *)o_ncoll.dev,
+                                  (unsigned long long *)ctx->walk_next.ptr));
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_status));
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_exit));
   GMC_CUDA_TRY(ctx, stage_out_finish(ctx, o_ncoll));

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -86,6 +87,8 @@ struct gmc_ctx {
   gmc::Buffer stage[9];
   // per-evaluation layer-1 bias of the tensor-core sampler
   gmc::Buffer bias1;
+  // work counter of the persistent random-walk kernels (8 bytes)
+  gmc::Buffer walk_next;
   // transport_solve engine (kept between calls) and the serving thread
   gmc::Engine *solver = nullptr;
   gmc::Server *server = nullptr;
@@ -109,6 +112,31 @@ cudaError_t ensure(Buffer &b, size_t bytes);
     if (e__ != cudaSuccess) return ::gmc::cuda_error(ctx, e__, #expr); \
   } while (0)
 
+// Blocks of a persistent launch of `kernel` with `threads` threads per block
+// and no dynamic shared memory: as many as are resident on the current device
+// at once (occupancy queried once per device and kernel), at most
+// ceil(items / threads).
+template <typename Kernel>
+unsigned persistent_blocks(Kernel kernel, int threads, int64_t items) {
+  static std::atomic<int> cached[kMaxDevices];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int fit = (dev >= 0 && dev < kMaxDevices) ? cached[dev].load(std::memory_order_relaxed) : 0;
+  if (fit < 1) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    fit = per_sm * (sms > 0 ? sms : 1);
+    if (dev >= 0 && dev < kMaxDevices) cached[dev].store(fit, std::memory_order_relaxed);
+  }
+  const int64_t need = (items + threads - 1) / threads;
+  return (unsigned)(need < fit ? (need > 0 ? need : 1) : fit);
+}
+
 // Launchers implemented in the kernel translation units. All are
 // asynchronous on `stream` and take device pointers only.
 cudaError_t launch_philox(cudaStream_t stream, int64_t n, uint64_t seed, uint64_t id0,
@@ -118,10 +146,12 @@ cudaError_t launch_normals(cudaStream_t stream, int64_t n, uint64_t seed, uint64
 cudaError_t launch_sampler_f32(cudaStream_t stream, const NetF32 &net, const NetStats &st,
                                int64_t n, const float *cond, const float *noise, uint64_t seed,
                                uint64_t id0, int steps, int integrator, float *y_raw, float *exit);
+// next: 8 bytes of device scratch (the persistent kernel's work counter),
+// cleared by the launcher.
 cudaError_t launch_analog(cudaStream_t stream, int64_t n, const float *xi, const float *cos_in,
                           const float *sin_in, const float *tau, const float *c, int mode,
                           uint64_t seed, uint64_t id0, uint32_t event0, int32_t *status,
-                          float *exit, uint32_t *ncoll);
+                          float *exit, uint32_t *ncoll, unsigned long long *next);
 cudaError_t launch_analog_rect(cudaStream_t stream, int64_t n, const float *xi, const float *cos_in,
                                const float *sin_in, const float *tx, const float *ty,
                                const float *c, int mode, uint64_t seed, uint64_t id0,
@@ -150,11 +180,13 @@ void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *pack
 void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
                       float *bias_host, float *scale_host);
 // packed: from tc_pack_host (fp8_scale null) or tc_pack_host_fp8 (fp8_scale =
-// its [3][256] scales on the device).
+// its [3][256] scales on the device). kernel: gmc_sampler_kernel of the BF16
+// path (GMC_KERNEL_PAIR: sampler_pair.cu).
 cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const float *bias,
                               const NetF32 &f32, const NetStats &st, int64_t n, const float *cond,
                               const float *noise, uint64_t seed, uint64_t id0, int steps,
                               int integrator, float *y_raw, float *exit, int *err,
-                              float *bias1_scratch, const float *fp8_scale);
+                              float *bias1_scratch, const float *fp8_scale,
+                              int kernel = GMC_KERNEL_TILE);
 
 }  // namespace gmc

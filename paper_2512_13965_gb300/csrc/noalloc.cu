@@ -92,7 +92,7 @@ extern "C" gmc_status gmc_transmit_noalloc(gmc_ctx *ctx, int64_t n, const float 
   if (st != GMC_OK) return st;
   e = launch_sampler_tc(ctx->stream, ctx->net.d_tc, ctx->net.d_tc_bias, ctx->net.f32, ctx->net.stats, n, cond,
                         noise, seed, id0, steps, integrator, y_raw, exit, ctx->d_err, scratch,
-                        nullptr);
+                        nullptr, ctx->cfg.sampler_kernel);
   if (e != cudaSuccess) return cuda_error(ctx, e, "gmc_transmit_noalloc launch");
   return GMC_OK;
 }

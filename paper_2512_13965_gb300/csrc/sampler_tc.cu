@@ -62,21 +62,20 @@
 #include "decode.cuh"
 #include "gmc_internal.cuh"
 #include "philox.cuh"
+#include "sampler_common.cuh"
 #include "tc_ptx.cuh"
 
 namespace gmc {
 namespace {
 
 using namespace ptx;
+using namespace smp;
 
 constexpr int TM = 128;
 constexpr int EPI_WARPS = 16;                 // two groups of 8, one per 128 output columns
 constexpr int GROUP_WARPS = EPI_WARPS / 2;    // 2 per TMEM lane quadrant, 64 columns each
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
 constexpr int NH = 128;                       // output columns of one epilogue group
-// Weight chunk: all 256 output rows x 128 bytes of K (64 BF16 or 128 E4M3
-// inputs), K-major, 128-byte swizzle; 32 KB.
-constexpr uint32_t CHUNK = 256u * 128u;
 constexpr int MMAS_PER_CHUNK = 4;             // 32 bytes of K per MMA
 #ifndef GMC_TC_STAGES
 #define GMC_TC_STAGES 5
@@ -85,22 +84,6 @@ constexpr int NST = GMC_TC_STAGES;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t COL_A = 0;                 // + 128 T: operand of tile T
 constexpr uint32_t COL_D = 256;               // the 128 x 256 FP32 accumulator
-
-// packed global operand buffer (bytes): hidden-layer chunks, then the BF16
-// operands of layers 1 and 5
-template <bool FP8>
-struct Packed {
-  static constexpr int NCH = 256 * (FP8 ? 1 : 2) / 128;  // chunks per hidden layer
-  static constexpr size_t OFF_HID = 0;                  // [layer 0..2][chunk] x CHUNK
-  static constexpr size_t OFF_B1 = 3 * (size_t)NCH * CHUNK;  // 256 rows x 32 B, 32-byte swizzle
-  static constexpr size_t OFF_B5 = OFF_B1 + 8192;       // 4 K-blocks x 16 rows x 128 B
-  // biases of layers 2-4 as one block per layer of 256 rows x 32 B (32-byte
-  // swizzle), K = 16 with the bias in columns 13 (BF16 value) and 14 (BF16
-  // remainder), the others zero: b/2 (BF16 variant) or b/s_c (FP8 variant,
-  // whose epilogue multiplies the accumulator by s_c/2)
-  static constexpr size_t OFF_BIAS = OFF_B5 + 8192;
-  static constexpr size_t BYTES = OFF_BIAS + 24576;
-};
 
 // shared memory (offsets from a 1024-byte aligned base)
 constexpr uint32_t S_A1 = 0;                     // layer-1 operands of tiles X, Y: 2 x 4 KB
@@ -128,121 +111,9 @@ struct Bars {
 };
 static_assert(sizeof(Bars) <= 256, "barrier block");
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  uint32_t u;
-  memcpy(&u, &v, 4);
-  return u;
-}
-
-// SiLU on two pre-activations already halved (the packed weights and biases
-// of layers 1-4 carry a factor 1/2, exact in BF16): with h = z/2,
-// SiLU(z) = z sigmoid(z) = h + h tanh(h). Packed BF16x2: one MUFU op and one
-// FMA for two outputs, already in the operand format of the next layer.
-__device__ __forceinline__ uint32_t silu2_halved(float h0, float h1) {
-  uint32_t h, t, o;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(h1), "f"(h0));
-  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
-  asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(o) : "r"(h), "r"(t));
-  return o;
-}
-
-// As silu2_halved, rounded to two E4M3 codes (low byte from h0): the SiLU in
-// packed FP16 (11-bit significand, so the E4M3 rounding sees an accurate
-// value), then one saturating conversion.
-__device__ __forceinline__ uint32_t silu2_halved_e4m3(float h0, float h1) {
-  const __half2 hh = __floats2half2_rn(h0, h1);
-  uint32_t h, t, o;
-  memcpy(&h, &hh, 4);
-  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
-  asm("fma.rn.f16x2 %0, %1, %2, %1;" : "=r"(o) : "r"(h), "r"(t));
-  __half2_raw raw;
-  raw.x = (unsigned short)(o & 0xFFFFu);
-  raw.y = (unsigned short)(o >> 16);
-  return (uint32_t)__nv_cvt_halfraw2_to_fp8x2(raw, __NV_SATFINITE, __NV_E4M3);
-}
-
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
-                                             uint32_t d) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
-               "r"(d)
-               : "memory");
-}
-
-// 16 B chunk `c` (0..1) of row `r` in a 32-byte-swizzled block.
-__device__ __forceinline__ uint32_t sw32(uint32_t base, int r, int c) {
-  return base + (uint32_t)((r >> 3) * 256 + (r & 7) * 32 + ((c ^ ((r >> 2) & 1)) << 4));
-}
-
 __device__ void fail(Bars &b, int *err, int code) {
   b.abort = 1;
   atomicExch(err, code);
-}
-
-// Layer-1 operand row: [x_hi0..3, x_lo0..3 | cn0..cn4, 1, 1, 0] in BF16. The
-// normalized condition (second 16 bytes) is written once per tile; every
-// evaluation rewrites only the ODE state (first 16 bytes). Layer 1's weights
-// are zero in columns 13-14; the bias blocks of layers 2-4 use them.
-__device__ __forceinline__ void write_a1_cond(uint32_t a_base, int r, const float (&cn)[kCond]) {
-  st_shared_v4(sw32(a_base, r, 1), pack_bf16x2(cn[0], cn[1]), pack_bf16x2(cn[2], cn[3]),
-               pack_bf16x2(cn[4], 1.0f), pack_bf16x2(1.0f, 0.0f));
-}
-
-__device__ __forceinline__ void write_a1_x(uint32_t a_base, int r, const float (&x)[4]) {
-  float hi[4], lo[4];
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    hi[d] = __bfloat162float(__float2bfloat16_rn(x[d]));
-    lo[d] = x[d] - hi[d];
-  }
-  st_shared_v4(sw32(a_base, r, 0), pack_bf16x2(hi[0], hi[1]), pack_bf16x2(hi[2], hi[3]),
-               pack_bf16x2(lo[0], lo[1]), pack_bf16x2(lo[2], lo[3]));
-}
-
-// Halved pre-activations of 4 accumulator columns: acc + bias.
-__device__ __forceinline__ float4 pre4(const uint32_t *p, const float4 *b4, int q) {
-  const float4 b = __ldg(b4 + q);
-  return make_float4(__uint_as_float(p[0]) + b.x, __uint_as_float(p[1]) + b.y,
-                     __uint_as_float(p[2]) + b.z, __uint_as_float(p[3]) + b.w);
-}
-
-
-// Epilogue pre-activation modes: the bias already in the accumulator (layers
-// 2-4, whose biases enter through the MMA), bias added here (layer 1, whose
-// bias depends on t), or a per-channel scale (FP8 layers 2-4, bias already in
-// the accumulator in units of that scale).
-enum : int { kPreNone = 0, kPreBias = 1, kPreScale = 2 };
-
-// SiLU of one thread's 16 accumulator columns starting at col0, packed as the
-// next layer's operand: 8 BF16x2 words or, with OUT8, 4 words of four E4M3
-// codes (low byte first).
-template <int MODE, bool OUT8>
-__device__ __forceinline__ void silu16(const uint32_t *v, const float *__restrict__ bias,
-                                       const float *__restrict__ scale, int col0, uint32_t (&w)[8]) {
-  const float4 *b4 = reinterpret_cast<const float4 *>(bias + col0);
-  const float4 *s4 = reinterpret_cast<const float4 *>(scale + col0);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    float4 z;
-    if constexpr (MODE == kPreNone) {
-      z = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                      __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
-    } else {
-      if constexpr (MODE == kPreScale) {
-        const float4 sc = __ldg(s4 + q);
-        z = make_float4(__uint_as_float(v[4 * q]) * sc.x, __uint_as_float(v[4 * q + 1]) * sc.y,
-                        __uint_as_float(v[4 * q + 2]) * sc.z, __uint_as_float(v[4 * q + 3]) * sc.w);
-      } else {
-        z = pre4(v + 4 * q, b4, q);
-      }
-    }
-    if constexpr (OUT8) {
-      w[q] = silu2_halved_e4m3(z.x, z.y) | (silu2_halved_e4m3(z.z, z.w) << 16);
-    } else {
-      w[2 * q] = silu2_halved(z.x, z.y);
-      w[2 * q + 1] = silu2_halved(z.z, z.w);
-    }
-  }
 }
 
 // One 16-column piece of layer L's epilogue: activations of accumulator
@@ -270,21 +141,6 @@ __device__ __forceinline__ void epi_piece(int L, const uint32_t *v, const float 
   }
   tmem_st8(a_row + (uint32_t)(col0 >> 1), w);
 }
-
-struct Params {
-  const unsigned char *packed;
-  const float *bias;    // [5][256]: rows 1..3 = b2..b4, row 4 = b5
-  const float *bias1;   // [n_eval][256]: W1[:, emb] emb(t_e) + b1
-  const float *scale;   // FP8 only: [3][256] per-output-channel scales of W2..W4, halved
-  NetStats st;
-  int64_t n;
-  const float *cond;
-  const float *noise;
-  uint64_t seed, id0;
-  int steps, integrator, n_eval;
-  float *y_raw, *exitp;
-  int *err;
-};
 
 // INTEG: the integrator (GMC_EULER, GMC_MIDPOINT, GMC_RK4) as a compile-time
 // choice, so an Euler kernel holds no midpoint or RK4 state in registers.
@@ -824,7 +680,7 @@ cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const flo
                               const NetF32 &f32, const NetStats &st, int64_t n, const float *cond,
                               const float *noise, uint64_t seed, uint64_t id0, int steps,
                               int integrator, float *y_raw, float *exit, int *err,
-                              float *bias1_scratch, const float *fp8_scale) {
+                              float *bias1_scratch, const float *fp8_scale, int kernel) {
   if (n <= 0) return cudaSuccess;
   const int n_eval = integrator == GMC_RK4 ? 4 * steps : (integrator == GMC_MIDPOINT ? 2 * steps : steps);
   layer1_bias_kernel<<<n_eval, kHidden, 0, stream>>>(f32.w1t, f32.b1, steps, integrator, n_eval,
@@ -856,6 +712,7 @@ cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const flo
     if (integrator == GMC_MIDPOINT) return launch_tc<true, GMC_MIDPOINT>(stream, p, sms);
     return launch_tc<true, GMC_EULER>(stream, p, sms);
   }
+  if (kernel == GMC_KERNEL_PAIR) return launch_sampler_pair(stream, p, sms);
   if (integrator == GMC_RK4) return launch_tc<false, GMC_RK4>(stream, p, sms);
   if (integrator == GMC_MIDPOINT) return launch_tc<false, GMC_MIDPOINT>(stream, p, sms);
   return launch_tc<false, GMC_EULER>(stream, p, sms);

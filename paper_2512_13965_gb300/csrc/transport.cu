@@ -91,21 +91,27 @@ struct Slot {
   const float *tau, *c;
   double *flux;
   uint64_t seed;
+  // GMC solves, per cell: the networks' condition (ln tau', c'), the factor
+  // c'/c of a sampled track length (scattering-equivalent condition, 1 inside
+  // the training box), and whether the random walk crosses the cell instead
+  // (no equivalent condition, or thinner than gmc_min_tau)
+  const float *ltau_n, *c_n, *s_scale;
+  const uint8_t *walk;
 };
 
 struct Rules {
   float w_cut, p_survive;
 };
 
-// Where stage 4 appends the survivors: the face bank, or, for a destination
-// cell thinner than min_tau in a GMC solve that walks thin cells (0: never),
-// the bank of face particles the random walk transmits.
+// Where stage 4 appends the survivors: the face bank, or, in a GMC solve
+// (gmc set) for a destination cell the random walk crosses (Slot::walk), the
+// bank of face particles the random walk transmits.
 struct Route {
   Bank out;
   int *count;
   Bank thin;
   int *thin_count;
-  float min_tau;
+  bool gmc;
 };
 
 // rotate (ux, uy) by k quarter turns counter-clockwise
@@ -200,7 +206,7 @@ __device__ void finish_transmission(const Exit &x, const Slot *__restrict__ slot
         keep = true;
         ncell = nj * S.nx + ni;
         nface = (x.gface + 2) & 3;
-        thin = rt.min_tau > 0.0f && S.tau[ncell] < rt.min_tau;
+        thin = rt.gmc && S.walk[ncell] != 0;
       }
     }
   }
@@ -327,21 +333,42 @@ __global__ void birth_kernel(int slot, int64_t first, int64_t count, const doubl
 // through the boundary), and joins the face bank at base + k with weight 1.
 __global__ void birth_wall_kernel(int slot, int64_t first, int64_t count,
                                   const double *__restrict__ cdf, double total,
-                                  const Slot *__restrict__ slots, Bank out, int64_t base) {
+                                  const Slot *__restrict__ slots, Route rt, int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= count) return;
+  const bool valid = k < count;
   const Slot S = slots[slot];
-  const uint64_t h = (uint64_t)(first + k);
-  const uint4 r = philox_draw(S.seed, h, 0u, kTagBirth);
-  const double u0 = ((double)r.x + 1.0) * (1.0 / 4294967296.0);
-  const int j = (int)cdf_search(cdf, (int64_t)S.ny, u0 * total);
-  const float sn = 2.0f * u01(r.z) - 1.0f;
-  const int64_t o = base + k;
+  uint64_t h = 0;
+  int cell = 0;
+  float xi = 0.0f, sn = 0.0f;
+  bool thin = false;
+  if (valid) {
+    h = (uint64_t)(first + k);
+    const uint4 r = philox_draw(S.seed, h, 0u, kTagBirth);
+    const double u0 = ((double)r.x + 1.0) * (1.0 / 4294967296.0);
+    const int j = (int)cdf_search(cdf, (int64_t)S.ny, u0 * total);
+    cell = j * S.nx;
+    xi = u01(r.y);
+    sn = 2.0f * u01(r.z) - 1.0f;
+    thin = rt.gmc && S.walk[cell] != 0;  // a cell the random walk crosses
+  }
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const unsigned mask_f = __ballot_sync(0xffffffffu, valid && !thin);
+  const unsigned mask_t = __ballot_sync(0xffffffffu, valid && thin);
+  int base_f = 0, base_t = 0;
+  if (lane == 0 && mask_f) base_f = atomicAdd(rt.count, __popc(mask_f));
+  if (lane == 0 && mask_t) base_t = atomicAdd(rt.thin_count, __popc(mask_t));
+  if (lane == 0 && (mask_f | mask_t)) atomicAdd(&slot_live[slot], __popc(mask_f | mask_t));
+  base_f = __shfl_sync(0xffffffffu, base_f, 0);
+  base_t = __shfl_sync(0xffffffffu, base_t, 0);
+  if (!valid) return;
+  const Bank out = thin ? rt.thin : rt.out;
+  const int64_t o = thin ? base_t + __popc(mask_t & below) : base_f + __popc(mask_f & below);
   out.hist[o] = h;
   out.slot[o] = slot;
-  out.cell[o] = j * S.nx;
+  out.cell[o] = cell;
   out.face[o] = 3;
-  out.xi[o] = u01(r.y);
+  out.xi[o] = xi;
   out.gx[o] = sqrtf(fmaxf(1.0f - sn * sn, 0.0f));
   out.gy[o] = sn;
   out.w[o] = 1.0f;
@@ -367,49 +394,111 @@ __device__ __forceinline__ void settle(const WalkResult &wr, const WalkState &ws
   x.ncoll = wr.ncoll;
 }
 
-// Up to `cap` more flights of every walk in progress.
-__global__ void inside_walk_kernel(int64_t live, IBank in, const Slot *__restrict__ slots, Rules R,
-                                   uint32_t cap, Route rt, IBank iout, int *in_count, DevStats *st,
-                                   int *slot_live) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  Exit x;
-  x.active = false;
-  x.slot = 0;
-  bool park = false;
+// Up to `cap` more flights of every walk in progress (FROM_FACE false: the
+// inside bank `iin`), or the start of the walk of every face particle
+// through its cell (FROM_FACE true: the face bank `fin`; the ANALOG method
+// and the thin cells of a hybrid GMC solve) in the cell's own
+// (global-oriented) frame, entering at the point its entry face and xi give.
+// A walk that leaves its cell does stages 3-4; one cut by the cap is parked
+// in `iout` for the next wave. Persistent, with lane refill (walk.cuh): the
+// lanes claim particles from *next in rounds of kWalkRound flights, and the
+// warp-collective stage 3-4 and parking run only in rounds where a lane's
+// walk ended.
+constexpr int kWalkThreads = 256;
+
+template <bool FROM_FACE>
+__global__ void __launch_bounds__(kWalkThreads) walk_wave_kernel(
+    int64_t live, Bank fin, IBank iin, const Slot *__restrict__ slots, Rules R, uint32_t cap,
+    Route rt, IBank iout, int *in_count, DevStats *st, int *slot_live, unsigned long long *next) {
+  int64_t k = live;  // this lane's particle (live: none)
+  bool drained = false;
   WalkState ws{};
   int slot = 0, cell = 0;
-  uint64_t h = 0;
-  float w = 0.0f;
-  if (k < live) {
-    slot = in.slot[k];
-    const Slot S = slots[slot];
-    cell = in.cell[k];
-    h = in.hist[k];
-    w = in.w[k];
-    ws.x = in.x[k];
-    ws.y = in.y[k];
-    ws.s = in.s[k];
-    ws.ux = in.ux[k];
-    ws.uy = in.uy[k];
-    ws.event = in.ev[k];
-    ws.ncoll = in.ncoll[k];
-    const WalkResult wr = walk_cell_resume(S.tau[cell], S.c[cell], 1, ws, cap, S.seed, h);
-    settle(wr, ws, slot, h, cell, w, x, park);
+  uint64_t h = 0, seed = 0;
+  float w = 0.0f, tau = 0.0f, cc = 0.0f;
+  uint32_t budget = 0;
+  for (;;) {
+    const bool need = k == live && !drained;
+    if (__any_sync(0xffffffffu, need)) {
+      const int64_t kk = warp_claim(need, next, live);
+      if (need) {
+        if (kk < live) {
+          k = kk;
+          if constexpr (FROM_FACE) {
+            slot = fin.slot[k];
+            cell = fin.cell[k];
+            h = fin.hist[k];
+            w = fin.w[k];
+          } else {
+            slot = iin.slot[k];
+            cell = iin.cell[k];
+            h = iin.hist[k];
+            w = iin.w[k];
+          }
+          const Slot S = slots[slot];
+          tau = S.tau[cell];
+          cc = S.c[cell];
+          seed = S.seed;
+          budget = cap;
+          if constexpr (FROM_FACE) {
+            // point on face F with counter-clockwise parameter 1 - xi
+            const float xi = fin.xi[k];
+            float X, Y;
+            switch (fin.face[k]) {
+              case 0: X = 1.0f - xi; Y = 0.0f; break;
+              case 1: X = 1.0f; Y = 1.0f - xi; break;
+              case 2: X = xi; Y = 1.0f; break;
+              default: X = 0.0f; Y = xi; break;
+            }
+            ws = walk_start(tau, X, Y, fin.gx[k], fin.gy[k], fin.ev[k]);
+          } else {
+            ws.x = iin.x[k];
+            ws.y = iin.y[k];
+            ws.s = iin.s[k];
+            ws.ux = iin.ux[k];
+            ws.uy = iin.uy[k];
+            ws.event = iin.ev[k];
+            ws.ncoll = iin.ncoll[k];
+          }
+        } else {
+          drained = true;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, k < live)) break;
+    bool ended = false;
+    WalkResult wr;
+    if (k < live) {
+      const uint32_t r = budget < kWalkRound ? budget : kWalkRound;
+      wr = walk_cell_resume(tau, cc, 1, ws, r, seed, h);
+      budget -= r;
+      ended = wr.status != kTruncated || budget == 0 || ws.ncoll >= kMaxFlights;
+    }
+    if (__any_sync(0xffffffffu, ended)) {
+      Exit x;
+      x.active = false;
+      x.slot = 0;
+      bool park = false;
+      if (ended) settle(wr, ws, slot, h, cell, w, x, park);
+      finish_transmission(x, slots, R, rt, st, slot_live);
+      append_inside(ended && park, slot, h, cell, ws, w, iout, in_count, slot_live);
+      if (ended) k = live;
+    }
   }
-  finish_transmission(x, slots, R, rt, st, slot_live);
-  append_inside(park, slot, h, cell, ws, w, iout, in_count, slot_live);
 }
 
 // GMC births with the internal model, stage 1: rows base .. base+count-1 of
 // the birth batch (row stride M): history, request and cell, the internal
 // condition (X, Y, ln tau, c, min(X, Y, 1 - X, 1 - Y)) and z ~ N(0, I) at
-// (id, 0, tag 2). Birth point and cell are those of birth_kernel. A birth in
-// a cell thinner than min_tau starts a random walk in the inside bank
-// instead (direction from the same draw) and its batch row is marked unused.
+// (id, 0, tag 2). Birth point and cell are those of birth_kernel; the
+// condition takes the cell's network condition (ln tau', c'). A birth in a
+// cell the random walk crosses (Slot::walk) starts a random walk in the
+// inside bank instead (direction from the same draw) and its batch row is
+// marked unused.
 __global__ void birth_gmc_kernel(int slot, int64_t first, int64_t count, int64_t base, int64_t M,
                                  const double *__restrict__ cdf, double total,
                                  const Slot *__restrict__ slots, uint64_t *bhist, int32_t *bslot,
-                                 int32_t *bcell, float *cond, float *noise, float min_tau,
+                                 int32_t *bcell, float *cond, float *noise,
                                  IBank iout, int *in_count, int *slot_live) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool walk = false;
@@ -427,12 +516,12 @@ __global__ void birth_gmc_kernel(int slot, int64_t first, int64_t count, int64_t
     const int64_t row = base + k;
     bhist[row] = h;
     bcell[row] = cell;
-    walk = tau < min_tau;
+    walk = S.walk[cell] != 0;
     bslot[row] = walk ? -1 : slot;
     cond[row] = X;
     cond[M + row] = Y;
-    cond[2 * M + row] = logf(tau);
-    cond[3 * M + row] = S.c[cell];
+    cond[2 * M + row] = S.ltau_n[cell];
+    cond[3 * M + row] = S.c_n[cell];
     cond[4 * M + row] = fminf(fminf(X, Y), fminf(1.0f - X, 1.0f - Y));
     const float4 z = box_muller4(philox_draw(S.seed, h, 0u, kTagNoise));
     noise[row] = z.x;
@@ -470,51 +559,11 @@ __global__ void birth_gmc_post_kernel(int64_t M, const uint64_t *__restrict__ bh
     x.gx = ex[M + k];
     x.gy = ex[2 * M + k];
     x.w = 1.0f;
-    x.s = ex[3 * M + k];
+    x.s = ex[3 * M + k] * slots[x.slot].s_scale[x.cell];
     x.ev = 1u;  // event 0 held the birth draw and the noise
     x.ncoll = 0;
   }
   finish_transmission(x, slots, R, rt, st, slot_live);
-}
-
-// ANALOG: start the walk of each face particle through its cell in the
-// cell's own (global-oriented) frame, entering at the point its entry face
-// and xi give; up to `cap` flights, then as inside_walk_kernel.
-__global__ void analog_wave_kernel(int64_t live, Bank in, const Slot *__restrict__ slots, Rules R,
-                                   uint32_t cap, Route rt, IBank iout, int *in_count, DevStats *st,
-                                   int *slot_live) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  Exit x;
-  x.active = false;
-  x.slot = 0;
-  bool park = false;
-  WalkState ws{};
-  int slot = 0, cell = 0;
-  uint64_t h = 0;
-  float w = 0.0f;
-  if (k < live) {
-    slot = in.slot[k];
-    const Slot S = slots[slot];
-    cell = in.cell[k];
-    const int F = in.face[k];
-    const float xi = in.xi[k];
-    // point on face F with counter-clockwise parameter 1 - xi
-    float X, Y;
-    switch (F) {
-      case 0: X = 1.0f - xi; Y = 0.0f; break;
-      case 1: X = 1.0f; Y = 1.0f - xi; break;
-      case 2: X = xi; Y = 1.0f; break;
-      default: X = 0.0f; Y = xi; break;
-    }
-    h = in.hist[k];
-    w = in.w[k];
-    const float tau = S.tau[cell];
-    ws = walk_start(tau, X, Y, in.gx[k], in.gy[k], in.ev[k]);
-    const WalkResult wr = walk_cell_resume(tau, S.c[cell], 1, ws, cap, S.seed, h);
-    settle(wr, ws, slot, h, cell, w, x, park);
-  }
-  finish_transmission(x, slots, R, rt, st, slot_live);
-  append_inside(park, slot, h, cell, ws, w, iout, in_count, slot_live);
 }
 
 // GMC stage 1 and the noise of stage 2.
@@ -529,8 +578,8 @@ __global__ void gmc_prep_kernel(int64_t live, Bank in, const Slot *__restrict__ 
   cond[k] = in.xi[k];
   cond[live + k] = ux;
   cond[2 * live + k] = uy;
-  cond[3 * live + k] = logf(S.tau[cell]);
-  cond[4 * live + k] = S.c[cell];
+  cond[3 * live + k] = S.ltau_n[cell];
+  cond[4 * live + k] = S.c_n[cell];
   const float4 z = box_muller4(philox_draw(S.seed, in.hist[k], in.ev[k], kTagNoise));
   noise[k] = z.x;
   noise[live + k] = z.y;
@@ -560,7 +609,7 @@ __global__ void gmc_post_kernel(int64_t live, Bank in, const float *__restrict__
     x.gx = ux;
     x.gy = uy;
     x.w = in.w[k];
-    x.s = ex[3 * live + k];
+    x.s = ex[3 * live + k] * slots[x.slot].s_scale[x.cell];
     x.ev = in.ev[k] + 1u;
     x.ncoll = 0;
   }
@@ -617,6 +666,8 @@ struct Request {
   int nx = 0, ny = 0;
   int64_t ncell = 0;
   std::vector<float> tau, c;
+  std::vector<float> ltau_n, c_n, s_scale;  // network condition and track-length factor
+  std::vector<uint8_t> walk;                // cells the random walk crosses (GMC)
   std::vector<double> cdf;
   double total = 0.0;
   int64_t n_hist = 0;
@@ -631,6 +682,8 @@ struct Request {
   size_t pool_off = 0, footprint = 0;
   double *d_cdf = nullptr, *d_flux = nullptr;
   float *d_tau = nullptr, *d_c = nullptr;
+  float *d_ltau_n = nullptr, *d_c_n = nullptr, *d_s_scale = nullptr;
+  uint8_t *d_walk = nullptr;
   // result
   std::vector<double> flux;
   gmc_solve_stats st{};
@@ -640,7 +693,34 @@ struct Request {
   cudaEvent_t ev0 = nullptr;
 };
 
-size_t request_footprint(int64_t ncell) { return 2 * align256(ncell * 4) + 2 * align256(ncell * 8); }
+// Device bytes of one request: tau, c, ln tau', c', c'/c (float), walk flags
+// (byte), source CDF and FP64 tally.
+size_t request_footprint(int64_t ncell) {
+  return 5 * align256(ncell * 4) + align256(ncell) + 2 * align256(ncell * 8);
+}
+
+// The scattering-equivalent condition of a cell (tau, c) in the training box
+// [t_lo, t_hi] x [c_lo, c_hi] of the networks. The networks learn the
+// implicit-capture walk (flights at rate c, absorption applied afterwards as
+// exp(-(1 - c) s), Eq. 4-5), which in a cell of side tau is the walk at rate
+// 1 in a cell of side c tau with every length divided by c: a cell (tau', c')
+// with c' tau' = c tau has the same exits, and s = s' c' / c. Inside the box
+// (tau', c') = (tau, c); outside, c' is the value of [max(c_lo, c tau / t_hi),
+// min(c_hi, c tau / t_lo)] nearest c and tau' = c tau / c' (clamped into the
+// box against rounding). Returns false where that interval is empty or
+// c tau = 0: no equivalent.
+bool equivalent_condition(double tau, double c, double t_lo, double t_hi, double c_lo,
+                          double c_hi, double *tau_n, double *c_n) {
+  *tau_n = tau;
+  *c_n = c;
+  if (tau >= t_lo && tau <= t_hi && c >= c_lo && c <= c_hi) return true;
+  const double w = c * tau;
+  const double lo = std::max(c_lo, w / t_hi), hi = std::min(c_hi, w / t_lo);
+  if (!(w > 0.0) || !(lo <= hi)) return false;
+  *c_n = std::min(std::max(c, lo), std::max(lo, hi));
+  *tau_n = std::min(std::max(w / *c_n, t_lo), t_hi);
+  return true;
+}
 
 // Validates a solve description and copies it into a Request.
 // wall: `source` holds ny strengths of a surface source on the left boundary
@@ -665,10 +745,6 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
   for (int64_t k = 0; k < ncell; ++k) {
     if (!(tau[k] > 0.0f) || !std::isfinite(tau[k]) || !(c[k] >= 0.0f && c[k] <= 1.0f))
       return set_error(ctx, GMC_EINVAL, "solve: cell %lld needs tau > 0, c in [0,1]", (long long)k);
-    if (method == GMC_METHOD_GMC && (tau[k] < 0.05f || tau[k] > 2000.0f || c[k] < 0.4f))
-      return set_error(ctx, GMC_EINVAL,
-                       "solve: cell %lld outside the sampler's range (tau in [0.05, 2000], c >= 0.4)",
-                       (long long)k);
     if (wall) continue;
     if (!(source[k] >= 0.0f) || !std::isfinite(source[k]))
       return set_error(ctx, GMC_EINVAL, "solve: source must be finite and >= 0");
@@ -680,6 +756,23 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
       return set_error(ctx, GMC_EINVAL, "solve: wall source must be finite and >= 0");
     acc += source[j] > 0.0f ? (double)source[j] : 0.0;
     R.cdf[j] = acc;
+  }
+  // the networks' condition per cell (GMC): the scattering-equivalent one,
+  // or the random walk where there is none or the cell is thinner than
+  // gmc_min_tau; FP64 on the host
+  const gmc_config &cf = ctx->cfg;
+  R.ltau_n.resize(ncell);
+  R.c_n.resize(ncell);
+  R.s_scale.resize(ncell);
+  R.walk.assign(ncell, 0);
+  for (int64_t k = 0; k < ncell; ++k) {
+    double tn, cn;
+    const bool ok = equivalent_condition((double)tau[k], (double)c[k], cf.net_tau_lo, cf.net_tau_hi,
+                                         cf.net_c_lo, cf.net_c_hi, &tn, &cn);
+    R.ltau_n[k] = (float)std::log(tn);
+    R.c_n[k] = (float)cn;
+    R.s_scale[k] = ok ? (float)(cn / (double)c[k]) : 1.0f;
+    R.walk[k] = (!ok || (cf.gmc_min_tau > 0.0 && (double)tau[k] < cf.gmc_min_tau)) ? 1 : 0;
   }
   R.wall = wall;
   if (n_histories > 0 && !(acc > 0.0)) return set_error(ctx, GMC_EINVAL, "solve: zero source");
@@ -753,7 +846,7 @@ class Engine {
     cudaStreamSynchronize(s_);
     void *bufs[] = {bank_mem_[0], bank_mem_[1], ibank_mem_[0], ibank_mem_[1], tbank_mem_[0],
                     tbank_mem_[1], d_cond_, d_noise_, d_exit_, d_slots_, d_stats_, d_counts_,
-                    d_bias1_, d_bmeta_};
+                    d_bias1_, d_bmeta_, d_next_};
     for (void *b : bufs)
       if (b) cudaFree(b);
     if (h_counts_) cudaFreeHost(h_counts_);
@@ -777,6 +870,7 @@ class Engine {
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_slots_, kMaxSlots * sizeof(Slot)));
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_stats_, kMaxSlots * sizeof(DevStats)));
     GMC_CUDA_TRY(ctx_, cudaMalloc(&d_counts_, kCounts * sizeof(int)));
+    GMC_CUDA_TRY(ctx_, cudaMalloc(&d_next_, 3 * sizeof(unsigned long long)));
     GMC_CUDA_TRY(ctx_, cudaMallocHost(&h_counts_, kCounts * sizeof(int)));
     bank_[0] = carve(bank_mem_[0], C_);
     bank_[1] = carve(bank_mem_[1], C_);
@@ -811,13 +905,23 @@ class Engine {
     char *p = pool_.base() + off;
     const int64_t n = R->ncell;
     R->pool_off = off;
+    const size_t a4 = align256(n * 4), a8 = align256(n * 8);
     R->d_tau = (float *)p;
-    R->d_c = (float *)(p + align256(n * 4));
-    R->d_cdf = (double *)(p + 2 * align256(n * 4));
-    R->d_flux = (double *)(p + 2 * align256(n * 4) + align256(n * 8));
-    Slot S{R->nx, R->ny, R->d_tau, R->d_c, R->d_flux, R->seed};
+    R->d_c = (float *)(p + a4);
+    R->d_ltau_n = (float *)(p + 2 * a4);
+    R->d_c_n = (float *)(p + 3 * a4);
+    R->d_s_scale = (float *)(p + 4 * a4);
+    R->d_cdf = (double *)(p + 5 * a4);
+    R->d_flux = (double *)(p + 5 * a4 + a8);
+    R->d_walk = (uint8_t *)(p + 5 * a4 + 2 * a8);
+    Slot S{R->nx, R->ny, R->d_tau, R->d_c, R->d_flux, R->seed,
+           R->d_ltau_n, R->d_c_n, R->d_s_scale, R->d_walk};
     cudaError_t e = cudaMemcpyAsync(R->d_tau, R->tau.data(), n * 4, cudaMemcpyHostToDevice, s_);
     if (!e) e = cudaMemcpyAsync(R->d_c, R->c.data(), n * 4, cudaMemcpyHostToDevice, s_);
+    if (!e) e = cudaMemcpyAsync(R->d_ltau_n, R->ltau_n.data(), n * 4, cudaMemcpyHostToDevice, s_);
+    if (!e) e = cudaMemcpyAsync(R->d_c_n, R->c_n.data(), n * 4, cudaMemcpyHostToDevice, s_);
+    if (!e) e = cudaMemcpyAsync(R->d_s_scale, R->s_scale.data(), n * 4, cudaMemcpyHostToDevice, s_);
+    if (!e) e = cudaMemcpyAsync(R->d_walk, R->walk.data(), n, cudaMemcpyHostToDevice, s_);
     if (!e) e = cudaMemcpyAsync(R->d_cdf, R->cdf.data(), n * 8, cudaMemcpyHostToDevice, s_);
     if (!e) e = cudaMemsetAsync(R->d_flux, 0, n * 8, s_);
     if (!e) e = cudaMemcpyAsync(d_slots_ + slot, &S, sizeof(Slot), cudaMemcpyHostToDevice, s_);
@@ -846,7 +950,7 @@ class Engine {
   gmc_status step(std::vector<Request *> &completed) {
     const Rules rules{(float)ctx_->cfg.w_cut, (float)ctx_->cfg.p_survive};
     const uint32_t cap = (uint32_t)ctx_->cfg.flights_per_wave;
-    const float min_tau = method_ == GMC_METHOD_GMC ? (float)ctx_->cfg.gmc_min_tau : 0.0f;
+    const bool gmc = method_ == GMC_METHOD_GMC;
     int *d_face = d_counts_, *d_in = d_counts_ + 1, *d_thin = d_counts_ + 2,
         *d_slot_live = d_counts_ + 3;
     // births: fair share of the free room among requests with histories left
@@ -855,7 +959,10 @@ class Engine {
       if (R && R->next_hist < R->n_hist) ++(R->wall ? pending_wall : pending);
     int64_t room = C_ - live_ - live_in_ - live_thin_;
     if (pending_wall > 0 && room > 0) {
-      // surface-source births enter the current face bank directly
+      // surface-source births enter the current face banks directly (the
+      // random walk's bank for cells it crosses in a GMC solve)
+      GMC_CUDA_TRY(ctx_, set_counts());
+      const Route wroute{bank_[cur_], d_face, tbank_[ctn_], d_thin, gmc};
       int left = pending + pending_wall;
       for (auto *R : reqs_) {
         if (!R || !R->wall || R->next_hist >= R->n_hist) continue;
@@ -863,16 +970,19 @@ class Engine {
         --left;
         if (m <= 0) continue;
         birth_wall_kernel<<<nblocks(m, 256), 256, 0, s_>>>(R->slot, R->next_hist, m, R->d_cdf,
-                                                            R->total, d_slots_, bank_[cur_], live_);
+                                                            R->total, d_slots_, wroute, d_slot_live);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
-        live_ += m;
-        R->live += (int)m;
         R->next_hist += m;
         room -= m;
       }
+      GMC_CUDA_TRY(ctx_, read_counts());
+      live_ = h_counts_[0];
+      live_thin_ = h_counts_[2];
+      for (auto *R : reqs_)
+        if (R) R->live += h_counts_[3 + R->slot];
     }
     if (pending > 0 && room > 0 && method_ == GMC_METHOD_GMC && ctx_->internal.loaded) {
-      const gmc_status sb = births_internal(pending, room, rules, min_tau);
+      const gmc_status sb = births_internal(pending, room, rules);
       if (sb != GMC_OK) return sb;
     } else if (pending > 0 && room > 0) {
       GMC_CUDA_TRY(ctx_, set_counts());
@@ -897,24 +1007,28 @@ class Engine {
     if (live_ + live_in_ + live_thin_ > 0) {
       ++waves_;
       const int nxt = cur_ ^ 1, nin = cin_ ^ 1, ntn = ctn_ ^ 1;
-      const Route route{bank_[nxt], d_face, tbank_[ntn], d_thin, min_tau};
+      const Route route{bank_[nxt], d_face, tbank_[ntn], d_thin, gmc};
       GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_counts_, 0, kCounts * sizeof(int), s_));
+      GMC_CUDA_TRY(ctx_, cudaMemsetAsync(d_next_, 0, 3 * sizeof(unsigned long long), s_));
       if (live_in_ > 0) {
-        inside_walk_kernel<<<nblocks(live_in_, 128), 128, 0, s_>>>(
-            live_in_, ibank_[cin_], d_slots_, rules, cap, route, ibank_[nin], d_in, d_stats_,
-            d_slot_live);
+        walk_wave_kernel<false>
+            <<<persistent_blocks(walk_wave_kernel<false>, kWalkThreads, live_in_), kWalkThreads, 0,
+               s_>>>(live_in_, bank_[cur_], ibank_[cin_], d_slots_, rules, cap, route, ibank_[nin],
+                     d_in, d_stats_, d_slot_live, d_next_);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
       }
       if (live_thin_ > 0) {  // face particles of thin cells in a GMC solve: random walk
-        analog_wave_kernel<<<nblocks(live_thin_, 128), 128, 0, s_>>>(
-            live_thin_, tbank_[ctn_], d_slots_, rules, cap, route, ibank_[nin], d_in, d_stats_,
-            d_slot_live);
+        walk_wave_kernel<true>
+            <<<persistent_blocks(walk_wave_kernel<true>, kWalkThreads, live_thin_), kWalkThreads,
+               0, s_>>>(live_thin_, tbank_[ctn_], ibank_[cin_], d_slots_, rules, cap, route,
+                        ibank_[nin], d_in, d_stats_, d_slot_live, d_next_ + 1);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
       }
       if (live_ > 0 && method_ == GMC_METHOD_ANALOG) {
-        analog_wave_kernel<<<nblocks(live_, 128), 128, 0, s_>>>(live_, bank_[cur_], d_slots_, rules,
-                                                                cap, route, ibank_[nin], d_in,
-                                                                d_stats_, d_slot_live);
+        walk_wave_kernel<true>
+            <<<persistent_blocks(walk_wave_kernel<true>, kWalkThreads, live_), kWalkThreads, 0,
+               s_>>>(live_, bank_[cur_], ibank_[cin_], d_slots_, rules, cap, route, ibank_[nin],
+                     d_in, d_stats_, d_slot_live, d_next_ + 2);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
       } else if (live_ > 0) {
         gmc_prep_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_slots_, d_cond_,
@@ -964,7 +1078,8 @@ class Engine {
       const bool fp8 = cfg.precision == GMC_FP8;
       e = launch_sampler_tc(s_, fp8 ? N.d_tc8 : N.d_tc, N.d_tc_bias, N.f32, N.stats, rows, d_cond_,
                             d_noise_, 0, 0, cfg.steps, cfg.integrator, nullptr, d_exit_,
-                            ctx_->d_err, d_bias1_, fp8 ? N.d_tc8_scale : nullptr);
+                            ctx_->d_err, d_bias1_, fp8 ? N.d_tc8_scale : nullptr,
+                            cfg.sampler_kernel);
     }
     if (e != cudaSuccess) return cuda_error(ctx_, e, "solve: sampler");
     return GMC_OK;
@@ -973,8 +1088,8 @@ class Engine {
   // Births of this wave through the internal model: every request's share of
   // the free room is sampled in one batch, tallied in its birth cell and
   // appended to the face banks, so it crosses its first face in this wave;
-  // births in cells thinner than min_tau start random walks instead.
-  gmc_status births_internal(int pending, int64_t room, const Rules &rules, float min_tau) {
+  // births in cells the random walk crosses start random walks instead.
+  gmc_status births_internal(int pending, int64_t room, const Rules &rules) {
     std::vector<std::pair<Request *, int64_t>> plan;
     int64_t M = 0;
     int left = pending;
@@ -1001,7 +1116,7 @@ class Engine {
       const int64_t m = pm.second;
       birth_gmc_kernel<<<nblocks(m, 256), 256, 0, s_>>>(R->slot, R->next_hist, m, base, M, R->d_cdf,
                                                          R->total, d_slots_, bhist, bslot, bcell,
-                                                         d_cond_, d_noise_, min_tau, ibank_[cin_],
+                                                         d_cond_, d_noise_, ibank_[cin_],
                                                          d_in, d_slot_live);
       GMC_CUDA_TRY(ctx_, cudaGetLastError());
       R->next_hist += m;
@@ -1009,7 +1124,7 @@ class Engine {
     }
     gmc_status st = sample(ctx_->internal, M);
     if (st != GMC_OK) return st;
-    const Route route{bank_[cur_], d_face, tbank_[ctn_], d_thin, min_tau};
+    const Route route{bank_[cur_], d_face, tbank_[ctn_], d_thin, true};
     birth_gmc_post_kernel<<<nblocks(M, 256), 256, 0, s_>>>(M, bhist, bslot, bcell, d_exit_, d_slots_,
                                                            rules, route, d_stats_, d_slot_live);
     GMC_CUDA_TRY(ctx_, cudaGetLastError());
@@ -1095,6 +1210,7 @@ class Engine {
   Slot *d_slots_ = nullptr;
   DevStats *d_stats_ = nullptr;
   int *d_counts_ = nullptr;
+  unsigned long long *d_next_ = nullptr;  // work counters of the persistent walk kernels
   int *h_counts_ = nullptr;
   Request *reqs_[kMaxSlots];
   int active_ = 0;

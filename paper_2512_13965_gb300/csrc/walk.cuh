@@ -6,7 +6,13 @@
 // by its analog method.
 //
 // Position arithmetic runs in T (float, or double in optically thick cells);
-// the variates (log, sincos) are drawn in float.
+// the variates (log, sincos) are drawn in float. In double cells the exit
+// decision of a flight is the FP64 one, reached cheaply: the wall distances
+// are first taken in FP32 from the FP64 gaps (flight_exits), and only a
+// flight whose length, or whose two wall distances, lie within the FP32
+// rounding bound of each other is decided by the FP64 divisions; an exiting
+// flight's distance is always the FP64 quotient. Histories are therefore the
+// same as with FP64 distances throughout.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -20,6 +26,59 @@ constexpr uint32_t kMaxFlights = 1u << 28;  // bound on one walk (never reached 
 constexpr float kTau64 = 64.0f;             // cells thicker than this walk in FP64
 
 enum : int { kExited = 0, kAbsorbed = 1, kTruncated = 2 };
+
+// Relative margin of the FP32 screen: an FP32 wall distance (the FP64 gap
+// rounded to FP32, then divided in FP32) is within 2 roundings (1.2e-7) of
+// the FP64 one; decisions closer than this margin are taken in FP64.
+constexpr float kScreen = 5e-7f;
+
+// Distance along the direction (ux, uy) from (x, y) to the wall it points at
+// in [0, wx] x [0, wy], one axis: +inf when the component is zero.
+template <typename T>
+__device__ __forceinline__ T wall_distance(T w, T p, float u) {
+  if (u > 0.0f) return (w - p) / (T)u;
+  if (u < 0.0f) return -p / (T)u;
+  return (T)INFINITY;
+}
+
+// Whether a flight of length d (a float value) from (x, y) with direction
+// (ux, uy) reaches a wall of the box [0, wx] x [0, wy] first (d >= distance,
+// ties exit), which wall (xface: a wall x = const; a corner picks x), and, if
+// so, the distance db >= 0 in T. Equal to the plain T computation.
+template <typename T>
+__device__ __forceinline__ bool flight_exits(T wx, T wy, T x, T y, float ux, float uy, float d,
+                                             bool &xface, T &db) {
+  if constexpr (sizeof(T) == sizeof(double)) {
+    bool sure = true;
+    float fx = INFINITY, fy = INFINITY;
+    if (ux != 0.0f) {
+      const float g = (float)(ux > 0.0f ? wx - x : -x);
+      sure = sure && fabsf(g) >= 1e-30f;
+      fx = g / ux;
+    }
+    if (uy != 0.0f) {
+      const float g = (float)(uy > 0.0f ? wy - y : -y);
+      sure = sure && fabsf(g) >= 1e-30f;
+      fy = g / uy;
+    }
+    const float lo = fminf(fx, fy), hi = fmaxf(fx, fy);
+    sure = sure && lo > 1e-20f && lo < 1e30f &&
+           (hi == INFINITY || lo <= hi * (1.0f - kScreen)) &&
+           (d >= lo * (1.0f + kScreen) || d < lo * (1.0f - kScreen));
+    if (sure) {
+      xface = fx <= fy;
+      if (d < lo) return false;
+      db = xface ? wall_distance(wx, x, ux) : wall_distance(wy, y, uy);
+      if (db < (T)0) db = (T)0;
+      return true;
+    }
+  }
+  const T dbx = wall_distance(wx, x, ux), dby = wall_distance(wy, y, uy);
+  xface = dbx <= dby;
+  db = xface ? dbx : dby;
+  if (db < (T)0) db = (T)0;
+  return (T)d >= db;
+}
 
 struct WalkResult {
   int status;       // kExited / kAbsorbed / kTruncated
@@ -42,7 +101,6 @@ __device__ __forceinline__ WalkResult walk_box_from(T tau, float c, int implicit
                                                     uint32_t &ncoll, uint32_t max_flights,
                                                     uint64_t seed, uint64_t id) {
   const float rate = implicit ? c : 1.0f;
-  const T inf = (T)INFINITY;
   WalkResult w;
   w.status = kTruncated;
   w.face = -1;
@@ -50,16 +108,11 @@ __device__ __forceinline__ WalkResult walk_box_from(T tau, float c, int implicit
   for (uint32_t it = 0; it < max_flights; ++it) {
     const uint4 r = philox_draw(seed, id, event, kTagWalk);
     ++event;
-    const T d = rate > 0.0f ? (T)(-logf(u01(r.x)) / rate) : inf;
-    T dbx = inf, dby = inf;
-    if (ux > 0.0f) dbx = (tau - x) / (T)ux;
-    else if (ux < 0.0f) dbx = -x / (T)ux;
-    if (uy > 0.0f) dby = (tau - y) / (T)uy;
-    else if (uy < 0.0f) dby = -y / (T)uy;
-    const bool xface = dbx <= dby;
-    T db = xface ? dbx : dby;
-    if (db < (T)0) db = (T)0;
-    if (d >= db) {
+    const float df = rate > 0.0f ? -logf(u01(r.x)) / rate : INFINITY;
+    const T d = (T)df;
+    bool xface;
+    T db;
+    if (flight_exits(tau, tau, x, y, ux, uy, df, xface, db)) {
       s += db;
       int face;
       T along;
@@ -104,6 +157,27 @@ __device__ __forceinline__ WalkResult walk_box(T tau, float c, int implicit, T x
   T s = 0;
   uint32_t ncoll = 0;
   return walk_box_from(tau, c, implicit, x, y, s, ux, uy, event, ncoll, kMaxFlights, seed, id);
+}
+
+// Persistent walk kernels refill their lanes: every lane walks one particle
+// at a time, kWalkRound flights per round, and a lane whose walk has ended
+// claims the next unprocessed particle. A warp then never idles while its
+// longest walk finishes, and the grid no longer waits for its slowest block.
+constexpr uint32_t kWalkRound = 8;
+
+// Claims the next particle index for every lane of the warp with `need` set,
+// with one atomic per warp on the counter *next; returns n once the n items
+// are exhausted (and for lanes without `need`). Every lane must call it.
+__device__ __forceinline__ int64_t warp_claim(bool need, unsigned long long *next, int64_t n) {
+  const unsigned m = __ballot_sync(0xffffffffu, need);
+  if (!m) return n;
+  const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == lead) base = atomicAdd(next, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, lead);
+  if (!need || base >= (unsigned long long)n) return n;
+  const unsigned long long k = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+  return k < (unsigned long long)n ? (int64_t)k : n;
 }
 
 // A walk in progress inside a cell, in optical units. Positions and track
@@ -169,7 +243,6 @@ __device__ __forceinline__ WalkResult walk_rect(T tx, T ty, float c, int implici
                                                 float ux, float uy, uint64_t seed, uint64_t id,
                                                 uint32_t event) {
   const float rate = implicit ? c : 1.0f;
-  const T inf = (T)INFINITY;
   T s = 0;
   uint32_t ncoll = 0;
   WalkResult w;
@@ -179,16 +252,11 @@ __device__ __forceinline__ WalkResult walk_rect(T tx, T ty, float c, int implici
   for (uint32_t it = 0; it < kMaxFlights; ++it) {
     const uint4 r = philox_draw(seed, id, event, kTagWalk);
     ++event;
-    const T d = rate > 0.0f ? (T)(-logf(u01(r.x)) / rate) : inf;
-    T dbx = inf, dby = inf;
-    if (ux > 0.0f) dbx = (tx - x) / (T)ux;
-    else if (ux < 0.0f) dbx = -x / (T)ux;
-    if (uy > 0.0f) dby = (ty - y) / (T)uy;
-    else if (uy < 0.0f) dby = -y / (T)uy;
-    const bool xface = dbx <= dby;
-    T db = xface ? dbx : dby;
-    if (db < (T)0) db = (T)0;
-    if (d >= db) {
+    const float df = rate > 0.0f ? -logf(u01(r.x)) / rate : INFINITY;
+    const T d = (T)df;
+    bool xface;
+    T db;
+    if (flight_exits(tx, ty, x, y, ux, uy, df, xface, db)) {
       s += db;
       int face;
       T qn;
@@ -236,7 +304,6 @@ __device__ __forceinline__ WalkResult walk_xy(T tx, T ty, float c, int implicit,
                                               float ux, float uy, uint64_t seed, uint64_t id,
                                               uint32_t event) {
   const float rate = implicit ? c : 1.0f;
-  const T inf = (T)INFINITY;
   T s = 0;
   uint32_t ncoll = 0;
   WalkResult w;
@@ -246,16 +313,11 @@ __device__ __forceinline__ WalkResult walk_xy(T tx, T ty, float c, int implicit,
   for (uint32_t it = 0; it < kMaxFlights; ++it) {
     const uint4 r = philox_draw(seed, id, event, kTagWalk);
     ++event;
-    const T d = rate > 0.0f ? (T)(-logf(u01(r.x)) / rate) : inf;
-    T dbx = inf, dby = inf;
-    if (ux > 0.0f) dbx = (tx - x) / (T)ux;
-    else if (ux < 0.0f) dbx = -x / (T)ux;
-    if (uy > 0.0f) dby = (ty - y) / (T)uy;
-    else if (uy < 0.0f) dby = -y / (T)uy;
-    const bool xface = dbx <= dby;
-    T db = xface ? dbx : dby;
-    if (db < (T)0) db = (T)0;
-    if (d >= db) {
+    const float df = rate > 0.0f ? -logf(u01(r.x)) / rate : INFINITY;
+    const T d = (T)df;
+    bool xface;
+    T db;
+    if (flight_exits(tx, ty, x, y, ux, uy, df, xface, db)) {
       s += db;
       int face;
       T qn;

@@ -10,6 +10,8 @@ import oracle
 import synth
 from oracle import transport as OT
 
+import _oracle_pool as P
+
 pytestmark = pytest.mark.gpu
 
 
@@ -86,26 +88,56 @@ def _set(ctx, **kw):
     g.gmc_set_config(ctx, cfg)
 
 
-def test_gmc_solve_with_internal_births_matches_oracle(ictx, kaiming_file):
+def test_gmc_solve_with_internal_births_per_cell(ictx, kaiming_file):
+    # births sampled by the internal model, transmissions by the boundary
+    # model (both FP32): K independent seeds per side against the oracle's
+    # event loop with the same two networks, compared cell by cell
     import paper_2512_13965_gb300 as g
-    net = oracle.mlp.read_weights(kaiming_file)
-    _set(ictx, precision=g.GMC_FP32, steps=4, integrator=g.GMC_EULER, bank_capacity=4096)
-    tau, c, src = synth.grid_problem(n=8, seed=31, tau_range=(0.1, 5.0), block=4, source=2)
-    n = 1500
+    _set(ictx, precision=g.GMC_FP32, steps=4, integrator=g.GMC_EULER, bank_capacity=1 << 16)
+    tau, c, src = synth.grid_problem(n=16, seed=31, tau_range=(0.1, 5.0), block=4, source=4)
     ny, nx = tau.shape
-    flux = np.zeros(ny * nx)
-    st = g.transport_solve(ictx, nx, ny, np.ascontiguousarray(tau, np.float32).ravel(),
-                           np.ascontiguousarray(c, np.float32).ravel(),
-                           np.ascontiguousarray(src, np.float32).ravel(), n, g.GMC_METHOD_GMC, 9,
-                           flux).as_dict()
-    fo, so = OT.solve_gmc(tau, c, src, n, 9, OT.mlp_sampler(net, 4, "euler", 9),
-                          internal=OT.mlp_internal_sampler(net, 4, "euler", 9))
-    fg = flux.reshape(ny, nx)
-    assert np.linalg.norm(fg - fo) / np.linalg.norm(fo) < 0.03
-    assert abs(st["leaked"] - so["leak"]) < 0.02 * n
-    assert abs(st["transmissions"] - so["transmissions"]) < 0.02 * so["transmissions"]
-    assert abs(st["absorbed"] + st["leaked"] - st["roulette_net"] - n) < 1e-4 * n
-    assert st["collisions"] == 0  # no birth was walked
+    args = [np.ascontiguousarray(a, np.float32).ravel() for a in (tau, c, src)]
+    n_gpu, n_orc, K = 20000, 4000, 8
+    gpu = []
+    for k in range(K):
+        flux = np.zeros(ny * nx)
+        st = g.transport_solve(ictx, nx, ny, *args, n_gpu, g.GMC_METHOD_GMC, 1000 + k, flux).as_dict()
+        gpu.append((flux.reshape(ny, nx), st))
+    spec = ("mlp", kaiming_file, 4, "euler")
+    orc = P.solve_many([{"grid": (tau, c, src), "n": n_orc, "seed": 2000 + k, "sampler": spec,
+                         "internal": spec} for k in range(K)])
+    P.assert_per_cell([f for f, _ in gpu], [f for f, _ in orc])
+    z = P.per_cell_z([[st["leaked"] / n_gpu] for _, st in gpu], [[st["leak"] / n_orc] for _, st in orc])
+    assert abs(z[0]) <= 4.0
+    for _, st in gpu:
+        assert abs(st["absorbed"] + st["leaked"] - st["roulette_net"] - n_gpu) < 1e-4 * n_gpu
+        assert st["collisions"] == 0  # no birth was walked
+
+
+def test_internal_births_at_equivalent_conditions_per_cell(ictx, kaiming_file):
+    # births in cells outside the training box sampled by the internal model
+    # at the scattering-equivalent condition, walked where there is none;
+    # against the oracle's event loop with the same reading
+    import paper_2512_13965_gb300 as g
+    from test_gpu_transport import BOX, _outside_box_grid
+    _set(ictx, precision=g.GMC_FP32, steps=4, integrator=g.GMC_EULER, bank_capacity=1 << 16)
+    tau, c, _ = _outside_box_grid(seed=41)
+    src = np.ones_like(tau) / tau.size  # births everywhere, walked cells included
+    ny, nx = tau.shape
+    args = [np.ascontiguousarray(a, np.float32).ravel() for a in (tau, c, src)]
+    n_gpu, n_orc, K = 20000, 4000, 8
+    gpu = []
+    for k in range(K):
+        flux = np.zeros(ny * nx)
+        st = g.transport_solve(ictx, nx, ny, *args, n_gpu, g.GMC_METHOD_GMC, 1000 + k, flux).as_dict()
+        gpu.append((flux.reshape(ny, nx), st))
+    spec = ("equivalent", kaiming_file, 4, "euler", BOX)
+    orc = P.solve_many([{"grid": (tau, c, src), "n": n_orc, "seed": 2000 + k, "sampler": spec,
+                         "internal": spec} for k in range(K)])
+    P.assert_per_cell([f for f, _ in gpu], [f for f, _ in orc])
+    for _, st in gpu:
+        assert abs(st["absorbed"] + st["leaked"] - st["roulette_net"] - n_gpu) < 1e-4 * n_gpu
+        assert st["collisions"] > 0
 
 
 def test_hybrid_with_internal_model_all_thin_equals_analog(ictx):

@@ -175,3 +175,47 @@ def test_network_solve_at_equivalent_conditions_balances_weight(tmp_path):
     sig_a = (1.0 - c.astype(np.float64)) * tau.astype(np.float64)
     assert abs(np.sum(flux * sig_a) * n - st["absorbed"]) < 1e-8 * n
     assert st["transmissions"] > n
+
+
+def test_births_at_equivalent_conditions_are_the_walked_births():
+    # births walked from their birth point at the equivalent condition, on
+    # the same counters, equal the births walked at the cell's own condition
+    # (same exits, track lengths scaled by c' / c): a solve with them equals
+    # the walk solve history by history; cells without an equivalent (c tau
+    # below 0.05) take the fallback
+    tau, c, src = synth.paper_lattice_problem(14)
+    src = np.where(c < 0.5, 1.0, src).astype(np.float32)  # births in absorbers too
+    src /= src.sum()
+    tau[0, 0] = 0.02
+    src[0, 0] = 0.05
+    w = T.walk_sampler(9)
+    wi = T.walk_internal_sampler(9)
+    a, sa = T.solve_gmc(tau, c, src, 800, 9, w, internal=wi)
+    b, sb = T.solve_gmc(tau, c, src, 800, 9, T.equivalent_sampler(w, w, *BOX),
+                        internal=T.equivalent_internal_sampler(wi, wi, *BOX))
+    np.testing.assert_allclose(b, a, rtol=1e-9, atol=1e-15)
+    assert sa["transmissions"] == sb["transmissions"]
+
+
+def test_internal_sampler_routes_cells_without_an_equivalent_to_the_fallback():
+    n = 300
+    X = np.linspace(0.1, 0.9, n)
+    Y = X[::-1].copy()
+    tau = np.where(np.arange(n) % 3 == 0, 0.2, 40.0)
+    c = np.where(np.arange(n) % 3 == 0, 0.1, 1.0)   # c tau = 0.02 (none) and 40 (c' 0.999)
+    calls = []
+
+    def tagged(tag):
+        def f(X, Y, tau, c, ids, u):
+            calls.append((tag, tau.copy(), c.copy()))
+            return (np.zeros(len(X), np.int64), X, Y, Y, np.ones(len(X)), np.ones(len(X), np.uint32))
+        return f
+
+    f = T.equivalent_internal_sampler(tagged("net"), tagged("walk"), *BOX)
+    face, q, ux, uy, s, ev = f(X, Y, tau, c, np.arange(n, dtype=np.uint64), np.zeros(n))
+    by = {t: (a, b) for t, a, b in calls}
+    assert np.allclose(by["walk"][0], 0.2) and np.allclose(by["walk"][1], 0.1)
+    assert np.allclose(by["net"][1], 0.999) and np.allclose(by["net"][0] * 0.999, 40.0)
+    net_rows = np.arange(n) % 3 != 0
+    assert np.allclose(s[net_rows], 0.999) and np.allclose(s[~net_rows], 1.0)
+    assert np.array_equal(q, X)
