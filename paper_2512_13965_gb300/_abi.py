@@ -20,6 +20,7 @@ GMC_FP32, GMC_BF16, GMC_FP8 = 0, 1, 2
 GMC_EULER, GMC_MIDPOINT, GMC_RK4 = 0, 1, 2
 GMC_ABSORB_ANALOG, GMC_ABSORB_IMPLICIT = 0, 1
 GMC_METHOD_ANALOG, GMC_METHOD_GMC = 0, 1
+GMC_KERNEL_TILE, GMC_KERNEL_PAIR = 0, 1
 
 
 class gmc_config(ctypes.Structure):
@@ -85,7 +86,10 @@ def _load():
         "gmc_load_weights_buffer": [P, P, sz],
         "gmc_load_internal_weights": [P, ctypes.c_char_p],
         "gmc_load_internal_weights_buffer": [P, P, sz],
+        "gmc_load_xy_weights": [P, ctypes.c_char_p],
+        "gmc_load_xy_weights_buffer": [P, P, sz],
         "gmc_sample_internal": [P, i64, P, P, u64, u64, i32, i32, i32, P, P],
+        "gmc_transmit_xy": [P, i64, P, P, u64, u64, i32, i32, i32, P, P],
         "gmc_transmit": [P, i64, P, P, u64, u64, i32, i32, i32, P, P],
         "gmc_transmit_noalloc": [P, i64, P, P, u64, u64, i32, i32, P, P],
         "analog_transmit": [P, i64, P, P, P, P, P, i32, u64, u64, u32, P, P, P],
@@ -104,6 +108,8 @@ def _load():
                            ctypes.c_float, P, P],
         "gmc_train_data_internal": [P, i64, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_float, P, P],
+        "gmc_train_data_xy": [P, i64, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, P, P],
         "gmc_train_begin": [P, i64, P, P, ctypes.POINTER(gmc_train_config)],
         "gmc_train_steps": [P, i64, P],
         "gmc_train_set_lr": [P, ctypes.c_double],
@@ -283,6 +289,21 @@ def gmc_load_internal_weights_buffer(ctx, blob):
                                                           len(blob)))
 
 
+def gmc_load_xy_weights(ctx, path):
+    return ctx.check(lib.gmc_load_xy_weights(ctx.handle, os.fsencode(path)))
+
+
+def gmc_load_xy_weights_buffer(ctx, blob):
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    return ctx.check(lib.gmc_load_xy_weights_buffer(ctx.handle, ctypes.addressof(buf), len(blob)))
+
+
+def gmc_transmit_xy(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw, exit):
+    return ctx.check(lib.gmc_transmit_xy(ctx.handle, n, *_sampler_args(n, cond, noise), seed, id0,
+                                         steps, integrator, precision,
+                                         *_sampler_out(n, y_raw, exit)))
+
+
 def gmc_sample_internal(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw, exit):
     return ctx.check(lib.gmc_sample_internal(ctx.handle, n, *_sampler_args(n, cond, noise),
                                              seed, id0, steps, integrator, precision,
@@ -349,6 +370,11 @@ def gmc_train_data_internal(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
     return ctx.check(lib.gmc_train_data_internal(ctx.handle, n, seed, tau_lo, tau_hi, c_lo, c_hi,
                                                  _arr(cond, 4, 5 * n, "cond"),
                                                  _arr(y, 4, 4 * n, "y")))
+
+
+def gmc_train_data_xy(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
+    return ctx.check(lib.gmc_train_data_xy(ctx.handle, n, seed, tau_lo, tau_hi, c_lo, c_hi,
+                                           _arr(cond, 4, 5 * n, "cond"), _arr(y, 4, 4 * n, "y")))
 
 
 def gmc_train_begin(ctx, n, cond, y, cfg):
