@@ -204,6 +204,15 @@ gmc_status gmc_load_internal_weights(gmc_ctx *ctx, const char *path);
 gmc_status gmc_load_internal_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes);
 
 /*
+ * Boundary model of x-y geometry (section "Network Architecture and Inputs":
+ * 3-D directions encoded by their projection on the unit disk): same GMCW
+ * layout and network shape, condition (xi, ux, uy, ln tau, c), state (p, ux,
+ * uy, ln s); used by gmc_transmit_xy. Errors as gmc_load_weights.
+ */
+gmc_status gmc_load_xy_weights(gmc_ctx *ctx, const char *path);
+gmc_status gmc_load_xy_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes);
+
+/*
  * Samples n exit states (Eq. 8, Eq. 11) with the loaded network.
  *  cond    [5][n] float: xi, cos theta_in, sin theta_in, ln tau, c (raw,
  *          standardized inside with the file's cond_mean / cond_std).
@@ -230,6 +239,19 @@ gmc_status gmc_transmit(gmc_ctx *ctx, int64_t n, const float *cond, const float 
 gmc_status gmc_sample_internal(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
                                uint64_t seed, uint64_t id0, int steps, int integrator,
                                int precision, float *y_raw, float *exit);
+/*
+ * gmc_transmit for x-y geometry (section "Network Architecture and Inputs",
+ * the direction encoded on the unit disk) with the network loaded by
+ * gmc_load_xy_weights (GMC_ENOWEIGHTS if none): cond [5][n] = (xi, ux, uy,
+ * ln tau, c) with (ux, uy) the projection of the 3-D entry direction; the
+ * decoded exit is (p, ux, uy, s) with the projected exit direction kept
+ * inside the unit disk (scaled onto the circle only when it lies outside),
+ * its normal component made outward (reflected, or the outward normal when
+ * none is left) and s the 3-D track length.
+ */
+gmc_status gmc_transmit_xy(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
+                           uint64_t seed, uint64_t id0, int steps, int integrator, int precision,
+                           float *y_raw, float *exit);
 
 /*
  * gmc_transmit without any device allocation during the call (the paper has
@@ -432,6 +454,22 @@ gmc_status gmc_train_data(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, 
  */
 gmc_status gmc_train_data_internal(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo,
                                    float tau_hi, float c_lo, float c_hi, float *cond, float *y);
+/*
+ * Training data of the boundary model in x-y geometry (section "Network
+ * Architecture and Inputs": the direction enters as its projection on the
+ * unit disk; the cell is the cross-section of an infinite prism and
+ * scattering is isotropic on the sphere, as analog_transmit_xy): for sample
+ * i, Philox block (i, 0, tag 8) gives ln tau uniform in [ln tau_lo,
+ * ln tau_hi], c uniform in [c_lo, c_hi], xi uniform and the cosine
+ * mu = sqrt(u) of the entry direction to the face normal; (i, 1, tag 8) its
+ * azimuth 2 pi u about the normal; the projected entry direction is
+ * (mu, sqrt(1 - mu^2) cos phi). The implicit-capture walk runs from the left
+ * face, flights from event 2. cond [5][n] = (xi, ux, uy, ln tau, c) and
+ * y [4][n] = (p, ux_out, uy_out, ln s) with (ux_out, uy_out) the projected
+ * exit direction and s the 3-D track length: device memory.
+ */
+gmc_status gmc_train_data_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, float tau_hi,
+                             float c_lo, float c_hi, float *cond, float *y);
 /*
  * Starts training on the device dataset (cond, y as gmc_train_data writes;
  * the caller keeps them alive while training). Standardization statistics

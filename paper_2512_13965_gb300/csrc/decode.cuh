@@ -9,7 +9,11 @@
 namespace gmc {
 
 // Returns (p, ux, uy, s); *inward is set when the sampled direction pointed
-// into the cell and was reflected about the face.
+// into the cell and was reflected about the face. With st.disk (x-y
+// geometry, Eq. 11 with the direction encoded by its projection on the unit
+// disk) the projection is kept, scaled back onto the unit circle only when it
+// lies outside the disk, and a projection with no outward component left
+// (parallel to the face, or zero) becomes the outward normal.
 __device__ __forceinline__ float4 decode_exit(float y0, float y1, float y2, float y3,
                                               const NetStats &st, bool *inward) {
   float p = fmaf(y0, st.y_std[0], st.y_mean[0]);
@@ -24,7 +28,12 @@ __device__ __forceinline__ float4 decode_exit(float y0, float y1, float y2, floa
   const float nx = face == 1 ? 1.0f : (face == 3 ? -1.0f : 0.0f);
   const float ny = face == 2 ? 1.0f : (face == 0 ? -1.0f : 0.0f);
   const float nrm = sqrtf(ux * ux + uy * uy);
-  if (nrm > 0.0f) {
+  if (st.disk) {
+    if (nrm > 1.0f) {
+      ux /= nrm;
+      uy /= nrm;
+    }
+  } else if (nrm > 0.0f) {
     ux /= nrm;
     uy /= nrm;
   } else {
@@ -36,6 +45,9 @@ __device__ __forceinline__ float4 decode_exit(float y0, float y1, float y2, floa
   if (dot < 0.0f) {
     ux -= 2.0f * dot * nx;
     uy -= 2.0f * dot * ny;
+  } else if (st.disk && dot == 0.0f) {
+    ux = nx;
+    uy = ny;
   }
   const float s = fmaxf(expf(ls), kSMin);
   return make_float4(p, ux, uy, s);

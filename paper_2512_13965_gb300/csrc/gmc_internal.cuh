@@ -29,6 +29,7 @@ struct NetF32 {
 // Standardization of the file: cond_mean[5], cond_std[5], y_mean[4], y_std[4].
 struct NetStats {
   float cond_mean[kCond], cond_inv_std[kCond], y_mean[kState], y_std[kState];
+  int disk;  // exits decoded for x-y geometry (direction projected on the unit disk)
 };
 
 // Packed operands of the tensor-core path (built by sampler_tc.cu).
@@ -78,6 +79,8 @@ struct gmc_ctx {
   // the internal model (births inside a source cell, gmc_load_internal_weights)
   gmc::NetDev net;
   gmc::NetDev internal;
+  // the boundary model of x-y geometry (gmc_load_xy_weights, gmc_transmit_xy)
+  gmc::NetDev xy;
   int *d_err = nullptr;  // device error word (bounded waits)
 
   // training state (gmc_train_begin .. gmc_destroy)
@@ -87,7 +90,7 @@ struct gmc_ctx {
   gmc::Buffer stage[9];
   // per-evaluation layer-1 bias of the tensor-core sampler
   gmc::Buffer bias1;
-  // work counter of the persistent random-walk kernels (8 bytes)
+  // work counter of the persistent random-walk kernel (8 bytes)
   gmc::Buffer walk_next;
   // transport_solve engine (kept between calls) and the serving thread
   gmc::Engine *solver = nullptr;

@@ -30,7 +30,7 @@
 
 namespace gmc {
 
-constexpr uint32_t kTagData = 5u, kTagTrain = 6u, kTagDataInternal = 7u;
+constexpr uint32_t kTagData = 5u, kTagTrain = 6u, kTagDataInternal = 7u, kTagDataXY = 8u;
 
 // parameter block offsets (floats): W1 [256][32] (columns 25..31 zero), b1,
 // W2, b2, W3, b3, W4, b4 ([256][256], [256]), W5 [4][256], b5 [4]
@@ -107,6 +107,44 @@ __global__ void internal_data_kernel(int64_t n, uint64_t seed, float ltau_lo, fl
   cond[2 * n + i] = ltau;
   cond[3 * n + i] = c;
   cond[4 * n + i] = fminf(fminf(X, Y), fminf(1.0f - X, 1.0f - Y));
+  y[i] = (float)(w.face < 0 ? 0 : w.face) + w.q;
+  y[n + i] = w.ux;
+  y[2 * n + i] = w.uy;
+  y[3 * n + i] = logf(fmaxf(w.s, kSMin));
+}
+
+// Training data of the boundary model in x-y geometry (the cell is the
+// cross-section of an infinite prism; directions are 3-D and enter the
+// network as their projection on the unit disk): Philox block (i, 0, tag 8)
+// gives ln tau, c, xi and mu = sqrt(u), the cosine of the entry direction to
+// the face normal (the cosine-law inflow of an isotropic flux); (i, 1, tag 8)
+// its azimuth 2 pi u about the normal, so the projection is (mu, sqrt(1 -
+// mu^2) cos phi). The implicit-capture walk with scattering on the sphere
+// runs from event 2 (FP64 positions in cells thicker than kTau64).
+// cond = (xi, ux, uy, ln tau, c); y = (p, ux_out, uy_out, ln s), s the 3-D
+// track length.
+__global__ void xy_data_kernel(int64_t n, uint64_t seed, float ltau_lo, float ltau_hi, float c_lo,
+                               float c_hi, float *__restrict__ cond, float *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 r = philox_draw(seed, (uint64_t)i, 0u, kTagDataXY);
+  const float ltau = ltau_lo + (ltau_hi - ltau_lo) * u01(r.x);
+  const float tau = expf(ltau);
+  const float c = c_lo + (c_hi - c_lo) * u01(r.y);
+  const float xi = u01(r.z);
+  const float mu = sqrtf(u01(r.w));
+  float sp, cp;
+  sincospif(2.0f * u01(philox_draw(seed, (uint64_t)i, 1u, kTagDataXY).x), &sp, &cp);
+  const float ux = mu, uy = sqrtf(fmaxf(1.0f - mu * mu, 0.0f)) * cp;
+  const WalkResult w =
+      tau > kTau64 ? walk_xy<double>((double)tau, (double)tau, c, 1, 0.0, (double)xi * tau, ux, uy,
+                                     seed, (uint64_t)i, 2u)
+                   : walk_xy<float>(tau, tau, c, 1, 0.0f, xi * tau, ux, uy, seed, (uint64_t)i, 2u);
+  cond[i] = xi;
+  cond[n + i] = ux;
+  cond[2 * n + i] = uy;
+  cond[3 * n + i] = ltau;
+  cond[4 * n + i] = c;
   y[i] = (float)(w.face < 0 ? 0 : w.face) + w.q;
   y[n + i] = w.ux;
   y[2 * n + i] = w.uy;
@@ -512,6 +550,24 @@ gmc_status gmc_train_data_internal(gmc_ctx *ctx, int64_t n, uint64_t seed, float
   cudaSetDevice(ctx->device);
   internal_data_kernel<<<nb(n, 128), 128, 0, ctx->stream>>>(n, seed, logf(tau_lo), logf(tau_hi), c_lo,
                                                             c_hi, cond, y);
+  GMC_CUDA_TRY(ctx, cudaGetLastError());
+  return GMC_OK;
+}
+
+gmc_status gmc_train_data_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, float tau_hi,
+                             float c_lo, float c_hi, float *cond, float *y) {
+  if (!ctx) return GMC_EINVAL;
+  if (n < 0 || (n > 0 && (!cond || !y)))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_data_xy: bad arguments");
+  if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
+    return set_error(ctx, GMC_EINVAL,
+                     "gmc_train_data_xy: need 0 < tau_lo <= tau_hi, 0 <= c_lo <= c_hi <= 1");
+  if (n == 0) return GMC_OK;
+  if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_data_xy: cond and y must be device memory");
+  cudaSetDevice(ctx->device);
+  xy_data_kernel<<<nb(n, 128), 128, 0, ctx->stream>>>(n, seed, logf(tau_lo), logf(tau_hi), c_lo, c_hi,
+                                                      cond, y);
   GMC_CUDA_TRY(ctx, cudaGetLastError());
   return GMC_OK;
 }

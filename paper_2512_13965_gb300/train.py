@@ -5,9 +5,11 @@
         [--lr-min 1e-5] [--warmup 500]
 
 Data: `gmc_train_data` (implicit-capture random walks from the left face,
-tau log-uniform in [0.1, 1000], c uniform in [0.5, 0.999]) or, with
---model internal, `gmc_train_data_internal` (walks from a uniform point inside
-the cell, for the internal-source model); objective: conditional flow
+tau log-uniform in [0.1, 1000], c uniform in [0.5, 0.999]), with
+--model internal `gmc_train_data_internal` (walks from a uniform point inside
+the cell, for the internal-source model), with --model xy
+`gmc_train_data_xy` (walks in x-y geometry: 3-D directions, the cell the
+cross-section of a prism); objective: conditional flow
 matching (Eq. 9) with AdamW, learning rate warmed up linearly and then
 decayed along a cosine to --lr-min; everything runs in libgmc.so, the GEMMs
 on tensor cores with BF16 operands and FP32 accumulation and master weights
@@ -40,9 +42,10 @@ def main(argv=None):
     ap.add_argument("--c", type=float, nargs=2, default=(0.5, 0.999))
     ap.add_argument("--report", type=int, default=1000)
     ap.add_argument("--device", type=int, default=0)
-    ap.add_argument("--model", default="boundary", choices=["boundary", "internal"],
+    ap.add_argument("--model", default="boundary", choices=["boundary", "internal", "xy"],
                     help="boundary: cell transmissions from the left face; internal: births "
-                         "inside a cell (volumetric source)")
+                         "inside a cell (volumetric source); xy: transmissions in x-y geometry "
+                         "(3-D directions projected on the unit disk)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"],
                     help="GEMM operands: bf16 (tensor cores) or fp32 (SIMT)")
     args = ap.parse_args(argv)
@@ -69,7 +72,8 @@ def main(argv=None):
         cond = torch.empty(5, n, device="cuda")
         y = torch.empty(4, n, device="cuda")
     t0 = time.perf_counter()
-    data = g.gmc_train_data if args.model == "boundary" else g.gmc_train_data_internal
+    data = {"boundary": g.gmc_train_data, "internal": g.gmc_train_data_internal,
+            "xy": g.gmc_train_data_xy}[args.model]
     data(ctx, n, args.seed, args.tau[0], args.tau[1], args.c[0], args.c[1], cond, y)
     g.gmc_synchronize(ctx)
     t_data = time.perf_counter() - t0
