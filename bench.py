@@ -37,6 +37,7 @@ METRIC = "cell transmissions/s GMC vs analog MC at flux err <=1%; p99 latency"
 # networks trained by the package's own trainer (commands in the weights folder)
 TRAINED_BOUNDARY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_boundary.bin")
 TRAINED_INTERNAL = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_internal.bin")
+TRAINED_XY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_xy.bin")
 # stated GMC-vs-analog relative L2 flux error at 1e7 histories, per precision
 # of the network (the metric's condition is the BF16 one, 1 %)
 FLUX_ERR_BOUND = {"bf16": 0.01, "fp8": 0.02}
@@ -193,6 +194,11 @@ def main():
                          "it; default: the package's trained network; 'none': births walked)")
     ap.add_argument("--serve-leg-requests", type=int, default=40,
                     help="requests of the short serving leg in the default line")
+    ap.add_argument("--model", default="boundary", choices=["boundary", "xy"],
+                    help="heldout: the square-cell boundary model or the x-y geometry model")
+    ap.add_argument("--capacity-sample", type=int, default=None,
+                    help="serve: estimate the server's capacity from the first N requests "
+                         "(default: the whole stream)")
     ap.add_argument("--histories", type=float, default=1e6)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--hist-range", type=float, nargs=2, default=(1e3, 1e5),
@@ -463,10 +469,12 @@ def solve_cfg4(g, ctx, n_hist, variants):
     return out
 
 
-def serve_stream(g, ctx, reqs, method, prec, integ, steps, rng, load=0.7, min_tau=0.0):
-    """One serving run: the capacity of the server (the whole stream submitted
-    at once), then the same requests arriving as a Poisson stream at `load`
-    of that capacity; latency = completion - submission per request."""
+def serve_stream(g, ctx, reqs, method, prec, integ, steps, rng, load=0.7, min_tau=0.0,
+                 capacity_sample=None):
+    """One serving run: the capacity of the server (the whole stream, or its
+    first `capacity_sample` requests, submitted at once), then the requests
+    arriving as a Poisson stream at `load` of that capacity; latency =
+    completion - submission per request."""
     import numpy as np
     cfg = g.gmc_get_config(ctx)
     cfg.steps, cfg.integrator, cfg.precision, cfg.gmc_min_tau = steps, integ, prec, min_tau
@@ -474,11 +482,12 @@ def serve_stream(g, ctx, reqs, method, prec, integ, steps, rng, load=0.7, min_ta
     g.gmc_set_config(ctx, cfg)
     g.gmc_serve_start(ctx, method, 4 << 30)
     try:
+        cap_reqs = reqs if not capacity_sample else reqs[:capacity_sample]
         t0 = time.perf_counter()
-        tks = [g.gmc_submit(ctx, n, n, tau, c, src, h, 7 + i) for i, (n, tau, c, src, h) in enumerate(reqs)]
-        for tk, r in zip(tks, reqs):
+        tks = [g.gmc_submit(ctx, n, n, tau, c, src, h, 7 + i) for i, (n, tau, c, src, h) in enumerate(cap_reqs)]
+        for tk, r in zip(tks, cap_reqs):
             g.gmc_wait(ctx, tk, 1800.0, np.zeros(r[0] * r[0]))
-        cap = len(reqs) / (time.perf_counter() - t0)
+        cap = len(cap_reqs) / (time.perf_counter() - t0)
         gaps = rng.exponential(1.0 / (load * cap), len(reqs))
         t0 = time.perf_counter()
         tks = []
@@ -497,8 +506,9 @@ def serve_stream(g, ctx, reqs, method, prec, integ, steps, rng, load=0.7, min_ta
     finally:
         g.gmc_serve_stop(ctx)
     return {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "solves_per_s": len(reqs) / wall, "capacity_solves_per_s": cap, "offered_load": load,
-            "transmissions_per_s": trans / wall}
+            "solves_per_s": len(reqs) / wall, "capacity_solves_per_s": cap,
+            "capacity_from_requests": len(cap_reqs), "offered_load": load,
+            "transmissions_per_s": trans / wall, "histories": int(sum(r[4] for r in reqs))}
 
 
 def serve_requests(n_req, hist_range, seed=4):
@@ -887,11 +897,22 @@ def run_heldout(args):
     import synth
     if args.weights == "kaiming":
         raise SystemExit("--workload heldout compares a trained network with the untrained one")
+    xy = args.model == "xy"
+    if xy and args.weights is None:
+        args.weights = TRAINED_XY
     g, ctx = _context(args)
     args_u = argparse.Namespace(**vars(args))
     args_u.weights = "kaiming"
     args_u.internal_weights = "none"
     _, ctx_u = _context(args_u)
+    if xy:
+        # the x-y network (and the untrained one) in the x-y slot: exits
+        # decoded into the unit disk
+        g.gmc_load_xy_weights(ctx, args.weights)
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "w.bin")
+            synth.write_weights(path, synth.kaiming_weights(1))
+            g.gmc_load_xy_weights(ctx_u, path)
     # one stream for torch and the library: inputs made by torch, outputs read
     # by torch, in stream order (a null stream would select the context's own)
     stream = torch.cuda.Stream()
@@ -899,9 +920,17 @@ def run_heldout(args):
     for cx in (ctx, ctx_u):
         g.gmc_set_stream(cx, stream)
     n = 100000
-    e = synth.cell_entries(n, 2024)
-    xi, cs, sn = (torch.from_numpy(e[k]).cuda() for k in ("xi", "cos", "sin"))
-    names = ("p", "cos", "sin", "ln_s")
+    if xy:
+        e = synth.cell_entries_xy(n, 2024)
+        xi, cs, sn = (torch.from_numpy(e[k].astype(np.float32)).cuda() for k in ("xi", "ux", "uy"))
+        names = ("p", "ux", "uy", "ln_s")
+    else:
+        e = synth.cell_entries(n, 2024)
+        xi, cs, sn = (torch.from_numpy(e[k]).cuda() for k in ("xi", "cos", "sin"))
+        names = ("p", "cos", "sin", "ln_s")
+    walk = (lambda *a: g.analog_transmit_xy(a[0], a[1], a[2], a[3], a[4], a[5], a[5], *a[6:])) if xy \
+        else g.analog_transmit
+    transmit = g.gmc_transmit_xy if xy else g.gmc_transmit
 
     def outputs(ex):
         a = ex.cpu().numpy().astype(np.float64)
@@ -922,7 +951,7 @@ def run_heldout(args):
             ref = []
             for seed in (11, 12):
                 ex = torch.empty(4, n, device="cuda")
-                g.analog_transmit(ctx, n, xi, cs, sn, tt, cc, g.GMC_ABSORB_IMPLICIT, seed, 0, 1, st, ex)
+                walk(ctx, n, xi, cs, sn, tt, cc, g.GMC_ABSORB_IMPLICIT, seed, 0, 1, st, ex)
                 ref.append(outputs(ex))
             cond = torch.stack([xi, cs, sn, torch.log(tt), cc])
             row = {"tau": tau, "c": c}
@@ -931,7 +960,7 @@ def run_heldout(args):
             row["analog_var"] = [float(ref[0][k].var()) for k in range(4)]
             for name, cx, integ, steps in samplers:
                 ex = torch.empty(4, n, device="cuda")
-                g.gmc_transmit(cx, n, cond, None, 31, 0, steps, integ, g.GMC_BF16, None, ex)
+                transmit(cx, n, cond, None, 31, 0, steps, integ, g.GMC_BF16, None, ex)
                 o = outputs(ex)
                 row[name + "_w1"] = [w1(o[k], ref[0][k]) for k in range(4)]
                 row[name + "_mean"] = [float(o[k].mean()) for k in range(4)]
@@ -946,7 +975,8 @@ def run_heldout(args):
     won = sum(all(row["gmc_rk4_12_w1"][k] < row["untrained_euler16_w1"][k] for k in range(4))
               for row in rows)
     line = {"metric": "1-D Wasserstein distance to the implicit-capture walk at 20 held-out (tau, c) pairs",
-            "workload": "held-out evaluation, 1e5 entries per pair, outputs " + ", ".join(names),
+            "workload": "held-out evaluation%s, 1e5 entries per pair, outputs " % (
+                " in x-y geometry (3-D directions on the unit disk)" if xy else "") + ", ".join(names),
             "weights": args.weights, "precision": "bf16", "summary": summ,
             "pairs_trained_beats_untrained_on_all_outputs": won, "rows": rows}
     print(json.dumps(line))
@@ -962,10 +992,14 @@ def run_serve(args):
     g, ctx = _context(args)
     reqs, rng = serve_requests(args.requests, args.hist_range)
     out = {}
+    want = None if args.solve_variants is None else set(args.solve_variants.split(","))
     for name, method, prec in (("gmc_fp8_midpoint8", g.GMC_METHOD_GMC, g.GMC_FP8),
                                ("gmc_bf16_midpoint8", g.GMC_METHOD_GMC, g.GMC_BF16),
                                ("analog", g.GMC_METHOD_ANALOG, g.GMC_BF16)):
-        out[name] = serve_stream(g, ctx, reqs, method, prec, g.GMC_MIDPOINT, 8, rng)
+        if want is not None and name not in want:
+            continue
+        out[name] = serve_stream(g, ctx, reqs, method, prec, g.GMC_MIDPOINT, 8, rng,
+                                 capacity_sample=args.capacity_sample)
     line = {"metric": METRIC, "workload": "serving: %d Poisson-arriving solves, n~U{16..256}, "
             "tau logU[0.1,1000], histories logU[%g,%g]" % (len(reqs), args.hist_range[0],
                                                           args.hist_range[1]), "results": out,
