@@ -622,7 +622,8 @@ def run_solve(args):
                                (g.GMC_BF16, g.GMC_MIDPOINT, 8), (g.GMC_BF16, g.GMC_MIDPOINT, 12),
                                (g.GMC_BF16, g.GMC_RK4, 4), (g.GMC_BF16, g.GMC_RK4, 6),
                                (g.GMC_BF16, g.GMC_RK4, 12), (g.GMC_FP8, g.GMC_EULER, 16),
-                               (g.GMC_FP8, g.GMC_EULER, 8), (g.GMC_FP8, g.GMC_RK4, 12)):
+                               (g.GMC_FP8, g.GMC_EULER, 8), (g.GMC_FP8, g.GMC_MIDPOINT, 8),
+                               (g.GMC_FP8, g.GMC_RK4, 12)):
         pname = "bf16" if prec == g.GMC_BF16 else "fp8"
         key = "gmc_%s_%s%d" % (pname, names[integ], steps)
         if want is not None and key not in want:
