@@ -308,8 +308,9 @@ def main():
     achieved = flops / avg_s / 1e12
     if prec == g.GMC_BF16:
         # DRAM read + write bytes of one launch of this kernel (BF16, Euler, 2^20 rows x
-        # 16 steps), from ncu dram__bytes_read.sum + dram__bytes_write.sum
-        traffic = 21640704 + 0 if ODE_STEPS == 16 and BATCH == 1 << 20 else None
+        # 16 steps), from ncu dram__bytes_read.sum + dram__bytes_write.sum of the
+        # current kernel (one CTA per SM, no clusters)
+        traffic = 21499904 + 0 if ODE_STEPS == 16 and BATCH == 1 << 20 else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16"], "unit": "TFLOP/s",
                 "frac": achieved / pk["bf16"], "traffic": traffic, "traffic_unit": "bytes per launch",
                 "peak_source": pk["src"] + " bf16 burst", "kernel": "sampler_tc_kernel"}
