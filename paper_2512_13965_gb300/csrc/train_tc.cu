@@ -63,6 +63,54 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
                : "memory");
 }
 
+// The chunk when rows are contiguous and K is strided (s_row == 1, s_k a
+// multiple of 4: the backward GEMMs' transposed operands). Work item = (group
+// of 4 rows, 8-column group c): 8 float4 loads, one per K index, each
+// covering the 4 rows (lanes take consecutive row groups, so a warp's load is
+// 512 contiguous bytes), transposed in registers into 4 rows of 8 BF16.
+// Row groups that cross nrows, or loads off 16-byte alignment, take scalar
+// loads; out-of-range entries are zero.
+template <int ROWS>
+__device__ __forceinline__ void stage_rows(uint32_t sbase, const float *__restrict__ P, int64_t s_k,
+                                           int row0, int nrows, int k0, int kend) {
+  constexpr int RG = ROWS / 4;
+  constexpr int ITEMS = RG * 8;
+  constexpr int PER = (ITEMS + TG_THREADS - 1) / TG_THREADS;
+  float v[PER][8][4];
+#pragma unroll
+  for (int it = 0; it < PER; ++it) {
+    const int i = threadIdx.x + it * TG_THREADS;
+    const int rg = i % RG, c = i / RG;
+    const int gr = row0 + 4 * rg, gk = k0 + 8 * c;
+    const bool whole = i < ITEMS && gr + 4 <= nrows;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float *src = P + (int64_t)gr + (int64_t)(gk + j) * s_k;
+      if (whole && gk + j < kend && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(src));
+        v[it][j][0] = a.x; v[it][j][1] = a.y; v[it][j][2] = a.z; v[it][j][3] = a.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          v[it][j][u] = (i < ITEMS && gr + u < nrows && gk + j < kend)
+                            ? __ldg(P + (int64_t)(gr + u) + (int64_t)(gk + j) * s_k)
+                            : 0.0f;
+      }
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < PER; ++it) {
+    const int i = threadIdx.x + it * TG_THREADS;
+    if (i >= ITEMS) break;
+    const int rg = i % RG, c = i / RG;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      sts128(sw128_addr(sbase, 4 * rg + u, c), bf16x2(v[it][0][u], v[it][1][u]),
+             bf16x2(v[it][2][u], v[it][3][u]), bf16x2(v[it][4][u], v[it][5][u]),
+             bf16x2(v[it][6][u], v[it][7][u]));
+  }
+}
+
 // ROWS x 64 operand chunk (rows row0.., K k0..) into shared memory as BF16.
 // Work item = (row r, 8-column group c); out-of-range entries are zero. Each
 // thread first issues the loads of all its items, then converts and stores
@@ -70,6 +118,10 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
 template <int ROWS>
 __device__ __forceinline__ void stage(uint32_t sbase, const float *__restrict__ P, int64_t s_row,
                                       int64_t s_k, int row0, int nrows, int k0, int kend) {
+  if (s_row == 1 && s_k != 1 && (s_k & 3) == 0 && ROWS % 4 == 0) {
+    stage_rows<ROWS>(sbase, P, s_k, row0, nrows, k0, kend);
+    return;
+  }
   constexpr int ITEMS = ROWS * 8;
   constexpr int PER = (ITEMS + TG_THREADS - 1) / TG_THREADS;
   const bool kcontig = s_k == 1;
