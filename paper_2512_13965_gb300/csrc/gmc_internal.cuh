@@ -164,17 +164,6 @@ cudaError_t launch_analog_xy(cudaStream_t stream, int64_t n, const float *xi, co
                              int mode, uint64_t seed, uint64_t id0, uint32_t event0,
                              int32_t *status, float *exit, uint32_t *ncoll);
 
-// BF16 tensor-core GEMM of the training step (train_tc.cu):
-// C[m][n] = epi(sum_k A[m sam + k sak] B[n sbn + k sbk]), FP32 in and out,
-// N <= 256. With splits > 1 (kTgStore only) the K range is cut into slices
-// written to `ws` (splits x M x N floats at most ws_floats) and summed into C
-// in slice order.
-enum { kTgStore = 0, kTgBiasSilu = 1, kTgBias = 2, kTgDSilu = 3 };
-cudaError_t tgemm(cudaStream_t st, int epi, int M, int N, int K, const float *A, int64_t sam,
-                  int64_t sak, const float *B, int64_t sbn, int64_t sbk, float *C,
-                  const float *bias, float *C2, const float *Zp, int splits, float *ws,
-                  size_t ws_floats, int *err);
-
 // Tensor-core sampler (sampler_tc.cu). The BF16 and FP8 variants share the
 // bias vector ([5][256]); the FP8 one also takes per-channel weight scales.
 size_t tc_packed_bytes(bool fp8);

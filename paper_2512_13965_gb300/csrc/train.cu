@@ -26,18 +26,12 @@
 #include "decode.cuh"
 #include "gmc_internal.cuh"
 #include "philox.cuh"
+#include "train_fused.h"
 #include "walk.cuh"
 
 namespace gmc {
 
 constexpr uint32_t kTagData = 5u, kTagTrain = 6u, kTagDataInternal = 7u, kTagDataXY = 8u;
-
-// parameter block offsets (floats): W1 [256][32] (columns 25..31 zero), b1,
-// W2, b2, W3, b3, W4, b4 ([256][256], [256]), W5 [4][256], b5 [4]
-constexpr int64_t P_W1 = 0, P_B1 = 8192, P_W2 = P_B1 + 256, P_B2 = P_W2 + 65536,
-                  P_W3 = P_B2 + 256, P_B3 = P_W3 + 65536, P_W4 = P_B3 + 256,
-                  P_B4 = P_W4 + 65536, P_W5 = P_B4 + 256, P_B5 = P_W5 + 1024,
-                  P_TOTAL = P_B5 + 4;
 
 struct TrainState {
   int64_t n = 0;
@@ -52,9 +46,8 @@ struct TrainState {
   double *loss = nullptr;  // [max steps per call]
   int64_t loss_cap = 0;
   double *stat_acc = nullptr;  // 18 sums
-  float *ws = nullptr;         // split-K slices of the weight-gradient GEMMs (tensor-core path)
-  float *colpart = nullptr;    // partial column sums of the bias gradients
-  size_t ws_floats = 0;
+  float *colpart = nullptr;    // partial column sums of the bias gradients (FP32 path)
+  tf::Bufs fb;                 // operand images of the BF16 tensor-core step
   int *err = nullptr;          // device error word of the context
 };
 
@@ -419,62 +412,12 @@ cudaError_t fwd_bwd(cudaStream_t s, TrainState &T, double *loss_slot) {
   return cudaGetLastError();
 }
 
-// The same step with the GEMMs on tensor cores (BF16 operands, FP32
-// accumulation). Weight gradients reduce over the batch in `splits` slices of
-// at least 256 rows, summed in a fixed order.
-cudaError_t fwd_bwd_tc(cudaStream_t s, TrainState &T, double *loss_slot) {
-  const int B = (int)T.B;
-  float *P = T.params, *G = T.grads;
-  const float *W[4] = {P + P_W1, P + P_W2, P + P_W3, P + P_W4};
-  const float *bb[4] = {P + P_B1, P + P_B2, P + P_B3, P + P_B4};
-  int splits = B / 256;
-  splits = splits < 1 ? 1 : (splits > 32 ? 32 : splits);
-  cudaError_t e;
-#define TG_TRY(...)                \
-  do {                             \
-    e = tgemm(__VA_ARGS__);        \
-    if (e != cudaSuccess) return e; \
-  } while (0)
-  // forward: Z_l = A_{l-1} W_l^T + b_l, A_l = SiLU(Z_l); B(n,k) = W_l[n][k]
-  TG_TRY(s, kTgBiasSilu, B, 256, 32, T.X0, 32, 1, W[0], 32, 1, T.Z[0], bb[0], T.A[0], nullptr, 1,
-         nullptr, 0, T.err);
-  for (int l = 1; l < 4; ++l)
-    TG_TRY(s, kTgBiasSilu, B, 256, 256, T.A[l - 1], 256, 1, W[l], 256, 1, T.Z[l], bb[l], T.A[l],
-           nullptr, 1, nullptr, 0, T.err);
-  TG_TRY(s, kTgBias, B, 4, 256, T.A[3], 256, 1, P + P_W5, 256, 1, T.V, P + P_B5, nullptr, nullptr, 1,
-         nullptr, 0, T.err);
-  loss_kernel<<<nb(B, 256), 256, 0, s>>>(B, T.V, T.U, T.dV, loss_slot);
-  // dW5 = dV^T A4 (contraction over the batch), db5, dZ4 = (dV W5) * SiLU'(Z4)
-  TG_TRY(s, kTgStore, 4, 256, B, T.dV, 1, 4, T.A[3], 1, 256, G + P_W5, nullptr, nullptr, nullptr,
-         splits, T.ws, T.ws_floats, T.err);
-  e = colsum(s, B, 4, T.dV, T.colpart, G + P_B5);
-  if (e) return e;
-  TG_TRY(s, kTgDSilu, B, 256, 4, T.dV, 4, 1, P + P_W5, 1, 256, T.dZ[0], nullptr, nullptr, T.Z[3], 1,
-         nullptr, 0, T.err);
-  int cur = 0;
-  const int64_t wofs[4] = {P_W1, P_W2, P_W3, P_W4}, bofs[4] = {P_B1, P_B2, P_B3, P_B4};
-  for (int l = 3; l >= 0; --l) {
-    const float *dz = T.dZ[cur];
-    const float *ain = l == 0 ? T.X0 : T.A[l - 1];
-    const int kin = l == 0 ? 32 : 256;
-    // dW_l[m][n] = sum_b dZ_l[b][m] A_{l-1}[b][n]
-    TG_TRY(s, kTgStore, 256, kin, B, dz, 1, 256, ain, 1, kin, G + wofs[l], nullptr, nullptr, nullptr,
-           splits, T.ws, T.ws_floats, T.err);
-    e = colsum(s, B, 256, dz, T.colpart, G + bofs[l]);
-    if (e) return e;
-    if (l > 0) {
-      // dZ_{l-1}[b][n] = SiLU'(Z_{l-1}[b][n]) sum_k dZ_l[b][k] W_l[k][n]
-      TG_TRY(s, kTgDSilu, B, 256, 256, dz, 256, 1, P + wofs[l], 1, 256, T.dZ[cur ^ 1], nullptr,
-             nullptr, T.Z[l - 1], 1, nullptr, 0, T.err);
-      cur ^= 1;
-    }
-  }
-#undef TG_TRY
-  return cudaGetLastError();
-}
-
-cudaError_t step_grads(cudaStream_t s, TrainState &T, double *loss_slot) {
-  return T.cfg.precision == GMC_BF16 ? fwd_bwd_tc(s, T, loss_slot) : fwd_bwd(s, T, loss_slot);
+// The gradient of the batch in X0/U into T.grads; on the BF16 path with
+// `adam` the same launches also apply AdamW (train_fused.cu).
+cudaError_t step_grads(cudaStream_t s, TrainState &T, double *loss_slot, const tf::Adam *adam = nullptr) {
+  if (T.cfg.precision == GMC_BF16)
+    return tf::step(s, T.fb, T.B, T.X0, T.U, T.params, T.grads, T.m, T.v, adam, loss_slot, T.err);
+  return fwd_bwd(s, T, loss_slot);
 }
 
 void free_train(TrainState *T) {
@@ -485,13 +428,16 @@ void free_train(TrainState *T) {
     if (b) cudaFree(b);
   if (T->loss) cudaFree(T->loss);
   if (T->stat_acc) cudaFree(T->stat_acc);
-  if (T->ws) cudaFree(T->ws);
   if (T->colpart) cudaFree(T->colpart);
+  tf::release(T->fb);
   delete T;
 }
 
-cudaError_t alloc_batch(TrainState &T, int64_t B) {
+// Batch buffers: X0 and U always; the FP32 path's activations, or the
+// operand images of the BF16 tensor-core step.
+cudaError_t alloc_batch(TrainState &T, int64_t B, cudaStream_t s) {
   if (T.B >= B) return cudaSuccess;
+  const bool f32 = T.cfg.precision != GMC_BF16;
   float **bufs[] = {&T.X0, &T.U, &T.V, &T.dV, &T.Z[0], &T.Z[1], &T.Z[2], &T.Z[3],
                     &T.A[0], &T.A[1], &T.A[2], &T.A[3], &T.dZ[0], &T.dZ[1]};
   const int64_t sizes[] = {B * 32, B * 4, B * 4, B * 4, B * 256, B * 256, B * 256, B * 256,
@@ -499,12 +445,14 @@ cudaError_t alloc_batch(TrainState &T, int64_t B) {
   for (int i = 0; i < 14; ++i) {
     if (*bufs[i]) cudaFree(*bufs[i]);
     *bufs[i] = nullptr;
+    if (i >= 2 && !f32) continue;
     cudaError_t e = cudaMalloc(bufs[i], sizes[i] * sizeof(float));
     if (e) return e;
   }
   if (T.colpart) cudaFree(T.colpart);
   T.colpart = nullptr;
-  cudaError_t e = cudaMalloc(&T.colpart, ((B + kColRows - 1) / kColRows) * 256 * sizeof(float));
+  cudaError_t e = f32 ? cudaMalloc(&T.colpart, ((B + kColRows - 1) / kColRows) * 256 * sizeof(float))
+                      : tf::alloc(T.fb, B, s);
   if (e) return e;
   T.B = B;
   return cudaSuccess;
@@ -632,12 +580,9 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
   GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->grads, 0, P_TOTAL * 4, s));
   GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->m, 0, P_TOTAL * 4, s));
   GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->v, 0, P_TOTAL * 4, s));
-  GMC_CUDA_TRY(ctx, alloc_batch(*T, cfg->batch));
+  GMC_CUDA_TRY(ctx, alloc_batch(*T, cfg->batch, s));
   T->err = ctx->d_err;
-  if (cfg->precision == GMC_BF16) {
-    T->ws_floats = (size_t)32 * 256 * 256;  // 32 split-K slices of a 256 x 256 gradient
-    GMC_CUDA_TRY(ctx, cudaMalloc(&T->ws, T->ws_floats * sizeof(float)));
-  }
+  if (cfg->precision == GMC_BF16) GMC_CUDA_TRY(ctx, tf::pack(s, T->fb, T->params));
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   return GMC_OK;
 }
@@ -669,13 +614,19 @@ gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses) {
   const gmc_train_config &c = T->cfg;
   for (int64_t i = 0; i < n_steps; ++i) {
     batch_kernel<<<nb(T->B, 256), 256, 0, s>>>(T->B, T->n, T->cond, T->y, sd, c.seed, T->step, T->X0, T->U);
-    GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i));
+    const float bc1 = 1.0f - (float)std::pow(c.beta1, (double)(T->step + 1));
+    const float bc2 = 1.0f - (float)std::pow(c.beta2, (double)(T->step + 1));
+    if (c.precision == GMC_BF16) {
+      const tf::Adam adam{(float)c.lr, (float)c.beta1, (float)c.beta2, (float)c.eps,
+                          (float)c.weight_decay, bc1, bc2};
+      GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i, &adam));
+    } else {
+      GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i));
+      adamw_kernel<<<nb(P_TOTAL, 256), 256, 0, s>>>(P_TOTAL, T->params, T->grads, T->m, T->v,
+                                                    (float)c.lr, (float)c.beta1, (float)c.beta2,
+                                                    (float)c.eps, (float)c.weight_decay, bc1, bc2);
+    }
     ++T->step;
-    const float bc1 = 1.0f - (float)std::pow(c.beta1, (double)T->step);
-    const float bc2 = 1.0f - (float)std::pow(c.beta2, (double)T->step);
-    adamw_kernel<<<nb(P_TOTAL, 256), 256, 0, s>>>(P_TOTAL, T->params, T->grads, T->m, T->v,
-                                                  (float)c.lr, (float)c.beta1, (float)c.beta2,
-                                                  (float)c.eps, (float)c.weight_decay, bc1, bc2);
     GMC_CUDA_TRY(ctx, cudaGetLastError());
   }
   if (losses) {
@@ -829,6 +780,7 @@ gmc_status gmc_train_load_state(gmc_ctx *ctx, const void *blob, size_t nbytes) {
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->params, body, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->m, body + P_TOTAL, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->v, body + 2 * P_TOTAL, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
+  if (T->cfg.precision == GMC_BF16) GMC_CUDA_TRY(ctx, tf::pack(s, T->fb, T->params));
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   T->step = h.step;
   T->cfg.lr = h.lr;

@@ -1,0 +1,863 @@
+// The BF16 training step of the velocity network (Eq. 9: conditional flow
+// matching loss, its hand-derived gradient, AdamW) in four tcgen05 kernels per
+// step instead of one GEMM launch per layer and direction.
+//
+// Work unit: a tile of 128 batch rows (rows past the batch are zero and carry
+// no gradient). Operands live in global memory as BF16 "images": the exact
+// bytes that tcgen05.mma reads from shared memory (K-major, 128-byte swizzle,
+// chunks of 64 K values = 128 B per row, 8-row groups 1024 B apart), so a
+// kernel moves them with plain bulk copies and never converts on the way in.
+//
+//   fwd   (one CTA per tile, persistent): X0 -> Z1..Z4 -> v, all five layers
+//         with the activations in shared memory; writes per layer the
+//         transposed activation image A_l^T (rows = channels, K = batch rows,
+//         the weight-gradient operand) and S_l = SiLU'(Z_l) (BF16 pairs);
+//         the loss (FP64 atomics per warp) and dV = 2 (v - u) / B as two
+//         images (rows = batch, and its transpose).
+//   bwd   (one CTA per tile): the input-gradient chain
+//         dZ4 = (dV W5) S4, dZ_{l-1} = (dZ_l W_l) S_{l-1}, with dZ_l in shared
+//         memory as the next A operand; writes dZ_l^T images.
+//   wgrad (jobs x batch slices): dW_l = dZ_l^T A_{l-1} and db_l = dZ_l^T 1
+//         (an N = 16 MMA against a constant-ones operand), both contracted
+//         over the batch on the tensor core, one FP32 slice per batch range.
+//   update (elementwise): the slices summed in a fixed order (deterministic)
+//         into the gradient, AdamW, and the BF16 weight images of the next
+//         step (forward W_l and the transposed W_l^T of the input gradients).
+//
+// Every wait is bounded; a timeout sets the context's device error word and
+// the CTA drains its MMAs and exits.
+#include <cuda_bf16.h>
+
+#include <atomic>
+#include <cstring>
+
+#include "gmc_internal.cuh"
+#include "tc_ptx.cuh"
+#include "train_fused.h"
+
+namespace gmc {
+namespace tf {
+namespace {
+
+using namespace ptx;
+
+// ---- image layout -----------------------------------------------------------
+
+// Byte offset of element (row r, K index k) in a K-major 128-byte-swizzled
+// chunk of 64 K values (rows of 128 B; 8-row groups of 1024 B).
+__host__ __device__ __forceinline__ uint32_t img_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k & 63) >> 3) ^ (r & 7)) << 4) +
+                    (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  __nv_bfloat16 h = __float2bfloat16_rn(x);
+  uint16_t u;
+  memcpy(&u, &h, 2);
+  return u;
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  uint32_t u;
+  memcpy(&u, &v, 4);
+  return u;
+}
+
+__device__ __forceinline__ float lo_f(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float hi_f(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// ---- weight images and the update kernel -----------------------------------
+
+// Element (n, k) of a B operand with rows n and K index k, chunked by 64 K:
+// chunk c = k / 64 at c * chunk_bytes.
+__device__ __forceinline__ void put_w(uint8_t *img, uint32_t base, uint32_t chunk_bytes, int n, int k,
+                                      float w) {
+  *reinterpret_cast<uint16_t *>(img + base + (uint32_t)(k >> 6) * chunk_bytes + img_off(n, k)) =
+      bf16_bits(w);
+}
+
+// The BF16 images of parameter i (weights only; biases enter in FP32).
+__device__ __forceinline__ void pack_param(uint8_t *img, int64_t i, float w) {
+  if (i < P_B1) {  // W1 [256][32]: forward operand, rows = outputs, K = inputs
+    put_w(img, WF1, 32768, (int)(i >> 5), (int)(i & 31), w);
+    return;
+  }
+  const int64_t wl[3] = {P_W2, P_W3, P_W4};
+  const uint32_t fo[3] = {WF2, WF3, WF4}, bo[3] = {WB2, WB3, WB4};
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    if (i >= wl[l] && i < wl[l] + 65536) {
+      const int o = (int)((i - wl[l]) >> 8), in = (int)((i - wl[l]) & 255);
+      put_w(img, fo[l], 32768, o, in, w);  // forward: rows = outputs, K = inputs
+      put_w(img, bo[l], 32768, in, o, w);  // input gradient: rows = inputs, K = outputs
+      return;
+    }
+  }
+  if (i >= P_W5 && i < P_B5) {
+    const int o = (int)((i - P_W5) >> 8), in = (int)((i - P_W5) & 255);
+    put_w(img, WF5, 2048, o, in, w);   // 16 rows (4 used) per chunk
+    put_w(img, WB5, 32768, in, o, w);  // K = the 4 outputs (the rest of the chunk zero)
+  }
+}
+
+// mode bit 0: grad[i] = sum over the S slices of ws (slice order);
+//      bit 1: AdamW on params with grad; bit 2: write the weight images.
+__global__ void update_kernel(int mode, const float *__restrict__ ws, int S, float *__restrict__ grad,
+                              float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                              float lr, float b1, float b2, float eps, float wd, float bc1, float bc2,
+                              uint8_t *__restrict__ img) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P_TOTAL) return;
+  if (mode & 1) {
+    float acc = 0.0f;
+    for (int s = 0; s < S; ++s) acc += ws[(int64_t)s * P_TOTAL + i];
+    grad[i] = acc;
+  }
+  float w = p[i];
+  if (mode & 2) {
+    const float gi = grad[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / bc1, vh = vi / bc2;
+    w = w * (1.0f - lr * wd) - lr * mh / (sqrtf(vh) + eps);
+    p[i] = w;
+  }
+  if (mode & 4) pack_param(img, i, w);
+}
+
+// ---- forward and input-gradient kernels ---------------------------------------
+
+constexpr int TR = 128;              // batch rows per tile
+constexpr uint32_t WCH = 32768;      // weight chunk: 256 rows x 128 B
+constexpr uint32_t ACH = 16384;      // activation chunk: 128 rows x 128 B
+constexpr int NEPI = 16;             // epilogue warps: 4 lane quadrants x 4 column quarters
+constexpr int FB_THREADS = 32 * (2 + NEPI);
+constexpr int NST = 3;               // weight stages
+constexpr int kTileChunks = 13;      // fwd: W1, W2..W4 (4 each); bwd: W5^T, W4^T..W2^T
+constexpr uint32_t kID256 = idesc_bf16_m128(256), kID32 = idesc_bf16_m128(32),
+                   kID16 = idesc_bf16_m128(16);
+
+struct KP {
+  int64_t B, ntiles;
+  const float *X0, *U, *params;
+  const uint8_t *img;
+  uint8_t *xt, *at[4], *dzt[4], *dv, *dvt;
+  uint32_t *s[4];
+  float *ws;
+  double *loss;
+  int *err;
+};
+
+struct Ctl {
+  uint64_t full[NST], empty[NST];
+  uint64_t aux_full, aux_empty;  // fwd: the resident W5 image; bwd: the tile's dV image
+  uint64_t a_full;               // the next A operand written (and the accumulator read)
+  uint64_t acc_full;             // the accumulator complete
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+// shared memory (offsets from a 1024-byte aligned base)
+constexpr uint32_t S_A = 0;                       // 4 chunks: the A operand (X0 in chunk 0)
+constexpr uint32_t S_ST = 4 * ACH;                // NST weight stages
+constexpr uint32_t S_AUX = S_ST + NST * WCH;      // fwd: W5 (8 KB); bwd: dV (16 KB)
+constexpr uint32_t S_BIAS = S_AUX + ACH;          // fwd: b1..b4, b5 (FP32)
+constexpr uint32_t S_CTL = S_BIAS + 4352;
+constexpr uint32_t FB_SMEM = S_CTL + 256 + 1024;  // + alignment slack
+static_assert(sizeof(Ctl) <= 256, "control block");
+static_assert(FB_SMEM <= 227 * 1024, "shared memory per CTA");
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) { return smem_desc(addr, 1024, kSwizzle128B); }
+
+__device__ __forceinline__ void fail(Ctl &c, int *err, int code) {
+  c.abort = 1;
+  atomicExch(err, code);
+}
+
+// The weight stream of one CTA (warp 0, lane 0): per tile the 13 chunks
+// base + g * WCH, g = 0..12; in the backward kernel also the tile's dV image.
+// Waits for every copy it issued before returning.
+template <bool BWD>
+__device__ void produce(Ctl &C, const KP &P, unsigned char *sm, uint32_t base, volatile int *abort) {
+  int issued = 0, it = 0;
+  bool ok = true;
+  for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x, ++it) {
+    if (BWD) {
+      if (it > 0 && !mbar_wait(&C.aux_empty, (uint32_t)(it - 1) & 1u, abort)) {
+        ok = false;
+        break;
+      }
+      mbar_arrive_expect_tx(&C.aux_full, ACH);
+      bulk_g2s(sm + S_AUX, P.dv + t * TILE_DV, ACH, &C.aux_full);
+    }
+    for (int g = 0; g < kTileChunks; ++g, ++issued) {
+      const int s = issued % NST;
+      if (issued >= NST && !mbar_wait(&C.empty[s], (uint32_t)(issued / NST - 1) & 1u, abort)) {
+        ok = false;
+        break;
+      }
+      mbar_arrive_expect_tx(&C.full[s], WCH);
+      bulk_g2s(sm + S_ST + s * WCH, P.img + base + (uint32_t)g * WCH, WCH, &C.full[s]);
+    }
+  }
+  if (!ok) fail(C, P.err, 21);
+  // copies in flight land before the CTA may exit
+  int never = 0;
+  for (int k = issued > NST ? issued - NST : 0; k < issued; ++k)
+    mbar_wait(&C.full[k % NST], (uint32_t)(k / NST) & 1u, &never, 1000000000ull);
+  if (BWD && it > 0) mbar_wait(&C.aux_full, (uint32_t)(it - 1) & 1u, &never, 1000000000ull);
+}
+
+// Transposed store of one warp's 32 rows x 2 columns: lane pairs (r, r+1)
+// swap halves so that each lane writes one 32-bit word: the even lane the
+// rows r, r+1 of column c, the odd lane those of column c + 1. `own` holds
+// this row's columns c (low) and c + 1 (high).
+__device__ __forceinline__ void st_transposed(uint8_t *img, int r, int c, uint32_t own, int lane) {
+  const uint32_t partner = __shfl_xor_sync(0xffffffffu, own, 1);
+  if (lane & 1)
+    *reinterpret_cast<uint32_t *>(img + img_off(c + 1, (r - 1) & 63)) = __byte_perm(partner, own, 0x7632);
+  else
+    *reinterpret_cast<uint32_t *>(img + img_off(c, r & 63)) = __byte_perm(own, partner, 0x5410);
+}
+
+// Forward: per tile, layer 1 (K = 32) and layers 2-4 (K = 256) with N = 256,
+// layer 5 with N = 16 (4 used); the accumulator is read by 16 epilogue warps
+// (lane quadrant q = warp % 4, columns 64 p .. 64 p + 63).
+__global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  unsigned char *sm = smem_raw + pad;
+  const uint32_t sb = raw + pad;
+  Ctl &C = *reinterpret_cast<Ctl *>(sm + S_CTL);
+  float *bias = reinterpret_cast<float *>(sm + S_BIAS);  // [4][256] then b5[4]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (int i = threadIdx.x; i < 1028; i += FB_THREADS) {
+    const int64_t src = i < 1024 ? (i < 256 ? P_B1 : i < 512 ? P_B2 - 256 : i < 768 ? P_B3 - 512 : P_B4 - 768) + i
+                                 : P_B5 + (i - 1024);
+    bias[i] = P.params[src];
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&C.full[s], 1);
+      mbar_init(&C.empty[s], 1);
+    }
+    mbar_init(&C.aux_full, 1);
+    mbar_init(&C.aux_empty, 1);
+    mbar_init(&C.a_full, NEPI);
+    mbar_init(&C.acc_full, 1);
+    mbar_init(&C.drain, 1);
+    C.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&C.tmem_base, 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = C.tmem_base;
+  volatile int *abort = &C.abort;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&C.aux_full, 8192);
+      bulk_g2s(sm + S_AUX, P.img + WF5, 8192, &C.aux_full);
+      produce<false>(C, P, sm, WF1, abort);
+      int never = 0;
+      mbar_wait(&C.aux_full, 0, &never, 1000000000ull);
+    }
+  } else if (warp == 1) {
+    int used = 0;
+    uint32_t af = 0;
+    bool ok = mbar_wait(&C.aux_full, 0, abort);
+    for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      for (int L = 0; L < 5 && ok; ++L) {
+        if (!mbar_wait(&C.a_full, af & 1u, abort)) {
+          ok = false;
+          break;
+        }
+        ++af;
+        tc_fence_after();
+        if (L < 4) {
+          const int nch = L == 0 ? 1 : 4, nk = L == 0 ? 2 : 4;
+          for (int c = 0; c < nch && ok; ++c, ++used) {
+            const int s = used % NST;
+            if (!mbar_wait(&C.full[s], (uint32_t)(used / NST) & 1u, abort)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t da = sdesc(sb + S_A + (uint32_t)c * ACH), db = sdesc(sb + S_ST + (uint32_t)s * WCH);
+            for (int k = 0; k < nk; ++k)
+              mma_f16_w(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kID256, (c | k) != 0);
+            mma_commit_w(&C.empty[s]);
+          }
+          if (!ok) break;
+        } else {
+          for (int c = 0; c < 4; ++c) {
+            const uint64_t da = sdesc(sb + S_A + (uint32_t)c * ACH), db = sdesc(sb + S_AUX + (uint32_t)c * 2048);
+            for (int k = 0; k < 4; ++k)
+              mma_f16_w(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kID16, (c | k) != 0);
+          }
+        }
+        mma_commit_w(&C.acc_full);
+      }
+    }
+    if (!ok && lane == 0) fail(C, P.err, 22);
+    // every MMA issued completes before tensor memory is freed
+    mma_commit_w(&C.drain);
+    int never = 0;
+    mbar_wait(&C.drain, 0, &never, 1000000000ull);
+  } else {
+    const int e = warp - 2, q = warp & 3, p = e >> 2;
+    const int r = 32 * q + lane;
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+    uint32_t accw = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      const int64_t b = t * TR + r;
+      const bool valid = b < P.B;
+      {  // X0 rows -> BF16 A image (chunk 0, K 0..31) and the X0^T image
+        const int ei = e * 32 + lane, rr = ei >> 2, gq = ei & 3;
+        const int64_t bb = t * TR + rr;
+        float x[8];
+        if (bb < P.B) {
+          const float4 lo = __ldg(reinterpret_cast<const float4 *>(P.X0 + bb * 32 + 8 * gq));
+          const float4 hi = __ldg(reinterpret_cast<const float4 *>(P.X0 + bb * 32 + 8 * gq + 4));
+          x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+          x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) x[j] = 0.0f;
+        }
+        sts128(sb + S_A + img_off(rr, 8 * gq), pack2(x[0], x[1]), pack2(x[2], x[3]), pack2(x[4], x[5]),
+               pack2(x[6], x[7]));
+        uint8_t *xt = P.xt + t * TILE_XT + (uint32_t)(rr >> 6) * 4096u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          *reinterpret_cast<uint16_t *>(xt + img_off(8 * gq + j, rr & 63)) = bf16_bits(x[j]);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&C.a_full);
+      for (int L = 0; L < 4; ++L) {
+        if (!mbar_wait(&C.acc_full, accw & 1u, abort)) {
+          ok = false;
+          break;
+        }
+        ++accw;
+        tc_fence_after();
+        uint32_t pa[2][16];
+        const float *bl = bias + L * 256;
+        uint32_t *sl = P.s[L] + t * (TILE_S / 4);
+#pragma unroll
+        for (int blk = 0; blk < 2; ++blk) {
+          const int col0 = 64 * p + 32 * blk;
+          uint32_t acc[32];
+          tmem_ld32_raw(tl + (uint32_t)col0, acc);
+          tmem_wait_ld_regs(acc);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int c = col0 + 2 * jj;
+            float a2[2], s2[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const float z = __uint_as_float(acc[2 * jj + u]) + bl[c + u];
+              const float sg = sigm(z);
+              a2[u] = valid ? z * sg : 0.0f;
+              s2[u] = valid ? sg * (1.0f + z * (1.0f - sg)) : 0.0f;
+            }
+            pa[blk][jj] = pack2(a2[0], a2[1]);
+            sl[(c >> 1) * TR + r] = pack2(s2[0], s2[1]);  // S_l for the backward kernel
+          }
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            sts128(sb + S_A + (uint32_t)p * ACH + img_off(r, 32 * blk + 8 * g), pa[blk][4 * g],
+                   pa[blk][4 * g + 1], pa[blk][4 * g + 2], pa[blk][4 * g + 3]);
+        }
+        tc_fence_before();
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&C.a_full);
+        // A_l^T for the weight gradients (off the MMA's critical path)
+        uint8_t *at = P.at[L] + t * TILE_AT + (uint32_t)(r >> 6) * 32768u;
+#pragma unroll
+        for (int blk = 0; blk < 2; ++blk)
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) st_transposed(at, r, 64 * p + 32 * blk + 2 * jj, pa[blk][jj], lane);
+      }
+      if (!ok) break;
+      // layer 5: v = A4 W5^T + b5, the loss and dV
+      if (!mbar_wait(&C.acc_full, accw & 1u, abort)) {
+        ok = false;
+        break;
+      }
+      ++accw;
+      tc_fence_after();
+      if (p == 0) {
+        float v[4];
+        tmem_ld4(tl, v);
+        tmem_wait_ld_regs4(v);
+        double part = 0.0;
+        float dv[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          dv[o] = 0.0f;
+          if (valid) {
+            const float res = (v[o] + bias[1024 + o]) - __ldg(P.U + b * 4 + o);
+            part += (double)res * res;
+            dv[o] = 2.0f * res / (float)P.B;
+          }
+        }
+        uint8_t *dvi = P.dv + t * TILE_DV;
+        *reinterpret_cast<uint4 *>(dvi + img_off(r, 0)) =
+            make_uint4(pack2(dv[0], dv[1]), pack2(dv[2], dv[3]), 0u, 0u);
+        *reinterpret_cast<uint4 *>(dvi + img_off(r, 8)) = make_uint4(0u, 0u, 0u, 0u);
+        uint8_t *dvt = P.dvt + t * TILE_DVT + (uint32_t)(r >> 6) * 2048u;
+#pragma unroll
+        for (int o = 0; o < 4; ++o)
+          *reinterpret_cast<uint16_t *>(dvt + img_off(o, r & 63)) = bf16_bits(dv[o]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        if (lane == 0 && part != 0.0) atomicAdd(P.loss, part / (double)P.B);
+      }
+      tc_fence_before();
+    }
+    if (!ok && lane == 0) fail(C, P.err, 23);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 256);
+}
+
+// Input gradients: per tile the rounds dZ4 = (dV W5) S4 (K = 16, the dV image
+// from the forward kernel), then dZ3, dZ2, dZ1 (K = 256 against W_l^T). The
+// epilogue of a round writes dZ as the next round's A operand (shared memory)
+// and dZ^T for the weight gradients; S_l is loaded before the accumulator is
+// ready. After the last round the epilogue still signals a_full: the next
+// tile's first MMA overwrites the accumulator it has just read.
+__global__ void __launch_bounds__(FB_THREADS, 1) bwd_kernel(KP P) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  unsigned char *sm = smem_raw + pad;
+  const uint32_t sb = raw + pad;
+  Ctl &C = *reinterpret_cast<Ctl *>(sm + S_CTL);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&C.full[s], 1);
+      mbar_init(&C.empty[s], 1);
+    }
+    mbar_init(&C.aux_full, 1);
+    mbar_init(&C.aux_empty, 1);
+    mbar_init(&C.a_full, NEPI);
+    mbar_init(&C.acc_full, 1);
+    mbar_init(&C.drain, 1);
+    C.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&C.tmem_base, 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = C.tmem_base;
+  volatile int *abort = &C.abort;
+
+  if (warp == 0) {
+    if (lane == 0) produce<true>(C, P, sm, WB5, abort);
+  } else if (warp == 1) {
+    int used = 0, it = 0;
+    uint32_t af = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x, ++it) {
+      for (int R = 0; R < 4 && ok; ++R) {
+        if ((R > 0 || it > 0)) {
+          if (!mbar_wait(&C.a_full, af & 1u, abort)) {
+            ok = false;
+            break;
+          }
+          ++af;
+        }
+        if (R == 0 && !mbar_wait(&C.aux_full, (uint32_t)it & 1u, abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int nch = R == 0 ? 1 : 4;
+        for (int c = 0; c < nch && ok; ++c, ++used) {
+          const int s = used % NST;
+          if (!mbar_wait(&C.full[s], (uint32_t)(used / NST) & 1u, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t db = sdesc(sb + S_ST + (uint32_t)s * WCH);
+          if (R == 0) {
+            mma_f16_w(tmem, sdesc(sb + S_AUX), db, kID256, 0u);
+          } else {
+            const uint64_t da = sdesc(sb + S_A + (uint32_t)c * ACH);
+            for (int k = 0; k < 4; ++k)
+              mma_f16_w(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kID256, (c | k) != 0);
+          }
+          mma_commit_w(&C.empty[s]);
+        }
+        if (!ok) break;
+        if (R == 0) mma_commit_w(&C.aux_empty);
+        mma_commit_w(&C.acc_full);
+      }
+    }
+    if (!ok && lane == 0) fail(C, P.err, 24);
+    mma_commit_w(&C.drain);
+    int never = 0;
+    mbar_wait(&C.drain, 0, &never, 1000000000ull);
+  } else {
+    const int e = warp - 2, q = warp & 3, p = e >> 2;
+    const int r = 32 * q + lane;
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+    uint32_t accw = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      for (int R = 0; R < 4; ++R) {
+        const int Lo = 3 - R;  // dZ of hidden layer Lo + 1
+        uint32_t sv[32];
+        const uint32_t *sl = P.s[Lo] + t * (TILE_S / 4) + (uint32_t)(32 * p) * TR + r;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sv[i] = __ldg(sl + i * TR);
+        if (!mbar_wait(&C.acc_full, accw & 1u, abort)) {
+          ok = false;
+          break;
+        }
+        ++accw;
+        tc_fence_after();
+        uint32_t pd[2][16];
+#pragma unroll
+        for (int blk = 0; blk < 2; ++blk) {
+          uint32_t acc[32];
+          tmem_ld32_raw(tl + (uint32_t)(64 * p + 32 * blk), acc);
+          tmem_wait_ld_regs(acc);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const uint32_t sw = sv[16 * blk + jj];
+            pd[blk][jj] = pack2(__uint_as_float(acc[2 * jj]) * lo_f(sw),
+                                __uint_as_float(acc[2 * jj + 1]) * hi_f(sw));
+          }
+          if (Lo > 0) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+              sts128(sb + S_A + (uint32_t)p * ACH + img_off(r, 32 * blk + 8 * g), pd[blk][4 * g],
+                     pd[blk][4 * g + 1], pd[blk][4 * g + 2], pd[blk][4 * g + 3]);
+          }
+        }
+        tc_fence_before();
+        if (Lo > 0) fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&C.a_full);
+        uint8_t *dz = P.dzt[Lo] + t * TILE_AT + (uint32_t)(r >> 6) * 32768u;
+#pragma unroll
+        for (int blk = 0; blk < 2; ++blk)
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) st_transposed(dz, r, 64 * p + 32 * blk + 2 * jj, pd[blk][jj], lane);
+      }
+    }
+    if (!ok && lane == 0) fail(C, P.err, 25);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 256);
+}
+
+// ---- weight gradients -------------------------------------------------------
+
+// Job j of the grid's x dimension, batch slice y:
+//   j < 8:  hidden layer l = j / 2, output rows 128 h .. (h = j % 2):
+//           D[o][i] = sum_b dZ_l^T[o][b] A_{l-1}^T[i][b] (N = 256; N = 32 for
+//           layer 1 against X0^T), and db[o] = sum_b dZ_l^T[o][b] (N = 16
+//           against the ones image, accumulator columns 256..271)
+//   j = 8, 9: W5 with M = its inputs 128 h ..: D[i][o] = sum_b A4^T[i][b] dV^T[o][b]
+//           (N = 16, 4 used); j = 8 also db5 (the ones image as A operand).
+// The slice's FP32 result goes to ws[y][...] at the parameter's own offset.
+constexpr int WG_THREADS = 192;  // producer, MMA, 4 epilogue warps
+constexpr int WNST = 4;
+constexpr uint32_t W_A = 16384, W_B = 32768, W_STAGE = W_A + W_B;
+constexpr uint32_t W_ONES16 = WNST * W_STAGE, W_ONES128 = W_ONES16 + 2048;
+constexpr uint32_t W_CTL = W_ONES128 + 16384;
+constexpr uint32_t WG_SMEM = W_CTL + 256 + 1024;
+static_assert(WG_SMEM <= 227 * 1024, "shared memory per CTA");
+
+struct WCtl {
+  uint64_t full[WNST], empty[WNST];
+  uint64_t acc_full, drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(KP P) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  unsigned char *sm = smem_raw + pad;
+  const uint32_t sb = raw + pad;
+  WCtl &C = *reinterpret_cast<WCtl *>(sm + W_CTL);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int job = blockIdx.x, split = blockIdx.y, S = gridDim.y;
+  const int64_t t0 = (int64_t)split * P.ntiles / S, t1 = (int64_t)(split + 1) * P.ntiles / S;
+  const int nchunks = (int)(2 * (t1 - t0));
+  const bool w5 = job >= 8;
+  const int layer = w5 ? 4 : job >> 1, h = w5 ? job - 8 : job & 1;
+  const uint32_t b_bytes = w5 ? 2048u : (layer == 0 ? 4096u : 32768u);
+  const uint32_t nmain = w5 ? 16u : (layer == 0 ? 32u : 256u);
+  const bool bias = job != 9;
+
+  // BF16 ones (0x3F80) for the bias contractions
+  uint32_t *ones = reinterpret_cast<uint32_t *>(sm + W_ONES16);
+  for (int i = threadIdx.x; i < (2048 + 16384) / 4; i += WG_THREADS) ones[i] = 0x3F803F80u;
+  fence_proxy_async_smem();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < WNST; ++s) {
+      mbar_init(&C.full[s], 1);
+      mbar_init(&C.empty[s], 1);
+    }
+    mbar_init(&C.acc_full, 1);
+    mbar_init(&C.drain, 1);
+    C.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&C.tmem_base, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = C.tmem_base;
+  volatile int *abort = &C.abort;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      bool ok = true;
+      int k = 0;
+      for (; k < nchunks; ++k) {
+        const int s = k % WNST;
+        if (k >= WNST && !mbar_wait(&C.empty[s], (uint32_t)(k / WNST - 1) & 1u, abort)) {
+          ok = false;
+          break;
+        }
+        const int64_t t = t0 + (k >> 1);
+        const uint32_t bc = (uint32_t)(k & 1);
+        const uint8_t *src_a = w5 ? P.at[3] + t * TILE_AT + bc * 32768u + (uint32_t)h * 16384u
+                                  : P.dzt[layer] + t * TILE_AT + bc * 32768u + (uint32_t)h * 16384u;
+        const uint8_t *src_b = w5 ? P.dvt + t * TILE_DVT + bc * 2048u
+                                  : (layer == 0 ? P.xt + t * TILE_XT + bc * 4096u
+                                                : P.at[layer - 1] + t * TILE_AT + bc * 32768u);
+        mbar_arrive_expect_tx(&C.full[s], W_A + b_bytes);
+        bulk_g2s(sm + (uint32_t)s * W_STAGE, src_a, W_A, &C.full[s]);
+        bulk_g2s(sm + (uint32_t)s * W_STAGE + W_A, src_b, b_bytes, &C.full[s]);
+      }
+      if (!ok) {
+        C.abort = 1;
+        atomicExch(P.err, 26);
+      }
+      int never = 0;
+      for (int j = k > WNST ? k - WNST : 0; j < k; ++j)
+        mbar_wait(&C.full[j % WNST], (uint32_t)(j / WNST) & 1u, &never, 1000000000ull);
+    }
+  } else if (warp == 1) {
+    bool ok = true;
+    const uint32_t idm = nmain == 256 ? kID256 : (nmain == 32 ? kID32 : kID16);
+    for (int k = 0; k < nchunks; ++k) {
+      const int s = k % WNST;
+      if (!mbar_wait(&C.full[s], (uint32_t)(k / WNST) & 1u, abort)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = sb + (uint32_t)s * W_STAGE, sbb = sa + W_A;
+      const uint64_t da = sdesc(sa), db = sdesc(sbb);
+      // bias: dZ^T against ones (layers), or ones against dV^T (W5)
+      const uint64_t xa = w5 ? sdesc(sb + W_ONES128) : da, xb = w5 ? db : sdesc(sb + W_ONES16);
+      for (int kk = 0; kk < 4; ++kk) {
+        mma_f16_w(tmem, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idm, (k | kk) != 0);
+        if (bias)
+          mma_f16_w(tmem + 256, xa + (uint64_t)(2 * kk), xb + (uint64_t)(2 * kk), kID16, (k | kk) != 0);
+      }
+      mma_commit_w(&C.empty[s]);
+    }
+    if (ok) mma_commit_w(&C.acc_full);
+    if (!ok && lane == 0) {
+      C.abort = 1;
+      atomicExch(P.err, 27);
+    }
+    mma_commit_w(&C.drain);
+    int never = 0;
+    mbar_wait(&C.drain, 0, &never, 1000000000ull);
+  } else {
+    const int q = warp & 3, m = 32 * q + lane;
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+    if (mbar_wait(&C.acc_full, 0, abort)) {
+      tc_fence_after();
+      float *ws = P.ws + (int64_t)split * P_TOTAL;
+      if (!w5) {
+        const int64_t wofs[4] = {P_W1, P_W2, P_W3, P_W4}, bofs[4] = {P_B1, P_B2, P_B3, P_B4};
+        const int o = 128 * h + m;
+        float *row = ws + wofs[layer] + (int64_t)o * nmain;
+        for (uint32_t cb = 0; cb < nmain; cb += 32) {
+          uint32_t acc[32];
+          tmem_ld32_raw(tl + cb, acc);
+          tmem_wait_ld_regs(acc);
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            *reinterpret_cast<float4 *>(row + cb + j) =
+                make_float4(__uint_as_float(acc[j]), __uint_as_float(acc[j + 1]),
+                            __uint_as_float(acc[j + 2]), __uint_as_float(acc[j + 3]));
+        }
+        float bv[4];
+        tmem_ld4(tl + 256, bv);
+        tmem_wait_ld_regs4(bv);
+        ws[bofs[layer] + o] = bv[0];
+      } else {
+        float v[4];
+        tmem_ld4(tl, v);
+        tmem_wait_ld_regs4(v);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) ws[P_W5 + o * 256 + 128 * h + m] = v[o];
+        if (bias) {
+          float bv[4];
+          tmem_ld4(tl + 256, bv);
+          tmem_wait_ld_regs4(bv);
+          if (m == 0)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) ws[P_B5 + o] = bv[o];
+        }
+      }
+    } else if (lane == 0) {
+      C.abort = 1;
+      atomicExch(P.err, 28);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+template <typename Kernel>
+cudaError_t set_smem(Kernel k, size_t bytes, std::atomic<bool> (&done)[kMaxDevices]) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < kMaxDevices && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) done[dev].store(true, std::memory_order_release);
+  return e;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+cudaError_t alloc(Bufs &b, int64_t batch, cudaStream_t s) {
+  const int64_t tiles = (batch + TR - 1) / TR;
+  if (b.img && b.tiles >= tiles) return cudaSuccess;
+  release(b);
+  cudaError_t e = cudaMalloc(&b.img, WIMG_BYTES);
+  if (e == cudaSuccess) e = cudaMalloc(&b.act, (size_t)tiles * TILE_BYTES);
+  b.max_splits = sm_count() / kJobs;
+  if (b.max_splits < 1) b.max_splits = 1;
+  if (e == cudaSuccess) e = cudaMalloc(&b.ws, (size_t)b.max_splits * P_TOTAL * sizeof(float));
+  // zero padding of the images (K beyond the operand, unused rows) stays zero
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.img, 0, WIMG_BYTES, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.act, 0, (size_t)tiles * TILE_BYTES, s);
+  if (e != cudaSuccess) {
+    release(b);
+    return e;
+  }
+  b.tiles = tiles;
+  uint8_t *p = b.act;
+  b.xt = p;
+  p += tiles * TILE_XT;
+  for (int l = 0; l < 4; ++l, p += tiles * TILE_AT) b.at[l] = p;
+  for (int l = 0; l < 4; ++l, p += tiles * TILE_AT) b.dzt[l] = p;
+  for (int l = 0; l < 4; ++l, p += tiles * TILE_S) b.s[l] = reinterpret_cast<uint32_t *>(p);
+  b.dv = p;
+  p += tiles * TILE_DV;
+  b.dvt = p;
+  return cudaSuccess;
+}
+
+void release(Bufs &b) {
+  if (b.img) cudaFree(b.img);
+  if (b.act) cudaFree(b.act);
+  if (b.ws) cudaFree(b.ws);
+  b = Bufs{};
+}
+
+cudaError_t pack(cudaStream_t s, Bufs &b, float *params) {
+  if (!b.img) return cudaErrorInvalidValue;
+  update_kernel<<<(unsigned)((P_TOTAL + 255) / 256), 256, 0, s>>>(
+      4, nullptr, 0, nullptr, params, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, b.img);
+  return cudaGetLastError();
+}
+
+cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const float *X0, const float *U, float *params,
+                 float *grad, float *m, float *v, const Adam *adam, double *loss, int *err) {
+  const int64_t ntiles = (B + TR - 1) / TR;
+  if (B < 1 || !b.img || ntiles > b.tiles) return cudaErrorInvalidValue;
+  static std::atomic<bool> a_fwd[kMaxDevices], a_bwd[kMaxDevices], a_wg[kMaxDevices];
+  cudaError_t e = set_smem(fwd_kernel, FB_SMEM, a_fwd);
+  if (e == cudaSuccess) e = set_smem(bwd_kernel, FB_SMEM, a_bwd);
+  if (e == cudaSuccess) e = set_smem(wgrad_kernel, WG_SMEM, a_wg);
+  if (e != cudaSuccess) return e;
+  KP P{};
+  P.B = B;
+  P.ntiles = ntiles;
+  P.X0 = X0;
+  P.U = U;
+  P.params = params;
+  P.img = b.img;
+  P.xt = b.xt;
+  for (int l = 0; l < 4; ++l) {
+    P.at[l] = b.at[l];
+    P.dzt[l] = b.dzt[l];
+    P.s[l] = b.s[l];
+  }
+  P.dv = b.dv;
+  P.dvt = b.dvt;
+  P.ws = b.ws;
+  P.loss = loss;
+  P.err = err;
+  const int sms = sm_count();
+  const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
+  fwd_kernel<<<grid, FB_THREADS, FB_SMEM, s>>>(P);
+  bwd_kernel<<<grid, FB_THREADS, FB_SMEM, s>>>(P);
+  const int S = (int)(ntiles < b.max_splits ? ntiles : b.max_splits);
+  wgrad_kernel<<<dim3(kJobs, (unsigned)S), WG_THREADS, WG_SMEM, s>>>(P);
+  const Adam a = adam ? *adam : Adam{0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f};
+  update_kernel<<<(unsigned)((P_TOTAL + 255) / 256), 256, 0, s>>>(
+      adam ? 7 : 1, b.ws, S, grad, params, m, v, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2, b.img);
+  return cudaGetLastError();
+}
+
+}  // namespace tf
+}  // namespace gmc
