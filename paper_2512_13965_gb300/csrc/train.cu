@@ -31,7 +31,7 @@
 
 namespace gmc {
 
-constexpr uint32_t kTagData = 5u, kTagTrain = 6u, kTagDataInternal = 7u, kTagDataXY = 8u;
+constexpr uint32_t kTagData = 5u, kTagDataInternal = 7u, kTagDataXY = 8u;  // kTagTrain: train_fused.h
 
 struct TrainState {
   int64_t n = 0;
@@ -167,10 +167,6 @@ __global__ void stats_kernel(int64_t n, const float *__restrict__ cond, const fl
   __syncthreads();
   if (threadIdx.x < 18) atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
 }
-
-struct Std {
-  float cm[5], cis[5], ym[4], yis[4];
-};
 
 // One batch row: sample index, t, x0 -> X0 row [cn, x_t, emb(t), 0...], U row.
 __global__ void batch_kernel(int64_t B, int64_t n, const float *__restrict__ cond,
@@ -414,9 +410,10 @@ cudaError_t fwd_bwd(cudaStream_t s, TrainState &T, double *loss_slot) {
 
 // The gradient of the batch in X0/U into T.grads; on the BF16 path with
 // `adam` the same launches also apply AdamW (train_fused.cu).
-cudaError_t step_grads(cudaStream_t s, TrainState &T, double *loss_slot, const tf::Adam *adam = nullptr) {
+cudaError_t step_grads(cudaStream_t s, TrainState &T, double *loss_slot, const tf::Adam *adam = nullptr,
+                       const tf::Gen *gen = nullptr) {
   if (T.cfg.precision == GMC_BF16)
-    return tf::step(s, T.fb, T.B, T.X0, T.U, T.params, T.grads, T.m, T.v, adam, loss_slot, T.err);
+    return tf::step(s, T.fb, T.B, gen, T.X0, T.U, T.params, T.grads, T.m, T.v, adam, loss_slot, T.err);
   return fwd_bwd(s, T, loss_slot);
 }
 
@@ -613,13 +610,15 @@ gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses) {
   }
   const gmc_train_config &c = T->cfg;
   for (int64_t i = 0; i < n_steps; ++i) {
-    batch_kernel<<<nb(T->B, 256), 256, 0, s>>>(T->B, T->n, T->cond, T->y, sd, c.seed, T->step, T->X0, T->U);
+    if (c.precision != GMC_BF16)
+      batch_kernel<<<nb(T->B, 256), 256, 0, s>>>(T->B, T->n, T->cond, T->y, sd, c.seed, T->step, T->X0, T->U);
     const float bc1 = 1.0f - (float)std::pow(c.beta1, (double)(T->step + 1));
     const float bc2 = 1.0f - (float)std::pow(c.beta2, (double)(T->step + 1));
     if (c.precision == GMC_BF16) {
       const tf::Adam adam{(float)c.lr, (float)c.beta1, (float)c.beta2, (float)c.eps,
                           (float)c.weight_decay, bc1, bc2};
-      GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i, &adam));
+      const tf::Gen gen{T->cond, T->y, T->n, sd, c.seed, T->step};
+      GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i, &adam, &gen));
     } else {
       GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i));
       adamw_kernel<<<nb(P_TOTAL, 256), 256, 0, s>>>(P_TOTAL, T->params, T->grads, T->m, T->v,

@@ -31,7 +31,9 @@
 #include <atomic>
 #include <cstring>
 
+#include "decode.cuh"
 #include "gmc_internal.cuh"
+#include "philox.cuh"
 #include "tc_ptx.cuh"
 #include "train_fused.h"
 
@@ -72,7 +74,17 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
                : "memory");
 }
 
-__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + expf(-z)); }
+// SiLU and its derivative from one MUFU tanh: sigma(z) = (1 + tanh(z/2)) / 2,
+// SiLU(z) = z sigma(z), SiLU'(z) = sigma(z) (1 + z (1 - sigma(z))). The
+// approximate tanh (relative error near 2^-11) sits below the BF16 rounding
+// that both values receive.
+__device__ __forceinline__ void silu_and_grad(float z, float &a, float &s) {
+  float th;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(0.5f * z));
+  const float sg = fmaf(0.5f, th, 0.5f);
+  a = z * sg;
+  s = sg * fmaf(z, 1.0f - sg, 1.0f);
+}
 
 // ---- weight images and the update kernel -----------------------------------
 
@@ -149,6 +161,8 @@ constexpr uint32_t kID256 = idesc_bf16_m128(256), kID32 = idesc_bf16_m128(32),
 
 struct KP {
   int64_t B, ntiles;
+  int gen;  // rows drawn in the forward kernel (Gen) instead of read from X0 / U
+  Gen g;
   const float *X0, *U, *params;
   const uint8_t *img;
   uint8_t *xt, *at[4], *dzt[4], *dv, *dvt;
@@ -229,6 +243,51 @@ __device__ __forceinline__ void st_transposed(uint8_t *img, int r, int c, uint32
     *reinterpret_cast<uint32_t *>(img + img_off(c + 1, (r - 1) & 63)) = __byte_perm(partner, own, 0x7632);
   else
     *reinterpret_cast<uint32_t *>(img + img_off(c, r & 63)) = __byte_perm(own, partner, 0x5410);
+}
+
+// Columns 8 gq .. 8 gq + 7 of batch row b (the X0 layout: standardized
+// condition, x_t, the 16 time-embedding features, zeros).
+__device__ __forceinline__ void batch_cols(const Gen &G, int64_t B, int64_t b, int gq, float (&x)[8]) {
+  const uint64_t rid = (uint64_t)G.step * (uint64_t)B + (uint64_t)b;
+  const uint4 r0 = philox_draw(G.seed, rid, 0u, kTagTrain);
+  const int64_t idx = (int64_t)(((uint64_t)r0.x * (uint64_t)G.n) >> 32);
+  const float t = u01(r0.y);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = 0.0f;
+  if (gq < 2) {
+    const float4 z = box_muller4(philox_draw(G.seed, rid, 1u, kTagTrain));
+    const float x0[4] = {z.x, z.y, z.z, z.w};
+    if (gq == 0) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) x[k] = (__ldg(G.cond + k * G.n + idx) - G.sd.cm[k]) * G.sd.cis[k];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float x1 = (__ldg(G.y + d * G.n + idx) - G.sd.ym[d]) * G.sd.yis[d];
+        x[5 + d] = (1.0f - t) * x0[d] + t * x1;
+      }
+    } else {
+      const float x1 = (__ldg(G.y + 3 * G.n + idx) - G.sd.ym[3]) * G.sd.yis[3];
+      x[0] = (1.0f - t) * x0[3] + t * x1;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) x[1 + j] = time_embedding(j, t);
+    }
+  } else if (gq == 2) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = time_embedding(7 + j, t);
+  } else {
+    x[0] = time_embedding(15, t);
+  }
+}
+
+// The regression target u = x1 - x0 of batch row b.
+__device__ __forceinline__ void batch_u(const Gen &G, int64_t B, int64_t b, float (&u)[4]) {
+  const uint64_t rid = (uint64_t)G.step * (uint64_t)B + (uint64_t)b;
+  const uint4 r0 = philox_draw(G.seed, rid, 0u, kTagTrain);
+  const int64_t idx = (int64_t)(((uint64_t)r0.x * (uint64_t)G.n) >> 32);
+  const float4 z = box_muller4(philox_draw(G.seed, rid, 1u, kTagTrain));
+  const float x0[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+  for (int d = 0; d < 4; ++d) u[d] = (__ldg(G.y + d * G.n + idx) - G.sd.ym[d]) * G.sd.yis[d] - x0[d];
 }
 
 // Forward: per tile, layer 1 (K = 32) and layers 2-4 (K = 256) with N = 256,
@@ -335,7 +394,9 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
         const int ei = e * 32 + lane, rr = ei >> 2, gq = ei & 3;
         const int64_t bb = t * TR + rr;
         float x[8];
-        if (bb < P.B) {
+        if (bb < P.B && P.gen) {
+          batch_cols(P.g, P.B, bb, gq, x);
+        } else if (bb < P.B) {
           const float4 lo = __ldg(reinterpret_cast<const float4 *>(P.X0 + bb * 32 + 8 * gq));
           const float4 hi = __ldg(reinterpret_cast<const float4 *>(P.X0 + bb * 32 + 8 * gq + 4));
           x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
@@ -376,10 +437,8 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
             float a2[2], s2[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-              const float z = __uint_as_float(acc[2 * jj + u]) + bl[c + u];
-              const float sg = sigm(z);
-              a2[u] = valid ? z * sg : 0.0f;
-              s2[u] = valid ? sg * (1.0f + z * (1.0f - sg)) : 0.0f;
+              silu_and_grad(__uint_as_float(acc[2 * jj + u]) + bl[c + u], a2[u], s2[u]);
+              if (!valid) a2[u] = s2[u] = 0.0f;
             }
             pa[blk][jj] = pack2(a2[0], a2[1]);
             sl[(c >> 1) * TR + r] = pack2(s2[0], s2[1]);  // S_l for the backward kernel
@@ -413,12 +472,18 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
         tmem_ld4(tl, v);
         tmem_wait_ld_regs4(v);
         double part = 0.0;
-        float dv[4];
+        float dv[4], u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (valid && P.gen) {
+          batch_u(P.g, P.B, b, u);
+        } else if (valid) {
+#pragma unroll
+          for (int o = 0; o < 4; ++o) u[o] = __ldg(P.U + b * 4 + o);
+        }
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
           dv[o] = 0.0f;
           if (valid) {
-            const float res = (v[o] + bias[1024 + o]) - __ldg(P.U + b * 4 + o);
+            const float res = (v[o] + bias[1024 + o]) - u[o];
             part += (double)res * res;
             dv[o] = 2.0f * res / (float)P.B;
           }
@@ -820,10 +885,10 @@ cudaError_t pack(cudaStream_t s, Bufs &b, float *params) {
   return cudaGetLastError();
 }
 
-cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const float *X0, const float *U, float *params,
-                 float *grad, float *m, float *v, const Adam *adam, double *loss, int *err) {
+cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const Gen *gen, const float *X0, const float *U,
+                 float *params, float *grad, float *m, float *v, const Adam *adam, double *loss, int *err) {
   const int64_t ntiles = (B + TR - 1) / TR;
-  if (B < 1 || !b.img || ntiles > b.tiles) return cudaErrorInvalidValue;
+  if (B < 1 || !b.img || ntiles > b.tiles || (!gen && (!X0 || !U))) return cudaErrorInvalidValue;
   static std::atomic<bool> a_fwd[kMaxDevices], a_bwd[kMaxDevices], a_wg[kMaxDevices];
   cudaError_t e = set_smem(fwd_kernel, FB_SMEM, a_fwd);
   if (e == cudaSuccess) e = set_smem(bwd_kernel, FB_SMEM, a_bwd);
@@ -832,6 +897,8 @@ cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const float *X0, const floa
   KP P{};
   P.B = B;
   P.ntiles = ntiles;
+  P.gen = gen != nullptr;
+  if (gen) P.g = *gen;
   P.X0 = X0;
   P.U = U;
   P.params = params;

@@ -14,7 +14,27 @@ constexpr int64_t P_W1 = 0, P_B1 = 8192, P_W2 = P_B1 + 256, P_B2 = P_W2 + 65536,
                   P_B4 = P_W4 + 65536, P_W5 = P_B4 + 256, P_B5 = P_W5 + 1024,
                   P_TOTAL = P_B5 + 4;
 
+// Standardization of the training data: condition and target means and
+// inverse standard deviations.
+struct Std {
+  float cm[5], cis[5], ym[4], yis[4];
+};
+
+constexpr uint32_t kTagTrain = 6u;  // Philox tag of the batch draws
+
 namespace tf {
+
+// Batch rows drawn inside the forward kernel (Eq. 9): for row b of step k,
+// Philox (seed, k B + b, event 0, kTagTrain) gives the sample index and t,
+// event 1 the four normals x0; X0 = [cn, (1 - t) x0 + t x1, emb(t), 0],
+// U = x1 - x0 (cn and x1 standardized).
+struct Gen {
+  const float *cond, *y;  // [5][n], [4][n]
+  int64_t n;
+  Std sd;
+  uint64_t seed;
+  int64_t step;
+};
 
 // Weight images (bytes; chunks of 64 K values, 128 B per row):
 //   WF1      W1 as rows = 256 outputs, K = 32 inputs (one chunk, K 32..63 zero)
@@ -57,10 +77,11 @@ struct Adam {
 cudaError_t pack(cudaStream_t s, Bufs &b, float *params);
 
 // Forward, loss (added to *loss), backward and weight gradients of a batch of
-// B rows already in X0 [B][32] and U [B][4]; the gradient lands in grad. With
-// adam non-null the same launch that sums the gradient applies AdamW to
-// params and repacks the weight images.
-cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const float *X0, const float *U,
+// B rows, drawn in the forward kernel (gen non-null) or already in X0 [B][32]
+// and U [B][4]; the gradient lands in grad. With adam non-null the same
+// launch that sums the gradient applies AdamW to params and repacks the
+// weight images.
+cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const Gen *gen, const float *X0, const float *U,
                  float *params, float *grad, float *m, float *v, const Adam *adam, double *loss,
                  int *err);
 

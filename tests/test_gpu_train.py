@@ -235,3 +235,34 @@ def test_training_bf16_reduces_loss(gpu_ctx, trainer, kaiming_file):
     g.gmc_train_steps(gpu_ctx, steps, losses)
     assert np.all(np.isfinite(losses))
     assert losses[-50:].mean() < 0.8 * losses[:20].mean()
+
+
+def test_bf16_first_step_matches_fp32(gpu_ctx, trainer):
+    # One training step of each precision from the same weights on the same
+    # batch: the FP32 step draws its rows in a batch kernel, the BF16 step
+    # inside its forward kernel, both from the same Philox counters. At step 1
+    # AdamW moves every parameter by -lr g / (|g| + eps) - lr wd p, i.e. by
+    # -lr sign(g) wherever |g| >> eps, so the two steps move the weights alike
+    # except where BF16 arithmetic flips the sign of a near-zero gradient.
+    import paper_2512_13965_gb300 as g
+    c = trainer["cfg"]
+    P = g.gmc_train_param_count()
+    res = {}
+    for prec in (g.GMC_FP32, g.GMC_BF16):
+        cfg = g.gmc_train_config(batch=c.batch, lr=c.lr, beta1=c.beta1, beta2=c.beta2, eps=c.eps,
+                                 weight_decay=c.weight_decay, seed=c.seed, precision=prec)
+        g.gmc_train_begin(gpu_ctx, trainer["n"], trainer["cond"], trainer["y"], cfg)
+        p0 = np.zeros(P, np.float32)
+        g.gmc_train_params(gpu_ctx, p0)
+        loss = np.zeros(1, np.float32)
+        g.gmc_train_steps(gpu_ctx, 1, loss)
+        p1 = np.zeros(P, np.float32)
+        g.gmc_train_params(gpu_ctx, p1)
+        res[prec] = (p0, p1 - p0, float(loss[0]))
+    (a0, da, la), (b0, db, lb) = res[g.GMC_FP32], res[g.GMC_BF16]
+    assert np.array_equal(a0, b0)
+    assert abs(la - lb) < 1e-2 * la, (la, lb)
+    moved = np.abs(da) > 0.5 * c.lr
+    same = np.abs(da - db) < 0.1 * c.lr
+    assert moved.mean() > 0.9
+    assert same[moved].mean() > 0.97, same[moved].mean()

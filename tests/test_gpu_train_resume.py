@@ -10,7 +10,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-def test_resume_continues_the_run(gpu_ctx, kaiming_file):
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_resume_continues_the_run(gpu_ctx, kaiming_file, precision):
     import torch
     import paper_2512_13965_gb300 as g
     ctx = g.Context(0)
@@ -22,7 +23,8 @@ def test_resume_continues_the_run(gpu_ctx, kaiming_file):
         g.gmc_train_data(ctx, n, 3, 0.1, 1000.0, 0.5, 0.999, cond, y)
         torch.cuda.synchronize()
         cfg = g.gmc_train_config(batch=1024, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
-                                 weight_decay=0.01, seed=5)
+                                 weight_decay=0.01, seed=5,
+                                 precision=g.GMC_BF16 if precision == "bf16" else g.GMC_FP32)
         P = g.gmc_train_param_count()
 
         def run(k1, k2, resume):
