@@ -74,16 +74,16 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
                : "memory");
 }
 
-// SiLU and its derivative from one MUFU tanh: sigma(z) = (1 + tanh(z/2)) / 2,
-// SiLU(z) = z sigma(z), SiLU'(z) = sigma(z) (1 + z (1 - sigma(z))). The
-// approximate tanh (relative error near 2^-11) sits below the BF16 rounding
-// that both values receive.
-__device__ __forceinline__ void silu_and_grad(float z, float &a, float &s) {
+// SiLU and its derivative from h = z / 2 and one MUFU tanh: with
+// sigma(z) = (1 + tanh h) / 2, SiLU(z) = h (1 + tanh h) and
+// SiLU'(z) = sigma (1 + h (1 - tanh h)). The approximate tanh (relative error
+// near 2^-11) sits below the BF16 rounding that both values receive.
+__device__ __forceinline__ void silu_and_grad(float h, float &a, float &s) {
   float th;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(0.5f * z));
+  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(h));
+  a = fmaf(h, th, h);
   const float sg = fmaf(0.5f, th, 0.5f);
-  a = z * sg;
-  s = sg * fmaf(z, 1.0f - sg, 1.0f);
+  s = fmaf(sg, fmaf(-h, th, h), sg);
 }
 
 // ---- weight images and the update kernel -----------------------------------
@@ -120,31 +120,51 @@ __device__ __forceinline__ void pack_param(uint8_t *img, int64_t i, float w) {
   }
 }
 
+// Four consecutive parameters per thread (P_TOTAL is a multiple of 4).
 // mode bit 0: grad[i] = sum over the S slices of ws (slice order);
 //      bit 1: AdamW on params with grad; bit 2: write the weight images.
+static_assert(P_TOTAL % 4 == 0, "float4 parameter groups");
 __global__ void update_kernel(int mode, const float *__restrict__ ws, int S, float *__restrict__ grad,
                               float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
                               float lr, float b1, float b2, float eps, float wd, float bc1, float bc2,
                               uint8_t *__restrict__ img) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P_TOTAL) return;
+  const int64_t i4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i4 >= P_TOTAL / 4) return;
+  const int64_t i = 4 * i4;
   if (mode & 1) {
-    float acc = 0.0f;
-    for (int s = 0; s < S; ++s) acc += ws[(int64_t)s * P_TOTAL + i];
-    grad[i] = acc;
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 4
+    for (int s = 0; s < S; ++s) {
+      const float4 w = __ldg(reinterpret_cast<const float4 *>(ws + (int64_t)s * P_TOTAL + i));
+      acc.x += w.x;
+      acc.y += w.y;
+      acc.z += w.z;
+      acc.w += w.w;
+    }
+    *reinterpret_cast<float4 *>(grad + i) = acc;
   }
-  float w = p[i];
+  float4 w4 = *reinterpret_cast<const float4 *>(p + i);
+  float w[4] = {w4.x, w4.y, w4.z, w4.w};
   if (mode & 2) {
-    const float gi = grad[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float mh = mi / bc1, vh = vi / bc2;
-    w = w * (1.0f - lr * wd) - lr * mh / (sqrtf(vh) + eps);
-    p[i] = w;
+    const float4 g4 = *reinterpret_cast<const float4 *>(grad + i);
+    const float4 m4 = *reinterpret_cast<const float4 *>(m + i), v4 = *reinterpret_cast<const float4 *>(v + i);
+    const float gi[4] = {g4.x, g4.y, g4.z, g4.w}, mo[4] = {m4.x, m4.y, m4.z, m4.w},
+                vo[4] = {v4.x, v4.y, v4.z, v4.w};
+    float mn[4], vn[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      mn[u] = b1 * mo[u] + (1.0f - b1) * gi[u];
+      vn[u] = b2 * vo[u] + (1.0f - b2) * gi[u] * gi[u];
+      const float mh = mn[u] / bc1, vh = vn[u] / bc2;
+      w[u] = w[u] * (1.0f - lr * wd) - lr * mh / (sqrtf(vh) + eps);
+    }
+    *reinterpret_cast<float4 *>(m + i) = make_float4(mn[0], mn[1], mn[2], mn[3]);
+    *reinterpret_cast<float4 *>(v + i) = make_float4(vn[0], vn[1], vn[2], vn[3]);
+    *reinterpret_cast<float4 *>(p + i) = make_float4(w[0], w[1], w[2], w[3]);
   }
-  if (mode & 4) pack_param(img, i, w);
+  if (mode & 4)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pack_param(img, i + u, w[u]);
 }
 
 // ---- forward and input-gradient kernels ---------------------------------------
@@ -175,8 +195,9 @@ struct KP {
 struct Ctl {
   uint64_t full[NST], empty[NST];
   uint64_t aux_full, aux_empty;  // fwd: the resident W5 image; bwd: the tile's dV image
-  uint64_t a_full;               // the next A operand written (and the accumulator read)
-  uint64_t acc_full;             // the accumulator complete
+  uint64_t a_full[4];            // K chunk c of the next A operand written by all epilogue warps
+  uint64_t acc_full[2];          // accumulator 0 / 1 complete (one barrier each: the MMA
+                                 // may finish the other accumulator before a wait)
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
@@ -233,16 +254,37 @@ __device__ void produce(Ctl &C, const KP &P, unsigned char *sm, uint32_t base, v
   if (BWD && it > 0) mbar_wait(&C.aux_full, (uint32_t)(it - 1) & 1u, &never, 1000000000ull);
 }
 
-// Transposed store of one warp's 32 rows x 2 columns: lane pairs (r, r+1)
-// swap halves so that each lane writes one 32-bit word: the even lane the
-// rows r, r+1 of column c, the odd lane those of column c + 1. `own` holds
-// this row's columns c (low) and c + 1 (high).
-__device__ __forceinline__ void st_transposed(uint8_t *img, int r, int c, uint32_t own, int lane) {
-  const uint32_t partner = __shfl_xor_sync(0xffffffffu, own, 1);
-  if (lane & 1)
-    *reinterpret_cast<uint32_t *>(img + img_off(c + 1, (r - 1) & 63)) = __byte_perm(partner, own, 0x7632);
-  else
-    *reinterpret_cast<uint32_t *>(img + img_off(c, r & 63)) = __byte_perm(own, partner, 0x5410);
+// Transposed stores of one warp's 32 rows x 16 columns (col0 .. col0 + 15,
+// col0 a multiple of 16) into an image whose rows are the columns and whose
+// K index is the row r & 63. Lane pairs (r, r + 1) swap halves so that each
+// lane writes one 32-bit word per column pair: the even lane rows r, r + 1 of
+// column c, the odd lane those of column c + 1. The swizzled offset of word
+// jj is (col0 / 8) * 1024 + (jj / 4) * 1024 + off[jj % 4], off[] fixed per lane.
+struct TOff {
+  uint32_t off[4];
+  uint32_t sel;  // byte selector: (own c lo, partner c lo) or (partner c+1 hi, own c+1 hi)
+};
+
+__device__ __forceinline__ TOff t_offsets(int r, int lane) {
+  const int odd = lane & 1, r0 = r & ~1, rk = (r0 & 63) >> 3;
+  TOff o;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int cc = 2 * j + odd;  // the word's image row within its 8-row group
+    o.off[j] = (uint32_t)(cc * 128 + ((rk ^ cc) << 4) + (r0 & 7) * 2);
+  }
+  o.sel = odd ? 0x3276u : 0x5410u;
+  return o;
+}
+
+// words[jj] holds this row's columns col0 + 2 jj (low) and + 1 (high).
+__device__ __forceinline__ void st_transposed16(uint8_t *img, int col0, const uint32_t (&w)[8], const TOff &o) {
+  uint8_t *base = img + (uint32_t)(col0 >> 3) * 1024u;
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const uint32_t partner = __shfl_xor_sync(0xffffffffu, w[jj], 1);
+    *reinterpret_cast<uint32_t *>(base + (jj >> 2) * 1024 + o.off[jj & 3]) = __byte_perm(w[jj], partner, o.sel);
+  }
 }
 
 // Columns 8 gq .. 8 gq + 7 of batch row b (the X0 layout: standardized
@@ -290,24 +332,9 @@ __device__ __forceinline__ void batch_u(const Gen &G, int64_t B, int64_t b, floa
   for (int d = 0; d < 4; ++d) u[d] = (__ldg(G.y + d * G.n + idx) - G.sd.ym[d]) * G.sd.yis[d] - x0[d];
 }
 
-// Forward: per tile, layer 1 (K = 32) and layers 2-4 (K = 256) with N = 256,
-// layer 5 with N = 16 (4 used); the accumulator is read by 16 epilogue warps
-// (lane quadrant q = warp % 4, columns 64 p .. 64 p + 63).
-__global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
-  extern __shared__ unsigned char smem_raw[];
-  const uint32_t raw = smem_u32(smem_raw);
-  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
-  unsigned char *sm = smem_raw + pad;
-  const uint32_t sb = raw + pad;
-  Ctl &C = *reinterpret_cast<Ctl *>(sm + S_CTL);
-  float *bias = reinterpret_cast<float *>(sm + S_BIAS);  // [4][256] then b5[4]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  for (int i = threadIdx.x; i < 1028; i += FB_THREADS) {
-    const int64_t src = i < 1024 ? (i < 256 ? P_B1 : i < 512 ? P_B2 - 256 : i < 768 ? P_B3 - 512 : P_B4 - 768) + i
-                                 : P_B5 + (i - 1024);
-    bias[i] = P.params[src];
-  }
+// Setup shared by the forward and input-gradient kernels: barriers, the
+// tensor memory of two accumulators (columns 0-255 and 256-511).
+__device__ __forceinline__ uint32_t fb_setup(Ctl &C, int warp) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(&C.full[s], 1);
@@ -315,20 +342,60 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
     }
     mbar_init(&C.aux_full, 1);
     mbar_init(&C.aux_empty, 1);
-    mbar_init(&C.a_full, NEPI);
-    mbar_init(&C.acc_full, 1);
+    for (int c = 0; c < 4; ++c) mbar_init(&C.a_full[c], NEPI);
+    mbar_init(&C.acc_full[0], 1);
+    mbar_init(&C.acc_full[1], 1);
     mbar_init(&C.drain, 1);
     C.abort = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(&C.tmem_base, 256);
+    tmem_alloc(&C.tmem_base, 512);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = C.tmem_base;
+  return C.tmem_base;
+}
+
+// One warp's 32 rows x 16 columns of an accumulator (columns col0 ..).
+__device__ __forceinline__ void acc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  tmem_ld16_raw(taddr, r);
+  tmem_wait_ld_regs16(r);
+}
+
+// K chunk c of the next A operand is in shared memory: this warp's part.
+__device__ __forceinline__ void chunk_written(Ctl &C, int c, int lane) {
+  tc_fence_before();
+  fence_proxy_async_smem();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&C.a_full[c]);
+}
+
+// Forward: per tile, layer 1 (K = 32) and layers 2-4 (K = 256) with N = 256,
+// layer 5 with N = 16 (4 used). The layers alternate between two
+// accumulators, and the A operand has a barrier per 64-channel K chunk: the
+// epilogue of layer l converts the accumulator chunk by chunk (16 warps: lane
+// quadrant q = warp % 4, 16 columns of every chunk each), and the MMAs of
+// layer l + 1 start on chunk c as soon as all warps have written it, while the
+// epilogue is still on the later chunks.
+__global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  unsigned char *sm = smem_raw + pad;
+  const uint32_t sb = raw + pad;
+  Ctl &C = *reinterpret_cast<Ctl *>(sm + S_CTL);
+  float *bias = reinterpret_cast<float *>(sm + S_BIAS);  // [4][256] halved, then b5[4]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (int i = threadIdx.x; i < 1028; i += FB_THREADS) {
+    const int64_t src = i < 1024 ? (i < 256 ? P_B1 : i < 512 ? P_B2 - 256 : i < 768 ? P_B3 - 512 : P_B4 - 768) + i
+                                 : P_B5 + (i - 1024);
+    bias[i] = i < 1024 ? 0.5f * P.params[src] : P.params[src];  // layers 1-4 halved (h = z / 2)
+  }
+  const uint32_t tmem = fb_setup(C, warp);
   volatile int *abort = &C.abort;
 
   if (warp == 0) {
@@ -340,40 +407,42 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
       mbar_wait(&C.aux_full, 0, &never, 1000000000ull);
     }
   } else if (warp == 1) {
-    int used = 0;
-    uint32_t af = 0;
+    int used = 0, gl = 0;
+    uint32_t af[4] = {0u, 0u, 0u, 0u};
     bool ok = mbar_wait(&C.aux_full, 0, abort);
     for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
-      for (int L = 0; L < 5 && ok; ++L) {
-        if (!mbar_wait(&C.a_full, af & 1u, abort)) {
-          ok = false;
-          break;
-        }
-        ++af;
-        tc_fence_after();
-        if (L < 4) {
-          const int nch = L == 0 ? 1 : 4, nk = L == 0 ? 2 : 4;
-          for (int c = 0; c < nch && ok; ++c, ++used) {
+      for (int L = 0; L < 5 && ok; ++L, ++gl) {
+        const uint32_t acc = tmem + (uint32_t)(gl & 1) * 256u;
+        const int nch = L == 0 ? 1 : 4;
+        for (int c = 0; c < nch && ok; ++c) {
+          if (!mbar_wait(&C.a_full[c], af[c] & 1u, abort)) {
+            ok = false;
+            break;
+          }
+          ++af[c];
+          const uint64_t da = sdesc(sb + S_A + (uint32_t)c * ACH);
+          if (L < 4) {
             const int s = used % NST;
             if (!mbar_wait(&C.full[s], (uint32_t)(used / NST) & 1u, abort)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint64_t da = sdesc(sb + S_A + (uint32_t)c * ACH), db = sdesc(sb + S_ST + (uint32_t)s * WCH);
+            const uint64_t db = sdesc(sb + S_ST + (uint32_t)s * WCH);
+            const int nk = L == 0 ? 2 : 4;
             for (int k = 0; k < nk; ++k)
-              mma_f16_w(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kID256, (c | k) != 0);
+              mma_f16_w(acc, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kID256, (c | k) != 0);
             mma_commit_w(&C.empty[s]);
-          }
-          if (!ok) break;
-        } else {
-          for (int c = 0; c < 4; ++c) {
-            const uint64_t da = sdesc(sb + S_A + (uint32_t)c * ACH), db = sdesc(sb + S_AUX + (uint32_t)c * 2048);
+            ++used;
+          } else {
+            tc_fence_after();
+            const uint64_t db = sdesc(sb + S_AUX + (uint32_t)c * 2048);
             for (int k = 0; k < 4; ++k)
-              mma_f16_w(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kID16, (c | k) != 0);
+              mma_f16_w(acc, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kID16, (c | k) != 0);
           }
         }
-        mma_commit_w(&C.acc_full);
+        if (!ok) break;
+        mma_commit_w(&C.acc_full[gl & 1]);
       }
     }
     if (!ok && lane == 0) fail(C, P.err, 22);
@@ -385,12 +454,22 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
     const int e = warp - 2, q = warp & 3, p = e >> 2;
     const int r = 32 * q + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
-    uint32_t accw = 0;
+    const TOff toff = t_offsets(r, lane);
+    int gl = 0;  // layers so far: accumulator gl & 1, its (gl >> 1)-th use
     bool ok = true;
     for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       const int64_t b = t * TR + r;
-      const bool valid = b < P.B;
-      {  // X0 rows -> BF16 A image (chunk 0, K 0..31) and the X0^T image
+      const bool valid = b < P.B;  // rows past the batch: finite values, zero dV
+      float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // the row's target, loaded ahead of layer 5
+      if (p == 0 && valid) {
+        if (P.gen) {
+          batch_u(P.g, P.B, b, u);
+        } else {
+#pragma unroll
+          for (int o = 0; o < 4; ++o) u[o] = __ldg(P.U + b * 4 + o);
+        }
+      }
+      {  // batch rows -> BF16 A image (chunk 0, K 0..31) and the X0^T image
         const int ei = e * 32 + lane, rr = ei >> 2, gq = ei & 3;
         const int64_t bb = t * TR + rr;
         float x[8];
@@ -407,78 +486,67 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
         }
         sts128(sb + S_A + img_off(rr, 8 * gq), pack2(x[0], x[1]), pack2(x[2], x[3]), pack2(x[4], x[5]),
                pack2(x[6], x[7]));
+        chunk_written(C, 0, lane);
         uint8_t *xt = P.xt + t * TILE_XT + (uint32_t)(rr >> 6) * 4096u;
 #pragma unroll
         for (int j = 0; j < 8; ++j)
           *reinterpret_cast<uint16_t *>(xt + img_off(8 * gq + j, rr & 63)) = bf16_bits(x[j]);
       }
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&C.a_full);
-      for (int L = 0; L < 4; ++L) {
-        if (!mbar_wait(&C.acc_full, accw & 1u, abort)) {
+      for (int L = 0; L < 4; ++L, ++gl) {
+        if (!mbar_wait(&C.acc_full[gl & 1], (uint32_t)(gl >> 1) & 1u, abort)) {
           ok = false;
           break;
         }
-        ++accw;
         tc_fence_after();
-        uint32_t pa[2][16];
+        const uint32_t tacc = tl + (uint32_t)(gl & 1) * 256u;
         const float *bl = bias + L * 256;
-        uint32_t *sl = P.s[L] + t * (TILE_S / 4);
+        uint32_t *sl = P.s[L] + t * (TILE_S / 4) + r;
+        uint8_t *at = P.at[L] + t * TILE_AT + (uint32_t)(r >> 6) * 32768u;
+        // chunk c + 1's accumulator columns load while chunk c converts
+        uint32_t acc[2][16];
+        acc_ld16(tacc + (uint32_t)(16 * p), acc[0]);
 #pragma unroll
-        for (int blk = 0; blk < 2; ++blk) {
-          const int col0 = 64 * p + 32 * blk;
-          uint32_t acc[32];
-          tmem_ld32_raw(tl + (uint32_t)col0, acc);
-          tmem_wait_ld_regs(acc);
+        for (int c = 0; c < 4; ++c) {
+          const int col0 = 64 * c + 16 * p;
+          if (c < 3) tmem_ld16_raw(tacc + (uint32_t)(col0 + 64), acc[(c + 1) & 1]);
+          uint32_t pa[8];
+          float hb[16];
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int c = col0 + 2 * jj;
-            float a2[2], s2[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              silu_and_grad(__uint_as_float(acc[2 * jj + u]) + bl[c + u], a2[u], s2[u]);
-              if (!valid) a2[u] = s2[u] = 0.0f;
-            }
-            pa[blk][jj] = pack2(a2[0], a2[1]);
-            sl[(c >> 1) * TR + r] = pack2(s2[0], s2[1]);  // S_l for the backward kernel
+          for (int i = 0; i < 4; ++i) {
+            const float4 v4 = *reinterpret_cast<const float4 *>(bl + col0 + 4 * i);
+            hb[4 * i] = v4.x; hb[4 * i + 1] = v4.y; hb[4 * i + 2] = v4.z; hb[4 * i + 3] = v4.w;
           }
 #pragma unroll
-          for (int g = 0; g < 4; ++g)
-            sts128(sb + S_A + (uint32_t)p * ACH + img_off(r, 32 * blk + 8 * g), pa[blk][4 * g],
-                   pa[blk][4 * g + 1], pa[blk][4 * g + 2], pa[blk][4 * g + 3]);
+          for (int jj = 0; jj < 8; ++jj) {
+            float a2[2], s2[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+              silu_and_grad(fmaf(__uint_as_float(acc[c & 1][2 * jj + u]), 0.5f, hb[2 * jj + u]), a2[u], s2[u]);
+            pa[jj] = pack2(a2[0], a2[1]);
+            sl[((col0 >> 1) + jj) * TR] = pack2(s2[0], s2[1]);  // S_l for the backward kernel
+          }
+          const uint32_t dst = sb + S_A + (uint32_t)c * ACH;
+          sts128(dst + img_off(r, 16 * p), pa[0], pa[1], pa[2], pa[3]);
+          sts128(dst + img_off(r, 16 * p + 8), pa[4], pa[5], pa[6], pa[7]);
+          chunk_written(C, c, lane);
+          // A_l^T for the weight gradients, off the MMA's critical path
+          st_transposed16(at, col0, pa, toff);
+          if (c < 3) tmem_wait_ld_regs16(acc[(c + 1) & 1]);
         }
-        tc_fence_before();
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&C.a_full);
-        // A_l^T for the weight gradients (off the MMA's critical path)
-        uint8_t *at = P.at[L] + t * TILE_AT + (uint32_t)(r >> 6) * 32768u;
-#pragma unroll
-        for (int blk = 0; blk < 2; ++blk)
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) st_transposed(at, r, 64 * p + 32 * blk + 2 * jj, pa[blk][jj], lane);
       }
       if (!ok) break;
       // layer 5: v = A4 W5^T + b5, the loss and dV
-      if (!mbar_wait(&C.acc_full, accw & 1u, abort)) {
+      if (!mbar_wait(&C.acc_full[gl & 1], (uint32_t)(gl >> 1) & 1u, abort)) {
         ok = false;
         break;
       }
-      ++accw;
       tc_fence_after();
       if (p == 0) {
         float v[4];
-        tmem_ld4(tl, v);
+        tmem_ld4(tl + (uint32_t)(gl & 1) * 256u, v);
         tmem_wait_ld_regs4(v);
         double part = 0.0;
-        float dv[4], u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (valid && P.gen) {
-          batch_u(P.g, P.B, b, u);
-        } else if (valid) {
-#pragma unroll
-          for (int o = 0; o < 4; ++o) u[o] = __ldg(P.U + b * 4 + o);
-        }
+        float dv[4];
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
           dv[o] = 0.0f;
@@ -500,21 +568,22 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
         for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
         if (lane == 0 && part != 0.0) atomicAdd(P.loss, part / (double)P.B);
       }
+      ++gl;
       tc_fence_before();
     }
     if (!ok && lane == 0) fail(C, P.err, 23);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, 256);
+  if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
 // Input gradients: per tile the rounds dZ4 = (dV W5) S4 (K = 16, the dV image
-// from the forward kernel), then dZ3, dZ2, dZ1 (K = 256 against W_l^T). The
-// epilogue of a round writes dZ as the next round's A operand (shared memory)
-// and dZ^T for the weight gradients; S_l is loaded before the accumulator is
-// ready. After the last round the epilogue still signals a_full: the next
-// tile's first MMA overwrites the accumulator it has just read.
+// from the forward kernel), then dZ3, dZ2, dZ1 (K = 256 against W_l^T), the
+// rounds alternating between two accumulators. The epilogue of a round
+// writes dZ chunk by chunk as the next round's A operand (shared memory;
+// the MMAs of the next round start on each chunk once written) and dZ^T for
+// the weight gradients; S_l is loaded before the accumulator is ready.
 __global__ void __launch_bounds__(FB_THREADS, 1) bwd_kernel(KP P) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -523,71 +592,49 @@ __global__ void __launch_bounds__(FB_THREADS, 1) bwd_kernel(KP P) {
   const uint32_t sb = raw + pad;
   Ctl &C = *reinterpret_cast<Ctl *>(sm + S_CTL);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) {
-      mbar_init(&C.full[s], 1);
-      mbar_init(&C.empty[s], 1);
-    }
-    mbar_init(&C.aux_full, 1);
-    mbar_init(&C.aux_empty, 1);
-    mbar_init(&C.a_full, NEPI);
-    mbar_init(&C.acc_full, 1);
-    mbar_init(&C.drain, 1);
-    C.abort = 0;
-    fence_mbar_init();
-  }
-  if (warp == 1) {
-    tmem_alloc(&C.tmem_base, 256);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = C.tmem_base;
+  const uint32_t tmem = fb_setup(C, warp);
   volatile int *abort = &C.abort;
 
   if (warp == 0) {
     if (lane == 0) produce<true>(C, P, sm, WB5, abort);
   } else if (warp == 1) {
-    int used = 0, it = 0;
-    uint32_t af = 0;
+    int used = 0, it = 0, gl = 0;
+    uint32_t af[4] = {0u, 0u, 0u, 0u};
     bool ok = true;
     for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x, ++it) {
-      for (int R = 0; R < 4 && ok; ++R) {
-        if ((R > 0 || it > 0)) {
-          if (!mbar_wait(&C.a_full, af & 1u, abort)) {
-            ok = false;
-            break;
-          }
-          ++af;
-        }
-        if (R == 0 && !mbar_wait(&C.aux_full, (uint32_t)it & 1u, abort)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const int nch = R == 0 ? 1 : 4;
-        for (int c = 0; c < nch && ok; ++c, ++used) {
+      for (int R = 0; R < 4 && ok; ++R, ++gl) {
+        const uint32_t acc = tmem + (uint32_t)(gl & 1) * 256u;
+        if (R == 0) {
           const int s = used % NST;
-          if (!mbar_wait(&C.full[s], (uint32_t)(used / NST) & 1u, abort)) {
+          if (!mbar_wait(&C.aux_full, (uint32_t)it & 1u, abort) ||
+              !mbar_wait(&C.full[s], (uint32_t)(used / NST) & 1u, abort)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint64_t db = sdesc(sb + S_ST + (uint32_t)s * WCH);
-          if (R == 0) {
-            mma_f16_w(tmem, sdesc(sb + S_AUX), db, kID256, 0u);
-          } else {
-            const uint64_t da = sdesc(sb + S_A + (uint32_t)c * ACH);
-            for (int k = 0; k < 4; ++k)
-              mma_f16_w(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kID256, (c | k) != 0);
-          }
+          mma_f16_w(acc, sdesc(sb + S_AUX), sdesc(sb + S_ST + (uint32_t)s * WCH), kID256, 0u);
           mma_commit_w(&C.empty[s]);
+          mma_commit_w(&C.aux_empty);
+          ++used;
+        } else {
+          for (int c = 0; c < 4 && ok; ++c) {
+            const int s = used % NST;
+            if (!mbar_wait(&C.a_full[c], af[c] & 1u, abort) ||
+                !mbar_wait(&C.full[s], (uint32_t)(used / NST) & 1u, abort)) {
+              ok = false;
+              break;
+            }
+            ++af[c];
+            tc_fence_after();
+            const uint64_t da = sdesc(sb + S_A + (uint32_t)c * ACH), db = sdesc(sb + S_ST + (uint32_t)s * WCH);
+            for (int k = 0; k < 4; ++k)
+              mma_f16_w(acc, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kID256, (c | k) != 0);
+            mma_commit_w(&C.empty[s]);
+            ++used;
+          }
+          if (!ok) break;
         }
-        if (!ok) break;
-        if (R == 0) mma_commit_w(&C.aux_empty);
-        mma_commit_w(&C.acc_full);
+        mma_commit_w(&C.acc_full[gl & 1]);
       }
     }
     if (!ok && lane == 0) fail(C, P.err, 24);
@@ -598,56 +645,59 @@ __global__ void __launch_bounds__(FB_THREADS, 1) bwd_kernel(KP P) {
     const int e = warp - 2, q = warp & 3, p = e >> 2;
     const int r = 32 * q + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
-    uint32_t accw = 0;
+    const TOff toff = t_offsets(r, lane);
+    int gl = 0;  // rounds so far: accumulator gl & 1, its (gl >> 1)-th use
     bool ok = true;
     for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
-      for (int R = 0; R < 4; ++R) {
+      for (int R = 0; R < 4; ++R, ++gl) {
         const int Lo = 3 - R;  // dZ of hidden layer Lo + 1
-        uint32_t sv[32];
-        const uint32_t *sl = P.s[Lo] + t * (TILE_S / 4) + (uint32_t)(32 * p) * TR + r;
+        // S_l of this thread's 16 columns of chunk c: words 32 c + 8 p .. + 7
+        // (one chunk ahead of its use)
+        uint32_t sv[8], sn[8];
+        const uint32_t *sl = P.s[Lo] + t * (TILE_S / 4) + r + (8 * p) * TR;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) sv[i] = __ldg(sl + i * TR);
-        if (!mbar_wait(&C.acc_full, accw & 1u, abort)) {
+        for (int jj = 0; jj < 8; ++jj) sv[jj] = __ldg(sl + jj * TR);
+        if (!mbar_wait(&C.acc_full[gl & 1], (uint32_t)(gl >> 1) & 1u, abort)) {
           ok = false;
           break;
         }
-        ++accw;
         tc_fence_after();
-        uint32_t pd[2][16];
-#pragma unroll
-        for (int blk = 0; blk < 2; ++blk) {
-          uint32_t acc[32];
-          tmem_ld32_raw(tl + (uint32_t)(64 * p + 32 * blk), acc);
-          tmem_wait_ld_regs(acc);
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const uint32_t sw = sv[16 * blk + jj];
-            pd[blk][jj] = pack2(__uint_as_float(acc[2 * jj]) * lo_f(sw),
-                                __uint_as_float(acc[2 * jj + 1]) * hi_f(sw));
-          }
-          if (Lo > 0) {
-#pragma unroll
-            for (int g = 0; g < 4; ++g)
-              sts128(sb + S_A + (uint32_t)p * ACH + img_off(r, 32 * blk + 8 * g), pd[blk][4 * g],
-                     pd[blk][4 * g + 1], pd[blk][4 * g + 2], pd[blk][4 * g + 3]);
-          }
-        }
-        tc_fence_before();
-        if (Lo > 0) fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&C.a_full);
+        const uint32_t tacc = tl + (uint32_t)(gl & 1) * 256u;
         uint8_t *dz = P.dzt[Lo] + t * TILE_AT + (uint32_t)(r >> 6) * 32768u;
+        // chunk c + 1's accumulator columns and S words load while chunk c converts
+        uint32_t acc[2][16];
+        acc_ld16(tacc + (uint32_t)(16 * p), acc[0]);
 #pragma unroll
-        for (int blk = 0; blk < 2; ++blk)
+        for (int c = 0; c < 4; ++c) {
+          const int col0 = 64 * c + 16 * p;
+          if (c < 3) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) st_transposed(dz, r, 64 * p + 32 * blk + 2 * jj, pd[blk][jj], lane);
+            for (int jj = 0; jj < 8; ++jj) sn[jj] = __ldg(sl + (32 * (c + 1) + jj) * TR);
+            tmem_ld16_raw(tacc + (uint32_t)(col0 + 64), acc[(c + 1) & 1]);
+          }
+          uint32_t pd[8];
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+            pd[jj] = pack2(__uint_as_float(acc[c & 1][2 * jj]) * lo_f(sv[jj]),
+                           __uint_as_float(acc[c & 1][2 * jj + 1]) * hi_f(sv[jj]));
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) sv[jj] = sn[jj];
+          if (Lo > 0) {
+            const uint32_t dst = sb + S_A + (uint32_t)c * ACH;
+            sts128(dst + img_off(r, 16 * p), pd[0], pd[1], pd[2], pd[3]);
+            sts128(dst + img_off(r, 16 * p + 8), pd[4], pd[5], pd[6], pd[7]);
+            chunk_written(C, c, lane);
+          }
+          st_transposed16(dz, col0, pd, toff);
+          if (c < 3) tmem_wait_ld_regs16(acc[(c + 1) & 1]);
+        }
       }
     }
     if (!ok && lane == 0) fail(C, P.err, 25);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, 256);
+  if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
 // ---- weight gradients -------------------------------------------------------
@@ -781,9 +831,10 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(KP P) {
       tc_fence_after();
       float *ws = P.ws + (int64_t)split * P_TOTAL;
       if (!w5) {
-        const int64_t wofs[4] = {P_W1, P_W2, P_W3, P_W4}, bofs[4] = {P_B1, P_B2, P_B3, P_B4};
+        const int64_t wofs = layer == 0 ? P_W1 : layer == 1 ? P_W2 : layer == 2 ? P_W3 : P_W4;
+        const int64_t bofs = layer == 0 ? P_B1 : layer == 1 ? P_B2 : layer == 2 ? P_B3 : P_B4;
         const int o = 128 * h + m;
-        float *row = ws + wofs[layer] + (int64_t)o * nmain;
+        float *row = ws + wofs + (int64_t)o * nmain;
         for (uint32_t cb = 0; cb < nmain; cb += 32) {
           uint32_t acc[32];
           tmem_ld32_raw(tl + cb, acc);
@@ -797,7 +848,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(KP P) {
         float bv[4];
         tmem_ld4(tl + 256, bv);
         tmem_wait_ld_regs4(bv);
-        ws[bofs[layer] + o] = bv[0];
+        ws[bofs + o] = bv[0];
       } else {
         float v[4];
         tmem_ld4(tl, v);
@@ -880,7 +931,7 @@ void release(Bufs &b) {
 
 cudaError_t pack(cudaStream_t s, Bufs &b, float *params) {
   if (!b.img) return cudaErrorInvalidValue;
-  update_kernel<<<(unsigned)((P_TOTAL + 255) / 256), 256, 0, s>>>(
+  update_kernel<<<(unsigned)((P_TOTAL / 4 + 255) / 256), 256, 0, s>>>(
       4, nullptr, 0, nullptr, params, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, b.img);
   return cudaGetLastError();
 }
@@ -921,7 +972,7 @@ cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const Gen *gen, const float
   const int S = (int)(ntiles < b.max_splits ? ntiles : b.max_splits);
   wgrad_kernel<<<dim3(kJobs, (unsigned)S), WG_THREADS, WG_SMEM, s>>>(P);
   const Adam a = adam ? *adam : Adam{0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f};
-  update_kernel<<<(unsigned)((P_TOTAL + 255) / 256), 256, 0, s>>>(
+  update_kernel<<<(unsigned)((P_TOTAL / 4 + 255) / 256), 256, 0, s>>>(
       adam ? 7 : 1, b.ws, S, grad, params, m, v, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2, b.img);
   return cudaGetLastError();
 }
