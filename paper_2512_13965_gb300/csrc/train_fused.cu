@@ -86,85 +86,131 @@ __device__ __forceinline__ void silu_and_grad(float h, float &a, float &s) {
   s = fmaf(sg, fmaf(-h, th, h), sg);
 }
 
-// ---- weight images and the update kernel -----------------------------------
+// ---- the update kernel ------------------------------------------------------
 
-// Element (n, k) of a B operand with rows n and K index k, chunked by 64 K:
-// chunk c = k / 64 at c * chunk_bytes.
-__device__ __forceinline__ void put_w(uint8_t *img, uint32_t base, uint32_t chunk_bytes, int n, int k,
-                                      float w) {
-  *reinterpret_cast<uint16_t *>(img + base + (uint32_t)(k >> 6) * chunk_bytes + img_off(n, k)) =
-      bf16_bits(w);
-}
+// One block per tile of a weight matrix (rows = outputs), four consecutive
+// parameters per thread: the batch slices of the gradient are loaded at once
+// and summed in slice order (deterministic), AdamW updates the FP32 master
+// weights and moments, and the BF16 images of the next step are written
+// coalesced: the forward image (rows = outputs, K = inputs) from each
+// thread's 4 inputs, the transposed image (rows = inputs, K = outputs)
+// through a transpose in shared memory with 16-byte stores.
+//   blocks 0-191:   W2..W4, tiles of 16 outputs x 64 inputs
+//   blocks 192-207: W1, tiles of 16 outputs x 32 inputs (forward image only)
+//   blocks 208-211: W5, 4 outputs x 64 inputs
+//   block 212:      the biases (no images)
+// mode bit 0: grad = sum of the slices; bit 1: AdamW; bit 2: the images.
+constexpr int kUpdBlocks = 213;
+constexpr int kMaxSplits = 16;
 
-// The BF16 images of parameter i (weights only; biases enter in FP32).
-__device__ __forceinline__ void pack_param(uint8_t *img, int64_t i, float w) {
-  if (i < P_B1) {  // W1 [256][32]: forward operand, rows = outputs, K = inputs
-    put_w(img, WF1, 32768, (int)(i >> 5), (int)(i & 31), w);
-    return;
-  }
-  const int64_t wl[3] = {P_W2, P_W3, P_W4};
-  const uint32_t fo[3] = {WF2, WF3, WF4}, bo[3] = {WB2, WB3, WB4};
+struct Upd {
+  int mode, S;
+  const float *ws;
+  float *grad, *p, *m, *v;
+  float lr, b1, b2, eps, wd, bc1, bc2;
+  uint8_t *img;
+};
+
+// Parameters i .. i + 3 (i a multiple of 4): slice sum, AdamW; the updated
+// weights in w.
+__device__ __forceinline__ void upd4(const Upd &U, int64_t i, float (&w)[4]) {
+  float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (U.mode & 1) {
+    float4 part[kMaxSplits];
 #pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    if (i >= wl[l] && i < wl[l] + 65536) {
-      const int o = (int)((i - wl[l]) >> 8), in = (int)((i - wl[l]) & 255);
-      put_w(img, fo[l], 32768, o, in, w);  // forward: rows = outputs, K = inputs
-      put_w(img, bo[l], 32768, in, o, w);  // input gradient: rows = inputs, K = outputs
-      return;
-    }
+    for (int s = 0; s < kMaxSplits; ++s)
+      if (s < U.S) part[s] = __ldg(reinterpret_cast<const float4 *>(U.ws + (int64_t)s * P_TOTAL + i));
+#pragma unroll
+    for (int s = 0; s < kMaxSplits; ++s)
+      if (s < U.S) {
+        g.x += part[s].x;
+        g.y += part[s].y;
+        g.z += part[s].z;
+        g.w += part[s].w;
+      }
+    *reinterpret_cast<float4 *>(U.grad + i) = g;
+  } else if (U.mode & 2) {
+    g = *reinterpret_cast<const float4 *>(U.grad + i);
   }
-  if (i >= P_W5 && i < P_B5) {
-    const int o = (int)((i - P_W5) >> 8), in = (int)((i - P_W5) & 255);
-    put_w(img, WF5, 2048, o, in, w);   // 16 rows (4 used) per chunk
-    put_w(img, WB5, 32768, in, o, w);  // K = the 4 outputs (the rest of the chunk zero)
-  }
-}
-
-// Four consecutive parameters per thread (P_TOTAL is a multiple of 4).
-// mode bit 0: grad[i] = sum over the S slices of ws (slice order);
-//      bit 1: AdamW on params with grad; bit 2: write the weight images.
-static_assert(P_TOTAL % 4 == 0, "float4 parameter groups");
-__global__ void update_kernel(int mode, const float *__restrict__ ws, int S, float *__restrict__ grad,
-                              float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
-                              float lr, float b1, float b2, float eps, float wd, float bc1, float bc2,
-                              uint8_t *__restrict__ img) {
-  const int64_t i4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i4 >= P_TOTAL / 4) return;
-  const int64_t i = 4 * i4;
-  if (mode & 1) {
-    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-#pragma unroll 4
-    for (int s = 0; s < S; ++s) {
-      const float4 w = __ldg(reinterpret_cast<const float4 *>(ws + (int64_t)s * P_TOTAL + i));
-      acc.x += w.x;
-      acc.y += w.y;
-      acc.z += w.z;
-      acc.w += w.w;
-    }
-    *reinterpret_cast<float4 *>(grad + i) = acc;
-  }
-  float4 w4 = *reinterpret_cast<const float4 *>(p + i);
-  float w[4] = {w4.x, w4.y, w4.z, w4.w};
-  if (mode & 2) {
-    const float4 g4 = *reinterpret_cast<const float4 *>(grad + i);
-    const float4 m4 = *reinterpret_cast<const float4 *>(m + i), v4 = *reinterpret_cast<const float4 *>(v + i);
-    const float gi[4] = {g4.x, g4.y, g4.z, g4.w}, mo[4] = {m4.x, m4.y, m4.z, m4.w},
-                vo[4] = {v4.x, v4.y, v4.z, v4.w};
+  const float4 p4 = *reinterpret_cast<const float4 *>(U.p + i);
+  w[0] = p4.x; w[1] = p4.y; w[2] = p4.z; w[3] = p4.w;
+  if (U.mode & 2) {
+    const float4 m4 = *reinterpret_cast<const float4 *>(U.m + i), v4 = *reinterpret_cast<const float4 *>(U.v + i);
+    const float gi[4] = {g.x, g.y, g.z, g.w}, mo[4] = {m4.x, m4.y, m4.z, m4.w}, vo[4] = {v4.x, v4.y, v4.z, v4.w};
     float mn[4], vn[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      mn[u] = b1 * mo[u] + (1.0f - b1) * gi[u];
-      vn[u] = b2 * vo[u] + (1.0f - b2) * gi[u] * gi[u];
-      const float mh = mn[u] / bc1, vh = vn[u] / bc2;
-      w[u] = w[u] * (1.0f - lr * wd) - lr * mh / (sqrtf(vh) + eps);
+      mn[u] = U.b1 * mo[u] + (1.0f - U.b1) * gi[u];
+      vn[u] = U.b2 * vo[u] + (1.0f - U.b2) * gi[u] * gi[u];
+      const float mh = mn[u] / U.bc1, vh = vn[u] / U.bc2;
+      w[u] = w[u] * (1.0f - U.lr * U.wd) - U.lr * mh / (sqrtf(vh) + U.eps);
     }
-    *reinterpret_cast<float4 *>(m + i) = make_float4(mn[0], mn[1], mn[2], mn[3]);
-    *reinterpret_cast<float4 *>(v + i) = make_float4(vn[0], vn[1], vn[2], vn[3]);
-    *reinterpret_cast<float4 *>(p + i) = make_float4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<float4 *>(U.m + i) = make_float4(mn[0], mn[1], mn[2], mn[3]);
+    *reinterpret_cast<float4 *>(U.v + i) = make_float4(vn[0], vn[1], vn[2], vn[3]);
+    *reinterpret_cast<float4 *>(U.p + i) = make_float4(w[0], w[1], w[2], w[3]);
   }
-  if (mode & 4)
+}
+
+__global__ void __launch_bounds__(256) update_kernel(Upd U) {
+  __shared__ __align__(16) uint16_t T[64][24];  // transposed tile [input][output], 48-byte rows
+  const int blk = blockIdx.x, tid = threadIdx.x;
+  const bool pack = (U.mode & 4) != 0;
+  if (blk == kUpdBlocks - 1) {  // biases: b1..b4 (256 each) and b5 (4), 257 groups of 4
+    for (int j = tid; j < 257; j += 256) {
+      const int l = j >> 6;
+      const int64_t i = (l == 0 ? P_B1 : l == 1 ? P_B2 : l == 2 ? P_B3 : l == 3 ? P_B4 : P_B5) + 4 * (j & 63);
+      float w[4];
+      upd4(U, i, w);
+    }
+    return;
+  }
+  int64_t base;
+  int R, Cn, stride, o0, i0;
+  uint32_t fimg, fchunk, timg;
+  if (blk < 192) {
+    const int l = blk >> 6, sub = blk & 63;
+    base = P_W2 + (int64_t)l * (65536 + 256);
+    R = 16; Cn = 64; stride = 256; o0 = (sub >> 2) * 16; i0 = (sub & 3) * 64;
+    fimg = l == 0 ? WF2 : l == 1 ? WF3 : WF4;
+    timg = l == 0 ? WB2 : l == 1 ? WB3 : WB4;
+    fchunk = 32768;
+  } else if (blk < 208) {
+    base = P_W1;
+    R = 16; Cn = 32; stride = 32; o0 = (blk - 192) * 16; i0 = 0;
+    fimg = WF1; fchunk = 32768; timg = 0;
+  } else {
+    base = P_W5;
+    R = 4; Cn = 64; stride = 256; o0 = 0; i0 = (blk - 208) * 64;
+    fimg = WF5; fchunk = 2048; timg = WB5;
+  }
+  const int groups = Cn / 4;
+  const int row = tid / groups, cg = (tid % groups) * 4;
+  if (row < R) {
+    const int o = o0 + row, i = i0 + cg;
+    float w[4];
+    upd4(U, base + (int64_t)o * stride + i, w);
+    if (pack) {
+      *reinterpret_cast<uint2 *>(U.img + fimg + (uint32_t)(i >> 6) * fchunk + img_off(o, i & 63)) =
+          make_uint2(pack2(w[0], w[1]), pack2(w[2], w[3]));
+      if (timg) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) pack_param(img, i + u, w[u]);
+        for (int u = 0; u < 4; ++u) T[cg + u][row] = bf16_bits(w[u]);
+      }
+    }
+  }
+  if (!pack || !timg) return;
+  __syncthreads();
+  if (R == 16) {  // 64 inputs x 2 groups of 8 outputs
+    if (tid < 128) {
+      const int ii = tid >> 1, og = (tid & 1) * 8;
+      const uint4 q = *reinterpret_cast<const uint4 *>(&T[ii][og]);
+      const int o = o0 + og, i = i0 + ii;
+      *reinterpret_cast<uint4 *>(U.img + timg + (uint32_t)(o >> 6) * 32768u + img_off(i, o & 63)) = q;
+    }
+  } else if (tid < 64) {  // W5: input rows, K = the 4 outputs (8 bytes)
+    const int i = i0 + tid;
+    *reinterpret_cast<uint2 *>(U.img + timg + img_off(i, 0)) = *reinterpret_cast<const uint2 *>(&T[tid][0]);
+  }
 }
 
 // ---- forward and input-gradient kernels ---------------------------------------
@@ -901,6 +947,7 @@ cudaError_t alloc(Bufs &b, int64_t batch, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMalloc(&b.act, (size_t)tiles * TILE_BYTES);
   b.max_splits = sm_count() / kJobs;
   if (b.max_splits < 1) b.max_splits = 1;
+  if (b.max_splits > kMaxSplits) b.max_splits = kMaxSplits;
   if (e == cudaSuccess) e = cudaMalloc(&b.ws, (size_t)b.max_splits * P_TOTAL * sizeof(float));
   // zero padding of the images (K beyond the operand, unused rows) stays zero
   if (e == cudaSuccess) e = cudaMemsetAsync(b.img, 0, WIMG_BYTES, s);
@@ -931,8 +978,12 @@ void release(Bufs &b) {
 
 cudaError_t pack(cudaStream_t s, Bufs &b, float *params) {
   if (!b.img) return cudaErrorInvalidValue;
-  update_kernel<<<(unsigned)((P_TOTAL / 4 + 255) / 256), 256, 0, s>>>(
-      4, nullptr, 0, nullptr, params, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, b.img);
+  Upd U{};
+  U.mode = 4;
+  U.p = params;
+  U.bc1 = U.bc2 = 1.0f;
+  U.img = b.img;
+  update_kernel<<<kUpdBlocks, 256, 0, s>>>(U);
   return cudaGetLastError();
 }
 
@@ -972,8 +1023,8 @@ cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const Gen *gen, const float
   const int S = (int)(ntiles < b.max_splits ? ntiles : b.max_splits);
   wgrad_kernel<<<dim3(kJobs, (unsigned)S), WG_THREADS, WG_SMEM, s>>>(P);
   const Adam a = adam ? *adam : Adam{0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f};
-  update_kernel<<<(unsigned)((P_TOTAL / 4 + 255) / 256), 256, 0, s>>>(
-      adam ? 7 : 1, b.ws, S, grad, params, m, v, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2, b.img);
+  const Upd upd{adam ? 7 : 1, S, b.ws, grad, params, m, v, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2, b.img};
+  update_kernel<<<kUpdBlocks, 256, 0, s>>>(upd);
   return cudaGetLastError();
 }
 
