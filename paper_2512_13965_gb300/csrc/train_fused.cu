@@ -86,6 +86,14 @@ __device__ __forceinline__ void silu_and_grad(float h, float &a, float &s) {
   s = fmaf(sg, fmaf(-h, th, h), sg);
 }
 
+// Programmatic dependent launch: the kernels of a step are launched so that
+// the next one may start while this one finishes. Work before grid_dep_wait()
+// touches nothing the previous kernel writes or reads; grid_dep_launch()
+// comes after it, so a dependent's early work never overlaps a kernel older
+// than its predecessor.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- the update kernel ------------------------------------------------------
 
 // One block per tile of a weight matrix (rows = outputs), four consecutive
@@ -154,6 +162,8 @@ __device__ __forceinline__ void upd4(const Upd &U, int64_t i, float (&w)[4]) {
 __global__ void __launch_bounds__(256) update_kernel(Upd U) {
   __shared__ __align__(16) uint16_t T[64][24];  // transposed tile [input][output], 48-byte rows
   const int blk = blockIdx.x, tid = threadIdx.x;
+  grid_dep_wait();  // the gradient slices
+  grid_dep_launch();
   const bool pack = (U.mode & 4) != 0;
   if (blk == kUpdBlocks - 1) {  // biases: b1..b4 (256 each) and b5 (4), 257 groups of 4
     for (int j = tid; j < 257; j += 256) {
@@ -261,6 +271,7 @@ static_assert(FB_SMEM <= 227 * 1024, "shared memory per CTA");
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) { return smem_desc(addr, 1024, kSwizzle128B); }
 
+
 __device__ __forceinline__ void fail(Ctl &c, int *err, int code) {
   c.abort = 1;
   atomicExch(err, code);
@@ -273,6 +284,15 @@ template <bool BWD>
 __device__ void produce(Ctl &C, const KP &P, unsigned char *sm, uint32_t base, volatile int *abort) {
   int issued = 0, it = 0;
   bool ok = true;
+  // the backward weight images were written before the previous kernel ran:
+  // the first stages fill before the wait
+  if (BWD)
+    for (; issued < NST; ++issued) {
+      mbar_arrive_expect_tx(&C.full[issued], WCH);
+      bulk_g2s(sm + S_ST + issued * WCH, P.img + base + (uint32_t)issued * WCH, WCH, &C.full[issued]);
+    }
+  grid_dep_wait();
+  grid_dep_launch();
   for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x, ++it) {
     if (BWD) {
       if (it > 0 && !mbar_wait(&C.aux_empty, (uint32_t)(it - 1) & 1u, abort)) {
@@ -282,7 +302,7 @@ __device__ void produce(Ctl &C, const KP &P, unsigned char *sm, uint32_t base, v
       mbar_arrive_expect_tx(&C.aux_full, ACH);
       bulk_g2s(sm + S_AUX, P.dv + t * TILE_DV, ACH, &C.aux_full);
     }
-    for (int g = 0; g < kTileChunks; ++g, ++issued) {
+    for (int g = (BWD && it == 0) ? NST : 0; g < kTileChunks; ++g, ++issued) {
       const int s = issued % NST;
       if (issued >= NST && !mbar_wait(&C.empty[s], (uint32_t)(issued / NST - 1) & 1u, abort)) {
         ok = false;
@@ -436,16 +456,12 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
   float *bias = reinterpret_cast<float *>(sm + S_BIAS);  // [4][256] halved, then b5[4]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  for (int i = threadIdx.x; i < 1028; i += FB_THREADS) {
-    const int64_t src = i < 1024 ? (i < 256 ? P_B1 : i < 512 ? P_B2 - 256 : i < 768 ? P_B3 - 512 : P_B4 - 768) + i
-                                 : P_B5 + (i - 1024);
-    bias[i] = i < 1024 ? 0.5f * P.params[src] : P.params[src];  // layers 1-4 halved (h = z / 2)
-  }
   const uint32_t tmem = fb_setup(C, warp);
   volatile int *abort = &C.abort;
 
   if (warp == 0) {
     if (lane == 0) {
+      grid_dep_wait();  // the weight images of this step
       mbar_arrive_expect_tx(&C.aux_full, 8192);
       bulk_g2s(sm + S_AUX, P.img + WF5, 8192, &C.aux_full);
       produce<false>(C, P, sm, WF1, abort);
@@ -503,6 +519,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
     const TOff toff = t_offsets(r, lane);
     int gl = 0;  // layers so far: accumulator gl & 1, its (gl >> 1)-th use
     bool ok = true;
+    if (!P.gen) grid_dep_wait();  // rows given in X0 / U by the previous kernel
     for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       const int64_t b = t * TR + r;
       const bool valid = b < P.B;  // rows past the batch: finite values, zero dV
@@ -532,6 +549,18 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
         }
         sts128(sb + S_A + img_off(rr, 8 * gq), pack2(x[0], x[1]), pack2(x[2], x[3]), pack2(x[4], x[5]),
                pack2(x[6], x[7]));
+        if (t == blockIdx.x) {
+          // the first tile's rows were drawn before the wait; the biases of
+          // this step are the previous kernel's output
+          grid_dep_wait();
+          grid_dep_launch();
+          for (int i = e * 32 + lane; i < 1028; i += 32 * NEPI) {
+            const int64_t src = i < 1024 ? (i < 256 ? P_B1 : i < 512 ? P_B2 - 256 : i < 768 ? P_B3 - 512 : P_B4 - 768) + i
+                                         : P_B5 + (i - 1024);
+            bias[i] = i < 1024 ? 0.5f * P.params[src] : P.params[src];  // layers 1-4 halved (h = z / 2)
+          }
+          asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");  // the epilogue warps only
+        }
         chunk_written(C, 0, lane);
         uint8_t *xt = P.xt + t * TILE_XT + (uint32_t)(rr >> 6) * 4096u;
 #pragma unroll
@@ -694,6 +723,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) bwd_kernel(KP P) {
     const TOff toff = t_offsets(r, lane);
     int gl = 0;  // rounds so far: accumulator gl & 1, its (gl >> 1)-th use
     bool ok = true;
+    grid_dep_wait();  // S_l and the images of the forward kernel
     for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       for (int R = 0; R < 4; ++R, ++gl) {
         const int Lo = 3 - R;  // dZ of hidden layer Lo + 1
@@ -816,6 +846,8 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(KP P) {
     if (lane == 0) {
       bool ok = true;
       int k = 0;
+      grid_dep_wait();  // dZ^T of the input-gradient kernel
+      grid_dep_launch();
       for (; k < nchunks; ++k) {
         const int s = k % WNST;
         if (k >= WNST && !mbar_wait(&C.empty[s], (uint32_t)(k / WNST - 1) & 1u, abort)) {
@@ -930,6 +962,23 @@ cudaError_t set_smem(Kernel k, size_t bytes, std::atomic<bool> (&done)[kMaxDevic
   return e;
 }
 
+// A launch that may begin while the previous kernel of the stream finishes
+// (the kernel's griddepcontrol.wait orders its dependent work).
+template <typename Arg>
+cudaError_t launch_dep(void (*k)(Arg), dim3 grid, int threads, size_t smem, cudaStream_t s, const Arg &arg) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, arg);
+}
+
 int sm_count() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1018,14 +1067,14 @@ cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const Gen *gen, const float
   P.err = err;
   const int sms = sm_count();
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-  fwd_kernel<<<grid, FB_THREADS, FB_SMEM, s>>>(P);
-  bwd_kernel<<<grid, FB_THREADS, FB_SMEM, s>>>(P);
   const int S = (int)(ntiles < b.max_splits ? ntiles : b.max_splits);
-  wgrad_kernel<<<dim3(kJobs, (unsigned)S), WG_THREADS, WG_SMEM, s>>>(P);
   const Adam a = adam ? *adam : Adam{0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f};
   const Upd upd{adam ? 7 : 1, S, b.ws, grad, params, m, v, a.lr, a.b1, a.b2, a.eps, a.wd, a.bc1, a.bc2, b.img};
-  update_kernel<<<kUpdBlocks, 256, 0, s>>>(upd);
-  return cudaGetLastError();
+  e = launch_dep(fwd_kernel, dim3(grid), FB_THREADS, FB_SMEM, s, P);
+  if (e == cudaSuccess) e = launch_dep(bwd_kernel, dim3(grid), FB_THREADS, FB_SMEM, s, P);
+  if (e == cudaSuccess) e = launch_dep(wgrad_kernel, dim3(kJobs, (unsigned)S), WG_THREADS, WG_SMEM, s, P);
+  if (e == cudaSuccess) e = launch_dep(update_kernel, dim3(kUpdBlocks), 256, 0, s, upd);
+  return e;
 }
 
 }  // namespace tf
