@@ -184,7 +184,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--workload", default="sampler",
                     choices=["sampler", "solve", "hohlraum", "serve", "sweep", "heldout", "sigma",
-                             "walks", "paper"])
+                             "walks", "paper", "train"])
     ap.add_argument("--weights", default=None,
                     help="GMCW file of the boundary model for the solve, serve, sigma, sweep and "
                          "heldout workloads (default: the package's trained network; 'kaiming': "
@@ -203,6 +203,7 @@ def main():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--hist-range", type=float, nargs=2, default=(1e3, 1e5),
                     help="serve: histories per request, log-uniform in [lo, hi]")
+    ap.add_argument("--train-batch", type=int, default=16384, help="train: batch rows per step")
     ap.add_argument("--solve-variants", default=None,
                     help="comma list for --workload solve, e.g. analog,gmc_bf16_rk412 (default: all)")
     args = ap.parse_args()
@@ -222,6 +223,8 @@ def main():
         return run_walks(args)
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "train":
+        return run_train(args)
 
     import numpy as np
     import torch
@@ -826,6 +829,65 @@ def run_walks(args):
                       "workload": "2^22 entries, tau logU[0.1,1000], c U[0.5,0.999], implicit capture",
                       "steps": args.steps, "warmup": args.warmup, "l2": "flushed (256 MiB write)",
                       "results": out}))
+    ctx.close()
+
+
+# FLOP per batch row of one training step: forward 2 (32*256 + 3*256^2 +
+# 256*4) (layer 1 at its 32 padded inputs) and twice that for the input and
+# weight gradients
+TRAIN_FLOP_PER_ROW = 3 * 2 * (32 * 256 + 3 * 256 * 256 + 256 * 4)
+
+
+def run_train(args):
+    """The BF16 training step of Eq. 9 (gmc_train_steps, precision BF16):
+    batch rows drawn from 2^20 GPU-walk training samples, forward, loss,
+    backward and AdamW, at --train-batch rows. Whole steps timed with CUDA
+    events on the context's stream: --warmup steps, then --steps steps, median
+    of 5 such runs (at least 2000 steps each). The working set is the step's own (about 100 MB of
+    operand images per 16384 rows), not flushed: consecutive steps of a
+    training run meet the same cache state."""
+    import numpy as np
+    import torch
+    g, ctx = _context(argparse.Namespace(**{**vars(args), "weights": "kaiming", "internal_weights": "none"}))
+    stream = torch.cuda.Stream()
+    g.gmc_set_stream(ctx, stream)
+    n = 1 << 20
+    cond = torch.empty(5, n, device="cuda")
+    y = torch.empty(4, n, device="cuda")
+    g.gmc_train_data(ctx, n, 3, 0.1, 1000.0, 0.5, 0.999, cond, y)
+    B = args.train_batch
+    cfg = g.gmc_train_config(batch=B, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01,
+                             seed=7, precision=g.GMC_BF16)
+    g.gmc_train_begin(ctx, n, cond, y, cfg)
+    steps = max(args.steps, 2000)  # long enough for the clock samples
+    clk = Clocks(0)
+    clk.start()
+    runs = []
+    for _ in range(5):
+        g.gmc_train_steps(ctx, max(args.warmup, 3))
+        g.gmc_synchronize(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.gmc_train_steps(ctx, steps)
+        e1.record(stream)
+        g.gmc_synchronize(ctx)
+        runs.append(e0.elapsed_time(e1) / steps)
+    clocks = clk.stop()
+    losses = np.zeros(8, np.float32)
+    g.gmc_train_steps(ctx, 8, losses)
+    ms = statistics.median(runs)
+    pk = peaks()
+    tflops = TRAIN_FLOP_PER_ROW * B / (ms * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "training rows/s (BF16 tensor-core step, Eq. 9)", "unit": "rows/s",
+        "value": B / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "warmup": max(args.warmup, 3),
+        "workload": "CFM training step, batch %d, 2^20 GPU-walk samples (tau logU[0.1,1000], "
+                    "c U[0.5,0.999]), untrained Kaiming-normal start" % B,
+        "flop_per_step": TRAIN_FLOP_PER_ROW * B, "loss_last": float(losses[-1]),
+        "runs_ms": runs, "gpu_launches_per_step": 4,
+        "roofline": {"bound": "tensor", "achieved": tflops, "peak": pk["bf16"], "unit": "TFLOP/s",
+                     "frac": tflops / pk["bf16"], "peak_src": pk["src"] + " bf16 burst"},
+        "clocks": clocks}))
     ctx.close()
 
 
