@@ -42,7 +42,7 @@
 // p = (w - 2) / 4; the warps with p = 0 (p = 1) keep the ODE state of tile X
 // (Y) in registers.
 //
-// Synchronization without multicast: the MMA completion is committed to the
+// Synchronization: the MMA completion is committed to the
 // even CTA's barriers only, and threads relay it to the odd CTA with remote
 // mbarrier arrivals (mapa + mbarrier.arrive.release.cluster); the odd CTA's
 // copy completions and activation writes reach the even CTA the same way.
