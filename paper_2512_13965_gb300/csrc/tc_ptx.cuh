@@ -435,7 +435,7 @@ __device__ __forceinline__ void mma_pair_f16_w(uint32_t d_tmem, uint64_t a_desc,
 }
 
 // Arrive on this CTA's mbarrier `bar` once the pair MMAs issued so far by
-// this thread have completed (warp-wide, one lane issues; no multicast).
+// this thread have completed (warp-wide, one lane issues; this CTA only).
 __device__ __forceinline__ void mma_pair_commit_w(uint64_t *bar) {
   asm volatile(
       "{\n\t.reg .pred e;\n\t"
