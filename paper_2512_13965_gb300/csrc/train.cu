@@ -411,9 +411,19 @@ cudaError_t fwd_bwd(cudaStream_t s, TrainState &T, double *loss_slot) {
 // The gradient of the batch in X0/U into T.grads; on the BF16 path with
 // `adam` the same launches also apply AdamW (train_fused.cu).
 cudaError_t step_grads(cudaStream_t s, TrainState &T, double *loss_slot, const tf::Adam *adam = nullptr,
-                       const tf::Gen *gen = nullptr) {
-  if (T.cfg.precision == GMC_BF16)
-    return tf::step(s, T.fb, T.B, gen, T.X0, T.U, T.params, T.grads, T.m, T.v, adam, loss_slot, T.err);
+                       const tf::Gen *gen = nullptr, const tf::Gen *next = nullptr) {
+  if (T.cfg.precision == GMC_BF16) {
+    if (!gen)  // rows in X0 / U from the kernel just before
+      return tf::step(s, T.fb, T.B, nullptr, T.X0, T.U, false, T.params, T.grads, T.m, T.v, adam,
+                      loss_slot, T.err);
+    // a training step: its rows were drawn during the previous step when
+    // that step knew it (same seed, step and data), else in the forward kernel
+    const bool have = T.fb.pregen_step == gen->step;
+    const cudaError_t e = tf::step(s, T.fb, T.B, have ? nullptr : gen, T.fb.x0n, T.fb.un, have,
+                                   T.params, T.grads, T.m, T.v, adam, loss_slot, T.err, next);
+    T.fb.pregen_step = next ? next->step : -1;
+    return e;
+  }
   return fwd_bwd(s, T, loss_slot);
 }
 
@@ -618,7 +628,8 @@ gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses) {
       const tf::Adam adam{(float)c.lr, (float)c.beta1, (float)c.beta2, (float)c.eps,
                           (float)c.weight_decay, bc1, bc2};
       const tf::Gen gen{T->cond, T->y, T->n, sd, c.seed, T->step};
-      GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i, &adam, &gen));
+      const tf::Gen next{T->cond, T->y, T->n, sd, c.seed, T->step + 1};
+      GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i, &adam, &gen, &next));
     } else {
       GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i));
       adamw_kernel<<<nb(P_TOTAL, 256), 256, 0, s>>>(P_TOTAL, T->params, T->grads, T->m, T->v,
@@ -779,7 +790,10 @@ gmc_status gmc_train_load_state(gmc_ctx *ctx, const void *blob, size_t nbytes) {
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->params, body, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->m, body + P_TOTAL, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->v, body + 2 * P_TOTAL, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
-  if (T->cfg.precision == GMC_BF16) GMC_CUDA_TRY(ctx, tf::pack(s, T->fb, T->params));
+  if (T->cfg.precision == GMC_BF16) {
+    GMC_CUDA_TRY(ctx, tf::pack(s, T->fb, T->params));
+    T->fb.pregen_step = -1;  // rows drawn for another step or seed
+  }
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   T->step = h.step;
   T->cfg.lr = h.lr;

@@ -94,6 +94,36 @@ __device__ __forceinline__ void silu_and_grad(float h, float &a, float &s) {
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// A whole batch row in the X0 layout and its target, the same values as
+// batch_cols (groups 0-3) and batch_u.
+__device__ __forceinline__ void batch_row(const Gen &G, int64_t B, int64_t b, float *__restrict__ x0row,
+                                          float *__restrict__ urow) {
+  const uint64_t rid = (uint64_t)G.step * (uint64_t)B + (uint64_t)b;
+  const uint4 r0 = philox_draw(G.seed, rid, 0u, kTagTrain);
+  const int64_t idx = (int64_t)(((uint64_t)r0.x * (uint64_t)G.n) >> 32);
+  const float t = u01(r0.y);
+  const float4 z = box_muller4(philox_draw(G.seed, rid, 1u, kTagTrain));
+  const float x0[4] = {z.x, z.y, z.z, z.w};
+  float x[32];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) x[k] = (__ldg(G.cond + k * G.n + idx) - G.sd.cm[k]) * G.sd.cis[k];
+  float u[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const float x1 = (__ldg(G.y + d * G.n + idx) - G.sd.ym[d]) * G.sd.yis[d];
+    x[5 + d] = (1.0f - t) * x0[d] + t * x1;
+    u[d] = x1 - x0[d];
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[9 + j] = time_embedding(j, t);
+#pragma unroll
+  for (int k = 25; k < 32; ++k) x[k] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 32; k += 4)
+    *reinterpret_cast<float4 *>(x0row + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+  *reinterpret_cast<float4 *>(urow) = make_float4(u[0], u[1], u[2], u[3]);
+}
+
 // ---- the update kernel ------------------------------------------------------
 
 // One block per tile of a weight matrix (rows = outputs), four consecutive
@@ -237,8 +267,11 @@ constexpr uint32_t kID256 = idesc_bf16_m128(256), kID32 = idesc_bf16_m128(32),
 
 struct KP {
   int64_t B, ntiles;
-  int gen;  // rows drawn in the forward kernel (Gen) instead of read from X0 / U
-  Gen g;
+  int gen;       // rows drawn in the forward kernel (Gen) instead of read from X0 / U
+  int x0_early;  // X0 / U written before the previous kernel: read before the wait
+  int gen_next;  // the weight-gradient kernel draws the next step's rows (gn) into x0n / un
+  Gen g, gn;
+  float *x0n, *un;
   const float *X0, *U, *params;
   const uint8_t *img;
   uint8_t *xt, *at[4], *dzt[4], *dv, *dvt;
@@ -519,7 +552,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
     const TOff toff = t_offsets(r, lane);
     int gl = 0;  // layers so far: accumulator gl & 1, its (gl >> 1)-th use
     bool ok = true;
-    if (!P.gen) grid_dep_wait();  // rows given in X0 / U by the previous kernel
+    if (!P.gen && !P.x0_early) grid_dep_wait();  // rows given in X0 / U by the previous kernel
     for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       const int64_t b = t * TR + r;
       const bool valid = b < P.B;  // rows past the batch: finite values, zero dV
@@ -905,6 +938,13 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(KP P) {
   } else {
     const int q = warp & 3, m = 32 * q + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+    if (P.gen_next) {
+      // the next step's batch rows (static data only: before any wait),
+      // about one per epilogue thread, drawn while the operands stream in
+      const int64_t nthr = (int64_t)gridDim.x * gridDim.y * 128;
+      for (int64_t b = ((int64_t)split * gridDim.x + job) * 128 + (warp - 2) * 32 + lane; b < P.B; b += nthr)
+        batch_row(P.gn, P.B, b, P.x0n + b * 32, P.un + b * 4);
+    }
     if (mbar_wait(&C.acc_full, 0, abort)) {
       tc_fence_after();
       float *ws = P.ws + (int64_t)split * P_TOTAL;
@@ -998,6 +1038,8 @@ cudaError_t alloc(Bufs &b, int64_t batch, cudaStream_t s) {
   if (b.max_splits < 1) b.max_splits = 1;
   if (b.max_splits > kMaxSplits) b.max_splits = kMaxSplits;
   if (e == cudaSuccess) e = cudaMalloc(&b.ws, (size_t)b.max_splits * P_TOTAL * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&b.x0n, (size_t)tiles * TR * 36 * sizeof(float));
+  if (e == cudaSuccess) b.un = b.x0n + (size_t)tiles * TR * 32;
   // zero padding of the images (K beyond the operand, unused rows) stays zero
   if (e == cudaSuccess) e = cudaMemsetAsync(b.img, 0, WIMG_BYTES, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.act, 0, (size_t)tiles * TILE_BYTES, s);
@@ -1022,6 +1064,7 @@ void release(Bufs &b) {
   if (b.img) cudaFree(b.img);
   if (b.act) cudaFree(b.act);
   if (b.ws) cudaFree(b.ws);
+  if (b.x0n) cudaFree(b.x0n);
   b = Bufs{};
 }
 
@@ -1037,7 +1080,8 @@ cudaError_t pack(cudaStream_t s, Bufs &b, float *params) {
 }
 
 cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const Gen *gen, const float *X0, const float *U,
-                 float *params, float *grad, float *m, float *v, const Adam *adam, double *loss, int *err) {
+                 bool rows_early, float *params, float *grad, float *m, float *v, const Adam *adam,
+                 double *loss, int *err, const Gen *next) {
   const int64_t ntiles = (B + TR - 1) / TR;
   if (B < 1 || !b.img || ntiles > b.tiles || (!gen && (!X0 || !U))) return cudaErrorInvalidValue;
   static std::atomic<bool> a_fwd[kMaxDevices], a_bwd[kMaxDevices], a_wg[kMaxDevices];
@@ -1050,6 +1094,12 @@ cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const Gen *gen, const float
   P.ntiles = ntiles;
   P.gen = gen != nullptr;
   if (gen) P.g = *gen;
+  P.x0_early = rows_early && !gen;
+  P.gen_next = next != nullptr;
+  if (next) P.gn = *next;
+  P.x0n = b.x0n;
+  P.un = b.un;
+
   P.X0 = X0;
   P.U = U;
   P.params = params;

@@ -63,6 +63,10 @@ struct Bufs {
   uint8_t *xt = nullptr, *at[4] = {}, *dzt[4] = {}, *dv = nullptr, *dvt = nullptr;
   uint32_t *s[4] = {};
   float *ws = nullptr;   // max_splits x P_TOTAL
+  // the rows of the following step, drawn by the weight-gradient kernel:
+  // X0 [rows][32] and U [rows][4], valid for step pregen_step (-1: none)
+  float *x0n = nullptr, *un = nullptr;
+  int64_t pregen_step = -1;
 };
 
 // Buffers for batches of up to `batch` rows (images zeroed on `s`).
@@ -78,12 +82,15 @@ cudaError_t pack(cudaStream_t s, Bufs &b, float *params);
 
 // Forward, loss (added to *loss), backward and weight gradients of a batch of
 // B rows, drawn in the forward kernel (gen non-null) or already in X0 [B][32]
-// and U [B][4]; the gradient lands in grad. With adam non-null the same
-// launch that sums the gradient applies AdamW to params and repacks the
-// weight images.
+// and U [B][4] (rows_early: written before the previous kernel ran, so the
+// forward kernel may read them before its wait); the gradient lands in grad.
+// With adam non-null the same launch that sums the gradient applies AdamW to
+// params and repacks the weight images. With next non-null the
+// weight-gradient kernel also draws the rows of step next->step into b.x0n /
+// b.un (its epilogue warps, while the operands stream in).
 cudaError_t step(cudaStream_t s, Bufs &b, int64_t B, const Gen *gen, const float *X0, const float *U,
-                 float *params, float *grad, float *m, float *v, const Adam *adam, double *loss,
-                 int *err);
+                 bool rows_early, float *params, float *grad, float *m, float *v, const Adam *adam,
+                 double *loss, int *err, const Gen *next = nullptr);
 
 }  // namespace tf
 }  // namespace gmc
