@@ -161,6 +161,10 @@ __device__ __forceinline__ void put_face(Bank out, int k, const Exit &x, int nce
   out.ev[k] = x.ev;
 }
 
+// BLOCK: every thread of the block calls this exactly once (grid kernels);
+// the per-request statistics are then combined over the block before the
+// atomics, one set per block when all its warps serve one request.
+template <bool BLOCK = false>
 __device__ void finish_transmission(const Exit &x, const Slot *__restrict__ slots, Rules R,
                                     const Route &rt, DevStats *st, int *slot_live) {
   double dabs = 0.0, dleak = 0.0, droul = 0.0;
@@ -226,10 +230,76 @@ __device__ void finish_transmission(const Exit &x, const Slot *__restrict__ slot
   // active lane belongs to the same request (the common case: births of a
   // request are contiguous and compaction keeps warp order), per lane otherwise
   const unsigned act = __ballot_sync(0xffffffffu, x.active);
-  if (!act) return;
-  const int lead = __ffs(act) - 1;
+  if (!BLOCK && !act) return;
+  const int lead = act ? __ffs(act) - 1 : 0;
   const int slot0 = __shfl_sync(0xffffffffu, x.slot, lead);
   const bool uniform = __all_sync(0xffffffffu, !x.active || x.slot == slot0);
+  if constexpr (BLOCK) {
+    __shared__ double s_d[32][3];              // absorbed, leaked, roulette per warp
+    __shared__ unsigned long long s_u[32][4];  // transmissions, collisions, kills, survivors
+    __shared__ int s_slot[32];                 // the warp's request; -1 none, -2 mixed
+    const int wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    double ab = 0.0, lk = 0.0, ro = 0.0;
+    unsigned long long nc = 0, nk = 0;
+    if (uniform) {
+      ab = warp_sum(dabs);
+      lk = warp_sum(dleak);
+      ro = warp_sum(droul);
+      nc = warp_sum((unsigned long long)(x.active ? x.ncoll : 0u));
+      nk = warp_sum(kills);
+    }
+    if (lane == 0) {
+      s_slot[wid] = !act ? -1 : (uniform ? slot0 : -2);
+      s_d[wid][0] = ab;
+      s_d[wid][1] = lk;
+      s_d[wid][2] = ro;
+      s_u[wid][0] = (unsigned long long)__popc(act);
+      s_u[wid][1] = nc;
+      s_u[wid][2] = nk;
+      s_u[wid][3] = (unsigned long long)__popc(mask);
+    }
+    __syncthreads();
+    int bslot = -1;
+    bool same = true;
+    for (int i = 0; i < nw; ++i) {
+      const int si = s_slot[i];
+      if (si == -2 || (si >= 0 && bslot >= 0 && si != bslot)) same = false;
+      if (si >= 0 && bslot < 0) bslot = si;
+    }
+    if (same) {
+      if (threadIdx.x == 0 && bslot >= 0) {
+        double t[3] = {0.0, 0.0, 0.0};
+        unsigned long long u[4] = {0, 0, 0, 0};
+        for (int i = 0; i < nw; ++i) {  // warp order: a fixed summation order
+          for (int j = 0; j < 3; ++j) t[j] += s_d[i][j];
+          for (int j = 0; j < 4; ++j) u[j] += s_u[i][j];
+        }
+        DevStats *sp = st + bslot;
+        atomicAdd(&sp->absorbed, t[0]);
+        atomicAdd(&sp->leaked, t[1]);
+        atomicAdd(&sp->roulette_net, t[2]);
+        atomicAdd(&sp->transmissions, u[0]);
+        atomicAdd(&sp->collisions, u[1]);
+        atomicAdd(&sp->kills, u[2]);
+        if (u[3]) atomicAdd(&slot_live[bslot], (int)u[3]);
+      }
+      return;
+    }
+    if (!act) return;
+    if (uniform) {
+      if (lane == 0) {
+        DevStats *sp = st + slot0;
+        atomicAdd(&sp->absorbed, ab);
+        atomicAdd(&sp->leaked, lk);
+        atomicAdd(&sp->roulette_net, ro);
+        atomicAdd(&sp->transmissions, (unsigned long long)__popc(act));
+        atomicAdd(&sp->collisions, nc);
+        atomicAdd(&sp->kills, nk);
+        if (mask) atomicAdd(&slot_live[slot0], __popc(mask));
+      }
+      return;
+    }
+  }
   if (uniform) {
     dabs = warp_sum(dabs);
     dleak = warp_sum(dleak);
@@ -563,7 +633,7 @@ __global__ void birth_gmc_post_kernel(int64_t M, const uint64_t *__restrict__ bh
     x.ev = 1u;  // event 0 held the birth draw and the noise
     x.ncoll = 0;
   }
-  finish_transmission(x, slots, R, rt, st, slot_live);
+  finish_transmission<true>(x, slots, R, rt, st, slot_live);
 }
 
 // GMC stage 1 and the noise of stage 2.
@@ -613,7 +683,7 @@ __global__ void gmc_post_kernel(int64_t live, Bank in, const float *__restrict__
     x.ev = in.ev[k] + 1u;
     x.ncoll = 0;
   }
-  finish_transmission(x, slots, R, rt, st, slot_live);
+  finish_transmission<true>(x, slots, R, rt, st, slot_live);
 }
 
 inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
