@@ -458,6 +458,7 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   }
   N.stats = ns;
   N.loaded = true;
+  ++N.generation;
   return GMC_OK;
 }
 

@@ -53,6 +53,7 @@ struct Buffer {
 // the tensor-core path.
 struct NetDev {
   bool loaded = false;
+  uint64_t generation = 0;  // counts loads: cached per-network data keys on it
   float host_w[5][256 * 256];  // W_l[out][in] as in the file (unused tail for small layers)
   float host_b[5][256];
   NetStats stats{};
@@ -173,12 +174,14 @@ void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *
                       float *bias_host, float *scale_host);
 // packed: from tc_pack_host (fp8_scale null) or tc_pack_host_fp8 (fp8_scale =
 // its [3][256] scales on the device). kernel: gmc_sampler_kernel of the BF16
-// path (GMC_KERNEL_PAIR: sampler_pair.cu).
+// path (GMC_KERNEL_PAIR: sampler_pair.cu). bias1_ready: bias1_scratch already
+// holds this network's per-evaluation layer-1 bias for these steps and
+// integrator, so its kernel is skipped.
 cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const float *bias,
                               const NetF32 &f32, const NetStats &st, int64_t n, const float *cond,
                               const float *noise, uint64_t seed, uint64_t id0, int steps,
                               int integrator, float *y_raw, float *exit, int *err,
                               float *bias1_scratch, const float *fp8_scale,
-                              int kernel = GMC_KERNEL_TILE);
+                              int kernel = GMC_KERNEL_TILE, bool bias1_ready = false);
 
 }  // namespace gmc

@@ -680,13 +680,16 @@ cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const flo
                               const NetF32 &f32, const NetStats &st, int64_t n, const float *cond,
                               const float *noise, uint64_t seed, uint64_t id0, int steps,
                               int integrator, float *y_raw, float *exit, int *err,
-                              float *bias1_scratch, const float *fp8_scale, int kernel) {
+                              float *bias1_scratch, const float *fp8_scale, int kernel,
+                              bool bias1_ready) {
   if (n <= 0) return cudaSuccess;
   const int n_eval = integrator == GMC_RK4 ? 4 * steps : (integrator == GMC_MIDPOINT ? 2 * steps : steps);
-  layer1_bias_kernel<<<n_eval, kHidden, 0, stream>>>(f32.w1t, f32.b1, steps, integrator, n_eval,
-                                                     bias1_scratch);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (!bias1_ready) {
+    layer1_bias_kernel<<<n_eval, kHidden, 0, stream>>>(f32.w1t, f32.b1, steps, integrator, n_eval,
+                                                       bias1_scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

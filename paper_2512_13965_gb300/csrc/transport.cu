@@ -932,7 +932,7 @@ class Engine {
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_cond_, C_ * 5 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_noise_, C_ * 4 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_exit_, C_ * 4 * sizeof(float)));
-      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bias1_, 4 * 256 * 256 * sizeof(float)));
+      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bias1_, 2 * kBias1Floats * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bmeta_, C_ * 16));  // birth batch: hist, slot, cell
       GMC_CUDA_TRY(ctx_, cudaMalloc(&tbank_mem_[0], C_ * kBankBytesPerParticle));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&tbank_mem_[1], C_ * kBankBytesPerParticle));
@@ -1146,10 +1146,17 @@ class Engine {
                              cfg.integrator, nullptr, d_exit_);
     else {
       const bool fp8 = cfg.precision == GMC_FP8;
+      // the per-evaluation layer-1 bias depends on the network, the steps and
+      // the integrator only: computed once per (network load, setting)
+      const int nk = &N == &ctx_->internal ? 1 : 0;
+      Bias1Key &key = bias1_key_[nk];
+      const bool ready = key.net == &N && key.generation == N.generation && key.steps == cfg.steps &&
+                         key.integrator == cfg.integrator;
       e = launch_sampler_tc(s_, fp8 ? N.d_tc8 : N.d_tc, N.d_tc_bias, N.f32, N.stats, rows, d_cond_,
                             d_noise_, 0, 0, cfg.steps, cfg.integrator, nullptr, d_exit_,
-                            ctx_->d_err, d_bias1_, fp8 ? N.d_tc8_scale : nullptr,
-                            cfg.sampler_kernel);
+                            ctx_->d_err, d_bias1_ + nk * kBias1Floats, fp8 ? N.d_tc8_scale : nullptr,
+                            cfg.sampler_kernel, ready);
+      if (e == cudaSuccess && rows > 0) key = Bias1Key{&N, N.generation, cfg.steps, cfg.integrator};
     }
     if (e != cudaSuccess) return cuda_error(ctx_, e, "solve: sampler");
     return GMC_OK;
@@ -1276,6 +1283,15 @@ class Engine {
   int init_[3] = {0, 0, 0};  // host source of the counters copied before births
   int64_t waves_ = 0;
   float *d_cond_ = nullptr, *d_noise_ = nullptr, *d_exit_ = nullptr, *d_bias1_ = nullptr;
+  // layer-1 bias of the boundary (0) and internal (1) networks: n_eval x 256
+  // floats each, n_eval <= 4 x 256 steps; valid for the key it was computed with
+  static constexpr size_t kBias1Floats = 4 * 256 * 256;
+  struct Bias1Key {
+    const NetDev *net = nullptr;
+    uint64_t generation = 0;
+    int steps = -1, integrator = -1;
+  };
+  Bias1Key bias1_key_[2];
   void *d_bmeta_ = nullptr;
   Slot *d_slots_ = nullptr;
   DevStats *d_stats_ = nullptr;
