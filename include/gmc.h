@@ -428,9 +428,11 @@ typedef struct gmc_train_config {
     double eps;          /* e.g. 1e-8 */
     double weight_decay; /* decoupled weight decay, e.g. 0.01 */
     uint64_t seed;       /* Philox key of the batch draws (tag 6) */
-    int precision;       /* GMC_FP32: SIMT FP32 GEMMs; GMC_BF16: tcgen05 GEMMs with BF16
-                            operands and FP32 accumulation (master weights, moments,
-                            activations and gradients stay FP32) */
+    int precision;       /* GMC_FP32: SIMT FP32 GEMMs, FP32 activations; GMC_BF16: the
+                            tcgen05 step (four kernels per step): BF16 activations,
+                            SiLU' factors and input gradients between layers, FP32
+                            accumulation, weight and bias gradients summed in FP32 in
+                            a fixed order, FP32 master weights and AdamW moments */
 } gmc_train_config;
 
 /*
