@@ -37,6 +37,11 @@ METRIC = "cell transmissions/s GMC vs analog MC at flux err <=1%; p99 latency"
 # networks trained by the package's own trainer (commands in the weights folder)
 TRAINED_BOUNDARY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_boundary.bin")
 TRAINED_INTERNAL = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_internal.bin")
+# networks trained on tau log-uniform in [0.01, 1000] (the paper's thin
+# benchmark cells map inside their box), with that box
+WIDE_BOUNDARY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_boundary_wide.bin")
+WIDE_INTERNAL = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_internal_wide.bin")
+WIDE_BOX = [0.01, 1000.0, 0.5, 0.999]
 TRAINED_XY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_xy.bin")
 # stated GMC-vs-analog relative L2 flux error at 1e7 histories, per precision
 # of the network (the metric's condition is the BF16 one, 1 %)
@@ -204,6 +209,10 @@ def main():
     ap.add_argument("--hist-range", type=float, nargs=2, default=(1e3, 1e5),
                     help="serve: histories per request, log-uniform in [lo, hi]")
     ap.add_argument("--train-batch", type=int, default=16384, help="train: batch rows per step")
+    ap.add_argument("--net-box", type=float, nargs=4, default=None,
+                    metavar=("TAU_LO", "TAU_HI", "C_LO", "C_HI"),
+                    help="solve/paper: the (tau, c) box the networks were trained on (default: "
+                         "the library's, [0.1, 1000] x [0.5, 0.999])")
     ap.add_argument("--solve-variants", default=None,
                     help="comma list for --workload solve, e.g. analog,gmc_bf16_rk412 (default: all)")
     args = ap.parse_args()
@@ -418,6 +427,11 @@ def _context(args):
             path = os.path.join(d, "w.bin")
             synth.write_weights(path, synth.kaiming_weights(1))
             g.gmc_load_weights(ctx, path)
+    box = getattr(args, "net_box", None)
+    if box:
+        cfg = g.gmc_get_config(ctx)
+        cfg.net_tau_lo, cfg.net_tau_hi, cfg.net_c_lo, cfg.net_c_hi = box
+        g.gmc_set_config(ctx, cfg)
     return g, ctx
 
 
@@ -709,16 +723,20 @@ def run_paper(args):
     cells that have none. --histories per solve: the random walk with two
     seeds (its run-to-run difference is the statistical floor), then GMC
     (trained networks, BF16, midpoint 8 and RK4 12); solve time,
-    transmissions/s and the flux error against the walk."""
+    transmissions/s and the flux error against the walk. Default networks:
+    the pair trained on tau log-uniform in [0.01, 1000], with that box."""
     import numpy as np
     import synth
+    if args.weights is None and args.internal_weights is None and args.net_box is None:
+        args.weights, args.internal_weights, args.net_box = WIDE_BOUNDARY, WIDE_INTERNAL, list(WIDE_BOX)
     g, ctx = _context(args)
     n_hist = int(args.histories)
     problems = {"lattice": (synth.paper_lattice_problem(112), g.transport_solve),
                 "hohlraum": (synth.paper_hohlraum_problem(112), g.transport_solve_wall)}
     out = {}
+    box = ((0.1, 1000.0), (0.5, 0.999)) if not args.net_box else (tuple(args.net_box[:2]), tuple(args.net_box[2:]))
     for name, ((tau, c, src), solve) in problems.items():
-        n_equiv, n_walk, n_inside = _equivalent_summary(tau, c)
+        n_equiv, n_walk, n_inside = _equivalent_summary(tau, c, box)
         tau, c, src = (np.ascontiguousarray(a.ravel()) for a in (tau, c, src))
 
         def run(method, seed, prec=g.GMC_BF16, integ=g.GMC_MIDPOINT, steps=8):
@@ -754,7 +772,7 @@ def run_paper(args):
                       "workload": "lattice and linearized hohlraum, 112x112 cells, printed cross "
                                   "sections, stand-in layouts, %d histories" % n_hist,
                       "weights": args.weights, "internal_weights": args.internal_weights,
-                      "results": out}))
+                      "net_box": [list(box[0]), list(box[1])], "results": out}))
     ctx.close()
 
 
