@@ -13,6 +13,19 @@ What it computes, in the paper's order:
   * v_theta is a plain feed-forward network: input [c_std (5), x (4),
     emb(t) (16)], four hidden layers of width 256 with SiLU, linear output 4.
     emb(t) = [sin(2^j pi t)]_{j<8} followed by [cos(2^j pi t)]_{j<8}.
+  * The residual-modulated network is this build's reading of the paper's
+    own architecture (section "Network Architecture and Inputs": residual
+    blocks with adaptive modulation conditioned on the physical context; its
+    specification is in a supplement that is not available). Layer 1 is as
+    above (t and c enter through its learned columns); layers 2-4 become
+    residual blocks whose pre-activation is shifted by a learned linear map
+    of the condition and scaled channel-wise by the cell's optical
+    properties (standardized ln tau and c, condition components 3 and 4):
+        z_l = W_l a_{l-1} + b_l + M_l c_std
+        g_l = 1 + G_l[0] c_std[3] + G_l[1] c_std[4]
+        a_l = a_{l-1} + SiLU(g_l * z_l)            (l = 2, 3, 4)
+    and v = W_5 a_4 + b_5. M_l is [256][5], G_l is [2][256]; with G = 0 and
+    M = 0 it is a plain residual network.
   * Decoding (the fourth stage of the transport algorithm): destandardize,
     wrap p into [0,4), split it into face and position, renormalize the
     direction, make it point out of the exit face, s = exp(ln s).
@@ -35,6 +48,8 @@ Weight file ("GMCW" version 1, little-endian):
   u32 n_cond, n_state, n_emb, flags;
   f32 cond_mean[5], cond_std[5], y_mean[4], y_std[4];
   then per layer l: f32 W_l[dims[l+1]][dims[l]] (out x in), f32 b_l[dims[l+1]].
+  flags bit 0 marks the residual-modulated network, whose file continues
+  with f32 M[3][256][5] (layers 2-4) and f32 G[3][2][256].
 """
 import struct
 
@@ -46,18 +61,25 @@ N_EMB = 16
 HIDDEN = 256
 DIMS = (N_COND + N_STATE + N_EMB, HIDDEN, HIDDEN, HIDDEN, HIDDEN, N_STATE)
 S_MIN = 1e-7
+FLAG_RM = 1  # weight-file flag of the residual-modulated network
 
 
 class Net:
-    """FP64 copy of a weight file: W[l] (out x in), b[l], standardization."""
+    """FP64 copy of a weight file: W[l] (out x in), b[l], standardization;
+    for the residual-modulated network also M[j] ([256][5]) and G[j]
+    ([2][256]) of hidden layer j + 2 (rm is True)."""
 
-    def __init__(self, W, b, cond_mean, cond_std, y_mean, y_std):
+    def __init__(self, W, b, cond_mean, cond_std, y_mean, y_std, M=None, G=None):
         self.W = [np.asarray(w, dtype=np.float64) for w in W]
         self.b = [np.asarray(v, dtype=np.float64) for v in b]
         self.cond_mean = np.asarray(cond_mean, dtype=np.float64)
         self.cond_std = np.asarray(cond_std, dtype=np.float64)
         self.y_mean = np.asarray(y_mean, dtype=np.float64)
         self.y_std = np.asarray(y_std, dtype=np.float64)
+        self.rm = M is not None
+        if self.rm:
+            self.M = [np.asarray(m, dtype=np.float64).reshape(HIDDEN, N_COND) for m in M]
+            self.G = [np.asarray(q, dtype=np.float64).reshape(2, HIDDEN) for q in G]
 
 
 def read_weights(path):
@@ -67,9 +89,9 @@ def read_weights(path):
         raise ValueError("not a GMCW weight file")
     version, n_layers = struct.unpack_from("<2I", blob, 4)
     dims = struct.unpack_from("<6I", blob, 12)
-    n_cond, n_state, n_emb, _flags = struct.unpack_from("<4I", blob, 36)
+    n_cond, n_state, n_emb, flags = struct.unpack_from("<4I", blob, 36)
     if version != 1 or n_layers != 5 or tuple(dims) != DIMS or (n_cond, n_state, n_emb) != (
-            N_COND, N_STATE, N_EMB):
+            N_COND, N_STATE, N_EMB) or flags & ~FLAG_RM:
         raise ValueError("unsupported weight file layout")
     off = 52
     stats = np.frombuffer(blob, dtype="<f4", count=18, offset=off).astype(np.float64)
@@ -82,9 +104,20 @@ def read_weights(path):
         off += n_out * n_in * 4
         b.append(np.frombuffer(blob, dtype="<f4", count=n_out, offset=off).astype(np.float64))
         off += n_out * 4
+    M = G = None
+    if flags & FLAG_RM:
+        M, G = [], []
+        for _ in range(3):
+            M.append(np.frombuffer(blob, dtype="<f4", count=HIDDEN * N_COND, offset=off)
+                     .reshape(HIDDEN, N_COND).astype(np.float64))
+            off += HIDDEN * N_COND * 4
+        for _ in range(3):
+            G.append(np.frombuffer(blob, dtype="<f4", count=2 * HIDDEN, offset=off)
+                     .reshape(2, HIDDEN).astype(np.float64))
+            off += 2 * HIDDEN * 4
     if off != len(blob):
         raise ValueError("weight file has trailing or missing bytes")
-    return Net(W, b, stats[0:5], stats[5:10], stats[10:14], stats[14:18])
+    return Net(W, b, stats[0:5], stats[5:10], stats[10:14], stats[14:18], M, G)
 
 
 def time_embedding(t):
@@ -128,6 +161,8 @@ def quantized_e4m3(net):
     replaced by s_c round_e4m3(W[c,:] / s_c) with s_c = max_k |W[c,k]| / 448
     (1 for an all-zero row), and the inputs of those layers rounded to E4M3.
     """
+    if getattr(net, "rm", False):
+        raise ValueError("the E4M3 network is defined for the plain MLP only")
     W = [w.copy() for w in net.W]
     for l in (1, 2, 3):
         amax = np.abs(W[l]).max(axis=1)
@@ -143,12 +178,25 @@ def velocity(net, cn, x, t):
     B = x.shape[0]
     t = np.broadcast_to(np.asarray(t, dtype=np.float64), (B,))
     h = np.concatenate([cn, x, time_embedding(t)], axis=1)
+    if getattr(net, "rm", False):
+        return velocity_rm(net, cn, h)
     e4m3 = getattr(net, "e4m3_inputs", False)
     for l in range(4):
         if e4m3 and l >= 1:
             h = round_e4m3(h)
         h = silu(h @ net.W[l].T + net.b[l])
     return h @ net.W[4].T + net.b[4]
+
+
+def velocity_rm(net, cn, h):
+    """The residual-modulated network (module note) on layer-1 inputs h
+    [B, 25] with standardized conditions cn [B, 5]."""
+    a = silu(h @ net.W[0].T + net.b[0])
+    for j in range(3):
+        z = a @ net.W[j + 1].T + net.b[j + 1] + cn @ net.M[j].T
+        g = 1.0 + cn[:, 3:4] * net.G[j][0][None, :] + cn[:, 4:5] * net.G[j][1][None, :]
+        a = a + silu(g * z)
+    return a @ net.W[4].T + net.b[4]
 
 
 def integrate(vfun, x0, steps, integrator="euler"):

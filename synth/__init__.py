@@ -92,6 +92,18 @@ def kaiming_weights(seed=1):
             "y_mean": np.zeros(4, np.float32), "y_std": np.ones(4, np.float32)}
 
 
+def rm_weights(seed=1, m_std=0.0, g_std=0.0, base=None):
+    """Weights of the residual-modulated network: the layers of `base` (default
+    `kaiming_weights(seed)`), condition shifts M[3][256][5] ~ N(0, m_std^2)
+    and channel scales G[3][2][256] ~ N(0, g_std^2) (zero by default: a
+    training start whose blocks are unmodulated)."""
+    net = dict(base if base is not None else kaiming_weights(seed))
+    g = generator(seed + 2000)
+    net["M"] = [(g.standard_normal((256, 5)) * m_std).astype(np.float32) for _ in range(3)]
+    net["G"] = [(g.standard_normal((2, 256)) * g_std).astype(np.float32) for _ in range(3)]
+    return net
+
+
 def biased_weights(seed=7, bias_std=0.3):
     """Kaiming-normal weights with N(0, bias_std^2) biases and a non-identity
     standardization (condition and output means and standard deviations of
@@ -107,17 +119,25 @@ def biased_weights(seed=7, bias_std=0.3):
 
 
 def write_weights(path, net):
-    """Write a dict like `kaiming_weights()` returns as a GMCW version-1 file."""
+    """Write a dict like `kaiming_weights()` returns as a GMCW version-1 file;
+    with keys "M" and "G" (`rm_weights()`) flag 1 and those arrays follow the
+    layers: M[3][256][5], then G[3][2][256]."""
+    rm = "M" in net
     with open(path, "wb") as f:
         f.write(b"GMCW")
         f.write(struct.pack("<2I", 1, 5))
         f.write(struct.pack("<6I", *DIMS))
-        f.write(struct.pack("<4I", 5, 4, 16, 0))
+        f.write(struct.pack("<4I", 5, 4, 16, 1 if rm else 0))
         for k in ("cond_mean", "cond_std", "y_mean", "y_std"):
             f.write(np.asarray(net[k], dtype="<f4").tobytes())
         for l in range(5):
             f.write(np.ascontiguousarray(net["W"][l], dtype="<f4").tobytes())
             f.write(np.ascontiguousarray(net["b"][l], dtype="<f4").tobytes())
+        if rm:
+            for m in net["M"]:
+                f.write(np.ascontiguousarray(m, dtype="<f4").reshape(256, 5).tobytes())
+            for q in net["G"]:
+                f.write(np.ascontiguousarray(q, dtype="<f4").reshape(2, 256).tobytes())
 
 
 def grid_problem(n=128, seed=2, tau_range=(0.1, 500.0), c_values=(0.5, 0.999), block=16,
