@@ -184,6 +184,15 @@ gmc_status gmc_normals(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uin
  * before, if any, is then kept unchanged), GMC_EBUSY while the server runs.
  * The FP32 weights are kept and the BF16 / FP8 packed copies are derived
  * from them.
+ * flags = 1 marks the residual-modulated network, a reading of the paper's
+ * architecture (section "Network Architecture and Inputs": residual blocks
+ * with adaptive modulation conditioned on the physical context): the file
+ * continues with f32 M[3][256][5] and G[3][2][256], and hidden layers 2-4
+ * become a_l = a_{l-1} + SiLU(g_l z_l) with z_l = W_l a_{l-1} + b_l + M_l c
+ * and g_l = 1 + G_l[0] c_3 + G_l[1] c_4 (c standardized; c_3 = ln tau,
+ * c_4 = c). It runs at GMC_FP32 and at GMC_BF16 with GMC_KERNEL_TILE;
+ * GMC_FP8 and GMC_KERNEL_PAIR give GMC_EINVAL in gmc_transmit, solves and
+ * serving. Other flag bits give GMC_EFORMAT.
  */
 gmc_status gmc_load_weights(gmc_ctx *ctx, const char *path);
 /* Same, from a host buffer holding the file's bytes. */
@@ -428,7 +437,8 @@ typedef struct gmc_train_config {
     double eps;          /* e.g. 1e-8 */
     double weight_decay; /* decoupled weight decay, e.g. 0.01 */
     uint64_t seed;       /* Philox key of the batch draws (tag 6) */
-    int precision;       /* GMC_FP32: SIMT FP32 GEMMs, FP32 activations; GMC_BF16: the
+    int precision;       /* GMC_FP32: SIMT FP32 GEMMs, FP32 activations (the only
+                            choice for the residual-modulated network); GMC_BF16: the
                             tcgen05 step (four kernels per step): BF16 activations,
                             SiLU' factors and input gradients between layers, FP32
                             accumulation, weight and bias gradients summed in FP32 in
@@ -506,6 +516,13 @@ gmc_status gmc_train_grad(gmc_ctx *ctx, int64_t B, const float *cn, const float 
 /* Copies the FP32 master weights (layout of gmc_train_grad) to host `out`. */
 gmc_status gmc_train_params(gmc_ctx *ctx, float *out);
 int64_t gmc_train_param_count(void);
+/* Parameters of the network being trained (GMC_EINVAL before
+   gmc_train_begin): gmc_train_param_count() for the MLP; for the
+   residual-modulated network (weight-file flag 1) 5376 more, appended in the
+   order M2..M4 [256][5] (condition shifts of hidden layers 2-4), then
+   G2..G4 [2][256] (their channel scales). gmc_train_grad and
+   gmc_train_params then read or write this many floats. */
+gmc_status gmc_train_param_count_ctx(const gmc_ctx *ctx, int64_t *count);
 /*
  * Training checkpoint (host memory): the FP32 master weights, AdamW's first
  * and second moments, the step count, the hyperparameters (learning rate as

@@ -115,6 +115,7 @@ def _load():
         "gmc_train_set_lr": [P, ctypes.c_double],
         "gmc_train_grad": [P, i64, P, P, P, P, P, P],
         "gmc_train_params": [P, P],
+        "gmc_train_param_count_ctx": [P, ctypes.POINTER(ctypes.c_int64)],
         "gmc_train_commit": [P, ctypes.c_char_p],
         "gmc_train_state_size": [P, ctypes.POINTER(ctypes.c_size_t)],
         "gmc_train_save_state": [P, P, sz],
@@ -392,7 +393,7 @@ def gmc_train_set_lr(ctx, lr):
 
 def gmc_train_grad(ctx, B, cn, x1, x0, t, grad):
     loss = ctypes.c_double()
-    P = gmc_train_param_count()
+    P = gmc_train_param_count_ctx(ctx)
     ctx.check(lib.gmc_train_grad(ctx.handle, B, _arr(cn, 4, 5 * B, "cn"), _arr(x1, 4, 4 * B, "x1"),
                                  _arr(x0, 4, 4 * B, "x0"), _arr(t, 4, B, "t"),
                                  ctypes.byref(loss), _arr(grad, 4, P, "grad")))
@@ -401,11 +402,17 @@ def gmc_train_grad(ctx, B, cn, x1, x0, t, grad):
 
 def gmc_train_params(ctx, out):
     return ctx.check(lib.gmc_train_params(ctx.handle,
-                                          _arr(out, 4, gmc_train_param_count(), "out")))
+                                          _arr(out, 4, gmc_train_param_count_ctx(ctx), "out")))
 
 
 def gmc_train_param_count():
     return int(lib.gmc_train_param_count())
+
+
+def gmc_train_param_count_ctx(ctx):
+    n = ctypes.c_int64()
+    ctx.check(lib.gmc_train_param_count_ctx(ctx.handle, ctypes.byref(n)))
+    return n.value
 
 
 def gmc_train_state_size(ctx):

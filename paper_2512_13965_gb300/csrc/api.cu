@@ -349,7 +349,17 @@ gmc_status gmc_normals(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uin
 }  // extern "C"
 
 namespace gmc {
+gmc_status check_net_path(gmc_ctx *ctx, const NetDev &N, int precision, int kernel, const char *who) {
+  if (!N.rm || precision == GMC_FP32 || (precision == GMC_BF16 && kernel == GMC_KERNEL_TILE))
+    return GMC_OK;
+  return set_error(ctx, GMC_EINVAL,
+                   "%s: the residual-modulated network runs at GMC_FP32, or GMC_BF16 with "
+                   "GMC_KERNEL_TILE", who);
+}
+
 // Parses a GMCW version 1 blob into N and uploads its FP32, BF16 and FP8 copies.
+// Flag 1 (the residual-modulated network) adds M[3][256][5] and G[3][2][256]
+// after the layers.
 // Nothing of N changes unless the blob parses; N stays marked unloaded from
 // the first change until every device copy is in place.
 gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
@@ -364,8 +374,9 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   for (int i = 0; i < 6 && ok; ++i) ok = rd.u32(&dims[i]);
   ok = ok && rd.u32(&ncond) && rd.u32(&nstate) && rd.u32(&nemb) && rd.u32(&flags);
   if (!ok) return set_error(ctx, GMC_EFORMAT, "weight file: truncated header");
-  if (version != 1 || nl != 5 || ncond != 5 || nstate != 4 || nemb != 16)
-    return set_error(ctx, GMC_EFORMAT, "weight file: unsupported version or layout");
+  if (version != 1 || nl != 5 || ncond != 5 || nstate != 4 || nemb != 16 || (flags & ~kFlagRM))
+    return set_error(ctx, GMC_EFORMAT, "weight file: unsupported version, layout or flags");
+  const bool rm = (flags & kFlagRM) != 0;
   for (int i = 0; i < 6; ++i)
     if (dims[i] != dims_ok[i])
       return set_error(ctx, GMC_EFORMAT, "weight file: layer dims must be 25-256-256-256-256-4");
@@ -377,6 +388,9 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
     if (!rd.f32(&tw[l * wl], (size_t)dims[l + 1] * dims[l]) || !rd.f32(&tb[l * bl], dims[l + 1]))
       return set_error(ctx, GMC_EFORMAT, "weight file: truncated layer %d", l);
   }
+  std::vector<float> tm(3 * 256 * kCond, 0.0f), tg(3 * 512, 0.0f);
+  if (rm && (!rd.f32(tm.data(), tm.size()) || !rd.f32(tg.data(), tg.size())))
+    return set_error(ctx, GMC_EFORMAT, "weight file: truncated modulation arrays");
   if (rd.off != nbytes) return set_error(ctx, GMC_EFORMAT, "weight file: trailing bytes");
   for (int k = 0; k < 5; ++k)
     if (!(st[5 + k] > 0.0f)) return set_error(ctx, GMC_EFORMAT, "weight file: cond_std must be > 0");
@@ -388,6 +402,9 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
     std::memcpy(N.host_w[l], &tw[l * wl], wl * sizeof(float));
     std::memcpy(N.host_b[l], &tb[l * bl], bl * sizeof(float));
   }
+  N.rm = rm;
+  std::memcpy(N.host_m, tm.data(), tm.size() * sizeof(float));
+  std::memcpy(N.host_g, tg.data(), tg.size() * sizeof(float));
   NetStats ns;
   for (int k = 0; k < 5; ++k) {
     ns.cond_mean[k] = st[k];
@@ -399,9 +416,11 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   }
   ns.disk = &N == &ctx->xy ? 1 : 0;  // the x-y geometry slot decodes into the unit disk
 
-  // FP32 transposed block
+  // FP32 transposed block (room for the modulation arrays in every load, so
+  // a later load of either network reuses it)
   const size_t n1 = 32 * 256, nh = 256 * 256;
-  const size_t total = n1 + 256 + 3 * (nh + 256) + 4 * 256 + 4;
+  const size_t nm = 3 * kCond * 256, ng = 3 * 2 * 256;
+  const size_t total = n1 + 256 + 3 * (nh + 256) + 4 * 256 + 4 + nm + ng;
   std::vector<float> h(total, 0.0f);
   float *p = h.data();
   float *w1t = p; p += n1;
@@ -410,6 +429,8 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   for (int l = 0; l < 3; ++l) { wt[l] = p; p += nh; bt[l] = p; p += 256; }
   float *w5 = p; p += 4 * 256;
   float *b5 = p; p += 4;
+  float *mt = p; p += nm;
+  float *gg = p; p += ng;
   for (int c = 0; c < 256; ++c)
     for (int k = 0; k < 25; ++k) w1t[k * 256 + c] = N.host_w[0][c * 25 + k];
   std::memcpy(b1, N.host_b[0], 256 * 4);
@@ -420,6 +441,10 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   }
   std::memcpy(w5, N.host_w[4], 4 * 256 * 4);
   std::memcpy(b5, N.host_b[4], 4 * 4);
+  for (int j = 0; j < 3; ++j)
+    for (int c = 0; c < 256; ++c)
+      for (int k = 0; k < kCond; ++k) mt[(j * kCond + k) * 256 + c] = N.host_m[j][c * kCond + k];
+  std::memcpy(gg, N.host_g, ng * sizeof(float));
 
   cudaSetDevice(ctx->device);
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -435,14 +460,17 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   N.f32.w4t = d; d += nh;
   N.f32.b4 = d; d += 256;
   N.f32.w5 = d; d += 4 * 256;
-  N.f32.b5 = d;
+  N.f32.b5 = d; d += 4;
+  N.f32.mt = d; d += nm;
+  N.f32.gg = d;
+  N.f32.rm = rm ? 1 : 0;
 
   // packed operands of the tensor-core path (BF16 and FP8 variants)
   {
     const size_t tcb = tc_packed_bytes(false), tcb8 = tc_packed_bytes(true);
     std::vector<unsigned char> packed(tcb), packed8(tcb8);
     std::vector<float> bias(5 * 256, 0.0f), scale(3 * 256, 0.0f);
-    tc_pack_host(N.host_w, N.host_b, packed.data(), bias.data());
+    tc_pack_host(N.host_w, N.host_b, packed.data(), bias.data(), rm ? N.host_m : nullptr);
     tc_pack_host_fp8(N.host_w, N.host_b, packed8.data(), bias.data(), scale.data());
     if (!N.d_tc) GMC_CUDA_TRY(ctx, cudaMalloc(&N.d_tc, tcb));
     if (!N.d_tc8) GMC_CUDA_TRY(ctx, cudaMalloc(&N.d_tc8, tcb8));
@@ -541,6 +569,8 @@ gmc_status transmit_net(gmc_ctx *ctx, const NetDev &N, int64_t n, const float *c
   if (!N.loaded) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_transmit: no weights loaded for this model");
   if (precision != GMC_FP32 && precision != GMC_BF16 && precision != GMC_FP8)
     return set_error(ctx, GMC_EINVAL, "gmc_transmit: unknown precision");
+  if (check_net_path(ctx, N, precision, ctx->cfg.sampler_kernel, "gmc_transmit") != GMC_OK)
+    return GMC_EINVAL;
   cudaSetDevice(ctx->device);
   Arg a_cond, a_noise, a_y, a_exit;
   a_cond.user = cond; a_cond.bytes = (size_t)n * 5 * 4;

@@ -21,10 +21,15 @@ constexpr float kSMin = 1e-7f;
 
 // FP32 network, transposed for the SIMT path: w1t [32][256] (rows 25..31
 // zero), w2t..w4t [256][256] with wt[k][c] = W[c][k]; w5 [4][256] as in the
-// file; biases as in the file.
+// file; biases as in the file. The residual-modulated network (rm = 1) also
+// has mt [3][5][256] (mt[j][k][c] = M_j[c][k], the condition shift of hidden
+// layer j + 2) and gg [3][2][256] (its channel scales G_j).
 struct NetF32 {
   const float *w1t, *b1, *w2t, *b2, *w3t, *b3, *w4t, *b4, *w5, *b5;
+  const float *mt, *gg;
+  int rm;
 };
+constexpr uint32_t kFlagRM = 1u;  // weight-file flag of the residual-modulated network
 
 // Standardization of the file: cond_mean[5], cond_std[5], y_mean[4], y_std[4].
 struct NetStats {
@@ -53,9 +58,12 @@ struct Buffer {
 // the tensor-core path.
 struct NetDev {
   bool loaded = false;
+  bool rm = false;  // residual-modulated network (weight-file flag 1)
   uint64_t generation = 0;  // counts loads: cached per-network data keys on it
   float host_w[5][256 * 256];  // W_l[out][in] as in the file (unused tail for small layers)
   float host_b[5][256];
+  float host_m[3][256 * kCond];  // M_j[c][k] (rm only)
+  float host_g[3][2 * 256];      // G_j[0..1][c] (rm only)
   NetStats stats{};
   float *d_f32 = nullptr;  // FP32 transposed block
   NetF32 f32{};
@@ -101,6 +109,10 @@ struct gmc_ctx {
 namespace gmc {
 
 gmc_status set_error(gmc_ctx *ctx, gmc_status s, const char *fmt, ...);
+// GMC_EINVAL (context error naming `who`) when network N cannot run on the
+// sampler path of `precision` and `kernel`: the residual-modulated network has
+// the FP32 and the BF16 one-CTA-per-SM tensor-core path only.
+gmc_status check_net_path(gmc_ctx *ctx, const NetDev &N, int precision, int kernel, const char *who);
 gmc_status cuda_error(gmc_ctx *ctx, cudaError_t e, const char *what);
 // Device memory of GPU ctx_device, or managed memory (not another GPU's memory).
 bool is_device_pointer(const void *p, int ctx_device);
@@ -168,15 +180,18 @@ cudaError_t launch_analog_xy(cudaStream_t stream, int64_t n, const float *xi, co
 // Tensor-core sampler (sampler_tc.cu). The BF16 and FP8 variants share the
 // bias vector ([5][256]); the FP8 one also takes per-channel weight scales.
 size_t tc_packed_bytes(bool fp8);
+// M: the condition shifts of the residual-modulated network (null for the
+// MLP), packed into the bias blocks of layers 2-4.
 void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
-                  float *bias_host);
+                  float *bias_host, const float (*M)[256 * kCond] = nullptr);
 void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
                       float *bias_host, float *scale_host);
 // packed: from tc_pack_host (fp8_scale null) or tc_pack_host_fp8 (fp8_scale =
 // its [3][256] scales on the device). kernel: gmc_sampler_kernel of the BF16
 // path (GMC_KERNEL_PAIR: sampler_pair.cu). bias1_ready: bias1_scratch already
 // holds this network's per-evaluation layer-1 bias for these steps and
-// integrator, so its kernel is skipped.
+// integrator, so its kernel is skipped. A residual-modulated network (f32.rm)
+// runs on the BF16 tile kernel only (cudaErrorNotSupported otherwise).
 cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const float *bias,
                               const NetF32 &f32, const NetStats &st, int64_t n, const float *cond,
                               const float *noise, uint64_t seed, uint64_t id0, int steps,

@@ -78,6 +78,8 @@ extern "C" gmc_status gmc_transmit_noalloc(gmc_ctx *ctx, int64_t n, const float 
                      max_steps, kNoallocMaxEvals, evals_per_step, steps);
   if (!ctx->net.loaded || !ctx->net.d_tc)
     return set_error(ctx, GMC_ENOWEIGHTS, "gmc_transmit_noalloc: no weights loaded");
+  if (check_net_path(ctx, ctx->net, GMC_BF16, ctx->cfg.sampler_kernel, "gmc_transmit_noalloc") != GMC_OK)
+    return GMC_EINVAL;
   if (n == 0) return GMC_OK;
   if (!cond || (!y_raw && !exit)) return set_error(ctx, GMC_EINVAL, "gmc_transmit_noalloc: null array");
   cudaError_t e = cudaSetDevice(ctx->device);

@@ -39,6 +39,7 @@ struct Params {
   const float *bias;    // [5][256]: rows 1..3 = b2..b4, row 4 = b5
   const float *bias1;   // [n_eval][256]: W1[:, emb] emb(t_e) + b1
   const float *scale;   // FP8 only: [3][256] per-output-channel scales of W2..W4, halved
+  const float *rmg;     // residual-modulated network only: channel scales G [3][2][256]
   NetStats st;
   int64_t n;
   const float *cond;

@@ -7,6 +7,10 @@
 // 256 threads computes a 4-row x 16-column register tile, columns
 // {4 cg + 64 q + e} so that a warp's float4 reads of a weight row are
 // contiguous. Accurate expf keeps SiLU within FP32 rounding.
+// Residual-modulated network (net.rm): hidden layers 2-4 add the condition
+// shift M_j c to the pre-activation, scale it by g = 1 + G_j[0] c_3 +
+// G_j[1] c_4 and add SiLU(g z) to the layer's input (the residual), each
+// thread reading the old activations of exactly the cells it overwrites.
 #include "decode.cuh"
 #include "gmc_internal.cuh"
 #include "philox.cuh"
@@ -32,9 +36,12 @@ struct Smem {
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
 
-// act[:, 0:K] (K = 32 or 256) times wt [K][256] (+ b) -> SiLU -> act[:, 0:256]
+// act[:, 0:K] (K = 32 or 256) times wt [K][256] (+ b) -> SiLU -> act[:, 0:256];
+// with mt non-null (a residual-modulated block, K = 256): act += SiLU(g z),
+// z = acc + b + mt^T cn, g = 1 + gg[0] cn_3 + gg[1] cn_4
 __device__ void dense_silu(Smem &s, const float *__restrict__ wt, const float *__restrict__ b,
-                           int K) {
+                           int K, const float *__restrict__ mt = nullptr,
+                           const float *__restrict__ gg = nullptr) {
   const int t = threadIdx.x, cg = t & 15, rg = t >> 4;
   float acc[4][16];
 #pragma unroll
@@ -73,6 +80,29 @@ __device__ void dense_silu(Smem &s, const float *__restrict__ wt, const float *_
     }
   }
   __syncthreads();  // every read of act is done: overwrite in place
+  if (mt) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = cg * 4 + 64 * q + e;
+        const float bc = __ldg(b + c), g0 = __ldg(gg + c), g1 = __ldg(gg + kHidden + c);
+        float m[kCond];
+#pragma unroll
+        for (int k = 0; k < kCond; ++k) m[k] = __ldg(mt + k * kHidden + c);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = rg * 4 + i;
+          float z = acc[i][q * 4 + e] + bc;
+#pragma unroll
+          for (int k = 0; k < kCond; ++k) z = fmaf(m[k], s.cn[r][k], z);
+          const float g = fmaf(g0, s.cn[r][3], fmaf(g1, s.cn[r][4], 1.0f));
+          s.act[r][c] += silu(g * z);
+        }
+      }
+    __syncthreads();
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const float4 bb = __ldg(reinterpret_cast<const float4 *>(b + cg * 4 + 64 * q));
@@ -104,9 +134,15 @@ __device__ void velocity(Smem &s, const NetF32 &net, const float (*xs)[4], float
     s.act[r][k] = v;
   }
   dense_silu(s, net.w1t, net.b1, kIn1Pad);
-  dense_silu(s, net.w2t, net.b2, kHidden);
-  dense_silu(s, net.w3t, net.b3, kHidden);
-  dense_silu(s, net.w4t, net.b4, kHidden);
+  if (net.rm) {
+    dense_silu(s, net.w2t, net.b2, kHidden, net.mt, net.gg);
+    dense_silu(s, net.w3t, net.b3, kHidden, net.mt + kCond * kHidden, net.gg + 2 * kHidden);
+    dense_silu(s, net.w4t, net.b4, kHidden, net.mt + 2 * kCond * kHidden, net.gg + 4 * kHidden);
+  } else {
+    dense_silu(s, net.w2t, net.b2, kHidden);
+    dense_silu(s, net.w3t, net.b3, kHidden);
+    dense_silu(s, net.w4t, net.b4, kHidden);
+  }
   {
     const int r = tid >> 2, d = tid & 3;
     const float4 *w = reinterpret_cast<const float4 *>(net.w5 + d * kHidden);

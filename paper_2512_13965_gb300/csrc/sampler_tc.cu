@@ -53,6 +53,17 @@
 // through them) and layer 4's epilogue writes BF16, so layer 5 (the velocity)
 // is the same BF16 MMA as above. A 32 KB weight chunk then holds 128 inputs
 // instead of 64; a K step is 32 bytes (8 A columns) in both variants.
+//
+// Residual-modulated variant (template argument RM, BF16 only): layers 2-4
+// are residual blocks a_l = a_{l-1} + SiLU(g z_l). The condition shift M_l c
+// of z_l enters through the bias MMA like the bias (the condition columns of
+// the layer-1 operand against M_l / 2 in the bias block), so the accumulator
+// already holds z_l / 2. The epilogue scales it by the channel modulation
+// g = 1 + G_l[0] c_3 + G_l[1] c_4 (FP32: the row's standardized ln tau and c
+// are held in registers, G is read through the L1 cache), applies the SiLU
+// and adds the block input, which it reads from A_T (the MMA that read it has
+// completed) just before overwriting it: the residual stream is the BF16
+// operand itself and costs no tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -92,7 +103,11 @@ constexpr uint32_t S_B5 = 16384;                 // 8 KB
 constexpr uint32_t S_BIAS = 24576;               // 24 KB (BF16 variant)
 constexpr uint32_t S_ST = 49152;                 // NST weight stages
 constexpr uint32_t S_BAR = S_ST + NST * CHUNK;   // barriers and flags
-constexpr uint32_t S_TOTAL = S_BAR + 256;
+// residual-modulated network: (ln tau, c) standardized, per tile, epilogue
+// thread and row ([T][epilogue warp][lane] float2; each thread reads only
+// what it wrote, so registers are spared without a barrier)
+constexpr uint32_t S_U = S_BAR + 256;
+constexpr uint32_t S_TOTAL = S_U + 2 * EPI_WARPS * 32 * 8;
 constexpr uint32_t SMEM_BYTES = S_TOTAL + 1024;  // + alignment slack
 // More than half of the SM's shared memory, so no second CTA (which would
 // wait for the 512 tensor-memory columns this one holds) shares the SM.
@@ -114,6 +129,47 @@ static_assert(sizeof(Bars) <= 256, "barrier block");
 __device__ void fail(Bars &b, int *err, int code) {
   b.abort = 1;
   atomicExch(err, code);
+}
+
+// Residual blocks (layers 2-4 of the residual-modulated network, L = 1..3):
+// rm_scale packs the scaled halved pre-activations g z / 2 of 32 accumulator
+// columns (col0 ..) into 16 BF16 pairs; rm_finish reads the block input of
+// this thread's 64 columns from a_row (BF16 columns col0 / 2 ..), adds the
+// SiLU and writes the sum back.
+__device__ __forceinline__ void rm_scale(int L, const uint32_t (&v)[32], const float *__restrict__ rmg,
+                                         float u3, float u4, int col0, uint32_t (&hp)[16]) {
+  const float4 *g0 = reinterpret_cast<const float4 *>(rmg + (L - 1) * 512 + col0);
+  const float4 *g1 = reinterpret_cast<const float4 *>(rmg + (L - 1) * 512 + 256 + col0);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 ga = __ldg(g0 + q), gb = __ldg(g1 + q);
+    const float h0 = __uint_as_float(v[4 * q]) * fmaf(ga.x, u3, fmaf(gb.x, u4, 1.0f));
+    const float h1 = __uint_as_float(v[4 * q + 1]) * fmaf(ga.y, u3, fmaf(gb.y, u4, 1.0f));
+    const float h2 = __uint_as_float(v[4 * q + 2]) * fmaf(ga.z, u3, fmaf(gb.z, u4, 1.0f));
+    const float h3 = __uint_as_float(v[4 * q + 3]) * fmaf(ga.w, u3, fmaf(gb.w, u4, 1.0f));
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hp[2 * q]) : "f"(h1), "f"(h0));
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hp[2 * q + 1]) : "f"(h3), "f"(h2));
+  }
+}
+
+__device__ __forceinline__ void rm_finish(const uint32_t (&h0)[16], const uint32_t (&h1)[16], int col0,
+                                          uint32_t a_row) {
+#pragma unroll
+  for (int pc = 0; pc < 4; ++pc) {
+    uint32_t a[8];  // the block input, overwritten by the block output
+    const uint32_t col = a_row + (uint32_t)((col0 + 16 * pc) >> 1);
+    tmem_ld8_raw(col, a);
+    tmem_wait_ld_regs8(a);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      uint32_t t, o;
+      const uint32_t h = pc < 2 ? h0[8 * pc + i] : h1[8 * (pc - 2) + i];
+      asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
+      asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(o) : "r"(h), "r"(t));
+      asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(a[i]) : "r"(o), "r"(a[i]));
+    }
+    tmem_st8(col, a);
+  }
 }
 
 // One 16-column piece of layer L's epilogue: activations of accumulator
@@ -144,8 +200,10 @@ __device__ __forceinline__ void epi_piece(int L, const uint32_t *v, const float 
 
 // INTEG: the integrator (GMC_EULER, GMC_MIDPOINT, GMC_RK4) as a compile-time
 // choice, so an Euler kernel holds no midpoint or RK4 state in registers.
-template <bool FP8, int INTEG>
+// RM: the residual-modulated network (BF16 only).
+template <bool FP8, int INTEG, bool RM = false>
 __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
+  static_assert(!(FP8 && RM), "the residual-modulated network has no FP8 variant");
   using PK = Packed<FP8>;
   constexpr int NCH = PK::NCH;
   extern __shared__ unsigned char smem_raw[];
@@ -340,10 +398,22 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
     const bool owner = p == 0;  // holds the ODE state of tile g's rows
     float x[4], xm[4], ka[4];
+    float2 *u_slot = reinterpret_cast<float2 *>(sm + S_U) + ew * 32 + lane;  // RM: + 512 T
     uint32_t dph = 0;
     bool ok = true;
     for (int64_t ip = 0; ip < n_iter && ok; ++ip) {
       const int64_t pr = blockIdx.x + ip * gridDim.x;
+      if constexpr (RM) {
+#pragma unroll
+        for (int T = 0; T < 2; ++T) {
+          const int64_t gi = (2 * pr + T) * TM + r;
+          const bool valid = gi < P.n;
+          u_slot[512 * T] = valid ? make_float2(
+                                        (P.cond[3 * P.n + gi] - P.st.cond_mean[3]) * P.st.cond_inv_std[3],
+                                        (P.cond[4 * P.n + gi] - P.st.cond_mean[4]) * P.st.cond_inv_std[4])
+                                  : make_float2(0.0f, 0.0f);
+        }
+      }
       {
         const int T = g;
         const int64_t gi = (2 * pr + T) * TM + r;
@@ -388,6 +458,30 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
             }
             ++dph;
             tc_fence_after();
+            if constexpr (RM) {
+              if (L > 0) {
+                // residual block: each 32-column half is scaled and packed as
+                // it arrives (fewer live registers), then the accumulator is
+                // released and the block output overwrites its input in A_T
+                const float2 u = u_slot[512 * T];
+                uint32_t h0[16], h1[16], v[32];
+                tmem_ld32_raw(d_col, v);
+                tmem_wait_ld_regs(v);
+                rm_scale(L, v, P.rmg, u.x, u.y, col0, h0);
+                tmem_ld32_raw(d_col + 32u, v);
+                tmem_wait_ld_regs(v);
+                rm_scale(L, v, P.rmg, u.x, u.y, col0 + 32, h1);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&B.dfree);
+                rm_finish(h0, h1, col0, a_row);
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&B.ar[T][g]);
+                continue;
+              }
+            }
             // the whole 64-column slice comes into registers first, so the
             // accumulator is released after one load latency; the MMA that
             // read A_T has completed, so the activations overwrite it at once
@@ -596,7 +690,7 @@ void pack_b1_b5_bias(const float (*W)[256 * 256], const float (*b)[256], unsigne
 size_t tc_packed_bytes(bool fp8) { return fp8 ? Packed<true>::BYTES : Packed<false>::BYTES; }
 
 void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
-                  float *bias_host) {
+                  float *bias_host, const float (*M)[256 * kCond]) {
   using PK = Packed<false>;
   unsigned char *P = (unsigned char *)packed_host;
   std::memset(P, 0, PK::BYTES);
@@ -625,6 +719,13 @@ void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *pack
       const size_t base = PK::OFF_BIAS + (size_t)L * 8192;
       std::memcpy(P + base + sw32_off(c, 13), &hi, 2);
       std::memcpy(P + base + sw32_off(c, 14), &lo, 2);
+      // residual-modulated network: the condition shift M_l c / 2 against the
+      // condition columns 8..12 of the layer-1 operand
+      if (M)
+        for (int k = 0; k < kCond; ++k) {
+          const uint16_t u = bf16_bits(0.5f * M[L][c * kCond + k]);
+          std::memcpy(P + base + sw32_off(c, 8 + k), &u, 2);
+        }
     }
 }
 
@@ -661,9 +762,9 @@ void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *
 }
 
 namespace {
-template <bool FP8, int INTEG>
+template <bool FP8, int INTEG, bool RM = false>
 cudaError_t launch_tc(cudaStream_t stream, const Params &p, int sms) {
-  auto kernel = sampler_tc_kernel<FP8, INTEG>;
+  auto kernel = sampler_tc_kernel<FP8, INTEG, RM>;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
@@ -710,6 +811,13 @@ cudaError_t launch_sampler_tc(cudaStream_t stream, const void *packed, const flo
   p.y_raw = y_raw;
   p.exitp = exit;
   p.err = err;
+  p.rmg = f32.rm ? f32.gg : nullptr;
+  if (f32.rm) {
+    if (fp8_scale || kernel == GMC_KERNEL_PAIR) return cudaErrorNotSupported;
+    if (integrator == GMC_RK4) return launch_tc<false, GMC_RK4, true>(stream, p, sms);
+    if (integrator == GMC_MIDPOINT) return launch_tc<false, GMC_MIDPOINT, true>(stream, p, sms);
+    return launch_tc<false, GMC_EULER, true>(stream, p, sms);
+  }
   if (fp8_scale) {
     if (integrator == GMC_RK4) return launch_tc<true, GMC_RK4>(stream, p, sms);
     if (integrator == GMC_MIDPOINT) return launch_tc<true, GMC_MIDPOINT>(stream, p, sms);

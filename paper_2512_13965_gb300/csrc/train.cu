@@ -14,9 +14,13 @@
 //                   hand-derived backward; AdamW (decoupled weight decay).
 //
 // The dense layers run either on tcgen05 tensor cores with BF16 operands
-// (train_tc.cu; the default of the command-line trainer) or on a tiled FP32
-// SIMT GEMM, both with fused epilogues (bias + SiLU forward, SiLU' backward)
-// and FP32 accumulation; master weights and AdamW moments are FP32 in both.
+// (train_fused.cu; the default of the command-line trainer) or on a tiled
+// FP32 SIMT GEMM with fused epilogues (bias + SiLU forward, SiLU' backward),
+// both with FP32 accumulation; master weights and AdamW moments are FP32.
+// The residual-modulated network (a loaded network with weight-file flag 1)
+// trains on the FP32 path: its blocks' epilogue adds the condition shift,
+// applies the channel scale and the residual, and the reverse pass carries
+// the block gradient through the residual path (fwd_bwd_rm).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -38,6 +42,8 @@ struct TrainState {
   const float *cond = nullptr, *y = nullptr;
   float stats[18];
   gmc_train_config cfg{};
+  bool rm = false;         // residual-modulated network
+  int64_t np = P_TOTAL;    // parameters (P_TOTAL_RM with rm)
   int64_t step = 0;
   float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
   int64_t B = 0;
@@ -207,7 +213,13 @@ __global__ void batch_explicit_kernel(int64_t B, const float *cn, const float *x
   for (int k = 25; k < 32; ++k) row[k] = 0.0f;
 }
 
-enum Epi { kEpiStore = 0, kEpiBiasSilu = 1, kEpiBias = 2, kEpiDSilu = 3 };
+enum Epi { kEpiStore = 0, kEpiBiasSilu = 1, kEpiBias = 2, kEpiDSilu = 3, kEpiRM = 4, kEpiAdd = 5 };
+
+// Extra operands of a residual-modulated block's forward epilogue: M [256][5],
+// G [2][256] and the batch rows X0 (standardized condition in columns 0..4).
+struct RMArgs {
+  const float *M = nullptr, *G = nullptr, *X0 = nullptr;
+};
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
 
@@ -220,7 +232,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
                                                    int64_t sbn, float *__restrict__ C,
                                                    const float *__restrict__ bias,
                                                    float *__restrict__ C2,
-                                                   const float *__restrict__ Zp) {
+                                                   const float *__restrict__ Zp, RMArgs rm) {
   __shared__ float As[16][64 + 4];
   __shared__ float Bs[16][64 + 4];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -269,6 +281,18 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
       } else if (EPI == kEpiDSilu) {
         const float z = Zp[o], s = sigmoidf_(z);
         C[o] = v * (s * (1.0f + z * (1.0f - s)));
+      } else if (EPI == kEpiRM) {
+        // z = acc + b + M c; output a_prev + SiLU(g z), g = 1 + G0 c_3 + G1 c_4
+        const float *cn = rm.X0 + (int64_t)m * 32;
+        float z = v + bias[nn];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) z = fmaf(rm.M[nn * 5 + k], cn[k], z);
+        const float g = fmaf(rm.G[nn], cn[3], fmaf(rm.G[256 + nn], cn[4], 1.0f));
+        const float pz = g * z;
+        C[o] = z;
+        C2[o] = Zp[o] + pz * sigmoidf_(pz);
+      } else if (EPI == kEpiAdd) {
+        C[o] += v;
       } else {
         C[o] = v;
       }
@@ -279,9 +303,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
 template <int EPI>
 cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float *A, int64_t sam, int64_t sak,
                  const float *B, int64_t sbk, int64_t sbn, float *C, const float *bias = nullptr,
-                 float *C2 = nullptr, const float *Zp = nullptr) {
+                 float *C2 = nullptr, const float *Zp = nullptr, RMArgs rm = RMArgs()) {
   dim3 grid((N + 63) / 64, (M + 63) / 64);
-  gemm_kernel<EPI><<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, bias, C2, Zp);
+  gemm_kernel<EPI><<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, bias, C2, Zp, rm);
   return cudaGetLastError();
 }
 
@@ -362,8 +386,88 @@ __global__ void adamw_kernel(int64_t n, float *__restrict__ p, const float *__re
 
 inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Reverse pass of a residual-modulated block's scale and SiLU: from dA (the
+// gradient reaching the block output) and z, dp = dA silu'(g z), dz = dp g
+// (out), and dp z replaces z (the factor of the channel-scale gradients).
+__global__ void rm_back_kernel(int64_t n, const float *__restrict__ dA, float *__restrict__ Z,
+                               const float *__restrict__ X0, const float *__restrict__ G,
+                               float *__restrict__ dz) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t b = i >> 8;
+  const int c = (int)(i & 255);
+  const float g = fmaf(G[c], X0[b * 32 + 3], fmaf(G[256 + c], X0[b * 32 + 4], 1.0f));
+  const float z = Z[i], pz = g * z, s = sigmoidf_(pz);
+  const float dp = dA[i] * (s * (1.0f + pz * (1.0f - s)));
+  dz[i] = dp * g;
+  Z[i] = dp * z;
+}
+
+// out = dA silu'(z), elementwise
+__global__ void dsilu_kernel(int64_t n, const float *__restrict__ dA, const float *__restrict__ Z,
+                             float *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float z = Z[i], s = sigmoidf_(z);
+  out[i] = dA[i] * (s * (1.0f + z * (1.0f - s)));
+}
+
+// forward + loss + backward of the residual-modulated network (the gradient
+// of each block as the reverse pass of the oracle states it); grads overwritten
+cudaError_t fwd_bwd_rm(cudaStream_t s, TrainState &T, double *loss_slot) {
+  const int B = (int)T.B;
+  const int64_t nh = (int64_t)B * 256;
+  float *P = T.params, *G = T.grads;
+  const int64_t wofs[4] = {P_W1, P_W2, P_W3, P_W4}, bofs[4] = {P_B1, P_B2, P_B3, P_B4};
+  cudaError_t e = gemm<kEpiBiasSilu>(s, B, 256, 32, T.X0, 32, 1, P + P_W1, 1, 32, T.Z[0], P + P_B1, T.A[0]);
+  if (e) return e;
+  for (int l = 1; l < 4; ++l) {
+    const int j = l - 1;
+    RMArgs ra;
+    ra.M = P + P_RM_M + j * 1280;
+    ra.G = P + P_RM_G + j * 512;
+    ra.X0 = T.X0;
+    e = gemm<kEpiRM>(s, B, 256, 256, T.A[l - 1], 256, 1, P + wofs[l], 1, 256, T.Z[l], P + bofs[l],
+                     T.A[l], T.A[l - 1], ra);
+    if (e) return e;
+  }
+  e = gemm<kEpiBias>(s, B, 4, 256, T.A[3], 256, 1, P + P_W5, 1, 256, T.V, P + P_B5);
+  if (e) return e;
+  loss_kernel<<<nb(B, 256), 256, 0, s>>>(B, T.V, T.U, T.dV, loss_slot);
+  e = gemm<kEpiStore>(s, 4, 256, B, T.dV, 1, 4, T.A[3], 256, 1, G + P_W5);
+  if (e) return e;
+  e = colsum(s, B, 4, T.dV, T.colpart, G + P_B5);
+  if (e) return e;
+  float *dA = T.dZ[0], *dz = T.dZ[1];
+  e = gemm<kEpiStore>(s, B, 256, 4, T.dV, 4, 1, P + P_W5, 256, 1, dA);  // dA = dV W5
+  if (e) return e;
+  for (int l = 3; l >= 1; --l) {
+    const int j = l - 1;
+    rm_back_kernel<<<nb(nh, 256), 256, 0, s>>>(nh, dA, T.Z[l], T.X0, P + P_RM_G + j * 512, dz);
+    // dW_l = dz^T A_{l-1}, db_l = sum dz, dM_j = dz^T c, dG_j = [c_3 c_4]^T (dp z)
+    e = gemm<kEpiStore>(s, 256, 256, B, dz, 1, 256, T.A[l - 1], 256, 1, G + wofs[l]);
+    if (e) return e;
+    e = colsum(s, B, 256, dz, T.colpart, G + bofs[l]);
+    if (e) return e;
+    e = gemm<kEpiStore>(s, 256, 5, B, dz, 1, 256, T.X0, 32, 1, G + P_RM_M + j * 1280);
+    if (e) return e;
+    e = gemm<kEpiStore>(s, 2, 256, B, T.X0 + 3, 1, 32, T.Z[l], 256, 1, G + P_RM_G + j * 512);
+    if (e) return e;
+    // the residual path: dA <- dA + dz W_l
+    e = gemm<kEpiAdd>(s, B, 256, 256, dz, 256, 1, P + wofs[l], 256, 1, dA);
+    if (e) return e;
+  }
+  dsilu_kernel<<<nb(nh, 256), 256, 0, s>>>(nh, dA, T.Z[0], dz);
+  e = gemm<kEpiStore>(s, 256, 32, B, dz, 1, 256, T.X0, 32, 1, G + P_W1);
+  if (e) return e;
+  e = colsum(s, B, 256, dz, T.colpart, G + P_B1);
+  if (e) return e;
+  return cudaGetLastError();
+}
+
 // forward + loss + backward for the batch already in X0/U; grads overwritten
 cudaError_t fwd_bwd(cudaStream_t s, TrainState &T, double *loss_slot) {
+  if (T.rm) return fwd_bwd_rm(s, T, loss_slot);
   const int B = (int)T.B;
   float *P = T.params, *G = T.grads;
   const float *W[4] = {P + P_W1, P + P_W2, P + P_W3, P + P_W4};
@@ -536,6 +640,8 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
   if (cfg->precision != GMC_FP32 && cfg->precision != GMC_BF16)
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: precision must be GMC_FP32 or GMC_BF16");
   if (!ctx->net.loaded) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_train_begin: load initial weights first");
+  if (ctx->net.rm && cfg->precision != GMC_FP32)
+    return set_error(ctx, GMC_EINVAL, "gmc_train_begin: the residual-modulated network trains at GMC_FP32");
   if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: data must be device memory");
   cudaSetDevice(ctx->device);
@@ -546,6 +652,8 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
   T->cond = cond;
   T->y = y;
   T->cfg = *cfg;
+  T->rm = ctx->net.rm;
+  T->np = T->rm ? P_TOTAL_RM : P_TOTAL;
   T->step = 0;
   cudaStream_t s = ctx->stream;
   GMC_CUDA_TRY(ctx, cudaMalloc(&T->stat_acc, 18 * sizeof(double)));
@@ -568,7 +676,8 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
     }
   }
   // master weights from the loaded network
-  std::vector<float> h(P_TOTAL, 0.0f);
+  const int64_t np = T->np;
+  std::vector<float> h(np, 0.0f);
   for (int c = 0; c < 256; ++c)
     for (int k = 0; k < 25; ++k) h[P_W1 + c * 32 + k] = ctx->net.host_w[0][c * 25 + k];
   std::memcpy(&h[P_B1], ctx->net.host_b[0], 256 * 4);
@@ -579,14 +688,18 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
   }
   std::memcpy(&h[P_W5], ctx->net.host_w[4], 1024 * 4);
   std::memcpy(&h[P_B5], ctx->net.host_b[4], 4 * 4);
-  GMC_CUDA_TRY(ctx, cudaMalloc(&T->params, P_TOTAL * 4));
-  GMC_CUDA_TRY(ctx, cudaMalloc(&T->grads, P_TOTAL * 4));
-  GMC_CUDA_TRY(ctx, cudaMalloc(&T->m, P_TOTAL * 4));
-  GMC_CUDA_TRY(ctx, cudaMalloc(&T->v, P_TOTAL * 4));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->params, h.data(), P_TOTAL * 4, cudaMemcpyHostToDevice, s));
-  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->grads, 0, P_TOTAL * 4, s));
-  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->m, 0, P_TOTAL * 4, s));
-  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->v, 0, P_TOTAL * 4, s));
+  if (T->rm) {
+    std::memcpy(&h[P_RM_M], ctx->net.host_m, 3 * 256 * 5 * 4);
+    std::memcpy(&h[P_RM_G], ctx->net.host_g, 3 * 512 * 4);
+  }
+  GMC_CUDA_TRY(ctx, cudaMalloc(&T->params, np * 4));
+  GMC_CUDA_TRY(ctx, cudaMalloc(&T->grads, np * 4));
+  GMC_CUDA_TRY(ctx, cudaMalloc(&T->m, np * 4));
+  GMC_CUDA_TRY(ctx, cudaMalloc(&T->v, np * 4));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->params, h.data(), np * 4, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->grads, 0, np * 4, s));
+  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->m, 0, np * 4, s));
+  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->v, 0, np * 4, s));
   GMC_CUDA_TRY(ctx, alloc_batch(*T, cfg->batch, s));
   T->err = ctx->d_err;
   if (cfg->precision == GMC_BF16) GMC_CUDA_TRY(ctx, tf::pack(s, T->fb, T->params));
@@ -632,7 +745,7 @@ gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses) {
       GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i, &adam, &gen, &next));
     } else {
       GMC_CUDA_TRY(ctx, step_grads(s, *T, T->loss + i));
-      adamw_kernel<<<nb(P_TOTAL, 256), 256, 0, s>>>(P_TOTAL, T->params, T->grads, T->m, T->v,
+      adamw_kernel<<<nb(T->np, 256), 256, 0, s>>>(T->np, T->params, T->grads, T->m, T->v,
                                                     (float)c.lr, (float)c.beta1, (float)c.beta2,
                                                     (float)c.eps, (float)c.weight_decay, bc1, bc2);
     }
@@ -677,12 +790,19 @@ gmc_status gmc_train_grad(gmc_ctx *ctx, int64_t B, const float *cn, const float 
   T->B = saveB;
   GMC_CUDA_TRY(ctx, e);
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(loss, ls, sizeof(double), cudaMemcpyDeviceToHost, s));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(grad, T->grads, P_TOTAL * 4, cudaMemcpyDeviceToHost, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(grad, T->grads, T->np * 4, cudaMemcpyDeviceToHost, s));
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   return check_device_error(ctx);
 }
 
 int64_t gmc_train_param_count(void) { return P_TOTAL; }
+
+gmc_status gmc_train_param_count_ctx(const gmc_ctx *ctx, int64_t *count) {
+  if (!ctx || !count) return GMC_EINVAL;
+  if (!ctx->train) return GMC_EINVAL;
+  *count = ctx->train->np;
+  return GMC_OK;
+}
 
 gmc_status gmc_train_set_lr(gmc_ctx *ctx, double lr) {
   if (!ctx) return GMC_EINVAL;
@@ -696,7 +816,8 @@ gmc_status gmc_train_params(gmc_ctx *ctx, float *out) {
   if (!ctx || !out) return GMC_EINVAL;
   if (!ctx->train) return set_error(ctx, GMC_EINVAL, "gmc_train_params: call gmc_train_begin first");
   cudaSetDevice(ctx->device);
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->train->params, P_TOTAL * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->train->params, ctx->train->np * 4, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return GMC_OK;
 }
@@ -713,7 +834,7 @@ struct TrainCkpt {
   char magic[4];
   uint32_t version;
   int64_t params, step, batch, n;
-  int32_t precision, reserved;
+  int32_t precision, arch;  // arch 1: the residual-modulated network
   double lr, beta1, beta2, eps, weight_decay;
   uint64_t seed;
   float stats[18];
@@ -721,7 +842,8 @@ struct TrainCkpt {
 
 gmc_status gmc_train_state_size(const gmc_ctx *ctx, size_t *bytes) {
   if (!ctx || !bytes) return GMC_EINVAL;
-  *bytes = sizeof(TrainCkpt) + 3 * (size_t)P_TOTAL * sizeof(float);
+  const int64_t np = ctx->train ? ctx->train->np : P_TOTAL;
+  *bytes = sizeof(TrainCkpt) + 3 * (size_t)np * sizeof(float);
   return GMC_OK;
 }
 
@@ -737,7 +859,8 @@ gmc_status gmc_train_save_state(gmc_ctx *ctx, void *blob, size_t nbytes) {
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "GMCT", 4);
   h.version = 2;
-  h.params = P_TOTAL;
+  h.params = T->np;
+  h.arch = T->rm ? 1 : 0;
   h.step = T->step;
   h.batch = T->cfg.batch;
   h.n = T->n;
@@ -754,9 +877,10 @@ gmc_status gmc_train_save_state(gmc_ctx *ctx, void *blob, size_t nbytes) {
   float *body = (float *)(out + sizeof(h));
   cudaSetDevice(ctx->device);
   cudaStream_t s = ctx->stream;
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(body, T->params, P_TOTAL * 4, cudaMemcpyDeviceToHost, s));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(body + P_TOTAL, T->m, P_TOTAL * 4, cudaMemcpyDeviceToHost, s));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(body + 2 * P_TOTAL, T->v, P_TOTAL * 4, cudaMemcpyDeviceToHost, s));
+  const int64_t np = T->np;
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(body, T->params, np * 4, cudaMemcpyDeviceToHost, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(body + np, T->m, np * 4, cudaMemcpyDeviceToHost, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(body + 2 * np, T->v, np * 4, cudaMemcpyDeviceToHost, s));
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   return check_device_error(ctx);
 }
@@ -771,8 +895,10 @@ gmc_status gmc_train_load_state(gmc_ctx *ctx, const void *blob, size_t nbytes) {
     return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: a checkpoint is %zu bytes", need);
   TrainCkpt h;
   std::memcpy(&h, blob, sizeof(h));
-  if (std::memcmp(h.magic, "GMCT", 4) != 0 || h.version != 2 || h.params != P_TOTAL)
-    return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: not a version-2 training checkpoint");
+  if (std::memcmp(h.magic, "GMCT", 4) != 0 || h.version != 2 || h.params != T->np ||
+      h.arch != (T->rm ? 1 : 0))
+    return set_error(ctx, GMC_EFORMAT,
+                     "gmc_train_load_state: not a version-2 training checkpoint of this network");
   for (int k = 0; k < 18; ++k)
     if (!std::isfinite(h.stats[k]) || (((k >= 5 && k < 10) || k >= 14) && !(h.stats[k] > 0.0f)))
       return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: bad standardization statistics");
@@ -787,9 +913,10 @@ gmc_status gmc_train_load_state(gmc_ctx *ctx, const void *blob, size_t nbytes) {
   const float *body = (const float *)((const unsigned char *)blob + sizeof(h));
   cudaSetDevice(ctx->device);
   cudaStream_t s = ctx->stream;
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->params, body, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->m, body + P_TOTAL, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->v, body + 2 * P_TOTAL, P_TOTAL * 4, cudaMemcpyHostToDevice, s));
+  const int64_t np = T->np;
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->params, body, np * 4, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->m, body + np, np * 4, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(T->v, body + 2 * np, np * 4, cudaMemcpyHostToDevice, s));
   if (T->cfg.precision == GMC_BF16) {
     GMC_CUDA_TRY(ctx, tf::pack(s, T->fb, T->params));
     T->fb.pregen_step = -1;  // rows drawn for another step or seed
@@ -811,8 +938,8 @@ gmc_status gmc_train_commit(gmc_ctx *ctx, const char *path) {
   if (!T) return set_error(ctx, GMC_EINVAL, "gmc_train_commit: call gmc_train_begin first");
   if (ctx->server) return set_error(ctx, GMC_EBUSY, "gmc_train_commit: the server is running");
   cudaSetDevice(ctx->device);
-  std::vector<float> h(P_TOTAL);
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), T->params, P_TOTAL * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<float> h(T->np);
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), T->params, T->np * 4, cudaMemcpyDeviceToHost, ctx->stream));
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   // GMCW version 1 blob
   std::vector<unsigned char> blob;
@@ -822,7 +949,7 @@ gmc_status gmc_train_commit(gmc_ctx *ctx, const char *path) {
   u32(1); u32(5);
   const uint32_t dims[6] = {25, 256, 256, 256, 256, 4};
   for (uint32_t dd : dims) u32(dd);
-  u32(5); u32(4); u32(16); u32(0);
+  u32(5); u32(4); u32(16); u32(T->rm ? kFlagRM : 0u);
   f32(T->stats, 18);
   std::vector<float> w1(256 * 25);
   for (int c = 0; c < 256; ++c)
@@ -833,6 +960,10 @@ gmc_status gmc_train_commit(gmc_ctx *ctx, const char *path) {
   f32(&h[P_W3], 65536); f32(&h[P_B3], 256);
   f32(&h[P_W4], 65536); f32(&h[P_B4], 256);
   f32(&h[P_W5], 1024); f32(&h[P_B5], 4);
+  if (T->rm) {
+    f32(&h[P_RM_M], 3 * 256 * 5);
+    f32(&h[P_RM_G], 3 * 512);
+  }
   if (path) {
     FILE *f = std::fopen(path, "wb");
     if (!f) return set_error(ctx, GMC_EIO, "cannot write '%s'", path);

@@ -13,6 +13,10 @@ constexpr int64_t P_W1 = 0, P_B1 = 8192, P_W2 = P_B1 + 256, P_B2 = P_W2 + 65536,
                   P_W3 = P_B2 + 256, P_B3 = P_W3 + 65536, P_W4 = P_B3 + 256,
                   P_B4 = P_W4 + 65536, P_W5 = P_B4 + 256, P_B5 = P_W5 + 1024,
                   P_TOTAL = P_B5 + 4;
+// the residual-modulated network continues the block with its condition
+// shifts M_j [256][5] and channel scales G_j [2][256] of hidden layers 2-4
+constexpr int64_t P_RM_M = P_TOTAL, P_RM_G = P_RM_M + 3 * 256 * 5,
+                  P_TOTAL_RM = P_RM_G + 3 * 2 * 256;
 
 // Standardization of the training data: condition and target means and
 // inverse standard deviations.

@@ -848,6 +848,13 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
   if (n_histories > 0 && !(acc > 0.0)) return set_error(ctx, GMC_EINVAL, "solve: zero source");
   if (method == GMC_METHOD_GMC && !ctx->net.loaded)
     return set_error(ctx, GMC_ENOWEIGHTS, "solve: GMC needs gmc_load_weights");
+  if (method == GMC_METHOD_GMC) {
+    const gmc_config &cf = ctx->cfg;
+    if (check_net_path(ctx, ctx->net, cf.precision, cf.sampler_kernel, "solve") != GMC_OK ||
+        (ctx->internal.loaded &&
+         check_net_path(ctx, ctx->internal, cf.precision, cf.sampler_kernel, "solve") != GMC_OK))
+      return GMC_EINVAL;
+  }
   R.total = acc;
   R.n_hist = n_histories;
   R.method = method;
@@ -1440,6 +1447,11 @@ gmc_status gmc_serve_start(gmc_ctx *ctx, const gmc_serve_config *cfg) {
     return set_error(ctx, GMC_EINVAL, "gmc_serve_start: memory_budget must be >= 1 MiB");
   if (cfg->method == GMC_METHOD_GMC && !ctx->net.loaded)
     return set_error(ctx, GMC_ENOWEIGHTS, "gmc_serve_start: GMC needs gmc_load_weights");
+  if (cfg->method == GMC_METHOD_GMC &&
+      (check_net_path(ctx, ctx->net, ctx->cfg.precision, ctx->cfg.sampler_kernel, "gmc_serve_start") != GMC_OK ||
+       (ctx->internal.loaded && check_net_path(ctx, ctx->internal, ctx->cfg.precision,
+                                               ctx->cfg.sampler_kernel, "gmc_serve_start") != GMC_OK)))
+    return GMC_EINVAL;
   cudaSetDevice(ctx->device);
   Server *S = new Server();
   S->ctx = ctx;
