@@ -59,11 +59,11 @@
 // of z_l enters through the bias MMA like the bias (the condition columns of
 // the layer-1 operand against M_l / 2 in the bias block), so the accumulator
 // already holds z_l / 2. The epilogue scales it by the channel modulation
-// g = 1 + G_l[0] c_3 + G_l[1] c_4 (FP32: the row's standardized ln tau and c
-// are held in registers, G is read through the L1 cache), applies the SiLU
-// and adds the block input, which it reads from A_T (the MMA that read it has
-// completed) just before overwriting it: the residual stream is the BF16
-// operand itself and costs no tensor memory.
+// g = 1 + G_l[0] c_3 + G_l[1] c_4 in packed BF16 (G as BF16 pairs in shared
+// memory, the row's standardized ln tau and c in a per-thread shared slot),
+// applies the SiLU and adds the block input, which it reads from A_T (the
+// MMA that read it has completed) just before overwriting it: the residual
+// stream is the BF16 operand itself and costs no tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -103,11 +103,13 @@ constexpr uint32_t S_B5 = 16384;                 // 8 KB
 constexpr uint32_t S_BIAS = 24576;               // 24 KB (BF16 variant)
 constexpr uint32_t S_ST = 49152;                 // NST weight stages
 constexpr uint32_t S_BAR = S_ST + NST * CHUNK;   // barriers and flags
-// residual-modulated network: (ln tau, c) standardized, per tile, epilogue
-// thread and row ([T][epilogue warp][lane] float2; each thread reads only
-// what it wrote, so registers are spared without a barrier)
+// residual-modulated network: (ln tau, c) standardized as BF16 pairs (each
+// value in both halves), per tile, epilogue thread and row ([T][epilogue
+// warp][lane] uint2; each thread reads only what it wrote, so registers are
+// spared without a barrier)
 constexpr uint32_t S_U = S_BAR + 256;
-constexpr uint32_t S_TOTAL = S_U + 2 * EPI_WARPS * 32 * 8;
+constexpr uint32_t S_G = S_U + 2 * EPI_WARPS * 32 * 8;  // RM: G as BF16 pairs [3][2][128]
+constexpr uint32_t S_TOTAL = S_G + 3 * 2 * 128 * 4;
 constexpr uint32_t SMEM_BYTES = S_TOTAL + 1024;  // + alignment slack
 // More than half of the SM's shared memory, so no second CTA (which would
 // wait for the 512 tensor-memory columns this one holds) shares the SM.
@@ -132,23 +134,32 @@ __device__ void fail(Bars &b, int *err, int code) {
 }
 
 // Residual blocks (layers 2-4 of the residual-modulated network, L = 1..3):
-// rm_scale packs the scaled halved pre-activations g z / 2 of 32 accumulator
-// columns (col0 ..) into 16 BF16 pairs; rm_finish reads the block input of
-// this thread's 64 columns from a_row (BF16 columns col0 / 2 ..), adds the
-// SiLU and writes the sum back.
-__device__ __forceinline__ void rm_scale(int L, const uint32_t (&v)[32], const float *__restrict__ rmg,
-                                         float u3, float u4, int col0, uint32_t (&hp)[16]) {
-  const float4 *g0 = reinterpret_cast<const float4 *>(rmg + (L - 1) * 512 + col0);
-  const float4 *g1 = reinterpret_cast<const float4 *>(rmg + (L - 1) * 512 + 256 + col0);
+// rm_scale turns 32 halved pre-activations h = z / 2 (accumulator columns
+// col0 ..) into 16 BF16 pairs of g h = h + h d, d = G[0] c_3 + G[1] c_4, in
+// packed BF16 (gs: the layer's G as BF16 pairs, [2][128]; u3p, u4p: the row's
+// c_3 and c_4 in both halves). Forming h + h d with one FMA rounds once
+// where g = 1 + d followed by g h would round twice. rm_finish reads the
+// block input of this thread's 64 columns from a_row (BF16 columns col0 / 2
+// ..), adds the SiLU and writes the sum back.
+__device__ __forceinline__ void rm_scale(const uint32_t (&v)[32], const uint32_t *gs, uint32_t u3p,
+                                         uint32_t u4p, int col0, uint32_t (&hp)[16]) {
+  const uint4 *g0 = reinterpret_cast<const uint4 *>(gs + (col0 >> 1));
+  const uint4 *g1 = reinterpret_cast<const uint4 *>(gs + 128 + (col0 >> 1));
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const float4 ga = __ldg(g0 + q), gb = __ldg(g1 + q);
-    const float h0 = __uint_as_float(v[4 * q]) * fmaf(ga.x, u3, fmaf(gb.x, u4, 1.0f));
-    const float h1 = __uint_as_float(v[4 * q + 1]) * fmaf(ga.y, u3, fmaf(gb.y, u4, 1.0f));
-    const float h2 = __uint_as_float(v[4 * q + 2]) * fmaf(ga.z, u3, fmaf(gb.z, u4, 1.0f));
-    const float h3 = __uint_as_float(v[4 * q + 3]) * fmaf(ga.w, u3, fmaf(gb.w, u4, 1.0f));
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hp[2 * q]) : "f"(h1), "f"(h0));
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hp[2 * q + 1]) : "f"(h3), "f"(h2));
+  for (int q = 0; q < 4; ++q) {
+    const uint4 a4 = g0[q], b4 = g1[q];
+    const uint32_t ga[4] = {a4.x, a4.y, a4.z, a4.w}, gb[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint32_t h, t, d;
+      const int k = 4 * q + i;
+      asm("cvt.rn.bf16x2.f32 %0, %1, %2;"
+          : "=r"(h)
+          : "f"(__uint_as_float(v[2 * k + 1])), "f"(__uint_as_float(v[2 * k])));
+      asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(t) : "r"(gb[i]), "r"(u4p));
+      asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(ga[i]), "r"(u3p), "r"(t));
+      asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(hp[k]) : "r"(h), "r"(d));
+    }
   }
 }
 
@@ -229,6 +240,16 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     mbar_init(&B.drain, 1);
     B.abort = 0;
     fence_mbar_init();
+  }
+  if constexpr (RM) {
+    // the channel scales of layers 2-4 as BF16 pairs, read by every epilogue
+    uint32_t *gs = reinterpret_cast<uint32_t *>(sm + S_G);
+    for (int i = threadIdx.x; i < 3 * 2 * 128; i += THREADS) {
+      const float lo = P.rmg[2 * i], hi = P.rmg[2 * i + 1];
+      uint32_t w;
+      asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+      gs[i] = w;
+    }
   }
   if (warp == 1) {
     tmem_alloc(&B.tmem_base, TMEM_COLS);
@@ -398,7 +419,7 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
     const bool owner = p == 0;  // holds the ODE state of tile g's rows
     float x[4], xm[4], ka[4];
-    float2 *u_slot = reinterpret_cast<float2 *>(sm + S_U) + ew * 32 + lane;  // RM: + 512 T
+    uint2 *u_slot = reinterpret_cast<uint2 *>(sm + S_U) + ew * 32 + lane;  // RM: + 512 T
     uint32_t dph = 0;
     bool ok = true;
     for (int64_t ip = 0; ip < n_iter && ok; ++ip) {
@@ -408,10 +429,14 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
         for (int T = 0; T < 2; ++T) {
           const int64_t gi = (2 * pr + T) * TM + r;
           const bool valid = gi < P.n;
-          u_slot[512 * T] = valid ? make_float2(
-                                        (P.cond[3 * P.n + gi] - P.st.cond_mean[3]) * P.st.cond_inv_std[3],
-                                        (P.cond[4 * P.n + gi] - P.st.cond_mean[4]) * P.st.cond_inv_std[4])
-                                  : make_float2(0.0f, 0.0f);
+          const float u3 =
+              valid ? (P.cond[3 * P.n + gi] - P.st.cond_mean[3]) * P.st.cond_inv_std[3] : 0.0f;
+          const float u4 =
+              valid ? (P.cond[4 * P.n + gi] - P.st.cond_mean[4]) * P.st.cond_inv_std[4] : 0.0f;
+          uint2 up;
+          asm("cvt.rn.bf16x2.f32 %0, %1, %1;" : "=r"(up.x) : "f"(u3));
+          asm("cvt.rn.bf16x2.f32 %0, %1, %1;" : "=r"(up.y) : "f"(u4));
+          u_slot[512 * T] = up;
         }
       }
       {
@@ -460,20 +485,21 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
             tc_fence_after();
             if constexpr (RM) {
               if (L > 0) {
-                // residual block: each 32-column half is scaled and packed as
-                // it arrives (fewer live registers), then the accumulator is
-                // released and the block output overwrites its input in A_T
-                const float2 u = u_slot[512 * T];
-                uint32_t h0[16], h1[16], v[32];
-                tmem_ld32_raw(d_col, v);
-                tmem_wait_ld_regs(v);
-                rm_scale(L, v, P.rmg, u.x, u.y, col0, h0);
-                tmem_ld32_raw(d_col + 32u, v);
-                tmem_wait_ld_regs(v);
-                rm_scale(L, v, P.rmg, u.x, u.y, col0 + 32, h1);
+                // residual block: the accumulator is read out and released at
+                // once, then scaled, and the block output overwrites its input
+                const uint2 u = u_slot[512 * T];
+                uint32_t va[32], vb[32];
+                tmem_ld32_raw(d_col, va);
+                tmem_ld32_raw(d_col + 32u, vb);
+                tmem_wait_ld_regs(va);
+                tmem_wait_ld_regs(vb);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&B.dfree);
+                uint32_t h0[16], h1[16];
+                const uint32_t *gs = reinterpret_cast<const uint32_t *>(sm + S_G) + (L - 1) * 256;
+                rm_scale(va, gs, u.x, u.y, col0, h0);
+                rm_scale(vb, gs, u.x, u.y, col0 + 32, h1);
                 rm_finish(h0, h1, col0, a_row);
                 tmem_wait_st();
                 tc_fence_before();

@@ -53,6 +53,7 @@ struct TrainState {
   int64_t loss_cap = 0;
   double *stat_acc = nullptr;  // 18 sums
   float *colpart = nullptr;    // partial column sums of the bias gradients (FP32 path)
+  float *ws = nullptr;         // K-split partial products of the weight gradients (FP32 path)
   tf::Bufs fb;                 // operand images of the BF16 tensor-core step
   int *err = nullptr;          // device error word of the context
 };
@@ -232,20 +233,26 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
                                                    int64_t sbn, float *__restrict__ C,
                                                    const float *__restrict__ bias,
                                                    float *__restrict__ C2,
-                                                   const float *__restrict__ Zp, RMArgs rm) {
+                                                   const float *__restrict__ Zp, RMArgs rm,
+                                                   int kslice) {
   __shared__ float As[16][64 + 4];
   __shared__ float Bs[16][64 + 4];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  // K split over blockIdx.z (kEpiStore only): slice z covers [z kslice,
+  // (z + 1) kslice) and writes its partial product to C + z M N
+  const int kb = blockIdx.z * kslice;
+  const int ke = K < kb + kslice ? K : kb + kslice;
+  if (EPI == kEpiStore) C += (int64_t)blockIdx.z * M * N;
   float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  for (int k0 = kb; k0 < ke; k0 += 16) {
     for (int e = threadIdx.x; e < 16 * 64; e += 256) {
       const int kk = e & 15, mm = e >> 4;
       const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < K) ? A[gm * sam + gk * sak] : 0.0f;
-      const int nn = e & 63, kb = e >> 6;
-      const int gn = n0 + nn, gk2 = k0 + kb;
-      Bs[kb][nn] = (gn < N && gk2 < K) ? Bm[gk2 * sbk + gn * sbn] : 0.0f;
+      As[kk][mm] = (gm < M && gk < ke) ? A[gm * sam + gk * sak] : 0.0f;
+      const int nn = e & 63, kr = e >> 6;
+      const int gn = n0 + nn, gk2 = k0 + kr;
+      Bs[kr][nn] = (gn < N && gk2 < ke) ? Bm[gk2 * sbk + gn * sbn] : 0.0f;
     }
     __syncthreads();
 #pragma unroll
@@ -305,7 +312,38 @@ cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float *A, int64_t sa
                  const float *B, int64_t sbk, int64_t sbn, float *C, const float *bias = nullptr,
                  float *C2 = nullptr, const float *Zp = nullptr, RMArgs rm = RMArgs()) {
   dim3 grid((N + 63) / 64, (M + 63) / 64);
-  gemm_kernel<EPI><<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, bias, C2, Zp, rm);
+  gemm_kernel<EPI><<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, bias, C2, Zp, rm, K);
+  return cudaGetLastError();
+}
+
+// out[i] = sum_z part[z][i], z in order (deterministic)
+__global__ void ksum_kernel(int64_t mn, int S, const float *__restrict__ part, float *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= mn) return;
+  float t = 0.0f;
+  for (int z = 0; z < S; ++z) t += part[z * mn + i];
+  out[i] = t;
+}
+
+constexpr int kMaxKSplit = 16;
+constexpr int64_t kKSplitWs = (int64_t)kMaxKSplit * 256 * 256;  // workspace floats
+
+// C = A B for a weight gradient (K = the batch): the few output tiles of a
+// 256 x 256 product would occupy 16 SMs, so K is split into up to 16 slices
+// of at least 1024 rows, each slice's partial product goes to ws, and one
+// pass adds the slices in a fixed order.
+cudaError_t gemm_wgrad(cudaStream_t s, int M, int N, int K, const float *A, int64_t sam, int64_t sak,
+                       const float *B, int64_t sbk, int64_t sbn, float *C, float *ws) {
+  int S = K / 1024;
+  if (S > kMaxKSplit) S = kMaxKSplit;
+  if (S < 2 || (int64_t)S * M * N > kKSplitWs) return gemm<kEpiStore>(s, M, N, K, A, sam, sak, B, sbk, sbn, C);
+  const int kslice = ((K + S - 1) / S + 15) / 16 * 16;
+  S = (K + kslice - 1) / kslice;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, S);
+  gemm_kernel<kEpiStore><<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, ws, nullptr, nullptr,
+                                              nullptr, RMArgs(), kslice);
+  const int64_t mn = (int64_t)M * N;
+  ksum_kernel<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(mn, S, ws, C);
   return cudaGetLastError();
 }
 
@@ -434,7 +472,7 @@ cudaError_t fwd_bwd_rm(cudaStream_t s, TrainState &T, double *loss_slot) {
   e = gemm<kEpiBias>(s, B, 4, 256, T.A[3], 256, 1, P + P_W5, 1, 256, T.V, P + P_B5);
   if (e) return e;
   loss_kernel<<<nb(B, 256), 256, 0, s>>>(B, T.V, T.U, T.dV, loss_slot);
-  e = gemm<kEpiStore>(s, 4, 256, B, T.dV, 1, 4, T.A[3], 256, 1, G + P_W5);
+  e = gemm_wgrad(s, 4, 256, B, T.dV, 1, 4, T.A[3], 256, 1, G + P_W5, T.ws);
   if (e) return e;
   e = colsum(s, B, 4, T.dV, T.colpart, G + P_B5);
   if (e) return e;
@@ -445,20 +483,20 @@ cudaError_t fwd_bwd_rm(cudaStream_t s, TrainState &T, double *loss_slot) {
     const int j = l - 1;
     rm_back_kernel<<<nb(nh, 256), 256, 0, s>>>(nh, dA, T.Z[l], T.X0, P + P_RM_G + j * 512, dz);
     // dW_l = dz^T A_{l-1}, db_l = sum dz, dM_j = dz^T c, dG_j = [c_3 c_4]^T (dp z)
-    e = gemm<kEpiStore>(s, 256, 256, B, dz, 1, 256, T.A[l - 1], 256, 1, G + wofs[l]);
+    e = gemm_wgrad(s, 256, 256, B, dz, 1, 256, T.A[l - 1], 256, 1, G + wofs[l], T.ws);
     if (e) return e;
     e = colsum(s, B, 256, dz, T.colpart, G + bofs[l]);
     if (e) return e;
-    e = gemm<kEpiStore>(s, 256, 5, B, dz, 1, 256, T.X0, 32, 1, G + P_RM_M + j * 1280);
+    e = gemm_wgrad(s, 256, 5, B, dz, 1, 256, T.X0, 32, 1, G + P_RM_M + j * 1280, T.ws);
     if (e) return e;
-    e = gemm<kEpiStore>(s, 2, 256, B, T.X0 + 3, 1, 32, T.Z[l], 256, 1, G + P_RM_G + j * 512);
+    e = gemm_wgrad(s, 2, 256, B, T.X0 + 3, 1, 32, T.Z[l], 256, 1, G + P_RM_G + j * 512, T.ws);
     if (e) return e;
     // the residual path: dA <- dA + dz W_l
     e = gemm<kEpiAdd>(s, B, 256, 256, dz, 256, 1, P + wofs[l], 256, 1, dA);
     if (e) return e;
   }
   dsilu_kernel<<<nb(nh, 256), 256, 0, s>>>(nh, dA, T.Z[0], dz);
-  e = gemm<kEpiStore>(s, 256, 32, B, dz, 1, 256, T.X0, 32, 1, G + P_W1);
+  e = gemm_wgrad(s, 256, 32, B, dz, 1, 256, T.X0, 32, 1, G + P_W1, T.ws);
   if (e) return e;
   e = colsum(s, B, 256, dz, T.colpart, G + P_B1);
   if (e) return e;
@@ -484,7 +522,7 @@ cudaError_t fwd_bwd(cudaStream_t s, TrainState &T, double *loss_slot) {
   if (e) return e;
   loss_kernel<<<nb(B, 256), 256, 0, s>>>(B, T.V, T.U, T.dV, loss_slot);
   // output layer: dW5 = dV^T A4, db5 = sum dV, dZ4 = (dV W5) * SiLU'(Z4)
-  e = gemm<kEpiStore>(s, 4, 256, B, T.dV, 1, 4, T.A[3], 256, 1, G + P_W5);
+  e = gemm_wgrad(s, 4, 256, B, T.dV, 1, 4, T.A[3], 256, 1, G + P_W5, T.ws);
   if (e) return e;
   e = colsum(s, B, 4, T.dV, T.colpart, G + P_B5);
   if (e) return e;
@@ -497,7 +535,7 @@ cudaError_t fwd_bwd(cudaStream_t s, TrainState &T, double *loss_slot) {
     const float *ain = l == 0 ? T.X0 : T.A[l - 1];
     const int kin = l == 0 ? 32 : 256;
     // dW_l = dZ_l^T A_{l-1}; db_l = column sums of dZ_l
-    e = gemm<kEpiStore>(s, 256, kin, B, dz, 1, 256, ain, kin, 1, G + wofs[l]);
+    e = gemm_wgrad(s, 256, kin, B, dz, 1, 256, ain, kin, 1, G + wofs[l], T.ws);
     if (e) return e;
     e = colsum(s, B, 256, dz, T.colpart, G + bofs[l]);
     if (e) return e;
@@ -540,6 +578,7 @@ void free_train(TrainState *T) {
   if (T->loss) cudaFree(T->loss);
   if (T->stat_acc) cudaFree(T->stat_acc);
   if (T->colpart) cudaFree(T->colpart);
+  if (T->ws) cudaFree(T->ws);
   tf::release(T->fb);
   delete T;
 }
@@ -565,6 +604,10 @@ cudaError_t alloc_batch(TrainState &T, int64_t B, cudaStream_t s) {
   cudaError_t e = f32 ? cudaMalloc(&T.colpart, ((B + kColRows - 1) / kColRows) * 256 * sizeof(float))
                       : tf::alloc(T.fb, B, s);
   if (e) return e;
+  if (f32 && !T.ws) {
+    e = cudaMalloc(&T.ws, kKSplitWs * sizeof(float));
+    if (e) return e;
+  }
   T.B = B;
   return cudaSuccess;
 }

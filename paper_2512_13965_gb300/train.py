@@ -15,6 +15,9 @@ decayed along a cosine to --lr-min; everything runs in libgmc.so, the GEMMs
 on tensor cores with BF16 operands and FP32 accumulation and master weights
 (--precision fp32 selects the FP32 SIMT GEMMs). The network
 starts from Kaiming-normal weights drawn by `synth` (seed --init-seed).
+--arch rm trains the residual-modulated network (residual blocks whose
+pre-activations are shifted by the condition and scaled channel-wise by the
+cell's ln tau and c; shifts and scales start at zero) on the FP32 path.
 Prints one JSON line per report interval (loss, samples/s).
 """
 import argparse
@@ -46,9 +49,16 @@ def main(argv=None):
                     help="boundary: cell transmissions from the left face; internal: births "
                          "inside a cell (volumetric source); xy: transmissions in x-y geometry "
                          "(3-D directions projected on the unit disk)")
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"],
-                    help="GEMM operands: bf16 (tensor cores) or fp32 (SIMT)")
+    ap.add_argument("--precision", default=None, choices=["bf16", "fp32"],
+                    help="GEMM operands: bf16 (tensor cores; the MLP's default) or fp32 (SIMT; "
+                         "the only choice for --arch rm)")
+    ap.add_argument("--arch", default="mlp", choices=["mlp", "rm"],
+                    help="mlp: 4 x 256 SiLU MLP; rm: residual-modulated blocks")
     args = ap.parse_args(argv)
+    if args.precision is None:
+        args.precision = "fp32" if args.arch == "rm" else "bf16"
+    if args.arch == "rm" and args.precision != "fp32":
+        ap.error("--arch rm trains at --precision fp32")
 
     import numpy as np
     import torch
@@ -65,7 +75,10 @@ def main(argv=None):
     g.gmc_set_stream(ctx, stream)
     with tempfile.TemporaryDirectory() as d:
         init = os.path.join(d, "init.bin")
-        synth.write_weights(init, synth.kaiming_weights(args.init_seed))
+        w0 = synth.kaiming_weights(args.init_seed)
+        if args.arch == "rm":
+            w0 = synth.rm_weights(args.init_seed, base=w0)
+        synth.write_weights(init, w0)
         g.gmc_load_weights(ctx, init)
     n = args.samples
     with torch.cuda.stream(stream):
