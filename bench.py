@@ -43,6 +43,12 @@ WIDE_BOUNDARY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_bou
 WIDE_INTERNAL = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_internal_wide.bin")
 WIDE_BOX = [0.01, 1000.0, 0.5, 0.999]
 TRAINED_XY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_xy.bin")
+# the architecture comparison: the residual-modulated boundary network and an
+# MLP control, both trained with the FP32 path on the same data and schedule
+ARCH_RM = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_boundary_rm.bin")
+ARCH_MLP = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_boundary_mlp_fp32.bin")
+SAMPLER_FLOP_PER_EVAL = 2 * (4 * 256 + 3 * 256 * 256 + 256 * 4)
+SAMPLER_FLOP_PER_TRANSMISSION = 2 * 5 * 256
 # stated GMC-vs-analog relative L2 flux error at 1e7 histories, per precision
 # of the network (the metric's condition is the BF16 one, 1 %)
 FLUX_ERR_BOUND = {"bf16": 0.01, "fp8": 0.02}
@@ -189,7 +195,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--workload", default="sampler",
                     choices=["sampler", "solve", "hohlraum", "serve", "sweep", "heldout", "sigma",
-                             "walks", "paper", "train"])
+                             "walks", "paper", "train", "arch"])
     ap.add_argument("--weights", default=None,
                     help="GMCW file of the boundary model for the solve, serve, sigma, sweep and "
                          "heldout workloads (default: the package's trained network; 'kaiming': "
@@ -209,6 +215,8 @@ def main():
     ap.add_argument("--hist-range", type=float, nargs=2, default=(1e3, 1e5),
                     help="serve: histories per request, log-uniform in [lo, hi]")
     ap.add_argument("--train-batch", type=int, default=16384, help="train: batch rows per step")
+    ap.add_argument("--sampler-weights", default=None,
+                    help="sampler: time this GMCW network instead of the Kaiming-normal MLP")
     ap.add_argument("--net-box", type=float, nargs=4, default=None,
                     metavar=("TAU_LO", "TAU_HI", "C_LO", "C_HI"),
                     help="solve/paper: the (tau, c) box the networks were trained on (default: "
@@ -234,6 +242,8 @@ def main():
         return run_paper(args)
     if args.workload == "train":
         return run_train(args)
+    if args.workload == "arch":
+        return run_arch(args)
 
     import numpy as np
     import torch
@@ -253,10 +263,17 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     g.gmc_set_stream(ctx, stream)
-    with tempfile.TemporaryDirectory() as d:
-        path = os.path.join(d, "w.bin")
-        synth.write_weights(path, synth.kaiming_weights(1))
-        g.gmc_load_weights(ctx, path)
+    workload = WORKLOAD
+    if args.sampler_weights:
+        # the same workload on another network (e.g. the residual-modulated one)
+        g.gmc_load_weights(ctx, args.sampler_weights)
+        workload = WORKLOAD.replace("25-256x4-4 SiLU velocity MLP, Kaiming-normal seed 1",
+                                    "velocity network " + os.path.relpath(args.sampler_weights, ROOT))
+    else:
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "w.bin")
+            synth.write_weights(path, synth.kaiming_weights(1))
+            g.gmc_load_weights(ctx, path)
     cond_h, _, _ = synth.sampler_conditions(BATCH, 1 + rank)
     cond = torch.from_numpy(cond_h).cuda()
     exit_d = torch.empty(4, BATCH, device="cuda")
@@ -321,8 +338,14 @@ def main():
     if prec == g.GMC_BF16:
         # DRAM read + write bytes of one launch of this kernel (BF16, Euler, 2^20 rows x
         # 16 steps), from ncu dram__bytes_read.sum + dram__bytes_write.sum of the
-        # current kernel (one CTA per SM, no clusters)
-        traffic = 21499904 + 0 if ODE_STEPS == 16 and BATCH == 1 << 20 else None
+        # current kernel (one CTA per SM, no clusters): the Kaiming MLP, and the
+        # committed residual-modulated network
+        traffic = None
+        if ODE_STEPS == 16 and BATCH == 1 << 20:
+            if not args.sampler_weights:
+                traffic = 21499904
+            elif os.path.abspath(args.sampler_weights) == ARCH_RM:
+                traffic = 21508608 + 2048
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16"], "unit": "TFLOP/s",
                 "frac": achieved / pk["bf16"], "traffic": traffic, "traffic_unit": "bytes per launch",
                 "peak_source": pk["src"] + " bf16 burst", "kernel": "sampler_tc_kernel"}
@@ -352,7 +375,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {g.GMC_BF16: "bf16", g.GMC_FP8: "e4m3+bf16", g.GMC_FP32: "f32"}[prec],
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "batch": BATCH, "ode_steps": ODE_STEPS,
+                "config": {"workload": workload, "batch": BATCH, "ode_steps": ODE_STEPS,
                            "integrator": "euler", "precision": args.precision,
                            "l2": "flushed between steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
@@ -788,6 +811,81 @@ def _equivalent_summary(tau, c, box=((0.1, 1000.0), (0.5, 0.999))):
     w = c * tau
     ok = inside | ((w > 0) & (np.maximum(c_lo, w / t_hi) <= np.minimum(c_hi, w / t_lo)))
     return int((ok & ~inside).sum()), int((~ok).sum()), int(inside.sum())
+
+
+def run_arch(args):
+    """The paper's architecture (residual blocks with adaptive modulation)
+    against the MLP at equal flux error: both boundary networks trained with
+    the FP32 path on the same data, batch, steps and schedule; the 128x128
+    solve (tau logU[0.1,500], c {0.5,0.999} per 16x16 block, central 8x8
+    source, the package's internal model for births) at --histories, GMC BF16
+    with midpoint K in {2, 4, 8} and Euler 16, flux error against the walk
+    (two half runs: the reference flux and the statistical floor); then the
+    BF16 sampler kernel of each network on 2^20 transmissions x 16 Euler steps
+    (CUDA events, median of 7 after 3 warm-up launches; algorithmic FLOPs as
+    the sampler workload's) against the measured BF16 peak."""
+    import numpy as np
+    import torch
+    import synth
+    args.weights = args.weights or ARCH_MLP
+    g, ctx = _context(args)
+    stream = torch.cuda.Stream()
+    g.gmc_set_stream(ctx, stream)
+    torch.cuda.set_stream(stream)
+    N = 128
+    tau, c, src = synth.grid_problem(n=N, seed=2)
+    tau, c, src = (np.ascontiguousarray(a.ravel()) for a in (tau, c, src))
+    n_hist = int(args.histories)
+
+    def solve(method, seed, n, integ=0, steps=16):
+        cfg = g.gmc_get_config(ctx)
+        cfg.steps, cfg.integrator, cfg.precision, cfg.gmc_min_tau = steps, integ, g.GMC_BF16, 0.0
+        g.gmc_set_config(ctx, cfg)
+        f = np.zeros(N * N)
+        st = g.transport_solve(ctx, N, N, tau, c, src, n, method, seed, f)
+        return f, st
+
+    half = n_hist // 2
+    f_a, st_a = solve(g.GMC_METHOD_ANALOG, 1, half)
+    f_b, st_b = solve(g.GMC_METHOD_ANALOG, 2, n_hist - half)
+    f_mc = 0.5 * (f_a + f_b)
+    out = {"analog": {"seconds": st_a.seconds + st_b.seconds,
+                      "flux_floor_at_n": _rel(f_a, f_b) / np.sqrt(2.0)}}
+    pk = peaks()
+    n = 1 << 20
+    cond, _, _ = synth.sampler_conditions(n, 3)
+    z = synth.gaussian_noise(n, 4)
+    dc, dz = torch.from_numpy(cond).cuda(), torch.from_numpy(z).cuda()
+    yb = torch.empty(4, n, device="cuda")
+    flop = n * (SAMPLER_FLOP_PER_EVAL * 16 + SAMPLER_FLOP_PER_TRANSMISSION)
+    for arch, path in (("mlp", args.weights), ("rm", ARCH_RM)):
+        g.gmc_load_weights(ctx, path)
+        res = {"weights": os.path.relpath(path, ROOT)}
+        for name, integ, steps in (("midpoint2", g.GMC_MIDPOINT, 2), ("midpoint4", g.GMC_MIDPOINT, 4),
+                                   ("midpoint8", g.GMC_MIDPOINT, 8), ("euler16", g.GMC_EULER, 16)):
+            f, st = solve(g.GMC_METHOD_GMC, 3, n_hist, integ, steps)
+            res[name] = {"seconds": st.seconds, "transmissions_per_s": st.transmissions / st.seconds,
+                         "flux_rel_err_vs_analog": _rel(f, f_mc)}
+        for _ in range(3):
+            g.gmc_transmit(ctx, n, dc, dz, 0, 0, 16, g.GMC_EULER, g.GMC_BF16, yb, None)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(7):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.gmc_transmit(ctx, n, dc, dz, 0, 0, 16, g.GMC_EULER, g.GMC_BF16, yb, None)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        tf = flop / (ms * 1e-3) / 1e12
+        res["sampler_2e20_euler16_bf16"] = {"ms": ms, "transmissions_per_s": n / (ms * 1e-3),
+                                            "tflops": tf, "frac_of_%s_bf16_peak" % pk["src"]: tf / pk["bf16"]}
+        out[arch] = res
+    print(json.dumps({"metric": "flux error and speed of the residual-modulated network vs the MLP",
+                      "workload": "transport solve 128x128, %d histories; sampler 2^20 x 16 Euler" % n_hist,
+                      "results": out}))
+    ctx.close()
 
 
 def run_walks(args):
