@@ -343,7 +343,7 @@ def main():
         traffic = None
         if ODE_STEPS == 16 and BATCH == 1 << 20:
             if not args.sampler_weights:
-                traffic = 21499904
+                traffic = 21712555
             elif os.path.abspath(args.sampler_weights) == ARCH_RM:
                 traffic = 21508608 + 2048
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16"], "unit": "TFLOP/s",
