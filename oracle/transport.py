@@ -167,6 +167,23 @@ def walk_one(tau, c, mode, x, y, ux, uy, seed, pid, event0):
             "ux": out[3], "uy": out[4], "s": out[5], "ncoll": ncoll.value, "event": ev.value}
 
 
+def walk_one_xy(tau, c, mode, x, y, ux, uy, seed, pid, event0):
+    """One random walk in x-y geometry (the cell is the cross-section of an
+    infinite prism, directions are 3-D and scatter isotropically on the
+    sphere) from an arbitrary point; (ux, uy) is the direction's projection
+    on the plane, s the 3-D track length. Same outputs as walk_one."""
+    status = ctypes.c_int32()
+    face = ctypes.c_int32()
+    ncoll = ctypes.c_int64()
+    ev = ctypes.c_uint32()
+    out = np.zeros(6, dtype=np.float64)
+    lib().orc_walk_one_xy(float(tau), float(c), mode, float(x), float(y), float(ux), float(uy),
+                          seed, int(pid), int(event0), ctypes.byref(status), ctypes.byref(face),
+                          out.ctypes.data, ctypes.byref(ncoll), ctypes.byref(ev))
+    return {"status": status.value, "face": face.value, "q": out[0], "x": out[1], "y": out[2],
+            "ux": out[3], "uy": out[4], "s": out[5], "ncoll": ncoll.value, "event": ev.value}
+
+
 def solve_analog(tau, c, src, n_hist, seed, w_cut=1e-4, p_survive=0.1):
     """Standard MC solve; tau, c, src are [ny, nx]. Returns (flux [ny, nx], stats dict)."""
     tau, c, src = (_c(a, np.float64) for a in (tau, c, src))
@@ -209,6 +226,18 @@ def mlp_sampler(net, steps, integrator, seed):
         cond = np.stack([xi, cos_c, sin_c, np.log(tau), c])
         z = rng.normals_for(seed, ids, events, rng.TAG_NOISE)
         d = mlp.decode(net, mlp.sample(net, cond, z, steps, integrator))
+        return d["face"], d["q"], d["ux"], d["uy"], d["s"], np.asarray(events, np.uint32) + 1
+    return f
+
+
+def mlp_sampler_xy(net, steps, integrator, seed):
+    """Stage 2 in x-y geometry with the x-y boundary network: the condition
+    holds the projected entry direction, exits are decoded into the unit
+    disk (decode_disk)."""
+    def f(xi, ux_c, uy_c, tau, c, ids, events, rot=None):
+        cond = np.stack([xi, ux_c, uy_c, np.log(tau), c])
+        z = rng.normals_for(seed, ids, events, rng.TAG_NOISE)
+        d = mlp.decode_disk(net, mlp.sample(net, cond, z, steps, integrator))
         return d["face"], d["q"], d["ux"], d["uy"], d["s"], np.asarray(events, np.uint32) + 1
     return f
 
@@ -370,6 +399,30 @@ def walk_sampler_global(seed):
     return f
 
 
+def walk_sampler_global_xy(seed):
+    """walk_sampler_global in x-y geometry (walk_one_xy): the random walk a
+    random-walk x-y solve takes through a cell, in the cell's own frame."""
+    def f(xi, ux_c, uy_c, tau, c, ids, events, rot=None):
+        n = len(ids)
+        face = np.zeros(n, np.int64)
+        out = [np.zeros(n) for _ in range(4)]
+        ev = np.zeros(n, np.uint32)
+        for k in range(n):
+            r = int(rot[k])
+            F = (r - 1) % 4
+            x = float(xi[k])
+            X, Y = {0: (1.0 - x, 0.0), 1: (1.0, 1.0 - x), 2: (x, 1.0), 3: (0.0, x)}[F]
+            gx, gy = rot_dir(ux_c[k], uy_c[k], r)
+            w = walk_one_xy(tau[k], c[k], MODE_IMPLICIT, X * tau[k], Y * tau[k], gx, gy, seed,
+                            int(ids[k]), int(events[k]))
+            face[k] = (w["face"] - r) % 4
+            ux, uy = rot_dir(w["ux"], w["uy"], -r)
+            out[0][k], out[1][k], out[2][k], out[3][k] = w["q"], ux, uy, w["s"]
+            ev[k] = w["event"]
+        return face, out[0], out[1], out[2], out[3], ev
+    return f
+
+
 def rot_dir(ux, uy, k):
     """Scalar form of rot."""
     rx, ry = rot(np.array([ux]), np.array([uy]), k)
@@ -392,8 +445,36 @@ def wall_births(wall, n_hist, seed):
     return j, ub[1], np.sqrt(np.maximum(1.0 - sn * sn, 0.0)), sn
 
 
+def wall_births_xy(wall, n_hist, seed):
+    """wall_births in x-y geometry: row j and entry point from u0, u1 as
+    there; the 3-D cosine law for the direction, cosine to the inward normal
+    mu = sqrt(u2) and azimuth about it 2 pi u3, so the projected entry
+    direction is (mu, sqrt(1 - mu^2) cos(2 pi u3))."""
+    cdf = np.cumsum(np.maximum(np.asarray(wall, dtype=np.float64), 0.0))
+    ids = np.arange(n_hist, dtype=np.uint64)
+    ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
+    j = np.searchsorted(cdf, ub[0] * cdf[-1], side="left")
+    mu = np.sqrt(ub[2])
+    return j, ub[1], mu, np.sqrt(np.maximum(1.0 - mu * mu, 0.0)) * np.cos(2.0 * np.pi * ub[3])
+
+
+def birth_directions(seed, ids, u_angle, geometry):
+    """Direction of a volumetric birth (isotropic): on the circle at angle
+    2 pi u_angle (flat), or on the sphere (xy) with that azimuth and polar
+    cosine 2 u - 1, u the first uniform of the draw (id, 1, TAG_BIRTH),
+    projected on the plane."""
+    ang = 2.0 * np.pi * np.asarray(u_angle, np.float64)
+    if geometry == "flat":
+        return np.cos(ang), np.sin(ang)
+    ids = np.asarray(ids, np.uint64)
+    u = rng.uniforms_for(seed, ids, np.ones(ids.size, np.uint32), rng.TAG_BIRTH)[0]
+    mu = 2.0 * u - 1.0
+    r = np.sqrt(np.maximum(1.0 - mu * mu, 0.0))
+    return r * np.cos(ang), r * np.sin(ang)
+
+
 def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max_waves=100000,
-              internal=None, wall=None):
+              internal=None, wall=None, geometry="flat"):
     """Event-based GMC solve; tau, c, src are [ny, nx]. Returns (flux, stats).
 
     internal: sampler of births (mlp_internal_sampler / walk_internal_sampler),
@@ -401,7 +482,18 @@ def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max
     wall: [ny] strengths of a surface source on the left boundary instead of
     the volumetric source src (see wall_births); each history enters its
     boundary cell through the west face with weight 1 and next event 0.
+    geometry: "flat" (directions on the circle) or "xy" (x-y geometry: every
+    cell is the cross-section of an infinite prism, directions are 3-D and
+    carried as their projection on the plane; births on the sphere
+    (birth_directions), wall entries with the 3-D cosine law
+    (wall_births_xy), walks by walk_one_xy; `sampler` must be an x-y one,
+    mlp_sampler_xy or walk_sampler_global_xy; no internal model).
     """
+    if geometry not in ("flat", "xy"):
+        raise ValueError(geometry)
+    if geometry == "xy" and internal is not None:
+        raise ValueError("x-y solves walk their births")
+    walker = walk_one if geometry == "flat" else walk_one_xy
     tau = np.asarray(tau, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)
     ny, nx = tau.shape
@@ -410,7 +502,7 @@ def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max
     st = np.zeros(6, dtype=np.float64)
     live = {k: [] for k in ("id", "i", "j", "F", "xi", "gx", "gy", "w", "ev")}
     if wall is not None:
-        j, xi, gx, gy = wall_births(wall, n_hist, seed)
+        j, xi, gx, gy = (wall_births if geometry == "flat" else wall_births_xy)(wall, n_hist, seed)
         for h in range(n_hist):
             for k, v in (("id", h), ("i", 0), ("j", int(j[h])), ("F", 3), ("xi", xi[h]),
                          ("gx", gx[h]), ("gy", gy[h]), ("w", 1.0), ("ev", 0)):
@@ -424,6 +516,7 @@ def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max
         ids = np.arange(n_hist, dtype=np.uint64)
         ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
         cells = np.searchsorted(cdf, ub[0] * total, side="left")
+        bux, buy = birth_directions(seed, ids, ub[3], geometry)
 
     # Births: walk from the birth point to the first face crossing (cell frame),
     # or sample that exit with the internal model.
@@ -446,9 +539,7 @@ def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max
         k = int(cells[h])
         i, j = k % nx, k // nx
         t, cc = tf[k], cf[k]
-        ang = 2.0 * np.pi * ub[3, h]
-        r = walk_one(t, cc, MODE_IMPLICIT, ub[1, h] * t, ub[2, h] * t, np.cos(ang), np.sin(ang),
-                     seed, h, 0)
+        r = walker(t, cc, MODE_IMPLICIT, ub[1, h] * t, ub[2, h] * t, bux[h], buy[h], seed, h, 0)
         st[3] += 1
         st[4] += r["ncoll"]
         dw, score = deposit(1.0, r["s"], t, cc)

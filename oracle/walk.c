@@ -138,6 +138,32 @@ void orc_walk_one(double tau, double c, int mode, double x, double y, double ux,
     *event = r.event;
 }
 
+/* Single walk in x-y geometry (a square cell of side tau, directions on the
+   sphere) from an arbitrary point, for the Python event-loop oracle: (ux, uy)
+   is the direction's projection on the plane and |uz| = sqrt(1 - ux^2 - uy^2)
+   (the sign of uz does not enter a walk in the plane). Outputs as
+   orc_walk_one. */
+void orc_walk_one_xy(double tau, double c, int mode, double x, double y, double ux, double uy,
+                     uint64_t seed, uint64_t id, uint32_t event0, int32_t *status, int32_t *face,
+                     double *out /* q, x, y, ux, uy, s */, int64_t *ncoll, uint32_t *event)
+{
+    orc_walk_result r;
+    double uz_out;
+    const double r2 = ux * ux + uy * uy;
+    const double uz = r2 < 1.0 ? sqrt(1.0 - r2) : 0.0;
+    orc_walk_xy(tau, tau, c, mode, 1, x, y, ux, uy, uz, seed, id, event0, &r, &uz_out);
+    *status = r.status;
+    *face = r.face;
+    out[0] = r.q;
+    out[1] = r.x;
+    out[2] = r.y;
+    out[3] = r.ux;
+    out[4] = r.uy;
+    out[5] = r.s;
+    *ncoll = r.ncoll;
+    *event = r.event;
+}
+
 /*
  * Canonical-frame transmission with per-particle Philox ids and first
  * events; event_out[i] receives the next unused event counter.

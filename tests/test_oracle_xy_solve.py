@@ -1,0 +1,201 @@
+"""Pins for the oracle's x-y geometry transport solve (the geometry variant of
+section "Network Architecture and Inputs": every cell the cross-section of an
+infinite prism, 3-D directions carried as their projection on the unit disk).
+
+* One pure-absorber cell (c = 0: straight 3-D chords, Eq. 6-7 scores) with a
+  surface source on the left face (3-D cosine law) and with a uniform
+  isotropic volumetric source: flux and leakage against quadrature of the
+  chord over entry point and direction.
+* A small heterogeneous grid with scattering: the cell-by-cell event loop
+  (walk_sampler_global_xy, births walked) against an independent walker
+  written here, which follows each history through the whole grid in global
+  coordinates (surface tracking across cells, implicit capture, the same
+  track-length estimator), compared cell by cell on independent seeds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import rng
+from oracle import transport as OT
+
+
+def _chord(x, y, ux, uy, tau):
+    """3-D length from (x, y) in [0, tau]^2 along a direction with projection
+    (ux, uy) to the prism wall."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        lx = np.where(ux > 0, (tau - x) / ux, np.where(ux < 0, -x / ux, np.inf))
+        ly = np.where(uy > 0, (tau - y) / uy, np.where(uy < 0, -y / uy, np.inf))
+    return np.minimum(lx, ly)
+
+
+def _midpoints(n, lo=0.0, hi=1.0):
+    return lo + (np.arange(n) + 0.5) * (hi - lo) / n
+
+
+@pytest.mark.parametrize("tau", [0.4, 1.7])
+def test_xy_wall_source_pure_absorber_quadrature(tau):
+    # entry at y = xi tau on the left face; mu = cos to the normal with
+    # density 2 mu, azimuth phi uniform: projection (mu, sqrt(1-mu^2) cos phi);
+    # score (1 - e^-l) / tau, leakage e^-l
+    xi = _midpoints(160)
+    m2 = _midpoints(160)          # mu^2 uniform (the cosine law)
+    phi = _midpoints(160, 0.0, 2.0 * np.pi)
+    X, M2, P = np.meshgrid(xi, m2, phi, indexing="ij")
+    mu = np.sqrt(M2)
+    l = _chord(np.zeros_like(X), X * tau, mu, np.sqrt(1.0 - M2) * np.cos(P), tau)
+    f_q = np.mean((1.0 - np.exp(-l)) / tau)
+    f2_q = np.mean(((1.0 - np.exp(-l)) / tau) ** 2)
+    leak_q = np.mean(np.exp(-l))
+    n = 40_000
+    f, st = OT.solve_gmc(np.full((1, 1), tau), np.zeros((1, 1)), None, n, 5,
+                         OT.walk_sampler_global_xy(5), wall=np.ones(1), geometry="xy", w_cut=0.0)
+    sd = math.sqrt((f2_q - f_q * f_q) / n)
+    assert abs(f[0, 0] - f_q) < 4 * sd + 1e-4 * f_q, (f[0, 0], f_q, sd)
+    assert abs(st["leak"] / n - leak_q) < 4 * math.sqrt(leak_q * (1 - leak_q) / n) + 1e-4
+    assert abs(st["leak"] + st["absorbed"] - n) < 1e-6 * n
+
+
+@pytest.mark.parametrize("tau", [0.6, 2.5])
+def test_xy_volumetric_source_pure_absorber_quadrature(tau):
+    # uniform birth point, isotropic direction on the sphere: polar cosine u
+    # uniform in [-1, 1] (by symmetry [0, 1]), azimuth uniform
+    xs = _midpoints(48)
+    mus = _midpoints(48)
+    phis = _midpoints(96, 0.0, 2.0 * np.pi)
+    acc = acc2 = leak = 0.0
+    for x in xs:
+        Y, MU, P = np.meshgrid(xs, mus, phis, indexing="ij")
+        r = np.sqrt(1.0 - MU * MU)
+        l = _chord(np.full_like(Y, x * tau), Y * tau, r * np.cos(P), r * np.sin(P), tau)
+        sc = (1.0 - np.exp(-l)) / tau
+        acc += sc.mean()
+        acc2 += (sc * sc).mean()
+        leak += np.exp(-l).mean()
+    f_q, f2_q, leak_q = acc / xs.size, acc2 / xs.size, leak / xs.size
+    n = 100_000
+    f, st = OT.solve_gmc(np.full((1, 1), tau), np.zeros((1, 1)), np.ones((1, 1)), n, 7,
+                         OT.walk_sampler_global_xy(7), geometry="xy", w_cut=0.0)
+    sd = math.sqrt((f2_q - f_q * f_q) / n)
+    assert abs(f[0, 0] - f_q) < 4 * sd + 2e-4 * f_q, (f[0, 0], f_q, sd)
+    assert abs(st["leak"] / n - leak_q) < 4 * math.sqrt(leak_q * (1 - leak_q) / n) + 2e-4
+
+
+def test_xy_births_follow_the_sphere():
+    # projected birth directions: |u|^2 = 1 - mu^2 with mu uniform in [-1, 1]
+    # (so E|u|^2 = 2/3), azimuth from the first draw's fourth uniform
+    ids = np.arange(50_000, dtype=np.uint64)
+    ub = rng.uniforms_for(3, ids, np.zeros(ids.size, np.uint32), rng.TAG_BIRTH)
+    ux, uy = OT.birth_directions(3, ids, ub[3], "xy")
+    r2 = ux * ux + uy * uy
+    assert abs(r2.mean() - 2.0 / 3.0) < 4 * math.sqrt(4.0 / 45.0 / ids.size)
+    np.testing.assert_allclose(np.arctan2(uy, ux) % (2 * np.pi), 2 * np.pi * ub[3], atol=1e-9)
+    fx, fy = OT.birth_directions(3, ids, ub[3], "flat")
+    np.testing.assert_allclose(fx * fx + fy * fy, 1.0, atol=1e-12)
+
+
+def _global_walk_xy(tau, c, src, n, seed):
+    """Independent x-y walker: each history from its birth through the whole
+    grid in global optical coordinates, flights sampled in scattering optical
+    depth across cells (surface tracking), implicit capture with the
+    track-length score of every segment, vacuum boundaries, no roulette. Its
+    own random numbers (numpy Philox): equal to the oracle in distribution,
+    not history by history."""
+    g = np.random.Generator(np.random.Philox(key=seed))
+    ny, nx = tau.shape
+    flux = np.zeros((ny, nx))
+    cdf = np.cumsum(src.ravel())
+    for _ in range(n):
+        k = int(np.searchsorted(cdf, g.random() * cdf[-1], side="left"))
+        i, j = k % nx, k // nx
+        px, py = i + g.random(), j + g.random()   # position in cell units
+        mu = 2.0 * g.random() - 1.0
+        ph = 2.0 * np.pi * g.random()
+        r = math.sqrt(max(1.0 - mu * mu, 0.0))
+        ux, uy = r * math.cos(ph), r * math.sin(ph)
+        w = 1.0
+        while True:
+            left = -math.log(1.0 - g.random())       # scattering optical depth to the next collision
+            scattered = False
+            while True:
+                ci, cj = int(math.floor(px)), int(math.floor(py))
+                t, cc = tau[cj, ci], c[cj, ci]
+                # 3-D length (in cell units) to the cell's wall
+                lx = ((ci + 1 - px) / ux if ux > 0 else ((ci - px) / ux if ux < 0 else math.inf))
+                ly = ((cj + 1 - py) / uy if uy > 0 else ((cj - py) / uy if uy < 0 else math.inf))
+                lw = min(lx, ly)
+                ls = left / (cc * t) if cc > 0 else math.inf   # cell units to the collision
+                seg = min(lw, ls)
+                s_opt = seg * t
+                a = 1.0 - cc
+                dw = w * (-math.expm1(-a * s_opt))
+                flux[cj, ci] += dw / (a * t) if a > 0 else w * s_opt / t
+                w -= dw
+                if ls < lw:
+                    px += seg * ux
+                    py += seg * uy
+                    scattered = True
+                    break
+                left -= seg * cc * t
+                px += seg * ux
+                py += seg * uy
+                # step across the wall just reached (just inside the neighbour)
+                if lx <= ly:
+                    ni = ci + (1 if ux > 0 else -1)
+                    if not 0 <= ni < nx:
+                        break
+                    px = float(ni) if ux > 0 else float(ci) - 1e-12
+                else:
+                    nj = cj + (1 if uy > 0 else -1)
+                    if not 0 <= nj < ny:
+                        break
+                    py = float(nj) if uy > 0 else float(cj) - 1e-12
+            if not scattered:
+                break
+            mu = 2.0 * g.random() - 1.0
+            ph = 2.0 * np.pi * g.random()
+            r = math.sqrt(max(1.0 - mu * mu, 0.0))
+            ux, uy = r * math.cos(ph), r * math.sin(ph)
+    return flux / n
+
+
+def test_xy_event_loop_matches_a_global_walker():
+    tau = np.array([[0.7, 2.0, 0.4], [1.5, 0.3, 1.1], [0.9, 2.6, 0.5]])
+    c = np.array([[0.9, 0.6, 0.99], [0.5, 0.95, 0.8], [0.7, 0.9, 0.6]])
+    src = np.zeros((3, 3))
+    src[1, 1] = 1.0
+    src[0, 0] = 0.5
+    K, n = 6, 3000
+    a = [OT.solve_gmc(tau, c, src, n, 100 + k, OT.walk_sampler_global_xy(100 + k), geometry="xy",
+                      w_cut=0.0)[0] for k in range(K)]
+    b = [_global_walk_xy(tau, c, src, n, 200 + k) for k in range(K)]
+    A = np.asarray(a).reshape(K, -1)
+    B = np.asarray(b).reshape(K, -1)
+    se = np.sqrt(A.var(0, ddof=1) / K + B.var(0, ddof=1) / K)
+    z = np.abs(A.mean(0) - B.mean(0)) / se
+    assert z.max() < 4.5, (z, A.mean(0), B.mean(0))
+    # flat and x-y geometry differ: the same event loop with 2-D directions
+    # puts measurably more flux in the far cells (longer in-plane flights)
+    f = np.mean([OT.solve_gmc(tau, c, src, n, 300 + k, OT.walk_sampler_global(300 + k),
+                              w_cut=0.0)[0] for k in range(K)], axis=0)
+    assert np.abs(f.ravel() - A.mean(0)).max() > 4 * se.max()
+
+
+def test_xy_solve_with_a_network_runs_and_balances(tmp_path):
+    # the x-y network sampler in the event loop: finite flux, weight balance
+    from oracle import mlp
+    p = str(tmp_path / "k.bin")
+    synth.write_weights(p, synth.kaiming_weights(1))
+    net = mlp.read_weights(p)
+    tau = np.array([[1.0, 3.0], [0.5, 2.0]])
+    c = np.array([[0.9, 0.7], [0.99, 0.5]])
+    src = np.array([[1.0, 0.0], [0.0, 0.0]])
+    f, st = OT.solve_gmc(tau, c, src, 400, 11, OT.mlp_sampler_xy(net, 4, "euler", 11),
+                         geometry="xy")
+    assert np.all(np.isfinite(f)) and f.sum() > 0
+    assert abs(st["leak"] + st["absorbed"] - st["roulette_net"] - 400) < 1e-6 * 400
+    with pytest.raises(ValueError):
+        OT.solve_gmc(tau, c, src, 10, 1, OT.mlp_sampler_xy(net, 4, "euler", 1), geometry="xy",
+                     internal=OT.walk_internal_sampler(1))
