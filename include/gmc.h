@@ -385,6 +385,28 @@ gmc_status transport_solve_wall(gmc_ctx *ctx, int nx, int ny, const float *tau, 
                                 const float *wall, int64_t n_histories, int method, uint64_t seed,
                                 double *flux, gmc_solve_stats *stats);
 
+/*
+ * The two solves in x-y geometry (the geometry variant of section "Network
+ * Architecture and Inputs": every cell is the cross-section of an infinite
+ * prism, directions are 3-D and enter the networks by their projection on
+ * the unit disk): a flight of 3-D length d moves the particle by d (ux, uy)
+ * in the plane, the track length s of Eq. 5-7 is the 3-D one, and the walk
+ * scatters isotropically on the sphere (azimuth 2 pi u2, polar cosine
+ * 2 u3 - 1 of the flight's draw). Volumetric births take the azimuth of
+ * transport_solve and the polar cosine 2 u - 1 from the first uniform of the
+ * draw (h, 1, tag 4); wall entries take the 3-D cosine law, cosine to the
+ * inward normal sqrt(u2) and azimuth about it 2 pi u3. GMC_METHOD_GMC samples
+ * cell crossings with the x-y boundary network (gmc_load_xy_weights;
+ * GMC_ENOWEIGHTS without it) and walks every birth. Other arguments, the
+ * result and blocking as for transport_solve and transport_solve_wall.
+ */
+gmc_status transport_solve_xy(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                              const float *source, int64_t n_histories, int method, uint64_t seed,
+                              double *flux, gmc_solve_stats *stats);
+gmc_status transport_solve_wall_xy(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                                   const float *wall, int64_t n_histories, int method,
+                                   uint64_t seed, double *flux, gmc_solve_stats *stats);
+
 /* ---- serving: continuous batching of transport solves ---------------------- */
 
 /* One transport solve (arguments of transport_solve; arrays are host memory

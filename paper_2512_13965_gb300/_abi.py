@@ -99,6 +99,10 @@ def _load():
                             ctypes.POINTER(gmc_solve_stats)],
         "transport_solve_wall": [P, i32, i32, P, P, P, i64, i32, u64, P,
                                  ctypes.POINTER(gmc_solve_stats)],
+        "transport_solve_xy": [P, i32, i32, P, P, P, i64, i32, u64, P,
+                               ctypes.POINTER(gmc_solve_stats)],
+        "transport_solve_wall_xy": [P, i32, i32, P, P, P, i64, i32, u64, P,
+                                    ctypes.POINTER(gmc_solve_stats)],
         "gmc_serve_start": [P, ctypes.POINTER(gmc_serve_config)],
         "gmc_submit": [P, ctypes.POINTER(gmc_solve_req), ctypes.POINTER(ctypes.c_uint64)],
         "gmc_poll": [P, u64, P, ctypes.POINTER(gmc_solve_stats)],
@@ -359,6 +363,25 @@ def transport_solve_wall(ctx, nx, ny, tau, c, wall, n_histories, method, seed, f
     ctx.check(lib.transport_solve_wall(ctx.handle, nx, ny, *_grid(m, tau, c),
                                        _arr(wall, 4, max(ny, 0), "wall"), n_histories, method,
                                        seed, _arr(flux, 8, m, "flux"), ctypes.byref(st)))
+    return st
+
+
+def transport_solve_xy(ctx, nx, ny, tau, c, source, n_histories, method, seed, flux, stats=None):
+    st = stats if stats is not None else gmc_solve_stats()
+    m = max(nx, 0) * max(ny, 0)
+    ctx.check(lib.transport_solve_xy(ctx.handle, nx, ny, *_grid(m, tau, c),
+                                     _arr(source, 4, m, "source"), n_histories, method, seed,
+                                     _arr(flux, 8, m, "flux"), ctypes.byref(st)))
+    return st
+
+
+def transport_solve_wall_xy(ctx, nx, ny, tau, c, wall, n_histories, method, seed, flux,
+                            stats=None):
+    st = stats if stats is not None else gmc_solve_stats()
+    m = max(nx, 0) * max(ny, 0)
+    ctx.check(lib.transport_solve_wall_xy(ctx.handle, nx, ny, *_grid(m, tau, c),
+                                          _arr(wall, 4, max(ny, 0), "wall"), n_histories, method,
+                                          seed, _arr(flux, 8, m, "flux"), ctypes.byref(st)))
     return st
 
 

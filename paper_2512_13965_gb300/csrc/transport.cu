@@ -97,6 +97,9 @@ struct Slot {
   // (no equivalent condition, or thinner than gmc_min_tau)
   const float *ltau_n, *c_n, *s_scale;
   const uint8_t *walk;
+  // x-y geometry: every cell the cross-section of an infinite prism,
+  // directions 3-D (carried as their projection on the plane)
+  int xy;
 };
 
 struct Rules {
@@ -362,6 +365,24 @@ __device__ void append_inside(bool keep, int slot, uint64_t hist, int cell, cons
   }
 }
 
+// Direction of a volumetric birth: isotropic on the circle (angle 2 pi u3 of
+// the birth draw) or, in x-y geometry, on the sphere with that azimuth and
+// polar cosine 2 u - 1, u the first uniform of the draw (h, 1, tag 4),
+// projected on the plane.
+__device__ __forceinline__ void birth_direction(const Slot &S, uint64_t h, const uint4 &r,
+                                                float &ux, float &uy) {
+  if (S.xy) {
+    float sp, cp;
+    sincospif(2.0f * u01(r.w), &sp, &cp);
+    const float mu = 2.0f * u01(philox_draw(S.seed, h, 1u, kTagBirth).x) - 1.0f;
+    const float rr = sqrtf(fmaxf(1.0f - mu * mu, 0.0f));
+    ux = rr * cp;
+    uy = rr * sp;
+  } else {
+    sincospif(2.0f * u01(r.w), &uy, &ux);
+  }
+}
+
 __device__ __forceinline__ int64_t cdf_search(const double *cdf, int64_t n, double target) {
   int64_t lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -389,7 +410,7 @@ __global__ void birth_kernel(int slot, int64_t first, int64_t count, const doubl
     const double u0 = ((double)r.x + 1.0) * (1.0 / 4294967296.0);
     cell = (int)cdf_search(cdf, (int64_t)S.nx * S.ny, u0 * total);
     float ux, uy;
-    sincospif(2.0f * u01(r.w), &uy, &ux);
+    birth_direction(S, h, r, ux, uy);
     ws = walk_start(S.tau[cell], u01(r.y), u01(r.z), ux, uy, 0u);
   }
   append_inside(keep, slot, h, cell, ws, 1.0f, out, in_count, slot_live);
@@ -401,6 +422,9 @@ __global__ void birth_kernel(int slot, int64_t first, int64_t count, const doubl
 // the west face of cell (0, j) at canonical position xi = u1, with the cosine
 // law for its direction, sin theta = 2 u2 - 1 (an isotropic radiance seen
 // through the boundary), and joins the face bank at base + k with weight 1.
+// In x-y geometry the cosine law is the 3-D one: cosine to the inward normal
+// mu = sqrt(u2), azimuth about it 2 pi u3, projection (mu, sqrt(1 - mu^2)
+// cos(2 pi u3)).
 __global__ void birth_wall_kernel(int slot, int64_t first, int64_t count,
                                   const double *__restrict__ cdf, double total,
                                   const Slot *__restrict__ slots, Route rt, int *slot_live) {
@@ -409,7 +433,7 @@ __global__ void birth_wall_kernel(int slot, int64_t first, int64_t count,
   const Slot S = slots[slot];
   uint64_t h = 0;
   int cell = 0;
-  float xi = 0.0f, sn = 0.0f;
+  float xi = 0.0f, gx = 0.0f, gy = 0.0f;
   bool thin = false;
   if (valid) {
     h = (uint64_t)(first + k);
@@ -418,7 +442,14 @@ __global__ void birth_wall_kernel(int slot, int64_t first, int64_t count,
     const int j = (int)cdf_search(cdf, (int64_t)S.ny, u0 * total);
     cell = j * S.nx;
     xi = u01(r.y);
-    sn = 2.0f * u01(r.z) - 1.0f;
+    if (S.xy) {
+      gx = sqrtf(u01(r.z));
+      gy = sqrtf(fmaxf(1.0f - gx * gx, 0.0f)) * cospif(2.0f * u01(r.w));
+    } else {
+      const float sn = 2.0f * u01(r.z) - 1.0f;
+      gx = sqrtf(fmaxf(1.0f - sn * sn, 0.0f));
+      gy = sn;
+    }
     thin = rt.gmc && S.walk[cell] != 0;  // a cell the random walk crosses
   }
   const int lane = threadIdx.x & 31;
@@ -439,8 +470,8 @@ __global__ void birth_wall_kernel(int slot, int64_t first, int64_t count,
   out.cell[o] = cell;
   out.face[o] = 3;
   out.xi[o] = xi;
-  out.gx[o] = sqrtf(fmaxf(1.0f - sn * sn, 0.0f));
-  out.gy[o] = sn;
+  out.gx[o] = gx;
+  out.gy[o] = gy;
   out.w[o] = 1.0f;
   out.ev[o] = 0u;
 }
@@ -487,6 +518,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_wave_kernel(
   uint64_t h = 0, seed = 0;
   float w = 0.0f, tau = 0.0f, cc = 0.0f;
   uint32_t budget = 0;
+  bool sph = false;
   for (;;) {
     const bool need = k == live && !drained;
     if (__any_sync(0xffffffffu, need)) {
@@ -509,6 +541,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_wave_kernel(
           tau = S.tau[cell];
           cc = S.c[cell];
           seed = S.seed;
+          sph = S.xy != 0;
           budget = cap;
           if constexpr (FROM_FACE) {
             // point on face F with counter-clockwise parameter 1 - xi
@@ -540,7 +573,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_wave_kernel(
     WalkResult wr;
     if (k < live) {
       const uint32_t r = budget < kWalkRound ? budget : kWalkRound;
-      wr = walk_cell_resume(tau, cc, 1, ws, r, seed, h);
+      wr = walk_cell_resume(tau, cc, 1, ws, r, seed, h, sph);
       budget -= r;
       ended = wr.status != kTruncated || budget == 0 || ws.ncoll >= kMaxFlights;
     }
@@ -600,7 +633,7 @@ __global__ void birth_gmc_kernel(int slot, int64_t first, int64_t count, int64_t
     noise[3 * M + row] = z.w;
     if (walk) {
       float ux, uy;
-      sincospif(2.0f * u01(r.w), &uy, &ux);
+      birth_direction(S, h, r, ux, uy);
       ws = walk_start(tau, X, Y, ux, uy, 0u);
     }
   }
@@ -744,6 +777,7 @@ struct Request {
   uint64_t seed = 0;
   int method = GMC_METHOD_ANALOG;
   bool wall = false;  // source on the left boundary (cdf over the ny rows)
+  bool xy = false;    // x-y geometry (transport_solve_xy, transport_solve_wall_xy)
   // engine state
   int slot = -1;
   int64_t next_hist = 0;
@@ -797,7 +831,7 @@ bool equivalent_condition(double tau, double c, double t_lo, double t_hi, double
 // instead of ny*nx volumetric strengths.
 gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
                         const float *source, int64_t n_histories, int method, uint64_t seed,
-                        Request &R, bool wall = false) {
+                        Request &R, bool wall = false, bool xy = false) {
   if (nx < 1 || ny < 1 || (int64_t)nx * ny > (1 << 26))
     return set_error(ctx, GMC_EINVAL, "solve: grid must be 1..2^26 cells");
   if (!tau || !c || !source) return set_error(ctx, GMC_EINVAL, "solve: null array");
@@ -845,10 +879,18 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
     R.walk[k] = (!ok || (cf.gmc_min_tau > 0.0 && (double)tau[k] < cf.gmc_min_tau)) ? 1 : 0;
   }
   R.wall = wall;
+  R.xy = xy;
   if (n_histories > 0 && !(acc > 0.0)) return set_error(ctx, GMC_EINVAL, "solve: zero source");
-  if (method == GMC_METHOD_GMC && !ctx->net.loaded)
+  if (xy && method == GMC_METHOD_GMC) {
+    // the x-y boundary network; births are walked (no x-y internal model)
+    if (!ctx->xy.loaded)
+      return set_error(ctx, GMC_ENOWEIGHTS, "x-y solve: GMC needs gmc_load_xy_weights");
+    if (check_net_path(ctx, ctx->xy, ctx->cfg.precision, ctx->cfg.sampler_kernel, "x-y solve") != GMC_OK)
+      return GMC_EINVAL;
+  } else if (method == GMC_METHOD_GMC && !ctx->net.loaded) {
     return set_error(ctx, GMC_ENOWEIGHTS, "solve: GMC needs gmc_load_weights");
-  if (method == GMC_METHOD_GMC) {
+  }
+  if (method == GMC_METHOD_GMC && !xy) {
     const gmc_config &cf = ctx->cfg;
     if (check_net_path(ctx, ctx->net, cf.precision, cf.sampler_kernel, "solve") != GMC_OK ||
         (ctx->internal.loaded &&
@@ -968,9 +1010,12 @@ class Engine {
   int active() const { return active_; }
 
   // Admits R if a slot and its pool footprint are free; false otherwise.
+  // The requests in the engine at one time share a geometry (their face
+  // particles go through one network).
   bool try_admit(Request *R, gmc_status *err) {
     *err = GMC_OK;
     if (active_ >= kMaxSlots) return false;
+    if (active_ > 0 && R->xy != xy_) return false;
     size_t off;
     if (!pool_.alloc(R->footprint, &off)) return false;
     int slot = -1;
@@ -992,7 +1037,7 @@ class Engine {
     R->d_flux = (double *)(p + 5 * a4 + a8);
     R->d_walk = (uint8_t *)(p + 5 * a4 + 2 * a8);
     Slot S{R->nx, R->ny, R->d_tau, R->d_c, R->d_flux, R->seed,
-           R->d_ltau_n, R->d_c_n, R->d_s_scale, R->d_walk};
+           R->d_ltau_n, R->d_c_n, R->d_s_scale, R->d_walk, R->xy ? 1 : 0};
     cudaError_t e = cudaMemcpyAsync(R->d_tau, R->tau.data(), n * 4, cudaMemcpyHostToDevice, s_);
     if (!e) e = cudaMemcpyAsync(R->d_c, R->c.data(), n * 4, cudaMemcpyHostToDevice, s_);
     if (!e) e = cudaMemcpyAsync(R->d_ltau_n, R->ltau_n.data(), n * 4, cudaMemcpyHostToDevice, s_);
@@ -1017,6 +1062,7 @@ class Engine {
     R->wave0 = waves_;
     reqs_[slot] = R;
     ++active_;
+    xy_ = R->xy;
     return true;
   }
 
@@ -1058,7 +1104,7 @@ class Engine {
       for (auto *R : reqs_)
         if (R) R->live += h_counts_[3 + R->slot];
     }
-    if (pending > 0 && room > 0 && method_ == GMC_METHOD_GMC && ctx_->internal.loaded) {
+    if (pending > 0 && room > 0 && method_ == GMC_METHOD_GMC && ctx_->internal.loaded && !xy_) {
       const gmc_status sb = births_internal(pending, room, rules);
       if (sb != GMC_OK) return sb;
     } else if (pending > 0 && room > 0) {
@@ -1111,7 +1157,7 @@ class Engine {
         gmc_prep_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_slots_, d_cond_,
                                                              d_noise_);
         GMC_CUDA_TRY(ctx_, cudaGetLastError());
-        gmc_status es = sample(ctx_->net, live_);
+        gmc_status es = sample(xy_ ? ctx_->xy : ctx_->net, live_);
         if (es != GMC_OK) return es;
         gmc_post_kernel<<<nblocks(live_, 256), 256, 0, s_>>>(live_, bank_[cur_], d_exit_, d_slots_,
                                                              rules, route, d_stats_, d_slot_live);
@@ -1307,6 +1353,7 @@ class Engine {
   int *h_counts_ = nullptr;
   Request *reqs_[kMaxSlots];
   int active_ = 0;
+  bool xy_ = false;  // geometry of the admitted requests
 };
 
 // The server: a worker thread running the engine over admitted requests.
@@ -1387,11 +1434,11 @@ extern "C" {
 namespace {
 gmc_status solve_one(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
                      const float *source, int64_t n_histories, int method, uint64_t seed,
-                     double *flux, gmc_solve_stats *stats, bool wall) {
+                     double *flux, gmc_solve_stats *stats, bool wall, bool xy = false) {
   if (!ctx) return GMC_EINVAL;
   if (!flux) return set_error(ctx, GMC_EINVAL, "transport_solve: null flux");
   Request R;
-  gmc_status st = make_request(ctx, nx, ny, tau, c, source, n_histories, method, seed, R, wall);
+  gmc_status st = make_request(ctx, nx, ny, tau, c, source, n_histories, method, seed, R, wall, xy);
   if (st != GMC_OK) return st;
   cudaSetDevice(ctx->device);
   const int64_t C = ctx->cfg.bank_capacity;
@@ -1436,6 +1483,18 @@ gmc_status transport_solve_wall(gmc_ctx *ctx, int nx, int ny, const float *tau, 
                                 const float *wall, int64_t n_histories, int method, uint64_t seed,
                                 double *flux, gmc_solve_stats *stats) {
   return solve_one(ctx, nx, ny, tau, c, wall, n_histories, method, seed, flux, stats, true);
+}
+
+gmc_status transport_solve_xy(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                              const float *source, int64_t n_histories, int method, uint64_t seed,
+                              double *flux, gmc_solve_stats *stats) {
+  return solve_one(ctx, nx, ny, tau, c, source, n_histories, method, seed, flux, stats, false, true);
+}
+
+gmc_status transport_solve_wall_xy(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
+                                   const float *wall, int64_t n_histories, int method,
+                                   uint64_t seed, double *flux, gmc_solve_stats *stats) {
+  return solve_one(ctx, nx, ny, tau, c, wall, n_histories, method, seed, flux, stats, true, true);
 }
 
 gmc_status gmc_serve_start(gmc_ctx *ctx, const gmc_serve_config *cfg) {

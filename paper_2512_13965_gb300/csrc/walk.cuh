@@ -94,12 +94,17 @@ struct WalkResult {
 // length s, direction, next Philox event and collision count are read and
 // updated in place. Status kExited / kAbsorbed ends the walk; kTruncated means
 // max_flights were taken and the walk resumes from the updated state, drawing
-// exactly the random numbers an uninterrupted walk would.
+// exactly the random numbers an uninterrupted walk would. sphere: x-y
+// geometry (the cell is the cross-section of an infinite prism): (ux, uy) is
+// the projection of a 3-D direction, a flight of 3-D length d moves the
+// position by d (ux, uy), and a scattering draws the direction on the sphere
+// (azimuth 2 pi u2 as on the circle, polar cosine 2 u3 - 1), as walk_xy.
 template <typename T>
 __device__ __forceinline__ WalkResult walk_box_from(T tau, float c, int implicit, T &x, T &y, T &s,
                                                     float &ux, float &uy, uint32_t &event,
                                                     uint32_t &ncoll, uint32_t max_flights,
-                                                    uint64_t seed, uint64_t id) {
+                                                    uint64_t seed, uint64_t id,
+                                                    bool sphere = false) {
   const float rate = implicit ? c : 1.0f;
   WalkResult w;
   w.status = kTruncated;
@@ -140,7 +145,16 @@ __device__ __forceinline__ WalkResult walk_box_from(T tau, float c, int implicit
       w.status = kAbsorbed;
       break;
     }
-    sincospif(2.0f * u01(r.z), &uy, &ux);
+    if (sphere) {
+      float sp, cp;
+      sincospif(2.0f * u01(r.z), &sp, &cp);
+      const float mu = 2.0f * u01(r.w) - 1.0f;
+      const float rr = sqrtf(fmaxf(1.0f - mu * mu, 0.0f));
+      ux = rr * cp;
+      uy = rr * sp;
+    } else {
+      sincospif(2.0f * u01(r.z), &uy, &ux);
+    }
   }
   w.ux = ux;
   w.uy = uy;
@@ -210,24 +224,25 @@ __device__ __forceinline__ WalkState walk_start(float tau, float X, float Y, flo
 
 // Up to max_flights more flights of the walk in `st` (updated in place); a
 // walk whose total collisions reach kMaxFlights ends as kTruncated with
-// face -1 regardless of max_flights.
+// face -1 regardless of max_flights. sphere: x-y geometry (walk_box_from).
 __device__ __forceinline__ WalkResult walk_cell_resume(float tau, float c, int implicit,
                                                        WalkState &st, uint32_t max_flights,
-                                                       uint64_t seed, uint64_t id) {
+                                                       uint64_t seed, uint64_t id,
+                                                       bool sphere = false) {
   const uint32_t left = st.ncoll < kMaxFlights ? kMaxFlights - st.ncoll : 0u;
   const uint32_t cap = max_flights < left ? max_flights : left;
   WalkResult w;
   if (tau > kTau64) {
     double x = st.x, y = st.y, s = st.s;
     w = walk_box_from<double>((double)tau, c, implicit, x, y, s, st.ux, st.uy, st.event, st.ncoll,
-                              cap, seed, id);
+                              cap, seed, id, sphere);
     st.x = x;
     st.y = y;
     st.s = s;
   } else {
     float x = (float)st.x, y = (float)st.y, s = (float)st.s;
     w = walk_box_from<float>(tau, c, implicit, x, y, s, st.ux, st.uy, st.event, st.ncoll, cap, seed,
-                             id);
+                             id, sphere);
     st.x = x;
     st.y = y;
     st.s = s;

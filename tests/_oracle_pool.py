@@ -9,7 +9,10 @@ oracle.transport do not cross process boundaries):
               | ("mlp_e4m3", weights_path, steps, integrator)
               | ("hybrid", weights_path, steps, min_tau)
               | ("equivalent", weights_path, steps, integrator, box)
-              | ("walk_global",),
+              | ("walk_global",)
+              | ("mlp_xy", weights_path, steps, integrator) | ("walk_global_xy",)
+              | ("equivalent_xy", weights_path, steps, integrator, box),
+     "geometry": "flat" (default) | "xy" (x-y solves: the *_xy samplers),
      "internal": None | ("mlp", weights_path, steps, integrator)
                | ("equivalent", weights_path, steps, integrator, box)}
 "equivalent" is the network at each cell's scattering-equivalent condition in
@@ -65,6 +68,13 @@ def _sampler(spec, seed):
     if kind == "equivalent":
         return OT.equivalent_sampler(OT.mlp_sampler(_net(spec[1]), spec[2], spec[3], seed),
                                      OT.walk_sampler_global(seed), *spec[4])
+    if kind == "mlp_xy":
+        return OT.mlp_sampler_xy(_net(spec[1]), spec[2], spec[3], seed)
+    if kind == "walk_global_xy":
+        return OT.walk_sampler_global_xy(seed)
+    if kind == "equivalent_xy":
+        return OT.equivalent_sampler(OT.mlp_sampler_xy(_net(spec[1]), spec[2], spec[3], seed),
+                                     OT.walk_sampler_global_xy(seed), *spec[4])
     raise ValueError(kind)
 
 
@@ -81,7 +91,8 @@ def solve_task(task):
             internal = OT.equivalent_internal_sampler(internal, OT.walk_internal_sampler(seed),
                                                       *spec[4])
     return OT.solve_gmc(tau, c, src, task["n"], seed, _sampler(task["sampler"], seed),
-                        internal=internal, wall=task.get("wall"))
+                        internal=internal, wall=task.get("wall"),
+                        geometry=task.get("geometry", "flat"))
 
 
 def _init():
