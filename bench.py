@@ -195,7 +195,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--workload", default="sampler",
                     choices=["sampler", "solve", "hohlraum", "serve", "sweep", "heldout", "sigma",
-                             "walks", "paper", "train", "arch"])
+                             "walks", "paper", "train", "arch", "xy"])
     ap.add_argument("--weights", default=None,
                     help="GMCW file of the boundary model for the solve, serve, sigma, sweep and "
                          "heldout workloads (default: the package's trained network; 'kaiming': "
@@ -244,6 +244,8 @@ def main():
         return run_train(args)
     if args.workload == "arch":
         return run_arch(args)
+    if args.workload == "xy":
+        return run_xy(args)
 
     import numpy as np
     import torch
@@ -885,6 +887,55 @@ def run_arch(args):
     print(json.dumps({"metric": "flux error and speed of the residual-modulated network vs the MLP",
                       "workload": "transport solve 128x128, %d histories; sampler 2^20 x 16 Euler" % n_hist,
                       "results": out}))
+    ctx.close()
+
+
+def run_xy(args):
+    """The 128x128 solve of the solve workload (tau logU[0.1,500], c
+    {0.5,0.999} per 16x16 block, seed 2, central 8x8 source, vacuum) in x-y
+    geometry (transport_solve_xy: prism cells, 3-D directions): the x-y
+    random walk as two half runs (reference flux and statistical floor),
+    then GMC with the committed x-y network (BF16, midpoint 8 and Euler 16;
+    births walked), at --histories; device seconds per solve, cell
+    transmissions/s and the flux error against the walk."""
+    import numpy as np
+    import synth
+    import paper_2512_13965_gb300 as g
+    import torch
+    torch.cuda.set_device(0)
+    ctx = g.Context(0)
+    g.gmc_load_xy_weights(ctx, args.weights or TRAINED_XY)
+    N = 128
+    tau, c, src = synth.grid_problem(n=N, seed=2)
+    tau, c, src = (np.ascontiguousarray(a.ravel()) for a in (tau, c, src))
+    n_hist = int(args.histories)
+
+    def solve(method, seed, n, integ=0, steps=16):
+        cfg = g.gmc_get_config(ctx)
+        cfg.steps, cfg.integrator, cfg.precision, cfg.gmc_min_tau = steps, integ, g.GMC_BF16, 0.0
+        g.gmc_set_config(ctx, cfg)
+        f = np.zeros(N * N)
+        st = g.transport_solve_xy(ctx, N, N, tau, c, src, n, method, seed, f)
+        return f, st
+
+    half = n_hist // 2
+    f_a, st_a = solve(g.GMC_METHOD_ANALOG, 1, half)
+    f_b, st_b = solve(g.GMC_METHOD_ANALOG, 2, n_hist - half)
+    f_mc = 0.5 * (f_a + f_b)
+    secs = st_a.seconds + st_b.seconds
+    trans = st_a.transmissions + st_b.transmissions
+    out = {"analog_xy": {"seconds": secs, "transmissions_per_s": trans / secs,
+                         "collisions": st_a.collisions + st_b.collisions,
+                         "flux_floor_at_n": _rel(f_a, f_b) / np.sqrt(2.0)}}
+    for name, integ, steps in (("gmc_xy_bf16_midpoint8", g.GMC_MIDPOINT, 8),
+                               ("gmc_xy_bf16_euler16", g.GMC_EULER, 16)):
+        f, st = solve(g.GMC_METHOD_GMC, 3, n_hist, integ, steps)
+        out[name] = {"seconds": st.seconds, "transmissions_per_s": st.transmissions / st.seconds,
+                     "collisions_of_walked_births": st.collisions,
+                     "flux_rel_err_vs_analog": _rel(f, f_mc), "solve_speedup_vs_analog": secs / st.seconds}
+    print(json.dumps({"metric": "x-y geometry solve, GMC vs the random walk",
+                      "workload": "transport solve 128x128 in x-y geometry, %d histories" % n_hist,
+                      "weights": os.path.relpath(args.weights or TRAINED_XY, ROOT), "results": out}))
     ctx.close()
 
 
