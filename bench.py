@@ -43,6 +43,7 @@ WIDE_BOUNDARY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_bou
 WIDE_INTERNAL = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_internal_wide.bin")
 WIDE_BOX = [0.01, 1000.0, 0.5, 0.999]
 TRAINED_XY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_xy.bin")
+WIDE_XY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_xy_wide.bin")
 # the architecture comparison: the residual-modulated boundary network and an
 # MLP control, both trained with the FP32 path on the same data and schedule
 ARCH_RM = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_boundary_rm.bin")
@@ -215,6 +216,8 @@ def main():
     ap.add_argument("--hist-range", type=float, nargs=2, default=(1e3, 1e5),
                     help="serve: histories per request, log-uniform in [lo, hi]")
     ap.add_argument("--train-batch", type=int, default=16384, help="train: batch rows per step")
+    ap.add_argument("--geometry", default="flat", choices=["flat", "xy"],
+                    help="paper: flat (directions on the circle) or xy (3-D directions)")
     ap.add_argument("--sampler-weights", default=None,
                     help="sampler: time this GMCW network instead of the Kaiming-normal MLP")
     ap.add_argument("--net-box", type=float, nargs=4, default=None,
@@ -749,15 +752,31 @@ def run_paper(args):
     seeds (its run-to-run difference is the statistical floor), then GMC
     (trained networks, BF16, midpoint 8 and RK4 12); solve time,
     transmissions/s and the flux error against the walk. Default networks:
-    the pair trained on tau log-uniform in [0.01, 1000], with that box."""
+    the pair trained on tau log-uniform in [0.01, 1000], with that box.
+    --geometry xy: both problems in x-y geometry (3-D directions;
+    transport_solve_xy / transport_solve_wall_xy), the walk on the sphere
+    against GMC with the x-y network trained on [0.01, 1000] (births
+    walked: there is no x-y internal model)."""
     import numpy as np
     import synth
+    xy = getattr(args, "geometry", "flat") == "xy"
     if args.weights is None and args.internal_weights is None and args.net_box is None:
         args.weights, args.internal_weights, args.net_box = WIDE_BOUNDARY, WIDE_INTERNAL, list(WIDE_BOX)
+        if xy:
+            args.weights, args.internal_weights = WIDE_XY, "none"
+    if xy:
+        xy_weights = args.weights
+        args.weights = "kaiming"  # the square-cell slot is unused by x-y solves
     g, ctx = _context(args)
+    if xy:
+        g.gmc_load_xy_weights(ctx, xy_weights)
+        args.weights = xy_weights
+        problems = {"lattice": (synth.paper_lattice_problem(112), g.transport_solve_xy),
+                    "hohlraum": (synth.paper_hohlraum_problem(112), g.transport_solve_wall_xy)}
+    else:
+        problems = {"lattice": (synth.paper_lattice_problem(112), g.transport_solve),
+                    "hohlraum": (synth.paper_hohlraum_problem(112), g.transport_solve_wall)}
     n_hist = int(args.histories)
-    problems = {"lattice": (synth.paper_lattice_problem(112), g.transport_solve),
-                "hohlraum": (synth.paper_hohlraum_problem(112), g.transport_solve_wall)}
     out = {}
     box = ((0.1, 1000.0), (0.5, 0.999)) if not args.net_box else (tuple(args.net_box[:2]), tuple(args.net_box[2:]))
     for name, ((tau, c, src), solve) in problems.items():
@@ -795,7 +814,8 @@ def run_paper(args):
         out[name] = res
     print(json.dumps({"metric": "solves of the paper's benchmark problems, GMC vs the random walk",
                       "workload": "lattice and linearized hohlraum, 112x112 cells, printed cross "
-                                  "sections, stand-in layouts, %d histories" % n_hist,
+                                  "sections, stand-in layouts, %d histories%s"
+                                  % (n_hist, ", x-y geometry" if xy else ""),
                       "weights": args.weights, "internal_weights": args.internal_weights,
                       "net_box": [list(box[0]), list(box[1])], "results": out}))
     ctx.close()
