@@ -43,7 +43,6 @@ WIDE_BOUNDARY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_bou
 WIDE_INTERNAL = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_internal_wide.bin")
 WIDE_BOX = [0.01, 1000.0, 0.5, 0.999]
 TRAINED_XY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_xy.bin")
-WIDE_XY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_xy_wide.bin")
 # the architecture comparison: the residual-modulated boundary network and an
 # MLP control, both trained with the FP32 path on the same data and schedule
 ARCH_RM = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_boundary_rm.bin")
@@ -755,15 +754,15 @@ def run_paper(args):
     the pair trained on tau log-uniform in [0.01, 1000], with that box.
     --geometry xy: both problems in x-y geometry (3-D directions;
     transport_solve_xy / transport_solve_wall_xy), the walk on the sphere
-    against GMC with the x-y network trained on [0.01, 1000] (births
-    walked: there is no x-y internal model)."""
+    against GMC with the package's x-y network and its box [0.1, 1000] x
+    [0.5, 0.999] (births walked: there is no x-y internal model)."""
     import numpy as np
     import synth
     xy = getattr(args, "geometry", "flat") == "xy"
     if args.weights is None and args.internal_weights is None and args.net_box is None:
         args.weights, args.internal_weights, args.net_box = WIDE_BOUNDARY, WIDE_INTERNAL, list(WIDE_BOX)
         if xy:
-            args.weights, args.internal_weights = WIDE_XY, "none"
+            args.weights, args.internal_weights, args.net_box = TRAINED_XY, "none", None
     if xy:
         xy_weights = args.weights
         args.weights = "kaiming"  # the square-cell slot is unused by x-y solves
