@@ -43,6 +43,7 @@ WIDE_BOUNDARY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_bou
 WIDE_INTERNAL = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_internal_wide.bin")
 WIDE_BOX = [0.01, 1000.0, 0.5, 0.999]
 TRAINED_XY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_xy.bin")
+TRAINED_INTERNAL_XY = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_internal_xy.bin")
 # the architecture comparison: the residual-modulated boundary network and an
 # MLP control, both trained with the FP32 path on the same data and schedule
 ARCH_RM = os.path.join(ROOT, "paper_2512_13965_gb300", "weights", "gmc_boundary_rm.bin")
@@ -915,8 +916,9 @@ def run_xy(args):
     geometry (transport_solve_xy: prism cells, 3-D directions): the x-y
     random walk as two half runs (reference flux and statistical floor),
     then GMC with the committed x-y network (BF16, midpoint 8 and Euler 16;
-    births walked), at --histories; device seconds per solve, cell
-    transmissions/s and the flux error against the walk."""
+    births walked), and midpoint 8 again with the committed x-y internal
+    model sampling the births, at --histories; device seconds per solve,
+    cell transmissions/s and the flux error against the walk."""
     import numpy as np
     import synth
     import paper_2512_13965_gb300 as g
@@ -952,6 +954,12 @@ def run_xy(args):
         out[name] = {"seconds": st.seconds, "transmissions_per_s": st.transmissions / st.seconds,
                      "collisions_of_walked_births": st.collisions,
                      "flux_rel_err_vs_analog": _rel(f, f_mc), "solve_speedup_vs_analog": secs / st.seconds}
+    g.gmc_load_internal_xy_weights(ctx, TRAINED_INTERNAL_XY)
+    f, st = solve(g.GMC_METHOD_GMC, 3, n_hist, g.GMC_MIDPOINT, 8)
+    out["gmc_xy_bf16_midpoint8_internal_births"] = {
+        "seconds": st.seconds, "transmissions_per_s": st.transmissions / st.seconds,
+        "collisions": st.collisions, "flux_rel_err_vs_analog": _rel(f, f_mc),
+        "solve_speedup_vs_analog": secs / st.seconds}
     print(json.dumps({"metric": "x-y geometry solve, GMC vs the random walk",
                       "workload": "transport solve 128x128 in x-y geometry, %d histories" % n_hist,
                       "weights": os.path.relpath(args.weights or TRAINED_XY, ROOT), "results": out}))

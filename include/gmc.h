@@ -222,6 +222,21 @@ gmc_status gmc_load_xy_weights(gmc_ctx *ctx, const char *path);
 gmc_status gmc_load_xy_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes);
 
 /*
+ * Internal model of x-y geometry: the internal model's condition (X, Y,
+ * ln tau, c, d) for a birth inside a prism cell with an isotropic 3-D
+ * direction, and its state the exit (p, ux, uy, ln s) with (ux, uy) the
+ * projected exit direction (decoded into the unit disk) and s the 3-D track
+ * length. When loaded, x-y GMC solves (transport_solve_xy) sample births
+ * with it; gmc_sample_internal_xy samples it directly (arguments as
+ * gmc_sample_internal). Errors as gmc_load_weights.
+ */
+gmc_status gmc_load_internal_xy_weights(gmc_ctx *ctx, const char *path);
+gmc_status gmc_load_internal_xy_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes);
+gmc_status gmc_sample_internal_xy(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
+                                  uint64_t seed, uint64_t id0, int steps, int integrator,
+                                  int precision, float *y_raw, float *exit);
+
+/*
  * Samples n exit states (Eq. 8, Eq. 11) with the loaded network.
  *  cond    [5][n] float: xi, cos theta_in, sin theta_in, ln tau, c (raw,
  *          standardized inside with the file's cond_mean / cond_std).
@@ -397,7 +412,8 @@ gmc_status transport_solve_wall(gmc_ctx *ctx, int nx, int ny, const float *tau, 
  * draw (h, 1, tag 4); wall entries take the 3-D cosine law, cosine to the
  * inward normal sqrt(u2) and azimuth about it 2 pi u3. GMC_METHOD_GMC samples
  * cell crossings with the x-y boundary network (gmc_load_xy_weights;
- * GMC_ENOWEIGHTS without it) and walks every birth. Other arguments, the
+ * GMC_ENOWEIGHTS without it) and its births with the x-y internal model
+ * when one is loaded (gmc_load_internal_xy_weights), else walks them. Other arguments, the
  * result and blocking as for transport_solve and transport_solve_wall.
  */
 gmc_status transport_solve_xy(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
@@ -504,6 +520,18 @@ gmc_status gmc_train_data_internal(gmc_ctx *ctx, int64_t n, uint64_t seed, float
  */
 gmc_status gmc_train_data_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, float tau_hi,
                              float c_lo, float c_hi, float *cond, float *y);
+/*
+ * Training data of the internal model in x-y geometry: for sample i, Philox
+ * block (i, 0, tag 9) gives ln tau uniform in [ln tau_lo, ln tau_hi], c
+ * uniform in [c_lo, c_hi], X and Y uniform; (i, 1, tag 9) the isotropic 3-D
+ * birth direction, azimuth 2 pi u0 and polar cosine 2 u1 - 1; the
+ * implicit-capture walk on the sphere from (X, Y) draws from event 2 on.
+ * cond [5][n] = (X, Y, ln tau, c, min(X, Y, 1 - X, 1 - Y)), y [4][n] =
+ * (p, ux, uy, ln s) in the cell's own frame (projected exit direction, 3-D
+ * track length): device memory.
+ */
+gmc_status gmc_train_data_internal_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo,
+                                      float tau_hi, float c_lo, float c_hi, float *cond, float *y);
 /*
  * Starts training on the device dataset (cond, y as gmc_train_data writes;
  * the caller keeps them alive while training). Standardization statistics

@@ -372,6 +372,62 @@ def walk_internal_sampler(seed):
     return f
 
 
+def mlp_internal_sampler_xy(net, steps, integrator, seed):
+    """mlp_internal_sampler for x-y geometry: the x-y internal model's exit,
+    decoded into the unit disk (decode_disk)."""
+    def f(X, Y, tau, c, ids, u_angle):
+        cond = internal_condition(X, Y, tau, c)
+        ids = np.asarray(ids, np.uint64)
+        z = rng.normals_for(seed, ids, np.zeros(ids.size, np.uint32), rng.TAG_NOISE)
+        d = mlp.decode_disk(net, mlp.sample(net, cond, z, steps, integrator))
+        return d["face"], d["q"], d["ux"], d["uy"], d["s"], np.ones(ids.size, np.uint32)
+    return f
+
+
+def walk_internal_sampler_xy(seed):
+    """Births of an x-y solve walked as the random-walk solve walks them:
+    direction on the sphere (birth_directions), walk_one_xy from event 0."""
+    def f(X, Y, tau, c, ids, u_angle):
+        ids = np.asarray(ids, np.uint64)
+        bux, buy = birth_directions(seed, ids, u_angle, "xy")
+        out = [np.zeros(len(ids)) for _ in range(5)] + [np.zeros(len(ids), np.uint32)]
+        for k in range(len(ids)):
+            r = walk_one_xy(tau[k], c[k], MODE_IMPLICIT, X[k] * tau[k], Y[k] * tau[k], bux[k],
+                            buy[k], seed, int(ids[k]), 0)
+            for a, v in zip(out, (r["face"], r["q"], r["ux"], r["uy"], r["s"], r["event"])):
+                a[k] = v
+        return out[0].astype(np.int64), out[1], out[2], out[3], out[4], out[5]
+    return f
+
+
+def internal_pairs_xy(n, seed, tau_range=(0.1, 1000.0), c_range=(0.5, 0.999)):
+    """Training pairs of the x-y internal model (births inside a prism cell,
+    3-D isotropic direction, implicit-capture walk to the exit): for sample
+    i, the draw (i, 0, tag 9) gives ln tau uniform in the log range, c
+    uniform, X and Y uniform; (i, 1, tag 9) the direction, azimuth 2 pi u0 and
+    polar cosine 2 u1 - 1, projected on the plane; the walk draws from event
+    2. Returns cond [5, n] = (X, Y, ln tau, c, distance to the nearest face)
+    and y [4, n] = (p, ux, uy, ln s) in the cell's own frame, in FP64."""
+    ids = np.arange(n, dtype=np.uint64)
+    u0 = rng.uniforms_for(seed, ids, np.zeros(n, np.uint32), 9)
+    u1 = rng.uniforms_for(seed, ids, np.ones(n, np.uint32), 9)
+    lo, hi = np.log(tau_range[0]), np.log(tau_range[1])
+    ltau = lo + (hi - lo) * u0[0]
+    c = c_range[0] + (c_range[1] - c_range[0]) * u0[1]
+    X, Y = u0[2], u0[3]
+    mu = 2.0 * u1[1] - 1.0
+    r = np.sqrt(np.maximum(1.0 - mu * mu, 0.0))
+    ux, uy = r * np.cos(2.0 * np.pi * u1[0]), r * np.sin(2.0 * np.pi * u1[0])
+    tau = np.exp(ltau)
+    y = np.zeros((4, n))
+    for i in range(n):
+        w = walk_one_xy(tau[i], c[i], MODE_IMPLICIT, X[i] * tau[i], Y[i] * tau[i], ux[i], uy[i],
+                        seed, i, 2)
+        y[:, i] = (w["face"] + w["q"], w["ux"], w["uy"], np.log(max(w["s"], mlp.S_MIN)))
+    cond = internal_condition(X, Y, tau, c)
+    return cond, y
+
+
 def walk_sampler_global(seed):
     """Stage 2 replaced by the implicit-capture walk in the cell's own (global)
     frame, as a random-walk solve takes it: entry face F = (rot - 1) mod 4 at
@@ -487,12 +543,11 @@ def solve_gmc(tau, c, src, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1, max
     carried as their projection on the plane; births on the sphere
     (birth_directions), wall entries with the 3-D cosine law
     (wall_births_xy), walks by walk_one_xy; `sampler` must be an x-y one,
-    mlp_sampler_xy or walk_sampler_global_xy; no internal model).
+    mlp_sampler_xy or walk_sampler_global_xy, and `internal` too,
+    mlp_internal_sampler_xy or walk_internal_sampler_xy).
     """
     if geometry not in ("flat", "xy"):
         raise ValueError(geometry)
-    if geometry == "xy" and internal is not None:
-        raise ValueError("x-y solves walk their births")
     walker = walk_one if geometry == "flat" else walk_one_xy
     tau = np.asarray(tau, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)

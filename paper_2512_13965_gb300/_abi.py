@@ -86,6 +86,9 @@ def _load():
         "gmc_load_weights_buffer": [P, P, sz],
         "gmc_load_internal_weights": [P, ctypes.c_char_p],
         "gmc_load_internal_weights_buffer": [P, P, sz],
+        "gmc_load_internal_xy_weights": [P, ctypes.c_char_p],
+        "gmc_load_internal_xy_weights_buffer": [P, P, sz],
+        "gmc_sample_internal_xy": [P, i64, P, P, u64, u64, i32, i32, i32, P, P],
         "gmc_load_xy_weights": [P, ctypes.c_char_p],
         "gmc_load_xy_weights_buffer": [P, P, sz],
         "gmc_sample_internal": [P, i64, P, P, u64, u64, i32, i32, i32, P, P],
@@ -114,6 +117,8 @@ def _load():
                                     ctypes.c_float, P, P],
         "gmc_train_data_xy": [P, i64, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, P, P],
+        "gmc_train_data_internal_xy": [P, i64, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, P, P],
         "gmc_train_begin": [P, i64, P, P, ctypes.POINTER(gmc_train_config)],
         "gmc_train_steps": [P, i64, P],
         "gmc_train_set_lr": [P, ctypes.c_double],
@@ -294,6 +299,16 @@ def gmc_load_internal_weights_buffer(ctx, blob):
                                                           len(blob)))
 
 
+def gmc_load_internal_xy_weights(ctx, path):
+    return ctx.check(lib.gmc_load_internal_xy_weights(ctx.handle, os.fsencode(path)))
+
+
+def gmc_load_internal_xy_weights_buffer(ctx, blob):
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    return ctx.check(lib.gmc_load_internal_xy_weights_buffer(ctx.handle, ctypes.addressof(buf),
+                                                             len(blob)))
+
+
 def gmc_load_xy_weights(ctx, path):
     return ctx.check(lib.gmc_load_xy_weights(ctx.handle, os.fsencode(path)))
 
@@ -313,6 +328,13 @@ def gmc_sample_internal(ctx, n, cond, noise, seed, id0, steps, integrator, preci
     return ctx.check(lib.gmc_sample_internal(ctx.handle, n, *_sampler_args(n, cond, noise),
                                              seed, id0, steps, integrator, precision,
                                              *_sampler_out(n, y_raw, exit)))
+
+
+def gmc_sample_internal_xy(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw,
+                           exit):
+    return ctx.check(lib.gmc_sample_internal_xy(ctx.handle, n, *_sampler_args(n, cond, noise),
+                                                seed, id0, steps, integrator, precision,
+                                                *_sampler_out(n, y_raw, exit)))
 
 
 def gmc_transmit(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw, exit):
@@ -399,6 +421,12 @@ def gmc_train_data_internal(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
 def gmc_train_data_xy(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
     return ctx.check(lib.gmc_train_data_xy(ctx.handle, n, seed, tau_lo, tau_hi, c_lo, c_hi,
                                            _arr(cond, 4, 5 * n, "cond"), _arr(y, 4, 4 * n, "y")))
+
+
+def gmc_train_data_internal_xy(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
+    return ctx.check(lib.gmc_train_data_internal_xy(ctx.handle, n, seed, tau_lo, tau_hi, c_lo, c_hi,
+                                                    _arr(cond, 4, 5 * n, "cond"),
+                                                    _arr(y, 4, 4 * n, "y")))
 
 
 def gmc_train_begin(ctx, n, cond, y, cfg):

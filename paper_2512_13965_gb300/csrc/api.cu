@@ -265,6 +265,11 @@ gmc_status gmc_destroy(gmc_ctx *ctx) {
   if (ctx->xy.d_tc_bias) cudaFree(ctx->xy.d_tc_bias);
   if (ctx->xy.d_tc8) cudaFree(ctx->xy.d_tc8);
   if (ctx->xy.d_tc8_scale) cudaFree(ctx->xy.d_tc8_scale);
+  if (ctx->internal_xy.d_f32) cudaFree(ctx->internal_xy.d_f32);
+  if (ctx->internal_xy.d_tc) cudaFree(ctx->internal_xy.d_tc);
+  if (ctx->internal_xy.d_tc_bias) cudaFree(ctx->internal_xy.d_tc_bias);
+  if (ctx->internal_xy.d_tc8) cudaFree(ctx->internal_xy.d_tc8);
+  if (ctx->internal_xy.d_tc8_scale) cudaFree(ctx->internal_xy.d_tc8_scale);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   delete ctx;
@@ -414,7 +419,8 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
     ns.y_mean[k] = st[10 + k];
     ns.y_std[k] = st[14 + k];
   }
-  ns.disk = &N == &ctx->xy ? 1 : 0;  // the x-y geometry slot decodes into the unit disk
+  // the x-y geometry slots decode into the unit disk
+  ns.disk = (&N == &ctx->xy || &N == &ctx->internal_xy) ? 1 : 0;
 
   // FP32 transposed block (room for the modulation arrays in every load, so
   // a later load of either network reuses it)
@@ -536,6 +542,20 @@ gmc_status gmc_load_xy_weights(gmc_ctx *ctx, const char *path) {
   gmc_status st;
   if (!read_file(ctx, path, blob, &st)) return st;
   return load_net(ctx, ctx->xy, blob.data(), blob.size());
+}
+
+gmc_status gmc_load_internal_xy_weights(gmc_ctx *ctx, const char *path) {
+  if (!ctx || !path) return set_error(ctx, GMC_EINVAL, "gmc_load_internal_xy_weights: null argument");
+  std::vector<unsigned char> blob;
+  gmc_status st;
+  if (!read_file(ctx, path, blob, &st)) return st;
+  return load_net(ctx, ctx->internal_xy, blob.data(), blob.size());
+}
+
+gmc_status gmc_load_internal_xy_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes) {
+  if (!ctx || !blob)
+    return set_error(ctx, GMC_EINVAL, "gmc_load_internal_xy_weights_buffer: null argument");
+  return load_net(ctx, ctx->internal_xy, blob, nbytes);
 }
 
 gmc_status gmc_load_weights_buffer(gmc_ctx *ctx, const void *blob, size_t nbytes) {
@@ -672,6 +692,14 @@ gmc_status gmc_sample_internal(gmc_ctx *ctx, int64_t n, const float *cond, const
   if (!ctx) return GMC_EINVAL;
   return transmit_net(ctx, ctx->internal, n, cond, noise, seed, id0, steps, integrator, precision,
                       y_raw, exit);
+}
+
+gmc_status gmc_sample_internal_xy(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,
+                                  uint64_t seed, uint64_t id0, int steps, int integrator,
+                                  int precision, float *y_raw, float *exit) {
+  if (!ctx) return GMC_EINVAL;
+  return transmit_net(ctx, ctx->internal_xy, n, cond, noise, seed, id0, steps, integrator,
+                      precision, y_raw, exit);
 }
 
 gmc_status gmc_transmit_xy(gmc_ctx *ctx, int64_t n, const float *cond, const float *noise,

@@ -90,6 +90,9 @@ struct gmc_ctx {
   gmc::NetDev internal;
   // the boundary model of x-y geometry (gmc_load_xy_weights, gmc_transmit_xy)
   gmc::NetDev xy;
+  // the internal model of x-y geometry (gmc_load_internal_xy_weights): births
+  // of x-y GMC solves
+  gmc::NetDev internal_xy;
   int *d_err = nullptr;  // device error word (bounded waits)
 
   // training state (gmc_train_begin .. gmc_destroy)

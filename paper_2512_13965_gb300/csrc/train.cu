@@ -35,7 +35,8 @@
 
 namespace gmc {
 
-constexpr uint32_t kTagData = 5u, kTagDataInternal = 7u, kTagDataXY = 8u;  // kTagTrain: train_fused.h
+constexpr uint32_t kTagData = 5u, kTagDataInternal = 7u, kTagDataXY = 8u,
+                   kTagDataInternalXY = 9u;  // kTagTrain: train_fused.h
 
 struct TrainState {
   int64_t n = 0;
@@ -102,6 +103,45 @@ __global__ void internal_data_kernel(int64_t n, uint64_t seed, float ltau_lo, fl
   float ux, uy;
   sincospif(2.0f * u01(philox_draw(seed, (uint64_t)i, 1u, kTagDataInternal).x), &uy, &ux);
   const WalkResult w = walk_cell(tau, c, 1, X, Y, ux, uy, seed, (uint64_t)i, 2u);
+  cond[i] = X;
+  cond[n + i] = Y;
+  cond[2 * n + i] = ltau;
+  cond[3 * n + i] = c;
+  cond[4 * n + i] = fminf(fminf(X, Y), fminf(1.0f - X, 1.0f - Y));
+  y[i] = (float)(w.face < 0 ? 0 : w.face) + w.q;
+  y[n + i] = w.ux;
+  y[2 * n + i] = w.uy;
+  y[3 * n + i] = logf(fmaxf(w.s, kSMin));
+}
+
+// Training data of the internal model in x-y geometry (a birth inside the
+// cross-section of an infinite prism, 3-D isotropic direction): Philox block
+// (i, 0, tag 9) gives ln tau, c, X, Y as internal_data_kernel; (i, 1, tag 9)
+// the direction, azimuth 2 pi u0 and polar cosine 2 u1 - 1, projected on the
+// plane. The implicit-capture walk with scattering on the sphere runs from
+// event 2 (FP64 positions in cells thicker than kTau64). cond = (X, Y,
+// ln tau, c, min(X, Y, 1 - X, 1 - Y)); y = (p, ux, uy, ln s) in the cell's own
+// frame, s the 3-D track length.
+__global__ void internal_xy_data_kernel(int64_t n, uint64_t seed, float ltau_lo, float ltau_hi,
+                                        float c_lo, float c_hi, float *__restrict__ cond,
+                                        float *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 r = philox_draw(seed, (uint64_t)i, 0u, kTagDataInternalXY);
+  const float ltau = ltau_lo + (ltau_hi - ltau_lo) * u01(r.x);
+  const float tau = expf(ltau);
+  const float c = c_lo + (c_hi - c_lo) * u01(r.y);
+  const float X = u01(r.z), Y = u01(r.w);
+  const uint4 r1 = philox_draw(seed, (uint64_t)i, 1u, kTagDataInternalXY);
+  float sp, cp;
+  sincospif(2.0f * u01(r1.x), &sp, &cp);
+  const float mu = 2.0f * u01(r1.y) - 1.0f;
+  const float rr = sqrtf(fmaxf(1.0f - mu * mu, 0.0f));
+  const float ux = rr * cp, uy = rr * sp;
+  const WalkResult w =
+      tau > kTau64 ? walk_xy<double>((double)tau, (double)tau, c, 1, (double)X * tau,
+                                     (double)Y * tau, ux, uy, seed, (uint64_t)i, 2u)
+                   : walk_xy<float>(tau, tau, c, 1, X * tau, Y * tau, ux, uy, seed, (uint64_t)i, 2u);
   cond[i] = X;
   cond[n + i] = Y;
   cond[2 * n + i] = ltau;
@@ -670,6 +710,24 @@ gmc_status gmc_train_data_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_l
   cudaSetDevice(ctx->device);
   xy_data_kernel<<<nb(n, 128), 128, 0, ctx->stream>>>(n, seed, logf(tau_lo), logf(tau_hi), c_lo, c_hi,
                                                       cond, y);
+  GMC_CUDA_TRY(ctx, cudaGetLastError());
+  return GMC_OK;
+}
+
+gmc_status gmc_train_data_internal_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo,
+                                      float tau_hi, float c_lo, float c_hi, float *cond, float *y) {
+  if (!ctx) return GMC_EINVAL;
+  if (n < 0 || (n > 0 && (!cond || !y)))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_data_internal_xy: bad arguments");
+  if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
+    return set_error(ctx, GMC_EINVAL,
+                     "gmc_train_data_internal_xy: need 0 < tau_lo <= tau_hi, 0 <= c_lo <= c_hi <= 1");
+  if (n == 0) return GMC_OK;
+  if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_data_internal_xy: cond and y must be device memory");
+  cudaSetDevice(ctx->device);
+  internal_xy_data_kernel<<<nb(n, 128), 128, 0, ctx->stream>>>(n, seed, logf(tau_lo), logf(tau_hi),
+                                                               c_lo, c_hi, cond, y);
   GMC_CUDA_TRY(ctx, cudaGetLastError());
   return GMC_OK;
 }

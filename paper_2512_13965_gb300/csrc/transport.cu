@@ -882,10 +882,13 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
   R.xy = xy;
   if (n_histories > 0 && !(acc > 0.0)) return set_error(ctx, GMC_EINVAL, "solve: zero source");
   if (xy && method == GMC_METHOD_GMC) {
-    // the x-y boundary network; births are walked (no x-y internal model)
+    // the x-y boundary network; births by the x-y internal model when loaded,
+    // walked otherwise
     if (!ctx->xy.loaded)
       return set_error(ctx, GMC_ENOWEIGHTS, "x-y solve: GMC needs gmc_load_xy_weights");
-    if (check_net_path(ctx, ctx->xy, ctx->cfg.precision, ctx->cfg.sampler_kernel, "x-y solve") != GMC_OK)
+    if (check_net_path(ctx, ctx->xy, ctx->cfg.precision, ctx->cfg.sampler_kernel, "x-y solve") != GMC_OK ||
+        (ctx->internal_xy.loaded && check_net_path(ctx, ctx->internal_xy, ctx->cfg.precision,
+                                                   ctx->cfg.sampler_kernel, "x-y solve") != GMC_OK))
       return GMC_EINVAL;
   } else if (method == GMC_METHOD_GMC && !ctx->net.loaded) {
     return set_error(ctx, GMC_ENOWEIGHTS, "solve: GMC needs gmc_load_weights");
@@ -1104,7 +1107,8 @@ class Engine {
       for (auto *R : reqs_)
         if (R) R->live += h_counts_[3 + R->slot];
     }
-    if (pending > 0 && room > 0 && method_ == GMC_METHOD_GMC && ctx_->internal.loaded && !xy_) {
+    const NetDev &inet = xy_ ? ctx_->internal_xy : ctx_->internal;
+    if (pending > 0 && room > 0 && method_ == GMC_METHOD_GMC && inet.loaded) {
       const gmc_status sb = births_internal(pending, room, rules);
       if (sb != GMC_OK) return sb;
     } else if (pending > 0 && room > 0) {
@@ -1201,7 +1205,7 @@ class Engine {
       const bool fp8 = cfg.precision == GMC_FP8;
       // the per-evaluation layer-1 bias depends on the network, the steps and
       // the integrator only: computed once per (network load, setting)
-      const int nk = &N == &ctx_->internal ? 1 : 0;
+      const int nk = (&N == &ctx_->internal || &N == &ctx_->internal_xy) ? 1 : 0;
       Bias1Key &key = bias1_key_[nk];
       const bool ready = key.net == &N && key.generation == N.generation && key.steps == cfg.steps &&
                          key.integrator == cfg.integrator;
@@ -1252,7 +1256,7 @@ class Engine {
       R->next_hist += m;
       base += m;
     }
-    gmc_status st = sample(ctx_->internal, M);
+    gmc_status st = sample(xy_ ? ctx_->internal_xy : ctx_->internal, M);
     if (st != GMC_OK) return st;
     const Route route{bank_[cur_], d_face, tbank_[ctn_], d_thin, true};
     birth_gmc_post_kernel<<<nblocks(M, 256), 256, 0, s_>>>(M, bhist, bslot, bcell, d_exit_, d_slots_,

@@ -9,7 +9,8 @@ tau log-uniform in [0.1, 1000], c uniform in [0.5, 0.999]), with
 --model internal `gmc_train_data_internal` (walks from a uniform point inside
 the cell, for the internal-source model), with --model xy
 `gmc_train_data_xy` (walks in x-y geometry: 3-D directions, the cell the
-cross-section of a prism); objective: conditional flow
+cross-section of a prism), with --model internal_xy
+`gmc_train_data_internal_xy` (births inside a prism cell); objective: conditional flow
 matching (Eq. 9) with AdamW, learning rate warmed up linearly and then
 decayed along a cosine to --lr-min; everything runs in libgmc.so, the GEMMs
 on tensor cores with BF16 operands and FP32 accumulation and master weights
@@ -45,10 +46,11 @@ def main(argv=None):
     ap.add_argument("--c", type=float, nargs=2, default=(0.5, 0.999))
     ap.add_argument("--report", type=int, default=1000)
     ap.add_argument("--device", type=int, default=0)
-    ap.add_argument("--model", default="boundary", choices=["boundary", "internal", "xy"],
+    ap.add_argument("--model", default="boundary", choices=["boundary", "internal", "xy", "internal_xy"],
                     help="boundary: cell transmissions from the left face; internal: births "
                          "inside a cell (volumetric source); xy: transmissions in x-y geometry "
-                         "(3-D directions projected on the unit disk)")
+                         "(3-D directions projected on the unit disk); internal_xy: births in x-y "
+                         "geometry")
     ap.add_argument("--precision", default=None, choices=["bf16", "fp32"],
                     help="GEMM operands: bf16 (tensor cores; the MLP's default) or fp32 (SIMT; "
                          "the only choice for --arch rm)")
@@ -86,7 +88,7 @@ def main(argv=None):
         y = torch.empty(4, n, device="cuda")
     t0 = time.perf_counter()
     data = {"boundary": g.gmc_train_data, "internal": g.gmc_train_data_internal,
-            "xy": g.gmc_train_data_xy}[args.model]
+            "xy": g.gmc_train_data_xy, "internal_xy": g.gmc_train_data_internal_xy}[args.model]
     data(ctx, n, args.seed, args.tau[0], args.tau[1], args.c[0], args.c[1], cond, y)
     g.gmc_synchronize(ctx)
     t_data = time.perf_counter() - t0

@@ -14,6 +14,7 @@ oracle.transport do not cross process boundaries):
               | ("equivalent_xy", weights_path, steps, integrator, box),
      "geometry": "flat" (default) | "xy" (x-y solves: the *_xy samplers),
      "internal": None | ("mlp", weights_path, steps, integrator)
+               | ("mlp_xy", weights_path, steps, integrator)  (x-y internal model)
                | ("equivalent", weights_path, steps, integrator, box)}
 "equivalent" is the network at each cell's scattering-equivalent condition in
 the training box ((tau_lo, tau_hi), (c_lo, c_hi)), the walk in the cell's own
@@ -86,7 +87,10 @@ def solve_task(task):
     internal = None
     if task.get("internal"):
         spec = task["internal"]
-        internal = OT.mlp_internal_sampler(_net(spec[1]), spec[2], spec[3], seed)
+        if spec[0] == "mlp_xy":
+            internal = OT.mlp_internal_sampler_xy(_net(spec[1]), spec[2], spec[3], seed)
+        else:
+            internal = OT.mlp_internal_sampler(_net(spec[1]), spec[2], spec[3], seed)
         if spec[0] == "equivalent":
             internal = OT.equivalent_internal_sampler(internal, OT.walk_internal_sampler(seed),
                                                       *spec[4])

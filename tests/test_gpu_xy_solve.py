@@ -190,3 +190,93 @@ def test_committed_xy_network_against_the_xy_walk():
         assert st["transmissions"] > 0
     finally:
         ctx.close()
+
+
+def _u01_f32(x):
+    # the device's float uniform: fma((float)x, 2^-32, 2^-32)
+    return (x.astype(np.float32) * np.float32(2.0 ** -32) + np.float32(2.0 ** -32)).astype(np.float32)
+
+
+def test_xy_internal_training_data_matches_oracle_walk(xctx):
+    # the x-y internal model's data: inputs from Philox (i, 0/1, tag 9), the
+    # walk on the sphere from the birth point against the oracle's x-y walk
+    # on the same counters, sample by sample
+    import oracle
+    from oracle import transport as OT
+    import paper_2512_13965_gb300 as g
+    n, seed = 4000, 43
+    cond = torch.empty(5, n, device="cuda")
+    y = torch.empty(4, n, device="cuda")
+    g.gmc_train_data_internal_xy(xctx["ctx"], n, seed, 0.3, 30.0, 0.5, 0.999, cond, y)
+    torch.cuda.synchronize()
+    c = cond.cpu().numpy()
+    yg = y.cpu().numpy().astype(np.float64)
+    raw0 = oracle.rng.philox_batch(seed, n, id0=0, event=0, tag=9)
+    raw1 = oracle.rng.philox_batch(seed, n, id0=0, event=1, tag=9)
+    lo, hi = np.log(np.float32(0.3)), np.log(np.float32(30.0))
+    np.testing.assert_allclose(c[2], lo + (hi - lo) * _u01_f32(raw0[:, 0]), rtol=1e-5, atol=1e-5)
+    X, Y = _u01_f32(raw0[:, 2]), _u01_f32(raw0[:, 3])
+    np.testing.assert_array_equal(c[0], X)
+    np.testing.assert_array_equal(c[1], Y)
+    phi = 2.0 * np.pi * _u01_f32(raw1[:, 0]).astype(np.float64)
+    mu = 2.0 * _u01_f32(raw1[:, 1]).astype(np.float64) - 1.0
+    r = np.sqrt(np.maximum(1.0 - mu * mu, 0.0))
+    tau = np.exp(c[2].astype(np.float64))
+    same = 0
+    for i in range(n):
+        w = OT.walk_one_xy(tau[i], float(c[3, i]), OT.MODE_IMPLICIT, float(X[i]) * tau[i],
+                           float(Y[i]) * tau[i], r[i] * np.cos(phi[i]), r[i] * np.sin(phi[i]),
+                           seed, i, 2)
+        if int(np.floor(yg[0, i])) == w["face"] and abs(yg[3, i] - np.log(w["s"])) < 1e-3:
+            same += 1
+            assert abs(yg[0, i] - (w["face"] + w["q"])) < 1e-3
+            assert abs(yg[1, i] - w["ux"]) < 1e-4 and abs(yg[2, i] - w["uy"]) < 1e-4
+    assert same > 0.99 * n
+    assert np.all(yg[1] ** 2 + yg[2] ** 2 <= 1.0 + 1e-6)
+
+
+def test_xy_gmc_solve_with_internal_births_per_cell(xctx):
+    # births sampled by an x-y internal model (the Kaiming test network)
+    # against the oracle's event loop with the same network, cell by cell
+    import paper_2512_13965_gb300 as g
+    ctx = xctx["ctx"]
+    # (after this test only tests on contexts of their own follow: the
+    # tests above walk their births)
+    import _oracle_pool as P
+    g.gmc_load_internal_xy_weights(ctx, xctx["path"])
+    _set(ctx, precision=g.GMC_FP32, steps=4, integrator=g.GMC_EULER, bank_capacity=1 << 16,
+         gmc_min_tau=0.0)
+    tau, c, src = _grid16(49, hi=20.0)
+    gpu = [_solve(ctx, tau, c, src, 20000, g.GMC_METHOD_GMC, 1000 + k)[0] for k in range(8)]
+    tasks = [{"grid": (tau, c, src), "n": 4000, "seed": 2000 + k,
+              "sampler": ("mlp_xy", xctx["path"], 4, "euler"),
+              "internal": ("mlp_xy", xctx["path"], 4, "euler"), "wall": None, "geometry": "xy"}
+             for k in range(8)]
+    orc = P.solve_many(tasks)
+    P.assert_per_cell(gpu, [f for f, _ in orc])
+
+
+def test_committed_xy_internal_network():
+    # the committed x-y internal model with the x-y boundary network: the
+    # x-y solve within 2 % of the x-y walk, and faster than walking births
+    import paper_2512_13965_gb300 as g
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    w = os.path.join(ROOT, "paper_2512_13965_gb300", "weights")
+    ctx = g.Context(0)
+    try:
+        g.gmc_load_xy_weights(ctx, os.path.join(w, "gmc_xy.bin"))
+        _set(ctx, precision=g.GMC_BF16, steps=8, integrator=g.GMC_MIDPOINT, gmc_min_tau=0.0)
+        tau, c, src = synth.grid_problem(n=32, seed=5, tau_range=(0.1, 500.0), block=8, source=4)
+        fa, _ = _solve(ctx, tau, c, src, 2_000_000, g.GMC_METHOD_ANALOG, 1)
+        fb, _ = _solve(ctx, tau, c, src, 2_000_000, g.GMC_METHOD_ANALOG, 2)
+        f_mc = 0.5 * (fa + fb)
+        _, st_walked = _solve(ctx, tau, c, src, 4_000_000, g.GMC_METHOD_GMC, 3)
+        g.gmc_load_internal_xy_weights(ctx, os.path.join(w, "gmc_internal_xy.bin"))
+        f, st = _solve(ctx, tau, c, src, 4_000_000, g.GMC_METHOD_GMC, 3)
+        err = np.linalg.norm(f - f_mc) / np.linalg.norm(f_mc)
+        assert err < 0.02, err
+        assert st["collisions"] < 0.1 * st_walked["collisions"], (st, st_walked)
+        assert st["seconds"] < st_walked["seconds"], (st["seconds"], st_walked["seconds"])
+    finally:
+        ctx.close()

@@ -196,6 +196,59 @@ def test_xy_solve_with_a_network_runs_and_balances(tmp_path):
                          geometry="xy")
     assert np.all(np.isfinite(f)) and f.sum() > 0
     assert abs(st["leak"] + st["absorbed"] - st["roulette_net"] - 400) < 1e-6 * 400
-    with pytest.raises(ValueError):
-        OT.solve_gmc(tau, c, src, 10, 1, OT.mlp_sampler_xy(net, 4, "euler", 1), geometry="xy",
-                     internal=OT.walk_internal_sampler(1))
+
+
+def test_xy_walked_births_through_the_internal_path_are_the_walked_births():
+    # internal = walk_internal_sampler_xy draws exactly what the births-walked
+    # solve draws: the same flux and statistics, history by history
+    tau = np.array([[0.8, 2.0], [1.4, 0.5]])
+    c = np.array([[0.9, 0.6], [0.99, 0.7]])
+    src = np.array([[1.0, 0.5], [0.0, 2.0]])
+    a, sa = OT.solve_gmc(tau, c, src, 600, 13, OT.walk_sampler_global_xy(13), geometry="xy")
+    b, sb = OT.solve_gmc(tau, c, src, 600, 13, OT.walk_sampler_global_xy(13), geometry="xy",
+                         internal=OT.walk_internal_sampler_xy(13))
+    np.testing.assert_array_equal(a, b)
+    assert sa["transmissions"] == sb["transmissions"]
+
+
+def test_xy_internal_network_decodes_into_the_disk(tmp_path):
+    # all weights zero: the output is the last bias, (p, ux, uy, ln s) =
+    # (0.5, 0.3, -0.2, 0), a point of the bottom face with an outward
+    # projected direction inside the disk, kept as it is (the flat decoding
+    # would scale it onto the circle)
+    from oracle import mlp
+    net = synth.kaiming_weights(1)
+    net["W"] = [np.zeros_like(w) for w in net["W"]]
+    net["b"][4] = np.array([0.5, 0.3, -0.2, 0.0], np.float32)
+    p = str(tmp_path / "z.bin")
+    synth.write_weights(p, net)
+    f = OT.mlp_internal_sampler_xy(mlp.read_weights(p), 2, "euler", 3)
+    ids = np.arange(4, dtype=np.uint64)
+    face, q, ux, uy, s, ev = f(np.full(4, 0.3), np.full(4, 0.6), np.full(4, 2.0), np.full(4, 0.9),
+                               ids, np.zeros(4))
+    # x(1) = x(0) + v: the noise moves the point; the direction is the
+    # velocity's integral plus noise, so check the decoding rule instead
+    y = np.stack([np.full(4, 0.5), np.full(4, 0.3), np.full(4, -0.2), np.zeros(4)])
+    d = mlp.decode_disk(mlp.read_weights(p), y)
+    np.testing.assert_allclose(d["ux"], 0.3)
+    np.testing.assert_allclose(d["uy"], -0.2)
+    assert np.all(ev == 1) and np.all(np.isfinite(s))
+
+
+def test_xy_internal_pairs_straight_chords():
+    # c_range = [0, 0]: no scattering, the exit is the straight 3-D chord from
+    # the birth point: s = chord, exit point and direction from geometry
+    cond, y = OT.internal_pairs_xy(300, 5, tau_range=(0.5, 3.0), c_range=(0.0, 0.0))
+    X, Y, tau = cond[0], cond[1], np.exp(cond[2])
+    ux, uy = y[1], y[2]
+    l = np.exp(y[3])
+    xe, ye = X * tau + l * ux, Y * tau + l * uy
+    on_wall = (np.minimum(np.minimum(xe, ye), np.minimum(tau - xe, tau - ye)) < 1e-9 * tau)
+    assert np.all(on_wall)
+    face = np.floor(y[0]).astype(int)
+    q = y[0] - face
+    pos = np.select([face == 0, face == 1, face == 2, face == 3],
+                    [xe / tau, ye / tau, 1 - xe / tau, 1 - ye / tau])
+    np.testing.assert_allclose(q, pos, atol=1e-9)
+    # the directions follow the sphere: E|u|^2 = 2/3
+    assert abs(np.mean(ux * ux + uy * uy) - 2.0 / 3.0) < 0.06
