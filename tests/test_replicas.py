@@ -107,6 +107,10 @@ def _worker_failure(rank, world, port, mode, q):
     tau, c, src = synth.grid_problem(n=4, seed=3, tau_range=(0.1, 2.0), block=2, source=2)
     f, _ = T.solve_analog(tau, c, src, 100, R.seed_for(11, rank))
     R.report(store, rank, 0)
+    # the healthy ranks start their bounded wait together, so the time one of
+    # them takes to start up (imports under load) is not read as a silence
+    store.set("test_ready_%d" % rank, "1")
+    store.wait(["test_ready_%d" % r for r in range(world) if r != 1], datetime.timedelta(seconds=60))
     t0 = time.monotonic()
     try:
         R.await_replicas(store, world, 0, 5.0)
