@@ -755,22 +755,26 @@ def run_paper(args):
     the pair trained on tau log-uniform in [0.01, 1000], with that box.
     --geometry xy: both problems in x-y geometry (3-D directions;
     transport_solve_xy / transport_solve_wall_xy), the walk on the sphere
-    against GMC with the package's x-y network and its box [0.1, 1000] x
-    [0.5, 0.999] (births walked: there is no x-y internal model)."""
+    against GMC with the package's x-y networks (boundary and internal
+    models, --weights and --internal-weights; 'none' walks the births) and
+    their box [0.1, 1000] x [0.5, 0.999]."""
     import numpy as np
     import synth
     xy = getattr(args, "geometry", "flat") == "xy"
     if args.weights is None and args.internal_weights is None and args.net_box is None:
         args.weights, args.internal_weights, args.net_box = WIDE_BOUNDARY, WIDE_INTERNAL, list(WIDE_BOX)
         if xy:
-            args.weights, args.internal_weights, args.net_box = TRAINED_XY, "none", None
+            args.weights, args.internal_weights, args.net_box = TRAINED_XY, TRAINED_INTERNAL_XY, None
     if xy:
-        xy_weights = args.weights
-        args.weights = "kaiming"  # the square-cell slot is unused by x-y solves
+        # the square-cell slots are unused by x-y solves
+        xy_weights, xy_internal = args.weights, args.internal_weights
+        args.weights, args.internal_weights = "kaiming", "none"
     g, ctx = _context(args)
     if xy:
         g.gmc_load_xy_weights(ctx, xy_weights)
-        args.weights = xy_weights
+        if xy_internal and xy_internal != "none":
+            g.gmc_load_internal_xy_weights(ctx, xy_internal)
+        args.weights, args.internal_weights = xy_weights, xy_internal
         problems = {"lattice": (synth.paper_lattice_problem(112), g.transport_solve_xy),
                     "hohlraum": (synth.paper_hohlraum_problem(112), g.transport_solve_wall_xy)}
     else:
