@@ -26,6 +26,13 @@ What it computes, in the paper's order:
         a_l = a_{l-1} + SiLU(g_l * z_l)            (l = 2, 3, 4)
     and v = W_5 a_4 + b_5. M_l is [256][5], G_l is [2][256]; with G = 0 and
     M = 0 it is a plain residual network.
+  * Rectangular cells (the condition of the section "Network Architecture
+    and Inputs" with W != H): a sixth condition component, ln(tau_y / tau_x)
+    for a cell of optical width tau_x (the depth, along the entry direction's
+    normal) and height tau_y (the entry face), after ln tau_x and c; it
+    enters the network as input column 25, after the time embedding, so the
+    first 25 columns keep the square network's meaning (a square cell has
+    aspect 0). Weight files of such networks have n_cond = 6 and 26 inputs.
   * Decoding (the fourth stage of the transport algorithm): destandardize,
     wrap p into [0,4), split it into face and position, renormalize the
     direction, make it point out of the exit face, s = exp(ln s).
@@ -46,7 +53,8 @@ so the FP64 results stay the reference for the size of the 8-bit error.
 Weight file ("GMCW" version 1, little-endian):
   char magic[4] = "GMCW"; u32 version; u32 n_layers = 5; u32 dims[6];
   u32 n_cond, n_state, n_emb, flags;
-  f32 cond_mean[5], cond_std[5], y_mean[4], y_std[4];
+  f32 cond_mean[n_cond], cond_std[n_cond], y_mean[4], y_std[4];
+  (n_cond = 5 with dims[0] = 25, or 6 with dims[0] = 26 for rectangular cells)
   then per layer l: f32 W_l[dims[l+1]][dims[l]] (out x in), f32 b_l[dims[l+1]].
   flags bit 0 marks the residual-modulated network, whose file continues
   with f32 M[3][256][5] (layers 2-4) and f32 G[3][2][256].
@@ -90,12 +98,15 @@ def read_weights(path):
     version, n_layers = struct.unpack_from("<2I", blob, 4)
     dims = struct.unpack_from("<6I", blob, 12)
     n_cond, n_state, n_emb, flags = struct.unpack_from("<4I", blob, 36)
-    if version != 1 or n_layers != 5 or tuple(dims) != DIMS or (n_cond, n_state, n_emb) != (
-            N_COND, N_STATE, N_EMB) or flags & ~FLAG_RM:
+    if (version != 1 or n_layers != 5 or n_cond not in (N_COND, N_COND + 1)
+            or tuple(dims) != (n_cond + N_STATE + N_EMB,) + DIMS[1:]
+            or (n_state, n_emb) != (N_STATE, N_EMB) or flags & ~FLAG_RM
+            or (n_cond != N_COND and flags & FLAG_RM)):
         raise ValueError("unsupported weight file layout")
     off = 52
-    stats = np.frombuffer(blob, dtype="<f4", count=18, offset=off).astype(np.float64)
-    off += 18 * 4
+    ns = 2 * n_cond + 2 * N_STATE
+    stats = np.frombuffer(blob, dtype="<f4", count=ns, offset=off).astype(np.float64)
+    off += ns * 4
     W, b = [], []
     for l in range(5):
         n_out, n_in = dims[l + 1], dims[l]
@@ -117,7 +128,9 @@ def read_weights(path):
             off += 2 * HIDDEN * 4
     if off != len(blob):
         raise ValueError("weight file has trailing or missing bytes")
-    return Net(W, b, stats[0:5], stats[5:10], stats[10:14], stats[14:18], M, G)
+    k = n_cond
+    return Net(W, b, stats[0:k], stats[k:2 * k], stats[2 * k:2 * k + 4], stats[2 * k + 4:2 * k + 8],
+               M, G)
 
 
 def time_embedding(t):
@@ -133,7 +146,7 @@ def silu(z):
 
 
 def standardize_cond(net, cond):
-    """cond: [5, B] raw features -> [B, 5] standardized."""
+    """cond: [n_cond, B] raw features -> [B, n_cond] standardized."""
     cond = np.asarray(cond, dtype=np.float64)
     return ((cond.T - net.cond_mean) / net.cond_std)
 
@@ -173,11 +186,18 @@ def quantized_e4m3(net):
     return q
 
 
+def network_input(cn, x, t):
+    """Layer-1 input [cn(5), x(4), emb(t)(16)] and, for rectangular cells
+    (cn with 6 columns), the aspect component as column 25."""
+    return np.concatenate([cn[:, :N_COND], x, time_embedding(t), cn[:, N_COND:]], axis=1)
+
+
 def velocity(net, cn, x, t):
-    """v_theta(x, t | c): cn [B,5] standardized condition, x [B,4], t scalar or [B]."""
+    """v_theta(x, t | c): cn [B,5] (or [B,6] for rectangular cells)
+    standardized condition, x [B,4], t scalar or [B]."""
     B = x.shape[0]
     t = np.broadcast_to(np.asarray(t, dtype=np.float64), (B,))
-    h = np.concatenate([cn, x, time_embedding(t)], axis=1)
+    h = network_input(cn, x, t)
     if getattr(net, "rm", False):
         return velocity_rm(net, cn, h)
     e4m3 = getattr(net, "e4m3_inputs", False)

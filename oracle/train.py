@@ -26,7 +26,7 @@ applied to every weight and bias.
 """
 import numpy as np
 
-from .mlp import time_embedding
+from .mlp import network_input
 
 
 def _sig(z):
@@ -35,7 +35,7 @@ def _sig(z):
 
 def forward_cache(W, b, cn, x, t):
     """Forward pass keeping pre-activations; returns (v, cache)."""
-    h = np.concatenate([cn, x, time_embedding(t)], axis=1)
+    h = network_input(cn, x, t)
     acts, pres = [h], []
     for l in range(4):
         z = h @ W[l].T + b[l]
@@ -49,7 +49,8 @@ def forward_cache(W, b, cn, x, t):
 def cfm_loss_grad(W, b, cn, x1, x0, t):
     """Returns (loss, gW list, gb list) for one batch (all arrays FP64).
 
-    cn [B,5] standardized conditions, x1 [B,4] standardized targets,
+    cn [B,5] standardized conditions ([B,6] for rectangular cells: W[0]
+    then has 26 columns), x1 [B,4] standardized targets,
     x0 [B,4] noise, t [B] flow times.
     """
     W = [np.asarray(w, np.float64) for w in W]
@@ -90,7 +91,7 @@ def adamw_step(p, g, m, v, k, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, wd=0.01):
 def forward_cache_rm(P, cn, x, t):
     """Forward pass of the residual-modulated network (P: dict of W, b, M, G
     as oracle.mlp.Net holds them) keeping every block's input, z and g."""
-    h = np.concatenate([cn, x, time_embedding(t)], axis=1)
+    h = network_input(cn, x, t)
     z1 = h @ P["W"][0].T + P["b"][0]
     a = z1 * _sig(z1)
     blocks = []

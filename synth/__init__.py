@@ -92,6 +92,32 @@ def kaiming_weights(seed=1):
             "y_mean": np.zeros(4, np.float32), "y_std": np.ones(4, np.float32)}
 
 
+def kaiming_weights_rect(seed=1):
+    """Kaiming-normal weights of the network for rectangular cells: 26
+    inputs (the aspect component ln(tau_y / tau_x) as input column 25), zero
+    biases, identity standardization of the 6 condition components."""
+    net = kaiming_weights(seed)
+    g = generator(seed + 3000)
+    net["W"][0] = (g.standard_normal((256, 26)) * np.sqrt(2.0 / 26)).astype(np.float32)
+    net["cond_mean"] = np.zeros(6, np.float32)
+    net["cond_std"] = np.ones(6, np.float32)
+    return net
+
+
+def rect_conditions(n, seed, tau_range=(0.1, 1000.0), aspect_range=(0.25, 4.0),
+                    c_range=(0.5, 0.999)):
+    """Conditions of rectangular cells [6, n] float32: (xi, cos, sin,
+    ln tau_x, c, ln(tau_y / tau_x)), tau_x log-uniform, the aspect
+    tau_y / tau_x log-uniform in aspect_range, entries as cell_entries."""
+    e = cell_entries(n, seed)
+    tau, c = materials(n, seed + 7919, tau_range, c_range)
+    g = generator(seed + 104729)
+    la = g.uniform(np.log(aspect_range[0]), np.log(aspect_range[1]), n)
+    cond = np.stack([e["xi"], e["cos"], e["sin"], np.log(tau).astype(np.float32), c,
+                     la.astype(np.float32)])
+    return np.ascontiguousarray(cond, dtype=np.float32)
+
+
 def rm_weights(seed=1, m_std=0.0, g_std=0.0, base=None):
     """Weights of the residual-modulated network: the layers of `base` (default
     `kaiming_weights(seed)`), condition shifts M[3][256][5] ~ N(0, m_std^2)
@@ -123,11 +149,12 @@ def write_weights(path, net):
     with keys "M" and "G" (`rm_weights()`) flag 1 and those arrays follow the
     layers: M[3][256][5], then G[3][2][256]."""
     rm = "M" in net
+    n_cond = len(net["cond_mean"])  # 6: a network for rectangular cells
     with open(path, "wb") as f:
         f.write(b"GMCW")
         f.write(struct.pack("<2I", 1, 5))
-        f.write(struct.pack("<6I", *DIMS))
-        f.write(struct.pack("<4I", 5, 4, 16, 1 if rm else 0))
+        f.write(struct.pack("<6I", n_cond + 20, *DIMS[1:]))
+        f.write(struct.pack("<4I", n_cond, 4, 16, 1 if rm else 0))
         for k in ("cond_mean", "cond_std", "y_mean", "y_std"):
             f.write(np.asarray(net[k], dtype="<f4").tobytes())
         for l in range(5):

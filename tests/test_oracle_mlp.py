@@ -307,3 +307,42 @@ def test_evaluation_counts_and_times():
         h = 1.0 / steps
         nodes = {round(k * h / 2, 12) for k in range(2 * steps + 1)}
         assert all(0.0 <= t <= 1.0 and round(t, 12) in nodes for t in seen)
+
+
+def test_rect_network_reads_the_aspect_as_input_25(tmp_path):
+    # a network for rectangular cells: 6 condition components, the aspect
+    # ln(tau_y / tau_x) entering as input column 25 (after the embedding).
+    # Only W1[0, 25] and the output chain through unit 0 are non-zero, so
+    # v_2 = silu^4(a * standardized aspect) and one Euler step adds it.
+    net = synth.kaiming_weights_rect(1)
+    net["W"] = [np.zeros_like(w) for w in net["W"]]
+    net["cond_mean"] = np.array([0, 0, 0, 0, 0, 0.5], np.float32)
+    net["cond_std"] = np.array([1, 1, 1, 1, 1, 2.0], np.float32)
+    a = float(np.float32(0.8))
+    net["W"][0][0, 25] = a
+    for l in (1, 2, 3):
+        net["W"][l][0, 0] = 1.0
+    net["W"][4][2, 0] = 1.0
+    o = _load(tmp_path, net, "rect.bin")
+    assert o.W[0].shape == (256, 26) and o.cond_mean.shape == (6,)
+    cond = synth.rect_conditions(6, 3)
+    z = synth.gaussian_noise(6, 4)
+    y = mlp.sample(o, cond, z, 1, "euler")
+    for i in range(6):
+        u = (float(cond[5, i]) - 0.5) / 2.0
+        expect = float(z[2, i]) + _silu(_silu(_silu(_silu(a * u))))
+        assert abs(y[2, i] - expect) < 1e-13
+    # a square-cell file and a rect file of the same first 25 columns agree
+    # on squares (aspect 0 with zero mean)
+    sq = synth.kaiming_weights(2)
+    rc = dict(sq)
+    rc["W"] = list(sq["W"])
+    rc["W"][0] = np.concatenate([sq["W"][0], np.full((256, 1), 0.3, np.float32)], axis=1)
+    rc["cond_mean"] = np.zeros(6, np.float32)
+    rc["cond_std"] = np.ones(6, np.float32)
+    o_sq, o_rc = _load(tmp_path, sq, "sq.bin"), _load(tmp_path, rc, "rc.bin")
+    cond5, _, _ = synth.sampler_conditions(8, 5)
+    cond6 = np.concatenate([cond5, np.zeros((1, 8), np.float32)])
+    z = synth.gaussian_noise(8, 6)
+    np.testing.assert_allclose(mlp.sample(o_rc, cond6, z, 3, "euler"),
+                               mlp.sample(o_sq, cond5, z, 3, "euler"), atol=1e-12)

@@ -105,3 +105,26 @@ def test_moments_and_sigma_bar():
     runs = g.standard_normal((5, 30))
     expect = np.mean(np.std(runs, axis=0, ddof=1))
     assert abs(ostats.sigma_bar(runs) - expect) < 1e-14
+
+
+def test_rect_network_gradient_by_central_differences():
+    # 6 condition components: W1 has 26 columns, the aspect in column 25
+    g = np.random.default_rng(4)
+    net = synth.kaiming_weights_rect(3)
+    W = [w.astype(np.float64) * 0.5 for w in net["W"]]
+    b = [g.standard_normal(v.shape) * 0.1 for v in net["b"]]
+    B = 6
+    cn = g.standard_normal((B, 6))
+    x1, x0, t = g.standard_normal((B, 4)), g.standard_normal((B, 4)), g.random(B)
+    _, gW, _ = train.cfm_loss_grad(W, b, cn, x1, x0, t)
+    assert gW[0].shape == (256, 26)
+    h = 1e-6
+    for j in (0, 7, 25):
+        for i in g.integers(256, size=4):
+            Wp = [w.copy() for w in W]
+            Wm = [w.copy() for w in W]
+            Wp[0][i, j] += h
+            Wm[0][i, j] -= h
+            fd = (train.cfm_loss_grad(Wp, b, cn, x1, x0, t)[0]
+                  - train.cfm_loss_grad(Wm, b, cn, x1, x0, t)[0]) / (2 * h)
+            assert abs(fd - gW[0][i, j]) < 1e-6 * max(1.0, abs(fd))
