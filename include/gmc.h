@@ -193,6 +193,14 @@ gmc_status gmc_normals(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uin
  * c_4 = c). It runs at GMC_FP32 and at GMC_BF16 with GMC_KERNEL_TILE;
  * GMC_FP8 and GMC_KERNEL_PAIR give GMC_EINVAL in gmc_transmit, solves and
  * serving. Other flag bits give GMC_EFORMAT.
+ * n_cond = 6 with dims[0] = 26 is a network for rectangular cells (section
+ * "Network Architecture and Inputs": the condition holds both optical
+ * dimensions): the sixth condition component ln(tau_y / tau_x) enters as
+ * input column 25, after the time embedding, and cond_mean / cond_std have 6
+ * entries. It samples single cells (gmc_transmit with [6][n] conditions) at
+ * GMC_FP32 and GMC_BF16 with GMC_KERNEL_TILE; solves, serving and
+ * gmc_transmit_noalloc, whose cells are squares, refuse it with GMC_EINVAL,
+ * and it cannot carry flag 1.
  */
 gmc_status gmc_load_weights(gmc_ctx *ctx, const char *path);
 /* Same, from a host buffer holding the file's bytes. */
@@ -239,7 +247,10 @@ gmc_status gmc_sample_internal_xy(gmc_ctx *ctx, int64_t n, const float *cond, co
 /*
  * Samples n exit states (Eq. 8, Eq. 11) with the loaded network.
  *  cond    [5][n] float: xi, cos theta_in, sin theta_in, ln tau, c (raw,
- *          standardized inside with the file's cond_mean / cond_std).
+ *          standardized inside with the file's cond_mean / cond_std);
+ *          [6][n] for a network of rectangular cells (its file has n_cond = 6):
+ *          xi, cos, sin, ln tau_x, c, ln(tau_y / tau_x) for a cell of optical
+ *          width tau_x and height tau_y entered on its left face.
  *  noise   [4][n] float x(0), or null: then x(0) is drawn as gmc_normals with
  *          ids id0+i, event 0, tag 2.
  *  steps   ODE steps K >= 1 (h = 1/K, t_k = k h); integrator gmc_integrator.
@@ -476,7 +487,8 @@ typedef struct gmc_train_config {
     double weight_decay; /* decoupled weight decay, e.g. 0.01 */
     uint64_t seed;       /* Philox key of the batch draws (tag 6) */
     int precision;       /* GMC_FP32: SIMT FP32 GEMMs, FP32 activations (the only
-                            choice for the residual-modulated network); GMC_BF16: the
+                            choice for the residual-modulated network and for a
+                            network of rectangular cells); GMC_BF16: the
                             tcgen05 step (four kernels per step): BF16 activations,
                             SiLU' factors and input gradients between layers, FP32
                             accumulation, weight and bias gradients summed in FP32 in
@@ -533,6 +545,21 @@ gmc_status gmc_train_data_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_l
 gmc_status gmc_train_data_internal_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo,
                                       float tau_hi, float c_lo, float c_hi, float *cond, float *y);
 /*
+ * Training data of the boundary model for rectangular cells (section
+ * "Network Architecture and Inputs": the condition holds both optical
+ * dimensions): for sample i, Philox block (i, 0, tag 10) gives ln tau_x
+ * uniform in [ln tau_lo, ln tau_hi], c uniform in [c_lo, c_hi], xi uniform and
+ * sin theta = 2 u - 1; (i, 1, tag 10) the aspect, ln(tau_y / tau_x) uniform in
+ * [ln aspect_lo, ln aspect_hi]. The implicit-capture walk in the cell
+ * [0, tau_x] x [0, tau_y] runs from (0, xi tau_y), flights from event 2.
+ * cond [6][n] = (xi, cos, sin, ln tau_x, c, ln(tau_y / tau_x)), y [4][n] =
+ * (p, cos, sin, ln s), q normalized per face: device memory. A network for
+ * rectangular cells (n_cond 6) trains on it with precision GMC_FP32.
+ */
+gmc_status gmc_train_data_rect(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, float tau_hi,
+                               float aspect_lo, float aspect_hi, float c_lo, float c_hi, float *cond,
+                               float *y);
+/*
  * Starts training on the device dataset (cond, y as gmc_train_data writes;
  * the caller keeps them alive while training). Standardization statistics
  * (mean and standard deviation of the 5 condition and 4 target components)
@@ -555,10 +582,12 @@ gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses);
 gmc_status gmc_train_set_lr(gmc_ctx *ctx, double lr);
 /*
  * Loss and gradient of Eq. 9 at the current master weights for an explicit
- * batch (host arrays): cn [B][5] standardized conditions, x1 [B][4]
- * standardized targets, x0 [B][4] noise, t [B]. grad: host array of
- * gmc_train_param_count() floats in the order W1 [256][32] (input columns
- * 25..31 are padding), b1, W2, b2, W3, b3, W4, b4, W5 [4][256], b5.
+ * batch (host arrays): cn [B][5] standardized conditions ([B][6] for a
+ * network of rectangular cells), x1 [B][4] standardized targets, x0 [B][4]
+ * noise, t [B]. grad: host array of gmc_train_param_count_ctx() floats in
+ * the order W1 [256][32] (input columns 25..31 are padding; column 25 is the
+ * aspect of a rectangular-cell network), b1, W2, b2, W3, b3, W4, b4,
+ * W5 [4][256], b5, then the residual-modulated network's M and G.
  * B must not exceed the configured batch.
  */
 gmc_status gmc_train_grad(gmc_ctx *ctx, int64_t B, const float *cn, const float *x1,

@@ -119,6 +119,8 @@ def _load():
                               ctypes.c_float, P, P],
         "gmc_train_data_internal_xy": [P, i64, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, P, P],
+        "gmc_train_data_rect": [P, i64, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P],
         "gmc_train_begin": [P, i64, P, P, ctypes.POINTER(gmc_train_config)],
         "gmc_train_steps": [P, i64, P],
         "gmc_train_set_lr": [P, ctypes.c_double],
@@ -222,8 +224,8 @@ class Context:
         return self.handle
 
 
-def _sampler_args(n, cond, noise):
-    return _arr(cond, 4, 5 * n, "cond"), _arr(noise, 4, 4 * n, "noise")
+def _sampler_args(n, cond, noise, n_cond=5):
+    return _arr(cond, 4, n_cond * n, "cond"), _arr(noise, 4, 4 * n, "noise")
 
 
 def _sampler_out(n, y_raw, exit):
@@ -337,8 +339,10 @@ def gmc_sample_internal_xy(ctx, n, cond, noise, seed, id0, steps, integrator, pr
                                                 *_sampler_out(n, y_raw, exit)))
 
 
-def gmc_transmit(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw, exit):
-    return ctx.check(lib.gmc_transmit(ctx.handle, n, *_sampler_args(n, cond, noise), seed, id0,
+def gmc_transmit(ctx, n, cond, noise, seed, id0, steps, integrator, precision, y_raw, exit,
+                 n_cond=5):
+    """n_cond: rows of cond, 5, or 6 for a network of rectangular cells."""
+    return ctx.check(lib.gmc_transmit(ctx.handle, n, *_sampler_args(n, cond, noise, n_cond), seed, id0,
                                       steps, integrator, precision,
                                       *_sampler_out(n, y_raw, exit)))
 
@@ -423,6 +427,12 @@ def gmc_train_data_xy(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
                                            _arr(cond, 4, 5 * n, "cond"), _arr(y, 4, 4 * n, "y")))
 
 
+def gmc_train_data_rect(ctx, n, seed, tau_lo, tau_hi, aspect_lo, aspect_hi, c_lo, c_hi, cond, y):
+    return ctx.check(lib.gmc_train_data_rect(ctx.handle, n, seed, tau_lo, tau_hi, aspect_lo,
+                                             aspect_hi, c_lo, c_hi, _arr(cond, 4, 6 * n, "cond"),
+                                             _arr(y, 4, 4 * n, "y")))
+
+
 def gmc_train_data_internal_xy(ctx, n, seed, tau_lo, tau_hi, c_lo, c_hi, cond, y):
     return ctx.check(lib.gmc_train_data_internal_xy(ctx.handle, n, seed, tau_lo, tau_hi, c_lo, c_hi,
                                                     _arr(cond, 4, 5 * n, "cond"),
@@ -442,10 +452,11 @@ def gmc_train_set_lr(ctx, lr):
     return ctx.check(lib.gmc_train_set_lr(ctx.handle, lr))
 
 
-def gmc_train_grad(ctx, B, cn, x1, x0, t, grad):
+def gmc_train_grad(ctx, B, cn, x1, x0, t, grad, n_cond=5):
+    """n_cond: columns of cn, 5, or 6 for a network of rectangular cells."""
     loss = ctypes.c_double()
     P = gmc_train_param_count_ctx(ctx)
-    ctx.check(lib.gmc_train_grad(ctx.handle, B, _arr(cn, 4, 5 * B, "cn"), _arr(x1, 4, 4 * B, "x1"),
+    ctx.check(lib.gmc_train_grad(ctx.handle, B, _arr(cn, 4, n_cond * B, "cn"), _arr(x1, 4, 4 * B, "x1"),
                                  _arr(x0, 4, 4 * B, "x0"), _arr(t, 4, B, "t"),
                                  ctypes.byref(loss), _arr(grad, 4, P, "grad")))
     return loss.value

@@ -355,20 +355,22 @@ gmc_status gmc_normals(gmc_ctx *ctx, int64_t n, uint64_t seed, uint64_t id0, uin
 
 namespace gmc {
 gmc_status check_net_path(gmc_ctx *ctx, const NetDev &N, int precision, int kernel, const char *who) {
-  if (!N.rm || precision == GMC_FP32 || (precision == GMC_BF16 && kernel == GMC_KERNEL_TILE))
+  const bool special = N.rm || N.stats.ncond != kCond;
+  if (!special || precision == GMC_FP32 || (precision == GMC_BF16 && kernel == GMC_KERNEL_TILE))
     return GMC_OK;
   return set_error(ctx, GMC_EINVAL,
-                   "%s: the residual-modulated network runs at GMC_FP32, or GMC_BF16 with "
-                   "GMC_KERNEL_TILE", who);
+                   "%s: the %s network runs at GMC_FP32, or GMC_BF16 with GMC_KERNEL_TILE", who,
+                   N.rm ? "residual-modulated" : "rectangular-cell");
 }
 
 // Parses a GMCW version 1 blob into N and uploads its FP32, BF16 and FP8 copies.
 // Flag 1 (the residual-modulated network) adds M[3][256][5] and G[3][2][256]
-// after the layers.
+// after the layers. n_cond = 6 with 26 inputs is a network for rectangular
+// cells (the aspect as input column 25; not with flag 1).
 // Nothing of N changes unless the blob parses; N stays marked unloaded from
 // the first change until every device copy is in place.
 gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
-  static const uint32_t dims_ok[6] = {25, 256, 256, 256, 256, 4};
+  static const uint32_t dims_ok[6] = {kIn, 256, 256, 256, 256, 4};
   if (ctx->server) return set_error(ctx, GMC_EBUSY, "loading weights: the server is running");
   Reader rd{(const unsigned char *)blob, nbytes};
   if (nbytes < 4 || std::memcmp(blob, "GMCW", 4) != 0)
@@ -379,14 +381,18 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   for (int i = 0; i < 6 && ok; ++i) ok = rd.u32(&dims[i]);
   ok = ok && rd.u32(&ncond) && rd.u32(&nstate) && rd.u32(&nemb) && rd.u32(&flags);
   if (!ok) return set_error(ctx, GMC_EFORMAT, "weight file: truncated header");
-  if (version != 1 || nl != 5 || ncond != 5 || nstate != 4 || nemb != 16 || (flags & ~kFlagRM))
+  if (version != 1 || nl != 5 || (ncond != kCond && ncond != kCondRect) || nstate != 4 ||
+      nemb != 16 || (flags & ~kFlagRM) || (ncond != kCond && (flags & kFlagRM)))
     return set_error(ctx, GMC_EFORMAT, "weight file: unsupported version, layout or flags");
   const bool rm = (flags & kFlagRM) != 0;
+  const int nc = (int)ncond, nin = nc + kState + kEmb;
   for (int i = 0; i < 6; ++i)
-    if (dims[i] != dims_ok[i])
-      return set_error(ctx, GMC_EFORMAT, "weight file: layer dims must be 25-256-256-256-256-4");
-  float st[18];
-  if (!rd.f32(st, 18)) return set_error(ctx, GMC_EFORMAT, "weight file: truncated statistics");
+    if (dims[i] != (i == 0 ? (uint32_t)nin : dims_ok[i]))
+      return set_error(ctx, GMC_EFORMAT,
+                       "weight file: layer dims must be 25-256-256-256-256-4 (26-... with n_cond 6)");
+  const int nst = 2 * nc + 2 * kState;
+  float st[2 * kCondRect + 2 * kState];
+  if (!rd.f32(st, nst)) return set_error(ctx, GMC_EFORMAT, "weight file: truncated statistics");
   const size_t wl = sizeof(N.host_w[0]) / sizeof(float), bl = sizeof(N.host_b[0]) / sizeof(float);
   std::vector<float> tw(5 * wl, 0.0f), tb(5 * bl, 0.0f);
   for (int l = 0; l < 5; ++l) {
@@ -397,9 +403,9 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   if (rm && (!rd.f32(tm.data(), tm.size()) || !rd.f32(tg.data(), tg.size())))
     return set_error(ctx, GMC_EFORMAT, "weight file: truncated modulation arrays");
   if (rd.off != nbytes) return set_error(ctx, GMC_EFORMAT, "weight file: trailing bytes");
-  for (int k = 0; k < 5; ++k)
-    if (!(st[5 + k] > 0.0f)) return set_error(ctx, GMC_EFORMAT, "weight file: cond_std must be > 0");
-  for (int k = 0; k < 18; ++k)
+  for (int k = 0; k < nc; ++k)
+    if (!(st[nc + k] > 0.0f)) return set_error(ctx, GMC_EFORMAT, "weight file: cond_std must be > 0");
+  for (int k = 0; k < nst; ++k)
     if (!std::isfinite(st[k])) return set_error(ctx, GMC_EFORMAT, "weight file: non-finite statistics");
 
   N.loaded = false;
@@ -408,17 +414,19 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
     std::memcpy(N.host_b[l], &tb[l * bl], bl * sizeof(float));
   }
   N.rm = rm;
+  N.nin = nin;
   std::memcpy(N.host_m, tm.data(), tm.size() * sizeof(float));
   std::memcpy(N.host_g, tg.data(), tg.size() * sizeof(float));
   NetStats ns;
-  for (int k = 0; k < 5; ++k) {
-    ns.cond_mean[k] = st[k];
-    ns.cond_inv_std[k] = 1.0f / st[5 + k];
+  for (int k = 0; k < kCondRect; ++k) {
+    ns.cond_mean[k] = k < nc ? st[k] : 0.0f;
+    ns.cond_inv_std[k] = k < nc ? 1.0f / st[nc + k] : 1.0f;
   }
   for (int k = 0; k < 4; ++k) {
-    ns.y_mean[k] = st[10 + k];
-    ns.y_std[k] = st[14 + k];
+    ns.y_mean[k] = st[2 * nc + k];
+    ns.y_std[k] = st[2 * nc + 4 + k];
   }
+  ns.ncond = nc;
   // the x-y geometry slots decode into the unit disk
   ns.disk = (&N == &ctx->xy || &N == &ctx->internal_xy) ? 1 : 0;
 
@@ -438,7 +446,7 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
   float *mt = p; p += nm;
   float *gg = p; p += ng;
   for (int c = 0; c < 256; ++c)
-    for (int k = 0; k < 25; ++k) w1t[k * 256 + c] = N.host_w[0][c * 25 + k];
+    for (int k = 0; k < nin; ++k) w1t[k * 256 + c] = N.host_w[0][c * nin + k];
   std::memcpy(b1, N.host_b[0], 256 * 4);
   for (int l = 0; l < 3; ++l) {
     for (int c = 0; c < 256; ++c)
@@ -476,8 +484,8 @@ gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
     const size_t tcb = tc_packed_bytes(false), tcb8 = tc_packed_bytes(true);
     std::vector<unsigned char> packed(tcb), packed8(tcb8);
     std::vector<float> bias(5 * 256, 0.0f), scale(3 * 256, 0.0f);
-    tc_pack_host(N.host_w, N.host_b, packed.data(), bias.data(), rm ? N.host_m : nullptr);
-    tc_pack_host_fp8(N.host_w, N.host_b, packed8.data(), bias.data(), scale.data());
+    tc_pack_host(N.host_w, N.host_b, packed.data(), bias.data(), rm ? N.host_m : nullptr, nin);
+    tc_pack_host_fp8(N.host_w, N.host_b, packed8.data(), bias.data(), scale.data(), nin);
     if (!N.d_tc) GMC_CUDA_TRY(ctx, cudaMalloc(&N.d_tc, tcb));
     if (!N.d_tc8) GMC_CUDA_TRY(ctx, cudaMalloc(&N.d_tc8, tcb8));
     if (!N.d_tc_bias) GMC_CUDA_TRY(ctx, cudaMalloc(&N.d_tc_bias, 5 * 256 * sizeof(float)));
@@ -593,7 +601,7 @@ gmc_status transmit_net(gmc_ctx *ctx, const NetDev &N, int64_t n, const float *c
     return GMC_EINVAL;
   cudaSetDevice(ctx->device);
   Arg a_cond, a_noise, a_y, a_exit;
-  a_cond.user = cond; a_cond.bytes = (size_t)n * 5 * 4;
+  a_cond.user = cond; a_cond.bytes = (size_t)n * N.stats.ncond * 4;
   a_noise.user = noise; a_noise.bytes = (size_t)n * 4 * 4;
   a_y.user = y_raw; a_y.bytes = (size_t)n * 4 * 4;
   a_exit.user = exit; a_exit.bytes = (size_t)n * 4 * 4;

@@ -15,6 +15,9 @@
 namespace gmc {
 
 constexpr int kCond = 5, kState = 4, kEmb = 16, kIn = kCond + kState + kEmb, kHidden = 256;
+// a network for rectangular cells has a sixth condition component, the
+// aspect ln(tau_y / tau_x), as input column kIn (after the time embedding)
+constexpr int kCondRect = kCond + 1;
 constexpr int kIn1Pad = 32;  // layer-1 input padded to 32 columns
 constexpr int kMaxDevices = 64;  // per-device launch caches (attributes, occupancy)
 constexpr float kSMin = 1e-7f;
@@ -31,9 +34,12 @@ struct NetF32 {
 };
 constexpr uint32_t kFlagRM = 1u;  // weight-file flag of the residual-modulated network
 
-// Standardization of the file: cond_mean[5], cond_std[5], y_mean[4], y_std[4].
+// Standardization of the file: cond_mean[ncond], cond_std[ncond], y_mean[4],
+// y_std[4]; ncond = 5, or 6 for a network of rectangular cells (entries past
+// ncond are 0 and 1).
 struct NetStats {
-  float cond_mean[kCond], cond_inv_std[kCond], y_mean[kState], y_std[kState];
+  float cond_mean[kCondRect], cond_inv_std[kCondRect], y_mean[kState], y_std[kState];
+  int ncond;
   int disk;  // exits decoded for x-y geometry (direction projected on the unit disk)
 };
 
@@ -59,6 +65,7 @@ struct Buffer {
 struct NetDev {
   bool loaded = false;
   bool rm = false;  // residual-modulated network (weight-file flag 1)
+  int nin = kIn;    // layer-1 inputs: 25, or 26 for rectangular cells
   uint64_t generation = 0;  // counts loads: cached per-network data keys on it
   float host_w[5][256 * 256];  // W_l[out][in] as in the file (unused tail for small layers)
   float host_b[5][256];
@@ -185,10 +192,12 @@ cudaError_t launch_analog_xy(cudaStream_t stream, int64_t n, const float *xi, co
 size_t tc_packed_bytes(bool fp8);
 // M: the condition shifts of the residual-modulated network (null for the
 // MLP), packed into the bias blocks of layers 2-4.
+// nin: layer-1 inputs (25, or 26 with the aspect of rectangular cells);
+// W[0] holds W1 as [256][nin].
 void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
-                  float *bias_host, const float (*M)[256 * kCond] = nullptr);
+                  float *bias_host, const float (*M)[256 * kCond] = nullptr, int nin = kIn);
 void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
-                      float *bias_host, float *scale_host);
+                      float *bias_host, float *scale_host, int nin = kIn);
 // packed: from tc_pack_host (fp8_scale null) or tc_pack_host_fp8 (fp8_scale =
 // its [3][256] scales on the device). kernel: gmc_sampler_kernel of the BF16
 // path (GMC_KERNEL_PAIR: sampler_pair.cu). bias1_ready: bias1_scratch already

@@ -80,6 +80,9 @@ extern "C" gmc_status gmc_transmit_noalloc(gmc_ctx *ctx, int64_t n, const float 
     return set_error(ctx, GMC_ENOWEIGHTS, "gmc_transmit_noalloc: no weights loaded");
   if (check_net_path(ctx, ctx->net, GMC_BF16, ctx->cfg.sampler_kernel, "gmc_transmit_noalloc") != GMC_OK)
     return GMC_EINVAL;
+  if (ctx->net.stats.ncond != kCond)
+    return set_error(ctx, GMC_EINVAL, "gmc_transmit_noalloc: takes [5][n] conditions (not a "
+                                      "rectangular-cell network)");
   if (n == 0) return GMC_OK;
   if (!cond || (!y_raw && !exit)) return set_error(ctx, GMC_EINVAL, "gmc_transmit_noalloc: null array");
   cudaError_t e = cudaSetDevice(ctx->device);

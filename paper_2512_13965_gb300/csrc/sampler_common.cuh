@@ -96,13 +96,24 @@ __device__ __forceinline__ uint32_t sw32(uint32_t base, int r, int c) {
   return base + (uint32_t)((r >> 3) * 256 + (r & 7) * 32 + ((c ^ ((r >> 2) & 1)) << 4));
 }
 
-// Layer-1 operand row: [x_hi0..3, x_lo0..3 | cn0..cn4, 1, 1, 0] in BF16. The
+// Layer-1 operand row: [x_hi0..3, x_lo0..3 | cn0..cn4, 1, 1, cn5] in BF16
+// (cn5: the aspect of a rectangular cell, 0 for square-cell networks). The
 // normalized condition (second 16 bytes) is written once per tile; every
 // evaluation rewrites only the ODE state (first 16 bytes). Layer 1's weights
-// are zero in columns 13-14; the bias blocks of layers 2-4 use them.
-__device__ __forceinline__ void write_a1_cond(uint32_t a_base, int r, const float (&cn)[kCond]) {
+// are zero in columns 13-14; the bias blocks of layers 2-4 use them (and
+// have zero in column 15).
+__device__ __forceinline__ void write_a1_cond(uint32_t a_base, int r, const float (&cn)[kCondRect]) {
   st_shared_v4(sw32(a_base, r, 1), pack_bf16x2(cn[0], cn[1]), pack_bf16x2(cn[2], cn[3]),
-               pack_bf16x2(cn[4], 1.0f), pack_bf16x2(1.0f, 0.0f));
+               pack_bf16x2(cn[4], 1.0f), pack_bf16x2(1.0f, cn[5]));
+}
+
+// Standardized condition of row gi (< n) into cn (zeros past st.ncond and
+// for rows past n).
+__device__ __forceinline__ void load_cond(const float *cond, const NetStats &st, int64_t n,
+                                          int64_t gi, bool valid, float (&cn)[kCondRect]) {
+#pragma unroll
+  for (int k = 0; k < kCondRect; ++k)
+    cn[k] = valid && k < st.ncond ? (cond[k * n + gi] - st.cond_mean[k]) * st.cond_inv_std[k] : 0.0f;
 }
 
 __device__ __forceinline__ void write_a1_x(uint32_t a_base, int r, const float (&x)[4]) {

@@ -328,10 +328,8 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_pair_kernel(Params P) {
         if (own == T) {
           const int64_t gi = (2 * pr + T) * (2 * PM) + (int64_t)rank * PM + r;
           const bool valid = gi < P.n;
-          float cn[kCond];
-#pragma unroll
-          for (int k = 0; k < kCond; ++k)
-            cn[k] = valid ? (P.cond[k * P.n + gi] - P.st.cond_mean[k]) * P.st.cond_inv_std[k] : 0.0f;
+          float cn[kCondRect];
+          load_cond(P.cond, P.st, P.n, gi, valid, cn);
           if (!valid) {
 #pragma unroll
             for (int dd = 0; dd < 4; ++dd) x[dd] = 0.0f;

@@ -30,7 +30,7 @@ struct Smem {
   float xm[R][4];
   float ka[R][4];
   float v[R][4];
-  float cn[R][kCond];
+  float cn[R][kCondRect];  // [5]: the aspect of a rectangular cell (0 otherwise)
   float emb[kEmb];
 };
 
@@ -124,13 +124,15 @@ __device__ void velocity(Smem &s, const NetF32 &net, const float (*xs)[4], float
   const int tid = threadIdx.x;
   if (tid < kEmb) s.emb[tid] = time_embedding(tid, t);
   __syncthreads();
-  // layer-1 input [cn(5), x(4), emb(16), 0 x 7]
+  // layer-1 input [cn(5), x(4), emb(16), aspect, 0 x 6] (the aspect is 0 for
+  // a square-cell network, whose w1t row 25 is zero)
   for (int e = tid; e < R * kIn1Pad; e += THREADS) {
     const int r = e / kIn1Pad, k = e % kIn1Pad;
     float v = 0.0f;
     if (k < kCond) v = s.cn[r][k];
     else if (k < kCond + kState) v = xs[r][k - kCond];
     else if (k < kIn) v = s.emb[k - kCond - kState];
+    else if (k == kIn) v = s.cn[r][kCond];
     s.act[r][k] = v;
   }
   dense_silu(s, net.w1t, net.b1, kIn1Pad);
@@ -174,7 +176,8 @@ __global__ void __launch_bounds__(THREADS) sampler_f32_kernel(
     const int64_t g = row0 + tid;
     if (g < n) {
 #pragma unroll
-      for (int k = 0; k < kCond; ++k) s.cn[tid][k] = (cond[k * n + g] - st.cond_mean[k]) * st.cond_inv_std[k];
+      for (int k = 0; k < kCondRect; ++k)
+        s.cn[tid][k] = k < st.ncond ? (cond[k * n + g] - st.cond_mean[k]) * st.cond_inv_std[k] : 0.0f;
       if (noise) {
 #pragma unroll
         for (int d = 0; d < 4; ++d) s.x[tid][d] = noise[d * n + g];
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(THREADS) sampler_f32_kernel(
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < kCond; ++k) s.cn[tid][k] = 0.0f;
+      for (int k = 0; k < kCondRect; ++k) s.cn[tid][k] = 0.0f;
 #pragma unroll
       for (int d = 0; d < 4; ++d) s.x[tid][d] = 0.0f;
     }

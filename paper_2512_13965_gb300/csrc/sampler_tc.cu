@@ -444,10 +444,8 @@ __global__ void __launch_bounds__(THREADS, 1) sampler_tc_kernel(Params P) {
         const int64_t gi = (2 * pr + T) * TM + r;
         const bool valid = gi < P.n;
         if (owner) {
-          float cn[kCond];
-#pragma unroll
-          for (int k = 0; k < kCond; ++k)
-            cn[k] = valid ? (P.cond[k * P.n + gi] - P.st.cond_mean[k]) * P.st.cond_inv_std[k] : 0.0f;
+          float cn[kCondRect];
+          load_cond(P.cond, P.st, P.n, gi, valid, cn);
           if (!valid) {
 #pragma unroll
             for (int d = 0; d < 4; ++d) x[d] = 0.0f;
@@ -687,19 +685,21 @@ uint8_t e4m3_bits(double x) {
 
 // Layers 1 and 5 (BF16 in both variants) and the per-layer bias vectors.
 void pack_b1_b5_bias(const float (*W)[256 * 256], const float (*b)[256], unsigned char *P,
-                     size_t off_b1, size_t off_b5, float *bias_host) {
+                     size_t off_b1, size_t off_b5, float *bias_host, int nin) {
   auto put = [&](size_t off, float v) {
     const uint16_t u = bf16_bits(v);
     std::memcpy(P + off, &u, 2);
   };
-  // layer 1: [x (4) for x_hi, x (4) again for x_lo, cond (5), 0 0 0]
+  // layer 1: [x (4) for x_hi, x (4) again for x_lo, cond (5), 0 0, aspect]
+  // (the aspect weight, input column 25, only for rectangular cells)
   for (int nrow = 0; nrow < 256; ++nrow) {
-    const float *w = &W[0][nrow * 25];
+    const float *w = &W[0][nrow * nin];
     for (int k = 0; k < 4; ++k) {
       put(off_b1 + sw32_off(nrow, k), 0.5f * w[5 + k]);
       put(off_b1 + sw32_off(nrow, 4 + k), 0.5f * w[5 + k]);
     }
     for (int k = 0; k < 5; ++k) put(off_b1 + sw32_off(nrow, 8 + k), 0.5f * w[k]);
+    if (nin > kIn) put(off_b1 + sw32_off(nrow, 15), 0.5f * w[kIn]);
   }
   // output layer: 16 rows (4 real) x 256 K in four 128-byte-swizzled K-blocks
   for (int d = 0; d < 4; ++d)
@@ -716,7 +716,7 @@ void pack_b1_b5_bias(const float (*W)[256 * 256], const float (*b)[256], unsigne
 size_t tc_packed_bytes(bool fp8) { return fp8 ? Packed<true>::BYTES : Packed<false>::BYTES; }
 
 void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
-                  float *bias_host, const float (*M)[256 * kCond]) {
+                  float *bias_host, const float (*M)[256 * kCond], int nin) {
   using PK = Packed<false>;
   unsigned char *P = (unsigned char *)packed_host;
   std::memset(P, 0, PK::BYTES);
@@ -731,7 +731,7 @@ void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *pack
           std::memcpy(P + base + chunk_byte_off(i, 2 * j), &u, 2);
         }
     }
-  pack_b1_b5_bias(W, b, P, PK::OFF_B1, PK::OFF_B5, bias_host);
+  pack_b1_b5_bias(W, b, P, PK::OFF_B1, PK::OFF_B5, bias_host, nin);
   // bias blocks of layers 2-4: b/2 = hi + lo, both BF16, against the two
   // constant-1 columns of the layer-1 operand
   for (int L = 0; L < 3; ++L)
@@ -756,7 +756,7 @@ void tc_pack_host(const float (*W)[256 * 256], const float (*b)[256], void *pack
 }
 
 void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *packed_host,
-                      float *bias_host, float *scale_host) {
+                      float *bias_host, float *scale_host, int nin) {
   using PK = Packed<true>;
   unsigned char *P = (unsigned char *)packed_host;
   std::memset(P, 0, PK::BYTES);
@@ -784,7 +784,7 @@ void tc_pack_host_fp8(const float (*W)[256 * 256], const float (*b)[256], void *
       std::memcpy(P + PK::OFF_BIAS + (size_t)L * 8192 + sw32_off(i, 13), &hi, 2);
       std::memcpy(P + PK::OFF_BIAS + (size_t)L * 8192 + sw32_off(i, 14), &lo, 2);
     }
-  pack_b1_b5_bias(W, b, P, PK::OFF_B1, PK::OFF_B5, bias_host);
+  pack_b1_b5_bias(W, b, P, PK::OFF_B1, PK::OFF_B5, bias_host, nin);
 }
 
 namespace {

@@ -36,14 +36,16 @@
 namespace gmc {
 
 constexpr uint32_t kTagData = 5u, kTagDataInternal = 7u, kTagDataXY = 8u,
-                   kTagDataInternalXY = 9u;  // kTagTrain: train_fused.h
+                   kTagDataInternalXY = 9u, kTagDataRect = 10u;  // kTagTrain: train_fused.h
 
 struct TrainState {
   int64_t n = 0;
   const float *cond = nullptr, *y = nullptr;
-  float stats[18];
+  // standardization: cond mean [ncond], cond sd [ncond], y mean [4], y sd [4]
+  float stats[20];
   gmc_train_config cfg{};
   bool rm = false;         // residual-modulated network
+  int ncond = 5;           // condition components (6: a network of rectangular cells)
   int64_t np = P_TOTAL;    // parameters (P_TOTAL_RM with rm)
   int64_t step = 0;
   float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
@@ -52,7 +54,7 @@ struct TrainState {
         *dV = nullptr;
   double *loss = nullptr;  // [max steps per call]
   int64_t loss_cap = 0;
-  double *stat_acc = nullptr;  // 18 sums
+  double *stat_acc = nullptr;  // sums and sums of squares of the ncond + 4 features
   float *colpart = nullptr;    // partial column sums of the bias gradients (FP32 path)
   float *ws = nullptr;         // K-split partial products of the weight gradients (FP32 path)
   tf::Bufs fb;                 // operand images of the BF16 tensor-core step
@@ -108,6 +110,44 @@ __global__ void internal_data_kernel(int64_t n, uint64_t seed, float ltau_lo, fl
   cond[2 * n + i] = ltau;
   cond[3 * n + i] = c;
   cond[4 * n + i] = fminf(fminf(X, Y), fminf(1.0f - X, 1.0f - Y));
+  y[i] = (float)(w.face < 0 ? 0 : w.face) + w.q;
+  y[n + i] = w.ux;
+  y[2 * n + i] = w.uy;
+  y[3 * n + i] = logf(fmaxf(w.s, kSMin));
+}
+
+// Training data of the boundary model for rectangular cells: Philox block
+// (i, 0, tag 10) gives ln tau_x uniform in [ln tau_lo, ln tau_hi], c uniform,
+// xi uniform and sin theta = 2 u - 1 (the cosine-law entry of the square
+// data); (i, 1, tag 10) the aspect, ln(tau_y / tau_x) uniform in
+// [ln a_lo, ln a_hi]. The implicit-capture walk in the cell [0, tau_x] x
+// [0, tau_y] runs from (0, xi tau_y), flights from event 2 (FP64 positions
+// when a side exceeds kTau64). cond = (xi, cos, sin, ln tau_x, c,
+// ln(tau_y / tau_x)); y = (p, ux, uy, ln s), q normalized per face.
+__global__ void rect_data_kernel(int64_t n, uint64_t seed, float ltau_lo, float ltau_hi,
+                                 float la_lo, float la_hi, float c_lo, float c_hi,
+                                 float *__restrict__ cond, float *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 r = philox_draw(seed, (uint64_t)i, 0u, kTagDataRect);
+  const float ltau = ltau_lo + (ltau_hi - ltau_lo) * u01(r.x);
+  const float c = c_lo + (c_hi - c_lo) * u01(r.y);
+  const float xi = u01(r.z);
+  const float sn = 2.0f * u01(r.w) - 1.0f;
+  const float cs = sqrtf(fmaxf(1.0f - sn * sn, 0.0f));
+  const float la = la_lo + (la_hi - la_lo) * u01(philox_draw(seed, (uint64_t)i, 1u, kTagDataRect).x);
+  const float tx = expf(ltau), ty = expf(ltau + la);
+  const WalkResult w =
+      fmaxf(tx, ty) > kTau64
+          ? walk_rect<double>((double)tx, (double)ty, c, 1, 0.0, (double)xi * ty, cs, sn, seed,
+                              (uint64_t)i, 2u)
+          : walk_rect<float>(tx, ty, c, 1, 0.0f, xi * ty, cs, sn, seed, (uint64_t)i, 2u);
+  cond[i] = xi;
+  cond[n + i] = cs;
+  cond[2 * n + i] = sn;
+  cond[3 * n + i] = ltau;
+  cond[4 * n + i] = c;
+  cond[5 * n + i] = la;
   y[i] = (float)(w.face < 0 ? 0 : w.face) + w.q;
   y[n + i] = w.ux;
   y[2 * n + i] = w.uy;
@@ -191,32 +231,36 @@ __global__ void xy_data_kernel(int64_t n, uint64_t seed, float ltau_lo, float lt
   y[3 * n + i] = logf(fmaxf(w.s, kSMin));
 }
 
-// sums and sums of squares of the 9 features (FP64)
-__global__ void stats_kernel(int64_t n, const float *__restrict__ cond, const float *__restrict__ y,
-                             double *acc) {
-  __shared__ double sh[18];
-  if (threadIdx.x < 18) sh[threadIdx.x] = 0.0;
+// sums and sums of squares of the nc + 4 features (FP64): acc[k] and
+// acc[nf + k], nf = nc + 4 (nc = 5, or 6 for rectangular cells)
+__global__ void stats_kernel(int64_t n, int nc, const float *__restrict__ cond,
+                             const float *__restrict__ y, double *acc) {
+  constexpr int kMaxF = 10;
+  const int nf = nc + 4;
+  __shared__ double sh[2 * kMaxF];
+  if (threadIdx.x < 2 * kMaxF) sh[threadIdx.x] = 0.0;
   __syncthreads();
-  double loc[18];
-  for (int k = 0; k < 18; ++k) loc[k] = 0.0;
+  double loc[2 * kMaxF];
+  for (int k = 0; k < 2 * kMaxF; ++k) loc[k] = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    for (int k = 0; k < 9; ++k) {
-      const double v = k < 5 ? cond[k * n + i] : y[(k - 5) * n + i];
+    for (int k = 0; k < nf; ++k) {
+      const double v = k < nc ? cond[k * n + i] : y[(k - nc) * n + i];
       loc[k] += v;
-      loc[9 + k] += v * v;
+      loc[nf + k] += v * v;
     }
   }
-  for (int k = 0; k < 18; ++k) {
+  for (int k = 0; k < 2 * nf; ++k) {
     double v = loc[k];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(&sh[k], v);
   }
   __syncthreads();
-  if (threadIdx.x < 18) atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
+  if (threadIdx.x < 2 * nf) atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
 }
 
-// One batch row: sample index, t, x0 -> X0 row [cn, x_t, emb(t), 0...], U row.
-__global__ void batch_kernel(int64_t B, int64_t n, const float *__restrict__ cond,
+// One batch row: sample index, t, x0 -> X0 row [cn, x_t, emb(t), aspect, 0...]
+// (the aspect, column 25, for a network of rectangular cells: nc = 6), U row.
+__global__ void batch_kernel(int64_t B, int64_t n, int nc, const float *__restrict__ cond,
                              const float *__restrict__ y, Std sd, uint64_t seed, int64_t step,
                              float *__restrict__ X0, float *__restrict__ U) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -235,23 +279,25 @@ __global__ void batch_kernel(int64_t B, int64_t n, const float *__restrict__ con
     U[b * 4 + d] = x1 - x0[d];
   }
   for (int j = 0; j < 16; ++j) row[9 + j] = time_embedding(j, t);
-  for (int k = 25; k < 32; ++k) row[k] = 0.0f;
+  row[25] = nc > 5 ? (cond[5 * n + idx] - sd.cm[5]) * sd.cis[5] : 0.0f;
+  for (int k = 26; k < 32; ++k) row[k] = 0.0f;
 }
 
-// Batch rows from explicit inputs (gradient check): cn [B][5], x1, x0 [B][4], t [B].
-__global__ void batch_explicit_kernel(int64_t B, const float *cn, const float *x1,
+// Batch rows from explicit inputs (gradient check): cn [B][nc], x1, x0 [B][4], t [B].
+__global__ void batch_explicit_kernel(int64_t B, int nc, const float *cn, const float *x1,
                                       const float *x0, const float *tt, float *X0, float *U) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const float t = tt[b];
   float *row = X0 + b * 32;
-  for (int k = 0; k < 5; ++k) row[k] = cn[b * 5 + k];
+  for (int k = 0; k < 5; ++k) row[k] = cn[b * nc + k];
   for (int d = 0; d < 4; ++d) {
     row[5 + d] = (1.0f - t) * x0[b * 4 + d] + t * x1[b * 4 + d];
     U[b * 4 + d] = x1[b * 4 + d] - x0[b * 4 + d];
   }
   for (int j = 0; j < 16; ++j) row[9 + j] = time_embedding(j, t);
-  for (int k = 25; k < 32; ++k) row[k] = 0.0f;
+  row[25] = nc > 5 ? cn[b * nc + 5] : 0.0f;
+  for (int k = 26; k < 32; ++k) row[k] = 0.0f;
 }
 
 enum Epi { kEpiStore = 0, kEpiBiasSilu = 1, kEpiBias = 2, kEpiDSilu = 3, kEpiRM = 4, kEpiAdd = 5 };
@@ -714,6 +760,28 @@ gmc_status gmc_train_data_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_l
   return GMC_OK;
 }
 
+gmc_status gmc_train_data_rect(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, float tau_hi,
+                               float aspect_lo, float aspect_hi, float c_lo, float c_hi, float *cond,
+                               float *y) {
+  if (!ctx) return GMC_EINVAL;
+  if (n < 0 || (n > 0 && (!cond || !y)))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_data_rect: bad arguments");
+  if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(aspect_lo > 0.0f) || !(aspect_hi >= aspect_lo) ||
+      !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
+    return set_error(ctx, GMC_EINVAL,
+                     "gmc_train_data_rect: need 0 < tau_lo <= tau_hi, 0 < aspect_lo <= aspect_hi, "
+                     "0 <= c_lo <= c_hi <= 1");
+  if (n == 0) return GMC_OK;
+  if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_data_rect: cond and y must be device memory");
+  cudaSetDevice(ctx->device);
+  rect_data_kernel<<<nb(n, 128), 128, 0, ctx->stream>>>(n, seed, logf(tau_lo), logf(tau_hi),
+                                                        logf(aspect_lo), logf(aspect_hi), c_lo, c_hi,
+                                                        cond, y);
+  GMC_CUDA_TRY(ctx, cudaGetLastError());
+  return GMC_OK;
+}
+
 gmc_status gmc_train_data_internal_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo,
                                       float tau_hi, float c_lo, float c_hi, float *cond, float *y) {
   if (!ctx) return GMC_EINVAL;
@@ -743,6 +811,8 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
   if (!ctx->net.loaded) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_train_begin: load initial weights first");
   if (ctx->net.rm && cfg->precision != GMC_FP32)
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: the residual-modulated network trains at GMC_FP32");
+  if (ctx->net.stats.ncond != kCond && cfg->precision != GMC_FP32)
+    return set_error(ctx, GMC_EINVAL, "gmc_train_begin: the rectangular-cell network trains at GMC_FP32");
   if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: data must be device memory");
   cudaSetDevice(ctx->device);
@@ -754,33 +824,35 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
   T->y = y;
   T->cfg = *cfg;
   T->rm = ctx->net.rm;
+  T->ncond = ctx->net.stats.ncond;
   T->np = T->rm ? P_TOTAL_RM : P_TOTAL;
   T->step = 0;
   cudaStream_t s = ctx->stream;
-  GMC_CUDA_TRY(ctx, cudaMalloc(&T->stat_acc, 18 * sizeof(double)));
-  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->stat_acc, 0, 18 * sizeof(double), s));
-  stats_kernel<<<1024, 256, 0, s>>>(n, cond, y, T->stat_acc);
+  const int nc = T->ncond, nf = nc + 4;
+  GMC_CUDA_TRY(ctx, cudaMalloc(&T->stat_acc, 20 * sizeof(double)));
+  GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->stat_acc, 0, 20 * sizeof(double), s));
+  stats_kernel<<<1024, 256, 0, s>>>(n, nc, cond, y, T->stat_acc);
   GMC_CUDA_TRY(ctx, cudaGetLastError());
-  double acc[18];
+  double acc[20];
   GMC_CUDA_TRY(ctx, cudaMemcpyAsync(acc, T->stat_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
   GMC_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  for (int k = 0; k < 9; ++k) {
+  for (int k = 0; k < nf; ++k) {
     const double mean = acc[k] / n;
-    double var = acc[9 + k] / n - mean * mean;
+    double var = acc[nf + k] / n - mean * mean;
     const double sd = var > 1e-12 ? std::sqrt(var) : 1.0;
-    if (k < 5) {
+    if (k < nc) {
       T->stats[k] = (float)mean;
-      T->stats[5 + k] = (float)sd;
+      T->stats[nc + k] = (float)sd;
     } else {
-      T->stats[10 + (k - 5)] = (float)mean;
-      T->stats[14 + (k - 5)] = (float)sd;
+      T->stats[2 * nc + (k - nc)] = (float)mean;
+      T->stats[2 * nc + 4 + (k - nc)] = (float)sd;
     }
   }
   // master weights from the loaded network
   const int64_t np = T->np;
   std::vector<float> h(np, 0.0f);
   for (int c = 0; c < 256; ++c)
-    for (int k = 0; k < 25; ++k) h[P_W1 + c * 32 + k] = ctx->net.host_w[0][c * 25 + k];
+    for (int k = 0; k < ctx->net.nin; ++k) h[P_W1 + c * 32 + k] = ctx->net.host_w[0][c * ctx->net.nin + k];
   std::memcpy(&h[P_B1], ctx->net.host_b[0], 256 * 4);
   const int64_t wo[3] = {P_W2, P_W3, P_W4}, bo[3] = {P_B2, P_B3, P_B4};
   for (int l = 0; l < 3; ++l) {
@@ -824,18 +896,20 @@ gmc_status gmc_train_steps(gmc_ctx *ctx, int64_t n_steps, float *losses) {
   }
   GMC_CUDA_TRY(ctx, cudaMemsetAsync(T->loss, 0, n_steps * sizeof(double), s));
   Std sd;
-  for (int k = 0; k < 5; ++k) {
-    sd.cm[k] = T->stats[k];
-    sd.cis[k] = 1.0f / T->stats[5 + k];
+  const int nc = T->ncond;
+  for (int k = 0; k < 6; ++k) {
+    sd.cm[k] = k < nc ? T->stats[k] : 0.0f;
+    sd.cis[k] = k < nc ? 1.0f / T->stats[nc + k] : 1.0f;
   }
   for (int k = 0; k < 4; ++k) {
-    sd.ym[k] = T->stats[10 + k];
-    sd.yis[k] = 1.0f / T->stats[14 + k];
+    sd.ym[k] = T->stats[2 * nc + k];
+    sd.yis[k] = 1.0f / T->stats[2 * nc + 4 + k];
   }
   const gmc_train_config &c = T->cfg;
   for (int64_t i = 0; i < n_steps; ++i) {
     if (c.precision != GMC_BF16)
-      batch_kernel<<<nb(T->B, 256), 256, 0, s>>>(T->B, T->n, T->cond, T->y, sd, c.seed, T->step, T->X0, T->U);
+      batch_kernel<<<nb(T->B, 256), 256, 0, s>>>(T->B, T->n, T->ncond, T->cond, T->y, sd, c.seed,
+                                                 T->step, T->X0, T->U);
     const float bc1 = 1.0f - (float)std::pow(c.beta1, (double)(T->step + 1));
     const float bc2 = 1.0f - (float)std::pow(c.beta2, (double)(T->step + 1));
     if (c.precision == GMC_BF16) {
@@ -873,14 +947,16 @@ gmc_status gmc_train_grad(gmc_ctx *ctx, int64_t B, const float *cn, const float 
   cudaSetDevice(ctx->device);
   cudaStream_t s = ctx->stream;
   float *d;
-  const size_t nbytes = (size_t)B * (5 + 4 + 4 + 1) * 4;
+  const int nc = T->ncond;
+  const size_t nbytes = (size_t)B * (nc + 4 + 4 + 1) * 4;
   GMC_CUDA_TRY(ctx, ensure(ctx->stage[0], nbytes));
   d = (float *)ctx->stage[0].ptr;
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d, cn, B * 20, cudaMemcpyHostToDevice, s));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d + B * 5, x1, B * 16, cudaMemcpyHostToDevice, s));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d + B * 9, x0, B * 16, cudaMemcpyHostToDevice, s));
-  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d + B * 13, t, B * 4, cudaMemcpyHostToDevice, s));
-  batch_explicit_kernel<<<nb(B, 256), 256, 0, s>>>(B, d, d + B * 5, d + B * 9, d + B * 13, T->X0, T->U);
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d, cn, B * nc * 4, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d + B * nc, x1, B * 16, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d + B * (nc + 4), x0, B * 16, cudaMemcpyHostToDevice, s));
+  GMC_CUDA_TRY(ctx, cudaMemcpyAsync(d + B * (nc + 8), t, B * 4, cudaMemcpyHostToDevice, s));
+  batch_explicit_kernel<<<nb(B, 256), 256, 0, s>>>(B, nc, d, d + B * nc, d + B * (nc + 4),
+                                                   d + B * (nc + 8), T->X0, T->U);
   const int64_t saveB = T->B;
   T->B = B;
   double *ls;
@@ -927,7 +1003,7 @@ gmc_status gmc_train_params(gmc_ctx *ctx, float *out) {
 // and second moments (P floats each). The batch of step k draws its rows from
 // Philox at (seed, k), so restoring these and the step count resumes the run
 // exactly where it stopped.
-// The dataset is identified by its size n and its 18 FP64-accumulated
+// The dataset is identified by its size n and its FP64-accumulated
 // standardization statistics (stored as FP32), which gmc_train_begin
 // recomputes from the data: a checkpoint restores only into a training state
 // begun on data with the same n and bit-identical statistics.
@@ -935,11 +1011,14 @@ struct TrainCkpt {
   char magic[4];
   uint32_t version;
   int64_t params, step, batch, n;
-  int32_t precision, arch;  // arch 1: the residual-modulated network
+  int32_t precision, arch;  // arch bit 0: residual-modulated; bit 1: rectangular cells
   double lr, beta1, beta2, eps, weight_decay;
   uint64_t seed;
-  float stats[18];
+  float stats[20];          // TrainState::stats (2 n_cond + 8 used)
 };
+constexpr uint32_t kCkptVersion = 3;
+
+int32_t ckpt_arch(const TrainState &T) { return (T.rm ? 1 : 0) | (T.ncond != kCond ? 2 : 0); }
 
 gmc_status gmc_train_state_size(const gmc_ctx *ctx, size_t *bytes) {
   if (!ctx || !bytes) return GMC_EINVAL;
@@ -959,9 +1038,9 @@ gmc_status gmc_train_save_state(gmc_ctx *ctx, void *blob, size_t nbytes) {
   TrainCkpt h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "GMCT", 4);
-  h.version = 2;
+  h.version = kCkptVersion;
   h.params = T->np;
-  h.arch = T->rm ? 1 : 0;
+  h.arch = ckpt_arch(*T);
   h.step = T->step;
   h.batch = T->cfg.batch;
   h.n = T->n;
@@ -996,12 +1075,14 @@ gmc_status gmc_train_load_state(gmc_ctx *ctx, const void *blob, size_t nbytes) {
     return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: a checkpoint is %zu bytes", need);
   TrainCkpt h;
   std::memcpy(&h, blob, sizeof(h));
-  if (std::memcmp(h.magic, "GMCT", 4) != 0 || h.version != 2 || h.params != T->np ||
-      h.arch != (T->rm ? 1 : 0))
+  if (std::memcmp(h.magic, "GMCT", 4) != 0 || h.version != kCkptVersion || h.params != T->np ||
+      h.arch != ckpt_arch(*T))
     return set_error(ctx, GMC_EFORMAT,
-                     "gmc_train_load_state: not a version-2 training checkpoint of this network");
-  for (int k = 0; k < 18; ++k)
-    if (!std::isfinite(h.stats[k]) || (((k >= 5 && k < 10) || k >= 14) && !(h.stats[k] > 0.0f)))
+                     "gmc_train_load_state: not a version-3 training checkpoint of this network");
+  const int nc = T->ncond;
+  for (int k = 0; k < 2 * nc + 8; ++k)
+    if (!std::isfinite(h.stats[k]) ||
+        (((k >= nc && k < 2 * nc) || k >= 2 * nc + 4) && !(h.stats[k] > 0.0f)))
       return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: bad standardization statistics");
   if (h.batch != T->cfg.batch || h.precision != T->cfg.precision || h.step < 0)
     return set_error(ctx, GMC_EINVAL,
@@ -1048,13 +1129,14 @@ gmc_status gmc_train_commit(gmc_ctx *ctx, const char *path) {
   auto f32 = [&](const float *v, size_t n) { const unsigned char *p = (const unsigned char *)v; blob.insert(blob.end(), p, p + 4 * n); };
   blob.insert(blob.end(), {'G', 'M', 'C', 'W'});
   u32(1); u32(5);
-  const uint32_t dims[6] = {25, 256, 256, 256, 256, 4};
+  const int nc = T->ncond, nin = nc + kState + kEmb;
+  const uint32_t dims[6] = {(uint32_t)nin, 256, 256, 256, 256, 4};
   for (uint32_t dd : dims) u32(dd);
-  u32(5); u32(4); u32(16); u32(T->rm ? kFlagRM : 0u);
-  f32(T->stats, 18);
-  std::vector<float> w1(256 * 25);
+  u32((uint32_t)nc); u32(4); u32(16); u32(T->rm ? kFlagRM : 0u);
+  f32(T->stats, 2 * nc + 8);
+  std::vector<float> w1(256 * nin);
   for (int c = 0; c < 256; ++c)
-    for (int k = 0; k < 25; ++k) w1[c * 25 + k] = h[P_W1 + c * 32 + k];
+    for (int k = 0; k < nin; ++k) w1[c * nin + k] = h[P_W1 + c * 32 + k];
   f32(w1.data(), w1.size());
   f32(&h[P_B1], 256);
   f32(&h[P_W2], 65536); f32(&h[P_B2], 256);

@@ -19,9 +19,10 @@ constexpr int64_t P_RM_M = P_TOTAL, P_RM_G = P_RM_M + 3 * 256 * 5,
                   P_TOTAL_RM = P_RM_G + 3 * 2 * 256;
 
 // Standardization of the training data: condition and target means and
-// inverse standard deviations.
+// inverse standard deviations (the sixth condition entry: the aspect of a
+// network for rectangular cells, trained on the FP32 path).
 struct Std {
-  float cm[5], cis[5], ym[4], yis[4];
+  float cm[6], cis[6], ym[4], yis[4];
 };
 
 constexpr uint32_t kTagTrain = 6u;  // Philox tag of the batch draws

@@ -880,6 +880,15 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
   }
   R.wall = wall;
   R.xy = xy;
+  // the solves' cells are squares: a network of rectangular cells (six
+  // condition rows) has no place in them
+  if (method == GMC_METHOD_GMC) {
+    const NetDev *nets[4] = {&ctx->net, &ctx->internal, &ctx->xy, &ctx->internal_xy};
+    for (const NetDev *N : nets)
+      if (N->loaded && N->stats.ncond != kCond &&
+          (xy ? (N == &ctx->xy || N == &ctx->internal_xy) : (N == &ctx->net || N == &ctx->internal)))
+        return set_error(ctx, GMC_EINVAL, "solve: a rectangular-cell network cannot sample square cells");
+  }
   if (n_histories > 0 && !(acc > 0.0)) return set_error(ctx, GMC_EINVAL, "solve: zero source");
   if (xy && method == GMC_METHOD_GMC) {
     // the x-y boundary network; births by the x-y internal model when loaded,
