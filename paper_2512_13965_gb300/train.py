@@ -10,7 +10,10 @@ tau log-uniform in [0.1, 1000], c uniform in [0.5, 0.999]), with
 the cell, for the internal-source model), with --model xy
 `gmc_train_data_xy` (walks in x-y geometry: 3-D directions, the cell the
 cross-section of a prism), with --model internal_xy
-`gmc_train_data_internal_xy` (births inside a prism cell); objective: conditional flow
+`gmc_train_data_internal_xy` (births inside a prism cell), with --model rect
+`gmc_train_data_rect` (rectangular cells, aspect log-uniform in --aspect; the
+network gets the aspect as a sixth condition and trains at --precision
+fp32); objective: conditional flow
 matching (Eq. 9) with AdamW, learning rate warmed up linearly and then
 decayed along a cosine to --lr-min; everything runs in libgmc.so, the GEMMs
 on tensor cores with BF16 operands and FP32 accumulation and master weights
@@ -46,11 +49,14 @@ def main(argv=None):
     ap.add_argument("--c", type=float, nargs=2, default=(0.5, 0.999))
     ap.add_argument("--report", type=int, default=1000)
     ap.add_argument("--device", type=int, default=0)
-    ap.add_argument("--model", default="boundary", choices=["boundary", "internal", "xy", "internal_xy"],
+    ap.add_argument("--model", default="boundary",
+                    choices=["boundary", "internal", "xy", "internal_xy", "rect"],
                     help="boundary: cell transmissions from the left face; internal: births "
                          "inside a cell (volumetric source); xy: transmissions in x-y geometry "
                          "(3-D directions projected on the unit disk); internal_xy: births in x-y "
-                         "geometry")
+                         "geometry; rect: transmissions of rectangular cells")
+    ap.add_argument("--aspect", type=float, nargs=2, default=(0.25, 4.0),
+                    help="rect: range of tau_y / tau_x (log-uniform)")
     ap.add_argument("--precision", default=None, choices=["bf16", "fp32"],
                     help="GEMM operands: bf16 (tensor cores; the MLP's default) or fp32 (SIMT; "
                          "the only choice for --arch rm)")
@@ -58,9 +64,11 @@ def main(argv=None):
                     help="mlp: 4 x 256 SiLU MLP; rm: residual-modulated blocks")
     args = ap.parse_args(argv)
     if args.precision is None:
-        args.precision = "fp32" if args.arch == "rm" else "bf16"
-    if args.arch == "rm" and args.precision != "fp32":
-        ap.error("--arch rm trains at --precision fp32")
+        args.precision = "fp32" if (args.arch == "rm" or args.model == "rect") else "bf16"
+    if (args.arch == "rm" or args.model == "rect") and args.precision != "fp32":
+        ap.error("--arch rm and --model rect train at --precision fp32")
+    if args.arch == "rm" and args.model == "rect":
+        ap.error("--arch rm has no rectangular-cell variant")
 
     import numpy as np
     import torch
@@ -77,19 +85,23 @@ def main(argv=None):
     g.gmc_set_stream(ctx, stream)
     with tempfile.TemporaryDirectory() as d:
         init = os.path.join(d, "init.bin")
-        w0 = synth.kaiming_weights(args.init_seed)
+        w0 = (synth.kaiming_weights_rect if args.model == "rect" else synth.kaiming_weights)(args.init_seed)
         if args.arch == "rm":
             w0 = synth.rm_weights(args.init_seed, base=w0)
         synth.write_weights(init, w0)
         g.gmc_load_weights(ctx, init)
     n = args.samples
     with torch.cuda.stream(stream):
-        cond = torch.empty(5, n, device="cuda")
+        cond = torch.empty(6 if args.model == "rect" else 5, n, device="cuda")
         y = torch.empty(4, n, device="cuda")
     t0 = time.perf_counter()
-    data = {"boundary": g.gmc_train_data, "internal": g.gmc_train_data_internal,
-            "xy": g.gmc_train_data_xy, "internal_xy": g.gmc_train_data_internal_xy}[args.model]
-    data(ctx, n, args.seed, args.tau[0], args.tau[1], args.c[0], args.c[1], cond, y)
+    if args.model == "rect":
+        g.gmc_train_data_rect(ctx, n, args.seed, args.tau[0], args.tau[1], args.aspect[0],
+                              args.aspect[1], args.c[0], args.c[1], cond, y)
+    else:
+        data = {"boundary": g.gmc_train_data, "internal": g.gmc_train_data_internal,
+                "xy": g.gmc_train_data_xy, "internal_xy": g.gmc_train_data_internal_xy}[args.model]
+        data(ctx, n, args.seed, args.tau[0], args.tau[1], args.c[0], args.c[1], cond, y)
     g.gmc_synchronize(ctx)
     t_data = time.perf_counter() - t0
     print(json.dumps({"phase": "data", "samples": n, "seconds": t_data}), flush=True)
