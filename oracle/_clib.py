@@ -57,6 +57,8 @@ def lib():
                                              P, P, P, P, P, P, P]
             L.orc_walk_one.argtypes = [dbl, dbl, i32, dbl, dbl, dbl, dbl, u64, u64, u32,
                                        P, P, P, P, P]
+            L.orc_walk_one_rect.argtypes = [dbl, dbl, dbl, i32, dbl, dbl, dbl, dbl, u64, u64,
+                                            u32, P, P, P, P, P]
             L.orc_walk_one_xy.argtypes = [dbl, dbl, i32, dbl, dbl, dbl, dbl, u64, u64, u32,
                                           P, P, P, P, P]
             L.orc_transmit_rect_ids.argtypes = [i64, P, P, P, P, P, P, i32, u64, P, P,

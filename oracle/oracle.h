@@ -53,6 +53,9 @@ void orc_walk_rect(double tx, double ty, double c, int mode, double x, double y,
 void orc_walk_xy(double tx, double ty, double c, int mode, int sphere, double x, double y,
                  double ux, double uy, double uz, uint64_t seed, uint64_t id, uint32_t event0,
                  orc_walk_result *res, double *uz_out);
+void orc_walk_one_rect(double tx, double ty, double c, int mode, double x, double y, double ux,
+                       double uy, uint64_t seed, uint64_t id, uint32_t event0, int32_t *status,
+                       int32_t *face, double *out, int64_t *ncoll, uint32_t *event);
 void orc_walk_one_xy(double tau, double c, int mode, double x, double y, double ux, double uy,
                      uint64_t seed, uint64_t id, uint32_t event0, int32_t *status, int32_t *face,
                      double *out, int64_t *ncoll, uint32_t *event);

@@ -668,3 +668,145 @@ def _advance_one(live, h, i, j, G, q, gx, gy, w, ev, nx, ny, st):
     for k, v in (("id", h), ("i", ni), ("j", nj), ("F", (G + 2) % 4), ("xi", q), ("gx", gx),
                  ("gy", gy), ("w", w), ("ev", ev)):
         live[k].append(v)
+
+
+# ---- rectangular cells in the solve (geometry variant with W != H) --------
+
+def walk_one_rect(tx, ty, c, mode, x, y, ux, uy, seed, pid, event0):
+    """One random walk in the rectangle [0, tx] x [0, ty] (optical units) from
+    an arbitrary point; q normalized per face. Same outputs as walk_one."""
+    status = ctypes.c_int32()
+    face = ctypes.c_int32()
+    ncoll = ctypes.c_int64()
+    ev = ctypes.c_uint32()
+    out = np.zeros(6, dtype=np.float64)
+    lib().orc_walk_one_rect(float(tx), float(ty), float(c), mode, float(x), float(y), float(ux),
+                            float(uy), seed, int(pid), int(event0), ctypes.byref(status),
+                            ctypes.byref(face), out.ctypes.data, ctypes.byref(ncoll),
+                            ctypes.byref(ev))
+    return {"status": status.value, "face": face.value, "q": out[0], "x": out[1], "y": out[2],
+            "ux": out[3], "uy": out[4], "s": out[5], "ncoll": ncoll.value, "event": ev.value}
+
+
+def canonical_sides(tx, ty, rot):
+    """Sides of a cell (tx along x, ty along y) in the canonical left-entry
+    frame reached by `rot` quarter turns: a quarter turn exchanges them, so
+    the canonical width (the depth behind the entry face) is ty and the
+    entry face's length tx for odd rot."""
+    odd = (np.asarray(rot) % 2) == 1
+    return np.where(odd, ty, tx), np.where(odd, tx, ty)
+
+
+def mlp_sampler_rect(net, steps, integrator, seed):
+    """Stage 2 with the network for rectangular cells: condition (xi, cos,
+    sin, ln tau_x, c, ln(tau_y / tau_x)) in the canonical frame."""
+    def f(xi, cos_c, sin_c, tx_c, ty_c, c, ids, events, rot=None):
+        cond = np.stack([xi, cos_c, sin_c, np.log(tx_c), c, np.log(ty_c / tx_c)])
+        z = rng.normals_for(seed, ids, events, rng.TAG_NOISE)
+        d = mlp.decode(net, mlp.sample(net, cond, z, steps, integrator))
+        return d["face"], d["q"], d["ux"], d["uy"], d["s"], np.asarray(events, np.uint32) + 1
+    return f
+
+
+def walk_sampler_global_rect(seed):
+    """The random walk through a rectangular cell in the cell's own (global)
+    frame, as a random-walk solve takes it (walk_sampler_global for
+    rectangles): entry face F = (rot - 1) mod 4 at counter-clockwise
+    parameter 1 - xi, the exit returned in the canonical frame."""
+    def f(xi, cos_c, sin_c, tx_c, ty_c, c, ids, events, rot=None):
+        n = len(ids)
+        face = np.zeros(n, np.int64)
+        out = [np.zeros(n) for _ in range(4)]
+        ev = np.zeros(n, np.uint32)
+        for k in range(n):
+            r = int(rot[k])
+            tx, ty = (ty_c[k], tx_c[k]) if r % 2 else (tx_c[k], ty_c[k])  # global sides
+            F = (r - 1) % 4
+            x = float(xi[k])
+            X, Y = {0: (1.0 - x, 0.0), 1: (1.0, 1.0 - x), 2: (x, 1.0), 3: (0.0, x)}[F]
+            gx, gy = rot_dir(cos_c[k], sin_c[k], r)
+            w = walk_one_rect(tx, ty, c[k], MODE_IMPLICIT, X * tx, Y * ty, gx, gy, seed,
+                              int(ids[k]), int(events[k]))
+            face[k] = (w["face"] - r) % 4
+            ux, uy = rot_dir(w["ux"], w["uy"], -r)
+            out[0][k], out[1][k], out[2][k], out[3][k] = w["q"], ux, uy, w["s"]
+            ev[k] = w["event"]
+        return face, out[0], out[1], out[2], out[3], ev
+    return f
+
+
+def solve_gmc_rect(sigma, c, src, dx, dy, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1,
+                   max_waves=100000):
+    """The event-based solve on a grid of rectangular cells of physical size
+    dx x dy (every cell alike) with cross sections sigma [ny, nx] and
+    scattering ratios c: cell (i, j) has optical sides tx = sigma dx (along x)
+    and ty = sigma dy. Births as solve_gmc (cell by the source CDF, point
+    (X tx, Y ty), direction on the circle), walked with walk_one_rect; every
+    later crossing goes to `sampler` in the canonical frame with the
+    canonical sides (canonical_sides). Flux per source particle per unit
+    area: Delta w / (sigma_a dx dy) per Eq. 7 (the track length w l / (dx dy)
+    for c = 1). Returns (flux [ny, nx], stats). With dx = dy = 1 this is
+    solve_gmc on tau = sigma."""
+    sig = np.asarray(sigma, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
+    ny, nx = sig.shape
+    sf, cf = sig.ravel(), c.ravel()
+    txf, tyf = sf * dx, sf * dy
+    area = float(dx) * float(dy)
+    flux = np.zeros(ny * nx, dtype=np.float64)
+    st = np.zeros(6, dtype=np.float64)
+    live = {k: [] for k in ("id", "i", "j", "F", "xi", "gx", "gy", "w", "ev")}
+    srcf = np.maximum(np.asarray(src, dtype=np.float64).ravel(), 0.0)
+    cdf = np.cumsum(srcf)
+    ids = np.arange(n_hist, dtype=np.uint64)
+    ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
+    cells = np.searchsorted(cdf, ub[0] * cdf[-1], side="left")
+    bux, buy = birth_directions(seed, ids, ub[3], "flat")
+    for h in range(n_hist):
+        k = int(cells[h])
+        r = walk_one_rect(txf[k], tyf[k], cf[k], MODE_IMPLICIT, ub[1, h] * txf[k], ub[2, h] * tyf[k],
+                          bux[h], buy[h], seed, h, 0)
+        st[3] += 1
+        st[4] += r["ncoll"]
+        dw, score = deposit(1.0, r["s"], sf[k], cf[k])
+        flux[k] += score / area
+        st[1] += dw
+        w, alive = _roulette(seed, np.array([h], np.uint64), np.array([r["event"]], np.uint32),
+                             np.array([1.0 - dw]), w_cut, p_survive, st)
+        if alive[0]:
+            _advance_one(live, h, k % nx, k // nx, r["face"], r["q"], r["ux"], r["uy"], w[0],
+                         r["event"], nx, ny, st)
+    L = {k: np.asarray(v) for k, v in live.items()}
+    L["id"] = L["id"].astype(np.uint64)
+    L["ev"] = L["ev"].astype(np.uint32)
+    for key in ("i", "j", "F"):
+        L[key] = L[key].astype(np.int64)
+    waves = 0
+    while L["id"].size > 0:
+        waves += 1
+        if waves > max_waves:
+            raise RuntimeError("too many waves")
+        cell = L["j"] * nx + L["i"]
+        rr = np.mod(L["F"] + 1, 4)
+        cx, cy = rot(L["gx"], L["gy"], -rr)
+        txc, tyc = canonical_sides(txf[cell], tyf[cell], rr)
+        face, q, ux, uy, s, ev = sampler(L["xi"], cx, cy, txc, tyc, cf[cell], L["id"], L["ev"],
+                                         rot=rr)
+        st[3] += cell.size
+        dw, score = deposit(L["w"], s, sf[cell], cf[cell])
+        np.add.at(flux, cell, score / area)
+        st[1] += dw.sum()
+        w, alive = _roulette(seed, L["id"], ev, L["w"] - dw, w_cut, p_survive, st)
+        G = np.mod(np.asarray(face) + rr, 4)
+        gx, gy = rot(ux, uy, rr)
+        ni = L["i"] + np.where(G == 1, 1, 0) - np.where(G == 3, 1, 0)
+        nj = L["j"] + np.where(G == 2, 1, 0) - np.where(G == 0, 1, 0)
+        inside = (ni >= 0) & (ni < nx) & (nj >= 0) & (nj < ny)
+        st[0] += w[alive & ~inside].sum()
+        keep = alive & inside
+        L = {"id": L["id"][keep], "i": ni[keep], "j": nj[keep], "F": np.mod(G[keep] + 2, 4),
+             "xi": np.asarray(q)[keep], "gx": gx[keep], "gy": gy[keep], "w": w[keep],
+             "ev": np.asarray(ev, np.uint32)[keep]}
+    stats = _stats(st)
+    stats["waves"] = waves
+    return (flux / n_hist).reshape(ny, nx), stats

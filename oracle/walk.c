@@ -138,6 +138,28 @@ void orc_walk_one(double tau, double c, int mode, double x, double y, double ux,
     *event = r.event;
 }
 
+/* Single walk in a rectangular cell [0, tx] x [0, ty] from an arbitrary
+   point, for the Python event-loop oracle. Outputs as orc_walk_one (q
+   normalized per face). */
+void orc_walk_one_rect(double tx, double ty, double c, int mode, double x, double y, double ux,
+                       double uy, uint64_t seed, uint64_t id, uint32_t event0, int32_t *status,
+                       int32_t *face, double *out /* q, x, y, ux, uy, s */, int64_t *ncoll,
+                       uint32_t *event)
+{
+    orc_walk_result r;
+    orc_walk_rect(tx, ty, c, mode, x, y, ux, uy, seed, id, event0, &r);
+    *status = r.status;
+    *face = r.face;
+    out[0] = r.q;
+    out[1] = r.x;
+    out[2] = r.y;
+    out[3] = r.ux;
+    out[4] = r.uy;
+    out[5] = r.s;
+    *ncoll = r.ncoll;
+    *event = r.event;
+}
+
 /* Single walk in x-y geometry (a square cell of side tau, directions on the
    sphere) from an arbitrary point, for the Python event-loop oracle: (ux, uy)
    is the direction's projection on the plane and |uz| = sqrt(1 - ux^2 - uy^2)

@@ -1,0 +1,145 @@
+"""Pins for the oracle's solve on rectangular cells (solve_gmc_rect: cells of
+physical size dx x dy with cross sections sigma, optical sides sigma dx and
+sigma dy; the geometry variant of section "Network Architecture and Inputs"
+with W != H).
+
+* Square cells (dx = dy = 1) reduce it to the square solve on tau = sigma,
+  history by history.
+* One pure-absorber rectangle with a uniform isotropic source: flux and
+  leakage against quadrature of the chord over birth point and direction.
+* A heterogeneous grid of flat rectangles with scattering: the cell-by-cell
+  event loop against an independent walker that follows each history
+  through the whole grid in physical coordinates, cell by cell on
+  independent seeds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp
+from oracle import transport as OT
+
+
+def test_square_cells_reduce_to_the_square_solve():
+    sig = np.array([[0.7, 2.0, 0.4], [1.5, 0.3, 1.1]])
+    c = np.array([[0.9, 0.6, 0.99], [0.5, 0.95, 0.8]])
+    src = np.array([[0.0, 1.0, 0.0], [0.5, 0.0, 0.0]])
+    a, sa = OT.solve_gmc_rect(sig, c, src, 1.0, 1.0, 500, 9, OT.walk_sampler_global_rect(9))
+    b, sb = OT.solve_gmc(sig, c, src, 500, 9, OT.walk_sampler_global(9))
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=0)
+    assert sa["transmissions"] == sb["transmissions"]
+
+
+def test_canonical_sides_exchange_on_quarter_turns():
+    tx, ty = np.array([2.0, 2.0, 2.0, 2.0]), np.array([0.5, 0.5, 0.5, 0.5])
+    w, h = OT.canonical_sides(tx, ty, np.array([0, 1, 2, 3]))
+    np.testing.assert_array_equal(w, [2.0, 0.5, 2.0, 0.5])
+    np.testing.assert_array_equal(h, [0.5, 2.0, 0.5, 2.0])
+
+
+def _chord2(x, y, ux, uy, tx, ty):
+    with np.errstate(divide="ignore", invalid="ignore"):
+        lx = np.where(ux > 0, (tx - x) / ux, np.where(ux < 0, -x / ux, np.inf))
+        ly = np.where(uy > 0, (ty - y) / uy, np.where(uy < 0, -y / uy, np.inf))
+    return np.minimum(lx, ly)
+
+
+@pytest.mark.parametrize("dx,dy,sig", [(1.0, 0.25, 2.0), (0.5, 2.0, 0.8)])
+def test_pure_absorber_rectangle_quadrature(dx, dy, sig):
+    tx, ty = sig * dx, sig * dy
+    m = 64
+    X, Y, T = np.meshgrid((np.arange(m) + 0.5) / m, (np.arange(m) + 0.5) / m,
+                          (np.arange(4 * m) + 0.5) * 2 * np.pi / (4 * m), indexing="ij")
+    l = _chord2(X * tx, Y * ty, np.cos(T), np.sin(T), tx, ty)
+    sc = (1.0 - np.exp(-l)) / sig / (dx * dy)
+    f_q, var, leak_q = sc.mean(), sc.var(), np.exp(-l).mean()
+    n = 100_000
+    f, st = OT.solve_gmc_rect(np.full((1, 1), sig), np.zeros((1, 1)), np.ones((1, 1)), dx, dy, n, 3,
+                              OT.walk_sampler_global_rect(3), w_cut=0.0)
+    assert abs(f[0, 0] - f_q) < 4 * math.sqrt(var / n) + 2e-4 * f_q, (f[0, 0], f_q)
+    assert abs(st["leak"] / n - leak_q) < 4 * math.sqrt(leak_q * (1 - leak_q) / n) + 2e-4
+
+
+def _global_walk_rect(sig, c, src, dx, dy, n, seed):
+    """Independent walker on the grid in physical coordinates: flights drawn
+    in scattering optical depth across cells (surface tracking), implicit
+    capture, the track-length score of every segment divided by the cell
+    area, vacuum boundaries, no roulette; its own random numbers."""
+    g = np.random.Generator(np.random.Philox(key=seed))
+    ny, nx = sig.shape
+    flux = np.zeros((ny, nx))
+    cdf = np.cumsum(src.ravel())
+    for _ in range(n):
+        k = int(np.searchsorted(cdf, g.random() * cdf[-1], side="left"))
+        i, j = k % nx, k // nx
+        px, py = (i + g.random()) * dx, (j + g.random()) * dy
+        ph = 2 * np.pi * g.random()
+        ux, uy = math.cos(ph), math.sin(ph)
+        w = 1.0
+        while True:
+            left = -math.log(1.0 - g.random())
+            scattered = False
+            while True:
+                ci, cj = int(math.floor(px / dx)), int(math.floor(py / dy))
+                s_, cc = sig[cj, ci], c[cj, ci]
+                lx = (((ci + 1) * dx - px) / ux if ux > 0 else ((ci * dx - px) / ux if ux < 0 else math.inf))
+                ly = (((cj + 1) * dy - py) / uy if uy > 0 else ((cj * dy - py) / uy if uy < 0 else math.inf))
+                lw = min(lx, ly)
+                ls = left / (cc * s_) if cc > 0 else math.inf
+                seg = min(lw, ls)
+                a = 1.0 - cc
+                dw = w * (-math.expm1(-a * s_ * seg))
+                flux[cj, ci] += (dw / (a * s_) if a > 0 else w * seg) / (dx * dy)
+                w -= dw
+                px += seg * ux
+                py += seg * uy
+                if ls < lw:
+                    scattered = True
+                    break
+                left -= seg * cc * s_
+                if lx <= ly:
+                    ni = ci + (1 if ux > 0 else -1)
+                    if not 0 <= ni < nx:
+                        break
+                    px = ni * dx if ux > 0 else ci * dx - 1e-12
+                else:
+                    nj = cj + (1 if uy > 0 else -1)
+                    if not 0 <= nj < ny:
+                        break
+                    py = nj * dy if uy > 0 else cj * dy - 1e-12
+            if not scattered:
+                break
+            ph = 2 * np.pi * g.random()
+            ux, uy = math.cos(ph), math.sin(ph)
+    return flux / n
+
+
+def test_rect_event_loop_matches_a_global_walker():
+    sig = np.array([[1.4, 4.0, 0.8], [3.0, 0.6, 2.2]])
+    c = np.array([[0.9, 0.6, 0.99], [0.5, 0.95, 0.8]])
+    src = np.zeros((2, 3))
+    src[0, 1] = 1.0
+    src[1, 0] = 0.5
+    dx, dy = 0.5, 1.5
+    K, n = 6, 3000
+    A = np.asarray([OT.solve_gmc_rect(sig, c, src, dx, dy, n, 100 + k,
+                                      OT.walk_sampler_global_rect(100 + k), w_cut=0.0)[0]
+                    for k in range(K)]).reshape(K, -1)
+    B = np.asarray([_global_walk_rect(sig, c, src, dx, dy, n, 200 + k) for k in range(K)]).reshape(K, -1)
+    se = np.sqrt(A.var(0, ddof=1) / K + B.var(0, ddof=1) / K)
+    z = np.abs(A.mean(0) - B.mean(0)) / se
+    assert z.max() < 4.5, (z, A.mean(0), B.mean(0))
+
+
+def test_rect_solve_with_a_network_runs_and_balances(tmp_path):
+    p = str(tmp_path / "r.bin")
+    synth.write_weights(p, synth.kaiming_weights_rect(1))
+    net = mlp.read_weights(p)
+    sig = np.array([[1.0, 3.0], [0.5, 2.0]])
+    c = np.array([[0.9, 0.7], [0.99, 0.5]])
+    src = np.array([[1.0, 0.0], [0.0, 0.0]])
+    f, st = OT.solve_gmc_rect(sig, c, src, 2.0, 0.5, 300, 11, OT.mlp_sampler_rect(net, 4, "euler", 11))
+    assert np.all(np.isfinite(f)) and f.sum() > 0
+    assert abs(st["leak"] + st["absorbed"] - st["roulette_net"] - 300) < 1e-6 * 300
