@@ -434,6 +434,25 @@ gmc_status transport_solve_wall_xy(gmc_ctx *ctx, int nx, int ny, const float *ta
                                    const float *wall, int64_t n_histories, int method,
                                    uint64_t seed, double *flux, gmc_solve_stats *stats);
 
+/*
+ * transport_solve on rectangular cells of physical size dx x dy (every cell
+ * alike; the geometry variant of section "Network Architecture and Inputs"
+ * with W != H): sigma [ny*nx] the cells' cross sections, so cell k has the
+ * optical width sigma[k] dx and height sigma[k] dy. The walk crosses the
+ * rectangle as in analog_transmit_rect; births are uniform in the cell and
+ * walked. GMC_METHOD_GMC samples cell crossings with a network of
+ * rectangular cells loaded by gmc_load_weights (n_cond 6; GMC_EINVAL
+ * otherwise): in the canonical frame of the entry face the condition's
+ * width is the depth behind it and the aspect the face's length over it (a
+ * quarter turn exchanges the two sides). flux: per source particle per unit
+ * area, Delta w / (sigma_a dx dy) (Eq. 7). The box of scattering-equivalent
+ * conditions (gmc_config.net_*) applies to sigma dx. Volumetric sources only.
+ * Other arguments, the result and blocking as for transport_solve.
+ */
+gmc_status transport_solve_rect(gmc_ctx *ctx, int nx, int ny, const float *sigma, const float *c,
+                                const float *source, float dx, float dy, int64_t n_histories,
+                                int method, uint64_t seed, double *flux, gmc_solve_stats *stats);
+
 /* ---- serving: continuous batching of transport solves ---------------------- */
 
 /* One transport solve (arguments of transport_solve; arrays are host memory

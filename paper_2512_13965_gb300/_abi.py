@@ -104,6 +104,8 @@ def _load():
                                  ctypes.POINTER(gmc_solve_stats)],
         "transport_solve_xy": [P, i32, i32, P, P, P, i64, i32, u64, P,
                                ctypes.POINTER(gmc_solve_stats)],
+        "transport_solve_rect": [P, i32, i32, P, P, P, ctypes.c_float, ctypes.c_float, i64, i32,
+                                 u64, P, ctypes.POINTER(gmc_solve_stats)],
         "transport_solve_wall_xy": [P, i32, i32, P, P, P, i64, i32, u64, P,
                                     ctypes.POINTER(gmc_solve_stats)],
         "gmc_serve_start": [P, ctypes.POINTER(gmc_serve_config)],
@@ -398,6 +400,16 @@ def transport_solve_xy(ctx, nx, ny, tau, c, source, n_histories, method, seed, f
     ctx.check(lib.transport_solve_xy(ctx.handle, nx, ny, *_grid(m, tau, c),
                                      _arr(source, 4, m, "source"), n_histories, method, seed,
                                      _arr(flux, 8, m, "flux"), ctypes.byref(st)))
+    return st
+
+
+def transport_solve_rect(ctx, nx, ny, sigma, c, source, dx, dy, n_histories, method, seed, flux,
+                         stats=None):
+    st = stats if stats is not None else gmc_solve_stats()
+    m = max(nx, 0) * max(ny, 0)
+    ctx.check(lib.transport_solve_rect(ctx.handle, nx, ny, *_grid(m, sigma, c),
+                                       _arr(source, 4, m, "source"), dx, dy, n_histories, method,
+                                       seed, _arr(flux, 8, m, "flux"), ctypes.byref(st)))
     return st
 
 

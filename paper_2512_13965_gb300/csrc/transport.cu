@@ -100,6 +100,11 @@ struct Slot {
   // x-y geometry: every cell the cross-section of an infinite prism,
   // directions 3-D (carried as their projection on the plane)
   int xy;
+  // rectangular cells (transport_solve_rect): tau holds the optical width
+  // tx = sigma dx, the height is tx ry (ry = dy / dx, lry = ln ry), and a
+  // flux score is divided by dy as well (Delta w / (sigma_a dx dy))
+  int rect;
+  float ry, lry, dy;
 };
 
 struct Rules {
@@ -188,6 +193,7 @@ __device__ void finish_transmission(const Exit &x, const Slot *__restrict__ slot
       dw = 0.0f;
       score = (double)x.w * (double)x.s / (double)tau;
     }
+    if (S.rect) score /= (double)S.dy;                      // per unit area dx dy
     atomicAdd(&S.flux[x.cell], score);
     dabs = dw;
     w = x.w - dw;                                           // Eq. 5
@@ -411,7 +417,8 @@ __global__ void birth_kernel(int slot, int64_t first, int64_t count, const doubl
     cell = (int)cdf_search(cdf, (int64_t)S.nx * S.ny, u0 * total);
     float ux, uy;
     birth_direction(S, h, r, ux, uy);
-    ws = walk_start(S.tau[cell], u01(r.y), u01(r.z), ux, uy, 0u);
+    ws = S.rect ? walk_start_rect(S.tau[cell], S.tau[cell] * S.ry, u01(r.y), u01(r.z), ux, uy, 0u)
+                : walk_start(S.tau[cell], u01(r.y), u01(r.z), ux, uy, 0u);
   }
   append_inside(keep, slot, h, cell, ws, 1.0f, out, in_count, slot_live);
 }
@@ -518,7 +525,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk_wave_kernel(
   uint64_t h = 0, seed = 0;
   float w = 0.0f, tau = 0.0f, cc = 0.0f;
   uint32_t budget = 0;
-  bool sph = false;
+  bool sph = false, rect = false;
+  float ty = 0.0f;
   for (;;) {
     const bool need = k == live && !drained;
     if (__any_sync(0xffffffffu, need)) {
@@ -542,6 +550,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk_wave_kernel(
           cc = S.c[cell];
           seed = S.seed;
           sph = S.xy != 0;
+          rect = S.rect != 0;
+          ty = tau * S.ry;
           budget = cap;
           if constexpr (FROM_FACE) {
             // point on face F with counter-clockwise parameter 1 - xi
@@ -553,7 +563,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk_wave_kernel(
               case 2: X = xi; Y = 1.0f; break;
               default: X = 0.0f; Y = xi; break;
             }
-            ws = walk_start(tau, X, Y, fin.gx[k], fin.gy[k], fin.ev[k]);
+            ws = rect ? walk_start_rect(tau, ty, X, Y, fin.gx[k], fin.gy[k], fin.ev[k])
+                      : walk_start(tau, X, Y, fin.gx[k], fin.gy[k], fin.ev[k]);
           } else {
             ws.x = iin.x[k];
             ws.y = iin.y[k];
@@ -573,7 +584,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk_wave_kernel(
     WalkResult wr;
     if (k < live) {
       const uint32_t r = budget < kWalkRound ? budget : kWalkRound;
-      wr = walk_cell_resume(tau, cc, 1, ws, r, seed, h, sph);
+      wr = rect ? walk_cell_resume_rect(tau, ty, cc, 1, ws, r, seed, h)
+                : walk_cell_resume(tau, cc, 1, ws, r, seed, h, sph);
       budget -= r;
       ended = wr.status != kTruncated || budget == 0 || ws.ncoll >= kMaxFlights;
     }
@@ -683,6 +695,12 @@ __global__ void gmc_prep_kernel(int64_t live, Bank in, const Slot *__restrict__ 
   cond[2 * live + k] = uy;
   cond[3 * live + k] = S.ltau_n[cell];
   cond[4 * live + k] = S.c_n[cell];
+  if (S.rect) {
+    // canonical sides: a quarter turn exchanges width and height
+    const bool odd = ((F + 1) & 1) != 0;
+    cond[3 * live + k] = S.ltau_n[cell] + (odd ? S.lry : 0.0f);
+    cond[5 * live + k] = odd ? -S.lry : S.lry;
+  }
   const float4 z = box_muller4(philox_draw(S.seed, in.hist[k], in.ev[k], kTagNoise));
   noise[k] = z.x;
   noise[live + k] = z.y;
@@ -778,6 +796,8 @@ struct Request {
   int method = GMC_METHOD_ANALOG;
   bool wall = false;  // source on the left boundary (cdf over the ny rows)
   bool xy = false;    // x-y geometry (transport_solve_xy, transport_solve_wall_xy)
+  bool rect = false;  // rectangular cells dx x dy (transport_solve_rect); tau holds sigma dx
+  float dx = 1.0f, dy = 1.0f;
   // engine state
   int slot = -1;
   int64_t next_hist = 0;
@@ -831,7 +851,7 @@ bool equivalent_condition(double tau, double c, double t_lo, double t_hi, double
 // instead of ny*nx volumetric strengths.
 gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
                         const float *source, int64_t n_histories, int method, uint64_t seed,
-                        Request &R, bool wall = false, bool xy = false) {
+                        Request &R, bool wall = false, bool xy = false, bool rect = false) {
   if (nx < 1 || ny < 1 || (int64_t)nx * ny > (1 << 26))
     return set_error(ctx, GMC_EINVAL, "solve: grid must be 1..2^26 cells");
   if (!tau || !c || !source) return set_error(ctx, GMC_EINVAL, "solve: null array");
@@ -880,9 +900,20 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
   }
   R.wall = wall;
   R.xy = xy;
-  // the solves' cells are squares: a network of rectangular cells (six
+  R.rect = rect;
+  if (rect && method == GMC_METHOD_GMC) {
+    // rectangular cells: the boundary network must take the aspect (six
+    // condition rows); births are walked
+    if (!ctx->net.loaded || ctx->net.stats.ncond != kCondRect)
+      return set_error(ctx, GMC_EINVAL,
+                       "rectangular-cell solve: GMC needs a network of rectangular cells");
+    if (check_net_path(ctx, ctx->net, ctx->cfg.precision, ctx->cfg.sampler_kernel,
+                       "rectangular-cell solve") != GMC_OK)
+      return GMC_EINVAL;
+  }
+  // the square solves' cells: a network of rectangular cells (six
   // condition rows) has no place in them
-  if (method == GMC_METHOD_GMC) {
+  if (method == GMC_METHOD_GMC && !rect) {
     const NetDev *nets[4] = {&ctx->net, &ctx->internal, &ctx->xy, &ctx->internal_xy};
     for (const NetDev *N : nets)
       if (N->loaded && N->stats.ncond != kCond &&
@@ -902,7 +933,7 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
   } else if (method == GMC_METHOD_GMC && !ctx->net.loaded) {
     return set_error(ctx, GMC_ENOWEIGHTS, "solve: GMC needs gmc_load_weights");
   }
-  if (method == GMC_METHOD_GMC && !xy) {
+  if (method == GMC_METHOD_GMC && !xy && !rect) {
     const gmc_config &cf = ctx->cfg;
     if (check_net_path(ctx, ctx->net, cf.precision, cf.sampler_kernel, "solve") != GMC_OK ||
         (ctx->internal.loaded &&
@@ -990,7 +1021,7 @@ class Engine {
     GMC_CUDA_TRY(ctx_, cudaMalloc(&ibank_mem_[0], C_ * kIBankBytesPerParticle));
     GMC_CUDA_TRY(ctx_, cudaMalloc(&ibank_mem_[1], C_ * kIBankBytesPerParticle));
     if (method_ == GMC_METHOD_GMC) {
-      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_cond_, C_ * 5 * sizeof(float)));
+      GMC_CUDA_TRY(ctx_, cudaMalloc(&d_cond_, C_ * 6 * sizeof(float)));  // 6 rows: rectangular cells
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_noise_, C_ * 4 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_exit_, C_ * 4 * sizeof(float)));
       GMC_CUDA_TRY(ctx_, cudaMalloc(&d_bias1_, 2 * kBias1Floats * sizeof(float)));
@@ -1027,7 +1058,7 @@ class Engine {
   bool try_admit(Request *R, gmc_status *err) {
     *err = GMC_OK;
     if (active_ >= kMaxSlots) return false;
-    if (active_ > 0 && R->xy != xy_) return false;
+    if (active_ > 0 && (R->xy != xy_ || R->rect != rect_)) return false;
     size_t off;
     if (!pool_.alloc(R->footprint, &off)) return false;
     int slot = -1;
@@ -1049,7 +1080,8 @@ class Engine {
     R->d_flux = (double *)(p + 5 * a4 + a8);
     R->d_walk = (uint8_t *)(p + 5 * a4 + 2 * a8);
     Slot S{R->nx, R->ny, R->d_tau, R->d_c, R->d_flux, R->seed,
-           R->d_ltau_n, R->d_c_n, R->d_s_scale, R->d_walk, R->xy ? 1 : 0};
+           R->d_ltau_n, R->d_c_n, R->d_s_scale, R->d_walk, R->xy ? 1 : 0,
+           R->rect ? 1 : 0, R->dy / R->dx, std::log(R->dy / R->dx), R->dy};
     cudaError_t e = cudaMemcpyAsync(R->d_tau, R->tau.data(), n * 4, cudaMemcpyHostToDevice, s_);
     if (!e) e = cudaMemcpyAsync(R->d_c, R->c.data(), n * 4, cudaMemcpyHostToDevice, s_);
     if (!e) e = cudaMemcpyAsync(R->d_ltau_n, R->ltau_n.data(), n * 4, cudaMemcpyHostToDevice, s_);
@@ -1075,6 +1107,7 @@ class Engine {
     reqs_[slot] = R;
     ++active_;
     xy_ = R->xy;
+    rect_ = R->rect;
     return true;
   }
 
@@ -1117,7 +1150,7 @@ class Engine {
         if (R) R->live += h_counts_[3 + R->slot];
     }
     const NetDev &inet = xy_ ? ctx_->internal_xy : ctx_->internal;
-    if (pending > 0 && room > 0 && method_ == GMC_METHOD_GMC && inet.loaded) {
+    if (pending > 0 && room > 0 && method_ == GMC_METHOD_GMC && inet.loaded && !rect_) {
       const gmc_status sb = births_internal(pending, room, rules);
       if (sb != GMC_OK) return sb;
     } else if (pending > 0 && room > 0) {
@@ -1366,7 +1399,8 @@ class Engine {
   int *h_counts_ = nullptr;
   Request *reqs_[kMaxSlots];
   int active_ = 0;
-  bool xy_ = false;  // geometry of the admitted requests
+  bool xy_ = false;    // geometry of the admitted requests
+  bool rect_ = false;
 };
 
 // The server: a worker thread running the engine over admitted requests.
@@ -1447,12 +1481,16 @@ extern "C" {
 namespace {
 gmc_status solve_one(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
                      const float *source, int64_t n_histories, int method, uint64_t seed,
-                     double *flux, gmc_solve_stats *stats, bool wall, bool xy = false) {
+                     double *flux, gmc_solve_stats *stats, bool wall, bool xy = false,
+                     bool rect = false, float dx = 1.0f, float dy = 1.0f) {
   if (!ctx) return GMC_EINVAL;
   if (!flux) return set_error(ctx, GMC_EINVAL, "transport_solve: null flux");
   Request R;
-  gmc_status st = make_request(ctx, nx, ny, tau, c, source, n_histories, method, seed, R, wall, xy);
+  gmc_status st =
+      make_request(ctx, nx, ny, tau, c, source, n_histories, method, seed, R, wall, xy, rect);
   if (st != GMC_OK) return st;
+  R.dx = dx;
+  R.dy = dy;
   cudaSetDevice(ctx->device);
   const int64_t C = ctx->cfg.bank_capacity;
   Engine *E = ctx->solver;
@@ -1496,6 +1534,21 @@ gmc_status transport_solve_wall(gmc_ctx *ctx, int nx, int ny, const float *tau, 
                                 const float *wall, int64_t n_histories, int method, uint64_t seed,
                                 double *flux, gmc_solve_stats *stats) {
   return solve_one(ctx, nx, ny, tau, c, wall, n_histories, method, seed, flux, stats, true);
+}
+
+gmc_status transport_solve_rect(gmc_ctx *ctx, int nx, int ny, const float *sigma, const float *c,
+                                const float *source, float dx, float dy, int64_t n_histories,
+                                int method, uint64_t seed, double *flux, gmc_solve_stats *stats) {
+  if (!ctx) return GMC_EINVAL;
+  if (!(dx > 0.0f) || !(dy > 0.0f) || !std::isfinite(dx) || !std::isfinite(dy))
+    return set_error(ctx, GMC_EINVAL, "transport_solve_rect: need finite dx, dy > 0");
+  if (nx < 1 || ny < 1 || (int64_t)nx * ny > (1 << 26) || !sigma)
+    return set_error(ctx, GMC_EINVAL, "transport_solve_rect: grid must be 1..2^26 cells");
+  // the cells' optical widths sigma dx (the heights follow as sigma dy)
+  std::vector<float> tx((size_t)nx * ny);
+  for (size_t k = 0; k < tx.size(); ++k) tx[k] = sigma[k] * dx;
+  return solve_one(ctx, nx, ny, tx.data(), c, source, n_histories, method, seed, flux, stats, false,
+                   false, true, dx, dy);
 }
 
 gmc_status transport_solve_xy(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,

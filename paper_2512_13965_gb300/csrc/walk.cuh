@@ -373,6 +373,107 @@ __device__ __forceinline__ WalkResult walk_xy(T tx, T ty, float c, int implicit,
   return w;
 }
 
+// walk_box_from in a rectangle [0, tx] x [0, ty] (rectangular cells in the
+// solve): the same flights, draws and exit rule, q normalized per face as
+// walk_rect. A separate function, so the square cells' walk is unchanged.
+template <typename T>
+__device__ __forceinline__ WalkResult walk_rect_from(T tx, T ty, float c, int implicit, T &x, T &y,
+                                                     T &s, float &ux, float &uy, uint32_t &event,
+                                                     uint32_t &ncoll, uint32_t max_flights,
+                                                     uint64_t seed, uint64_t id) {
+  const float rate = implicit ? c : 1.0f;
+  WalkResult w;
+  w.status = kTruncated;
+  w.face = -1;
+  w.q = 0.0f;
+  for (uint32_t it = 0; it < max_flights; ++it) {
+    const uint4 r = philox_draw(seed, id, event, kTagWalk);
+    ++event;
+    const float df = rate > 0.0f ? -logf(u01(r.x)) / rate : INFINITY;
+    const T d = (T)df;
+    bool xface;
+    T db;
+    if (flight_exits(tx, ty, x, y, ux, uy, df, xface, db)) {
+      s += db;
+      int face;
+      T qn;
+      if (xface) {
+        face = ux > 0.0f ? 1 : 3;
+        const T along = y + db * (T)uy;
+        qn = face == 1 ? along / ty : (ty - along) / ty;
+      } else {
+        face = uy > 0.0f ? 2 : 0;
+        const T along = x + db * (T)ux;
+        qn = face == 0 ? along / tx : (tx - along) / tx;
+      }
+      w.status = kExited;
+      w.face = face;
+      w.q = fminf(fmaxf((float)qn, 0.0f), 1.0f);
+      break;
+    }
+    s += d;
+    x += d * (T)ux;
+    y += d * (T)uy;
+    ++ncoll;
+    if (!implicit && u01(r.y) > c) {
+      w.status = kAbsorbed;
+      break;
+    }
+    sincospif(2.0f * u01(r.z), &uy, &ux);
+  }
+  w.ux = ux;
+  w.uy = uy;
+  w.s = (float)s;
+  w.ncoll = ncoll;
+  w.event = event;
+  return w;
+}
+
+// A walk in a rectangle [0, tx] x [0, ty] started at (X, Y) in normalized
+// cell coordinates (positions in FP64 when a side exceeds kTau64, as the
+// square cell's walk_start), and its resumption (walk_cell_resume).
+__device__ __forceinline__ WalkState walk_start_rect(float tx, float ty, float X, float Y, float ux,
+                                                     float uy, uint32_t event) {
+  WalkState st;
+  if (fmaxf(tx, ty) > kTau64) {
+    st.x = (double)X * (double)tx;
+    st.y = (double)Y * (double)ty;
+  } else {
+    st.x = (double)(X * tx);
+    st.y = (double)(Y * ty);
+  }
+  st.s = 0.0;
+  st.ux = ux;
+  st.uy = uy;
+  st.event = event;
+  st.ncoll = 0;
+  return st;
+}
+
+__device__ __forceinline__ WalkResult walk_cell_resume_rect(float tx, float ty, float c, int implicit,
+                                                            WalkState &st, uint32_t max_flights,
+                                                            uint64_t seed, uint64_t id) {
+  const uint32_t left = st.ncoll < kMaxFlights ? kMaxFlights - st.ncoll : 0u;
+  const uint32_t cap = max_flights < left ? max_flights : left;
+  WalkResult w;
+  if (fmaxf(tx, ty) > kTau64) {
+    double x = st.x, y = st.y, s = st.s;
+    w = walk_rect_from<double>((double)tx, (double)ty, c, implicit, x, y, s, st.ux, st.uy, st.event,
+                               st.ncoll, cap, seed, id);
+    st.x = x;
+    st.y = y;
+    st.s = s;
+  } else {
+    float x = (float)st.x, y = (float)st.y, s = (float)st.s;
+    w = walk_rect_from<float>(tx, ty, c, implicit, x, y, s, st.ux, st.uy, st.event, st.ncoll, cap,
+                              seed, id);
+    st.x = x;
+    st.y = y;
+    st.s = s;
+  }
+  return w;
+}
+
 // Walk from a point given in normalized cell coordinates (X, Y in [0,1]),
 // picking the position precision from the cell's optical size.
 __device__ __forceinline__ WalkResult walk_cell(float tau, float c, int implicit, float X, float Y,

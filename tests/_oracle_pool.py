@@ -13,6 +13,8 @@ oracle.transport do not cross process boundaries):
               | ("mlp_xy", weights_path, steps, integrator) | ("walk_global_xy",)
               | ("equivalent_xy", weights_path, steps, integrator, box),
      "geometry": "flat" (default) | "xy" (x-y solves: the *_xy samplers),
+     "cell": None | (dx, dy): rectangular cells (solve_gmc_rect; tau holds sigma;
+             samplers ("mlp_rect", weights_path, steps, integrator) | ("walk_global_rect",)),
      "internal": None | ("mlp", weights_path, steps, integrator)
                | ("mlp_xy", weights_path, steps, integrator)  (x-y internal model)
                | ("equivalent", weights_path, steps, integrator, box)}
@@ -69,6 +71,10 @@ def _sampler(spec, seed):
     if kind == "equivalent":
         return OT.equivalent_sampler(OT.mlp_sampler(_net(spec[1]), spec[2], spec[3], seed),
                                      OT.walk_sampler_global(seed), *spec[4])
+    if kind == "mlp_rect":
+        return OT.mlp_sampler_rect(_net(spec[1]), spec[2], spec[3], seed)
+    if kind == "walk_global_rect":
+        return OT.walk_sampler_global_rect(seed)
     if kind == "mlp_xy":
         return OT.mlp_sampler_xy(_net(spec[1]), spec[2], spec[3], seed)
     if kind == "walk_global_xy":
@@ -94,6 +100,9 @@ def solve_task(task):
         if spec[0] == "equivalent":
             internal = OT.equivalent_internal_sampler(internal, OT.walk_internal_sampler(seed),
                                                       *spec[4])
+    if task.get("cell"):  # rectangular cells: (dx, dy), tau holds sigma
+        dx, dy = task["cell"]
+        return OT.solve_gmc_rect(tau, c, src, dx, dy, task["n"], seed, _sampler(task["sampler"], seed))
     return OT.solve_gmc(tau, c, src, task["n"], seed, _sampler(task["sampler"], seed),
                         internal=internal, wall=task.get("wall"),
                         geometry=task.get("geometry", "flat"))

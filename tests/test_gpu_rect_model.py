@@ -13,6 +13,9 @@ against the oracle.
   a checkpoint that continues the run.
 * Paths that take square cells (solves, gmc_transmit_noalloc) and paths the
   network does not have (FP8, the CTA-pair kernel, BF16 training) refuse it.
+* Solves on rectangular cells (transport_solve_rect): on squares they are
+  the square solve; the random walk and GMC with a rectangular-cell network
+  against the oracle's solve on rectangles, cell by cell.
 """
 import numpy as np
 import pytest
@@ -266,3 +269,80 @@ def test_rect_training_lowers_loss_commits_and_resumes(rctx, rtrain, tmp_path):
     b = np.zeros_like(a)
     g.gmc_train_params(ctx, b)
     assert np.abs(b - a).max() <= 1e-6 * max(1.0, np.abs(a).max())
+
+
+# ---- rectangular cells in the solve (transport_solve_rect) -----------------
+
+def _solve_rect(ctx, sig, c, src, dx, dy, n, method, seed):
+    import paper_2512_13965_gb300 as g
+    ny, nx = sig.shape
+    f = np.zeros(ny * nx)
+    st = g.transport_solve_rect(ctx, nx, ny, *(np.ascontiguousarray(a, np.float32).ravel()
+                                               for a in (sig, c, src)), dx, dy, n, method, seed, f)
+    return f.reshape(ny, nx), st.as_dict()
+
+
+def test_rect_solve_on_square_cells_is_the_square_solve(rctx):
+    # dx = dy = 1: the walk of the rectangle with equal sides, flux divided by
+    # 1: the random-walk solve equals transport_solve on tau = sigma
+    import paper_2512_13965_gb300 as g
+    ctx = rctx["ctx"]
+    tau, c, src = synth.grid_problem(n=16, seed=61, tau_range=(0.1, 5.0), block=4, source=4)
+    a, sa = _solve_rect(ctx, tau, c, src, 1.0, 1.0, 20000, g.GMC_METHOD_ANALOG, 5)
+    f = np.zeros(256)
+    sb = g.transport_solve(ctx, 16, 16, *(np.ascontiguousarray(x, np.float32).ravel()
+                                           for x in (tau, c, src)), 20000, g.GMC_METHOD_ANALOG, 5, f)
+    np.testing.assert_allclose(a.ravel(), f, rtol=1e-12, atol=1e-15)
+    assert sa["transmissions"] == sb.transmissions
+
+
+def _percell_rect(ctx, sig, c, src, dx, dy, method, sampler, K=8, n_gpu=20000, n_oracle=4000):
+    import _oracle_pool as P
+    gpu = [_solve_rect(ctx, sig, c, src, dx, dy, n_gpu, method, 1000 + k)[0] for k in range(K)]
+    tasks = [{"grid": (sig, c, src), "n": n_oracle, "seed": 2000 + k, "sampler": sampler,
+              "internal": None, "wall": None, "cell": (dx, dy)} for k in range(K)]
+    orc = P.solve_many(tasks)
+    P.assert_per_cell(gpu, [f for f, _ in orc])
+
+
+def test_rect_analog_solve_per_cell(rctx):
+    import paper_2512_13965_gb300 as g
+    sig, c, src = synth.grid_problem(n=16, seed=63, tau_range=(0.2, 8.0), block=4, source=4)
+    _percell_rect(rctx["ctx"], sig, c, src, 0.5, 1.5, g.GMC_METHOD_ANALOG, ("walk_global_rect",))
+
+
+def test_rect_gmc_solve_per_cell(rctx):
+    # GMC with the rectangular-cell test network, FP32, against the oracle's
+    # event loop with the same network (canonical sides per entry face)
+    # (the Kaiming rectangular-cell network: zero biases and identity
+    # standardization keep the track lengths free of a heavy tail, so the
+    # per-cell spread is estimable from 8 runs)
+    import paper_2512_13965_gb300 as g
+    ctx = rctx["ctx"]
+    path = str(rctx["dir"] / "rect_kaiming.bin")
+    synth.write_weights(path, synth.kaiming_weights_rect(1))
+    g.gmc_load_weights(ctx, path)
+    cfg = g.gmc_get_config(ctx)
+    cfg.precision, cfg.steps, cfg.integrator, cfg.gmc_min_tau = g.GMC_FP32, 4, g.GMC_EULER, 0.0
+    cfg.bank_capacity = 1 << 16
+    g.gmc_set_config(ctx, cfg)
+    # sigma dx and sigma dy inside the networks' box [0.1, 1000], c in [0.5, 0.999]
+    sig, c, src = synth.grid_problem(n=16, seed=65, tau_range=(0.4, 8.0), block=4, source=4)
+    _percell_rect(ctx, sig, c, src, 0.5, 1.5, g.GMC_METHOD_GMC, ("mlp_rect", path, 4, "euler"))
+
+
+def test_rect_solve_needs_a_rect_network():
+    import os
+    import paper_2512_13965_gb300 as g
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    ctx = g.Context(0)
+    try:
+        g.gmc_load_weights(ctx, os.path.join(root, "paper_2512_13965_gb300", "weights", "gmc_boundary.bin"))
+        sig, c, src = synth.grid_problem(n=8, seed=3, block=4, source=2)
+        with pytest.raises(g.GMCError) as e:
+            _solve_rect(ctx, sig, c, src, 0.5, 1.5, 100, g.GMC_METHOD_GMC, 1)
+        assert e.value.status == g.GMC_EINVAL
+    finally:
+        ctx.close()
