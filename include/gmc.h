@@ -447,7 +447,10 @@ gmc_status transport_solve_wall_xy(gmc_ctx *ctx, int nx, int ny, const float *ta
  * quarter turn exchanges the two sides). flux: per source particle per unit
  * area, Delta w / (sigma_a dx dy) (Eq. 7). The box of scattering-equivalent
  * conditions (gmc_config.net_*) applies to sigma dx. Volumetric sources only.
- * Other arguments, the result and blocking as for transport_solve.
+ * GMC_EINVAL as well for dx or dy not finite and > 0, dy / dx outside
+ * [1e-37, 1e37], or a cell with sigma dy outside (0, 1e38] (the walk forms
+ * the height in FP32). Other arguments, the result and blocking as for
+ * transport_solve.
  */
 gmc_status transport_solve_rect(gmc_ctx *ctx, int nx, int ny, const float *sigma, const float *c,
                                 const float *source, float dx, float dy, int64_t n_histories,

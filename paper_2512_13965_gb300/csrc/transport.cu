@@ -1544,9 +1544,19 @@ gmc_status transport_solve_rect(gmc_ctx *ctx, int nx, int ny, const float *sigma
     return set_error(ctx, GMC_EINVAL, "transport_solve_rect: need finite dx, dy > 0");
   if (nx < 1 || ny < 1 || (int64_t)nx * ny > (1 << 26) || !sigma)
     return set_error(ctx, GMC_EINVAL, "transport_solve_rect: grid must be 1..2^26 cells");
+  // the kernels form the height as tx (dy / dx) in FP32: the aspect and
+  // every height must stay finite there (1e38 leaves room for the rounding)
+  const double ry = (double)dy / (double)dx;
+  if (!(ry >= 1e-37 && ry <= 1e37))
+    return set_error(ctx, GMC_EINVAL, "transport_solve_rect: dy / dx must lie in [1e-37, 1e37]");
   // the cells' optical widths sigma dx (the heights follow as sigma dy)
   std::vector<float> tx((size_t)nx * ny);
-  for (size_t k = 0; k < tx.size(); ++k) tx[k] = sigma[k] * dx;
+  for (size_t k = 0; k < tx.size(); ++k) {
+    const double h = (double)sigma[k] * dy;
+    if (!(h > 0.0 && h <= 1e38))
+      return set_error(ctx, GMC_EINVAL, "transport_solve_rect: cell %zu needs 0 < sigma dy <= 1e38", k);
+    tx[k] = sigma[k] * dx;
+  }
   return solve_one(ctx, nx, ny, tx.data(), c, source, n_histories, method, seed, flux, stats, false,
                    false, true, dx, dy);
 }

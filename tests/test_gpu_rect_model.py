@@ -344,5 +344,11 @@ def test_rect_solve_needs_a_rect_network():
         with pytest.raises(g.GMCError) as e:
             _solve_rect(ctx, sig, c, src, 0.5, 1.5, 100, g.GMC_METHOD_GMC, 1)
         assert e.value.status == g.GMC_EINVAL
+        # sizes the walk cannot hold in FP32: refused on the host, any method
+        for dx, dy, s in ((0.0, 1.0, 1.0), (1.0, float("inf"), 1.0), (1e-30, 1e10, 1.0),
+                          (1.0, 1e30, 1e10)):
+            with pytest.raises(g.GMCError) as e:
+                _solve_rect(ctx, sig * s, c, src, dx, dy, 100, g.GMC_METHOD_ANALOG, 1)
+            assert e.value.status == g.GMC_EINVAL, (dx, dy, s)
     finally:
         ctx.close()
