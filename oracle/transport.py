@@ -708,6 +708,19 @@ def mlp_sampler_rect(net, steps, integrator, seed):
     return f
 
 
+def walk_sampler_rect(seed):
+    """Stage 2 replaced by the implicit-capture walk in the canonical frame of
+    a rectangular cell, as the training pairs take it (transmit_rect: entry
+    on the left face at y = xi ty_c, width tx_c behind it): the solve with
+    this sampler reproduces a random-walk solve only if the canonical sides
+    the solve hands over match the convention of the training pairs."""
+    def f(xi, cos_c, sin_c, tx_c, ty_c, c, ids, events, rot=None):
+        r = transmit_rect(xi, cos_c, sin_c, tx_c, ty_c, c, MODE_IMPLICIT, seed, ids=ids,
+                          events=events)
+        return r["face"], r["q"], r["ux"], r["uy"], r["s"], r["events"]
+    return f
+
+
 def walk_sampler_global_rect(seed):
     """The random walk through a rectangular cell in the cell's own (global)
     frame, as a random-walk solve takes it (walk_sampler_global for

@@ -143,3 +143,44 @@ def test_rect_solve_with_a_network_runs_and_balances(tmp_path):
     f, st = OT.solve_gmc_rect(sig, c, src, 2.0, 0.5, 300, 11, OT.mlp_sampler_rect(net, 4, "euler", 11))
     assert np.all(np.isfinite(f)) and f.sum() > 0
     assert abs(st["leak"] + st["absorbed"] - st["roulette_net"] - 300) < 1e-6 * 300
+
+
+_CANON = dict(sig=np.array([[1.4, 4.0, 0.8], [3.0, 0.6, 2.2]]),
+              c=np.array([[0.9, 0.6, 0.99], [0.5, 0.95, 0.8]]),
+              src=np.array([[0.0, 1.0, 0.0], [0.5, 0.0, 0.0]]), dx=0.5, dy=1.5, K=8, n=12000)
+
+
+@pytest.fixture(scope="module")
+def global_walk_rect_runs():
+    P = _CANON
+    return np.asarray([_global_walk_rect(P["sig"], P["c"], P["src"], P["dx"], P["dy"], P["n"], 400 + k)
+                       for k in range(P["K"])]).reshape(P["K"], -1)
+
+
+def _canonical_walk_z(B):
+    P = _CANON
+    A = np.asarray([OT.solve_gmc_rect(P["sig"], P["c"], P["src"], P["dx"], P["dy"], P["n"], 300 + k,
+                                      OT.walk_sampler_rect(300 + k), w_cut=0.0)[0]
+                    for k in range(P["K"])]).reshape(P["K"], -1)
+    se = np.sqrt(A.var(0, ddof=1) / P["K"] + B.var(0, ddof=1) / P["K"])
+    return np.abs(A.mean(0) - B.mean(0)) / se
+
+
+def test_canonical_sides_match_the_training_convention(global_walk_rect_runs):
+    # stage 2 as the walk the training pairs take (transmit_rect in the
+    # canonical rectangle tx_c x ty_c, entered on its left face): the solve
+    # must reproduce the independent whole-grid walker cell by cell, which
+    # holds only if the sides handed over per entry face are the ones the
+    # training pairs were drawn with (aspect 3 cells, so an exchange shows)
+    z = _canonical_walk_z(global_walk_rect_runs)
+    assert z.max() < 4.5, z
+
+
+@pytest.mark.parametrize("wrong", ["never_exchanged", "always_exchanged"])
+def test_a_wrong_side_convention_is_detected(global_walk_rect_runs, monkeypatch, wrong):
+    # the same comparison with the quarter-turn rule broken in the oracle
+    # (measured: z up to 10 and 15 at these sizes, against 1.4 for the rule)
+    bad = {"never_exchanged": lambda tx, ty, rot: (tx, ty),
+           "always_exchanged": lambda tx, ty, rot: (ty, tx)}[wrong]
+    monkeypatch.setattr(OT, "canonical_sides", bad)
+    assert _canonical_walk_z(global_walk_rect_runs).max() > 6.0
