@@ -242,6 +242,19 @@ def mlp_sampler_xy(net, steps, integrator, seed):
     return f
 
 
+def walk_sampler_xy(seed):
+    """Stage 2 in x-y geometry replaced by the walk the x-y training pairs
+    take (transmit_xy in the canonical frame, out-of-plane entry component
+    sqrt(1 - ux^2 - uy^2) from the handed-over projection)."""
+    def f(xi, ux_c, uy_c, tau, c, ids, events, rot=None):
+        ux_c, uy_c = np.asarray(ux_c, np.float64), np.asarray(uy_c, np.float64)
+        uz = np.sqrt(np.maximum(1.0 - ux_c * ux_c - uy_c * uy_c, 0.0))
+        r = transmit_xy(xi, ux_c, uy_c, uz, tau, tau, c, MODE_IMPLICIT, seed, ids=ids,
+                        events=events)
+        return r["face"], r["q"], r["ux"], r["uy"], r["s"], r["events"]
+    return f
+
+
 def walk_sampler(seed):
     """Stage 2 replaced by the implicit-capture random walk in the canonical frame."""
     def f(xi, cos_c, sin_c, tau, c, ids, events, rot=None):

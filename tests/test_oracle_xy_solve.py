@@ -252,3 +252,45 @@ def test_xy_internal_pairs_straight_chords():
     np.testing.assert_allclose(q, pos, atol=1e-9)
     # the directions follow the sphere: E|u|^2 = 2/3
     assert abs(np.mean(ux * ux + uy * uy) - 2.0 / 3.0) < 0.06
+
+
+_CANON = dict(tau=np.array([[0.7, 2.0, 0.4], [1.5, 0.3, 1.1], [0.9, 2.6, 0.5]]),
+              c=np.array([[0.9, 0.6, 0.99], [0.5, 0.95, 0.8], [0.7, 0.9, 0.6]]),
+              src=np.array([[0.5, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 0.0]]), K=8, n=8000)
+
+
+@pytest.fixture(scope="module")
+def global_walk_xy_runs():
+    P = _CANON
+    return np.asarray([_global_walk_xy(P["tau"], P["c"], P["src"], P["n"], 500 + k)
+                       for k in range(P["K"])]).reshape(P["K"], -1)
+
+
+def _canonical_xy_z(B, wrap=lambda f: f):
+    P = _CANON
+    A = np.asarray([OT.solve_gmc(P["tau"], P["c"], P["src"], P["n"], 600 + k,
+                                 wrap(OT.walk_sampler_xy(600 + k)), geometry="xy", w_cut=0.0)[0]
+                    for k in range(P["K"])]).reshape(P["K"], -1)
+    se = np.sqrt(A.var(0, ddof=1) / P["K"] + B.var(0, ddof=1) / P["K"])
+    return np.abs(A.mean(0) - B.mean(0)) / se
+
+
+def test_xy_hand_over_matches_the_training_convention(global_walk_xy_runs):
+    # stage 2 as the walk the x-y training pairs take (transmit_xy in the
+    # canonical frame, the out-of-plane component rebuilt from the handed-over
+    # projection): the x-y event loop must reproduce the independent
+    # whole-grid walker cell by cell (measured max z 1.95)
+    assert _canonical_xy_z(global_walk_xy_runs).max() < 4.5
+
+
+def test_xy_hand_over_as_unit_circle_is_detected(global_walk_xy_runs):
+    # planted: exits handed on as unit in-plane directions (the disk
+    # encoding lost, uz = 0 in the next cell); measured max z 13
+    def wrap(f):
+        def g(*a, **k):
+            face, q, ux, uy, s, ev = f(*a, **k)
+            r = np.hypot(ux, uy)
+            r = np.where(r > 0, r, 1.0)
+            return face, q, ux / r, uy / r, s, ev
+        return g
+    assert _canonical_xy_z(global_walk_xy_runs, wrap).max() > 6.0
