@@ -470,7 +470,10 @@ typedef struct gmc_solve_req {
 typedef struct gmc_serve_config {
     int method;           /* gmc_method used for every request */
     size_t memory_budget; /* device bytes for admitted requests' grids and
-                             tallies (24 B per cell, rounded); >= 1 MiB */
+                             tallies: 37 B per cell (tau, c, the networks'
+                             condition and track-length factor, the walk
+                             flag, source CDF, FP64 tally; each array
+                             rounded up to 256 B); >= 1 MiB */
 } gmc_serve_config;
 
 /*
@@ -629,11 +632,13 @@ gmc_status gmc_train_param_count_ctx(const gmc_ctx *ctx, int64_t *count);
  * and second moments, the step count, the hyperparameters (learning rate as
  * last set, betas, eps, weight decay, seed) and the standardization
  * statistics. gmc_train_state_size gives the size in bytes (a header plus
- * 3 gmc_train_param_count() floats). gmc_train_save_state writes a
+ * 3 gmc_train_param_count_ctx() floats). gmc_train_save_state writes a
  * checkpoint into `blob` (exactly that many bytes). gmc_train_load_state
  * restores one into the training state of gmc_train_begin, which must have
  * been called on the same dataset with the same batch and precision
- * (GMC_EINVAL otherwise; GMC_EFORMAT for a blob that is not a checkpoint).
+ * (GMC_EINVAL otherwise; GMC_EFORMAT for a blob that is not a checkpoint,
+ * or one of another network form: residual-modulated or not, square or
+ * rectangular cells).
  * The checkpoint records the dataset's size and its standardization
  * statistics, which gmc_train_begin recomputes from the data: other data (a
  * different size, or statistics that differ in any bit) gives GMC_EINVAL.
