@@ -292,7 +292,8 @@ def test_rect_solve_on_square_cells_is_the_square_solve(rctx):
     f = np.zeros(256)
     sb = g.transport_solve(ctx, 16, 16, *(np.ascontiguousarray(x, np.float32).ravel()
                                            for x in (tau, c, src)), 20000, g.GMC_METHOD_ANALOG, 5, f)
-    np.testing.assert_allclose(a.ravel(), f, rtol=1e-12, atol=1e-15)
+    # the same histories; FP64 atomic tallies add in any order
+    np.testing.assert_allclose(a.ravel(), f, rtol=1e-9, atol=1e-12 * np.abs(f).max())
     assert sa["transmissions"] == sb.transmissions
 
 
