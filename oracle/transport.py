@@ -762,7 +762,7 @@ def walk_sampler_global_rect(seed):
 
 
 def solve_gmc_rect(sigma, c, src, dx, dy, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1,
-                   max_waves=100000):
+                   max_waves=100000, wall=None):
     """The event-based solve on a grid of rectangular cells of physical size
     dx x dy (every cell alike) with cross sections sigma [ny, nx] and
     scattering ratios c: cell (i, j) has optical sides tx = sigma dx (along x)
@@ -772,7 +772,11 @@ def solve_gmc_rect(sigma, c, src, dx, dy, n_hist, seed, sampler, w_cut=1e-4, p_s
     canonical sides (canonical_sides). Flux per source particle per unit
     area: Delta w / (sigma_a dx dy) per Eq. 7 (the track length w l / (dx dy)
     for c = 1). Returns (flux [ny, nx], stats). With dx = dy = 1 this is
-    solve_gmc on tau = sigma."""
+    solve_gmc on tau = sigma.
+    wall: [ny] strengths of a surface source on the left boundary instead of
+    src (wall_births: row by strength, uniform height on the boundary cell's
+    left face, the cosine law; weight 1, next event 0); its first crossing
+    goes to `sampler` like every later one."""
     sig = np.asarray(sigma, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)
     ny, nx = sig.shape
@@ -782,13 +786,22 @@ def solve_gmc_rect(sigma, c, src, dx, dy, n_hist, seed, sampler, w_cut=1e-4, p_s
     flux = np.zeros(ny * nx, dtype=np.float64)
     st = np.zeros(6, dtype=np.float64)
     live = {k: [] for k in ("id", "i", "j", "F", "xi", "gx", "gy", "w", "ev")}
-    srcf = np.maximum(np.asarray(src, dtype=np.float64).ravel(), 0.0)
-    cdf = np.cumsum(srcf)
-    ids = np.arange(n_hist, dtype=np.uint64)
-    ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
-    cells = np.searchsorted(cdf, ub[0] * cdf[-1], side="left")
-    bux, buy = birth_directions(seed, ids, ub[3], "flat")
-    for h in range(n_hist):
+    n_src = n_hist
+    if wall is not None:
+        j, xi, gx, gy = wall_births(wall, n_hist, seed)
+        for h in range(n_hist):
+            for k, v in (("id", h), ("i", 0), ("j", int(j[h])), ("F", 3), ("xi", xi[h]),
+                         ("gx", gx[h]), ("gy", gy[h]), ("w", 1.0), ("ev", 0)):
+                live[k].append(v)
+        n_src = 0
+    else:
+        srcf = np.maximum(np.asarray(src, dtype=np.float64).ravel(), 0.0)
+        cdf = np.cumsum(srcf)
+        ids = np.arange(n_hist, dtype=np.uint64)
+        ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
+        cells = np.searchsorted(cdf, ub[0] * cdf[-1], side="left")
+        bux, buy = birth_directions(seed, ids, ub[3], "flat")
+    for h in range(n_src):
         k = int(cells[h])
         r = walk_one_rect(txf[k], tyf[k], cf[k], MODE_IMPLICIT, ub[1, h] * txf[k], ub[2, h] * tyf[k],
                           bux[h], buy[h], seed, h, 0)

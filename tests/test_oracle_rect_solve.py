@@ -11,6 +11,9 @@ with W != H).
   event loop against an independent walker that follows each history
   through the whole grid in physical coordinates, cell by cell on
   independent seeds.
+* A surface source on the left boundary: the square reduction history by
+  history, one pure-absorber rectangle by quadrature of the chord over the
+  entry height and the cosine law, and the grid walker started on the wall.
 """
 import math
 
@@ -62,21 +65,28 @@ def test_pure_absorber_rectangle_quadrature(dx, dy, sig):
     assert abs(st["leak"] / n - leak_q) < 4 * math.sqrt(leak_q * (1 - leak_q) / n) + 2e-4
 
 
-def _global_walk_rect(sig, c, src, dx, dy, n, seed):
+def _global_walk_rect(sig, c, src, dx, dy, n, seed, wall=None):
     """Independent walker on the grid in physical coordinates: flights drawn
     in scattering optical depth across cells (surface tracking), implicit
     capture, the track-length score of every segment divided by the cell
-    area, vacuum boundaries, no roulette; its own random numbers."""
+    area, vacuum boundaries, no roulette; its own random numbers. wall: [ny]
+    strengths of an isotropic surface source on x = 0 (row by strength,
+    uniform height, the cosine law) instead of src."""
     g = np.random.Generator(np.random.Philox(key=seed))
     ny, nx = sig.shape
     flux = np.zeros((ny, nx))
-    cdf = np.cumsum(src.ravel())
+    cdf = np.cumsum(src.ravel() if wall is None else wall)
     for _ in range(n):
         k = int(np.searchsorted(cdf, g.random() * cdf[-1], side="left"))
-        i, j = k % nx, k // nx
-        px, py = (i + g.random()) * dx, (j + g.random()) * dy
-        ph = 2 * np.pi * g.random()
-        ux, uy = math.cos(ph), math.sin(ph)
+        if wall is None:
+            i, j = k % nx, k // nx
+            px, py = (i + g.random()) * dx, (j + g.random()) * dy
+            ph = 2 * np.pi * g.random()
+            ux, uy = math.cos(ph), math.sin(ph)
+        else:
+            px, py = 0.0, (k + g.random()) * dy
+            uy = 2.0 * g.random() - 1.0
+            ux = math.sqrt(max(1.0 - uy * uy, 0.0))
         w = 1.0
         while True:
             left = -math.log(1.0 - g.random())
@@ -184,3 +194,48 @@ def test_a_wrong_side_convention_is_detected(global_walk_rect_runs, monkeypatch,
            "always_exchanged": lambda tx, ty, rot: (ty, tx)}[wrong]
     monkeypatch.setattr(OT, "canonical_sides", bad)
     assert _canonical_walk_z(global_walk_rect_runs).max() > 6.0
+
+
+def test_wall_source_on_square_cells_is_the_square_wall_solve():
+    sig = np.array([[0.7, 2.0, 0.4], [1.5, 0.3, 1.1]])
+    c = np.array([[0.9, 0.6, 0.99], [0.5, 0.95, 0.8]])
+    wall = np.array([1.0, 0.5])
+    a, sa = OT.solve_gmc_rect(sig, c, None, 1.0, 1.0, 500, 9, OT.walk_sampler_global_rect(9),
+                              wall=wall)
+    b, sb = OT.solve_gmc(sig, c, None, 500, 9, OT.walk_sampler_global(9), wall=wall)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=0)
+    assert sa["transmissions"] == sb["transmissions"] and sa["leak"] == sb["leak"]
+
+
+@pytest.mark.parametrize("dx,dy,sig", [(1.0, 0.25, 2.0), (0.5, 2.0, 0.8)])
+def test_wall_lit_pure_absorber_rectangle_quadrature(dx, dy, sig):
+    # entry at height eta ty on the left face, sin(theta) uniform in (-1, 1)
+    # (the cosine law), straight chord l: flux (1 - e^-l) / (sigma dx dy),
+    # leakage e^-l, averaged over eta and sin(theta) by the midpoint rule
+    tx, ty = sig * dx, sig * dy
+    m = 400
+    E, S = np.meshgrid((np.arange(m) + 0.5) / m, -1.0 + (np.arange(2 * m) + 0.5) / m, indexing="ij")
+    l = _chord2(np.zeros_like(E), E * ty, np.sqrt(1.0 - S * S), S, tx, ty)
+    sc = (1.0 - np.exp(-l)) / sig / (dx * dy)
+    f_q, var, leak_q = sc.mean(), sc.var(), np.exp(-l).mean()
+    n = 30_000
+    f, st = OT.solve_gmc_rect(np.full((1, 1), sig), np.zeros((1, 1)), None, dx, dy, n, 5,
+                              OT.walk_sampler_global_rect(5), w_cut=0.0, wall=np.ones(1))
+    assert abs(f[0, 0] - f_q) < 4 * math.sqrt(var / n) + 2e-4 * f_q, (f[0, 0], f_q)
+    assert abs(st["leak"] / n - leak_q) < 4 * math.sqrt(leak_q * (1 - leak_q) / n) + 2e-4
+
+
+def test_wall_source_event_loop_matches_the_grid_walker():
+    sig = np.array([[1.4, 4.0, 0.8], [3.0, 0.6, 2.2]])
+    c = np.array([[0.9, 0.6, 0.99], [0.5, 0.95, 0.8]])
+    wall = np.array([1.0, 0.4])
+    dx, dy = 0.5, 1.5
+    K, n = 8, 6000
+    A = np.asarray([OT.solve_gmc_rect(sig, c, None, dx, dy, n, 700 + k,
+                                      OT.walk_sampler_rect(700 + k), w_cut=0.0, wall=wall)[0]
+                    for k in range(K)]).reshape(K, -1)
+    B = np.asarray([_global_walk_rect(sig, c, None, dx, dy, n, 800 + k, wall=wall)
+                    for k in range(K)]).reshape(K, -1)
+    se = np.sqrt(A.var(0, ddof=1) / K + B.var(0, ddof=1) / K)
+    z = np.abs(A.mean(0) - B.mean(0)) / se
+    assert z.max() < 4.5, (z, A.mean(0), B.mean(0))
