@@ -686,11 +686,11 @@ __global__ void __launch_bounds__(FB_THREADS, 1) fwd_kernel(KP P) {
   if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
-// Input gradients: per tile the rounds dZ4 = (dV W5) S4 (K = 16, the dV image
+// Input gradients: per tile the stages dZ4 = (dV W5) S4 (K = 16, the dV image
 // from the forward kernel), then dZ3, dZ2, dZ1 (K = 256 against W_l^T), the
-// rounds alternating between two accumulators. The epilogue of a round
-// writes dZ chunk by chunk as the next round's A operand (shared memory;
-// the MMAs of the next round start on each chunk once written) and dZ^T for
+// stages alternating between two accumulators. The epilogue of a stage
+// writes dZ chunk by chunk as the next stage's A operand (shared memory;
+// the MMAs of the next stage start on each chunk once written) and dZ^T for
 // the weight gradients; S_l is loaded before the accumulator is ready.
 __global__ void __launch_bounds__(FB_THREADS, 1) bwd_kernel(KP P) {
   extern __shared__ unsigned char smem_raw[];
