@@ -1,0 +1,81 @@
+// Host-side rules of a transport solve that decide what the kernels are
+// given: each cell's network condition and routing, and the sizes a solve on
+// rectangular cells accepts. Plain C++ with no CUDA headers, so a host-only
+// unit test checks them against the oracle without a GPU.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+
+namespace gmc {
+
+// The scattering-equivalent condition of a cell (tau, c) in the training box
+// [t_lo, t_hi] x [c_lo, c_hi] of the networks. The networks learn the
+// implicit-capture walk (flights at rate c, absorption applied afterwards as
+// exp(-(1 - c) s), Eq. 4-5), which in a cell of side tau is the walk at rate
+// 1 in a cell of side c tau with every length divided by c: a cell (tau', c')
+// with c' tau' = c tau has the same exits, and s = s' c' / c. Inside the box
+// (tau', c') = (tau, c); outside, c' is the value of [max(c_lo, c tau / t_hi),
+// min(c_hi, c tau / t_lo)] nearest c and tau' = c tau / c' (clamped into the
+// box against rounding). Returns false where that interval is empty or
+// c tau = 0: no equivalent.
+inline bool equivalent_condition(double tau, double c, double t_lo, double t_hi, double c_lo,
+                                 double c_hi, double *tau_n, double *c_n) {
+  *tau_n = tau;
+  *c_n = c;
+  if (tau >= t_lo && tau <= t_hi && c >= c_lo && c <= c_hi) return true;
+  const double w = c * tau;
+  const double lo = std::max(c_lo, w / t_hi), hi = std::min(c_hi, w / t_lo);
+  if (!(w > 0.0) || !(lo <= hi)) return false;
+  *c_n = std::min(std::max(c, lo), std::max(lo, hi));
+  *tau_n = std::min(std::max(w / *c_n, t_lo), t_hi);
+  return true;
+}
+
+// What stage 1 and stage 3 of a GMC solve read per cell: the network's
+// condition (ln tau', c'), the track-length factor c' / c, and whether the
+// random walk crosses the cell instead (no equivalent condition, or thinner
+// than min_tau when min_tau > 0). FP64 arithmetic, stored as the kernels
+// read it.
+struct CellCondition {
+  float ltau_n;
+  float c_n;
+  float s_scale;
+  uint8_t walk;
+};
+
+inline CellCondition cell_condition(double tau, double c, double t_lo, double t_hi, double c_lo,
+                                    double c_hi, double min_tau) {
+  double tn, cn;
+  const bool ok = equivalent_condition(tau, c, t_lo, t_hi, c_lo, c_hi, &tn, &cn);
+  CellCondition r;
+  r.ltau_n = (float)std::log(tn);
+  r.c_n = (float)cn;
+  r.s_scale = ok ? (float)(cn / c) : 1.0f;
+  r.walk = (!ok || (min_tau > 0.0 && tau < min_tau)) ? 1 : 0;
+  return r;
+}
+
+// Sizes of a solve on rectangular cells dx x dy with cross sections sigma[n]:
+// the kernels form a cell's height as its optical width sigma dx times
+// dy / dx in FP32, so dx and dy must be finite and > 0, dy / dx within
+// [1e-37, 1e37], and every sigma dy within (0, 1e38] (room for the rounding
+// of the product). Returns 0 when the sizes are accepted; 1 for dx or dy,
+// 2 for the aspect, 3 for a cell, whose index goes to *bad_cell.
+inline int rect_sizes_check(const float *sigma, size_t n, float dx, float dy, size_t *bad_cell) {
+  if (!(dx > 0.0f) || !(dy > 0.0f) || !std::isfinite(dx) || !std::isfinite(dy)) return 1;
+  const double ry = (double)dy / (double)dx;
+  if (!(ry >= 1e-37 && ry <= 1e37)) return 2;
+  for (size_t k = 0; k < n; ++k) {
+    const double h = (double)sigma[k] * dy;
+    if (!(h > 0.0 && h <= 1e38)) {
+      *bad_cell = k;
+      return 3;
+    }
+  }
+  return 0;
+}
+
+}  // namespace gmc

@@ -53,6 +53,7 @@
 
 #include "decode.cuh"
 #include "gmc_internal.cuh"
+#include "host_rules.h"
 #include "philox.cuh"
 #include "walk.cuh"
 
@@ -823,29 +824,6 @@ size_t request_footprint(int64_t ncell) {
   return 5 * align256(ncell * 4) + align256(ncell) + 2 * align256(ncell * 8);
 }
 
-// The scattering-equivalent condition of a cell (tau, c) in the training box
-// [t_lo, t_hi] x [c_lo, c_hi] of the networks. The networks learn the
-// implicit-capture walk (flights at rate c, absorption applied afterwards as
-// exp(-(1 - c) s), Eq. 4-5), which in a cell of side tau is the walk at rate
-// 1 in a cell of side c tau with every length divided by c: a cell (tau', c')
-// with c' tau' = c tau has the same exits, and s = s' c' / c. Inside the box
-// (tau', c') = (tau, c); outside, c' is the value of [max(c_lo, c tau / t_hi),
-// min(c_hi, c tau / t_lo)] nearest c and tau' = c tau / c' (clamped into the
-// box against rounding). Returns false where that interval is empty or
-// c tau = 0: no equivalent.
-bool equivalent_condition(double tau, double c, double t_lo, double t_hi, double c_lo,
-                          double c_hi, double *tau_n, double *c_n) {
-  *tau_n = tau;
-  *c_n = c;
-  if (tau >= t_lo && tau <= t_hi && c >= c_lo && c <= c_hi) return true;
-  const double w = c * tau;
-  const double lo = std::max(c_lo, w / t_hi), hi = std::min(c_hi, w / t_lo);
-  if (!(w > 0.0) || !(lo <= hi)) return false;
-  *c_n = std::min(std::max(c, lo), std::max(lo, hi));
-  *tau_n = std::min(std::max(w / *c_n, t_lo), t_hi);
-  return true;
-}
-
 // Validates a solve description and copies it into a Request.
 // wall: `source` holds ny strengths of a surface source on the left boundary
 // instead of ny*nx volumetric strengths.
@@ -890,13 +868,12 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
   R.s_scale.resize(ncell);
   R.walk.assign(ncell, 0);
   for (int64_t k = 0; k < ncell; ++k) {
-    double tn, cn;
-    const bool ok = equivalent_condition((double)tau[k], (double)c[k], cf.net_tau_lo, cf.net_tau_hi,
-                                         cf.net_c_lo, cf.net_c_hi, &tn, &cn);
-    R.ltau_n[k] = (float)std::log(tn);
-    R.c_n[k] = (float)cn;
-    R.s_scale[k] = ok ? (float)(cn / (double)c[k]) : 1.0f;
-    R.walk[k] = (!ok || (cf.gmc_min_tau > 0.0 && (double)tau[k] < cf.gmc_min_tau)) ? 1 : 0;
+    const CellCondition cc = cell_condition((double)tau[k], (double)c[k], cf.net_tau_lo,
+                                            cf.net_tau_hi, cf.net_c_lo, cf.net_c_hi, cf.gmc_min_tau);
+    R.ltau_n[k] = cc.ltau_n;
+    R.c_n[k] = cc.c_n;
+    R.s_scale[k] = cc.s_scale;
+    R.walk[k] = cc.walk;
   }
   R.wall = wall;
   R.xy = xy;
@@ -1540,23 +1517,21 @@ gmc_status transport_solve_rect(gmc_ctx *ctx, int nx, int ny, const float *sigma
                                 const float *source, float dx, float dy, int64_t n_histories,
                                 int method, uint64_t seed, double *flux, gmc_solve_stats *stats) {
   if (!ctx) return GMC_EINVAL;
-  if (!(dx > 0.0f) || !(dy > 0.0f) || !std::isfinite(dx) || !std::isfinite(dy))
-    return set_error(ctx, GMC_EINVAL, "transport_solve_rect: need finite dx, dy > 0");
   if (nx < 1 || ny < 1 || (int64_t)nx * ny > (1 << 26) || !sigma)
     return set_error(ctx, GMC_EINVAL, "transport_solve_rect: grid must be 1..2^26 cells");
-  // the kernels form the height as tx (dy / dx) in FP32: the aspect and
-  // every height must stay finite there (1e38 leaves room for the rounding)
-  const double ry = (double)dy / (double)dx;
-  if (!(ry >= 1e-37 && ry <= 1e37))
-    return set_error(ctx, GMC_EINVAL, "transport_solve_rect: dy / dx must lie in [1e-37, 1e37]");
+  size_t bad = 0;
+  switch (rect_sizes_check(sigma, (size_t)nx * ny, dx, dy, &bad)) {
+    case 0: break;
+    case 1: return set_error(ctx, GMC_EINVAL, "transport_solve_rect: need finite dx, dy > 0");
+    case 2:
+      return set_error(ctx, GMC_EINVAL, "transport_solve_rect: dy / dx must lie in [1e-37, 1e37]");
+    default:
+      return set_error(ctx, GMC_EINVAL, "transport_solve_rect: cell %zu needs 0 < sigma dy <= 1e38",
+                       bad);
+  }
   // the cells' optical widths sigma dx (the heights follow as sigma dy)
   std::vector<float> tx((size_t)nx * ny);
-  for (size_t k = 0; k < tx.size(); ++k) {
-    const double h = (double)sigma[k] * dy;
-    if (!(h > 0.0 && h <= 1e38))
-      return set_error(ctx, GMC_EINVAL, "transport_solve_rect: cell %zu needs 0 < sigma dy <= 1e38", k);
-    tx[k] = sigma[k] * dx;
-  }
+  for (size_t k = 0; k < tx.size(); ++k) tx[k] = sigma[k] * dx;
   return solve_one(ctx, nx, ny, tx.data(), c, source, n_histories, method, seed, flux, stats, false,
                    false, true, dx, dy);
 }

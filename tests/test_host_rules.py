@@ -1,0 +1,149 @@
+"""The solve engine's host-side rules (csrc/host_rules.h), compiled into a
+host-only library with no GPU and checked against the oracle: each cell's
+scattering-equivalent condition and routing (the values stage 1 and stage 3
+of a GMC solve read), and the sizes a solve on rectangular cells accepts.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import transport as OT
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2512_13965_gb300", "csrc")
+
+WRAPPER = r'''
+#include "host_rules.h"
+using namespace gmc;
+extern "C" {
+void hr_equivalent(long n, const double *tau, const double *c, double t_lo, double t_hi,
+                   double c_lo, double c_hi, double *tau_n, double *c_n, int *ok) {
+  for (long k = 0; k < n; ++k)
+    ok[k] = equivalent_condition(tau[k], c[k], t_lo, t_hi, c_lo, c_hi, &tau_n[k], &c_n[k]);
+}
+void hr_cell_condition(long n, const float *tau, const float *c, double t_lo, double t_hi,
+                       double c_lo, double c_hi, double min_tau, float *ltau_n, float *c_n,
+                       float *s_scale, unsigned char *walk) {
+  for (long k = 0; k < n; ++k) {
+    const CellCondition r = cell_condition((double)tau[k], (double)c[k], t_lo, t_hi, c_lo, c_hi,
+                                           min_tau);
+    ltau_n[k] = r.ltau_n;
+    c_n[k] = r.c_n;
+    s_scale[k] = r.s_scale;
+    walk[k] = r.walk;
+  }
+}
+int hr_rect_sizes_check(const float *sigma, long n, float dx, float dy, long *bad) {
+  size_t b = (size_t)-1;
+  const int r = rect_sizes_check(sigma, (size_t)n, dx, dy, &b);
+  *bad = r == 3 ? (long)b : -1;
+  return r;
+}
+}
+'''
+
+BOX = (0.1, 1000.0, 0.5, 0.999)
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("needs g++")
+    d = tmp_path_factory.mktemp("host_rules")
+    src, so = d / "w.cpp", d / "libhr.so"
+    src.write_text(WRAPPER)
+    r = subprocess.run([gxx, "-std=c++17", "-O2", "-shared", "-fPIC", "-I", CSRC, str(src), "-o",
+                        str(so)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    L = ctypes.CDLL(str(so))
+    P, D, F, LG = ctypes.c_void_p, ctypes.c_double, ctypes.c_float, ctypes.c_long
+    L.hr_equivalent.argtypes = [LG, P, P, D, D, D, D, P, P, P]
+    L.hr_cell_condition.argtypes = [LG, P, P, D, D, D, D, D, P, P, P, P]
+    L.hr_rect_sizes_check.argtypes = [P, LG, F, F, P]
+    L.hr_rect_sizes_check.restype = ctypes.c_int
+    return L
+
+
+def _cells(n, seed):
+    # tau log-uniform over [1e-4, 1e5], c uniform in [0, 1], plus the edges:
+    # c = 0 and 1, the box's corners and sides, c tau at both ends of the
+    # range that has an equivalent (c_lo tau_lo, c_hi tau_hi), just inside
+    # and outside it
+    g = np.random.default_rng(seed)
+    tau = np.exp(g.uniform(np.log(1e-4), np.log(1e5), n))
+    c = g.uniform(0.0, 1.0, n)
+    t_lo, t_hi, c_lo, c_hi = BOX
+    edge_t = [t_lo, t_hi, 1.0, 0.05, 2000.0, t_lo * c_lo / 0.2, np.nextafter(t_lo, 0)]
+    edge_c = [0.0, 1.0, c_lo, c_hi, 0.2, np.nextafter(c_lo, 0), np.nextafter(c_hi, 2)]
+    et, ec = np.meshgrid(edge_t, edge_c)
+    lo_w, hi_w = c_lo * t_lo, c_hi * t_hi
+    wt = np.array([lo_w, hi_w, lo_w * (1 - 1e-12), hi_w * (1 + 1e-12), lo_w * (1 + 1e-12)])
+    return np.concatenate([tau, et.ravel(), wt / 0.3]), np.concatenate([c, ec.ravel(), np.full(5, 0.3)])
+
+
+def test_equivalent_condition_is_the_oracles(lib):
+    tau, c = _cells(20000, 3)
+    n = tau.size
+    tn, cn, ok = np.zeros(n), np.zeros(n), np.zeros(n, np.int32)
+    lib.hr_equivalent(n, tau.ctypes.data, c.ctypes.data, *BOX, tn.ctypes.data, cn.ctypes.data,
+                      ok.ctypes.data)
+    tp, cp, okp = OT.equivalent_condition(tau, c, BOX[:2], BOX[2:])
+    np.testing.assert_array_equal(ok.astype(bool), okp)
+    np.testing.assert_array_equal(tn, tp)
+    np.testing.assert_array_equal(cn, cp)
+    # what the map promises where it applies: c' tau' = c tau (to rounding)
+    # and (tau', c') inside the box
+    m = okp
+    np.testing.assert_allclose(cn[m] * tn[m], c[m] * tau[m], rtol=1e-14)
+    assert np.all((tn[m] >= BOX[0]) & (tn[m] <= BOX[1]) & (cn[m] >= BOX[2]) & (cn[m] <= BOX[3]))
+    # both sides of the reachable band, and c = 0, occur in the sample
+    assert okp.sum() > 1000 and (~okp).sum() > 1000 and not okp[c == 0].any()
+
+
+@pytest.mark.parametrize("min_tau", [0.0, 0.5])
+def test_cell_condition_is_what_the_kernels_read(lib, min_tau):
+    tau, c = _cells(20000, 5)
+    tau32, c32 = tau.astype(np.float32), c.astype(np.float32)
+    n = tau.size
+    lt, cn, ss = (np.zeros(n, np.float32) for _ in range(3))
+    walk = np.zeros(n, np.uint8)
+    lib.hr_cell_condition(n, tau32.ctypes.data, c32.ctypes.data, *BOX, min_tau, lt.ctypes.data,
+                          cn.ctypes.data, ss.ctypes.data, walk.ctypes.data)
+    t64, c64 = tau32.astype(np.float64), c32.astype(np.float64)
+    tp, cp, ok = OT.equivalent_condition(t64, c64, BOX[:2], BOX[2:])
+    np.testing.assert_array_equal(lt, np.log(tp).astype(np.float32))
+    np.testing.assert_array_equal(cn, cp.astype(np.float32))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        expect_s = np.where(ok, cp / c64, 1.0).astype(np.float32)
+    np.testing.assert_array_equal(ss, expect_s)
+    expect_walk = ~ok | ((min_tau > 0.0) & (t64 < min_tau))
+    np.testing.assert_array_equal(walk.astype(bool), expect_walk)
+    if min_tau > 0.0:
+        assert (walk.astype(bool) & ok).any()  # thin cells with an equivalent are walked too
+
+
+def _rect(lib, sigma, dx, dy):
+    s = np.ascontiguousarray(sigma, np.float32)
+    bad = ctypes.c_long(0)
+    r = lib.hr_rect_sizes_check(s.ctypes.data, s.size, dx, dy, ctypes.byref(bad))
+    return r, bad.value
+
+
+def test_rect_sizes_accepted_and_refused(lib):
+    sig = np.array([0.5, 3.0, 1e-3, 200.0])
+    assert _rect(lib, sig, 0.5, 1.5) == (0, -1)
+    assert _rect(lib, sig, 1.0, 1.0) == (0, -1)
+    for dx, dy in ((0.0, 1.0), (1.0, -1.0), (float("inf"), 1.0), (1.0, float("nan"))):
+        assert _rect(lib, sig, dx, dy)[0] == 1, (dx, dy)
+    assert _rect(lib, sig, 1e-30, 1e10)[0] == 2  # dy / dx = 1e40
+    assert _rect(lib, sig, 1e10, 1e-30)[0] == 2
+    assert _rect(lib, sig, 1e-20, 1e15)[0] == 0  # dy / dx = 1e35 with small heights
+    assert _rect(lib, [0.5, 1e10, 1.0], 1.0, 1e30) == (3, 1)  # sigma dy = 1e40
+    assert _rect(lib, [0.5, 0.0, 1.0], 1.0, 1.0) == (3, 1)
+    assert _rect(lib, [0.5, 1.0, -2.0], 1.0, 1.0) == (3, 2)
+    assert _rect(lib, [0.5, 1.0, float("nan")], 1.0, 1.0) == (3, 2)
