@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "gmc_internal.cuh"
+#include "gmcw.h"
 
 namespace gmc {
 
@@ -162,23 +163,6 @@ gmc_config default_config() {
   c.sampler_kernel = GMC_KERNEL_TILE;
   return c;
 }
-
-struct Reader {
-  const unsigned char *p;
-  size_t n, off = 0;
-  bool u32(uint32_t *v) {
-    if (off + 4 > n) return false;
-    std::memcpy(v, p + off, 4);
-    off += 4;
-    return true;
-  }
-  bool f32(float *v, size_t count) {
-    if (off + 4 * count > n) return false;
-    std::memcpy(v, p + off, 4 * count);
-    off += 4 * count;
-    return true;
-  }
-};
 
 }  // namespace
 }  // namespace gmc
@@ -370,53 +354,35 @@ gmc_status check_net_path(gmc_ctx *ctx, const NetDev &N, int precision, int kern
 // Nothing of N changes unless the blob parses; N stays marked unloaded from
 // the first change until every device copy is in place.
 gmc_status load_net(gmc_ctx *ctx, NetDev &N, const void *blob, size_t nbytes) {
-  static const uint32_t dims_ok[6] = {kIn, 256, 256, 256, 256, 4};
+  static_assert(kGmcwCond == kCond && kGmcwCondRect == kCondRect && kGmcwState == kState &&
+                    kGmcwEmb == kEmb && kGmcwHidden == kHidden && kGmcwFlagRM == kFlagRM,
+                "weight-file constants");
   if (ctx->server) return set_error(ctx, GMC_EBUSY, "loading weights: the server is running");
-  Reader rd{(const unsigned char *)blob, nbytes};
-  if (nbytes < 4 || std::memcmp(blob, "GMCW", 4) != 0)
-    return set_error(ctx, GMC_EFORMAT, "weight file: bad magic");
-  rd.off = 4;
-  uint32_t version, nl, dims[6], ncond, nstate, nemb, flags;
-  bool ok = rd.u32(&version) && rd.u32(&nl);
-  for (int i = 0; i < 6 && ok; ++i) ok = rd.u32(&dims[i]);
-  ok = ok && rd.u32(&ncond) && rd.u32(&nstate) && rd.u32(&nemb) && rd.u32(&flags);
-  if (!ok) return set_error(ctx, GMC_EFORMAT, "weight file: truncated header");
-  if (version != 1 || nl != 5 || (ncond != kCond && ncond != kCondRect) || nstate != 4 ||
-      nemb != 16 || (flags & ~kFlagRM) || (ncond != kCond && (flags & kFlagRM)))
-    return set_error(ctx, GMC_EFORMAT, "weight file: unsupported version, layout or flags");
-  const bool rm = (flags & kFlagRM) != 0;
-  const int nc = (int)ncond, nin = nc + kState + kEmb;
-  for (int i = 0; i < 6; ++i)
-    if (dims[i] != (i == 0 ? (uint32_t)nin : dims_ok[i]))
-      return set_error(ctx, GMC_EFORMAT,
-                       "weight file: layer dims must be 25-256-256-256-256-4 (26-... with n_cond 6)");
-  const int nst = 2 * nc + 2 * kState;
-  float st[2 * kCondRect + 2 * kState];
-  if (!rd.f32(st, nst)) return set_error(ctx, GMC_EFORMAT, "weight file: truncated statistics");
-  const size_t wl = sizeof(N.host_w[0]) / sizeof(float), bl = sizeof(N.host_b[0]) / sizeof(float);
-  std::vector<float> tw(5 * wl, 0.0f), tb(5 * bl, 0.0f);
-  for (int l = 0; l < 5; ++l) {
-    if (!rd.f32(&tw[l * wl], (size_t)dims[l + 1] * dims[l]) || !rd.f32(&tb[l * bl], dims[l + 1]))
-      return set_error(ctx, GMC_EFORMAT, "weight file: truncated layer %d", l);
-  }
-  std::vector<float> tm(3 * 256 * kCond, 0.0f), tg(3 * 512, 0.0f);
-  if (rm && (!rd.f32(tm.data(), tm.size()) || !rd.f32(tg.data(), tg.size())))
-    return set_error(ctx, GMC_EFORMAT, "weight file: truncated modulation arrays");
-  if (rd.off != nbytes) return set_error(ctx, GMC_EFORMAT, "weight file: trailing bytes");
-  for (int k = 0; k < nc; ++k)
-    if (!(st[nc + k] > 0.0f)) return set_error(ctx, GMC_EFORMAT, "weight file: cond_std must be > 0");
-  for (int k = 0; k < nst; ++k)
-    if (!std::isfinite(st[k])) return set_error(ctx, GMC_EFORMAT, "weight file: non-finite statistics");
+  GmcwNet P;
+  int bad_layer = -1;
+  const int ps = gmcw_parse(blob, nbytes, &P, &bad_layer);
+  if (ps == kGmcwTruncatedLayer)
+    return set_error(ctx, GMC_EFORMAT, "weight file: truncated layer %d", bad_layer);
+  if (ps != kGmcwOk) return set_error(ctx, GMC_EFORMAT, "weight file: %s", gmcw_status_text(ps));
+  const bool rm = P.rm;
+  const int nc = P.ncond, nin = P.nin;
+  const float *st = P.stats.data();
 
   N.loaded = false;
   for (int l = 0; l < 5; ++l) {
-    std::memcpy(N.host_w[l], &tw[l * wl], wl * sizeof(float));
-    std::memcpy(N.host_b[l], &tb[l * bl], bl * sizeof(float));
+    std::memset(N.host_w[l], 0, sizeof(N.host_w[l]));
+    std::memset(N.host_b[l], 0, sizeof(N.host_b[l]));
+    std::memcpy(N.host_w[l], P.w[l].data(), P.w[l].size() * sizeof(float));
+    std::memcpy(N.host_b[l], P.b[l].data(), P.b[l].size() * sizeof(float));
   }
   N.rm = rm;
   N.nin = nin;
-  std::memcpy(N.host_m, tm.data(), tm.size() * sizeof(float));
-  std::memcpy(N.host_g, tg.data(), tg.size() * sizeof(float));
+  std::memset(N.host_m, 0, sizeof(N.host_m));
+  std::memset(N.host_g, 0, sizeof(N.host_g));
+  if (rm) {
+    std::memcpy(N.host_m, P.m.data(), P.m.size() * sizeof(float));
+    std::memcpy(N.host_g, P.g.data(), P.g.size() * sizeof(float));
+  }
   NetStats ns;
   for (int k = 0; k < kCondRect; ++k) {
     ns.cond_mean[k] = k < nc ? st[k] : 0.0f;
