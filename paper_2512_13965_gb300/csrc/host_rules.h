@@ -1,13 +1,17 @@
 // Host-side rules of a transport solve that decide what the kernels are
-// given: each cell's network condition and routing, and the sizes a solve on
-// rectangular cells accepts. Plain C++ with no CUDA headers, so a host-only
-// unit test checks them against the oracle without a GPU.
+// given: each cell's network condition and routing, the sizes a solve on
+// rectangular cells accepts, and the bookkeeping of the serving engine's
+// device-memory pool. Plain C++ with no CUDA headers, so a host-only unit
+// test checks them (against the oracle where it has a counterpart) without a
+// GPU.
 #pragma once
 
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
+#include <iterator>
+#include <map>
 
 namespace gmc {
 
@@ -77,5 +81,50 @@ inline int rect_sizes_check(const float *sigma, size_t n, float dx, float dy, si
   }
   return 0;
 }
+
+// Free regions of the serving engine's device-memory pool: first fit by
+// offset (a request takes the lowest-addressed free region that holds its
+// footprint, from that region's start), and a released region merges with
+// free neighbours, so releasing everything leaves one region again.
+class FreeList {
+ public:
+  void reset(size_t bytes) {
+    free_.clear();
+    if (bytes) free_[0] = bytes;
+  }
+  bool alloc(size_t bytes, size_t *off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t noff = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[noff] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  // offset -> length of every free region, in address order
+  const std::map<size_t, size_t> &regions() const { return free_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+};
 
 }  // namespace gmc

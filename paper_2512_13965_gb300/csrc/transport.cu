@@ -931,47 +931,21 @@ class Pool {
   cudaError_t init(size_t bytes) {
     bytes_ = align256(bytes);
     cudaError_t e = cudaMalloc(&base_, bytes_);
-    if (e == cudaSuccess) free_[0] = bytes_;
+    if (e == cudaSuccess) list_.reset(bytes_);
     return e;
   }
   ~Pool() {
     if (base_) cudaFree(base_);
   }
   size_t capacity() const { return bytes_; }
-  bool alloc(size_t bytes, size_t *off) {
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= bytes) {
-        *off = it->first;
-        const size_t rest = it->second - bytes;
-        const size_t noff = it->first + bytes;
-        free_.erase(it);
-        if (rest) free_[noff] = rest;
-        return true;
-      }
-    }
-    return false;
-  }
-  void release(size_t off, size_t bytes) {
-    auto it = free_.emplace(off, bytes).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
+  bool alloc(size_t bytes, size_t *off) { return list_.alloc(bytes, off); }
+  void release(size_t off, size_t bytes) { list_.release(off, bytes); }
   char *base() const { return (char *)base_; }
 
  private:
   void *base_ = nullptr;
   size_t bytes_ = 0;
-  std::map<size_t, size_t> free_;
+  FreeList list_;
 };
 
 // The wave engine: every admitted request owns a slot, a pool region (grid,

@@ -1,7 +1,9 @@
 """The solve engine's host-side rules (csrc/host_rules.h), compiled into a
 host-only library with no GPU and checked against the oracle: each cell's
 scattering-equivalent condition and routing (the values stage 1 and stage 3
-of a GMC solve read), and the sizes a solve on rectangular cells accepts.
+of a GMC solve read), and the sizes a solve on rectangular cells accepts;
+and the serving pool's free list (admission by memory) against a model of
+the pool's bytes.
 """
 import ctypes
 import os
@@ -37,6 +39,22 @@ void hr_cell_condition(long n, const float *tau, const float *c, double t_lo, do
     walk[k] = r.walk;
   }
 }
+void *fl_new(size_t bytes) {
+  FreeList *f = new FreeList();
+  f->reset(bytes);
+  return f;
+}
+void fl_delete(void *h) { delete (FreeList *)h; }
+int fl_alloc(void *h, size_t bytes, size_t *off) { return ((FreeList *)h)->alloc(bytes, off); }
+void fl_release(void *h, size_t off, size_t bytes) { ((FreeList *)h)->release(off, bytes); }
+long fl_regions(void *h, size_t *offs, size_t *lens, long cap) {
+  long k = 0;
+  for (const auto &r : ((FreeList *)h)->regions()) {
+    if (k < cap) { offs[k] = r.first; lens[k] = r.second; }
+    ++k;
+  }
+  return k;
+}
 int hr_rect_sizes_check(const float *sigma, long n, float dx, float dy, long *bad) {
   size_t b = (size_t)-1;
   const int r = rect_sizes_check(sigma, (size_t)n, dx, dy, &b);
@@ -66,6 +84,12 @@ def lib(tmp_path_factory):
     L.hr_cell_condition.argtypes = [LG, P, P, D, D, D, D, D, P, P, P, P]
     L.hr_rect_sizes_check.argtypes = [P, LG, F, F, P]
     L.hr_rect_sizes_check.restype = ctypes.c_int
+    S = ctypes.c_size_t
+    L.fl_new.argtypes, L.fl_new.restype = [S], P
+    L.fl_delete.argtypes = [P]
+    L.fl_alloc.argtypes, L.fl_alloc.restype = [P, S, P], ctypes.c_int
+    L.fl_release.argtypes = [P, S, S]
+    L.fl_regions.argtypes, L.fl_regions.restype = [P, P, P, LG], LG
     return L
 
 
@@ -147,3 +171,69 @@ def test_rect_sizes_accepted_and_refused(lib):
     assert _rect(lib, [0.5, 0.0, 1.0], 1.0, 1.0) == (3, 1)
     assert _rect(lib, [0.5, 1.0, -2.0], 1.0, 1.0) == (3, 2)
     assert _rect(lib, [0.5, 1.0, float("nan")], 1.0, 1.0) == (3, 2)
+
+
+def _regions(lib, h):
+    offs, lens = np.zeros(4096, np.uintp), np.zeros(4096, np.uintp)
+    k = lib.fl_regions(h, offs.ctypes.data, lens.ctypes.data, 4096)
+    assert k <= 4096
+    return [(int(o), int(n)) for o, n in zip(offs[:k], lens[:k])]
+
+
+def _free_runs(used, cap):
+    # maximal free intervals of a byte map, in address order
+    runs, k = [], 0
+    while k < cap:
+        if used[k]:
+            k += 1
+            continue
+        j = k
+        while j < cap and not used[j]:
+            j += 1
+        runs.append((k, j - k))
+        k = j
+    return runs
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_pool_free_list_against_a_byte_map(lib, seed):
+    # random admissions and completions in units of 256 B (footprints are
+    # sums of 256-byte-aligned arrays): every grant is the lowest-addressed
+    # free run that holds it, no two grants overlap, a refusal means no run
+    # is large enough, the free list is exactly the maximal free runs after
+    # every step, and releasing everything leaves the whole pool free
+    cap = 2048  # in 256-byte units
+    g = np.random.default_rng(seed)
+    h = lib.fl_new(cap * 256)
+    try:
+        used = np.zeros(cap, bool)
+        live = []
+        refused = 0
+        for _ in range(2000):
+            if live and (g.random() < 0.45 or len(live) > 60):
+                off, n = live.pop(int(g.integers(len(live))))
+                lib.fl_release(h, off * 256, n * 256)
+                assert used[off:off + n].all()
+                used[off:off + n] = False
+            else:
+                n = int(min(cap, np.ceil(g.lognormal(3.0, 1.2))))
+                o = ctypes.c_size_t(0)
+                runs = _free_runs(used, cap)
+                fits = [r for r in runs if r[1] >= n]
+                if lib.fl_alloc(h, n * 256, ctypes.byref(o)):
+                    assert o.value % 256 == 0
+                    off = o.value // 256
+                    assert fits and off == fits[0][0], (off, fits[:2])
+                    assert not used[off:off + n].any() and off + n <= cap
+                    used[off:off + n] = True
+                    live.append((off, n))
+                else:
+                    assert not fits
+                    refused += 1
+            assert _regions(lib, h) == [(o * 256, n * 256) for o, n in _free_runs(used, cap)]
+        assert refused > 0 and len(live) > 10
+        for off, n in reversed(live):
+            lib.fl_release(h, off * 256, n * 256)
+        assert _regions(lib, h) == [(0, cap * 256)]
+    finally:
+        lib.fl_delete(h)
