@@ -10,29 +10,15 @@
 #include <cstring>
 
 #include "gmc_internal.cuh"
+#include "tc_pack.h"
 
 namespace gmc {
 namespace smp {
 
-// Weight chunk: all 256 output rows x 128 bytes of K (64 BF16 or 128 E4M3
-// inputs), K-major, 128-byte swizzle; 32 KB.
-constexpr uint32_t CHUNK = 256u * 128u;
-
-// packed global operand buffer (bytes): hidden-layer chunks, then the BF16
-// operands of layers 1 and 5
+// the packed weight buffer's layout (tc_pack.h)
+constexpr uint32_t CHUNK = pack::CHUNK;
 template <bool FP8>
-struct Packed {
-  static constexpr int NCH = 256 * (FP8 ? 1 : 2) / 128;  // chunks per hidden layer
-  static constexpr size_t OFF_HID = 0;                  // [layer 0..2][chunk] x CHUNK
-  static constexpr size_t OFF_B1 = 3 * (size_t)NCH * CHUNK;  // 256 rows x 32 B, 32-byte swizzle
-  static constexpr size_t OFF_B5 = OFF_B1 + 8192;       // 4 K-blocks x 16 rows x 128 B
-  // biases of layers 2-4 as one block per layer of 256 rows x 32 B (32-byte
-  // swizzle), K = 16 with the bias in columns 13 (BF16 value) and 14 (BF16
-  // remainder), the others zero: b/2 (BF16 variant) or b/s_c (FP8 variant,
-  // whose epilogue multiplies the accumulator by s_c/2)
-  static constexpr size_t OFF_BIAS = OFF_B5 + 8192;
-  static constexpr size_t BYTES = OFF_BIAS + 24576;
-};
+using Packed = pack::Packed<FP8>;
 
 struct Params {
   const unsigned char *packed;
