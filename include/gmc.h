@@ -637,8 +637,10 @@ gmc_status gmc_train_param_count_ctx(const gmc_ctx *ctx, int64_t *count);
  * restores one into the training state of gmc_train_begin, which must have
  * been called on the same dataset with the same batch and precision
  * (GMC_EINVAL otherwise; GMC_EFORMAT for a blob that is not a checkpoint,
- * or one of another network form: residual-modulated or not, square or
- * rectangular cells).
+ * one of another network form: residual-modulated or not, square or
+ * rectangular cells, or one whose statistics or hyperparameters are out of
+ * range: a non-finite statistic, a standard deviation <= 0, lr <= 0, a beta
+ * outside [0, 1), eps <= 0, a negative weight decay).
  * The checkpoint records the dataset's size and its standardization
  * statistics, which gmc_train_begin recomputes from the data: other data (a
  * different size, or statistics that differ in any bit) gives GMC_EINVAL.

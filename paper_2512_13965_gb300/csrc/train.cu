@@ -27,6 +27,7 @@
 #include <cstring>
 #include <vector>
 
+#include "ckpt.h"
 #include "decode.cuh"
 #include "gmc_internal.cuh"
 #include "philox.cuh"
@@ -999,26 +1000,7 @@ gmc_status gmc_train_params(gmc_ctx *ctx, float *out) {
   return GMC_OK;
 }
 
-// Training checkpoint: header, then the FP32 master weights, Adam's first
-// and second moments (P floats each). The batch of step k draws its rows from
-// Philox at (seed, k), so restoring these and the step count resumes the run
-// exactly where it stopped.
-// The dataset is identified by its size n and its FP64-accumulated
-// standardization statistics (stored as FP32), which gmc_train_begin
-// recomputes from the data: a checkpoint restores only into a training state
-// begun on data with the same n and bit-identical statistics.
-struct TrainCkpt {
-  char magic[4];
-  uint32_t version;
-  int64_t params, step, batch, n;
-  int32_t precision, arch;  // arch bit 0: residual-modulated; bit 1: rectangular cells
-  double lr, beta1, beta2, eps, weight_decay;
-  uint64_t seed;
-  float stats[20];          // TrainState::stats (2 n_cond + 8 used)
-};
-constexpr uint32_t kCkptVersion = 3;
-
-int32_t ckpt_arch(const TrainState &T) { return (T.rm ? 1 : 0) | (T.ncond != kCond ? 2 : 0); }
+int32_t ckpt_arch(const TrainState &T) { return ckpt_arch_bits(T.rm, T.ncond); }
 
 gmc_status gmc_train_state_size(const gmc_ctx *ctx, size_t *bytes) {
   if (!ctx || !bytes) return GMC_EINVAL;
@@ -1075,23 +1057,28 @@ gmc_status gmc_train_load_state(gmc_ctx *ctx, const void *blob, size_t nbytes) {
     return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: a checkpoint is %zu bytes", need);
   TrainCkpt h;
   std::memcpy(&h, blob, sizeof(h));
-  if (std::memcmp(h.magic, "GMCT", 4) != 0 || h.version != kCkptVersion || h.params != T->np ||
-      h.arch != ckpt_arch(*T))
-    return set_error(ctx, GMC_EFORMAT,
-                     "gmc_train_load_state: not a version-3 training checkpoint of this network");
-  const int nc = T->ncond;
-  for (int k = 0; k < 2 * nc + 8; ++k)
-    if (!std::isfinite(h.stats[k]) ||
-        (((k >= nc && k < 2 * nc) || k >= 2 * nc + 4) && !(h.stats[k] > 0.0f)))
+  static_assert(sizeof(T->stats) == sizeof(h.stats), "checkpoint statistics");
+  const CkptTarget tgt{T->np, T->cfg.batch, T->n, T->cfg.precision, ckpt_arch(*T), T->ncond, T->stats};
+  switch (ckpt_check(h, tgt)) {
+    case kCkptOk: break;
+    case kCkptNotThisNetwork:
+      return set_error(ctx, GMC_EFORMAT,
+                       "gmc_train_load_state: not a version-3 training checkpoint of this network");
+    case kCkptBadStats:
       return set_error(ctx, GMC_EFORMAT, "gmc_train_load_state: bad standardization statistics");
-  if (h.batch != T->cfg.batch || h.precision != T->cfg.precision || h.step < 0)
-    return set_error(ctx, GMC_EINVAL,
-                     "gmc_train_load_state: begin training with the checkpoint's batch and precision");
-  if (h.n != T->n || std::memcmp(h.stats, T->stats, sizeof(h.stats)) != 0)
-    return set_error(ctx, GMC_EINVAL,
-                     "gmc_train_load_state: the checkpoint was saved on other data (size %lld, "
-                     "or different statistics) than this training state's (size %lld)",
-                     (long long)h.n, (long long)T->n);
+    case kCkptBadHyper:
+      return set_error(ctx, GMC_EFORMAT,
+                       "gmc_train_load_state: bad hyperparameters (lr > 0, betas in [0, 1), "
+                       "eps > 0, weight decay >= 0, all finite)");
+    case kCkptOtherRun:
+      return set_error(ctx, GMC_EINVAL,
+                       "gmc_train_load_state: begin training with the checkpoint's batch and precision");
+    default:
+      return set_error(ctx, GMC_EINVAL,
+                       "gmc_train_load_state: the checkpoint was saved on other data (size %lld, "
+                       "or different statistics) than this training state's (size %lld)",
+                       (long long)h.n, (long long)T->n);
+  }
   const float *body = (const float *)((const unsigned char *)blob + sizeof(h));
   cudaSetDevice(ctx->device);
   cudaStream_t s = ctx->stream;
