@@ -721,6 +721,60 @@ def mlp_sampler_rect(net, steps, integrator, seed):
     return f
 
 
+def equivalent_condition_rect(tx, ty, c, tau_range=(0.1, 1000.0), c_range=(0.5, 0.999)):
+    """equivalent_condition for rectangular cells (optical sides tx, ty): the
+    implicit-capture walk in the rectangle depends on (c tx, c ty) only, so a
+    cell (tx', ty', c') with c' tx' = c tx and c' ty' = c ty has the same
+    exits and s = s' c' / c. Both sides must lie in [tau_lo, tau_hi] whatever
+    face the particle enters by, so c' is c moved into [c_lo, c_hi] and
+    [c max(tx, ty) / tau_hi, c min(tx, ty) / tau_lo]; cells inside the box
+    keep (tx, ty, c). Returns (tx', c', ok) with ty' = tx' ty / tx; where no
+    equivalent exists (that interval empty, or c = 0) ok is False and the
+    cell keeps (tx, c). With tx = ty this is equivalent_condition."""
+    tx, ty, c = (np.asarray(a, dtype=np.float64) for a in (tx, ty, c))
+    (t_lo, t_hi), (c_lo, c_hi) = tau_range, c_range
+    big, small = np.maximum(tx, ty), np.minimum(tx, ty)
+    lo = np.maximum(c_lo, c * big / t_hi)
+    hi = np.minimum(c_hi, c * small / t_lo)
+    ok = (c * small > 0.0) & (lo <= hi)
+    inside = ((tx >= t_lo) & (tx <= t_hi) & (ty >= t_lo) & (ty <= t_hi) & (c >= c_lo)
+              & (c <= c_hi))
+    ok = ok | inside
+    cp = np.where(inside, c, np.where(ok, np.clip(c, lo, np.maximum(lo, hi)), c))
+    txp = np.where(inside | ~ok, tx, np.clip(c * tx / np.where(ok, cp, 1.0), t_lo, t_hi))
+    return txp, cp, ok
+
+
+def equivalent_sampler_rect(sampler, fallback, tau_range=(0.1, 1000.0), c_range=(0.5, 0.999)):
+    """equivalent_sampler for rectangular cells: each particle sampled by
+    `sampler` at its cell's equivalent condition (equivalent_condition_rect,
+    in the canonical frame: the interval for c' is the same for either
+    orientation) with its track length scaled by c' / c; cells without an
+    equivalent go to `fallback` at their own condition."""
+    def f(xi, cos_c, sin_c, tx_c, ty_c, c, ids, events, rot=None):
+        xi, cos_c, sin_c, tx_c, ty_c, c = (np.asarray(a, dtype=np.float64)
+                                           for a in (xi, cos_c, sin_c, tx_c, ty_c, c))
+        ids = np.asarray(ids, dtype=np.uint64)
+        events = np.asarray(events, dtype=np.uint32)
+        txp, cp, ok = equivalent_condition_rect(tx_c, ty_c, c, tau_range, c_range)
+        typ = txp * (ty_c / tx_c)
+        n = xi.shape[0]
+        face = np.zeros(n, np.int64)
+        q, ux, uy, s = (np.zeros(n) for _ in range(4))
+        ev = np.zeros(n, np.uint32)
+        for sel, fn, a, b, cc in ((ok, sampler, txp, typ, cp), (~ok, fallback, tx_c, ty_c, c)):
+            k = np.nonzero(sel)[0]
+            if k.size == 0:
+                continue
+            r = None if rot is None else np.asarray(rot)[k]
+            fa, qa, uxa, uya, sa, eva = fn(xi[k], cos_c[k], sin_c[k], a[k], b[k], cc[k], ids[k],
+                                           events[k], rot=r)
+            face[k], q[k], ux[k], uy[k], ev[k] = fa, qa, uxa, uya, eva
+            s[k] = np.asarray(sa) * (cc[k] / c[k]) if fn is sampler else sa
+        return face, q, ux, uy, s, ev
+    return f
+
+
 def walk_sampler_rect(seed):
     """Stage 2 replaced by the implicit-capture walk in the canonical frame of
     a rectangular cell, as the training pairs take it (transmit_rect: entry

@@ -38,6 +38,27 @@ inline bool equivalent_condition(double tau, double c, double t_lo, double t_hi,
   return true;
 }
 
+// equivalent_condition for a rectangular cell with optical sides tx, ty: the
+// implicit-capture walk in the rectangle depends on (c tx, c ty) only, and
+// the network sees either side as the depth behind the entry face, so both
+// must lie in [t_lo, t_hi]: c' is c moved into [c_lo, c_hi] and
+// [c max(tx, ty) / t_hi, c min(tx, ty) / t_lo], tx' = c tx / c' (clamped into
+// the box against rounding), ty' = tx' ty / tx. Cells inside the box keep
+// (tx, c). Returns false where that interval is empty or c = 0. With
+// tx = ty this is equivalent_condition.
+inline bool equivalent_condition_rect(double tx, double ty, double c, double t_lo, double t_hi,
+                                      double c_lo, double c_hi, double *tx_n, double *c_n) {
+  *tx_n = tx;
+  *c_n = c;
+  if (tx >= t_lo && tx <= t_hi && ty >= t_lo && ty <= t_hi && c >= c_lo && c <= c_hi) return true;
+  const double big = std::max(tx, ty), small = std::min(tx, ty);
+  const double lo = std::max(c_lo, c * big / t_hi), hi = std::min(c_hi, c * small / t_lo);
+  if (!(c * small > 0.0) || !(lo <= hi)) return false;
+  *c_n = std::min(std::max(c, lo), std::max(lo, hi));
+  *tx_n = std::min(std::max(c * tx / *c_n, t_lo), t_hi);
+  return true;
+}
+
 // What stage 1 and stage 3 of a GMC solve read per cell: the network's
 // condition (ln tau', c'), the track-length factor c' / c, and whether the
 // random walk crosses the cell instead (no equivalent condition, or thinner
@@ -50,10 +71,14 @@ struct CellCondition {
   uint8_t walk;
 };
 
+// ty > 0: a rectangular cell of optical sides tau (along x) and ty, whose
+// condition holds ln tx' (the kernels add ln(ty / tau) for entries through
+// the bottom or top face); ty <= 0: a square cell of side tau.
 inline CellCondition cell_condition(double tau, double c, double t_lo, double t_hi, double c_lo,
-                                    double c_hi, double min_tau) {
+                                    double c_hi, double min_tau, double ty = 0.0) {
   double tn, cn;
-  const bool ok = equivalent_condition(tau, c, t_lo, t_hi, c_lo, c_hi, &tn, &cn);
+  const bool ok = ty > 0.0 ? equivalent_condition_rect(tau, ty, c, t_lo, t_hi, c_lo, c_hi, &tn, &cn)
+                           : equivalent_condition(tau, c, t_lo, t_hi, c_lo, c_hi, &tn, &cn);
   CellCondition r;
   r.ltau_n = (float)std::log(tn);
   r.c_n = (float)cn;

@@ -829,7 +829,8 @@ size_t request_footprint(int64_t ncell) {
 // instead of ny*nx volumetric strengths.
 gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const float *c,
                         const float *source, int64_t n_histories, int method, uint64_t seed,
-                        Request &R, bool wall = false, bool xy = false, bool rect = false) {
+                        Request &R, bool wall = false, bool xy = false, bool rect = false,
+                        double aspect = 1.0) {
   if (nx < 1 || ny < 1 || (int64_t)nx * ny > (1 << 26))
     return set_error(ctx, GMC_EINVAL, "solve: grid must be 1..2^26 cells");
   if (!tau || !c || !source) return set_error(ctx, GMC_EINVAL, "solve: null array");
@@ -868,8 +869,10 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
   R.s_scale.resize(ncell);
   R.walk.assign(ncell, 0);
   for (int64_t k = 0; k < ncell; ++k) {
-    const CellCondition cc = cell_condition((double)tau[k], (double)c[k], cf.net_tau_lo,
-                                            cf.net_tau_hi, cf.net_c_lo, cf.net_c_hi, cf.gmc_min_tau);
+    // rectangular cells: tau holds the optical width, the height is tau dy/dx
+    const CellCondition cc =
+        cell_condition((double)tau[k], (double)c[k], cf.net_tau_lo, cf.net_tau_hi, cf.net_c_lo,
+                       cf.net_c_hi, cf.gmc_min_tau, rect ? (double)tau[k] * aspect : 0.0);
     R.ltau_n[k] = cc.ltau_n;
     R.c_n[k] = cc.c_n;
     R.s_scale[k] = cc.s_scale;
@@ -1437,8 +1440,8 @@ gmc_status solve_one(gmc_ctx *ctx, int nx, int ny, const float *tau, const float
   if (!ctx) return GMC_EINVAL;
   if (!flux) return set_error(ctx, GMC_EINVAL, "transport_solve: null flux");
   Request R;
-  gmc_status st =
-      make_request(ctx, nx, ny, tau, c, source, n_histories, method, seed, R, wall, xy, rect);
+  gmc_status st = make_request(ctx, nx, ny, tau, c, source, n_histories, method, seed, R, wall, xy,
+                               rect, (double)dy / (double)dx);
   if (st != GMC_OK) return st;
   R.dx = dx;
   R.dy = dy;

@@ -75,6 +75,9 @@ def _sampler(spec, seed):
         return OT.mlp_sampler_rect(_net(spec[1]), spec[2], spec[3], seed)
     if kind == "walk_global_rect":
         return OT.walk_sampler_global_rect(seed)
+    if kind == "equivalent_rect":
+        return OT.equivalent_sampler_rect(OT.mlp_sampler_rect(_net(spec[1]), spec[2], spec[3], seed),
+                                          OT.walk_sampler_global_rect(seed), *spec[4])
     if kind == "mlp_xy":
         return OT.mlp_sampler_xy(_net(spec[1]), spec[2], spec[3], seed)
     if kind == "walk_global_xy":

@@ -27,6 +27,23 @@ void hr_equivalent(long n, const double *tau, const double *c, double t_lo, doub
   for (long k = 0; k < n; ++k)
     ok[k] = equivalent_condition(tau[k], c[k], t_lo, t_hi, c_lo, c_hi, &tau_n[k], &c_n[k]);
 }
+void hr_equivalent_rect(long n, const double *tx, const double *ty, const double *c, double t_lo,
+                        double t_hi, double c_lo, double c_hi, double *tx_n, double *c_n, int *ok) {
+  for (long k = 0; k < n; ++k)
+    ok[k] = equivalent_condition_rect(tx[k], ty[k], c[k], t_lo, t_hi, c_lo, c_hi, &tx_n[k], &c_n[k]);
+}
+void hr_cell_condition_rect(long n, const float *tau, const float *c, double aspect, double t_lo,
+                            double t_hi, double c_lo, double c_hi, float *ltau_n, float *c_n,
+                            float *s_scale, unsigned char *walk) {
+  for (long k = 0; k < n; ++k) {
+    const CellCondition r = cell_condition((double)tau[k], (double)c[k], t_lo, t_hi, c_lo, c_hi,
+                                           0.0, (double)tau[k] * aspect);
+    ltau_n[k] = r.ltau_n;
+    c_n[k] = r.c_n;
+    s_scale[k] = r.s_scale;
+    walk[k] = r.walk;
+  }
+}
 void hr_cell_condition(long n, const float *tau, const float *c, double t_lo, double t_hi,
                        double c_lo, double c_hi, double min_tau, float *ltau_n, float *c_n,
                        float *s_scale, unsigned char *walk) {
@@ -82,6 +99,8 @@ def lib(tmp_path_factory):
     P, D, F, LG = ctypes.c_void_p, ctypes.c_double, ctypes.c_float, ctypes.c_long
     L.hr_equivalent.argtypes = [LG, P, P, D, D, D, D, P, P, P]
     L.hr_cell_condition.argtypes = [LG, P, P, D, D, D, D, D, P, P, P, P]
+    L.hr_equivalent_rect.argtypes = [LG, P, P, P, D, D, D, D, P, P, P]
+    L.hr_cell_condition_rect.argtypes = [LG, P, P, D, D, D, D, D, P, P, P, P]
     L.hr_rect_sizes_check.argtypes = [P, LG, F, F, P]
     L.hr_rect_sizes_check.restype = ctypes.c_int
     S = ctypes.c_size_t
@@ -149,6 +168,40 @@ def test_cell_condition_is_what_the_kernels_read(lib, min_tau):
     np.testing.assert_array_equal(walk.astype(bool), expect_walk)
     if min_tau > 0.0:
         assert (walk.astype(bool) & ok).any()  # thin cells with an equivalent are walked too
+
+
+def test_rect_equivalent_condition_is_the_oracles(lib):
+    g = np.random.default_rng(6)
+    tau, c = _cells(20000, 7)
+    n = tau.size
+    ty = tau * np.exp(g.uniform(np.log(1 / 60), np.log(60), n))
+    ty[:500] = tau[:500]  # square cells among them
+    tn, cn, ok = np.zeros(n), np.zeros(n), np.zeros(n, np.int32)
+    lib.hr_equivalent_rect(n, tau.ctypes.data, ty.ctypes.data, c.ctypes.data, *BOX, tn.ctypes.data,
+                           cn.ctypes.data, ok.ctypes.data)
+    tp, cp, okp = OT.equivalent_condition_rect(tau, ty, c, BOX[:2], BOX[2:])
+    np.testing.assert_array_equal(ok.astype(bool), okp)
+    np.testing.assert_array_equal(tn, tp)
+    np.testing.assert_array_equal(cn, cp)
+    assert okp.sum() > 1000 and (~okp).sum() > 1000
+
+
+@pytest.mark.parametrize("aspect", [0.2, 1.0, 7.5])
+def test_rect_cell_condition_is_what_the_kernels_read(lib, aspect):
+    tau, c = _cells(20000, 9)
+    tau32, c32 = tau.astype(np.float32), c.astype(np.float32)
+    n = tau.size
+    lt, cn, ss = (np.zeros(n, np.float32) for _ in range(3))
+    walk = np.zeros(n, np.uint8)
+    lib.hr_cell_condition_rect(n, tau32.ctypes.data, c32.ctypes.data, aspect, *BOX, lt.ctypes.data,
+                               cn.ctypes.data, ss.ctypes.data, walk.ctypes.data)
+    t64, c64 = tau32.astype(np.float64), c32.astype(np.float64)
+    tp, cp, ok = OT.equivalent_condition_rect(t64, t64 * aspect, c64, BOX[:2], BOX[2:])
+    np.testing.assert_array_equal(lt, np.log(tp).astype(np.float32))
+    np.testing.assert_array_equal(cn, cp.astype(np.float32))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        np.testing.assert_array_equal(ss, np.where(ok, cp / c64, 1.0).astype(np.float32))
+    np.testing.assert_array_equal(walk.astype(bool), ~ok)
 
 
 def _rect(lib, sigma, dx, dy):

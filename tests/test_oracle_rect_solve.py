@@ -239,3 +239,77 @@ def test_wall_source_event_loop_matches_the_grid_walker():
     se = np.sqrt(A.var(0, ddof=1) / K + B.var(0, ddof=1) / K)
     z = np.abs(A.mean(0) - B.mean(0)) / se
     assert z.max() < 4.5, (z, A.mean(0), B.mean(0))
+
+
+BOX = ((0.1, 1000.0), (0.5, 0.999))
+
+
+def test_rect_equivalent_condition_reduces_to_the_square_map():
+    g = np.random.default_rng(4)
+    tau = np.exp(g.uniform(np.log(1e-3), np.log(1e5), 5000))
+    c = np.concatenate([g.uniform(0.0, 1.0, 4990), [0.0, 1.0, 0.5, 0.999, 0.2, 0.3, 0.05, 0.8,
+                                                    0.9, 0.6]])
+    a = OT.equivalent_condition_rect(tau, tau, c, *BOX)
+    b = OT.equivalent_condition(tau, c, *BOX)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_rect_equivalent_condition_keeps_both_scattering_thicknesses_in_the_box():
+    g = np.random.default_rng(5)
+    n = 20000
+    tx = np.exp(g.uniform(np.log(1e-3), np.log(1e5), n))
+    ty = tx * np.exp(g.uniform(np.log(1 / 50), np.log(50), n))
+    c = g.uniform(0.0, 1.0, n)
+    c[:200] = 0.0
+    c[200:400] = 1.0
+    (t_lo, t_hi), (c_lo, c_hi) = BOX
+    txp, cp, ok = OT.equivalent_condition_rect(tx, ty, c, *BOX)
+    typ = txp * ty / tx
+    inside = (tx >= t_lo) & (tx <= t_hi) & (ty >= t_lo) & (ty <= t_hi) & (c >= c_lo) & (c <= c_hi)
+    mapped = ok & ~inside
+    assert inside.sum() > 1000 and mapped.sum() > 1000 and (~ok).sum() > 1000
+    np.testing.assert_array_equal(txp[inside], tx[inside])
+    np.testing.assert_array_equal(cp[inside], c[inside])
+    # the walk's law is kept: c' tx' = c tx and c' ty' = c ty
+    np.testing.assert_allclose(cp[mapped] * txp[mapped], c[mapped] * tx[mapped], rtol=1e-14)
+    np.testing.assert_allclose(cp[mapped] * typ[mapped], c[mapped] * ty[mapped], rtol=1e-14)
+    # every side the network can see lies in the box (to rounding), c' too
+    for side in (txp[ok], typ[ok]):
+        assert np.all(side >= t_lo * (1 - 1e-12)) and np.all(side <= t_hi * (1 + 1e-12))
+    assert np.all((cp[ok] >= c_lo) & (cp[ok] <= c_hi))
+    assert not ok[c == 0.0].any()
+    # c' is c itself where c already fits the interval; where no equivalent
+    # exists, no c' on a fine grid of [c_lo, c_hi] puts both sides in the box
+    grid = np.linspace(c_lo, c_hi, 4001)
+    for k in np.nonzero(~ok)[0][:300]:
+        w = c[k] * np.array([tx[k], ty[k]])
+        fits = (w[None, :] / grid[:, None] >= t_lo) & (w[None, :] / grid[:, None] <= t_hi)
+        assert not fits.all(axis=1).any(), (tx[k], ty[k], c[k])
+    for k in np.nonzero(mapped)[0][:300]:
+        lo = max(c_lo, c[k] * max(tx[k], ty[k]) / t_hi)
+        hi = min(c_hi, c[k] * min(tx[k], ty[k]) / t_lo)
+        if lo <= c[k] <= hi:
+            assert cp[k] == c[k]
+
+
+def test_walk_solve_at_rect_equivalent_conditions_is_the_walk_solve():
+    # stage 2 as the canonical rectangle walk at each cell's equivalent
+    # condition (track lengths scaled by c'/c) equals the walk at the cell's
+    # own condition history by history; the grid has cells inside the box,
+    # cells mapped into it (a side below 0.1, pure scatterers, strong
+    # absorbers) and cells with no equivalent (c = 0.02)
+    sig = np.array([[0.5, 3.0, 40.0, 1.2], [8.0, 0.8, 2.0, 20.0], [1.5, 60.0, 0.6, 4.0]])
+    c = np.array([[0.9, 1.0, 0.05, 0.7], [0.02, 0.95, 1.0, 0.6], [0.5, 0.99, 0.3, 0.02]])
+    src = np.zeros((3, 4))
+    src[1, 1], src[0, 0], src[2, 2] = 1.0, 0.5, 0.5
+    dx, dy = 0.1, 1.6
+    txp, cp, ok = OT.equivalent_condition_rect(sig * dx, sig * dy, c, *BOX)
+    inside = (sig * dx >= 0.1) & (sig * dy <= 1000) & (c >= 0.5) & (c <= 0.999)
+    assert (ok & ~inside).sum() >= 4 and (~ok).sum() >= 2 and inside.sum() >= 1
+    w = OT.walk_sampler_rect(21)
+    a, sa = OT.solve_gmc_rect(sig, c, src, dx, dy, 1500, 21, w)
+    b, sb = OT.solve_gmc_rect(sig, c, src, dx, dy, 1500, 21,
+                              OT.equivalent_sampler_rect(w, w, *BOX))
+    np.testing.assert_allclose(b, a, rtol=1e-9, atol=1e-15)
+    assert sa["transmissions"] == sb["transmissions"]
