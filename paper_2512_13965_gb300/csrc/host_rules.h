@@ -87,6 +87,44 @@ inline CellCondition cell_condition(double tau, double c, double t_lo, double t_
   return r;
 }
 
+// Checks a solve's cells and source and accumulates the source CDF that
+// births search (FP64, in cell order): every cell needs tau > 0 (finite) and
+// c in [0, 1]; a volumetric source (wall false) has ncell strengths, a
+// surface source on the left boundary (wall true) ny, each finite and >= 0.
+// cdf[k] is the sum of the first k + 1 strengths (ncell entries, or ny), and
+// *total the sum of all. Returns 0, or for the first defect in cell order
+// (a cell's tau and c before its source strength) 1 (tau or c of cell
+// *bad), 2 (the volumetric strength of cell *bad) or 3 (the wall strength
+// of row *bad).
+inline int grid_source_check(int64_t ncell, int ny, const float *tau, const float *c,
+                             const float *source, bool wall, double *cdf, double *total,
+                             int64_t *bad) {
+  double acc = 0.0;
+  for (int64_t k = 0; k < ncell; ++k) {
+    if (!(tau[k] > 0.0f) || !std::isfinite(tau[k]) || !(c[k] >= 0.0f && c[k] <= 1.0f)) {
+      *bad = k;
+      return 1;
+    }
+    if (wall) continue;
+    if (!(source[k] >= 0.0f) || !std::isfinite(source[k])) {
+      *bad = k;
+      return 2;
+    }
+    acc += source[k] > 0.0f ? (double)source[k] : 0.0;
+    cdf[k] = acc;
+  }
+  for (int j = 0; wall && j < ny; ++j) {
+    if (!(source[j] >= 0.0f) || !std::isfinite(source[j])) {
+      *bad = j;
+      return 3;
+    }
+    acc += source[j] > 0.0f ? (double)source[j] : 0.0;
+    cdf[j] = acc;
+  }
+  *total = acc;
+  return 0;
+}
+
 // Sizes of a solve on rectangular cells dx x dy with cross sections sigma[n]:
 // the kernels form a cell's height as its optical width sigma dx times
 // dy / dx in FP32, so dx and dy must be finite and > 0, dy / dx within

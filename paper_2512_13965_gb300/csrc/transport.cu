@@ -845,20 +845,13 @@ gmc_status make_request(gmc_ctx *ctx, int nx, int ny, const float *tau, const fl
   R.c.assign(c, c + ncell);
   R.cdf.resize(ncell);
   double acc = 0.0;
-  for (int64_t k = 0; k < ncell; ++k) {
-    if (!(tau[k] > 0.0f) || !std::isfinite(tau[k]) || !(c[k] >= 0.0f && c[k] <= 1.0f))
-      return set_error(ctx, GMC_EINVAL, "solve: cell %lld needs tau > 0, c in [0,1]", (long long)k);
-    if (wall) continue;
-    if (!(source[k] >= 0.0f) || !std::isfinite(source[k]))
-      return set_error(ctx, GMC_EINVAL, "solve: source must be finite and >= 0");
-    acc += source[k] > 0.0f ? (double)source[k] : 0.0;
-    R.cdf[k] = acc;
-  }
-  for (int j = 0; wall && j < ny; ++j) {
-    if (!(source[j] >= 0.0f) || !std::isfinite(source[j]))
-      return set_error(ctx, GMC_EINVAL, "solve: wall source must be finite and >= 0");
-    acc += source[j] > 0.0f ? (double)source[j] : 0.0;
-    R.cdf[j] = acc;
+  int64_t bad = 0;
+  switch (grid_source_check(ncell, ny, tau, c, source, wall, R.cdf.data(), &acc, &bad)) {
+    case 0: break;
+    case 1:
+      return set_error(ctx, GMC_EINVAL, "solve: cell %lld needs tau > 0, c in [0,1]", (long long)bad);
+    case 2: return set_error(ctx, GMC_EINVAL, "solve: source must be finite and >= 0");
+    default: return set_error(ctx, GMC_EINVAL, "solve: wall source must be finite and >= 0");
   }
   // the networks' condition per cell (GMC): the scattering-equivalent one,
   // or the random walk where there is none or the cell is thinner than

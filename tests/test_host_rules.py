@@ -72,6 +72,13 @@ long fl_regions(void *h, size_t *offs, size_t *lens, long cap) {
   }
   return k;
 }
+int hr_grid(long ncell, int ny, const float *tau, const float *c, const float *src, int wall,
+            double *cdf, double *total, long *bad) {
+  int64_t b = -1;
+  const int r = grid_source_check(ncell, ny, tau, c, src, wall != 0, cdf, total, &b);
+  *bad = (long)b;
+  return r;
+}
 int hr_rect_sizes_check(const float *sigma, long n, float dx, float dy, long *bad) {
   size_t b = (size_t)-1;
   const int r = rect_sizes_check(sigma, (size_t)n, dx, dy, &b);
@@ -103,6 +110,8 @@ def lib(tmp_path_factory):
     L.hr_cell_condition_rect.argtypes = [LG, P, P, D, D, D, D, D, P, P, P, P]
     L.hr_rect_sizes_check.argtypes = [P, LG, F, F, P]
     L.hr_rect_sizes_check.restype = ctypes.c_int
+    L.hr_grid.argtypes = [LG, ctypes.c_int, P, P, P, ctypes.c_int, P, P, P]
+    L.hr_grid.restype = ctypes.c_int
     S = ctypes.c_size_t
     L.fl_new.argtypes, L.fl_new.restype = [S], P
     L.fl_delete.argtypes = [P]
@@ -290,3 +299,53 @@ def test_pool_free_list_against_a_byte_map(lib, seed):
         assert _regions(lib, h) == [(0, cap * 256)]
     finally:
         lib.fl_delete(h)
+
+
+def _grid(lib, tau, c, src, wall, ny):
+    tau, c, src = (np.ascontiguousarray(a, np.float32) for a in (tau, c, src))
+    n = tau.size
+    cdf = np.full(n, -1.0)
+    tot, bad = ctypes.c_double(-1.0), ctypes.c_long(-2)
+    r = lib.hr_grid(n, ny, tau.ctypes.data, c.ctypes.data, src.ctypes.data, int(wall),
+                    cdf.ctypes.data, ctypes.byref(tot), ctypes.byref(bad))
+    return r, bad.value, cdf, tot.value
+
+
+def test_grid_checks_and_source_cdf(lib):
+    g = np.random.default_rng(8)
+    ny, nx = 24, 40
+    tau = np.exp(g.uniform(np.log(0.01), np.log(1e4), ny * nx)).astype(np.float32)
+    c = g.uniform(0.0, 1.0, ny * nx).astype(np.float32)
+    c[:5] = [0.0, 1.0, 0.5, 0.0, 1.0]
+    src = np.where(g.random(ny * nx) < 0.3, g.exponential(1.0, ny * nx), 0.0).astype(np.float32)
+    # volumetric: the CDF the births search is the running FP64 sum
+    r, _, cdf, tot = _grid(lib, tau, c, src, False, ny)
+    assert r == 0
+    np.testing.assert_array_equal(cdf, np.cumsum(src.astype(np.float64)))
+    assert tot == cdf[-1]
+    # wall: ny strengths (the rest of the array is not read)
+    wall = np.concatenate([g.exponential(1.0, ny), np.full(ny * nx - ny, np.nan)]).astype(np.float32)
+    r, _, cdfw, totw = _grid(lib, tau, c, wall, True, ny)
+    assert r == 0
+    np.testing.assert_array_equal(cdfw[:ny], np.cumsum(wall[:ny].astype(np.float64)))
+    assert totw == cdfw[ny - 1] and np.all(cdfw[ny:] == -1.0)
+    # refusals, each with the first defect in cell order
+    for k, field, v, code in ((17, "tau", 0.0, 1), (3, "tau", -1.0, 1), (90, "tau", np.inf, 1),
+                              (5, "tau", np.nan, 1), (60, "c", -1e-7, 1), (61, "c", 1.0001, 1),
+                              (62, "c", np.nan, 1), (33, "src", -1.0, 2), (34, "src", np.inf, 2),
+                              (35, "src", np.nan, 2)):
+        a = {"tau": tau.copy(), "c": c.copy(), "src": src.copy()}
+        a[field][k] = v
+        assert _grid(lib, a["tau"], a["c"], a["src"], False, ny)[:2] == (code, k), (field, k)
+    # a cell's tau before its own source, an earlier source before a later tau
+    t2, s2 = tau.copy(), src.copy()
+    t2[40], s2[40] = 0.0, -1.0
+    assert _grid(lib, t2, c, s2, False, ny)[:2] == (1, 40)
+    t2[40], s2[20] = tau[40], -1.0
+    assert _grid(lib, t2, c, s2, False, ny)[:2] == (2, 20)
+    w2 = wall.copy()
+    w2[7] = -2.0
+    assert _grid(lib, tau, c, w2, True, ny)[:2] == (3, 7)
+    t3 = tau.copy()
+    t3[ny * nx - 1] = np.nan  # every cell is checked before the wall strengths
+    assert _grid(lib, t3, c, w2, True, ny)[:2] == (1, ny * nx - 1)
