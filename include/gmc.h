@@ -82,7 +82,7 @@ typedef struct gmc_ctx gmc_ctx;
 
 /* Options of the GMC sampler and of transport solves (gmc_set_config). */
 typedef struct gmc_config {
-    int steps;             /* ODE steps K (Eq. 8), >= 1; default 16 */
+    int steps;             /* ODE steps K (Eq. 8), 1..256; default 16 */
     int integrator;        /* gmc_integrator; default GMC_EULER */
     int precision;         /* gmc_precision of the velocity network; default GMC_BF16 */
     double w_cut;          /* roulette threshold on the particle weight; default 1e-4 */
@@ -445,8 +445,12 @@ gmc_status transport_solve_wall_xy(gmc_ctx *ctx, int nx, int ny, const float *ta
  * otherwise): in the canonical frame of the entry face the condition's
  * width is the depth behind it and the aspect the face's length over it (a
  * quarter turn exchanges the two sides). flux: per source particle per unit
- * area, Delta w / (sigma_a dx dy) (Eq. 7). The box of scattering-equivalent
- * conditions (gmc_config.net_*) applies to sigma dx. Volumetric sources only.
+ * area, Delta w / (sigma_a dx dy) (Eq. 7). A cell outside the networks' box
+ * (gmc_config.net_*) is sampled at the equivalent condition that keeps both
+ * optical sides in it: c' in [net_c_lo, net_c_hi] and in
+ * [c max(tx, ty) / net_tau_hi, c min(tx, ty) / net_tau_lo] (nearest c),
+ * tx' = c tx / c', ty' = c ty / c', track lengths times c'/c; a cell where
+ * no such c' exists is crossed by the random walk. Volumetric sources only.
  * GMC_EINVAL as well for dx or dy not finite and > 0, dy / dx outside
  * [1e-37, 1e37], or a cell with sigma dy outside (0, 1e38] (the walk forms
  * the height in FP32). Other arguments, the result and blocking as for

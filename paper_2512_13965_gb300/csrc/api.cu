@@ -11,6 +11,7 @@
 
 #include "gmc_internal.cuh"
 #include "gmcw.h"
+#include "host_rules.h"
 
 namespace gmc {
 
@@ -282,25 +283,20 @@ gmc_status gmc_get_config(const gmc_ctx *ctx, gmc_config *out) {
 gmc_status gmc_set_config(gmc_ctx *ctx, const gmc_config *cfg) {
   if (!ctx || !cfg) return GMC_EINVAL;
   if (ctx->server) return set_error(ctx, GMC_EBUSY, "gmc_set_config: the server is running");
-  if (cfg->steps < 1 || cfg->steps > 256)
-    return set_error(ctx, GMC_EINVAL, "steps must be in [1, 256], got %d", cfg->steps);
-  if (cfg->integrator != GMC_EULER && cfg->integrator != GMC_MIDPOINT && cfg->integrator != GMC_RK4)
-    return set_error(ctx, GMC_EINVAL, "unknown integrator %d", cfg->integrator);
-  if (cfg->precision < GMC_FP32 || cfg->precision > GMC_FP8)
-    return set_error(ctx, GMC_EINVAL, "unknown precision %d", cfg->precision);
-  if (!(cfg->w_cut >= 0.0) || !(cfg->p_survive > 0.0 && cfg->p_survive <= 1.0))
-    return set_error(ctx, GMC_EINVAL, "need w_cut >= 0 and p_survive in (0, 1]");
-  if (cfg->bank_capacity < 1024 || cfg->bank_capacity > ((int64_t)1 << 28))
-    return set_error(ctx, GMC_EINVAL, "bank_capacity must be in [1024, 2^28]");
-  if (cfg->flights_per_wave < 1)
-    return set_error(ctx, GMC_EINVAL, "flights_per_wave must be >= 1");
-  if (!(cfg->gmc_min_tau >= 0.0)) return set_error(ctx, GMC_EINVAL, "gmc_min_tau must be >= 0");
-  if (!(cfg->net_tau_lo > 0.0 && cfg->net_tau_hi >= cfg->net_tau_lo && std::isfinite(cfg->net_tau_hi)) ||
-      !(cfg->net_c_lo > 0.0 && cfg->net_c_hi >= cfg->net_c_lo && cfg->net_c_hi <= 1.0))
-    return set_error(ctx, GMC_EINVAL,
-                     "need 0 < net_tau_lo <= net_tau_hi (finite), 0 < net_c_lo <= net_c_hi <= 1");
-  if (cfg->sampler_kernel != GMC_KERNEL_TILE && cfg->sampler_kernel != GMC_KERNEL_PAIR)
-    return set_error(ctx, GMC_EINVAL, "unknown sampler_kernel %d", cfg->sampler_kernel);
+  switch (config_check(*cfg)) {
+    case 0: break;
+    case 1: return set_error(ctx, GMC_EINVAL, "steps must be in [1, 256], got %d", cfg->steps);
+    case 2: return set_error(ctx, GMC_EINVAL, "unknown integrator %d", cfg->integrator);
+    case 3: return set_error(ctx, GMC_EINVAL, "unknown precision %d", cfg->precision);
+    case 4: return set_error(ctx, GMC_EINVAL, "need w_cut >= 0 and p_survive in (0, 1]");
+    case 5: return set_error(ctx, GMC_EINVAL, "bank_capacity must be in [1024, 2^28]");
+    case 6: return set_error(ctx, GMC_EINVAL, "flights_per_wave must be >= 1");
+    case 7: return set_error(ctx, GMC_EINVAL, "gmc_min_tau must be >= 0");
+    case 8:
+      return set_error(ctx, GMC_EINVAL,
+                       "need 0 < net_tau_lo <= net_tau_hi (finite), 0 < net_c_lo <= net_c_hi <= 1");
+    default: return set_error(ctx, GMC_EINVAL, "unknown sampler_kernel %d", cfg->sampler_kernel);
+  }
   ctx->cfg = *cfg;
   return GMC_OK;
 }

@@ -13,6 +13,8 @@
 #include <iterator>
 #include <map>
 
+#include "gmc.h"
+
 namespace gmc {
 
 // The scattering-equivalent condition of a cell (tau, c) in the training box
@@ -142,6 +144,26 @@ inline int rect_sizes_check(const float *sigma, size_t n, float dx, float dy, si
       return 3;
     }
   }
+  return 0;
+}
+
+// The ranges gmc_set_config accepts. Returns 0, or the first field out of
+// range: 1 steps (1..256), 2 integrator, 3 precision, 4 w_cut (>= 0) or
+// p_survive ((0, 1]), 5 bank_capacity (1024..2^28), 6 flights_per_wave
+// (>= 1), 7 gmc_min_tau (>= 0), 8 the networks' box (0 < tau_lo <= tau_hi
+// finite, 0 < c_lo <= c_hi <= 1), 9 sampler_kernel.
+inline int config_check(const gmc_config &c) {
+  if (c.steps < 1 || c.steps > 256) return 1;
+  if (c.integrator != GMC_EULER && c.integrator != GMC_MIDPOINT && c.integrator != GMC_RK4) return 2;
+  if (c.precision < GMC_FP32 || c.precision > GMC_FP8) return 3;
+  if (!(c.w_cut >= 0.0) || !(c.p_survive > 0.0 && c.p_survive <= 1.0)) return 4;
+  if (c.bank_capacity < 1024 || c.bank_capacity > ((int64_t)1 << 28)) return 5;
+  if (c.flights_per_wave < 1) return 6;
+  if (!(c.gmc_min_tau >= 0.0)) return 7;
+  if (!(c.net_tau_lo > 0.0 && c.net_tau_hi >= c.net_tau_lo && std::isfinite(c.net_tau_hi)) ||
+      !(c.net_c_lo > 0.0 && c.net_c_hi >= c.net_c_lo && c.net_c_hi <= 1.0))
+    return 8;
+  if (c.sampler_kernel != GMC_KERNEL_TILE && c.sampler_kernel != GMC_KERNEL_PAIR) return 9;
   return 0;
 }
 

@@ -17,6 +17,7 @@ from oracle import transport as OT
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2512_13965_gb300", "csrc")
+INCLUDE = os.path.join(ROOT, "include")
 
 WRAPPER = r'''
 #include "host_rules.h"
@@ -72,6 +73,25 @@ long fl_regions(void *h, size_t *offs, size_t *lens, long cap) {
   }
   return k;
 }
+int hr_config(int steps, int integ, int prec, double w_cut, double p_survive, long long cap,
+              int fpw, double min_tau, double t_lo, double t_hi, double c_lo, double c_hi,
+              int kernel) {
+  gmc_config c;
+  c.steps = steps;
+  c.integrator = integ;
+  c.precision = prec;
+  c.w_cut = w_cut;
+  c.p_survive = p_survive;
+  c.bank_capacity = cap;
+  c.flights_per_wave = fpw;
+  c.gmc_min_tau = min_tau;
+  c.net_tau_lo = t_lo;
+  c.net_tau_hi = t_hi;
+  c.net_c_lo = c_lo;
+  c.net_c_hi = c_hi;
+  c.sampler_kernel = kernel;
+  return config_check(c);
+}
 int hr_grid(long ncell, int ny, const float *tau, const float *c, const float *src, int wall,
             double *cdf, double *total, long *bad) {
   int64_t b = -1;
@@ -99,8 +119,8 @@ def lib(tmp_path_factory):
     d = tmp_path_factory.mktemp("host_rules")
     src, so = d / "w.cpp", d / "libhr.so"
     src.write_text(WRAPPER)
-    r = subprocess.run([gxx, "-std=c++17", "-O2", "-shared", "-fPIC", "-I", CSRC, str(src), "-o",
-                        str(so)], capture_output=True, text=True)
+    r = subprocess.run([gxx, "-std=c++17", "-O2", "-shared", "-fPIC", "-I", CSRC, "-I", INCLUDE,
+                        str(src), "-o", str(so)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     L = ctypes.CDLL(str(so))
     P, D, F, LG = ctypes.c_void_p, ctypes.c_double, ctypes.c_float, ctypes.c_long
@@ -110,6 +130,9 @@ def lib(tmp_path_factory):
     L.hr_cell_condition_rect.argtypes = [LG, P, P, D, D, D, D, D, P, P, P, P]
     L.hr_rect_sizes_check.argtypes = [P, LG, F, F, P]
     L.hr_rect_sizes_check.restype = ctypes.c_int
+    I = ctypes.c_int
+    L.hr_config.argtypes = [I, I, I, D, D, ctypes.c_longlong, I, D, D, D, D, D, I]
+    L.hr_config.restype = I
     L.hr_grid.argtypes = [LG, ctypes.c_int, P, P, P, ctypes.c_int, P, P, P]
     L.hr_grid.restype = ctypes.c_int
     S = ctypes.c_size_t
@@ -349,3 +372,36 @@ def test_grid_checks_and_source_cdf(lib):
     t3 = tau.copy()
     t3[ny * nx - 1] = np.nan  # every cell is checked before the wall strengths
     assert _grid(lib, t3, c, w2, True, ny)[:2] == (1, ny * nx - 1)
+
+
+CONFIG = dict(steps=16, integ=0, prec=1, w_cut=1e-4, p_survive=0.1, cap=1 << 21, fpw=512,
+              min_tau=0.0, t_lo=0.1, t_hi=1000.0, c_lo=0.5, c_hi=0.999, kernel=0)
+
+
+def _config(lib, **kw):
+    c = dict(CONFIG)
+    c.update(kw)
+    return lib.hr_config(*c.values())
+
+
+def test_config_ranges(lib):
+    inf, nan = float("inf"), float("nan")
+    assert _config(lib) == 0
+    # the edges of every range are accepted
+    for kw in (dict(steps=1), dict(steps=256), dict(integ=2), dict(prec=0), dict(prec=2),
+               dict(w_cut=0.0), dict(p_survive=1.0), dict(cap=1024), dict(cap=1 << 28),
+               dict(fpw=1), dict(min_tau=inf), dict(t_lo=5.0, t_hi=5.0), dict(c_lo=1.0, c_hi=1.0),
+               dict(kernel=1)):
+        assert _config(lib, **kw) == 0, kw
+    for kw, code in ((dict(steps=0), 1), (dict(steps=257), 1), (dict(integ=3), 2),
+                     (dict(integ=-1), 2), (dict(prec=3), 3), (dict(prec=-1), 3),
+                     (dict(w_cut=-1e-9), 4), (dict(w_cut=nan), 4), (dict(p_survive=0.0), 4),
+                     (dict(p_survive=1.5), 4), (dict(p_survive=nan), 4), (dict(cap=1023), 5),
+                     (dict(cap=(1 << 28) + 1), 5), (dict(fpw=0), 6), (dict(min_tau=-1.0), 7),
+                     (dict(min_tau=nan), 7), (dict(t_lo=0.0), 8), (dict(t_hi=0.05), 8),
+                     (dict(t_hi=inf), 8), (dict(t_lo=nan), 8), (dict(c_lo=0.0), 8),
+                     (dict(c_hi=1.01), 8), (dict(c_lo=0.9, c_hi=0.8), 8), (dict(kernel=2), 9)):
+        assert _config(lib, **kw) == code, (kw, code)
+    # the first field out of range is the one reported
+    assert _config(lib, steps=0, kernel=7, cap=1) == 1
+    assert _config(lib, fpw=0, kernel=7) == 6
