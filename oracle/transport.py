@@ -17,6 +17,12 @@
   Births in a source cell are walked to their first face crossing with the
   random walk, or, given an internal sampler (the paper's internal model for
   volumetric sources), their exit from the birth cell is sampled by it.
+  Variants: a surface source on the left boundary (`wall=`), x-y geometry
+  with 3-D directions carried as their projection on the plane
+  (`geometry="xy"`), and cells cut into rectangles dx x dy (`solve_gmc_rect`);
+  cells outside a network's training box are sampled at their
+  scattering-equivalent condition (`equivalent_condition`,
+  `equivalent_condition_rect`) or walked.
 
 Global faces use the same counter-clockwise numbering as a cell in its own
 frame: 0 = south (y-), 1 = east (x+), 2 = north (y+), 3 = west (x-). A
