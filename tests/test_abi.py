@@ -79,6 +79,19 @@ def test_binding_checks_buffer_sizes_and_types(libgmc):
         _abi.analog_transmit(ctx, n, *[np.zeros(n, np.float32)] * 5, 0, 0, 0, 0,
                              np.zeros(n, np.int32), np.zeros((4, n - 1), np.float32))
     assert "exit" in str(e.value)
+    # the geometry variants' solves: a short flux or wall array is refused
+    g16 = [np.ones(16, np.float32)] * 3
+    with pytest.raises(_abi.GMCError) as e:
+        _abi.transport_solve_rect(ctx, 4, 4, *g16, 0.5, 1.5, 10, 0, 1, np.zeros(15))
+    assert "flux" in str(e.value)
+    with pytest.raises(_abi.GMCError) as e:
+        _abi.transport_solve_xy(ctx, 4, 4, np.ones(16, np.float32), np.ones(16, np.float32),
+                                np.ones(16), 10, 0, 1, np.zeros(16))
+    assert "source" in str(e.value)
+    with pytest.raises(_abi.GMCError) as e:
+        _abi.transport_solve_wall_xy(ctx, 4, 4, np.ones(16, np.float32), np.ones(16, np.float32),
+                                     np.ones(3, np.float32), 10, 0, 1, np.zeros(16))
+    assert "wall" in str(e.value)
     ctx.handle = None
 
 
