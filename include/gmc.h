@@ -510,10 +510,10 @@ gmc_status gmc_serve_stop(gmc_ctx *ctx);
 /* AdamW and batch options of gmc_train_begin. */
 typedef struct gmc_train_config {
     int64_t batch;       /* rows per step, in [1, 2^20]; e.g. 8192 */
-    double lr;           /* learning rate, e.g. 1e-3 */
-    double beta1, beta2; /* e.g. 0.9, 0.999 */
-    double eps;          /* e.g. 1e-8 */
-    double weight_decay; /* decoupled weight decay, e.g. 0.01 */
+    double lr;           /* learning rate, > 0 and finite, e.g. 1e-3 */
+    double beta1, beta2; /* each in [0, 1), e.g. 0.9, 0.999 */
+    double eps;          /* > 0 and finite, e.g. 1e-8 */
+    double weight_decay; /* decoupled weight decay, >= 0 and finite, e.g. 0.01 */
     uint64_t seed;       /* Philox key of the batch draws (tag 6) */
     int precision;       /* GMC_FP32: SIMT FP32 GEMMs, FP32 activations (the only
                             choice for the residual-modulated network and for a
@@ -532,6 +532,9 @@ typedef struct gmc_train_config {
  * walk (analog_transmit mode GMC_ABSORB_IMPLICIT, flights from event 1) runs
  * from the left face. cond [5][n] = (xi, cos, sin, ln tau, c) and
  * y [4][n] = (p, cos theta_out, sin theta_out, ln s): device memory.
+ * GMC_EINVAL unless 0 < tau_lo <= tau_hi (finite) and 0 <= c_lo <= c_hi <= 1
+ * (the same ranges for every training-data generator below; for
+ * gmc_train_data_rect also 0 < aspect_lo <= aspect_hi, finite).
  */
 gmc_status gmc_train_data(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, float tau_hi,
                           float c_lo, float c_hi, float *cond, float *y);
@@ -594,6 +597,7 @@ gmc_status gmc_train_data_rect(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau
  * (mean and standard deviation of the 5 condition and 4 target components)
  * are computed from the data; the FP32 master weights start from the loaded
  * network (gmc_load_weights must have been called); AdamW moments start at 0.
+ * GMC_EINVAL for a configuration outside the ranges of gmc_train_config.
  */
 gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const float *y,
                            const gmc_train_config *cfg);

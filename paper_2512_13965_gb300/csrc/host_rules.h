@@ -167,6 +167,33 @@ inline int config_check(const gmc_config &c) {
   return 0;
 }
 
+// The ranges a training-data generator draws from: tau log-uniform in
+// [tau_lo, tau_hi] with 0 < tau_lo <= tau_hi finite, c uniform in
+// [c_lo, c_hi] within [0, 1], and for rectangular cells the aspect
+// tau_y / tau_x log-uniform in [aspect_lo, aspect_hi] with
+// 0 < aspect_lo <= aspect_hi finite (1, 1 for square cells).
+inline bool data_ranges_ok(float tau_lo, float tau_hi, float c_lo, float c_hi,
+                           float aspect_lo = 1.0f, float aspect_hi = 1.0f) {
+  return tau_lo > 0.0f && tau_hi >= tau_lo && std::isfinite(tau_hi) && c_lo >= 0.0f &&
+         c_hi >= c_lo && c_hi <= 1.0f && aspect_lo > 0.0f && aspect_hi >= aspect_lo &&
+         std::isfinite(aspect_hi);
+}
+
+// The training configuration gmc_train_begin accepts. Returns 0, or 1 batch
+// (1..2^20), 2 lr (> 0, finite), 3 precision (GMC_FP32 or GMC_BF16), 4 the
+// optimizer's constants (betas in [0, 1), eps > 0, weight decay >= 0, all
+// finite): the ranges a checkpoint's hyperparameters are held to as well.
+inline int train_config_check(const gmc_train_config &c) {
+  if (c.batch < 1 || c.batch > (1 << 20)) return 1;
+  if (!(c.lr > 0.0) || !std::isfinite(c.lr)) return 2;
+  if (c.precision != GMC_FP32 && c.precision != GMC_BF16) return 3;
+  if (!(c.beta1 >= 0.0 && c.beta1 < 1.0) || !(c.beta2 >= 0.0 && c.beta2 < 1.0) ||
+      !(c.eps > 0.0) || !std::isfinite(c.eps) || !(c.weight_decay >= 0.0) ||
+      !std::isfinite(c.weight_decay))
+    return 4;
+  return 0;
+}
+
 // Free regions of the serving engine's device-memory pool: first fit by
 // offset (a request takes the lowest-addressed free region that holds its
 // footprint, from that region's start), and a released region merges with

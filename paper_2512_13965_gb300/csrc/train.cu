@@ -30,6 +30,7 @@
 #include "ckpt.h"
 #include "decode.cuh"
 #include "gmc_internal.cuh"
+#include "host_rules.h"
 #include "philox.cuh"
 #include "train_fused.h"
 #include "walk.cuh"
@@ -713,8 +714,9 @@ gmc_status gmc_train_data(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_lo, 
                           float c_lo, float c_hi, float *cond, float *y) {
   if (!ctx) return GMC_EINVAL;
   if (n < 0 || (n > 0 && (!cond || !y))) return set_error(ctx, GMC_EINVAL, "gmc_train_data: bad arguments");
-  if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
-    return set_error(ctx, GMC_EINVAL, "gmc_train_data: need 0 < tau_lo <= tau_hi, 0 <= c_lo <= c_hi <= 1");
+  if (!data_ranges_ok(tau_lo, tau_hi, c_lo, c_hi))
+    return set_error(ctx, GMC_EINVAL,
+                     "gmc_train_data: need 0 < tau_lo <= tau_hi (finite), 0 <= c_lo <= c_hi <= 1");
   if (n == 0) return GMC_OK;
   if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data: cond and y must be device memory");
@@ -730,9 +732,9 @@ gmc_status gmc_train_data_internal(gmc_ctx *ctx, int64_t n, uint64_t seed, float
   if (!ctx) return GMC_EINVAL;
   if (n < 0 || (n > 0 && (!cond || !y)))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data_internal: bad arguments");
-  if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
+  if (!data_ranges_ok(tau_lo, tau_hi, c_lo, c_hi))
     return set_error(ctx, GMC_EINVAL,
-                     "gmc_train_data_internal: need 0 < tau_lo <= tau_hi, 0 <= c_lo <= c_hi <= 1");
+                     "gmc_train_data_internal: need 0 < tau_lo <= tau_hi (finite), 0 <= c_lo <= c_hi <= 1");
   if (n == 0) return GMC_OK;
   if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data_internal: cond and y must be device memory");
@@ -748,9 +750,9 @@ gmc_status gmc_train_data_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau_l
   if (!ctx) return GMC_EINVAL;
   if (n < 0 || (n > 0 && (!cond || !y)))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data_xy: bad arguments");
-  if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
+  if (!data_ranges_ok(tau_lo, tau_hi, c_lo, c_hi))
     return set_error(ctx, GMC_EINVAL,
-                     "gmc_train_data_xy: need 0 < tau_lo <= tau_hi, 0 <= c_lo <= c_hi <= 1");
+                     "gmc_train_data_xy: need 0 < tau_lo <= tau_hi (finite), 0 <= c_lo <= c_hi <= 1");
   if (n == 0) return GMC_OK;
   if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data_xy: cond and y must be device memory");
@@ -767,11 +769,10 @@ gmc_status gmc_train_data_rect(gmc_ctx *ctx, int64_t n, uint64_t seed, float tau
   if (!ctx) return GMC_EINVAL;
   if (n < 0 || (n > 0 && (!cond || !y)))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data_rect: bad arguments");
-  if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(aspect_lo > 0.0f) || !(aspect_hi >= aspect_lo) ||
-      !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
+  if (!data_ranges_ok(tau_lo, tau_hi, c_lo, c_hi, aspect_lo, aspect_hi))
     return set_error(ctx, GMC_EINVAL,
-                     "gmc_train_data_rect: need 0 < tau_lo <= tau_hi, 0 < aspect_lo <= aspect_hi, "
-                     "0 <= c_lo <= c_hi <= 1");
+                     "gmc_train_data_rect: need 0 < tau_lo <= tau_hi, 0 < aspect_lo <= aspect_hi "
+                     "(finite), 0 <= c_lo <= c_hi <= 1");
   if (n == 0) return GMC_OK;
   if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data_rect: cond and y must be device memory");
@@ -788,9 +789,9 @@ gmc_status gmc_train_data_internal_xy(gmc_ctx *ctx, int64_t n, uint64_t seed, fl
   if (!ctx) return GMC_EINVAL;
   if (n < 0 || (n > 0 && (!cond || !y)))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data_internal_xy: bad arguments");
-  if (!(tau_lo > 0.0f) || !(tau_hi >= tau_lo) || !(c_lo >= 0.0f) || !(c_hi <= 1.0f) || !(c_hi >= c_lo))
+  if (!data_ranges_ok(tau_lo, tau_hi, c_lo, c_hi))
     return set_error(ctx, GMC_EINVAL,
-                     "gmc_train_data_internal_xy: need 0 < tau_lo <= tau_hi, 0 <= c_lo <= c_hi <= 1");
+                     "gmc_train_data_internal_xy: need 0 < tau_lo <= tau_hi (finite), 0 <= c_lo <= c_hi <= 1");
   if (n == 0) return GMC_OK;
   if (!is_device_pointer(cond, ctx->device) || !is_device_pointer(y, ctx->device))
     return set_error(ctx, GMC_EINVAL, "gmc_train_data_internal_xy: cond and y must be device memory");
@@ -805,10 +806,16 @@ gmc_status gmc_train_begin(gmc_ctx *ctx, int64_t n, const float *cond, const flo
                            const gmc_train_config *cfg) {
   if (!ctx || !cfg) return GMC_EINVAL;
   if (n < 2 || !cond || !y) return set_error(ctx, GMC_EINVAL, "gmc_train_begin: need n >= 2 samples");
-  if (cfg->batch < 1 || cfg->batch > (1 << 20) || !(cfg->lr > 0.0))
-    return set_error(ctx, GMC_EINVAL, "gmc_train_begin: batch in [1, 2^20], lr > 0");
-  if (cfg->precision != GMC_FP32 && cfg->precision != GMC_BF16)
-    return set_error(ctx, GMC_EINVAL, "gmc_train_begin: precision must be GMC_FP32 or GMC_BF16");
+  switch (train_config_check(*cfg)) {
+    case 0: break;
+    case 1:
+    case 2: return set_error(ctx, GMC_EINVAL, "gmc_train_begin: batch in [1, 2^20], lr > 0 (finite)");
+    case 3:
+      return set_error(ctx, GMC_EINVAL, "gmc_train_begin: precision must be GMC_FP32 or GMC_BF16");
+    default:
+      return set_error(ctx, GMC_EINVAL,
+                       "gmc_train_begin: need betas in [0, 1), eps > 0, weight decay >= 0 (finite)");
+  }
   if (!ctx->net.loaded) return set_error(ctx, GMC_ENOWEIGHTS, "gmc_train_begin: load initial weights first");
   if (ctx->net.rm && cfg->precision != GMC_FP32)
     return set_error(ctx, GMC_EINVAL, "gmc_train_begin: the residual-modulated network trains at GMC_FP32");
@@ -985,7 +992,8 @@ gmc_status gmc_train_param_count_ctx(const gmc_ctx *ctx, int64_t *count) {
 gmc_status gmc_train_set_lr(gmc_ctx *ctx, double lr) {
   if (!ctx) return GMC_EINVAL;
   if (!ctx->train) return set_error(ctx, GMC_EINVAL, "gmc_train_set_lr: call gmc_train_begin first");
-  if (!(lr > 0.0)) return set_error(ctx, GMC_EINVAL, "gmc_train_set_lr: lr must be > 0");
+  if (!(lr > 0.0) || !std::isfinite(lr))
+    return set_error(ctx, GMC_EINVAL, "gmc_train_set_lr: lr must be > 0 and finite");
   ctx->train->cfg.lr = lr;
   return GMC_OK;
 }

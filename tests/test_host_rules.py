@@ -20,6 +20,8 @@ CSRC = os.path.join(ROOT, "paper_2512_13965_gb300", "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 
 WRAPPER = r'''
+#include <cstring>
+#include "ckpt.h"
 #include "host_rules.h"
 using namespace gmc;
 extern "C" {
@@ -92,6 +94,43 @@ int hr_config(int steps, int integ, int prec, double w_cut, double p_survive, lo
   c.sampler_kernel = kernel;
   return config_check(c);
 }
+int hr_data_ranges(float tl, float th, float cl, float ch, float al, float ah) {
+  return data_ranges_ok(tl, th, cl, ch, al, ah);
+}
+int hr_train_config(int batch, double lr, double b1, double b2, double eps, double wd, int prec) {
+  gmc_train_config c;
+  std::memset(&c, 0, sizeof(c));
+  c.batch = batch;
+  c.lr = lr;
+  c.beta1 = b1;
+  c.beta2 = b2;
+  c.eps = eps;
+  c.weight_decay = wd;
+  c.precision = prec;
+  return train_config_check(c);
+}
+// a checkpoint header that is valid but for the given hyperparameters
+int hr_ckpt_hyper(double lr, double b1, double b2, double eps, double wd) {
+  float st[20] = {0};
+  for (int k = 5; k < 10; ++k) st[k] = 1.0f;
+  for (int k = 14; k < 18; ++k) st[k] = 1.0f;
+  TrainCkpt h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "GMCT", 4);
+  h.version = kCkptVersion;
+  h.params = 10;
+  h.batch = 16;
+  h.n = 100;
+  h.precision = 1;
+  h.lr = lr;
+  h.beta1 = b1;
+  h.beta2 = b2;
+  h.eps = eps;
+  h.weight_decay = wd;
+  std::memcpy(h.stats, st, sizeof(st));
+  const CkptTarget t{10, 16, 100, 1, 0, 5, st};
+  return ckpt_check(h, t);
+}
 int hr_grid(long ncell, int ny, const float *tau, const float *c, const float *src, int wall,
             double *cdf, double *total, long *bad) {
   int64_t b = -1;
@@ -133,6 +172,12 @@ def lib(tmp_path_factory):
     I = ctypes.c_int
     L.hr_config.argtypes = [I, I, I, D, D, ctypes.c_longlong, I, D, D, D, D, D, I]
     L.hr_config.restype = I
+    L.hr_data_ranges.argtypes = [F] * 6
+    L.hr_data_ranges.restype = I
+    L.hr_train_config.argtypes = [I, D, D, D, D, D, I]
+    L.hr_train_config.restype = I
+    L.hr_ckpt_hyper.argtypes = [D] * 5
+    L.hr_ckpt_hyper.restype = I
     L.hr_grid.argtypes = [LG, ctypes.c_int, P, P, P, ctypes.c_int, P, P, P]
     L.hr_grid.restype = ctypes.c_int
     S = ctypes.c_size_t
@@ -405,3 +450,47 @@ def test_config_ranges(lib):
     # the first field out of range is the one reported
     assert _config(lib, steps=0, kernel=7, cap=1) == 1
     assert _config(lib, fpw=0, kernel=7) == 6
+
+
+def test_training_data_ranges(lib):
+    inf, nan = float("inf"), float("nan")
+    ok = (0.1, 1000.0, 0.5, 0.999, 1.0, 1.0)
+    assert lib.hr_data_ranges(*ok) == 1
+    for args in ((1.0, 1.0, 0.0, 1.0, 1.0, 1.0), (0.1, 1000.0, 0.5, 0.5, 0.25, 4.0),
+                 (1e-30, 1e30, 0.0, 0.0, 1.0, 1.0)):
+        assert lib.hr_data_ranges(*args) == 1, args
+    for k, v in ((0, 0.0), (0, -1.0), (0, nan), (1, 0.05), (1, inf), (1, nan), (2, -0.1),
+                 (2, nan), (3, 0.4), (3, 1.01), (3, nan), (4, 0.0), (4, nan), (5, 0.5),
+                 (5, inf)):
+        a = list(ok)
+        a[k] = v
+        assert lib.hr_data_ranges(*a) == 0, (k, v)
+
+
+def test_training_config_ranges_match_the_checkpoints(lib):
+    inf, nan = float("inf"), float("nan")
+    base = dict(batch=16384, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, wd=0.01, prec=1)
+
+    def chk(**kw):
+        c = dict(base)
+        c.update(kw)
+        return lib.hr_train_config(*c.values())
+    assert chk() == 0 and chk(batch=1) == 0 and chk(batch=1 << 20) == 0 and chk(prec=0) == 0
+    assert chk(b1=0.0, b2=0.0, wd=0.0) == 0
+    for kw, code in ((dict(batch=0), 1), (dict(batch=(1 << 20) + 1), 1), (dict(lr=0.0), 2),
+                     (dict(lr=inf), 2), (dict(lr=nan), 2), (dict(prec=2), 3), (dict(prec=-1), 3),
+                     (dict(b1=1.0), 4), (dict(b2=-1e-9), 4), (dict(eps=0.0), 4), (dict(eps=inf), 4),
+                     (dict(wd=-1.0), 4), (dict(wd=nan), 4)):
+        assert chk(**kw) == code, kw
+    # a configuration gmc_train_begin accepts writes a checkpoint whose
+    # hyperparameters a restore accepts, and the other way round
+    g = np.random.default_rng(3)
+    vals = [0.0, 1e-12, 0.5, 0.999, 1.0, 1.5, -1e-9, inf, nan]
+    seen = set()
+    for _ in range(600):
+        lr, b1, b2, eps, wd = (float(g.choice(vals)) for _ in range(5))
+        begin_ok = chk(lr=lr, b1=b1, b2=b2, eps=eps, wd=wd) == 0
+        restore_ok = lib.hr_ckpt_hyper(lr, b1, b2, eps, wd) == 0
+        assert begin_ok == restore_ok, (lr, b1, b2, eps, wd)
+        seen.add(begin_ok)
+    assert seen == {True, False}
