@@ -1,9 +1,11 @@
-// Host-side rules of a transport solve that decide what the kernels are
-// given: each cell's network condition and routing, the sizes a solve on
-// rectangular cells accepts, and the bookkeeping of the serving engine's
-// device-memory pool. Plain C++ with no CUDA headers, so a host-only unit
-// test checks them (against the oracle where it has a counterpart) without a
-// GPU.
+// Host-side rules that decide what the kernels are given: each cell's
+// network condition and routing, the checks of a solve's grid and source and
+// the source CDF births search, the sizes a solve on rectangular cells
+// accepts, the ranges of the configuration, of the training data and of the
+// training configuration the C ABI accepts, and the bookkeeping of the
+// serving engine's device-memory pool. Plain C++ with no CUDA headers (the C
+// ABI's gmc.h only), so a host-only unit test checks them (against the
+// oracle where it has a counterpart) without a GPU.
 #pragma once
 
 #include <algorithm>
