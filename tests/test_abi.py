@@ -134,3 +134,18 @@ int main() {
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     assert subprocess.run([str(exe)]).returncode == 0
+
+
+def test_header_is_plain_c(tmp_path):
+    # include/gmc.h is the boundary for C callers: it compiles as strict C99
+    # (no C++ in it) and as C++, with every warning on and none given
+    import shutil
+    import subprocess
+    inc = os.path.join(ROOT, "include", "gmc.h")
+    for cc, lang, std in (("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++17")):
+        exe = shutil.which(cc)
+        if not exe:
+            pytest.skip("needs " + cc)
+        r = subprocess.run([exe, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                            "-x", lang, inc], capture_output=True, text=True)
+        assert r.returncode == 0, (cc, r.stderr)
