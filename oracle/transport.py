@@ -781,6 +781,101 @@ def equivalent_sampler_rect(sampler, fallback, tau_range=(0.1, 1000.0), c_range=
     return f
 
 
+def internal_condition_rect(X, Y, tx, ty, c):
+    """Condition of the internal model for births in rectangular cells
+    (reading of the paper's internal model on the geometry variant with
+    W != H): the square model's five components (X, Y, ln tx, c, distance to
+    the nearest face in normalized cell units) and the aspect ln(ty / tx),
+    the same sixth component as the boundary network's -> [6, B]."""
+    X, Y, tx, ty, c = (np.asarray(a, dtype=np.float64) for a in (X, Y, tx, ty, c))
+    d = np.minimum(np.minimum(X, Y), np.minimum(1.0 - X, 1.0 - Y))
+    return np.stack([X, Y, np.log(tx), c, d, np.log(ty / tx)])
+
+
+def mlp_internal_sampler_rect(net, steps, integrator, seed):
+    """Births in rectangular cells with an internal network of six
+    condition components (internal_condition_rect): the exit in the cell's
+    own frame from the flow ODE with noise at (id, 0, TAG_NOISE); the next
+    event is 1."""
+    def f(X, Y, tx, ty, c, ids, u_angle):
+        cond = internal_condition_rect(X, Y, tx, ty, c)
+        ids = np.asarray(ids, np.uint64)
+        z = rng.normals_for(seed, ids, np.zeros(ids.size, np.uint32), rng.TAG_NOISE)
+        d = mlp.decode(net, mlp.sample(net, cond, z, steps, integrator))
+        return d["face"], d["q"], d["ux"], d["uy"], d["s"], np.ones(ids.size, np.uint32)
+    return f
+
+
+def walk_internal_sampler_rect(seed):
+    """Births in rectangular cells walked exactly as the rectangle solve
+    walks them: direction on the circle at angle 2 pi u_angle, walk_one_rect
+    from (X tx, Y ty) at event 0."""
+    def f(X, Y, tx, ty, c, ids, u_angle):
+        out = [np.zeros(len(ids)) for _ in range(5)] + [np.zeros(len(ids), np.uint32)]
+        for k in range(len(ids)):
+            ang = 2.0 * np.pi * u_angle[k]
+            r = walk_one_rect(tx[k], ty[k], c[k], MODE_IMPLICIT, X[k] * tx[k], Y[k] * ty[k],
+                              np.cos(ang), np.sin(ang), seed, int(ids[k]), 0)
+            for a, v in zip(out, (r["face"], r["q"], r["ux"], r["uy"], r["s"], r["event"])):
+                a[k] = v
+        return out[0].astype(np.int64), out[1], out[2], out[3], out[4], out[5]
+    return f
+
+
+def equivalent_internal_sampler_rect(internal, fallback, tau_range=(0.1, 1000.0),
+                                     c_range=(0.5, 0.999)):
+    """equivalent_internal_sampler for rectangular cells: births in cells with
+    an equivalent condition (equivalent_condition_rect) sampled by `internal`
+    at (tx', ty', c') with s scaled by c'/c, the others by `fallback` at their
+    own condition."""
+    def f(X, Y, tx, ty, c, ids, u_angle):
+        X, Y, tx, ty, c = (np.asarray(a, dtype=np.float64) for a in (X, Y, tx, ty, c))
+        ids = np.asarray(ids, dtype=np.uint64)
+        u_angle = np.asarray(u_angle, dtype=np.float64)
+        txp, cp, ok = equivalent_condition_rect(tx, ty, c, tau_range, c_range)
+        typ = txp * (ty / tx)
+        n = X.shape[0]
+        face = np.zeros(n, np.int64)
+        q, ux, uy, s = (np.zeros(n) for _ in range(4))
+        ev = np.zeros(n, np.uint32)
+        for sel, fn, a, b, cc in ((ok, internal, txp, typ, cp), (~ok, fallback, tx, ty, c)):
+            k = np.nonzero(sel)[0]
+            if k.size == 0:
+                continue
+            fa, qa, uxa, uya, sa, eva = fn(X[k], Y[k], a[k], b[k], cc[k], ids[k], u_angle[k])
+            face[k], q[k], ux[k], uy[k], ev[k] = fa, qa, uxa, uya, eva
+            s[k] = np.asarray(sa) * (cc[k] / c[k]) if fn is internal else sa
+        return face, q, ux, uy, s, ev
+    return f
+
+
+def internal_pairs_rect(n, seed, tau_range=(0.1, 1000.0), aspect_range=(0.25, 4.0),
+                        c_range=(0.5, 0.999)):
+    """Training pairs of the internal model for rectangular cells: for
+    sample i, the draw (i, 0, tag 11) gives ln tx uniform in the log range, c
+    uniform, X and Y uniform; (i, 1, tag 11) the aspect ty / tx log-uniform in
+    aspect_range (u0) and the birth direction at angle 2 pi u1 on the circle;
+    the implicit-capture walk in the rectangle from (X tx, Y ty) draws from
+    event 2. Returns cond [6, n] (internal_condition_rect) and y [4, n] =
+    (p, ux, uy, ln s) in the cell's own frame, q normalized per face."""
+    ids = np.arange(n, dtype=np.uint64)
+    u0 = rng.uniforms_for(seed, ids, np.zeros(n, np.uint32), 11)
+    u1 = rng.uniforms_for(seed, ids, np.ones(n, np.uint32), 11)
+    lo, hi = np.log(tau_range[0]), np.log(tau_range[1])
+    tx = np.exp(lo + (hi - lo) * u0[0])
+    c = c_range[0] + (c_range[1] - c_range[0]) * u0[1]
+    X, Y = u0[2], u0[3]
+    alo, ahi = np.log(aspect_range[0]), np.log(aspect_range[1])
+    ty = tx * np.exp(alo + (ahi - alo) * u1[0])
+    ang = 2.0 * np.pi * u1[1]
+    y = np.zeros((4, n))
+    for i in range(n):
+        w = walk_one_rect(tx[i], ty[i], c[i], MODE_IMPLICIT, X[i] * tx[i], Y[i] * ty[i],
+                          np.cos(ang[i]), np.sin(ang[i]), seed, i, 2)
+        y[:, i] = (w["face"] + w["q"], w["ux"], w["uy"], np.log(max(w["s"], mlp.S_MIN)))
+    return internal_condition_rect(X, Y, tx, ty, c), y
+
+
 def walk_sampler_rect(seed):
     """Stage 2 replaced by the implicit-capture walk in the canonical frame of
     a rectangular cell, as the training pairs take it (transmit_rect: entry
@@ -822,7 +917,7 @@ def walk_sampler_global_rect(seed):
 
 
 def solve_gmc_rect(sigma, c, src, dx, dy, n_hist, seed, sampler, w_cut=1e-4, p_survive=0.1,
-                   max_waves=100000, wall=None):
+                   max_waves=100000, wall=None, internal=None):
     """The event-based solve on a grid of rectangular cells of physical size
     dx x dy (every cell alike) with cross sections sigma [ny, nx] and
     scattering ratios c: cell (i, j) has optical sides tx = sigma dx (along x)
@@ -836,7 +931,10 @@ def solve_gmc_rect(sigma, c, src, dx, dy, n_hist, seed, sampler, w_cut=1e-4, p_s
     wall: [ny] strengths of a surface source on the left boundary instead of
     src (wall_births: row by strength, uniform height on the boundary cell's
     left face, the cosine law; weight 1, next event 0); its first crossing
-    goes to `sampler` like every later one."""
+    goes to `sampler` like every later one.
+    internal: sampler of births (mlp_internal_sampler_rect,
+    walk_internal_sampler_rect) called as internal(X, Y, tx, ty, c, ids,
+    u_angle), or None to walk every birth."""
     sig = np.asarray(sigma, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)
     ny, nx = sig.shape
@@ -861,10 +959,17 @@ def solve_gmc_rect(sigma, c, src, dx, dy, n_hist, seed, sampler, w_cut=1e-4, p_s
         ub = rng.uniforms_for(seed, ids, np.zeros(n_hist, np.uint32), rng.TAG_BIRTH)
         cells = np.searchsorted(cdf, ub[0] * cdf[-1], side="left")
         bux, buy = birth_directions(seed, ids, ub[3], "flat")
+    if internal is not None and n_src > 0:
+        bf, bq, bux_, buy_, bs, bev = internal(ub[1], ub[2], txf[cells], tyf[cells], cf[cells], ids,
+                                               ub[3])
     for h in range(n_src):
         k = int(cells[h])
-        r = walk_one_rect(txf[k], tyf[k], cf[k], MODE_IMPLICIT, ub[1, h] * txf[k], ub[2, h] * tyf[k],
-                          bux[h], buy[h], seed, h, 0)
+        if internal is not None:
+            r = {"face": int(bf[h]), "q": bq[h], "ux": bux_[h], "uy": buy_[h], "s": bs[h],
+                 "event": int(bev[h]), "ncoll": 0}
+        else:
+            r = walk_one_rect(txf[k], tyf[k], cf[k], MODE_IMPLICIT, ub[1, h] * txf[k],
+                              ub[2, h] * tyf[k], bux[h], buy[h], seed, h, 0)
         st[3] += 1
         st[4] += r["ncoll"]
         dw, score = deposit(1.0, r["s"], sf[k], cf[k])

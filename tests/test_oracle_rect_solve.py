@@ -313,3 +313,79 @@ def test_walk_solve_at_rect_equivalent_conditions_is_the_walk_solve():
                               OT.equivalent_sampler_rect(w, w, *BOX))
     np.testing.assert_allclose(b, a, rtol=1e-9, atol=1e-15)
     assert sa["transmissions"] == sb["transmissions"]
+
+
+def test_walked_births_through_the_rect_internal_path_are_the_walked_births():
+    # internal = walk_internal_sampler_rect draws exactly what the rectangle
+    # solve's own birth walk draws: same flux and transmissions per history
+    sig = np.array([[1.4, 4.0, 0.8], [3.0, 0.6, 2.2]])
+    c = np.array([[0.9, 0.6, 0.99], [0.5, 0.95, 0.8]])
+    src = np.array([[0.3, 1.0, 0.0], [0.5, 0.0, 0.7]])
+    w = OT.walk_sampler_rect(13)
+    a, sa = OT.solve_gmc_rect(sig, c, src, 0.5, 1.5, 600, 13, w)
+    b, sb = OT.solve_gmc_rect(sig, c, src, 0.5, 1.5, 600, 13, w,
+                              internal=OT.walk_internal_sampler_rect(13))
+    np.testing.assert_allclose(b, a, rtol=1e-12, atol=0)
+    assert sa["transmissions"] == sb["transmissions"] and sa["leak"] == sb["leak"]
+
+
+def test_rect_internal_condition_by_hand():
+    cond = OT.internal_condition_rect([0.25, 0.9], [0.5, 0.05], [2.0, 0.5], [8.0, 0.5], [0.7, 1.0])
+    np.testing.assert_allclose(cond[:, 0], [0.25, 0.5, np.log(2.0), 0.7, 0.25, np.log(4.0)])
+    np.testing.assert_allclose(cond[:, 1], [0.9, 0.05, np.log(0.5), 1.0, 0.05, 0.0])
+
+
+def test_rect_internal_pairs_straight_chords():
+    # c = 0: no flight ends inside, the exit is the straight chord from the
+    # birth point (X tx, Y ty) along the birth direction
+    cond, y = OT.internal_pairs_rect(400, 5, tau_range=(0.5, 3.0), aspect_range=(0.2, 5.0),
+                                     c_range=(0.0, 0.0))
+    X, Y, tx, d, asp = cond[0], cond[1], np.exp(cond[2]), cond[4], np.exp(cond[5])
+    ty = tx * asp
+    ux, uy = y[1], y[2]
+    l = np.exp(y[3])
+    np.testing.assert_allclose(np.hypot(ux, uy), 1.0, atol=1e-12)
+    np.testing.assert_allclose(l, _chord2(X * tx, Y * ty, ux, uy, tx, ty), rtol=1e-9)
+    ex, ey = X * tx + l * ux, Y * ty + l * uy
+    face = np.floor(y[0]).astype(int)
+    q = y[0] - face
+    along = np.select([face == 0, face == 1, face == 2, face == 3],
+                      [ex / tx, ey / ty, (tx - ex) / tx, (ty - ey) / ty])
+    np.testing.assert_allclose(q, along, atol=1e-9)
+    np.testing.assert_allclose(d, np.minimum(np.minimum(X, Y), np.minimum(1 - X, 1 - Y)))
+    assert asp.min() >= 0.2 - 1e-12 and asp.max() <= 5.0 + 1e-12 and len(set(face)) == 4
+
+
+def test_rect_internal_births_at_equivalent_conditions_are_the_walked_births():
+    # births walked at their cell's equivalent condition (the internal path)
+    # and crossings walked at equivalent conditions equal the plain walk
+    # solve history by history; cells without an equivalent take the
+    # fallback; births in mapped cells and in cells without an equivalent
+    sig = np.array([[0.5, 3.0, 40.0], [8.0, 0.8, 20.0]])
+    c = np.array([[0.9, 1.0, 0.05], [0.02, 0.95, 0.6]])
+    src = np.array([[1.0, 0.5, 0.5], [0.5, 1.0, 0.0]])
+    dx, dy = 0.1, 1.6
+    w, wi = OT.walk_sampler_rect(23), OT.walk_internal_sampler_rect(23)
+    a, sa = OT.solve_gmc_rect(sig, c, src, dx, dy, 1000, 23, w)
+    b, sb = OT.solve_gmc_rect(sig, c, src, dx, dy, 1000, 23, OT.equivalent_sampler_rect(w, w, *BOX),
+                              internal=OT.equivalent_internal_sampler_rect(wi, wi, *BOX))
+    np.testing.assert_allclose(b, a, rtol=1e-9, atol=1e-15)
+    assert sa["transmissions"] == sb["transmissions"]
+
+
+def test_rect_solve_with_an_internal_network_balances(tmp_path):
+    # a six-component network (the rectangular-cell layout) as the internal
+    # model: finite flux, exact weight balance, the Eq. 7 tally identity
+    p = str(tmp_path / "ri.bin")
+    synth.write_weights(p, synth.kaiming_weights_rect(3))
+    net = mlp.read_weights(p)
+    sig = np.array([[1.0, 3.0], [0.5, 2.0]])
+    c = np.array([[0.9, 0.7], [0.99, 0.5]])
+    src = np.array([[1.0, 0.0], [0.5, 0.5]])
+    n = 300
+    f, st = OT.solve_gmc_rect(sig, c, src, 2.0, 0.5, n, 11, OT.mlp_sampler_rect(net, 4, "euler", 11),
+                              internal=OT.mlp_internal_sampler_rect(net, 4, "euler", 11))
+    assert np.all(np.isfinite(f)) and f.sum() > 0
+    assert abs(st["leak"] + st["absorbed"] - st["roulette_net"] - n) < 1e-6 * n
+    sig_a = (1.0 - c) * sig
+    assert abs(np.sum(f * sig_a) * 2.0 * 0.5 * n - st["absorbed"]) < 1e-8 * n
