@@ -391,6 +391,30 @@ def walk_internal_sampler(seed):
     return f
 
 
+def internal_pairs(n, seed, tau_range=(0.1, 1000.0), c_range=(0.5, 0.999)):
+    """Training pairs of the internal model ("Network Architecture and
+    Inputs": births inside a cell, the implicit-capture walk to the exit):
+    for sample i, the draw (i, 0, tag 7) gives ln tau uniform in the log
+    range, c uniform, X and Y uniform; (i, 1, tag 7) the birth direction at
+    angle 2 pi u0 on the circle; the walk draws from event 2. Returns cond
+    [5, n] (internal_condition) and y [4, n] = (p, ux, uy, ln s) in the
+    cell's own frame, in FP64."""
+    ids = np.arange(n, dtype=np.uint64)
+    u0 = rng.uniforms_for(seed, ids, np.zeros(n, np.uint32), 7)
+    u1 = rng.uniforms_for(seed, ids, np.ones(n, np.uint32), 7)
+    lo, hi = np.log(tau_range[0]), np.log(tau_range[1])
+    tau = np.exp(lo + (hi - lo) * u0[0])
+    c = c_range[0] + (c_range[1] - c_range[0]) * u0[1]
+    X, Y = u0[2], u0[3]
+    ang = 2.0 * np.pi * u1[0]
+    y = np.zeros((4, n))
+    for i in range(n):
+        w = walk_one(tau[i], c[i], MODE_IMPLICIT, X[i] * tau[i], Y[i] * tau[i], np.cos(ang[i]),
+                     np.sin(ang[i]), seed, i, 2)
+        y[:, i] = (w["face"] + w["q"], w["ux"], w["uy"], np.log(max(w["s"], mlp.S_MIN)))
+    return internal_condition(X, Y, tau, c), y
+
+
 def mlp_internal_sampler_xy(net, steps, integrator, seed):
     """mlp_internal_sampler for x-y geometry: the x-y internal model's exit,
     decoded into the unit disk (decode_disk)."""

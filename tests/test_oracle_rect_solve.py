@@ -389,3 +389,22 @@ def test_rect_solve_with_an_internal_network_balances(tmp_path):
     assert abs(st["leak"] + st["absorbed"] - st["roulette_net"] - n) < 1e-6 * n
     sig_a = (1.0 - c) * sig
     assert abs(np.sum(f * sig_a) * 2.0 * 0.5 * n - st["absorbed"]) < 1e-8 * n
+
+
+def test_internal_pairs_straight_chords_and_the_rectangle_at_aspect_one():
+    # square cells' internal pairs: at c = 0 the exit is the straight chord
+    # from the birth point; and the rectangle walk with equal sides, started
+    # from the same point, direction and counters, gives the same exits
+    cond, y = OT.internal_pairs(300, 7, tau_range=(0.5, 3.0), c_range=(0.0, 0.0))
+    X, Y, tau = cond[0], cond[1], np.exp(cond[2])
+    l = np.exp(y[3])
+    np.testing.assert_allclose(l, _chord2(X * tau, Y * tau, y[1], y[2], tau, tau), rtol=1e-9)
+    cond, y = OT.internal_pairs(200, 8, tau_range=(0.3, 30.0))
+    X, Y, tau, c = cond[0], cond[1], np.exp(cond[2]), cond[3]
+    u1 = OT.rng.uniforms_for(8, np.arange(200, dtype=np.uint64), np.ones(200, np.uint32), 7)
+    for i in range(200):
+        a = 2 * np.pi * u1[0, i]
+        w = OT.walk_one_rect(tau[i], tau[i], c[i], OT.MODE_IMPLICIT, X[i] * tau[i], Y[i] * tau[i],
+                             np.cos(a), np.sin(a), 8, i, 2)
+        np.testing.assert_allclose(y[:, i], [w["face"] + w["q"], w["ux"], w["uy"], np.log(w["s"])],
+                                   rtol=1e-12, atol=1e-12)
